@@ -1,0 +1,252 @@
+"""Oracle for the event-chain (EC) Monte Carlo move of tethered hard-sphere
+bead chains (arXiv:1502.06447, Sec. II and Sec. II.B-D).
+
+TEST INFRASTRUCTURE ONLY.  This is the plain, serial, FP64 checker that the
+CUDA library is compared against.  Only ``tests/``, ``__graft_entry__.smoke()``
+and the ``cpu_baseline`` / ``--impl reference`` legs of ``bench.py`` may import
+it.  It shares no code with the CUDA library (own Philox4x64-10, own geometry,
+own cell list) and neither side imports the other.
+
+The arithmetic lives in ``ecmc_oracle.c`` (compiled with
+``-O2 -ffp-contract=off``: every FP64 expression evaluated as written, no
+fused multiply-add).  This module is ctypes marshalling only.
+
+Functions and the passage each follows:
+  run_serial / run_domain   EC move, Sec. II (four-step rule, min over
+                            partners); tile-joint decomposition and
+                            reflections, Sec. II.B, Fig. 2c; swap, Sec. II.D
+  domain_tags               tile-joint partition, Sec. II.B
+  lattice                   initial lattice melt (a reading: the paper grows
+                            random walks instead; the lattice start is the
+                            workload's stated synthetic input)
+  chain_obs                 end-to-end distance R_e^2 (Sec. III), bond lengths
+  min_pair                  hard-sphere constraint check, Eq. 1
+All functions are pinned by ``tests/test_oracle_pins.py``.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = [os.path.join(_HERE, "ecmc_oracle.c")]
+_HDR = [os.path.join(_HERE, "orc.h")]
+_SO = os.path.join(_HERE, "_liboracle.so")
+_lock = threading.Lock()
+_lib = None
+
+MODE_SERIAL, MODE_DOMAIN = 0, 1
+DIR_CART3, DIR_ISO, DIR_PLUSX = 0, 1, 2
+OUT_NAMES = ("end", "pass", "wall", "hs_lift", "hs_reflect", "te_lift",
+             "te_reflect", "swap")
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle with gcc (no fused multiply-add, IEEE FP64)."""
+    newest = max(os.path.getmtime(p) for p in _SRC + _HDR)
+    if force or not os.path.exists(_SO) or os.path.getmtime(_SO) < newest:
+        tmp = _SO + ".%d.tmp" % os.getpid()
+        cmd = ["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math",
+               "-fPIC", "-shared", "-o", tmp] + _SRC + ["-lm"]
+        subprocess.run(cmd, check=True)
+        os.replace(tmp, _SO)
+    return _SO
+
+
+class Params(C.Structure):
+    _fields_ = [
+        ("n", C.c_int64), ("N", C.c_int32), ("mode", C.c_int32),
+        ("L", C.c_double * 3), ("sigma", C.c_double), ("b_max", C.c_double),
+        ("s_cap", C.c_double), ("dir_mode", C.c_int32), ("D", C.c_int32 * 3),
+        ("w", C.c_double), ("p_swap", C.c_double), ("event_cap", C.c_int64),
+        ("use_cells", C.c_int32), ("ecs_per_tile", C.c_int32),
+        ("seed", C.c_uint64), ("replica", C.c_uint64),
+    ]
+
+
+class Stats(C.Structure):
+    _fields_ = [
+        ("ecs", C.c_int64), ("events", C.c_int64), ("out", C.c_int64 * 8),
+        ("swap_tried", C.c_int64), ("lift_sum", C.c_double),
+        ("refl_sum", C.c_double), ("disp_sum", C.c_double),
+        ("status", C.c_int64),
+    ]
+
+    def as_dict(self) -> dict:
+        d = {"ecs": self.ecs, "events": self.events,
+             "swap_tried": self.swap_tried, "lift_sum": self.lift_sum,
+             "refl_sum": self.refl_sum, "disp_sum": self.disp_sum,
+             "status": self.status}
+        for k, name in enumerate(OUT_NAMES):
+            d[name] = self.out[k]
+        return d
+
+
+EVENT_DTYPE = np.dtype([("unit", "<i8"), ("pivot", "<i4"), ("kind", "<i4"),
+                        ("partner", "<i8"), ("x", "<f8")])
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is None:
+            lib = C.CDLL(build())
+            P = C.POINTER
+            lib.orc_philox4x64_10.argtypes = [P(C.c_uint64), P(C.c_uint64), P(C.c_uint64)]
+            lib.orc_philox4x64_10.restype = None
+            run_args = [P(Params), P(C.c_double), P(C.c_int32), C.c_int64, C.c_int64,
+                        C.c_double, P(Stats), P(C.c_uint64), P(C.c_double),
+                        P(C.c_int64), C.c_void_p, C.c_int64, P(C.c_int64)]
+            lib.orc_run_serial.argtypes = run_args
+            lib.orc_run_domain.argtypes = run_args
+            lib.orc_run_serial.restype = C.c_int
+            lib.orc_run_domain.restype = C.c_int
+            lib.orc_domain_tags.argtypes = [P(Params), P(C.c_double), C.c_uint64,
+                                            P(C.c_int32), P(C.c_double)]
+            lib.orc_lattice.argtypes = [P(C.c_int32), C.c_double, C.c_double, C.c_uint64,
+                                        C.c_uint64, P(C.c_double)]
+            lib.orc_chain_obs.argtypes = [P(Params), P(C.c_double), P(C.c_double),
+                                          P(C.c_double)]
+            lib.orc_min_pair.argtypes = [P(Params), P(C.c_double), P(C.c_double),
+                                         P(C.c_int64)]
+            lib.orc_min_pair_cells.argtypes = lib.orc_min_pair.argtypes
+            lib.orc_start_draws.argtypes = [P(Params), C.c_int64, C.c_int64, P(C.c_int64),
+                                            P(C.c_double)]
+            _lib = lib
+    return _lib
+
+
+def _ptr(a, ct):
+    return a.ctypes.data_as(C.POINTER(ct))
+
+
+def philox4x64_10(ctr, key) -> np.ndarray:
+    lib = _load()
+    c = np.ascontiguousarray(ctr, dtype=np.uint64)
+    k = np.ascontiguousarray(key, dtype=np.uint64)
+    out = np.zeros(4, dtype=np.uint64)
+    lib.orc_philox4x64_10(_ptr(c, C.c_uint64), _ptr(k, C.c_uint64), _ptr(out, C.c_uint64))
+    return out
+
+
+def lattice(dims, a: float, jitter: float = 0.0, seed: int = 0, replica: int = 0) -> np.ndarray:
+    """Snake-ordered simple-cubic lattice, optionally jittered (Philox tag 4)."""
+    lib = _load()
+    d = np.asarray(dims, dtype=np.int32)
+    r = np.zeros((int(np.prod(d)), 3), dtype=np.float64)
+    lib.orc_lattice(_ptr(d, C.c_int32), float(a), float(jitter), int(seed) & (2**64 - 1),
+                    int(replica) & (2**64 - 1), _ptr(r, C.c_double))
+    return r
+
+
+class System:
+    """One melt: positions (n,3) wrapped in [0,L), image counters, parameters."""
+
+    def __init__(self, r, L, N, sigma=1.0, b_max=1.2, s_cap=0.25, mode=MODE_SERIAL,
+                 dir_mode=DIR_CART3, D=(1, 1, 1), w=None, p_swap=0.0,
+                 event_cap=10_000_000, use_cells=1, ecs_per_tile=1, seed=0,
+                 replica=0, img=None):
+        self.r = np.ascontiguousarray(r, dtype=np.float64).reshape(-1, 3).copy()
+        self.img = (np.zeros_like(self.r, dtype=np.int32) if img is None
+                    else np.ascontiguousarray(img, dtype=np.int32).reshape(-1, 3).copy())
+        p = Params()
+        p.n = self.r.shape[0]
+        p.N = int(N)
+        p.mode = int(mode)
+        Lv = np.broadcast_to(np.asarray(L, dtype=np.float64), (3,))
+        for a in range(3):
+            p.L[a] = float(Lv[a])
+            p.D[a] = int(np.broadcast_to(np.asarray(D), (3,))[a])
+        p.sigma = float(sigma)
+        p.b_max = float(b_max)
+        p.s_cap = float(s_cap)
+        p.dir_mode = int(dir_mode)
+        p.w = float(b_max if w is None else w)
+        p.p_swap = float(p_swap)
+        p.event_cap = int(event_cap)
+        p.use_cells = int(use_cells)
+        p.ecs_per_tile = int(ecs_per_tile)
+        p.seed = int(seed) & (2**64 - 1)
+        p.replica = int(replica) & (2**64 - 1)
+        self.P = p
+
+    @property
+    def L(self) -> np.ndarray:
+        return np.array([self.P.L[0], self.P.L[1], self.P.L[2]])
+
+    def _run(self, fn, start, count, ell, digests, log_cap, units):
+        lib = _load()
+        st = Stats()
+        dig = np.zeros(units, dtype=np.uint64) if digests else None
+        lift = np.zeros(units, dtype=np.float64) if digests else None
+        nev = np.zeros(units, dtype=np.int64) if digests else None
+        log = np.zeros(max(log_cap, 1), dtype=EVENT_DTYPE) if log_cap else None
+        log_n = C.c_int64(0)
+        rc = fn(C.byref(self.P), _ptr(self.r, C.c_double), _ptr(self.img, C.c_int32),
+                int(start), int(count), float(ell), C.byref(st),
+                _ptr(dig, C.c_uint64) if dig is not None else None,
+                _ptr(lift, C.c_double) if lift is not None else None,
+                _ptr(nev, C.c_int64) if nev is not None else None,
+                log.ctypes.data if log is not None else None, int(log_cap),
+                C.byref(log_n))
+        res = {"rc": rc, "stats": st.as_dict()}
+        if digests:
+            res.update(digest=dig, ec_lift=lift, ec_events=nev)
+        if log is not None:
+            res["log"] = log[: log_n.value]
+        return res
+
+    def run_serial(self, n_ec, ell, ec0=0, digests=False, log_cap=0):
+        """n_ec serial ECs of length ell (Sec. II); ECs numbered from ec0."""
+        return self._run(_load().orc_run_serial, ec0, n_ec, ell, digests, log_cap,
+                         int(n_ec))
+
+    def run_domain(self, n_sweeps, ell, sweep0=0, digests=False, log_cap=0):
+        """Domain-decomposed sweeps (Sec. II.B), one EC per tile per sweep x
+        ecs_per_tile; sweeps numbered from sweep0."""
+        nt = self.P.D[0] * self.P.D[1] * self.P.D[2]
+        units = int(n_sweeps) * nt * self.P.ecs_per_tile
+        return self._run(_load().orc_run_domain, sweep0, n_sweeps, ell, digests,
+                         log_cap, units)
+
+    def domain_tags(self, sweep):
+        lib = _load()
+        tags = np.zeros(self.r.shape[0], dtype=np.int32)
+        shift = np.zeros(3, dtype=np.float64)
+        lib.orc_domain_tags(C.byref(self.P), _ptr(self.r, C.c_double), int(sweep),
+                            _ptr(tags, C.c_int32), _ptr(shift, C.c_double))
+        return tags, shift
+
+    def chain_obs(self):
+        lib = _load()
+        nch = self.r.shape[0] // self.P.N
+        re2 = np.zeros(nch)
+        bonds = np.zeros(max(nch * (self.P.N - 1), 1))
+        lib.orc_chain_obs(C.byref(self.P), _ptr(self.r, C.c_double), _ptr(re2, C.c_double),
+                          _ptr(bonds, C.c_double))
+        return re2, bonds[: nch * (self.P.N - 1)]
+
+    def min_pair(self, cells=None):
+        lib = _load()
+        dmin = C.c_double(0)
+        cnt = C.c_int64(0)
+        use_cells = self.r.shape[0] > 3000 if cells is None else cells
+        fn = lib.orc_min_pair_cells if use_cells else lib.orc_min_pair
+        fn(C.byref(self.P), _ptr(self.r, C.c_double), C.byref(dmin), C.byref(cnt))
+        return dmin.value, cnt.value
+
+    def start_draws(self, n, ec0=0):
+        """Start bead and direction of serial ECs ec0..ec0+n-1."""
+        lib = _load()
+        idx = np.zeros(int(n), dtype=np.int64)
+        v = np.zeros((int(n), 3), dtype=np.float64)
+        lib.orc_start_draws(C.byref(self.P), int(ec0), int(n), _ptr(idx, C.c_int64),
+                            _ptr(v, C.c_double))
+        return idx, v
+
+    def unwrapped(self):
+        return self.r + self.img * self.L

@@ -1,0 +1,828 @@
+/*
+ * Oracle for the event-chain Monte Carlo move of tethered hard-sphere chains
+ * (arXiv:1502.06447).  TEST INFRASTRUCTURE ONLY: see orc.h.
+ *
+ * What it follows:
+ *   - EC move, Sec. II (the four-step rule): pick pivot and direction v, move
+ *     the pivot by the largest admissible x <= x_max, hand the move to the
+ *     bead that limits it, repeat until x_max = 0.
+ *   - Min-over-partners rule, Sec. II: with several interaction partners the
+ *     admissible displacement is the minimum over partners and the chain is
+ *     continued at the partner realising it.  For tethers of length b_max
+ *     (Sec. II, model paragraph) the partner limit is where the bond becomes
+ *     taut; hard spheres (Eq. 1) limit at contact.
+ *   - Parallelisation, Sec. II.B: a spatial decomposition re-drawn every
+ *     sweep, tile-joint partition, reflection of the EC at cell walls and, for
+ *     a bond partner that cannot move, reflection of v at the plane normal to
+ *     the bond (Fig. 2c); the same reflection at a hard-sphere contact with a
+ *     bead that cannot move.
+ *   - Swap move, Sec. II.D: at hard-sphere contact a swap of the two touching
+ *     beads is proposed and accepted by Metropolis (infinite tether walls:
+ *     accept iff every bond stays <= b_max); accepted -> beads exchanged and
+ *     the same pivot continues; rejected -> ordinary transfer.
+ * Readings where the paper is silent (the tie order, the pass event, the
+ * random-number layout, the joint width) are the same as the CUDA library's
+ * and are written out at each place below.
+ *
+ * Compiled with -O2 -ffp-contract=off: every FP64 expression is evaluated
+ * exactly as written, in IEEE round-to-nearest, no fused multiply-add.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include "orc.h"
+
+/* ---------------------------------------------------------------------
+ * Philox4x64-10 (Salmon, Moraes, Dror, Shaw, "Parallel random numbers: as
+ * easy as 1, 2, 3", SC'11).  Round: two 64x64->128 products of the even
+ * counter words with the round multipliers, the high halves xor-ed with the
+ * odd words and the key, words permuted; the key is bumped by the Weyl
+ * constants between rounds.
+ * ------------------------------------------------------------------- */
+#define PH_M0 0xD2E7470EE14C6C93ULL
+#define PH_M1 0xCA5A826395121157ULL
+#define PH_W0 0x9E3779B97F4A7C15ULL
+#define PH_W1 0xBB67AE8584CAA73BULL
+
+void orc_philox4x64_10(const uint64_t ctr[4], const uint64_t key[2],
+                       uint64_t out[4]) {
+  uint64_t x0 = ctr[0], x1 = ctr[1], x2 = ctr[2], x3 = ctr[3];
+  uint64_t k0 = key[0], k1 = key[1];
+  for (int r = 0; r < 10; ++r) {
+    unsigned __int128 p0 = (unsigned __int128)PH_M0 * x0;
+    unsigned __int128 p1 = (unsigned __int128)PH_M1 * x2;
+    uint64_t hi0 = (uint64_t)(p0 >> 64), lo0 = (uint64_t)p0;
+    uint64_t hi1 = (uint64_t)(p1 >> 64), lo1 = (uint64_t)p1;
+    uint64_t y0 = hi1 ^ x1 ^ k0;
+    uint64_t y1 = lo1;
+    uint64_t y2 = hi0 ^ x3 ^ k1;
+    uint64_t y3 = lo0;
+    x0 = y0; x1 = y1; x2 = y2; x3 = y3;
+    k0 += PH_W0;
+    k1 += PH_W1;
+  }
+  out[0] = x0; out[1] = x1; out[2] = x2; out[3] = x3;
+}
+
+/* random-number layout (a reading; the paper fixes none):
+ *   key  = (seed, replica)
+ *   ctr  = (tag | ec<<8, sweep, unit, attempt)
+ *   tag 1: start bead + direction; tag 2: domain shift; tag 3: swap draws */
+enum { TAG_START = 1, TAG_SHIFT = 2, TAG_SWAP = 3 };
+
+static void draw(const orc_params *P, uint64_t tag, uint64_t sweep,
+                 uint64_t unit, uint64_t attempt, uint64_t out[4]) {
+  uint64_t ctr[4] = {tag, sweep, unit, attempt};
+  uint64_t key[2] = {P->seed, P->replica};
+  orc_philox4x64_10(ctr, key, out);
+}
+
+/* uniform double in [0,1) from the top 53 bits */
+static double u53(uint64_t w) { return (double)(w >> 11) * 0x1.0p-53; }
+
+/* floor(w * m / 2^64): uniform integer in [0, m) */
+static int64_t below(uint64_t w, int64_t m) {
+  return (int64_t)(((unsigned __int128)w * (uint64_t)m) >> 64);
+}
+
+/* ---------------------------------------------------------------------
+ * geometry
+ * ------------------------------------------------------------------- */
+static double minimg(double d, double L) {
+  double h = 0.5 * L;
+  if (d > h) d -= L;
+  else if (d < -h) d += L;
+  return d;
+}
+
+/* r += x v on one axis, then back into [0,L) with the image counter */
+static void advance(double *r, int32_t *img, double x, double v, double L) {
+  double y = *r + x * v;
+  if (y >= L) {
+    y -= L;
+    *img += 1;
+  } else if (y < 0.0) {
+    y += L;
+    *img -= 1;
+    if (y >= L) { /* -tiny + L rounded up to L */
+      y = 0.0;
+      *img += 1;
+    }
+  }
+  *r = y;
+}
+
+/* ---------------------------------------------------------------------
+ * state
+ * ------------------------------------------------------------------- */
+typedef struct {
+  orc_params P;
+  double *r;       /* 3n */
+  int32_t *img;    /* 3n */
+  /* own cell list (doubly linked, always current) */
+  int nc[3];
+  double cs[3];
+  int32_t *head, *next, *prev, *cell;
+  /* domain mode */
+  int32_t *tag;    /* tile of each bead this sweep, -1 = joint */
+  double shift[3], T[3], W[3];
+  /* output */
+  orc_stats *st;
+  orc_event *log;
+  int64_t log_cap, *log_n;
+  uint64_t *digest;   /* per EC, or NULL */
+  double *ec_lift;    /* per EC lift sum, or NULL */
+  int64_t *ec_events; /* per EC event count, or NULL */
+} ctx_t;
+
+static int cell_of(const ctx_t *c, int64_t b) {
+  int id[3];
+  for (int a = 0; a < 3; ++a) {
+    int k = (int)(c->r[3 * b + a] / c->cs[a]);
+    if (k >= c->nc[a]) k = c->nc[a] - 1;
+    if (k < 0) k = 0;
+    id[a] = k;
+  }
+  return (id[2] * c->nc[1] + id[1]) * c->nc[0] + id[0];
+}
+
+static void cell_insert(ctx_t *c, int64_t b, int ci) {
+  c->cell[b] = ci;
+  c->prev[b] = -1;
+  c->next[b] = c->head[ci];
+  if (c->head[ci] >= 0) c->prev[c->head[ci]] = (int32_t)b;
+  c->head[ci] = (int32_t)b;
+}
+
+static void cell_remove(ctx_t *c, int64_t b) {
+  int ci = c->cell[b];
+  if (c->prev[b] >= 0) c->next[c->prev[b]] = c->next[b];
+  else c->head[ci] = c->next[b];
+  if (c->next[b] >= 0) c->prev[c->next[b]] = c->prev[b];
+}
+
+static void cell_update(ctx_t *c, int64_t b) {
+  if (!c->P.use_cells) return;
+  int ci = cell_of(c, b);
+  if (ci != c->cell[b]) {
+    cell_remove(c, b);
+    cell_insert(c, b, ci);
+  }
+}
+
+static int ctx_init(ctx_t *c, const orc_params *P, double *r, int32_t *img) {
+  memset(c, 0, sizeof(*c));
+  c->P = *P;
+  c->r = r;
+  c->img = img;
+  if (c->P.use_cells) {
+    /* cell side >= (s_cap + sigma)(1 + 1e-9): every bead that can be hit
+     * within one free flight sits in the 27 cells around the pivot */
+    double reach = (P->s_cap + P->sigma) * (1.0 + 1e-9);
+    int64_t ncell = 1;
+    for (int a = 0; a < 3; ++a) {
+      c->nc[a] = (int)floor(P->L[a] / reach);
+      if (c->nc[a] < 3) {
+        c->P.use_cells = 0;
+        break;
+      }
+      c->cs[a] = P->L[a] / c->nc[a];
+      ncell *= c->nc[a];
+    }
+    if (c->P.use_cells) {
+      c->head = (int32_t *)malloc(sizeof(int32_t) * ncell);
+      c->next = (int32_t *)malloc(sizeof(int32_t) * P->n);
+      c->prev = (int32_t *)malloc(sizeof(int32_t) * P->n);
+      c->cell = (int32_t *)malloc(sizeof(int32_t) * P->n);
+      for (int64_t i = 0; i < ncell; ++i) c->head[i] = -1;
+      for (int64_t b = P->n - 1; b >= 0; --b) cell_insert(c, b, cell_of(c, b));
+    }
+  }
+  c->tag = (int32_t *)malloc(sizeof(int32_t) * (P->n > 0 ? P->n : 1));
+  for (int64_t b = 0; b < P->n; ++b) c->tag[b] = 0;
+  return ORC_OK;
+}
+
+static void ctx_free(ctx_t *c) {
+  free(c->head);
+  free(c->next);
+  free(c->prev);
+  free(c->cell);
+  free(c->tag);
+}
+
+/* ---------------------------------------------------------------------
+ * candidate search
+ * ------------------------------------------------------------------- */
+typedef struct {
+  double x;
+  int kind;
+  int64_t partner;
+} cand_t;
+
+static void consider(cand_t *best, double x, int kind, int64_t partner) {
+  if (x < best->x ||
+      (x == best->x &&
+       (kind < best->kind || (kind == best->kind && partner < best->partner)))) {
+    best->x = x;
+    best->kind = kind;
+    best->partner = partner;
+  }
+}
+
+/* hard-sphere contact distance of pivot i moving along v towards bead k
+ * (Eq. 1: contact at |r_i + x v - r_k| = sigma); returns -1 if none */
+static double hs_dist(const ctx_t *c, int64_t i, int64_t k, const double v[3]) {
+  const double *L = c->P.L;
+  double d0 = minimg(c->r[3 * i + 0] - c->r[3 * k + 0], L[0]);
+  double d1 = minimg(c->r[3 * i + 1] - c->r[3 * k + 1], L[1]);
+  double d2 = minimg(c->r[3 * i + 2] - c->r[3 * k + 2], L[2]);
+  double dv = d0 * v[0] + d1 * v[1] + d2 * v[2];
+  if (!(dv < 0.0)) return -1.0;
+  double dd = d0 * d0 + d1 * d1 + d2 * d2;
+  double sig2 = c->P.sigma * c->P.sigma;
+  double disc = sig2 - (dd - dv * dv);
+  if (!(disc > 0.0)) return -1.0;
+  double x = -dv - sqrt(disc);
+  if (x < 0.0) x = 0.0;
+  return x;
+}
+
+/* tether limit of pivot i bonded to j: |r_i + x v - r_j| = b_max, the
+ * positive root (the bond can always shorten first) */
+static double te_dist(const ctx_t *c, int64_t i, int64_t j, const double v[3]) {
+  const double *L = c->P.L;
+  double d0 = minimg(c->r[3 * i + 0] - c->r[3 * j + 0], L[0]);
+  double d1 = minimg(c->r[3 * i + 1] - c->r[3 * j + 1], L[1]);
+  double d2 = minimg(c->r[3 * i + 2] - c->r[3 * j + 2], L[2]);
+  double dv = d0 * v[0] + d1 * v[1] + d2 * v[2];
+  double dd = d0 * d0 + d1 * d1 + d2 * d2;
+  double b2 = c->P.b_max * c->P.b_max;
+  double rad = b2 - (dd - dv * dv);
+  if (rad < 0.0) rad = 0.0;
+  double x = -dv + sqrt(rad);
+  if (x < 0.0) x = 0.0;
+  return x;
+}
+
+static void hs_all(const ctx_t *c, int64_t i, const double v[3], cand_t *best) {
+  if (c->P.use_cells) {
+    int ci = c->cell[i];
+    int ix = ci % c->nc[0];
+    int iy = (ci / c->nc[0]) % c->nc[1];
+    int iz = ci / (c->nc[0] * c->nc[1]);
+    for (int dz = -1; dz <= 1; ++dz)
+      for (int dy = -1; dy <= 1; ++dy)
+        for (int dx = -1; dx <= 1; ++dx) {
+          int jx = (ix + dx + c->nc[0]) % c->nc[0];
+          int jy = (iy + dy + c->nc[1]) % c->nc[1];
+          int jz = (iz + dz + c->nc[2]) % c->nc[2];
+          int cj = (jz * c->nc[1] + jy) * c->nc[0] + jx;
+          for (int32_t k = c->head[cj]; k >= 0; k = c->next[k]) {
+            if (k == i) continue;
+            double x = hs_dist(c, i, k, v);
+            if (x >= 0.0) consider(best, x, K_HS, k);
+          }
+        }
+  } else {
+    for (int64_t k = 0; k < c->P.n; ++k) {
+      if (k == i) continue;
+      double x = hs_dist(c, i, k, v);
+      if (x >= 0.0) consider(best, x, K_HS, k);
+    }
+  }
+}
+
+/* ---------------------------------------------------------------------
+ * one event chain
+ * ------------------------------------------------------------------- */
+typedef struct {
+  int active;      /* domain mode */
+  int32_t t;       /* tile index */
+  double corner[3];
+} tile_t;
+
+static int motile(const ctx_t *c, const tile_t *tl, int64_t b) {
+  return !tl->active || c->tag[b] == tl->t;
+}
+
+static void fnv(uint64_t *h, uint64_t w) {
+  *h ^= w;
+  *h *= 0x100000001B3ULL;
+}
+
+/* reflect v at the plane normal to d (Fig. 2c) */
+static void reflect(double v[3], double d0, double d1, double d2) {
+  double nd = sqrt(d0 * d0 + d1 * d1 + d2 * d2);
+  double n0 = d0 / nd, n1 = d1 / nd, n2 = d2 / nd;
+  double vn = v[0] * n0 + v[1] * n1 + v[2] * n2;
+  double t = 2.0 * vn;
+  v[0] = v[0] - t * n0;
+  v[1] = v[1] - t * n1;
+  v[2] = v[2] - t * n2;
+}
+
+/* swap test (Sec. II.D): with pivot i and the touched bead k exchanged,
+ * every bond of i and of k must stay within b_max */
+static int bond_ok(const ctx_t *c, int64_t a, const double *pa, int64_t b,
+                   const double *pb) {
+  const double *L = c->P.L;
+  double d0 = minimg(pa[0] - pb[0], L[0]);
+  double d1 = minimg(pa[1] - pb[1], L[1]);
+  double d2 = minimg(pa[2] - pb[2], L[2]);
+  double dd = d0 * d0 + d1 * d1 + d2 * d2;
+  (void)a;
+  (void)b;
+  return dd <= c->P.b_max * c->P.b_max;
+}
+
+static const double *pos_after_swap(const ctx_t *c, int64_t q, int64_t i,
+                                    int64_t k) {
+  if (q == i) return &c->r[3 * k];
+  if (q == k) return &c->r[3 * i];
+  return &c->r[3 * q];
+}
+
+static int swap_allowed(const ctx_t *c, int64_t i, int64_t k) {
+  int32_t N = c->P.N;
+  int64_t ends[2] = {i, k};
+  for (int e = 0; e < 2; ++e) {
+    int64_t a = ends[e];
+    int64_t nb[2] = {(a % N != 0) ? a - 1 : -1, (a % N != N - 1) ? a + 1 : -1};
+    for (int s = 0; s < 2; ++s) {
+      int64_t b = nb[s];
+      if (b < 0) continue;
+      if (!bond_ok(c, a, pos_after_swap(c, a, i, k), b,
+                   pos_after_swap(c, b, i, k)))
+        return 0;
+    }
+  }
+  return 1;
+}
+
+static void exchange(ctx_t *c, int64_t i, int64_t k) {
+  for (int a = 0; a < 3; ++a) {
+    double tr = c->r[3 * i + a];
+    c->r[3 * i + a] = c->r[3 * k + a];
+    c->r[3 * k + a] = tr;
+    int32_t ti = c->img[3 * i + a];
+    c->img[3 * i + a] = c->img[3 * k + a];
+    c->img[3 * k + a] = ti;
+  }
+  if (c->P.use_cells) {
+    int ci = c->cell[i], ck = c->cell[k];
+    if (ci != ck) {
+      cell_remove(c, i);
+      cell_remove(c, k);
+      cell_insert(c, i, ck);
+      cell_insert(c, k, ci);
+    }
+  }
+}
+
+static void run_ec(ctx_t *c, int64_t pivot, double v[3], double ell,
+                   const tile_t *tl, uint64_t ec, uint64_t sweep,
+                   uint64_t unit, int64_t ordinal) {
+  const orc_params *P = &c->P;
+  orc_stats *st = c->st;
+  double xrem = ell;
+  int64_t nev = 0, ncontact = 0;
+  uint64_t h = 0xCBF29CE484222325ULL;
+  double lift = 0.0;
+  uint64_t sw[4] = {0, 0, 0, 0};
+  for (;;) {
+    if (nev >= P->event_cap) {
+      st->status = ORC_ESTUCK;
+      break;
+    }
+    const int64_t i = pivot;
+    cand_t best = {xrem, K_END, -1};
+    consider(&best, P->s_cap, K_PASS, -1);
+    if (tl->active) {
+      for (int a = 0; a < 3; ++a) {
+        if (v[a] == 0.0) continue;
+        double loc = minimg(c->r[3 * i + a] - tl->corner[a], P->L[a]);
+        double x = (v[a] > 0.0) ? (c->W[a] - loc) / v[a] : (0.0 - loc) / v[a];
+        if (x < 0.0) x = 0.0;
+        consider(&best, x, K_WALL, a);
+      }
+    }
+    if (P->N > 1) {
+      if (i % P->N != 0) consider(&best, te_dist(c, i, i - 1, v), K_TETHER, i - 1);
+      if (i % P->N != P->N - 1) consider(&best, te_dist(c, i, i + 1, v), K_TETHER, i + 1);
+    }
+    hs_all(c, i, v, &best);
+
+    /* move the pivot */
+    const double x = best.x;
+    for (int a = 0; a < 3; ++a)
+      advance(&c->r[3 * i + a], &c->img[3 * i + a], x, v[a], P->L[a]);
+    cell_update(c, i);
+    st->disp_sum += x;
+    ++nev;
+    ++st->events;
+
+    int out;
+    int64_t next = i;
+    if (best.kind == K_END) {
+      out = O_END;
+    } else if (best.kind == K_PASS) {
+      out = O_PASS;
+    } else if (best.kind == K_WALL) {
+      out = O_WALL;
+      v[best.partner] = -v[best.partner];
+    } else {
+      const int64_t k = best.partner;
+      double d0 = minimg(c->r[3 * i + 0] - c->r[3 * k + 0], P->L[0]);
+      double d1 = minimg(c->r[3 * i + 1] - c->r[3 * k + 1], P->L[1]);
+      double d2 = minimg(c->r[3 * i + 2] - c->r[3 * k + 2], P->L[2]);
+      double proj = 0.0 - (d0 * v[0] + d1 * v[1] + d2 * v[2]);
+      if (!motile(c, tl, k)) {
+        /* partner cannot move: reflect at the contact / bond normal */
+        out = (best.kind == K_HS) ? O_HS_REFLECT : O_TE_REFLECT;
+        st->refl_sum += proj;
+        reflect(v, d0, d1, d2);
+      } else if (best.kind == K_HS) {
+        lift += proj;
+        int swapped = 0;
+        if (P->p_swap > 0.0) {
+          int go;
+          if (P->p_swap >= 1.0) {
+            go = 1;
+          } else {
+            if ((ncontact & 3) == 0)
+              draw(P, TAG_SWAP | (ec << 8), sweep, unit, (uint64_t)(ncontact >> 2), sw);
+            go = u53(sw[ncontact & 3]) < P->p_swap;
+          }
+          ++ncontact;
+          if (go) {
+            ++st->swap_tried;
+            if (swap_allowed(c, i, k)) {
+              exchange(c, i, k);
+              swapped = 1;
+            }
+          }
+        }
+        if (swapped) {
+          out = O_SWAP;
+        } else {
+          out = O_HS_LIFT;
+          next = k;
+        }
+      } else {
+        lift += proj;
+        out = O_TE_LIFT;
+        next = k;
+      }
+    }
+    st->out[out] += 1;
+    fnv(&h, (uint64_t)i);
+    fnv(&h, ((uint64_t)(uint32_t)out << 32) | (uint64_t)(uint32_t)best.partner);
+    {
+      uint64_t xb;
+      memcpy(&xb, &x, 8);
+      fnv(&h, xb);
+    }
+    if (c->log && *c->log_n < c->log_cap) {
+      orc_event *e = &c->log[*c->log_n];
+      e->unit = ordinal;
+      e->pivot = (int32_t)i;
+      e->kind = out;
+      e->partner = best.partner;
+      e->x = x;
+      *c->log_n += 1;
+    }
+    if (out == O_END) break;
+    xrem = xrem - x;
+    pivot = next;
+  }
+  st->lift_sum += lift;
+  st->ecs += 1;
+  if (c->digest) c->digest[ordinal] = h;
+  if (c->ec_lift) c->ec_lift[ordinal] = lift;
+  if (c->ec_events) c->ec_events[ordinal] = nev;
+}
+
+/* direction: {+x,+y,+z} (global balance, Sec. II), isotropic by rejection
+ * from the cube (no trigonometry), or +x only (one-dimensional checks) */
+static void draw_start(const ctx_t *c, uint64_t tag, uint64_t sweep,
+                       uint64_t unit, int64_t m, int64_t *idx, double v[3]) {
+  uint64_t w[4];
+  draw(&c->P, tag, sweep, unit, 0, w);
+  *idx = below(w[0], m);
+  v[0] = v[1] = v[2] = 0.0;
+  if (c->P.dir_mode == ORC_DIR_CART3) {
+    v[below(w[1], 3)] = 1.0;
+  } else if (c->P.dir_mode == ORC_DIR_PLUSX) {
+    v[0] = 1.0;
+  } else {
+    uint64_t a = 0;
+    double p = 2.0 * u53(w[1]) - 1.0;
+    double q = 2.0 * u53(w[2]) - 1.0;
+    double s3 = 2.0 * u53(w[3]) - 1.0;
+    for (;;) {
+      double s = p * p + q * q + s3 * s3;
+      if (s > 1e-6 && s <= 1.0) {
+        double nr = sqrt(s);
+        v[0] = p / nr;
+        v[1] = q / nr;
+        v[2] = s3 / nr;
+        break;
+      }
+      ++a;
+      draw(&c->P, tag, sweep, unit, a, w);
+      p = 2.0 * u53(w[0]) - 1.0;
+      q = 2.0 * u53(w[1]) - 1.0;
+      s3 = 2.0 * u53(w[2]) - 1.0;
+    }
+  }
+}
+
+/* ---------------------------------------------------------------------
+ * public entry points (ctypes)
+ * ------------------------------------------------------------------- */
+
+/* serial, undecomposed: EC j (j = 0..n_ec-1 of this call, global ordinal
+ * ec0 + j) starts at a uniform bead with a direction from Philox. */
+int orc_run_serial(const orc_params *P, double *r, int32_t *img, int64_t ec0,
+                   int64_t n_ec, double ell, orc_stats *st, uint64_t *digest,
+                   double *ec_lift, int64_t *ec_events, orc_event *log,
+                   int64_t log_cap, int64_t *log_n) {
+  if (P->n < 1 || P->N < 1 || P->n % P->N != 0 || !(P->sigma > 0.0) ||
+      !(P->s_cap > 0.0) || !(ell >= 0.0))
+    return ORC_EINVAL;
+  for (int a = 0; a < 3; ++a)
+    if (!(P->s_cap + P->sigma < 0.5 * P->L[a])) return ORC_EINVAL;
+  ctx_t c;
+  ctx_init(&c, P, r, img);
+  c.st = st;
+  c.log = log;
+  c.log_cap = log_cap;
+  c.log_n = log_n;
+  c.digest = digest;
+  c.ec_lift = ec_lift;
+  c.ec_events = ec_events;
+  tile_t tl = {0, 0, {0, 0, 0}};
+  for (int64_t j = 0; j < n_ec && st->status == 0; ++j) {
+    int64_t idx;
+    double v[3];
+    draw_start(&c, TAG_START, 0, (uint64_t)(ec0 + j), P->n, &idx, v);
+    run_ec(&c, idx, v, ell, &tl, 0, 0, (uint64_t)(ec0 + j), j);
+  }
+  ctx_free(&c);
+  return (int)st->status;
+}
+
+/* domain assignment (Sec. II.B): shift o in [0,T)^3 drawn per sweep; along
+ * each axis tile k covers [o + kT, o + (k+1)T - w), the last w is joint. */
+static void domain_setup(ctx_t *c, uint64_t sweep) {
+  const orc_params *P = &c->P;
+  uint64_t w[4];
+  draw(P, TAG_SHIFT, sweep, 0, 0, w);
+  for (int a = 0; a < 3; ++a) {
+    c->T[a] = P->L[a] / P->D[a];
+    c->W[a] = c->T[a] - P->w;
+    c->shift[a] = u53(w[a]) * c->T[a];
+  }
+  for (int64_t b = 0; b < P->n; ++b) {
+    int k[3], in = 1;
+    for (int a = 0; a < 3; ++a) {
+      double u = c->r[3 * b + a] - c->shift[a];
+      if (u < 0.0) u += P->L[a];
+      if (u >= P->L[a]) u -= P->L[a];
+      int t = (int)(u / c->T[a]);
+      if (t > P->D[a] - 1) t = P->D[a] - 1;
+      double loc = u - t * c->T[a];
+      if (!(loc < c->W[a])) in = 0;
+      k[a] = t;
+    }
+    c->tag[b] = in ? (k[2] * P->D[1] + k[1]) * P->D[0] + k[0] : -1;
+  }
+}
+
+int orc_domain_tags(const orc_params *P, double *r, uint64_t sweep,
+                    int32_t *tags_out, double *shift_out) {
+  int32_t dummy_img[3] = {0, 0, 0};
+  orc_params Q = *P;
+  Q.use_cells = 0;
+  ctx_t c;
+  ctx_init(&c, &Q, r, dummy_img);
+  domain_setup(&c, sweep);
+  memcpy(tags_out, c.tag, sizeof(int32_t) * P->n);
+  for (int a = 0; a < 3; ++a) shift_out[a] = c.shift[a];
+  ctx_free(&c);
+  return 0;
+}
+
+/* domain-parallel sweeps: tiles are independent within a sweep (joint width
+ * w >= b_max > sigma), so running them one after another in increasing tile
+ * index gives the same result as running them at the same time. */
+int orc_run_domain(const orc_params *P, double *r, int32_t *img, int64_t sweep0,
+                   int64_t n_sweeps, double ell, orc_stats *st,
+                   uint64_t *digest, double *ec_lift, int64_t *ec_events,
+                   orc_event *log, int64_t log_cap, int64_t *log_n) {
+  if (P->n < 1 || P->N < 1 || P->n % P->N != 0 || !(P->sigma > 0.0) ||
+      !(P->s_cap > 0.0) || !(ell >= 0.0) || P->ecs_per_tile < 1)
+    return ORC_EINVAL;
+  if (!(P->w >= P->b_max) || !(P->b_max >= P->sigma)) return ORC_EINVAL;
+  for (int a = 0; a < 3; ++a) {
+    if (P->D[a] < 1) return ORC_EINVAL;
+    double T = P->L[a] / P->D[a];
+    if (!(T - P->w + 2.0 * P->sigma < 0.5 * P->L[a])) return ORC_EINVAL;
+    if (!(P->s_cap + P->sigma < 0.5 * P->L[a])) return ORC_EINVAL;
+  }
+  ctx_t c;
+  ctx_init(&c, P, r, img);
+  c.st = st;
+  c.log = log;
+  c.log_cap = log_cap;
+  c.log_n = log_n;
+  c.digest = digest;
+  c.ec_lift = ec_lift;
+  c.ec_events = ec_events;
+  const int64_t ntile = (int64_t)P->D[0] * P->D[1] * P->D[2];
+  const int k = P->ecs_per_tile;
+  int64_t *cnt = (int64_t *)calloc(ntile + 1, sizeof(int64_t));
+  int64_t *list = (int64_t *)malloc(sizeof(int64_t) * P->n);
+  for (int64_t s = 0; s < n_sweeps && st->status == 0; ++s) {
+    const uint64_t sweep = (uint64_t)(sweep0 + s);
+    domain_setup(&c, sweep);
+    /* motile beads of every tile, in increasing bead id */
+    memset(cnt, 0, sizeof(int64_t) * (ntile + 1));
+    for (int64_t b = 0; b < P->n; ++b)
+      if (c.tag[b] >= 0) cnt[c.tag[b] + 1] += 1;
+    for (int64_t t = 0; t < ntile; ++t) cnt[t + 1] += cnt[t];
+    {
+      int64_t *fill = (int64_t *)malloc(sizeof(int64_t) * (ntile + 1));
+      memcpy(fill, cnt, sizeof(int64_t) * (ntile + 1));
+      for (int64_t b = 0; b < P->n; ++b)
+        if (c.tag[b] >= 0) list[fill[c.tag[b]]++] = b;
+      free(fill);
+    }
+    for (int64_t t = 0; t < ntile && st->status == 0; ++t) {
+      int64_t m = cnt[t + 1] - cnt[t];
+      if (m == 0) continue;
+      tile_t tl;
+      tl.active = 1;
+      tl.t = (int32_t)t;
+      int kx = (int)(t % P->D[0]);
+      int ky = (int)((t / P->D[0]) % P->D[1]);
+      int kz = (int)(t / ((int64_t)P->D[0] * P->D[1]));
+      tl.corner[0] = c.shift[0] + kx * c.T[0];
+      tl.corner[1] = c.shift[1] + ky * c.T[1];
+      tl.corner[2] = c.shift[2] + kz * c.T[2];
+      for (int e = 0; e < k && st->status == 0; ++e) {
+        int64_t idx;
+        double v[3];
+        draw_start(&c, TAG_START | ((uint64_t)e << 8), sweep, (uint64_t)t, m,
+                   &idx, v);
+        int64_t ord = (s * ntile + t) * k + e;
+        run_ec(&c, list[cnt[t] + idx], v, ell, &tl, (uint64_t)e, sweep,
+               (uint64_t)t, ord);
+      }
+    }
+  }
+  free(cnt);
+  free(list);
+  ctx_free(&c);
+  return (int)st->status;
+}
+
+/* ---------------------------------------------------------------------
+ * initial state and observables
+ * ------------------------------------------------------------------- */
+
+/* simple-cubic lattice n0 x n1 x n2 with spacing a, visited in a 3-D snake
+ * (x fastest and reversing every row, y reversing every plane), cut into
+ * consecutive runs of N = chains.  Every bond is one lattice step.  Each
+ * coordinate is then moved by jitter*(2u-1), u from Philox (tag 4, unit =
+ * bead): an exact lattice combined with {+x,+y,+z} directions holds bonded
+ * pairs with equal coordinates whose bond, once taut and perpendicular to v,
+ * stops the hard-tether EC (zero-length tether events back and forth). */
+int orc_lattice(const int32_t dims[3], double a, double jitter, uint64_t seed,
+                uint64_t replica, double *r) {
+  orc_params P;
+  memset(&P, 0, sizeof(P));
+  P.seed = seed;
+  P.replica = replica;
+  int64_t b = 0;
+  for (int z = 0; z < dims[2]; ++z) {
+    for (int yy = 0; yy < dims[1]; ++yy) {
+      int y = (z % 2 == 0) ? yy : dims[1] - 1 - yy;
+      int row = z * dims[1] + yy;
+      for (int xx = 0; xx < dims[0]; ++xx) {
+        int x = (row % 2 == 0) ? xx : dims[0] - 1 - xx;
+        int site[3] = {x, y, z};
+        uint64_t w[4] = {0, 0, 0, 0};
+        if (jitter != 0.0) draw(&P, 4, 0, (uint64_t)b, 0, w);
+        for (int ax = 0; ax < 3; ++ax) {
+          double p = (site[ax] + 0.5) * a;
+          if (jitter != 0.0) p = p + jitter * (2.0 * u53(w[ax]) - 1.0);
+          r[3 * b + ax] = p;
+        }
+        ++b;
+      }
+    }
+  }
+  return 0;
+}
+
+/* per-chain end-to-end vector from minimum-image bonds, per-bond lengths */
+int orc_chain_obs(const orc_params *P, const double *r, double *re2_chain,
+                  double *bond_len) {
+  int64_t nch = P->n / P->N;
+  for (int64_t ch = 0; ch < nch; ++ch) {
+    double R[3] = {0, 0, 0};
+    for (int32_t j = 0; j + 1 < P->N; ++j) {
+      int64_t b = ch * P->N + j;
+      double dd = 0.0;
+      for (int a = 0; a < 3; ++a) {
+        double d = minimg(r[3 * (b + 1) + a] - r[3 * b + a], P->L[a]);
+        R[a] += d;
+        dd += d * d;
+      }
+      if (bond_len) bond_len[ch * (P->N - 1) + j] = sqrt(dd);
+    }
+    re2_chain[ch] = R[0] * R[0] + R[1] * R[1] + R[2] * R[2];
+  }
+  return 0;
+}
+
+/* smallest pair distance (all pairs, minimum image) and the number of pairs
+ * closer than sigma*(1 - 1e-10)^(1/2) */
+int orc_min_pair(const orc_params *P, const double *r, double *dmin,
+                 int64_t *n_overlap) {
+  double best = INFINITY;
+  int64_t cnt = 0;
+  double lim = P->sigma * P->sigma * (1.0 - 1e-10);
+  for (int64_t i = 0; i < P->n; ++i)
+    for (int64_t j = i + 1; j < P->n; ++j) {
+      double dd = 0.0;
+      for (int a = 0; a < 3; ++a) {
+        double d = minimg(r[3 * i + a] - r[3 * j + a], P->L[a]);
+        dd += d * d;
+      }
+      if (dd < best) best = dd;
+      if (dd < lim) ++cnt;
+    }
+  *dmin = sqrt(best);
+  *n_overlap = cnt;
+  return 0;
+}
+
+/* same check through the oracle's own cell list (large systems) */
+int orc_min_pair_cells(const orc_params *P, double *r, double *dmin,
+                       int64_t *n_overlap) {
+  orc_params Q = *P;
+  Q.use_cells = 1;
+  Q.s_cap = 0.25 * P->sigma;
+  int32_t dummy[3] = {0, 0, 0};
+  ctx_t c;
+  ctx_init(&c, &Q, r, dummy);
+  if (!c.P.use_cells) {
+    ctx_free(&c);
+    return orc_min_pair(P, r, dmin, n_overlap);
+  }
+  double best = INFINITY;
+  int64_t cnt = 0;
+  double lim = P->sigma * P->sigma * (1.0 - 1e-10);
+  for (int64_t i = 0; i < P->n; ++i) {
+    int ci = c.cell[i];
+    int ix = ci % c.nc[0], iy = (ci / c.nc[0]) % c.nc[1],
+        iz = ci / (c.nc[0] * c.nc[1]);
+    for (int dz = -1; dz <= 1; ++dz)
+      for (int dy = -1; dy <= 1; ++dy)
+        for (int dx = -1; dx <= 1; ++dx) {
+          int cj = (((iz + dz + c.nc[2]) % c.nc[2]) * c.nc[1] +
+                    (iy + dy + c.nc[1]) % c.nc[1]) * c.nc[0] +
+                   (ix + dx + c.nc[0]) % c.nc[0];
+          for (int32_t j = c.head[cj]; j >= 0; j = c.next[j]) {
+            if (j <= i) continue;
+            double dd = 0.0;
+            for (int a = 0; a < 3; ++a) {
+              double d = minimg(r[3 * i + a] - r[3 * j + a], P->L[a]);
+              dd += d * d;
+            }
+            if (dd < best) best = dd;
+            if (dd < lim) ++cnt;
+          }
+        }
+  }
+  ctx_free(&c);
+  *dmin = sqrt(best);
+  *n_overlap = cnt;
+  return 0;
+}
+
+/* start draws of serial ECs ec0..ec0+n-1 (for the direction/start checks) */
+int orc_start_draws(const orc_params *P, int64_t ec0, int64_t n, int64_t *idx,
+                    double *v) {
+  ctx_t c;
+  memset(&c, 0, sizeof(c));
+  c.P = *P;
+  for (int64_t j = 0; j < n; ++j)
+    draw_start(&c, TAG_START, 0, (uint64_t)(ec0 + j), P->n, &idx[j], &v[3 * j]);
+  return 0;
+}

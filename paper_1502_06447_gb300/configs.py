@@ -1,0 +1,102 @@
+"""Synthetic workloads: seeded, deterministic melt specifications.
+
+This module holds input data only (lattice shapes, spacings, chain lengths,
+run lengths, seeds) and none of the method's arithmetic.  Both the CUDA
+library's tests/benchmark and the oracle read their inputs from here.
+
+The paper measures on synthetic melts too (Systems I-III, Sec. III: M chains
+of N hard-sphere beads in a periodic cube); these workloads stand in for them
+with lattice starts and hard tethers (b_max = 1.2 sigma).
+"""
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass, field
+
+import numpy as np
+
+
+@dataclass(frozen=True)
+class Melt:
+    name: str
+    dims: tuple            # simple-cubic lattice sites per axis
+    spacing: float         # lattice spacing a (bond length of the start)
+    N: int                 # beads per chain
+    sigma: float = 1.0
+    b_max: float = 1.2
+    ell: float = 5.0       # total displacement of one EC
+    seed: int = 0xEC0001
+    # run shape
+    mode: str = "serial"   # "serial" or "domain"
+    dir_mode: str = "cart3"
+    n_ec: int = 0          # serial ECs
+    sweeps: int = 0        # domain sweeps
+    D: tuple = (1, 1, 1)   # tiles per axis for parity runs
+    p_swap: float = 0.0
+    jitter: float = 0.01   # seeded per-coordinate perturbation of the lattice
+
+    @property
+    def n(self) -> int:
+        return int(self.dims[0] * self.dims[1] * self.dims[2])
+
+    @property
+    def n_chains(self) -> int:
+        return self.n // self.N
+
+    @property
+    def L(self) -> tuple:
+        return tuple(d * self.spacing for d in self.dims)
+
+    @property
+    def phi(self) -> float:
+        return self.n * math.pi * self.sigma ** 3 / (6.0 * self.L[0] * self.L[1] * self.L[2])
+
+
+# C1: 64 chains x N=10 on 8x8x10, a=1.05, serial, 1e5 ECs, ell=5, {+x,+y,+z}
+C1 = Melt("c1_serial_640", (8, 8, 10), 1.05, 10, ell=5.0, seed=0xEC0001,
+          mode="serial", dir_mode="cart3", n_ec=100_000)
+# C2: 4096 x 64 on 64^3, a=1.05, domain, ell=10, 100 sweeps
+C2 = Melt("c2_domain_262k", (64, 64, 64), 1.05, 64, ell=10.0, seed=0xEC0002,
+          mode="domain", dir_mode="iso", sweeps=100, D=(16, 16, 16))
+# C3: 2000 x 256 on 80^3, a=1.0156, domain, ell=10
+C3 = Melt("c3_fp32f_512k", (80, 80, 80), 1.0156, 256, ell=10.0, seed=0xEC0003,
+          mode="domain", dir_mode="iso", sweeps=20, D=(16, 16, 16))
+# C5: 1000 x 1000 on 100^3, a=1.05, domain + swap, ell=20
+C5 = Melt("c5_swap_1m", (100, 100, 100), 1.05, 1000, ell=20.0, seed=0xEC0005,
+          mode="domain", dir_mode="iso", sweeps=10, D=(20, 20, 20))
+
+CONFIGS = {m.name: m for m in (C1, C2, C3, C5)}
+
+
+def small_domain(N=8, dims=(16, 16, 16), spacing=1.05, D=(3, 3, 3), seed=0xEC00A1,
+                 ell=4.0, sweeps=3, dir_mode="iso", p_swap=0.0) -> Melt:
+    """Small domain-mode melt for parity runs (several tiles, ragged counts)."""
+    return Melt(f"small_domain_{dims[0]}x{dims[1]}x{dims[2]}_N{N}", tuple(dims), spacing,
+                N, ell=ell, seed=seed, mode="domain", dir_mode=dir_mode,
+                sweeps=sweeps, D=tuple(D), p_swap=p_swap)
+
+
+def replica_specs(n_replicas=256, seed=0xEC0004):
+    """C4: replicas with N ~ U{10,20,40,80,160}, target beads 2^U[11,16],
+    phi ~ U[0.35,0.50], spacing a = (pi/(6 phi))^(1/3); lattice (k,k,m) with
+    k,m >= 8, N | k*k*m, closest to the target."""
+    rng = np.random.default_rng(seed)
+    specs = []
+    for r in range(n_replicas):
+        N = int(rng.choice([10, 20, 40, 80, 160]))
+        target = 2.0 ** rng.uniform(11, 16)
+        phi = float(rng.uniform(0.35, 0.50))
+        a = (math.pi / (6.0 * phi)) ** (1.0 / 3.0)
+        best = None
+        for k in range(8, 65):
+            for m in range(8, 257):
+                nb = k * k * m
+                if nb % N:
+                    continue
+                score = abs(math.log(nb / target))
+                if best is None or score < best[0]:
+                    best = (score, k, m)
+        _, k, m = best
+        specs.append(Melt(f"replica_{r}", (k, k, m), a, N, ell=5.0, seed=seed,
+                          mode="domain", dir_mode="iso", sweeps=1))
+    return specs
