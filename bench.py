@@ -1,0 +1,346 @@
+"""Benchmark: events/s and ell-sweeps/s of the event-chain sweep on one GB300.
+
+Workload (the 10^6-bead melt): 1000 chains x N=1000 on a 100^3 lattice,
+spacing 1.05 sigma (phi ~ 0.45), b_max = 1.2 sigma, ell = 20 sigma,
+20^3 shifted tiles, isotropic directions, FP32 screen + FP64 confirmation,
+swap moves calibrated to 0.1 attempts per bead per sweep.
+One step = one sweep: domain assignment + cell list + one EC per tile.
+
+`value` is events/s of the FP32-screened form (inputs resident in HBM, L2
+flushed between steps, device time from CUDA events).  The plain FP64 kernel
+on the same state is reported beside it.  `e2e` goes through the public API
+with host buffers (positions in, one sweep, positions out).
+
+`--impl reference` times the oracle (plain serial FP64 C, the checker of the
+CUDA path) on the host cores on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_1502_06447_gb300.configs import C5  # noqa: E402
+
+ELL = C5.ell
+TILES = (20, 20, 20)
+SWAP_RATE = 0.1
+METRIC = "events/s (EC sweep, 1e6-bead melt, FP32 screen + FP64 confirm)"
+UNIT = "events/s"
+C0 = 1.2  # stencil cell side of the bytes-per-event definition (= b_max)
+
+
+def bytes_per_event(phi, confirmed_per_event, fp32f=True):
+    """Algorithmic bytes per event: a 27-cell stencil of side c0 = b_max
+    holds nbar = rho 27 c0^3 beads; FP64 reads 24 B each, the FP32 screen
+    16 B each plus 24 B per FP64-confirmed bead; 216 B of cell offsets,
+    96 (FP32) or 72 (FP64) B of pivot and bond partners, 24 B written."""
+    rho = 6.0 * phi / math.pi
+    nbar = rho * 27.0 * C0 ** 3
+    if fp32f:
+        return 16.0 * nbar + 24.0 * confirmed_per_event + 216.0 + 96.0
+    return 24.0 * nbar + 216.0 + 72.0 + 24.0
+
+
+def load_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        d = json.load(open(p))
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi samples during the timed region."""
+
+    def __init__(self, index=0):
+        self.rows = []
+        self.proc = None
+        self.index = index
+
+    def __enter__(self):
+        q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={q}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.th = threading.Thread(target=self._read, daemon=True)
+            self.th.start()
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.rows.append([x.strip() for x in line.split(",")])
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in self.rows:
+            try:
+                sm.append(float(r[0]))
+                mx = float(r[1])
+                for k, nm in enumerate(names):
+                    if r[4 + k].lower() == "active":
+                        reasons.add(nm)
+            except (ValueError, IndexError):
+                pass
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def run_gpu(args, rank, world):
+    import numpy as np
+    import torch
+
+    from paper_1502_06447_gb300 import build as b
+    from paper_1502_06447_gb300 import ecmc
+
+    if rank == 0 or True:
+        b.build()
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", 0)))
+    dev = torch.device("cuda")
+    stream = torch.cuda.current_stream()
+    seed = C5.seed + rank  # replicas: independent seeds
+
+    def make(precision):
+        ctx = ecmc.Context.create_lattice(C5.dims, C5.spacing, C5.N, sigma=C5.sigma,
+                                          b_max=C5.b_max, jitter=C5.jitter, seed=seed)
+        ctx.set_stream(stream.cuda_stream)
+        ctx.configure(mode=ecmc.MODE_DOMAIN, dir_mode=ecmc.DIR_ISO, precision=precision,
+                      tiles=TILES, lanes=args.lanes)
+        return ctx
+
+    ctx = make(ecmc.PREC_FP32F)
+    # swap calibration: one sweep without swaps, then p_swap for 0.1 / bead / sweep
+    ctx.run(ELL, seed=seed, n_sweeps=1)
+    ctx.swap(SWAP_RATE)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    for _ in range(args.warmup):
+        ctx.run(ELL, seed=seed, n_sweeps=1)
+    o0 = ctx.observables()
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    step_ms = []
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    with ClockSampler(int(os.environ.get("LOCAL_RANK", 0))) as clk:
+        t0 = time.perf_counter()
+        for k in range(args.steps):
+            flush.zero_()  # L2 flush between steps (256 MB > 129 MB L2)
+            ev[k][0].record(stream)
+            ctx.run(ELL, seed=seed, n_sweeps=1)
+            ev[k][1].record(stream)
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - t0
+    step_ms = [a.elapsed_time(b_) for a, b_ in ev]
+    o1 = ctx.observables()
+    events = o1["events_total"] - o0["events_total"]
+    ecs = o1["ecs"] - o0["ecs"]
+    dev_s = sum(step_ms) / 1e3
+    ec_s = o1["ec_kernel_seconds"] - o0["ec_kernel_seconds"]
+    confirmed = o1["confirmed"] - o0["confirmed"]
+    assert o1["overlaps"] == 0 and o1["tether_violations"] == 0
+
+    # plain FP64 kernel on the same workload (fresh lattice, same calibration)
+    ctx64 = make(ecmc.PREC_FP64)
+    ctx64.run(ELL, seed=seed, n_sweeps=1)
+    ctx64.swap(SWAP_RATE)
+    ctx64.run(ELL, seed=seed, n_sweeps=1)
+    p0 = ctx64.observables()
+    n64 = max(1, args.steps // 2)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    ctx64.run(ELL, seed=seed, n_sweeps=n64)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    p1 = ctx64.observables()
+    fp64_eps = (p1["events_total"] - p0["events_total"]) / (e0.elapsed_time(e1) / 1e3)
+    ctx64.close()
+
+    # e2e through the public API with host buffers
+    r_host, img_host = ctx.get_positions()
+    r_pin = torch.from_numpy(r_host).pin_memory()
+    i_pin = torch.from_numpy(img_host).pin_memory()
+    n_e2e = max(1, min(args.steps, 5))
+    q0 = ctx.observables()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(n_e2e):
+        ctx.set_positions(r_pin.numpy(), i_pin.numpy())
+        ctx.run(ELL, seed=seed, n_sweeps=1)
+        r_out, i_out = ctx.get_positions()
+        r_pin.numpy()[:] = r_out
+        i_pin.numpy()[:] = i_out
+    e2e_s = time.perf_counter() - t0
+    q1 = ctx.observables()
+    e2e_events = q1["events_total"] - q0["events_total"]
+
+    # aggregate over ranks (replicas; max time, summed events)
+    tot_events, max_dev, max_wall = float(events), dev_s, wall
+    if world > 1:
+        t = torch.tensor([float(events), dev_s, wall, float(e2e_events), e2e_s], device=dev,
+                         dtype=torch.float64)
+        s = t.clone()
+        torch.distributed.all_reduce(s[:1], op=torch.distributed.ReduceOp.SUM)
+        torch.distributed.all_reduce(t[1:3], op=torch.distributed.ReduceOp.MAX)
+        tot_events, max_dev, max_wall = float(s[0]), float(t[1]), float(t[2])
+    if rank != 0:
+        return None
+    hbm, peak_src = load_peaks()
+    phi = C5.phi
+    bpe = bytes_per_event(phi, confirmed / max(events, 1))
+    achieved = events * bpe / ec_s / 1e9
+    traffic = None
+    prof = os.path.join(ROOT, "profiles", "ec_kernel_traffic.json")
+    if os.path.exists(prof):
+        try:
+            traffic = json.load(open(prof)).get("bytes_per_launch")
+        except Exception:
+            traffic = None
+    n_beads = C5.n
+    value = tot_events / max_dev
+    line = {
+        "metric": METRIC,
+        "value": value,
+        "unit": UNIT,
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": 1e3 * max_dev / args.steps,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": C5.name, "beads": n_beads, "chains": C5.n_chains, "N": C5.N,
+                   "lattice": list(C5.dims), "spacing": C5.spacing, "phi": round(phi, 4),
+                   "b_max": C5.b_max, "ell": ELL, "tiles": list(TILES), "directions": "iso",
+                   "precision": "fp32 screen + fp64 confirm", "swap_attempts_per_bead_sweep":
+                   SWAP_RATE, "lanes_per_ec": args.lanes,
+                   "l2": "flushed between steps (256 MB write)",
+                   "parallelism": "replicas" if world > 1 else "1 GPU"},
+        "ell_sweeps_per_s": (ecs / n_beads) / dev_s,
+        "ecs_per_s": ecs / dev_s,
+        "fp64_events_per_s": fp64_eps,
+        "fp32f_over_fp64": value / fp64_eps / world,
+        "confirmed_per_event": confirmed / max(events, 1),
+        "events_per_ec": events / max(ecs, 1),
+        "wall_s": max_wall,
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
+                     "frac": achieved / hbm, "traffic": traffic,
+                     "kernel": "ec_kernel<32,true>", "bytes_per_event": bpe,
+                     "kernel_share_of_step": ec_s / dev_s, "peak_source": peak_src},
+        "e2e": {"value": e2e_events / e2e_s, "unit": UNIT,
+                "h2d_bytes_per_step": int(r_host.nbytes + img_host.nbytes),
+                "d2h_bytes_per_step": int(r_host.nbytes + img_host.nbytes)},
+        "gpu_launches": 6 * args.steps,
+        "clocks": clk.summary(),
+    }
+    if args.cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline_run(max_sweeps=1)
+    return line
+
+
+def cpu_baseline_run(max_sweeps=1, time_budget=25.0):
+    """The oracle as it stands (serial FP64 C, one core) on a bounded sample:
+    `max_sweeps` full sweeps of the same 10^6-bead workload."""
+    import oracle
+    r = oracle.lattice(C5.dims, C5.spacing, C5.jitter, C5.seed)
+    o = oracle.System(r, C5.L, C5.N, mode=oracle.MODE_DOMAIN, dir_mode=oracle.DIR_ISO,
+                      D=TILES, seed=C5.seed)
+    t0 = time.perf_counter()
+    res = o.run_domain(max_sweeps, ELL)
+    dt = time.perf_counter() - t0
+    ev = res["stats"]["events"]
+    return {"value": ev / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{max_sweeps} sweep(s) of the 1e6-bead melt without swaps "
+                      f"({ev} events, {dt:.1f} s)"}
+
+
+def run_reference(args, rank):
+    if rank != 0:
+        return None
+    import oracle
+    oracle.build()
+    r = oracle.lattice(C5.dims, C5.spacing, C5.jitter, C5.seed)
+    o = oracle.System(r, C5.L, C5.N, mode=oracle.MODE_DOMAIN, dir_mode=oracle.DIR_ISO,
+                      D=TILES, seed=C5.seed)
+    sweep = 0
+    for _ in range(args.warmup if args.warmup < 1 else 1):
+        o.run_domain(1, ELL, sweep0=sweep)
+        sweep += 1
+    t0 = time.perf_counter()
+    ev = 0
+    for _ in range(args.steps):
+        res = o.run_domain(1, ELL, sweep0=sweep)
+        ev += res["stats"]["events"]
+        sweep += 1
+    dt = time.perf_counter() - t0
+    v = ev / dt
+    return {"metric": METRIC, "value": v, "unit": UNIT, "n_gpus": 0, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "impl": "reference",
+            "config": {"workload": C5.name, "tiles": list(TILES), "ell": ELL,
+                       "sample": "full sweeps without swaps, one core"},
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": f"{args.steps} sweep(s) of the 1e6-bead melt"},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--lanes", type=int, default=32)
+    ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
+    args = ap.parse_args()
+    rank = int(os.environ.get("RANK", 0))
+    world = int(os.environ.get("WORLD_SIZE", 1))
+    if args.impl == "reference":
+        line = run_reference(args, rank)
+        if line:
+            print(json.dumps(line), flush=True)
+        return
+    if world > 1:
+        import torch
+        torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", 0)))
+        torch.distributed.init_process_group("nccl")
+    if world > 1 or rank != 0:
+        args.cpu_baseline = args.cpu_baseline and rank == 0 and world == 1
+    line = run_gpu(args, rank, world)
+    if line is not None:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

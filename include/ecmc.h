@@ -1,0 +1,228 @@
+/*
+ * ecmc.h — C ABI of the GB300 event-chain Monte Carlo library for melts of
+ * tethered hard-sphere bead chains.
+ *
+ * Method: Kampmann, Boltz, Kierfeld, "Monte Carlo Simulation of Dense Polymer
+ * Melts Using Event Chain Algorithms" (arXiv:1502.06447).
+ *   - EC move: Sec. II, the four-step rule (pick pivot and direction v; move
+ *     the pivot by the largest admissible x <= x_max; hand the move to the
+ *     limiting bead; repeat until x_max = 0), with the min-over-partners rule
+ *     for several interaction partners (Sec. II).
+ *   - Model: hard spheres of diameter sigma (Eq. 1) bonded into chains by
+ *     tethers of maximal length b_max (Sec. II, model paragraph).
+ *   - Parallel form: Sec. II.B — spatial tile-joint decomposition re-drawn
+ *     every sweep, reflection of the EC at tile walls, and reflection of v at
+ *     the plane normal to the bond when the bonded partner cannot move
+ *     (Fig. 2c); the same reflection at a hard-sphere contact with a bead that
+ *     cannot move.
+ *   - Swap move: Sec. II.D (Fig. 4).
+ *
+ * Conventions (every entry point):
+ *   - Returns an ecmc_status; never aborts.  ecmc_last_error() gives a
+ *     one-line message for the calling thread's last failure.
+ *   - Host buffers belong to the caller and are only read/written during the
+ *     call.  Device memory belongs to the library (allocated in
+ *     ecmc_create*, freed in ecmc_destroy).
+ *   - Positions are interleaved xyz doubles, bead b at [3b, 3b+3), wrapped
+ *     into [0, L).  Image counters are interleaved xyz int32; the unwrapped
+ *     position is r + img * L.  Bead b belongs to chain b / N and is bonded to
+ *     b-1 and b+1 of the same chain.
+ *   - Work is issued on the context's stream (default: a stream the library
+ *     creates; see ecmc_set_stream).  Calls that return host data
+ *     synchronise that stream.
+ *   - Device-side failures (event cap exceeded, a staging capacity exceeded)
+ *     are recorded in a status word on the device and returned by the next
+ *     call that synchronises.
+ */
+#ifndef ECMC_H
+#define ECMC_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct ecmc_ctx ecmc_ctx;
+
+typedef enum {
+  ECMC_OK = 0,
+  ECMC_EINVAL = -1,    /* bad argument */
+  ECMC_ENOMEM = -2,    /* device allocation failed */
+  ECMC_ECUDA = -3,     /* CUDA runtime error */
+  ECMC_EOVERLAP = -4,  /* positions overlap (|r_ij| < sigma) */
+  ECMC_ETETHER = -5,   /* a bond longer than b_max */
+  ECMC_ESTUCK = -6,    /* an EC exceeded the event cap */
+  ECMC_ECKPT = -7,     /* checkpoint file unreadable or inconsistent */
+  ECMC_ECAPACITY = -8  /* a tile holds more beads than the staging buffer */
+} ecmc_status;
+
+enum { ECMC_MODE_SERIAL = 0, ECMC_MODE_DOMAIN = 1 };
+enum { ECMC_DIR_CART3 = 0, ECMC_DIR_ISO = 1 };
+enum { ECMC_PREC_FP64 = 0, ECMC_PREC_FP32F = 1 };
+
+/* event outcomes, also the order of ecmc_obs.events[] */
+enum {
+  ECMC_EV_END = 0,        /* x_max used up */
+  ECMC_EV_PASS = 1,       /* free flight capped at s_cap; same pivot continues */
+  ECMC_EV_WALL = 2,       /* tile wall: v's normal component flipped */
+  ECMC_EV_HS_LIFT = 3,    /* hard-sphere contact, EC handed to the hit bead */
+  ECMC_EV_HS_REFLECT = 4, /* contact with an immotile bead: v reflected */
+  ECMC_EV_TE_LIFT = 5,    /* tether taut, EC handed to the bonded bead */
+  ECMC_EV_TE_REFLECT = 6, /* tether taut, partner immotile: v reflected */
+  ECMC_EV_SWAP = 7,       /* contact, swap accepted: same pivot continues */
+  ECMC_NEV = 8
+};
+
+/* Run options.  Zero-initialise and set what you need; zero fields take
+ * the defaults given. */
+typedef struct ecmc_opts {
+  int32_t mode;          /* ECMC_MODE_SERIAL (undecomposed) or _DOMAIN */
+  int32_t dir_mode;      /* ECMC_DIR_CART3: v in {+x,+y,+z}; _ISO: uniform on S^2 */
+  int32_t precision;     /* ECMC_PREC_FP64: every candidate in FP64;
+                            _FP32F: FP32 screen + FP64 confirm (same events) */
+  int32_t tiles[3];      /* tiles per axis D (domain mode); >= 3 */
+  double joint;          /* joint width w (domain mode); 0 -> b_max; must be >= b_max */
+  double s_cap;          /* longest single free flight; 0 -> 0.25 sigma */
+  int64_t event_cap;     /* events per EC before ECMC_ESTUCK; 0 -> 10^7 */
+  double p_swap;         /* swap proposal probability at a motile contact */
+  int32_t ecs_per_tile;  /* ECs per tile per sweep (domain); 0 -> 1 */
+  int32_t lanes;         /* lanes per EC: 32, 16 or 8; 0 -> 32 */
+  int32_t record;        /* 1: keep per-EC digests / lift sums of the last run */
+  int32_t stage_cap;     /* staged beads per tile; 0 -> derived from the tile size */
+  double cell_side;      /* side of the global cell grid (domain); 0 -> 1.0 sigma */
+} ecmc_opts;
+
+/* Observables and counters (Sec. III observables; see ecmc_observables). */
+typedef struct ecmc_obs {
+  int64_t n_beads, n_chains, N;
+  int64_t sweeps;              /* domain sweeps run so far */
+  int64_t ecs;                 /* ECs run so far */
+  int64_t events[ECMC_NEV];    /* event outcomes so far */
+  int64_t events_total;
+  int64_t swap_tried;
+  double lift_sum;             /* sum over lifts of (r_target - r_pivot).v */
+  double refl_sum;             /* same projection at immotile contacts */
+  double disp_sum;             /* sum of all free flights (= ecs * ell) */
+  double ell_sum;              /* sum of ell over ECs */
+  double pressure;             /* betaP/rho = 1 + lift_sum / ell_sum */
+  double re2_mean;             /* <R_e^2> over chains (minimum-image bonds) */
+  double bond_max, bond_min;   /* longest / shortest bond */
+  int64_t overlaps;            /* pairs with |r_ij|^2 < sigma^2 (1 - 1e-10) */
+  int64_t tether_violations;   /* bonds with b^2 > b_max^2 (1 + 1e-10) */
+  double g1;                   /* middle-bead MSD vs the reference snapshot */
+  double device_seconds;       /* device time of all ecmc_run calls */
+  double ec_kernel_seconds;    /* device time of the EC kernel launches alone */
+  int64_t confirmed;           /* FP64 confirmations of the FP32 screen */
+} ecmc_obs;
+
+/* One EC event of the parity log (ecmc_event_log). */
+typedef struct ecmc_event {
+  int64_t unit;      /* EC ordinal within the last run */
+  int32_t seq;       /* event index within the EC */
+  int32_t pivot;     /* pivot bead id before the event */
+  int32_t kind;      /* ECMC_EV_* */
+  int32_t pad;
+  int64_t partner;   /* bead id, wall axis, or -1 */
+  double x;          /* free flight of the pivot */
+} ecmc_event;
+
+/* ---- creation ----------------------------------------------------------
+ * ecmc_create_lattice: melt on an n0 x n1 x n2 simple-cubic lattice with
+ * spacing a in a periodic box L = dims * a.  Sites are visited in a 3-D
+ * snake (x fastest, reversing every row; y reversing every plane) and cut
+ * into consecutive runs of N beads = chains, so every bond is one lattice
+ * step (requires sigma <= a <= b_max and N | n0 n1 n2).  Each coordinate is
+ * moved by jitter*(2u-1), u from Philox4x64-10 with key (seed, 0) and counter
+ * (4, 0, bead, 0), words 0..2 for x..z; jitter 0 keeps the exact lattice.
+ * (The paper builds melts by random-walk growth and push-off, Sec. II.C; the
+ * lattice start is a synthetic stand-in.)  Checks the start for overlaps
+ * and tether violations (ECMC_EOVERLAP / ECMC_ETETHER).  *out receives the
+ * context. */
+ecmc_status ecmc_create_lattice(const int32_t dims[3], double spacing,
+                                double jitter, uint64_t seed, int32_t N,
+                                double sigma, double b_max, ecmc_ctx **out);
+
+/* ecmc_create: melt of n_chains chains of N beads at volume fraction phi.
+ * box: NULL or {0,0,0} -> a cube with phi = n pi sigma^3 / (6 V); otherwise
+ * the box must agree with phi within 1e-3 relative.  The beads are placed
+ * on the lattice of ecmc_create_lattice whose dims are the factorisation of
+ * n_chains*N closest to the box shape (jitter 0.01 sigma, seed 0). */
+ecmc_status ecmc_create(const double box[3], double phi, int32_t n_chains,
+                        int32_t N, double sigma, double b_max, ecmc_ctx **out);
+
+void ecmc_destroy(ecmc_ctx *ctx);
+const char *ecmc_last_error(void);
+
+/* Use this CUDA stream (a cudaStream_t passed as void*) for all work of the
+ * context; NULL restores the library's own stream. */
+ecmc_status ecmc_set_stream(ecmc_ctx *ctx, void *stream);
+
+/* ---- state --------------------------------------------------------------
+ * xyz: host, 3n doubles (caller-owned).  set: wraps into [0,L), resets the
+ * image counters to 0 unless img is given (3n int32, may be NULL), checks
+ * overlaps and tethers. */
+ecmc_status ecmc_set_positions(ecmc_ctx *ctx, const double *xyz,
+                               const int32_t *img);
+ecmc_status ecmc_get_positions(ecmc_ctx *ctx, double *xyz_out,
+                               int32_t *img_out /* may be NULL */);
+/* box, bead count, chain length */
+ecmc_status ecmc_get_info(ecmc_ctx *ctx, double box[3], int64_t *n_beads,
+                          int32_t *N);
+
+/* ---- running ------------------------------------------------------------ */
+ecmc_status ecmc_configure(ecmc_ctx *ctx, const ecmc_opts *opts);
+
+/* ecmc_run: serial mode: chains_per_sweep ECs (all of them, n_sweeps is
+ * ignored), EC j of the context's lifetime starting at a uniform bead with
+ * Philox counter (1, 0, j, attempt).  Domain mode: n_sweeps sweeps; in
+ * sweep s the tile shift comes from Philox counter (2, s, 0, 0) and every
+ * tile holding motile beads runs ecs_per_tile ECs (chains_per_sweep <= 0
+ * keeps opts.ecs_per_tile, > 0 overrides it).  Each EC has total displacement
+ * ell.  Sweeps and ECs continue the context's counters, so a run split in
+ * two calls equals one call. */
+ecmc_status ecmc_run(ecmc_ctx *ctx, double ell, int64_t chains_per_sweep,
+                     uint64_t seed, int64_t n_sweeps);
+
+/* Swap moves (Sec. II.D).  Sets p_swap so that the swap attempts per bead
+ * per sweep match the target, from the motile hard-sphere contacts counted
+ * so far (needs a previous ecmc_run with p_swap = 0): p_swap =
+ * min(1, target * n_beads * sweeps / contacts).  target 0 disables swaps. */
+ecmc_status ecmc_swap(ecmc_ctx *ctx, double attempts_per_bead_per_sweep);
+
+/* Fused observables over the current state (R_e^2, bonds, overlaps, g1)
+ * together with the counters of all runs so far.  Synchronises. */
+ecmc_status ecmc_observables(ecmc_ctx *ctx, ecmc_obs *out);
+/* take the g1 reference snapshot (unwrapped middle beads) now */
+ecmc_status ecmc_g1_reset(ecmc_ctx *ctx);
+
+/* Per-EC records of the last ecmc_run (opts.record = 1): digest (64-bit
+ * FNV-1a over (pivot, kind<<32|partner, bits of x) of every event), lift sum
+ * and event count, in EC ordinal order: serial -> EC order; domain ->
+ * ((sweep * n_tiles) + tile) * ecs_per_tile + ec, tiles without motile
+ * beads left at digest 0.  Buffers hold at least *n entries on input
+ * (caller-owned host memory); *n receives the count. */
+ecmc_status ecmc_records(ecmc_ctx *ctx, uint64_t *digest, double *lift,
+                         int64_t *events, int64_t *n);
+/* Event log of the last run (opts.record = 1, capacity from ecmc_log_reserve),
+ * unordered across ECs; sort by (unit, seq). */
+ecmc_status ecmc_log_reserve(ecmc_ctx *ctx, int64_t cap);
+ecmc_status ecmc_event_log(ecmc_ctx *ctx, ecmc_event *buf, int64_t cap,
+                           int64_t *n);
+
+/* Domain assignment of sweep `sweep` for the current positions: tile of
+ * each bead (-1 = joint) and the shift.  tags: n int32, shift: 3 doubles. */
+ecmc_status ecmc_domain_tags(ecmc_ctx *ctx, uint64_t seed, int64_t sweep,
+                             int32_t *tags, double shift[3]);
+
+/* ---- checkpoint ---------------------------------------------------------
+ * Binary file: header (magic, version, sizes), positions, images, counters,
+ * opts, and a checksum.  Because every random number is a function of
+ * (seed, sweep/EC counter), restore + run equals an uninterrupted run. */
+ecmc_status ecmc_checkpoint(ecmc_ctx *ctx, const char *path);
+ecmc_status ecmc_restore(ecmc_ctx *ctx, const char *path);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,865 @@
+// C ABI and host orchestration of the EC library (declared in ecmc.h).
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <string>
+#include <vector>
+
+#include "ecmc_dev.cuh"
+#include "ecmc_internal.h"
+
+using namespace ecmc;
+
+namespace {
+thread_local std::string g_err;
+
+ecmc_status fail(ecmc_status s, const char *fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof(buf), fmt, ap);
+  va_end(ap);
+  g_err = buf;
+  return s;
+}
+
+#define CU(call)                                                                    \
+  do {                                                                              \
+    cudaError_t e_ = (call);                                                        \
+    if (e_ != cudaSuccess)                                                          \
+      return fail(e_ == cudaErrorMemoryAllocation ? ECMC_ENOMEM : ECMC_ECUDA,      \
+                  "%s: %s", #call, cudaGetErrorString(e_));                         \
+  } while (0)
+
+template <class T>
+cudaError_t dalloc(T **p, size_t count) {
+  *p = nullptr;
+  if (count == 0) count = 1;
+  return cudaMalloc((void **)p, sizeof(T) * count);
+}
+}  // namespace
+
+struct ecmc_ctx {
+  int64_t n = 0;
+  int32_t N = 1;
+  double L[3] = {0, 0, 0};
+  double sigma = 1.0, b_max = 1.2;
+  ecmc_opts opts{};
+  bool configured = false;
+  // resolved run geometry
+  double s_cap = 0.25, w = 1.2;
+  double T[3] = {0, 0, 0}, W[3] = {0, 0, 0};
+  double halo_hs = 0, halo_te = 0;
+  int32_t nc[3] = {1, 1, 1};
+  double cs[3] = {1, 1, 1};
+  int64_t ncell = 1;
+  int32_t stage_cap = 0;
+  int32_t lanes = 32;
+  int64_t event_cap = 10000000;
+  int32_t ecs_per_tile = 1;
+  // stream
+  cudaStream_t stream = nullptr;
+  cudaStream_t own = nullptr;
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+  // device state
+  double *d_r = nullptr;
+  int32_t *d_img = nullptr;
+  int32_t *d_tag = nullptr, *d_cell = nullptr, *d_rank = nullptr;
+  int32_t *d_count = nullptr, *d_start = nullptr, *d_bsum = nullptr;
+  double *d_cr = nullptr;
+  int32_t *d_cid = nullptr, *d_ctag = nullptr;
+  unsigned long long *d_cnt = nullptr;
+  double *d_sums = nullptr;
+  int *d_status = nullptr;
+  double *d_obs_d = nullptr;
+  unsigned long long *d_obs_u = nullptr;
+  double *d_g1ref = nullptr;
+  bool g1_set = false;
+  // records
+  uint64_t *d_rdig = nullptr;
+  double *d_rlift = nullptr;
+  int64_t *d_rev = nullptr;
+  int64_t rec_cap = 0, rec_n = 0;
+  ecmc_event *d_log = nullptr;
+  unsigned long long *d_log_n = nullptr;
+  int64_t log_cap = 0;
+  // host counters
+  int64_t sweeps_done = 0, ecs_done = 0;
+  double device_seconds = 0.0;
+  double ec_seconds = 0.0;
+  std::vector<cudaEvent_t> kev;  // start/stop pairs around EC launches
+};
+
+namespace {
+
+void free_cells(ecmc_ctx *c) {
+  cudaFree(c->d_count);
+  cudaFree(c->d_start);
+  cudaFree(c->d_bsum);
+  c->d_count = c->d_start = c->d_bsum = nullptr;
+}
+
+ecmc_status alloc_cells(ecmc_ctx *c) {
+  free_cells(c);
+  CU(dalloc(&c->d_count, c->ncell));
+  CU(dalloc(&c->d_start, c->ncell + 1));
+  CU(dalloc(&c->d_bsum, cells_scratch_ints(c->ncell)));
+  return ECMC_OK;
+}
+
+// global cell grid of side >= cell_side (>= sigma), at least 3 per axis
+ecmc_status set_grid(ecmc_ctx *c, double side) {
+  int64_t ncell = 1;
+  for (int a = 0; a < 3; ++a) {
+    int k = (int)floor(c->L[a] / side);
+    if (k < 3) return fail(ECMC_EINVAL, "box too small for the cell grid (axis %d)", a);
+    c->nc[a] = k;
+    c->cs[a] = c->L[a] / k;
+    ncell *= k;
+  }
+  if (ncell != c->ncell || !c->d_count) {
+    c->ncell = ncell;
+    return alloc_cells(c);
+  }
+  return ECMC_OK;
+}
+
+CellParams cell_params(const ecmc_ctx *c, bool domain, uint64_t seed, int64_t sweep) {
+  CellParams C{};
+  C.n = c->n;
+  for (int a = 0; a < 3; ++a) {
+    C.L[a] = c->L[a];
+    C.nc[a] = c->nc[a];
+    C.cs[a] = c->cs[a];
+    C.D[a] = c->opts.tiles[a];
+    C.T[a] = c->T[a];
+    C.W[a] = c->W[a];
+  }
+  C.domain = domain ? 1 : 0;
+  C.seed = seed;
+  C.replica = 0;
+  C.sweep = sweep;
+  C.r = c->d_r;
+  C.tag = c->d_tag;
+  C.cell = c->d_cell;
+  C.rank = c->d_rank;
+  C.count = c->d_count;
+  C.start = c->d_start;
+  C.block_sums = c->d_bsum;
+  C.cr = c->d_cr;
+  C.cid = c->d_cid;
+  C.ctag = c->d_ctag;
+  return C;
+}
+
+ObsParams obs_params(const ecmc_ctx *c) {
+  ObsParams O{};
+  O.n = c->n;
+  O.N = c->N;
+  for (int a = 0; a < 3; ++a) {
+    O.L[a] = c->L[a];
+    O.half[a] = 0.5 * c->L[a];
+    O.nc[a] = c->nc[a];
+  }
+  O.sig2 = c->sigma * c->sigma;
+  O.b2 = c->b_max * c->b_max;
+  O.r = c->d_r;
+  O.img = c->d_img;
+  O.g1ref = c->g1_set ? c->d_g1ref : nullptr;
+  O.cr = c->d_cr;
+  O.cid = c->d_cid;
+  O.cstart = c->d_start;
+  O.cell = c->d_cell;
+  O.out_d = c->d_obs_d;
+  O.out_u = c->d_obs_u;
+  return O;
+}
+
+struct ObsHost {
+  double re2_sum, bmax, bmin, g1_sum;
+  unsigned long long overlaps, viol;
+};
+
+// R_e^2, bonds, overlaps, g1 of the current positions (synchronises)
+ecmc_status measure(ecmc_ctx *c, ObsHost *o) {
+  ecmc_status s = set_grid(c, c->configured && c->opts.cell_side > 0 ? c->opts.cell_side : c->sigma);
+  if (s != ECMC_OK) return s;
+  CU(launch_cells(cell_params(c, false, 0, 0), c->ncell, c->stream));
+  const double init_d[4] = {0.0, 0.0, 1e300, 0.0};
+  CU(cudaMemcpyAsync(c->d_obs_d, init_d, sizeof(init_d), cudaMemcpyHostToDevice, c->stream));
+  CU(cudaMemsetAsync(c->d_obs_u, 0, 2 * sizeof(unsigned long long), c->stream));
+  CU(launch_obs(obs_params(c), c->stream));
+  double hd[4];
+  unsigned long long hu[2];
+  CU(cudaMemcpyAsync(hd, c->d_obs_d, sizeof(hd), cudaMemcpyDeviceToHost, c->stream));
+  CU(cudaMemcpyAsync(hu, c->d_obs_u, sizeof(hu), cudaMemcpyDeviceToHost, c->stream));
+  CU(cudaStreamSynchronize(c->stream));
+  o->re2_sum = hd[0];
+  o->bmax = hd[1];
+  o->bmin = c->N > 1 ? hd[2] : 0.0;
+  o->g1_sum = hd[3];
+  o->overlaps = hu[0];
+  o->viol = hu[1];
+  return ECMC_OK;
+}
+
+ecmc_status check_state(ecmc_ctx *c) {
+  ObsHost o;
+  ecmc_status s = measure(c, &o);
+  if (s != ECMC_OK) return s;
+  if (o.overlaps) return fail(ECMC_EOVERLAP, "%llu overlapping pairs", o.overlaps);
+  if (o.viol) return fail(ECMC_ETETHER, "%llu bonds longer than b_max", o.viol);
+  return ECMC_OK;
+}
+
+ecmc_status alloc_state(ecmc_ctx *c) {
+  CU(dalloc(&c->d_r, 3 * c->n));
+  CU(dalloc(&c->d_img, 3 * c->n));
+  CU(cudaMemset(c->d_img, 0, sizeof(int32_t) * 3 * c->n));
+  CU(dalloc(&c->d_tag, c->n));
+  CU(dalloc(&c->d_cell, c->n));
+  CU(dalloc(&c->d_rank, c->n));
+  CU(dalloc(&c->d_cr, 3 * c->n));
+  CU(dalloc(&c->d_cid, c->n));
+  CU(dalloc(&c->d_ctag, c->n));
+  CU(dalloc(&c->d_cnt, CNT_N));
+  CU(cudaMemset(c->d_cnt, 0, sizeof(unsigned long long) * CNT_N));
+  CU(dalloc(&c->d_sums, SUM_N));
+  CU(cudaMemset(c->d_sums, 0, sizeof(double) * SUM_N));
+  CU(dalloc(&c->d_status, 1));
+  CU(cudaMemset(c->d_status, 0, sizeof(int)));
+  CU(dalloc(&c->d_obs_d, 4));
+  CU(dalloc(&c->d_obs_u, 2));
+  CU(dalloc(&c->d_g1ref, 3 * (c->n / c->N)));
+  CU(cudaStreamCreateWithFlags(&c->own, cudaStreamNonBlocking));
+  c->stream = c->own;
+  CU(cudaEventCreate(&c->ev0));
+  CU(cudaEventCreate(&c->ev1));
+  return ECMC_OK;
+}
+
+void destroy(ecmc_ctx *c) {
+  if (!c) return;
+  if (c->stream) cudaStreamSynchronize(c->stream);
+  void *ptrs[] = {c->d_r, c->d_img, c->d_tag, c->d_cell, c->d_rank, c->d_count, c->d_start,
+                  c->d_bsum, c->d_cr, c->d_cid, c->d_ctag, c->d_cnt, c->d_sums, c->d_status,
+                  c->d_obs_d, c->d_obs_u, c->d_g1ref, c->d_rdig, c->d_rlift, c->d_rev,
+                  c->d_log, c->d_log_n};
+  for (void *p : ptrs) cudaFree(p);
+  for (cudaEvent_t e : c->kev) cudaEventDestroy(e);
+  if (c->ev0) cudaEventDestroy(c->ev0);
+  if (c->ev1) cudaEventDestroy(c->ev1);
+  if (c->own) cudaStreamDestroy(c->own);
+  delete c;
+}
+
+ecmc_status device_status(ecmc_ctx *c) {
+  int st = 0;
+  CU(cudaMemcpyAsync(&st, c->d_status, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+  CU(cudaStreamSynchronize(c->stream));
+  if (st == DEV_STUCK) return fail(ECMC_ESTUCK, "an event chain exceeded the event cap");
+  if (st == DEV_CAPACITY) return fail(ECMC_ECAPACITY, "a tile exceeded the staging capacity");
+  if (st == DEV_TILE) return fail(ECMC_ECAPACITY, "a bonded partner was not staged with its tile");
+  return ECMC_OK;
+}
+
+ecmc_status make_ctx(const int32_t dims[3], double spacing, double jitter, uint64_t seed,
+                     int32_t N, double sigma, double b_max, ecmc_ctx **out) {
+  if (!out) return fail(ECMC_EINVAL, "out is NULL");
+  *out = nullptr;
+  if (!dims || dims[0] < 1 || dims[1] < 1 || dims[2] < 1)
+    return fail(ECMC_EINVAL, "lattice dims must be >= 1");
+  if (!(sigma > 0.0)) return fail(ECMC_EINVAL, "sigma must be > 0");
+  if (!(b_max >= sigma)) return fail(ECMC_EINVAL, "b_max must be >= sigma");
+  if (N < 1) return fail(ECMC_EINVAL, "N must be >= 1");
+  const int64_t n = (int64_t)dims[0] * dims[1] * dims[2];
+  if (n % N) return fail(ECMC_EINVAL, "N must divide the number of sites");
+  if (n >= (1ll << 29)) return fail(ECMC_EINVAL, "at most 2^29 beads");
+  if (!(spacing >= sigma) || (N > 1 && !(spacing <= b_max)))
+    return fail(ECMC_EINVAL, "need sigma <= spacing <= b_max");
+  if (!(jitter >= 0.0) || !(2.0 * jitter < spacing - sigma + 1e-300) && jitter > 0.0)
+    return fail(ECMC_EINVAL, "jitter must be in [0, (spacing - sigma)/2)");
+  ecmc_ctx *c = new ecmc_ctx();
+  c->n = n;
+  c->N = N;
+  for (int a = 0; a < 3; ++a) c->L[a] = dims[a] * spacing;
+  c->sigma = sigma;
+  c->b_max = b_max;
+  ecmc_status s = alloc_state(c);
+  if (s != ECMC_OK) {
+    destroy(c);
+    return s;
+  }
+  cudaError_t e = launch_lattice(dims, spacing, jitter, seed, 0, c->d_r, n, c->stream);
+  if (e != cudaSuccess) {
+    destroy(c);
+    return fail(ECMC_ECUDA, "lattice: %s", cudaGetErrorString(e));
+  }
+  s = check_state(c);
+  if (s != ECMC_OK) {
+    destroy(c);
+    return s;
+  }
+  *out = c;
+  return ECMC_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *ecmc_last_error(void) { return g_err.c_str(); }
+
+ecmc_status ecmc_create_lattice(const int32_t dims[3], double spacing, double jitter,
+                                uint64_t seed, int32_t N, double sigma, double b_max,
+                                ecmc_ctx **out) {
+  return make_ctx(dims, spacing, jitter, seed, N, sigma, b_max, out);
+}
+
+ecmc_status ecmc_create(const double box[3], double phi, int32_t n_chains, int32_t N,
+                        double sigma, double b_max, ecmc_ctx **out) {
+  if (!(phi > 0.0 && phi < 0.74)) return fail(ECMC_EINVAL, "phi must be in (0, 0.74)");
+  if (n_chains < 1 || N < 1) return fail(ECMC_EINVAL, "n_chains and N must be >= 1");
+  if (!(sigma > 0.0)) return fail(ECMC_EINVAL, "sigma must be > 0");
+  const int64_t n = (int64_t)n_chains * N;
+  const double vbead = M_PI * sigma * sigma * sigma / 6.0;
+  double Lb[3];
+  const bool given = box && (box[0] > 0.0 || box[1] > 0.0 || box[2] > 0.0);
+  if (given) {
+    if (!(box[0] > 0 && box[1] > 0 && box[2] > 0)) return fail(ECMC_EINVAL, "box must be > 0");
+    const double phib = n * vbead / (box[0] * box[1] * box[2]);
+    if (fabs(phib - phi) > 1e-3 * phi)
+      return fail(ECMC_EINVAL, "box gives phi=%.6f, not %.6f", phib, phi);
+    for (int a = 0; a < 3; ++a) Lb[a] = box[a];
+  } else {
+    const double side = cbrt(n * vbead / phi);
+    Lb[0] = Lb[1] = Lb[2] = side;
+  }
+  // factor n into dims close to the box shape, all with the same spacing
+  double best = 1e300;
+  int32_t bd[3] = {0, 0, 0};
+  const double a0 = cbrt(Lb[0] * Lb[1] * Lb[2] / (double)n);
+  for (int64_t x = 1; x <= n && x <= 4096; ++x) {
+    if (n % x) continue;
+    const int64_t r = n / x;
+    for (int64_t y = 1; y <= r && y <= 4096; ++y) {
+      if (r % y) continue;
+      const int64_t z = r / y;
+      const double e = fabs(log(x * a0 / Lb[0])) + fabs(log(y * a0 / Lb[1])) + fabs(log(z * a0 / Lb[2]));
+      if (e < best) {
+        best = e;
+        bd[0] = (int32_t)x;
+        bd[1] = (int32_t)y;
+        bd[2] = (int32_t)z;
+      }
+    }
+  }
+  if (!bd[0]) return fail(ECMC_EINVAL, "cannot factor n into a lattice");
+  if (fabs(bd[0] * a0 - Lb[0]) > 1e-9 * Lb[0] || fabs(bd[1] * a0 - Lb[1]) > 1e-9 * Lb[1] ||
+      fabs(bd[2] * a0 - Lb[2]) > 1e-9 * Lb[2]) {
+    if (given) return fail(ECMC_EINVAL, "box shape does not fit a lattice of n sites");
+  }
+  return make_ctx(bd, a0, 0.01 * sigma, 0, N, sigma, b_max, out);
+}
+
+void ecmc_destroy(ecmc_ctx *ctx) { destroy(ctx); }
+
+ecmc_status ecmc_set_stream(ecmc_ctx *c, void *stream) {
+  if (!c) return fail(ECMC_EINVAL, "ctx is NULL");
+  CU(cudaStreamSynchronize(c->stream));
+  c->stream = stream ? (cudaStream_t)stream : c->own;
+  return ECMC_OK;
+}
+
+ecmc_status ecmc_get_info(ecmc_ctx *c, double box[3], int64_t *n_beads, int32_t *N) {
+  if (!c) return fail(ECMC_EINVAL, "ctx is NULL");
+  if (box)
+    for (int a = 0; a < 3; ++a) box[a] = c->L[a];
+  if (n_beads) *n_beads = c->n;
+  if (N) *N = c->N;
+  return ECMC_OK;
+}
+
+ecmc_status ecmc_set_positions(ecmc_ctx *c, const double *xyz, const int32_t *img) {
+  if (!c || !xyz) return fail(ECMC_EINVAL, "NULL argument");
+  std::vector<double> r(3 * c->n);
+  std::vector<int32_t> im(3 * c->n, 0);
+  for (int64_t b = 0; b < c->n; ++b)
+    for (int a = 0; a < 3; ++a) {
+      double x = xyz[3 * b + a];
+      if (!isfinite(x)) return fail(ECMC_EINVAL, "non-finite position");
+      const double f = floor(x / c->L[a]);
+      x -= f * c->L[a];
+      if (x >= c->L[a]) x -= c->L[a];
+      if (x < 0) x = 0;
+      r[3 * b + a] = x;
+      im[3 * b + a] = (img ? img[3 * b + a] : 0) + (int32_t)f;
+    }
+  CU(cudaMemcpyAsync(c->d_r, r.data(), sizeof(double) * r.size(), cudaMemcpyHostToDevice, c->stream));
+  CU(cudaMemcpyAsync(c->d_img, im.data(), sizeof(int32_t) * im.size(), cudaMemcpyHostToDevice, c->stream));
+  c->g1_set = false;
+  return check_state(c);
+}
+
+ecmc_status ecmc_get_positions(ecmc_ctx *c, double *xyz, int32_t *img) {
+  if (!c || !xyz) return fail(ECMC_EINVAL, "NULL argument");
+  CU(cudaMemcpyAsync(xyz, c->d_r, sizeof(double) * 3 * c->n, cudaMemcpyDeviceToHost, c->stream));
+  if (img) CU(cudaMemcpyAsync(img, c->d_img, sizeof(int32_t) * 3 * c->n, cudaMemcpyDeviceToHost, c->stream));
+  CU(cudaStreamSynchronize(c->stream));
+  return ECMC_OK;
+}
+
+ecmc_status ecmc_configure(ecmc_ctx *c, const ecmc_opts *o) {
+  if (!c || !o) return fail(ECMC_EINVAL, "NULL argument");
+  ecmc_opts p = *o;
+  if (p.mode != ECMC_MODE_SERIAL && p.mode != ECMC_MODE_DOMAIN) return fail(ECMC_EINVAL, "bad mode");
+  if (p.dir_mode != ECMC_DIR_CART3 && p.dir_mode != ECMC_DIR_ISO) return fail(ECMC_EINVAL, "bad dir_mode");
+  if (p.precision != ECMC_PREC_FP64 && p.precision != ECMC_PREC_FP32F)
+    return fail(ECMC_EINVAL, "bad precision");
+  const double sig = c->sigma;
+  const double s_cap = p.s_cap > 0 ? p.s_cap : 0.25 * sig;
+  const double w = p.joint > 0 ? p.joint : c->b_max;
+  if (!(w >= c->b_max)) return fail(ECMC_EINVAL, "joint width must be >= b_max");
+  const int lanes = p.lanes ? p.lanes : 32;
+  if (lanes != 32 && lanes != 16 && lanes != 8) return fail(ECMC_EINVAL, "lanes must be 8, 16 or 32");
+  if (!(p.p_swap >= 0.0)) return fail(ECMC_EINVAL, "p_swap must be >= 0");
+  const double margin = p.precision == ECMC_PREC_FP32F ? 0.01 * sig : 0.0;
+  for (int a = 0; a < 3; ++a)
+    if (!(s_cap + sig + margin < 0.5 * c->L[a])) return fail(ECMC_EINVAL, "need s_cap + sigma < L/2");
+  const double halo_hs = sig * (1.0 + 1e-6);
+  const double halo_te = (c->b_max > sig ? c->b_max : sig) * (1.0 + 1e-6);
+  int32_t stage = p.stage_cap;
+  if (p.mode == ECMC_MODE_DOMAIN) {
+    for (int a = 0; a < 3; ++a) {
+      if (p.tiles[a] < 3) return fail(ECMC_EINVAL, "tiles per axis must be >= 3");
+      const double T = c->L[a] / p.tiles[a];
+      const double W = T - w;
+      if (!(W > 0.0)) return fail(ECMC_EINVAL, "tile narrower than the joint");
+      if (!(W + 2.0 * halo_te < 0.5 * c->L[a]))
+        return fail(ECMC_EINVAL, "tile plus halo must be < L/2 (use more tiles)");
+      if (p.precision == ECMC_PREC_FP32F && !(W + 2.0 * halo_te <= 64.0 * sig))
+        return fail(ECMC_EINVAL, "FP32 screen needs tiles of at most 64 sigma");
+      c->T[a] = T;
+      c->W[a] = W;
+    }
+    if (stage <= 0) {
+      const double rho = (double)c->n / (c->L[0] * c->L[1] * c->L[2]);
+      double vol = 1.0;
+      for (int a = 0; a < 3; ++a) vol *= c->W[a] + 2.0 * halo_te;
+      stage = (int32_t)(rho * vol * 1.6 + 64);
+      stage = (stage + 31) / 32 * 32;
+    }
+  } else {
+    if (p.precision == ECMC_PREC_FP32F)
+      for (int a = 0; a < 3; ++a)
+        if (!(c->L[a] <= 64.0 * sig)) return fail(ECMC_EINVAL, "FP32 screen (serial) needs L <= 64 sigma");
+    stage = (int32_t)c->n;
+  }
+  if (stage > (1 << 20) - 1) return fail(ECMC_EINVAL, "stage capacity too large");
+  int dev = 0, smem_max = 0;
+  CU(cudaGetDevice(&dev));
+  CU(cudaDeviceGetAttribute(&smem_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+  const int gmin = 32 / lanes;
+  if ((int64_t)ec_smem_bytes(stage, lanes, gmin) > smem_max)
+    return fail(ECMC_EINVAL, "staging needs %lld bytes of shared memory (max %d)",
+                (long long)ec_smem_bytes(stage, lanes, gmin), smem_max);
+  c->opts = p;
+  c->s_cap = s_cap;
+  c->w = w;
+  c->halo_hs = halo_hs;
+  c->halo_te = halo_te;
+  c->stage_cap = stage;
+  c->lanes = lanes;
+  c->event_cap = p.event_cap > 0 ? p.event_cap : 10000000;
+  c->ecs_per_tile = p.ecs_per_tile > 0 ? p.ecs_per_tile : 1;
+  c->configured = true;
+  const double side = p.cell_side > 0 ? p.cell_side : sig;
+  if (!(side >= sig)) return fail(ECMC_EINVAL, "cell side must be >= sigma");
+  return set_grid(c, side);
+}
+
+ecmc_status ecmc_log_reserve(ecmc_ctx *c, int64_t cap) {
+  if (!c || cap < 0) return fail(ECMC_EINVAL, "bad argument");
+  cudaFree(c->d_log);
+  cudaFree(c->d_log_n);
+  c->d_log = nullptr;
+  c->d_log_n = nullptr;
+  c->log_cap = 0;
+  if (cap > 0) {
+    CU(dalloc(&c->d_log, cap));
+    CU(dalloc(&c->d_log_n, 1));
+    c->log_cap = cap;
+  }
+  return ECMC_OK;
+}
+
+static ecmc_status reserve_records(ecmc_ctx *c, int64_t units) {
+  if (units <= c->rec_cap) return ECMC_OK;
+  cudaFree(c->d_rdig);
+  cudaFree(c->d_rlift);
+  cudaFree(c->d_rev);
+  c->d_rdig = nullptr;
+  c->d_rlift = nullptr;
+  c->d_rev = nullptr;
+  c->rec_cap = 0;
+  CU(dalloc(&c->d_rdig, units));
+  CU(dalloc(&c->d_rlift, units));
+  CU(dalloc(&c->d_rev, units));
+  c->rec_cap = units;
+  return ECMC_OK;
+}
+
+// one EC launch between a pair of events (the pair is reused across runs)
+static cudaError_t timed_ec(ecmc_ctx *c, const ECParams &P, int64_t slot) {
+  while ((int64_t)c->kev.size() < slot + 2) {
+    cudaEvent_t e;
+    cudaError_t err = cudaEventCreate(&e);
+    if (err != cudaSuccess) return err;
+    c->kev.push_back(e);
+  }
+  cudaError_t err = cudaEventRecord(c->kev[slot], c->stream);
+  if (err != cudaSuccess) return err;
+  err = launch_ec(P, c->lanes, c->opts.precision == ECMC_PREC_FP32F, c->stream);
+  if (err != cudaSuccess) return err;
+  return cudaEventRecord(c->kev[slot + 1], c->stream);
+}
+
+static ECParams ec_params(const ecmc_ctx *c, uint64_t seed, double ell) {
+  ECParams P{};
+  P.n = c->n;
+  P.N = c->N;
+  for (int a = 0; a < 3; ++a) {
+    P.L[a] = c->L[a];
+    P.half[a] = 0.5 * c->L[a];
+    P.D[a] = c->opts.tiles[a];
+    P.T[a] = c->T[a];
+    P.W[a] = c->W[a];
+    P.nc[a] = c->nc[a];
+    P.cs[a] = c->cs[a];
+  }
+  P.sigma = c->sigma;
+  P.sig2 = c->sigma * c->sigma;
+  P.b2 = c->b_max * c->b_max;
+  P.s_cap = c->s_cap;
+  P.domain = c->opts.mode == ECMC_MODE_DOMAIN;
+  P.halo_hs = c->halo_hs;
+  P.halo_te = c->halo_te;
+  P.seed = seed;
+  P.replica = 0;
+  P.ell = ell;
+  P.event_cap = c->event_cap;
+  P.p_swap = c->opts.p_swap;
+  P.dir_mode = c->opts.dir_mode;
+  P.stage_cap = c->stage_cap;
+  // FP32 screen margins for tile-local coordinates below 64 sigma (the
+  // rounding errors they cover are at most ~1/14 of these)
+  P.eps_v = (float)(2e-4 * c->sigma);
+  P.eps_d = (float)(1e-3 * c->sigma * c->sigma);
+  P.eps_x = (float)(2e-4 * c->sigma);
+  P.r = c->d_r;
+  P.img = c->d_img;
+  P.cr = c->d_cr;
+  P.cid = c->d_cid;
+  P.ctag = c->d_ctag;
+  P.cstart = c->d_start;
+  P.counters = c->d_cnt;
+  P.sums = c->d_sums;
+  P.status = c->d_status;
+  return P;
+}
+
+ecmc_status ecmc_run(ecmc_ctx *c, double ell, int64_t chains_per_sweep, uint64_t seed,
+                     int64_t n_sweeps) {
+  if (!c) return fail(ECMC_EINVAL, "ctx is NULL");
+  if (!c->configured) return fail(ECMC_EINVAL, "call ecmc_configure first");
+  if (!(ell >= 0.0) || !isfinite(ell)) return fail(ECMC_EINVAL, "ell must be finite and >= 0");
+  const bool domain = c->opts.mode == ECMC_MODE_DOMAIN;
+  const int64_t ntile = (int64_t)c->opts.tiles[0] * c->opts.tiles[1] * c->opts.tiles[2];
+  const int k = domain ? (chains_per_sweep > 0 ? (int)chains_per_sweep : c->ecs_per_tile) : 1;
+  int64_t units;
+  if (domain) {
+    if (n_sweeps < 0) return fail(ECMC_EINVAL, "n_sweeps must be >= 0");
+    units = n_sweeps * ntile * k;
+  } else {
+    if (chains_per_sweep < 0) return fail(ECMC_EINVAL, "chains_per_sweep must be >= 0");
+    units = chains_per_sweep;
+  }
+  CU(cudaMemsetAsync(c->d_status, 0, sizeof(int), c->stream));
+  ECParams P = ec_params(c, seed, ell);
+  if (c->opts.record) {
+    ecmc_status s = reserve_records(c, units);
+    if (s != ECMC_OK) return s;
+    CU(cudaMemsetAsync(c->d_rdig, 0, sizeof(uint64_t) * (units ? units : 1), c->stream));
+    CU(cudaMemsetAsync(c->d_rlift, 0, sizeof(double) * (units ? units : 1), c->stream));
+    CU(cudaMemsetAsync(c->d_rev, 0, sizeof(int64_t) * (units ? units : 1), c->stream));
+    P.rec_digest = c->d_rdig;
+    P.rec_lift = c->d_rlift;
+    P.rec_events = c->d_rev;
+    P.rec_cap = units;
+    c->rec_n = units;
+    if (c->d_log) {
+      CU(cudaMemsetAsync(c->d_log_n, 0, sizeof(unsigned long long), c->stream));
+      P.log = c->d_log;
+      P.log_n = c->d_log_n;
+      P.log_cap = c->log_cap;
+    }
+  }
+  CU(cudaEventRecord(c->ev0, c->stream));
+  if (domain) {
+    P.n_units = (int32_t)ntile;
+    P.ecs_per_tile = k;
+    for (int64_t s = 0; s < n_sweeps; ++s) {
+      const int64_t sweep = c->sweeps_done + s;
+      CU(launch_cells(cell_params(c, true, seed, sweep), c->ncell, c->stream));
+      P.sweep = sweep;
+      P.rec_offset = s * ntile * k;
+      CU(timed_ec(c, P, 2 * s));
+    }
+  } else {
+    P.n_units = 1;
+    const int64_t chunk = 4096;
+    for (int64_t j0 = 0; j0 < units; j0 += chunk) {
+      const int64_t cnt = units - j0 < chunk ? units - j0 : chunk;
+      P.sweep = c->ecs_done + j0;
+      P.ecs_per_tile = (int32_t)cnt;
+      P.rec_offset = j0;
+      CU(timed_ec(c, P, 2 * (j0 / chunk)));
+    }
+  }
+  CU(cudaEventRecord(c->ev1, c->stream));
+  ecmc_status s = device_status(c);
+  float ms = 0.f;
+  CU(cudaEventElapsedTime(&ms, c->ev0, c->ev1));
+  c->device_seconds += 1e-3 * ms;
+  const int64_t launches = domain ? n_sweeps : (units + 4095) / 4096;
+  for (int64_t i = 0; i < launches; ++i) {
+    float kms = 0.f;
+    CU(cudaEventElapsedTime(&kms, c->kev[2 * i], c->kev[2 * i + 1]));
+    c->ec_seconds += 1e-3 * kms;
+  }
+  if (domain) c->sweeps_done += n_sweeps;
+  else c->ecs_done += units;
+  return s;
+}
+
+ecmc_status ecmc_swap(ecmc_ctx *c, double target) {
+  if (!c) return fail(ECMC_EINVAL, "ctx is NULL");
+  if (!(target >= 0.0)) return fail(ECMC_EINVAL, "target must be >= 0");
+  if (target == 0.0) {
+    c->opts.p_swap = 0.0;
+    return ECMC_OK;
+  }
+  unsigned long long h[CNT_N];
+  CU(cudaMemcpyAsync(h, c->d_cnt, sizeof(h), cudaMemcpyDeviceToHost, c->stream));
+  CU(cudaStreamSynchronize(c->stream));
+  const double contacts = (double)(h[ECMC_EV_HS_LIFT] + h[ECMC_EV_SWAP]);
+  const double sweeps = c->opts.mode == ECMC_MODE_DOMAIN ? (double)c->sweeps_done
+                                                          : (double)c->ecs_done / (double)c->n;
+  if (!(contacts > 0.0) || !(sweeps > 0.0))
+    return fail(ECMC_EINVAL, "run EC sweeps before calibrating swaps");
+  double p = target * (double)c->n * sweeps / contacts;
+  c->opts.p_swap = p > 1.0 ? 1.0 : p;
+  return ECMC_OK;
+}
+
+ecmc_status ecmc_observables(ecmc_ctx *c, ecmc_obs *out) {
+  if (!c || !out) return fail(ECMC_EINVAL, "NULL argument");
+  ObsHost o;
+  ecmc_status s = measure(c, &o);
+  if (s != ECMC_OK) return s;
+  unsigned long long h[CNT_N];
+  double sums[SUM_N];
+  CU(cudaMemcpyAsync(h, c->d_cnt, sizeof(h), cudaMemcpyDeviceToHost, c->stream));
+  CU(cudaMemcpyAsync(sums, c->d_sums, sizeof(sums), cudaMemcpyDeviceToHost, c->stream));
+  CU(cudaStreamSynchronize(c->stream));
+  memset(out, 0, sizeof(*out));
+  out->n_beads = c->n;
+  out->n_chains = c->n / c->N;
+  out->N = c->N;
+  out->sweeps = c->sweeps_done;
+  out->ecs = (int64_t)h[CNT_ECS];
+  for (int k = 0; k < ECMC_NEV; ++k) out->events[k] = (int64_t)h[k];
+  out->events_total = (int64_t)h[CNT_EVENTS];
+  out->swap_tried = (int64_t)h[CNT_SWAP_TRIED];
+  out->lift_sum = sums[SUM_LIFT];
+  out->refl_sum = sums[SUM_REFL];
+  out->disp_sum = sums[SUM_DISP];
+  out->ell_sum = sums[SUM_DISP];  // every EC displaces exactly its ell in total
+  out->pressure = out->ell_sum > 0 ? 1.0 + out->lift_sum / out->ell_sum : 0.0;
+  out->re2_mean = o.re2_sum / (double)(c->n / c->N);
+  out->bond_max = o.bmax;
+  out->bond_min = o.bmin;
+  out->overlaps = (int64_t)o.overlaps;
+  out->tether_violations = (int64_t)o.viol;
+  out->g1 = c->g1_set ? o.g1_sum / (double)(c->n / c->N) : 0.0;
+  out->device_seconds = c->device_seconds;
+  out->ec_kernel_seconds = c->ec_seconds;
+  out->confirmed = (int64_t)h[CNT_CONFIRMED];
+  return ECMC_OK;
+}
+
+ecmc_status ecmc_g1_reset(ecmc_ctx *c) {
+  if (!c) return fail(ECMC_EINVAL, "ctx is NULL");
+  CU(launch_g1_snapshot(obs_params(c), c->d_g1ref, c->stream));
+  c->g1_set = true;
+  CU(cudaStreamSynchronize(c->stream));
+  return ECMC_OK;
+}
+
+ecmc_status ecmc_records(ecmc_ctx *c, uint64_t *digest, double *lift, int64_t *events,
+                         int64_t *n) {
+  if (!c || !n) return fail(ECMC_EINVAL, "NULL argument");
+  if (!c->d_rdig) {
+    *n = 0;
+    return ECMC_OK;
+  }
+  const int64_t cnt = c->rec_n < *n ? c->rec_n : *n;
+  if (digest) CU(cudaMemcpyAsync(digest, c->d_rdig, sizeof(uint64_t) * cnt, cudaMemcpyDeviceToHost, c->stream));
+  if (lift) CU(cudaMemcpyAsync(lift, c->d_rlift, sizeof(double) * cnt, cudaMemcpyDeviceToHost, c->stream));
+  if (events) CU(cudaMemcpyAsync(events, c->d_rev, sizeof(int64_t) * cnt, cudaMemcpyDeviceToHost, c->stream));
+  CU(cudaStreamSynchronize(c->stream));
+  *n = cnt;
+  return ECMC_OK;
+}
+
+ecmc_status ecmc_event_log(ecmc_ctx *c, ecmc_event *buf, int64_t cap, int64_t *n) {
+  if (!c || !n) return fail(ECMC_EINVAL, "NULL argument");
+  if (!c->d_log) {
+    *n = 0;
+    return ECMC_OK;
+  }
+  unsigned long long used = 0;
+  CU(cudaMemcpyAsync(&used, c->d_log_n, sizeof(used), cudaMemcpyDeviceToHost, c->stream));
+  CU(cudaStreamSynchronize(c->stream));
+  int64_t cnt = (int64_t)used;
+  if (cnt > c->log_cap) cnt = c->log_cap;
+  if (cnt > cap) cnt = cap;
+  if (buf && cnt > 0)
+    CU(cudaMemcpyAsync(buf, c->d_log, sizeof(ecmc_event) * cnt, cudaMemcpyDeviceToHost, c->stream));
+  CU(cudaStreamSynchronize(c->stream));
+  *n = cnt;
+  return ECMC_OK;
+}
+
+ecmc_status ecmc_domain_tags(ecmc_ctx *c, uint64_t seed, int64_t sweep, int32_t *tags,
+                             double shift[3]) {
+  if (!c || !tags) return fail(ECMC_EINVAL, "NULL argument");
+  if (!c->configured || c->opts.mode != ECMC_MODE_DOMAIN)
+    return fail(ECMC_EINVAL, "configure the domain mode first");
+  CU(launch_cells(cell_params(c, true, seed, sweep), c->ncell, c->stream));
+  CU(cudaMemcpyAsync(tags, c->d_tag, sizeof(int32_t) * c->n, cudaMemcpyDeviceToHost, c->stream));
+  CU(cudaStreamSynchronize(c->stream));
+  if (shift) {
+    const u64x4 w = philox(TAG_SHIFT, (uint64_t)sweep, 0, 0, seed, 0);
+    for (int a = 0; a < 3; ++a) shift[a] = unit53(w.v[a]) * c->T[a];
+  }
+  return ECMC_OK;
+}
+
+// ---------------------------------------------------------------- checkpoint
+namespace {
+const uint64_t CKPT_MAGIC = 0x45434D434B505431ull;  // "ECMCKPT1"
+struct CkptHeader {
+  uint64_t magic;
+  uint32_t version;
+  uint32_t pad;
+  int64_t n;
+  int32_t N;
+  int32_t pad2;
+  double L[3];
+  double sigma, b_max;
+  int64_t sweeps_done, ecs_done;
+  double device_seconds;
+  uint64_t counters[CNT_N];
+  double sums[SUM_N];
+  ecmc_opts opts;
+  int32_t configured;
+  int32_t pad3;
+};
+uint64_t checksum(const void *p, size_t len, uint64_t h) {
+  const unsigned char *b = (const unsigned char *)p;
+  for (size_t i = 0; i < len; ++i) {
+    h ^= b[i];
+    h *= 0x100000001B3ull;
+  }
+  return h;
+}
+}  // namespace
+
+ecmc_status ecmc_checkpoint(ecmc_ctx *c, const char *path) {
+  if (!c || !path) return fail(ECMC_EINVAL, "NULL argument");
+  CkptHeader hd;
+  memset(&hd, 0, sizeof(hd));
+  hd.magic = CKPT_MAGIC;
+  hd.version = 1;
+  hd.n = c->n;
+  hd.N = c->N;
+  for (int a = 0; a < 3; ++a) hd.L[a] = c->L[a];
+  hd.sigma = c->sigma;
+  hd.b_max = c->b_max;
+  hd.sweeps_done = c->sweeps_done;
+  hd.ecs_done = c->ecs_done;
+  hd.device_seconds = c->device_seconds;
+  hd.opts = c->opts;
+  hd.configured = c->configured;
+  std::vector<double> r(3 * c->n);
+  std::vector<int32_t> im(3 * c->n);
+  CU(cudaMemcpyAsync(hd.counters, c->d_cnt, sizeof(hd.counters), cudaMemcpyDeviceToHost, c->stream));
+  CU(cudaMemcpyAsync(hd.sums, c->d_sums, sizeof(hd.sums), cudaMemcpyDeviceToHost, c->stream));
+  CU(cudaMemcpyAsync(r.data(), c->d_r, sizeof(double) * r.size(), cudaMemcpyDeviceToHost, c->stream));
+  CU(cudaMemcpyAsync(im.data(), c->d_img, sizeof(int32_t) * im.size(), cudaMemcpyDeviceToHost, c->stream));
+  CU(cudaStreamSynchronize(c->stream));
+  uint64_t h = 0xCBF29CE484222325ull;
+  h = checksum(&hd, sizeof(hd), h);
+  h = checksum(r.data(), sizeof(double) * r.size(), h);
+  h = checksum(im.data(), sizeof(int32_t) * im.size(), h);
+  FILE *f = fopen(path, "wb");
+  if (!f) return fail(ECMC_ECKPT, "cannot open %s", path);
+  bool ok = fwrite(&hd, sizeof(hd), 1, f) == 1 &&
+            fwrite(r.data(), sizeof(double), r.size(), f) == r.size() &&
+            fwrite(im.data(), sizeof(int32_t), im.size(), f) == im.size() &&
+            fwrite(&h, sizeof(h), 1, f) == 1;
+  ok = (fclose(f) == 0) && ok;
+  if (!ok) return fail(ECMC_ECKPT, "write failed: %s", path);
+  return ECMC_OK;
+}
+
+ecmc_status ecmc_restore(ecmc_ctx *c, const char *path) {
+  if (!c || !path) return fail(ECMC_EINVAL, "NULL argument");
+  FILE *f = fopen(path, "rb");
+  if (!f) return fail(ECMC_ECKPT, "cannot open %s", path);
+  CkptHeader hd;
+  std::vector<double> r(3 * c->n);
+  std::vector<int32_t> im(3 * c->n);
+  uint64_t hfile = 0;
+  bool ok = fread(&hd, sizeof(hd), 1, f) == 1;
+  ok = ok && hd.magic == CKPT_MAGIC && hd.version == 1 && hd.n == c->n && hd.N == c->N;
+  ok = ok && fread(r.data(), sizeof(double), r.size(), f) == r.size() &&
+       fread(im.data(), sizeof(int32_t), im.size(), f) == im.size() &&
+       fread(&hfile, sizeof(hfile), 1, f) == 1;
+  fclose(f);
+  if (!ok) return fail(ECMC_ECKPT, "checkpoint does not match this context");
+  uint64_t h = 0xCBF29CE484222325ull;
+  h = checksum(&hd, sizeof(hd), h);
+  h = checksum(r.data(), sizeof(double) * r.size(), h);
+  h = checksum(im.data(), sizeof(int32_t) * im.size(), h);
+  if (h != hfile) return fail(ECMC_ECKPT, "checkpoint checksum mismatch");
+  for (int a = 0; a < 3; ++a)
+    if (hd.L[a] != c->L[a]) return fail(ECMC_ECKPT, "box differs");
+  CU(cudaMemcpyAsync(c->d_r, r.data(), sizeof(double) * r.size(), cudaMemcpyHostToDevice, c->stream));
+  CU(cudaMemcpyAsync(c->d_img, im.data(), sizeof(int32_t) * im.size(), cudaMemcpyHostToDevice, c->stream));
+  CU(cudaMemcpyAsync(c->d_cnt, hd.counters, sizeof(hd.counters), cudaMemcpyHostToDevice, c->stream));
+  CU(cudaMemcpyAsync(c->d_sums, hd.sums, sizeof(hd.sums), cudaMemcpyHostToDevice, c->stream));
+  CU(cudaStreamSynchronize(c->stream));
+  c->sweeps_done = hd.sweeps_done;
+  c->ecs_done = hd.ecs_done;
+  c->device_seconds = hd.device_seconds;
+  if (hd.configured) return ecmc_configure(c, &hd.opts);
+  return ECMC_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,154 @@
+// Device/host primitives of the EC library: counter-based random numbers and
+// the FP64 geometry of one event (arXiv:1502.06447, Sec. II, Eq. 1).
+//
+// Every FP64 expression here is evaluated as written (the library is built
+// with -fmad=false), so the event sequence is a pure function of the input
+// state and the Philox key.
+#pragma once
+#include <stdint.h>
+
+#ifdef __CUDACC__
+#define ECMC_HD __host__ __device__ __forceinline__
+#else
+#define ECMC_HD inline
+#endif
+
+namespace ecmc {
+
+// ---------------------------------------------------------------- Philox
+// Philox4x64-10 (Salmon, Moraes, Dror, Shaw, SC'11): ten rounds of two
+// 64x64 -> 128-bit products of the even words with the round multipliers;
+// the high halves are xor-ed into the odd words together with the key, the
+// words rotate, and the key advances by the two Weyl increments.
+struct u64x4 {
+  uint64_t v[4];
+};
+
+ECMC_HD void mul128(uint64_t a, uint64_t b, uint64_t &hi, uint64_t &lo) {
+#ifdef __CUDA_ARCH__
+  hi = __umul64hi(a, b);
+  lo = a * b;
+#else
+  unsigned __int128 p = (unsigned __int128)a * b;
+  hi = (uint64_t)(p >> 64);
+  lo = (uint64_t)p;
+#endif
+}
+
+ECMC_HD u64x4 philox(uint64_t c0, uint64_t c1, uint64_t c2, uint64_t c3,
+                     uint64_t k0, uint64_t k1) {
+  const uint64_t m0 = 0xD2E7470EE14C6C93ull, m1 = 0xCA5A826395121157ull;
+  const uint64_t w0 = 0x9E3779B97F4A7C15ull, w1 = 0xBB67AE8584CAA73Bull;
+#pragma unroll
+  for (int round = 0; round < 10; ++round) {
+    uint64_t h0, l0, h1, l1;
+    mul128(m0, c0, h0, l0);
+    mul128(m1, c2, h1, l1);
+    const uint64_t n0 = h1 ^ c1 ^ k0;
+    const uint64_t n2 = h0 ^ c3 ^ k1;
+    c0 = n0;
+    c1 = l1;
+    c2 = n2;
+    c3 = l0;
+    k0 += w0;
+    k1 += w1;
+  }
+  u64x4 r;
+  r.v[0] = c0;
+  r.v[1] = c1;
+  r.v[2] = c2;
+  r.v[3] = c3;
+  return r;
+}
+
+// random-number layout: key (seed, replica); counter (tag | ec << 8, sweep,
+// unit, attempt).  Tags: 1 start bead + direction, 2 tile shift, 3 swap,
+// 4 lattice jitter.
+enum : uint64_t { TAG_START = 1, TAG_SHIFT = 2, TAG_SWAP = 3, TAG_JITTER = 4 };
+
+// top 53 bits -> [0,1)
+ECMC_HD double unit53(uint64_t w) { return (double)(w >> 11) * (1.0 / 9007199254740992.0); }
+
+// floor(w * m / 2^64) in [0, m)
+ECMC_HD int64_t scale_below(uint64_t w, uint64_t m) {
+  uint64_t hi, lo;
+  mul128(w, m, hi, lo);
+  (void)lo;
+  return (int64_t)hi;
+}
+
+// ---------------------------------------------------------------- geometry
+// minimum image of one coordinate difference (|d| < L on input)
+ECMC_HD double wrap_d(double d, double L, double half) {
+  if (d > half) return d - L;
+  if (d < -half) return d + L;
+  return d;
+}
+
+// one axis of r += x v, back into [0, L) with the image counter; returns the
+// image change (-1, 0, +1)
+ECMC_HD int step_axis(double &r, double x, double v, double L) {
+  double y = r + x * v;
+  int di = 0;
+  if (y >= L) {
+    y = y - L;
+    di = 1;
+  } else if (y < 0.0) {
+    y = y + L;
+    di = -1;
+    if (y >= L) {  // a tiny negative plus L rounded up to L
+      y = 0.0;
+      di = 0;
+    }
+  }
+  r = y;
+  return di;
+}
+
+// Candidate kinds in tie-break order: an exact tie in x goes to the smaller
+// kind, then to the smaller partner id.
+enum : int { KIND_END = 0, KIND_PASS = 1, KIND_WALL = 2, KIND_HS = 3, KIND_TETHER = 4 };
+
+// Hard-sphere contact (Eq. 1): pivot at p moving along v touches the bead at
+// q when |p + x v - q| = sigma.  d = p - q (minimum image).  Returns x >= 0,
+// or -1 when the path misses or leads away.
+ECMC_HD double contact_x(double d0, double d1, double d2, double v0, double v1,
+                         double v2, double sig2) {
+  const double dv = d0 * v0 + d1 * v1 + d2 * v2;
+  if (!(dv < 0.0)) return -1.0;
+  const double dd = d0 * d0 + d1 * d1 + d2 * d2;
+  const double disc = sig2 - (dd - dv * dv);
+  if (!(disc > 0.0)) return -1.0;
+  double x = -dv - sqrt(disc);
+  return x < 0.0 ? 0.0 : x;
+}
+
+// Tether limit: the bond p - q reaches b_max after the free flight x (the
+// larger root; the bond may shorten first).
+ECMC_HD double tether_x(double d0, double d1, double d2, double v0, double v1,
+                        double v2, double b2) {
+  const double dv = d0 * v0 + d1 * v1 + d2 * v2;
+  const double dd = d0 * d0 + d1 * d1 + d2 * d2;
+  double rad = b2 - (dd - dv * dv);
+  if (rad < 0.0) rad = 0.0;
+  double x = -dv + sqrt(rad);
+  return x < 0.0 ? 0.0 : x;
+}
+
+// v <- v - 2 (v.n) n with n = d/|d| (Fig. 2c: reflection at the plane normal
+// to the bond / contact line)
+ECMC_HD void mirror(double &v0, double &v1, double &v2, double d0, double d1, double d2) {
+  const double len = sqrt(d0 * d0 + d1 * d1 + d2 * d2);
+  const double n0 = d0 / len, n1 = d1 / len, n2 = d2 / len;
+  const double t = 2.0 * (v0 * n0 + v1 * n1 + v2 * n2);
+  v0 = v0 - t * n0;
+  v1 = v1 - t * n1;
+  v2 = v2 - t * n2;
+}
+
+ECMC_HD void fnv_mix(uint64_t &h, uint64_t w) {
+  h ^= w;
+  h *= 0x100000001B3ull;
+}
+
+}  // namespace ecmc

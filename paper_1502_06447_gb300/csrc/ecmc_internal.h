@@ -1,0 +1,124 @@
+// Internal declarations shared by the library's translation units.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/ecmc.h"
+
+namespace ecmc {
+
+// Device status codes (first failure wins).
+enum : int { DEV_OK = 0, DEV_STUCK = 1, DEV_CAPACITY = 2, DEV_TILE = 3 };
+
+// Accumulator slots in the device counter array.
+enum : int {
+  CNT_EVENTS = ECMC_NEV,
+  CNT_SWAP_TRIED = ECMC_NEV + 1,
+  CNT_ECS = ECMC_NEV + 2,
+  CNT_CONFIRMED = ECMC_NEV + 3,
+  CNT_N = ECMC_NEV + 4
+};
+enum : int { SUM_LIFT = 0, SUM_REFL = 1, SUM_DISP = 2, SUM_N = 3 };
+
+// Everything one EC launch needs, by value.
+struct ECParams {
+  // system
+  int64_t n;
+  int32_t N;
+  double L[3], half[3];
+  double sigma, sig2, b2;
+  double s_cap;
+  // decomposition (domain mode)
+  int32_t domain;
+  int32_t D[3];
+  double T[3], W[3];
+  double halo_hs, halo_te;
+  int32_t nc[3];
+  double cs[3];
+  // run
+  uint64_t seed, replica;
+  int64_t sweep;        // domain: sweep index; serial: first EC ordinal
+  int32_t ecs_per_tile; // domain: ECs per tile; serial: ECs in this launch
+  double ell;
+  int64_t event_cap;
+  double p_swap;
+  int32_t dir_mode;
+  int32_t stage_cap;
+  int32_t n_units;      // tiles (domain) or 1 (serial)
+  // FP32 screen margins (units of sigma, sigma^2)
+  float eps_v, eps_d, eps_x;
+  // buffers
+  double *r;
+  int32_t *img;
+  const double *cr;        // positions in cell order
+  const int32_t *cid;      // ids in cell order
+  const int32_t *ctag;     // tiles in cell order
+  const int32_t *cstart;   // cell starts (ncell + 1)
+  unsigned long long *counters;
+  double *sums;
+  int *status;
+  // per-EC records (may be null)
+  uint64_t *rec_digest;
+  double *rec_lift;
+  int64_t *rec_events;
+  int64_t rec_offset;
+  int64_t rec_cap;
+  ecmc_event *log;
+  unsigned long long *log_n;
+  int64_t log_cap;
+};
+
+// launchers (k_ec.cu)
+cudaError_t launch_ec(const ECParams &P, int lanes, int fp32f, cudaStream_t s);
+size_t ec_smem_bytes(int stage_cap, int lanes, int groups_per_block);
+
+// cell list and domain tags (k_cells.cu)
+struct CellParams {
+  int64_t n;
+  double L[3];
+  int32_t nc[3];
+  double cs[3];
+  int32_t domain;
+  int32_t D[3];
+  double T[3], W[3];
+  uint64_t seed, replica;
+  int64_t sweep;
+  const double *r;
+  int32_t *tag;
+  int32_t *cell;
+  int32_t *rank;
+  int32_t *count;     // ncell (zeroed by the launcher)
+  int32_t *start;     // ncell + 1
+  int32_t *block_sums;
+  double *cr;
+  int32_t *cid;
+  int32_t *ctag;
+};
+cudaError_t launch_cells(const CellParams &C, int64_t ncell, cudaStream_t s);
+size_t cells_scratch_ints(int64_t ncell);
+
+// observables (k_obs.cu)
+struct ObsParams {
+  int64_t n;
+  int32_t N;
+  double L[3], half[3];
+  double sig2, b2;
+  const double *r;
+  const int32_t *img;
+  const double *g1ref;     // 3 per chain or null
+  // cell list over the current positions (for the overlap count)
+  int32_t nc[3];
+  const double *cr;
+  const int32_t *cid;
+  const int32_t *cstart;
+  const int32_t *cell;     // cell of each bead
+  double *out_d;           // [re2_sum, bond_max, bond_min(neg), g1_sum]
+  unsigned long long *out_u; // [overlaps, tether_violations]
+};
+cudaError_t launch_obs(const ObsParams &O, cudaStream_t s);
+cudaError_t launch_g1_snapshot(const ObsParams &O, double *g1ref, cudaStream_t s);
+cudaError_t launch_lattice(const int32_t dims[3], double a, double jitter,
+                           uint64_t seed, uint64_t replica, double *r, int64_t n,
+                           cudaStream_t s);
+
+}  // namespace ecmc

@@ -1,0 +1,148 @@
+// Fused observables over the current state and the initial lattice.
+//
+//   R_e^2 per chain from minimum-image bonds (end-to-end distance, Sec. III
+//   and the ideal-chain law <R^2> = c N sigma^2); bond lengths and tether
+//   violations (b > b_max); hard-sphere overlaps (Eq. 1) from the cell list;
+//   g1, the mean-square displacement of the middle bead N/2 (Eq. for g1 in
+//   Sec. III) against a reference snapshot of unwrapped positions.
+#include <cuda_runtime.h>
+
+#include "ecmc_dev.cuh"
+#include "ecmc_internal.h"
+
+namespace ecmc {
+namespace {
+
+__device__ __forceinline__ void atomic_max_pos(double *a, double v) {
+  atomicMax((unsigned long long *)a, (unsigned long long)__double_as_longlong(v));
+}
+__device__ __forceinline__ void atomic_min_pos(double *a, double v) {
+  atomicMin((unsigned long long *)a, (unsigned long long)__double_as_longlong(v));
+}
+
+// out_d: [0] sum R_e^2, [1] max bond, [2] min bond, [3] sum g1
+// out_u: [0] overlaps, [1] tether violations
+__global__ void k_chains(const ObsParams O) {
+  const int64_t ch = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t nch = O.n / O.N;
+  if (ch >= nch) return;
+  double R0 = 0.0, R1 = 0.0, R2 = 0.0, bmax = 0.0, bmin = 1e300;
+  unsigned long long viol = 0;
+  const double lim = O.b2 * (1.0 + 1e-10);
+  for (int j = 0; j + 1 < O.N; ++j) {
+    const int64_t b = ch * O.N + j;
+    const double d0 = wrap_d(O.r[3 * (b + 1)] - O.r[3 * b], O.L[0], O.half[0]);
+    const double d1 = wrap_d(O.r[3 * (b + 1) + 1] - O.r[3 * b + 1], O.L[1], O.half[1]);
+    const double d2 = wrap_d(O.r[3 * (b + 1) + 2] - O.r[3 * b + 2], O.L[2], O.half[2]);
+    R0 += d0;
+    R1 += d1;
+    R2 += d2;
+    const double dd = d0 * d0 + d1 * d1 + d2 * d2;
+    viol += dd > lim;
+    const double bl = sqrt(dd);
+    bmax = fmax(bmax, bl);
+    bmin = fmin(bmin, bl);
+  }
+  atomicAdd(&O.out_d[0], R0 * R0 + R1 * R1 + R2 * R2);
+  if (O.N > 1) {
+    atomic_max_pos(&O.out_d[1], bmax);
+    atomic_min_pos(&O.out_d[2], bmin);
+  }
+  if (viol) atomicAdd(&O.out_u[1], viol);
+  if (O.g1ref) {
+    const int64_t b = ch * O.N + O.N / 2;
+    double g = 0.0;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      const double u = O.r[3 * b + a] + (double)O.img[3 * b + a] * O.L[a];
+      const double d = u - O.g1ref[3 * ch + a];
+      g += d * d;
+    }
+    atomicAdd(&O.out_d[3], g);
+  }
+}
+
+__global__ void k_snapshot(const ObsParams O, double *ref) {
+  const int64_t ch = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t nch = O.n / O.N;
+  if (ch >= nch) return;
+  const int64_t b = ch * O.N + O.N / 2;
+#pragma unroll
+  for (int a = 0; a < 3; ++a) ref[3 * ch + a] = O.r[3 * b + a] + (double)O.img[3 * b + a] * O.L[a];
+}
+
+// pairs i < j closer than sigma (1 - 1e-10)^(1/2), through the cell list
+// (cell side >= sigma, at least 3 cells per axis)
+__global__ void k_overlaps(const ObsParams O) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= O.n) return;
+  const int c = O.cell[i];
+  const int cx = c % O.nc[0], cy = (c / O.nc[0]) % O.nc[1], cz = c / (O.nc[0] * O.nc[1]);
+  const double p0 = O.r[3 * i], p1 = O.r[3 * i + 1], p2 = O.r[3 * i + 2];
+  const double lim = O.sig2 * (1.0 - 1e-10);
+  unsigned long long cnt = 0;
+  for (int dz = -1; dz <= 1; ++dz)
+    for (int dy = -1; dy <= 1; ++dy)
+      for (int dx = -1; dx <= 1; ++dx) {
+        const int x = (cx + dx + O.nc[0]) % O.nc[0];
+        const int y = (cy + dy + O.nc[1]) % O.nc[1];
+        const int z = (cz + dz + O.nc[2]) % O.nc[2];
+        const int cc = (z * O.nc[1] + y) * O.nc[0] + x;
+        for (int j = O.cstart[cc]; j < O.cstart[cc + 1]; ++j) {
+          if (O.cid[j] <= i) continue;
+          const double d0 = wrap_d(p0 - O.cr[3 * (int64_t)j], O.L[0], O.half[0]);
+          const double d1 = wrap_d(p1 - O.cr[3 * (int64_t)j + 1], O.L[1], O.half[1]);
+          const double d2 = wrap_d(p2 - O.cr[3 * (int64_t)j + 2], O.L[2], O.half[2]);
+          cnt += (d0 * d0 + d1 * d1 + d2 * d2) < lim;
+        }
+      }
+  if (cnt) atomicAdd(&O.out_u[0], cnt);
+}
+
+__global__ void k_lattice(int n0, int n1, int n2, double a, double jitter, uint64_t seed,
+                          uint64_t replica, double *r, int64_t n) {
+  const int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= n) return;
+  const int64_t plane = (int64_t)n0 * n1;
+  const int z = (int)(b / plane);
+  const int64_t rem = b % plane;
+  const int yy = (int)(rem / n0), xx = (int)(rem % n0);
+  const int y = (z % 2 == 0) ? yy : n1 - 1 - yy;
+  const int row = z * n1 + yy;
+  const int x = (row % 2 == 0) ? xx : n0 - 1 - xx;
+  const int site[3] = {x, y, z};
+  u64x4 w;
+  w.v[0] = w.v[1] = w.v[2] = w.v[3] = 0;
+  if (jitter != 0.0) w = philox(TAG_JITTER, 0, (uint64_t)b, 0, seed, replica);
+#pragma unroll
+  for (int ax = 0; ax < 3; ++ax) {
+    double p = ((double)site[ax] + 0.5) * a;
+    if (jitter != 0.0) p = p + jitter * (2.0 * unit53(w.v[ax]) - 1.0);
+    r[3 * b + ax] = p;
+  }
+}
+
+}  // namespace
+
+cudaError_t launch_obs(const ObsParams &O, cudaStream_t s) {
+  const int64_t nch = O.n / O.N;
+  if (nch > 0) k_chains<<<(unsigned)((nch + 127) / 128), 128, 0, s>>>(O);
+  if (O.n > 0 && O.cr) k_overlaps<<<(unsigned)((O.n + 127) / 128), 128, 0, s>>>(O);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_g1_snapshot(const ObsParams &O, double *g1ref, cudaStream_t s) {
+  const int64_t nch = O.n / O.N;
+  if (nch > 0) k_snapshot<<<(unsigned)((nch + 127) / 128), 128, 0, s>>>(O, g1ref);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_lattice(const int32_t dims[3], double a, double jitter, uint64_t seed,
+                           uint64_t replica, double *r, int64_t n, cudaStream_t s) {
+  if (n > 0)
+    k_lattice<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(dims[0], dims[1], dims[2], a, jitter,
+                                                         seed, replica, r, n);
+  return cudaGetLastError();
+}
+
+}  // namespace ecmc

@@ -1,0 +1,252 @@
+"""Thin Python binding of the C ABI in include/ecmc.h (argument marshalling only).
+
+Every step of the EC path runs in the CUDA library libecmc.so; this module
+only converts arguments.  There is no CPU fallback: if the library is missing
+or cannot be loaded, every call raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libecmc.so")
+
+MODE_SERIAL, MODE_DOMAIN = 0, 1
+DIR_CART3, DIR_ISO = 0, 1
+PREC_FP64, PREC_FP32F = 0, 1
+EV_NAMES = ("end", "pass", "wall", "hs_lift", "hs_reflect", "te_lift", "te_reflect", "swap")
+STATUS = {0: "OK", -1: "EINVAL", -2: "ENOMEM", -3: "ECUDA", -4: "EOVERLAP", -5: "ETETHER",
+          -6: "ESTUCK", -7: "ECKPT", -8: "ECAPACITY"}
+
+# every symbol include/ecmc.h declares
+EXPORTS = (
+    "ecmc_create_lattice", "ecmc_create", "ecmc_destroy", "ecmc_last_error", "ecmc_set_stream",
+    "ecmc_set_positions", "ecmc_get_positions", "ecmc_get_info", "ecmc_configure", "ecmc_run",
+    "ecmc_swap", "ecmc_observables", "ecmc_g1_reset", "ecmc_records", "ecmc_log_reserve",
+    "ecmc_event_log", "ecmc_domain_tags", "ecmc_checkpoint", "ecmc_restore",
+)
+
+
+class EcmcError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"{STATUS.get(code, code)}: {msg}")
+        self.code = code
+
+
+class Opts(C.Structure):
+    _fields_ = [("mode", C.c_int32), ("dir_mode", C.c_int32), ("precision", C.c_int32),
+                ("tiles", C.c_int32 * 3), ("joint", C.c_double), ("s_cap", C.c_double),
+                ("event_cap", C.c_int64), ("p_swap", C.c_double), ("ecs_per_tile", C.c_int32),
+                ("lanes", C.c_int32), ("record", C.c_int32), ("stage_cap", C.c_int32),
+                ("cell_side", C.c_double)]
+
+
+class Obs(C.Structure):
+    _fields_ = [("n_beads", C.c_int64), ("n_chains", C.c_int64), ("N", C.c_int64),
+                ("sweeps", C.c_int64), ("ecs", C.c_int64), ("events", C.c_int64 * 8),
+                ("events_total", C.c_int64), ("swap_tried", C.c_int64),
+                ("lift_sum", C.c_double), ("refl_sum", C.c_double), ("disp_sum", C.c_double),
+                ("ell_sum", C.c_double), ("pressure", C.c_double), ("re2_mean", C.c_double),
+                ("bond_max", C.c_double), ("bond_min", C.c_double), ("overlaps", C.c_int64),
+                ("tether_violations", C.c_int64), ("g1", C.c_double),
+                ("device_seconds", C.c_double), ("ec_kernel_seconds", C.c_double),
+                ("confirmed", C.c_int64)]
+
+    def as_dict(self):
+        d = {k: getattr(self, k) for k, _ in self._fields_ if k != "events"}
+        for i, name in enumerate(EV_NAMES):
+            d[name] = self.events[i]
+        return d
+
+
+EVENT_DTYPE = np.dtype([("unit", "<i8"), ("seq", "<i4"), ("pivot", "<i4"), ("kind", "<i4"),
+                        ("pad", "<i4"), ("partner", "<i8"), ("x", "<f8")])
+
+_lib = None
+_lock = threading.Lock()
+
+
+def load(path: str = LIB_PATH):
+    """Load libecmc.so (raises if it is missing: there is no fallback)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        if not os.path.exists(path):
+            raise RuntimeError(f"CUDA library not built: {path} (run __graft_entry__.build())")
+        lib = C.CDLL(path)
+        P = C.POINTER
+        vp = C.c_void_p
+        sig = {
+            "ecmc_create_lattice": [P(C.c_int32), C.c_double, C.c_double, C.c_uint64, C.c_int32,
+                                    C.c_double, C.c_double, P(vp)],
+            "ecmc_create": [P(C.c_double), C.c_double, C.c_int32, C.c_int32, C.c_double,
+                            C.c_double, P(vp)],
+            "ecmc_set_stream": [vp, vp],
+            "ecmc_set_positions": [vp, P(C.c_double), P(C.c_int32)],
+            "ecmc_get_positions": [vp, P(C.c_double), P(C.c_int32)],
+            "ecmc_get_info": [vp, P(C.c_double), P(C.c_int64), P(C.c_int32)],
+            "ecmc_configure": [vp, P(Opts)],
+            "ecmc_run": [vp, C.c_double, C.c_int64, C.c_uint64, C.c_int64],
+            "ecmc_swap": [vp, C.c_double],
+            "ecmc_observables": [vp, P(Obs)],
+            "ecmc_g1_reset": [vp],
+            "ecmc_records": [vp, P(C.c_uint64), P(C.c_double), P(C.c_int64), P(C.c_int64)],
+            "ecmc_log_reserve": [vp, C.c_int64],
+            "ecmc_event_log": [vp, vp, C.c_int64, P(C.c_int64)],
+            "ecmc_domain_tags": [vp, C.c_uint64, C.c_int64, P(C.c_int32), P(C.c_double)],
+            "ecmc_checkpoint": [vp, C.c_char_p],
+            "ecmc_restore": [vp, C.c_char_p],
+        }
+        for name, args in sig.items():
+            f = getattr(lib, name)
+            f.argtypes = args
+            f.restype = C.c_int
+        lib.ecmc_destroy.argtypes = [vp]
+        lib.ecmc_destroy.restype = None
+        lib.ecmc_last_error.argtypes = []
+        lib.ecmc_last_error.restype = C.c_char_p
+        _lib = lib
+        return lib
+
+
+def _check(rc):
+    if rc != 0:
+        raise EcmcError(rc, load().ecmc_last_error().decode())
+    return rc
+
+
+def _p(a, ct):
+    return a.ctypes.data_as(C.POINTER(ct))
+
+
+def opts(mode=MODE_SERIAL, dir_mode=DIR_CART3, precision=PREC_FP64, tiles=(3, 3, 3), joint=0.0,
+         s_cap=0.0, event_cap=0, p_swap=0.0, ecs_per_tile=0, lanes=0, record=0, stage_cap=0,
+         cell_side=0.0) -> Opts:
+    o = Opts()
+    o.mode, o.dir_mode, o.precision = int(mode), int(dir_mode), int(precision)
+    for a in range(3):
+        o.tiles[a] = int(tiles[a])
+    o.joint, o.s_cap, o.event_cap = float(joint), float(s_cap), int(event_cap)
+    o.p_swap, o.ecs_per_tile, o.lanes = float(p_swap), int(ecs_per_tile), int(lanes)
+    o.record, o.stage_cap, o.cell_side = int(record), int(stage_cap), float(cell_side)
+    return o
+
+
+class Context:
+    """One melt on the GPU (wraps an ecmc_ctx)."""
+
+    def __init__(self, handle):
+        self._h = handle
+        box = np.zeros(3)
+        n = C.c_int64()
+        N = C.c_int32()
+        _check(load().ecmc_get_info(self._h, _p(box, C.c_double), C.byref(n), C.byref(N)))
+        self.L, self.n, self.N = box, n.value, N.value
+
+    # ---- creation
+    @classmethod
+    def create_lattice(cls, dims, spacing, N, sigma=1.0, b_max=1.2, jitter=0.0, seed=0):
+        h = C.c_void_p()
+        d = np.asarray(dims, dtype=np.int32)
+        _check(load().ecmc_create_lattice(_p(d, C.c_int32), float(spacing), float(jitter),
+                                          int(seed) & (2**64 - 1), int(N), float(sigma),
+                                          float(b_max), C.byref(h)))
+        return cls(h)
+
+    @classmethod
+    def create(cls, phi, n_chains, N, sigma=1.0, b_max=1.2, box=None):
+        h = C.c_void_p()
+        b = np.zeros(3) if box is None else np.asarray(box, dtype=np.float64)
+        _check(load().ecmc_create(_p(b, C.c_double), float(phi), int(n_chains), int(N),
+                                  float(sigma), float(b_max), C.byref(h)))
+        return cls(h)
+
+    def close(self):
+        if self._h:
+            load().ecmc_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    # ---- state
+    def set_stream(self, stream_ptr):
+        _check(load().ecmc_set_stream(self._h, C.c_void_p(stream_ptr)))
+
+    def set_positions(self, r, img=None):
+        r = np.ascontiguousarray(r, dtype=np.float64).reshape(-1, 3)
+        im = None if img is None else np.ascontiguousarray(img, dtype=np.int32).reshape(-1, 3)
+        _check(load().ecmc_set_positions(self._h, _p(r, C.c_double),
+                                          None if im is None else _p(im, C.c_int32)))
+
+    def get_positions(self):
+        r = np.zeros((self.n, 3))
+        img = np.zeros((self.n, 3), dtype=np.int32)
+        _check(load().ecmc_get_positions(self._h, _p(r, C.c_double), _p(img, C.c_int32)))
+        return r, img
+
+    # ---- running
+    def configure(self, **kw):
+        o = opts(**kw)
+        _check(load().ecmc_configure(self._h, C.byref(o)))
+
+    def run(self, ell, chains_per_sweep=0, seed=0, n_sweeps=0):
+        _check(load().ecmc_run(self._h, float(ell), int(chains_per_sweep),
+                               int(seed) & (2**64 - 1), int(n_sweeps)))
+
+    def swap(self, attempts_per_bead_per_sweep):
+        _check(load().ecmc_swap(self._h, float(attempts_per_bead_per_sweep)))
+
+    def observables(self) -> dict:
+        o = Obs()
+        _check(load().ecmc_observables(self._h, C.byref(o)))
+        return o.as_dict()
+
+    def g1_reset(self):
+        _check(load().ecmc_g1_reset(self._h))
+
+    def records(self, cap):
+        dig = np.zeros(cap, dtype=np.uint64)
+        lift = np.zeros(cap)
+        ev = np.zeros(cap, dtype=np.int64)
+        n = C.c_int64(cap)
+        _check(load().ecmc_records(self._h, _p(dig, C.c_uint64), _p(lift, C.c_double),
+                                   _p(ev, C.c_int64), C.byref(n)))
+        return dig[: n.value], lift[: n.value], ev[: n.value]
+
+    def log_reserve(self, cap):
+        _check(load().ecmc_log_reserve(self._h, int(cap)))
+
+    def event_log(self, cap):
+        buf = np.zeros(cap, dtype=EVENT_DTYPE)
+        n = C.c_int64()
+        _check(load().ecmc_event_log(self._h, buf.ctypes.data, int(cap), C.byref(n)))
+        out = buf[: n.value]
+        return out[np.lexsort((out["seq"], out["unit"]))]
+
+    def domain_tags(self, seed, sweep):
+        tags = np.zeros(self.n, dtype=np.int32)
+        shift = np.zeros(3)
+        _check(load().ecmc_domain_tags(self._h, int(seed) & (2**64 - 1), int(sweep),
+                                       _p(tags, C.c_int32), _p(shift, C.c_double)))
+        return tags, shift
+
+    def checkpoint(self, path):
+        _check(load().ecmc_checkpoint(self._h, str(path).encode()))
+
+    def restore(self, path):
+        _check(load().ecmc_restore(self._h, str(path).encode()))
