@@ -29,8 +29,10 @@ import time
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-from paper_1502_06447_gb300.configs import C5  # noqa: E402
+from paper_1502_06447_gb300.configs import C2, C3, C5  # noqa: E402
 
+WORKLOADS = {"c5": (C5, (20, 20, 20)), "c3": (C3, (16, 16, 16)), "c2": (C2, (16, 16, 16))}
+C5_DEFAULT = C5
 ELL = C5.ell
 TILES = (20, 20, 20)
 SWAP_RATE = 0.1
@@ -320,7 +322,12 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--lanes", type=int, default=32)
     ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
+    ap.add_argument("--workload", default="c5", choices=sorted(WORKLOADS),
+                    help="c5: the 1e6-bead melt (default); c2/c3: smaller melts")
     args = ap.parse_args()
+    global C5, ELL, TILES
+    C5, TILES = WORKLOADS[args.workload]
+    ELL = C5.ell
     rank = int(os.environ.get("RANK", 0))
     world = int(os.environ.get("WORLD_SIZE", 1))
     if args.impl == "reference":
