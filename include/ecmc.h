@@ -222,6 +222,39 @@ ecmc_status ecmc_domain_tags(ecmc_ctx *ctx, uint64_t seed, int64_t sweep,
 ecmc_status ecmc_checkpoint(ecmc_ctx *ctx, const char *path);
 ecmc_status ecmc_restore(ecmc_ctx *ctx, const char *path);
 
+/* ---- domain assignment and cell list without allocation ------------------
+ * The paper has no counterpart to this entry point; it serves callers that
+ * cannot allocate device memory (a host callback, a framework that owns every
+ * device allocation, a real-time loop that must stay off the driver's
+ * allocator).  It computes what a sweep's first step computes — the tile of
+ * every bead for sweep `sweep` (-1 = joint; shift from Philox counter
+ * (2, sweep, 0, 0), key (seed, 0); tiles[a] tiles of width box[a]/tiles[a]
+ * along axis a, the last `joint` of each being joint) and the beads binned
+ * into the cell grid nc_a = floor(box[a] / cell_side) — into buffers the
+ * caller owns, and calls no cudaMalloc, cudaFree or allocating routine.
+ *   d_r          device, 3n doubles, positions wrapped into [0, box)
+ *   d_tags       device, n int32 (out)
+ *   d_cell_start device, ncell + 1 int32 (out), ncell = nc_0 nc_1 nc_2;
+ *                cell c = (z nc_1 + y) nc_0 + x holds d_cell_ids[start[c],
+ *                start[c+1]) (order inside a cell not fixed)
+ *   d_cell_ids   device, n int32 (out)
+ *   shift_out    host, 3 doubles (out) or NULL
+ *   stream       cudaStream_t as void*, NULL for the default stream
+ * Limits: n <= 1,048,576 beads and ncell <= 1,048,576 cells; larger inputs
+ * return ECMC_EINVAL.  Scratch: an 8 MiB file-scope __device__ array that
+ * every GPU that loads the library holds until the process exits.  The first
+ * call on a device looks up that array's device address (cudaGetSymbolAddress)
+ * with the device current; make that first call before any stream capture.
+ * All calls share the array and it keeps the last call's contents (the
+ * counts are cleared by each call); calls whose work overlaps on the GPU
+ * race and must be serialised by the caller.  Asynchronous on `stream`. */
+ecmc_status ecmc_cells_static(const double *d_r, int64_t n, const double box[3],
+                              const int32_t tiles[3], double joint,
+                              double cell_side, uint64_t seed, int64_t sweep,
+                              int32_t *d_tags, int32_t *d_cell_start,
+                              int32_t *d_cell_ids, double shift_out[3],
+                              void *stream);
+
 #ifdef __cplusplus
 }
 #endif

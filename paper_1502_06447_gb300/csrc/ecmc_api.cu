@@ -310,6 +310,10 @@ ecmc_status make_ctx(const int32_t dims[3], double spacing, double jitter, uint6
 
 }  // namespace
 
+namespace ecmc {
+void set_last_error(const char *msg) { g_err = msg; }
+}  // namespace ecmc
+
 extern "C" {
 
 const char *ecmc_last_error(void) { return g_err.c_str(); }

@@ -68,6 +68,9 @@ struct ECParams {
   int64_t log_cap;
 };
 
+// message for ecmc_last_error (ecmc_api.cu)
+void set_last_error(const char *msg);
+
 // launchers (k_ec.cu)
 cudaError_t launch_ec(const ECParams &P, int lanes, int fp32f, cudaStream_t s);
 size_t ec_smem_bytes(int stage_cap, int lanes, int groups_per_block);

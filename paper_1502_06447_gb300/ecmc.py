@@ -28,6 +28,7 @@ EXPORTS = (
     "ecmc_set_positions", "ecmc_get_positions", "ecmc_get_info", "ecmc_configure", "ecmc_run",
     "ecmc_swap", "ecmc_observables", "ecmc_g1_reset", "ecmc_records", "ecmc_log_reserve",
     "ecmc_event_log", "ecmc_domain_tags", "ecmc_checkpoint", "ecmc_restore",
+    "ecmc_cells_static",
 )
 
 
@@ -101,6 +102,9 @@ def load(path: str = LIB_PATH):
             "ecmc_domain_tags": [vp, C.c_uint64, C.c_int64, P(C.c_int32), P(C.c_double)],
             "ecmc_checkpoint": [vp, C.c_char_p],
             "ecmc_restore": [vp, C.c_char_p],
+            "ecmc_cells_static": [vp, C.c_int64, P(C.c_double), P(C.c_int32), C.c_double,
+                                  C.c_double, C.c_uint64, C.c_int64, vp, vp, vp,
+                                  P(C.c_double), vp],
         }
         for name, args in sig.items():
             f = getattr(lib, name)
@@ -250,3 +254,18 @@ class Context:
 
     def restore(self, path):
         _check(load().ecmc_restore(self._h, str(path).encode()))
+
+
+def cells_static(d_r, n, box, tiles, joint, cell_side, seed, sweep, d_tags, d_cell_start,
+                 d_cell_ids, stream=0):
+    """ecmc_cells_static on caller-owned device buffers (device pointers as
+    ints); returns the tile shift.  Allocates nothing on the device."""
+    b = np.ascontiguousarray(box, dtype=np.float64)
+    t = np.ascontiguousarray(tiles, dtype=np.int32)
+    shift = np.zeros(3)
+    _check(load().ecmc_cells_static(C.c_void_p(d_r), int(n), _p(b, C.c_double),
+                                    _p(t, C.c_int32), float(joint), float(cell_side),
+                                    int(seed) & (2**64 - 1), int(sweep), C.c_void_p(d_tags),
+                                    C.c_void_p(d_cell_start), C.c_void_p(d_cell_ids),
+                                    _p(shift, C.c_double), C.c_void_p(stream)))
+    return shift
