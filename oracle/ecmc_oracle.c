@@ -220,26 +220,30 @@ typedef struct {
   double x;
   int kind;
   int64_t partner;
+  double dv; /* (r_pivot - r_partner).v before the flight (contact, tether) */
 } cand_t;
 
-static void consider(cand_t *best, double x, int kind, int64_t partner) {
+static void consider(cand_t *best, double x, int kind, int64_t partner, double dv) {
   if (x < best->x ||
       (x == best->x &&
        (kind < best->kind || (kind == best->kind && partner < best->partner)))) {
     best->x = x;
     best->kind = kind;
     best->partner = partner;
+    best->dv = dv;
   }
 }
 
 /* hard-sphere contact distance of pivot i moving along v towards bead k
  * (Eq. 1: contact at |r_i + x v - r_k| = sigma); returns -1 if none */
-static double hs_dist(const ctx_t *c, int64_t i, int64_t k, const double v[3]) {
+static double hs_dist(const ctx_t *c, int64_t i, int64_t k, const double v[3],
+                      double *dv_out) {
   const double *L = c->P.L;
   double d0 = minimg(c->r[3 * i + 0] - c->r[3 * k + 0], L[0]);
   double d1 = minimg(c->r[3 * i + 1] - c->r[3 * k + 1], L[1]);
   double d2 = minimg(c->r[3 * i + 2] - c->r[3 * k + 2], L[2]);
   double dv = d0 * v[0] + d1 * v[1] + d2 * v[2];
+  *dv_out = dv;
   if (!(dv < 0.0)) return -1.0;
   double dd = d0 * d0 + d1 * d1 + d2 * d2;
   double sig2 = c->P.sigma * c->P.sigma;
@@ -252,12 +256,14 @@ static double hs_dist(const ctx_t *c, int64_t i, int64_t k, const double v[3]) {
 
 /* tether limit of pivot i bonded to j: |r_i + x v - r_j| = b_max, the
  * positive root (the bond can always shorten first) */
-static double te_dist(const ctx_t *c, int64_t i, int64_t j, const double v[3]) {
+static double te_dist(const ctx_t *c, int64_t i, int64_t j, const double v[3],
+                      double *dv_out) {
   const double *L = c->P.L;
   double d0 = minimg(c->r[3 * i + 0] - c->r[3 * j + 0], L[0]);
   double d1 = minimg(c->r[3 * i + 1] - c->r[3 * j + 1], L[1]);
   double d2 = minimg(c->r[3 * i + 2] - c->r[3 * j + 2], L[2]);
   double dv = d0 * v[0] + d1 * v[1] + d2 * v[2];
+  *dv_out = dv;
   double dd = d0 * d0 + d1 * d1 + d2 * d2;
   double b2 = c->P.b_max * c->P.b_max;
   double rad = b2 - (dd - dv * dv);
@@ -282,15 +288,17 @@ static void hs_all(const ctx_t *c, int64_t i, const double v[3], cand_t *best) {
           int cj = (jz * c->nc[1] + jy) * c->nc[0] + jx;
           for (int32_t k = c->head[cj]; k >= 0; k = c->next[k]) {
             if (k == i) continue;
-            double x = hs_dist(c, i, k, v);
-            if (x >= 0.0) consider(best, x, K_HS, k);
+            double dv;
+            double x = hs_dist(c, i, k, v, &dv);
+            if (x >= 0.0) consider(best, x, K_HS, k, dv);
           }
         }
   } else {
     for (int64_t k = 0; k < c->P.n; ++k) {
       if (k == i) continue;
-      double x = hs_dist(c, i, k, v);
-      if (x >= 0.0) consider(best, x, K_HS, k);
+      double dv;
+      double x = hs_dist(c, i, k, v, &dv);
+      if (x >= 0.0) consider(best, x, K_HS, k, dv);
     }
   }
 }
@@ -313,15 +321,14 @@ static void fnv(uint64_t *h, uint64_t w) {
   *h *= 0x100000001B3ULL;
 }
 
-/* reflect v at the plane normal to d (Fig. 2c) */
+/* reflect v at the plane normal to d (Fig. 2c): v' = v - (2 v.d / d.d) d */
 static void reflect(double v[3], double d0, double d1, double d2) {
-  double nd = sqrt(d0 * d0 + d1 * d1 + d2 * d2);
-  double n0 = d0 / nd, n1 = d1 / nd, n2 = d2 / nd;
-  double vn = v[0] * n0 + v[1] * n1 + v[2] * n2;
-  double t = 2.0 * vn;
-  v[0] = v[0] - t * n0;
-  v[1] = v[1] - t * n1;
-  v[2] = v[2] - t * n2;
+  double dd = d0 * d0 + d1 * d1 + d2 * d2;
+  double vd = v[0] * d0 + v[1] * d1 + v[2] * d2;
+  double t = (2.0 * vd) / dd;
+  v[0] = v[0] - t * d0;
+  v[1] = v[1] - t * d1;
+  v[2] = v[2] - t * d2;
 }
 
 /* swap test (Sec. II.D): with pivot i and the touched bead k exchanged,
@@ -398,20 +405,27 @@ static void run_ec(ctx_t *c, int64_t pivot, double v[3], double ell,
       break;
     }
     const int64_t i = pivot;
-    cand_t best = {xrem, K_END, -1};
-    consider(&best, P->s_cap, K_PASS, -1);
+    cand_t best = {xrem, K_END, -1, 0.0};
+    consider(&best, P->s_cap, K_PASS, -1, 0.0);
     if (tl->active) {
       for (int a = 0; a < 3; ++a) {
         if (v[a] == 0.0) continue;
         double loc = minimg(c->r[3 * i + a] - tl->corner[a], P->L[a]);
         double x = (v[a] > 0.0) ? (c->W[a] - loc) / v[a] : (0.0 - loc) / v[a];
         if (x < 0.0) x = 0.0;
-        consider(&best, x, K_WALL, a);
+        consider(&best, x, K_WALL, a, 0.0);
       }
     }
     if (P->N > 1) {
-      if (i % P->N != 0) consider(&best, te_dist(c, i, i - 1, v), K_TETHER, i - 1);
-      if (i % P->N != P->N - 1) consider(&best, te_dist(c, i, i + 1, v), K_TETHER, i + 1);
+      double dv, x;
+      if (i % P->N != 0) {
+        x = te_dist(c, i, i - 1, v, &dv);
+        consider(&best, x, K_TETHER, i - 1, dv);
+      }
+      if (i % P->N != P->N - 1) {
+        x = te_dist(c, i, i + 1, v, &dv);
+        consider(&best, x, K_TETHER, i + 1, dv);
+      }
     }
     hs_all(c, i, v, &best);
 
@@ -438,7 +452,9 @@ static void run_ec(ctx_t *c, int64_t pivot, double v[3], double ell,
       double d0 = minimg(c->r[3 * i + 0] - c->r[3 * k + 0], P->L[0]);
       double d1 = minimg(c->r[3 * i + 1] - c->r[3 * k + 1], P->L[1]);
       double d2 = minimg(c->r[3 * i + 2] - c->r[3 * k + 2], P->L[2]);
-      double proj = 0.0 - (d0 * v[0] + d1 * v[1] + d2 * v[2]);
+      /* (r_k - r_i).v at contact = -(d.v) - x, d the separation before the
+       * flight x (the pressure projection, R8) */
+      double proj = -best.dv - x;
       if (!motile(c, tl, k)) {
         /* partner cannot move: reflect at the contact / bond normal */
         out = (best.kind == K_HS) ? O_HS_REFLECT : O_TE_REFLECT;
