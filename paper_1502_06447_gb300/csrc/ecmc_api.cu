@@ -454,7 +454,7 @@ ecmc_status ecmc_configure(ecmc_ctx *c, const ecmc_opts *o) {
       const double rho = (double)c->n / (c->L[0] * c->L[1] * c->L[2]);
       double vol = 1.0;
       for (int a = 0; a < 3; ++a) vol *= c->W[a] + 2.0 * halo_te;
-      stage = (int32_t)(rho * vol * 1.6 + 64);
+      stage = (int32_t)(rho * vol * 1.3 + 32);
       stage = (stage + 31) / 32 * 32;
     }
   } else {
@@ -463,7 +463,7 @@ ecmc_status ecmc_configure(ecmc_ctx *c, const ecmc_opts *o) {
         if (!(c->L[a] <= 64.0 * sig)) return fail(ECMC_EINVAL, "FP32 screen (serial) needs L <= 64 sigma");
     stage = (int32_t)c->n;
   }
-  if (stage > (1 << 20) - 1) return fail(ECMC_EINVAL, "stage capacity too large");
+  if (stage > 65534) return fail(ECMC_EINVAL, "at most 65534 staged beads per tile (serial: beads)");
   int dev = 0, smem_max = 0;
   CU(cudaGetDevice(&dev));
   CU(cudaDeviceGetAttribute(&smem_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
@@ -691,8 +691,8 @@ ecmc_status ecmc_observables(ecmc_ctx *c, ecmc_obs *out) {
   out->swap_tried = (int64_t)h[CNT_SWAP_TRIED];
   out->lift_sum = sums[SUM_LIFT];
   out->refl_sum = sums[SUM_REFL];
-  out->disp_sum = sums[SUM_DISP];
-  out->ell_sum = sums[SUM_DISP];  // every EC displaces exactly its ell in total
+  out->disp_sum = sums[SUM_DISP];  // ell summed per EC (the flights add up to it)
+  out->ell_sum = sums[SUM_DISP];
   out->pressure = out->ell_sum > 0 ? 1.0 + out->lift_sum / out->ell_sum : 0.0;
   out->re2_mean = o.re2_sum / (double)(c->n / c->N);
   out->bond_max = o.bmax;

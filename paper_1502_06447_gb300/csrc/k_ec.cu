@@ -13,8 +13,15 @@
 // The start bead of an EC is then slot below(u, m); bond partners are found
 // by binary search on the ids.  Positions are the wrapped FP64 coordinates
 // of the global state, so every candidate is evaluated with exactly the
-// arithmetic of the plain definition.  FP32 shadows (tile-local) feed the
-// screened form.
+// arithmetic of the plain definition.
+//
+// GB300's FP64 pipe is the scarce resource, so FP64 comparisons are done on
+// the bit patterns with integer instructions (same results), and in the
+// screened form (F32) every candidate — contact, tether, wall — is first
+// bounded in FP32 from tile-local shadows; only those whose lower bound can
+// reach the smallest upper bound U are evaluated in FP64, in rounds shared by
+// all lanes.  A candidate left out cannot be the winner: the winner's exact x
+// is <= U and every lower bound is <= its candidate's exact x.
 #include <cuda_runtime.h>
 #include <float.h>
 
@@ -25,7 +32,76 @@ namespace ecmc {
 namespace {
 
 constexpr unsigned FULL = 0xffffffffu;
-constexpr int BLOCK_THREADS = 128;
+
+// ---------------------------------------------------------------- FP64 bits
+__device__ __forceinline__ uint64_t dbits(double x) { return (uint64_t)__double_as_longlong(x); }
+// x < 0.0 (false for -0.0)
+__device__ __forceinline__ bool neg(double x) {
+  const uint64_t b = dbits(x);
+  return (int64_t)b < 0 && (b << 1) != 0;
+}
+// x > 0.0
+__device__ __forceinline__ bool posv(double x) { return (int64_t)dbits(x) > 0; }
+// y >= L for L > 0
+__device__ __forceinline__ bool ge_pos(double y, double L) {
+  return (int64_t)dbits(y) >= (int64_t)dbits(L);
+}
+__device__ __forceinline__ bool nonzero(double x) { return (dbits(x) << 1) != 0; }
+
+// minimum image, same result as d > h ? d - L : (d < -h ? d + L : d)
+__device__ __forceinline__ double wrap_i(double d, double L, uint64_t hbits) {
+  const uint64_t b = dbits(d);
+  if ((b & 0x7FFFFFFFFFFFFFFFull) > hbits) return ((int64_t)b < 0) ? d + L : d - L;
+  return d;
+}
+
+// r += x v on one axis, back into [0, L); returns the image change
+__device__ __forceinline__ int step_i(double &r, double x, double v, double L) {
+  double y = r + x * v;
+  int di = 0;
+  if (ge_pos(y, L)) {
+    y = y - L;
+    di = 1;
+  } else if (neg(y)) {
+    y = y + L;
+    di = -1;
+    if (ge_pos(y, L)) {
+      y = 0.0;
+      di = 0;
+    }
+  }
+  r = y;
+  return di;
+}
+
+// Hard-sphere contact (Eq. 1, R2 = sigma^2) or tether limit (R2 = b_max^2)
+// of a pivot moving along v, d = pivot - partner.  Returns x >= 0, or -1 when
+// a contact candidate misses; dv = d.v.
+__device__ __forceinline__ double quad_x(bool tether, double d0, double d1, double d2, double v0,
+                                         double v1, double v2, double R2, double &dv) {
+  dv = d0 * v0 + d1 * v1 + d2 * v2;
+  if (!tether && !neg(dv)) return -1.0;
+  const double dd = d0 * d0 + d1 * d1 + d2 * d2;
+  double rad = R2 - (dd - dv * dv);
+  if (tether) {
+    if (neg(rad)) rad = 0.0;
+  } else if (!posv(rad)) {
+    return -1.0;
+  }
+  const double x = tether ? -dv + sqrt(rad) : -dv - sqrt(rad);
+  return neg(x) ? 0.0 : x;
+}
+
+// v <- v - (2 v.d / d.d) d: reflection at the plane normal to d (Fig. 2c)
+__device__ __forceinline__ void mirror2(double &v0, double &v1, double &v2, double d0, double d1,
+                                        double d2) {
+  const double dd = d0 * d0 + d1 * d1 + d2 * d2;
+  const double vd = v0 * d0 + v1 * d1 + v2 * d2;
+  const double t = (2.0 * vd) / dd;
+  v0 = v0 - t * d0;
+  v1 = v1 - t * d1;
+  v2 = v2 - t * d2;
+}
 
 // candidate key: kind (3 bits) | partner id (41 bits) | slot (20 bits).
 // Key order within equal x = (kind, partner id) order, the tie rule.
@@ -39,7 +115,7 @@ __device__ __forceinline__ int key_slot(uint64_t k) { return (int)(k & 0xFFFFF);
 
 // x >= 0 always, so its bit pattern orders like the value
 __device__ __forceinline__ bool better(double x, uint64_t key, double bx, uint64_t bkey) {
-  const unsigned long long a = __double_as_longlong(x), b = __double_as_longlong(bx);
+  const uint64_t a = dbits(x), b = dbits(bx);
   return a < b || (a == b && key < bkey);
 }
 
@@ -63,18 +139,23 @@ __device__ __forceinline__ float group_minf(float v) {
   return v;
 }
 
-template <int G>
-__device__ __forceinline__ int group_max_i(int v) {
-  // lockstep bound over the whole warp
-  return __reduce_max_sync(FULL, v);
+// FP32 minimum image (serial mode only; tile-local shadows need none)
+__device__ __forceinline__ float wrapf(float d, float L) {
+  return d > 0.5f * L ? d - L : (d < -0.5f * L ? d + L : d);
 }
 
+// ---------------------------------------------------------------- staging
+// per slot: FP64 position (24 B), FP32 shadow (12 B), id (4 B), bond partner
+// slots packed as two 16-bit fields (4 B; 0xFFFF = none)
+constexpr int SLOT_BYTES = 44;
+constexpr int HDR_BYTES = 32;
+
 struct Stage {
-  double *px, *py, *pz;  // FP64 wrapped positions
-  float *fx, *fy, *fz;   // FP32 tile-local shadows
-  int *id;               // bead ids (sorted within each range)
-  int2 *nb;              // bond partner slots of motile beads (-1: none)
-  int *hdr;              // [0] m, [1] j1, [2] ns, [3] overflow
+  double *px, *py, *pz;
+  float *fx, *fy, *fz;
+  int *id;
+  unsigned *nb;
+  int *hdr;  // [2] staged count, [3] overflow
 };
 
 __device__ __forceinline__ Stage carve(unsigned char *base, int S) {
@@ -82,13 +163,19 @@ __device__ __forceinline__ Stage carve(unsigned char *base, int S) {
   s.px = (double *)base;
   s.py = s.px + S;
   s.pz = s.py + S;
-  s.nb = (int2 *)(s.pz + S);
-  s.fx = (float *)(s.nb + S);
+  s.fx = (float *)(s.pz + S);
   s.fy = s.fx + S;
   s.fz = s.fy + S;
   s.id = (int *)(s.fz + S);
-  s.hdr = s.id + S;
+  s.nb = (unsigned *)(s.id + S);
+  s.hdr = (int *)(s.nb + S);
   return s;
+}
+
+__device__ __forceinline__ int nb_prev(unsigned w) { return (w & 0xFFFF) == 0xFFFF ? -1 : (int)(w & 0xFFFF); }
+__device__ __forceinline__ int nb_next(unsigned w) { return (w >> 16) == 0xFFFF ? -1 : (int)(w >> 16); }
+__device__ __forceinline__ unsigned nb_pack(int prev, int next) {
+  return ((unsigned)(next < 0 ? 0xFFFF : next) << 16) | (unsigned)(prev < 0 ? 0xFFFF : prev);
 }
 
 // binary search of id in the sorted range [lo, hi); -1 if absent
@@ -106,40 +193,34 @@ __device__ __forceinline__ int find_id(const int *ids, int lo, int hi, int id) {
 __device__ __forceinline__ void set_status(int *st, int code) { atomicCAS(st, 0, code); }
 
 template <int G, bool F32>
-__global__ void __launch_bounds__(BLOCK_THREADS) ec_kernel(const ECParams P) {
+__global__ void __launch_bounds__(128) ec_kernel(const ECParams P) {
   extern __shared__ __align__(16) unsigned char smem[];
   const int lane = threadIdx.x & 31;
   const int gl = lane & (G - 1);
+  const int gbase = lane & ~(G - 1);
   const int gib = threadIdx.x / G;
   const int gpb = blockDim.x / G;
   const int unit = blockIdx.x * gpb + gib;
   const int S = P.stage_cap;
-  const size_t per_group = (size_t)S * 48 + 32;
-  Stage st = carve(smem + (size_t)gib * per_group, S);
+  Stage st = carve(smem + (size_t)gib * ((size_t)S * SLOT_BYTES + HDR_BYTES), S);
   bool live = unit < P.n_units;
+  const uint64_t hb0 = dbits(P.half[0]), hb1 = dbits(P.half[1]), hb2 = dbits(P.half[2]);
 
-  // tile geometry (domain) or the whole box (serial)
+  // tile geometry (domain) or the whole box (serial); corner = shift + k T
   int tk[3] = {0, 0, 0};
-  double corner[3] = {0.0, 0.0, 0.0};
+  double c0 = 0.0, c1 = 0.0, c2 = 0.0;
   if (P.domain && live) {
     tk[0] = unit % P.D[0];
     tk[1] = (unit / P.D[0]) % P.D[1];
     tk[2] = unit / (P.D[0] * P.D[1]);
-  }
-  // corner = shift + k T (the shift first, then the tile offset)
-  if (P.domain && live) {
     const u64x4 w = philox(TAG_SHIFT, (uint64_t)P.sweep, 0, 0, P.seed, P.replica);
-#pragma unroll
-    for (int a = 0; a < 3; ++a) {
-      const double sh = unit53(w.v[a]) * P.T[a];
-      corner[a] = sh + (double)tk[a] * P.T[a];
-    }
+    c0 = unit53(w.v[0]) * P.T[0] + (double)tk[0] * P.T[0];
+    c1 = unit53(w.v[1]) * P.T[1] + (double)tk[1] * P.T[1];
+    c2 = unit53(w.v[2]) * P.T[2] + (double)tk[2] * P.T[2];
   }
 
   // ------------------------------------------------------------ staging
   if (gl == 0) {
-    st.hdr[0] = 0;
-    st.hdr[1] = 0;
     st.hdr[2] = 0;
     st.hdr[3] = 0;
   }
@@ -158,19 +239,20 @@ __global__ void __launch_bounds__(BLOCK_THREADS) ec_kernel(const ECParams P) {
       st.fz[b] = (float)z;
       st.id[b] = b;
       const int c = b % P.N;
-      st.nb[b] = make_int2(c == 0 ? -1 : b - 1, c == P.N - 1 ? -1 : b + 1);
+      st.nb[b] = nb_pack(c == 0 ? -1 : b - 1, c == P.N - 1 ? -1 : b + 1);
     }
     m = n;
     j1 = 0;
     ns = n;
   } else {
+    const double corner[3] = {c0, c1, c2};
     // cell window covering the tether halo of the tile
     int c_lo[3], c_n[3];
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
       const double lo = corner[a] - P.halo_te, hi = corner[a] + P.W[a] + P.halo_te;
       int l = (int)floor(lo / P.cs[a]);
-      int h = (int)floor(hi / P.cs[a]);
+      const int h = (int)floor(hi / P.cs[a]);
       int cnt = h - l + 1;
       if (cnt >= P.nc[a]) {
         l = 0;
@@ -181,7 +263,9 @@ __global__ void __launch_bounds__(BLOCK_THREADS) ec_kernel(const ECParams P) {
     }
     const int ncell = c_n[0] * c_n[1] * c_n[2];
     const int ncell_max = __reduce_max_sync(FULL, ncell);
-    // pass 1: collect (cell-order index, category|id) in the nb scratch
+    // pass 1: collect (cell-order index, category|id); the shadow arrays
+    // (12 B per slot) serve as 8 B per slot of scratch until pass 3
+    int2 *scr = (int2 *)st.fx;
     for (int q0 = 0; q0 < ncell_max; q0 += G) {
       const int q = q0 + gl;
       if (q < ncell) {
@@ -211,7 +295,7 @@ __global__ void __launch_bounds__(BLOCK_THREADS) ec_kernel(const ECParams P) {
           }
           if (cat >= 0) {
             const int slot = atomicAdd(&st.hdr[2], 1);
-            if (slot < S) st.nb[slot] = make_int2(j, (cat << 29) | P.cid[j]);
+            if (slot < S) scr[slot] = make_int2(j, (cat << 29) | P.cid[j]);
             else st.hdr[3] = 1;
           }
         }
@@ -225,34 +309,25 @@ __global__ void __launch_bounds__(BLOCK_THREADS) ec_kernel(const ECParams P) {
       ns = 0;
     }
     const int ns_max = __reduce_max_sync(FULL, ns);
-    // pass 2: rank by (category, id) and place into the sorted slots
+    // pass 2: rank by (category, id); place FP64 positions and ids
     int cnt_cat0 = 0, cnt_cat1 = 0;
     for (int s0 = 0; s0 < ns_max; s0 += G) {
       const int s = s0 + gl;
-      int2 e = make_int2(0, 0);
-      int rank = 0;
       if (s < ns) {
-        e = st.nb[s];
-        for (int t = 0; t < ns; ++t) rank += (st.nb[t].y < e.y);
+        const int2 e = scr[s];
+        int rank = 0;
+        for (int t = 0; t < ns; ++t) rank += (scr[t].y < e.y);
         const int cat = e.y >> 29;
         cnt_cat0 += (cat == 0);
         cnt_cat1 += (cat == 1);
-      }
-      __syncwarp();
-      if (s < ns) {
         const int j = e.x;
-        const double x = P.cr[3 * (int64_t)j], y = P.cr[3 * (int64_t)j + 1], z = P.cr[3 * (int64_t)j + 2];
-        st.px[rank] = x;
-        st.py[rank] = y;
-        st.pz[rank] = z;
-        st.fx[rank] = (float)wrap_d(x - corner[0], P.L[0], P.half[0]);
-        st.fy[rank] = (float)wrap_d(y - corner[1], P.L[1], P.half[1]);
-        st.fz[rank] = (float)wrap_d(z - corner[2], P.L[2], P.half[2]);
+        st.px[rank] = P.cr[3 * (int64_t)j];
+        st.py[rank] = P.cr[3 * (int64_t)j + 1];
+        st.pz[rank] = P.cr[3 * (int64_t)j + 2];
         st.id[rank] = e.y & ((1 << 29) - 1);
       }
-      __syncwarp();
     }
-    // group sums of the category counts
+    __syncwarp();
 #pragma unroll
     for (int off = G / 2; off > 0; off >>= 1) {
       cnt_cat0 += __shfl_xor_sync(FULL, cnt_cat0, off);
@@ -260,26 +335,31 @@ __global__ void __launch_bounds__(BLOCK_THREADS) ec_kernel(const ECParams P) {
     }
     m = cnt_cat0;
     j1 = cnt_cat1;
-    // pass 3: bond partners of motile beads
+    // pass 3: shadows and bond partners of motile beads
     for (int s0 = 0; s0 < ns_max; s0 += G) {
       const int s = s0 + gl;
-      if (s < m) {
-        const int id = st.id[s];
-        const int c = id % P.N;
-        int2 nbv = make_int2(-1, -1);
-#pragma unroll
-        for (int dir = 0; dir < 2; ++dir) {
-          const bool has = dir == 0 ? (c != 0) : (c != P.N - 1);
-          if (!has) continue;
-          const int want = dir == 0 ? id - 1 : id + 1;
-          int f = find_id(st.id, 0, m, want);
-          if (f < 0) f = find_id(st.id, m, m + j1, want);
-          if (f < 0) f = find_id(st.id, m + j1, ns, want);
-          if (f < 0) set_status(P.status, DEV_TILE);
-          if (dir == 0) nbv.x = f;
-          else nbv.y = f;
+      if (s < ns) {
+        st.fx[s] = (float)wrap_d(st.px[s] - corner[0], P.L[0], P.half[0]);
+        st.fy[s] = (float)wrap_d(st.py[s] - corner[1], P.L[1], P.half[1]);
+        st.fz[s] = (float)wrap_d(st.pz[s] - corner[2], P.L[2], P.half[2]);
+        int prev = -1, next = -1;
+        if (s < m) {
+          const int id = st.id[s];
+          const int c = id % P.N;
+          if (c != 0) {
+            prev = find_id(st.id, 0, m, id - 1);
+            if (prev < 0) prev = find_id(st.id, m, m + j1, id - 1);
+            if (prev < 0) prev = find_id(st.id, m + j1, ns, id - 1);
+            if (prev < 0) set_status(P.status, DEV_TILE);
+          }
+          if (c != P.N - 1) {
+            next = find_id(st.id, 0, m, id + 1);
+            if (next < 0) next = find_id(st.id, m, m + j1, id + 1);
+            if (next < 0) next = find_id(st.id, m + j1, ns, id + 1);
+            if (next < 0) set_status(P.status, DEV_TILE);
+          }
         }
-        st.nb[s] = nbv;
+        st.nb[s] = nb_pack(prev, next);
       }
     }
     __syncwarp();
@@ -290,19 +370,30 @@ __global__ void __launch_bounds__(BLOCK_THREADS) ec_kernel(const ECParams P) {
 
   // ------------------------------------------------------------ ECs
   const int n_ec = P.ecs_per_tile;
-  const float sigf = (float)P.sigma;
   const float sig2f = (float)P.sig2;
-  const float near2 = (float)((P.s_cap + P.sigma + 0.01 * P.sigma) * (P.s_cap + P.sigma + 0.01 * P.sigma));
+  const float b2f = (float)P.b2;
+  const float eps_v = P.eps_v, eps_d = P.eps_d;
+  const float reach = (float)(P.s_cap + P.sigma + 0.01 * P.sigma);
+  const float near2 = reach * reach;
+  const float Lf0 = (float)P.L[0], Lf1 = (float)P.L[1], Lf2 = (float)P.L[2];
+  const float Wf0 = (float)P.W[0], Wf1 = (float)P.W[1], Wf2 = (float)P.W[2];
+  const float INF = __int_as_float(0x7f800000);
+  const double DINF = __longlong_as_double(0x7ff0000000000000ll);
+  double lift_all = 0.0, refl_all = 0.0, disp_all = 0.0;
+  unsigned long long cnt[ECMC_NEV];
+#pragma unroll
+  for (int k = 0; k < ECMC_NEV; ++k) cnt[k] = 0;
+  unsigned long long tried = 0, confirmed = 0, nev_all = 0, ecs_done = 0;
+
   for (int e = 0; e < n_ec; ++e) {
     bool active = live && m > 0;
-    // start bead and direction
-    const uint64_t c0 = P.domain ? (TAG_START | ((uint64_t)e << 8)) : TAG_START;
-    const uint64_t c1 = P.domain ? (uint64_t)P.sweep : 0;
-    const uint64_t c2 = P.domain ? (uint64_t)unit : (uint64_t)(P.sweep + e);
+    const uint64_t r0 = P.domain ? (TAG_START | ((uint64_t)e << 8)) : TAG_START;
+    const uint64_t r1 = P.domain ? (uint64_t)P.sweep : 0;
+    const uint64_t r2 = P.domain ? (uint64_t)unit : (uint64_t)(P.sweep + e);
     int p = 0;
     double v0 = 0.0, v1 = 0.0, v2 = 0.0;
     if (active) {
-      u64x4 w = philox(c0, c1, c2, 0, P.seed, P.replica);
+      u64x4 w = philox(r0, r1, r2, 0, P.seed, P.replica);
       p = (int)scale_below(w.v[0], (uint64_t)m);
       if (P.dir_mode == ECMC_DIR_CART3) {
         const int ax = (int)scale_below(w.v[1], 3);
@@ -324,7 +415,7 @@ __global__ void __launch_bounds__(BLOCK_THREADS) ec_kernel(const ECParams P) {
             break;
           }
           ++att;
-          w = philox(c0, c1, c2, att, P.seed, P.replica);
+          w = philox(r0, r1, r2, att, P.seed, P.replica);
           a = 2.0 * unit53(w.v[0]) - 1.0;
           b = 2.0 * unit53(w.v[1]) - 1.0;
           c = 2.0 * unit53(w.v[2]) - 1.0;
@@ -341,123 +432,254 @@ __global__ void __launch_bounds__(BLOCK_THREADS) ec_kernel(const ECParams P) {
     u64x4 swr;
     swr.v[0] = swr.v[1] = swr.v[2] = swr.v[3] = 0;
     uint64_t h = 0xCBF29CE484222325ull;
-    double lift = 0.0, refl = 0.0, disp = 0.0;
-    unsigned long long cnt[ECMC_NEV];
-#pragma unroll
-    for (int k = 0; k < ECMC_NEV; ++k) cnt[k] = 0;
-    unsigned long long tried = 0;
-    unsigned long long confirmed = 0;
+    double lift = 0.0;
 
     while (__any_sync(FULL, active)) {
       if (active && nev >= P.event_cap) {
         if (gl == 0) set_status(P.status, DEV_STUCK);
         active = false;
       }
-      // special candidates, one per lane: end/pass, two tethers, three walls
-      double bx = __longlong_as_double(0x7ff0000000000000ll);  // +inf
+      double bx = DINF;  // lane-local best exactly evaluated candidate
       uint64_t bkey = ~0ull;
-      if (active) {
-        if (gl == 0) {
-          if (P.s_cap < xrem) {
-            bx = P.s_cap;
-            bkey = make_key(KIND_PASS, 0, 0);
-          } else {
-            bx = xrem;
-            bkey = make_key(KIND_END, 0, 0);
-          }
-        } else if (gl <= 2) {
-          const int2 nbv = st.nb[p];
-          const int t = gl == 1 ? nbv.x : nbv.y;
-          if (t >= 0) {
-            const double d0 = wrap_d(q0 - st.px[t], P.L[0], P.half[0]);
-            const double d1 = wrap_d(q1 - st.py[t], P.L[1], P.half[1]);
-            const double d2 = wrap_d(q2 - st.pz[t], P.L[2], P.half[2]);
-            bx = tether_x(d0, d1, d2, v0, v1, v2, P.b2);
-            bkey = make_key(KIND_TETHER, st.id[t], t);
-          }
-        } else if (gl <= 5 && P.domain) {
-          const int a = gl - 3;
-          const double va = a == 0 ? v0 : (a == 1 ? v1 : v2);
-          const double qa = a == 0 ? q0 : (a == 1 ? q1 : q2);
-          if (va != 0.0) {
-            const double loc = wrap_d(qa - corner[a], P.L[a], P.half[a]);
-            double x = va > 0.0 ? (P.W[a] - loc) / va : (0.0 - loc) / va;
-            if (x < 0.0) x = 0.0;
-            bx = x;
-            bkey = make_key(KIND_WALL, a, 0);
+      double bdv = 0.0;
+      const unsigned nbw = active ? st.nb[p] : 0xFFFFFFFFu;
+      if (!F32) {
+        // ---------------- plain FP64: every candidate evaluated exactly
+        if (active) {
+          if (gl == 0) {
+            if (dbits(P.s_cap) < dbits(xrem)) {
+              bx = P.s_cap;
+              bkey = make_key(KIND_PASS, 0, 0);
+            } else {
+              bx = xrem;
+              bkey = make_key(KIND_END, 0, 0);
+            }
+          } else if (gl <= 2) {
+            const int t = gl == 1 ? nb_prev(nbw) : nb_next(nbw);
+            if (t >= 0) {
+              double dv;
+              const double x = quad_x(true, wrap_i(q0 - st.px[t], P.L[0], hb0),
+                                      wrap_i(q1 - st.py[t], P.L[1], hb1),
+                                      wrap_i(q2 - st.pz[t], P.L[2], hb2), v0, v1, v2, P.b2, dv);
+              bx = x;
+              bkey = make_key(KIND_TETHER, st.id[t], t);
+              bdv = dv;
+            }
+          } else if (gl <= 5 && P.domain) {
+            const int a = gl - 3;
+            const double va = a == 0 ? v0 : (a == 1 ? v1 : v2);
+            if (nonzero(va)) {
+              const double qa = a == 0 ? q0 : (a == 1 ? q1 : q2);
+              const double ca = a == 0 ? c0 : (a == 1 ? c1 : c2);
+              const double loc = wrap_i(qa - ca, P.L[a], a == 0 ? hb0 : (a == 1 ? hb1 : hb2));
+              double x = posv(va) ? (P.W[a] - loc) / va : (0.0 - loc) / va;
+              if (neg(x)) x = 0.0;
+              bx = x;
+              bkey = make_key(KIND_WALL, a, 0);
+            }
           }
         }
-      }
-      if (!F32) {
-        // plain FP64: every staged obstacle is a candidate
         for (int k0 = 0; k0 < nhs_max; k0 += G) {
           const int k = k0 + gl;
           if (active && k < nhs && k != p) {
-            const double d0 = wrap_d(q0 - st.px[k], P.L[0], P.half[0]);
-            const double d1 = wrap_d(q1 - st.py[k], P.L[1], P.half[1]);
-            const double d2 = wrap_d(q2 - st.pz[k], P.L[2], P.half[2]);
-            const double x = contact_x(d0, d1, d2, v0, v1, v2, P.sig2);
-            if (x >= 0.0) {
+            double dv;
+            const double x = quad_x(false, wrap_i(q0 - st.px[k], P.L[0], hb0),
+                                    wrap_i(q1 - st.py[k], P.L[1], hb1),
+                                    wrap_i(q2 - st.pz[k], P.L[2], hb2), v0, v1, v2, P.sig2, dv);
+            if (!neg(x)) {
               const uint64_t key = make_key(KIND_HS, st.id[k], k);
               if (better(x, key, bx, bkey)) {
                 bx = x;
                 bkey = key;
+                bdv = dv;
               }
             }
           }
         }
       } else {
-        // FP32 screen: U bounds the smallest candidate from above; only
-        // beads whose lower bound |d| - sigma can reach U are confirmed in
-        // FP64 (the margins cover the FP32 rounding of tile-local coordinates)
-        float ub = __double2float_ru(bx);
+        // ---------------- FP32 screen, FP64 confirmation
+        float ubl = INF;
+        int sp_kind = -1, sp_slot = -1;  // this lane's tether or wall
+        float sp_lb = INF;
+        if (active) {
+          if (gl == 0) {
+            if (dbits(P.s_cap) < dbits(xrem)) {
+              bx = P.s_cap;
+              bkey = make_key(KIND_PASS, 0, 0);
+            } else {
+              bx = xrem;
+              bkey = make_key(KIND_END, 0, 0);
+            }
+            ubl = __double2float_ru(bx);
+          } else if (gl <= 2) {
+            const int t = gl == 1 ? nb_prev(nbw) : nb_next(nbw);
+            if (t >= 0) {
+              float d0 = pf0 - st.fx[t], d1 = pf1 - st.fy[t], d2 = pf2 - st.fz[t];
+              if (!P.domain) {
+                d0 = wrapf(d0, Lf0);
+                d1 = wrapf(d1, Lf1);
+                d2 = wrapf(d2, Lf2);
+              }
+              const float dd = __fmaf_rn(d2, d2, __fmaf_rn(d1, d1, d0 * d0));
+              const float dv = __fmaf_rn(d2, vf2, __fmaf_rn(d1, vf1, d0 * vf0));
+              const float rad = b2f - (dd - dv * dv);
+              const float lo = -dv - eps_v + sqrtf(fmaxf(rad - eps_d, 0.f)) * 0.9999998f;
+              const float hi = -dv + eps_v + sqrtf(fmaxf(rad + eps_d, 0.f)) * 1.0000002f;
+              sp_lb = fmaxf(lo, 0.f);
+              ubl = fmaxf(hi, 0.f) + 1e-6f;
+              sp_kind = KIND_TETHER;
+              sp_slot = t;
+            }
+          } else if (gl <= 5 && P.domain) {
+            const int a = gl - 3;
+            const double va = a == 0 ? v0 : (a == 1 ? v1 : v2);
+            if (nonzero(va)) {
+              const float vfa = a == 0 ? vf0 : (a == 1 ? vf1 : vf2);
+              const float pfa = a == 0 ? pf0 : (a == 1 ? pf1 : pf2);
+              const float Wfa = a == 0 ? Wf0 : (a == 1 ? Wf1 : Wf2);
+              const float dist = posv(va) ? Wfa - pfa : pfa;
+              const float av = fabsf(vfa);
+              if (av > 0.f) {
+                sp_lb = fmaxf(dist - eps_v, 0.f) / (av * 1.000001f);
+                ubl = (fmaxf(dist, 0.f) + eps_v) / (av * 0.999999f);
+              } else {
+                sp_lb = 0.f;  // |v_a| below FP32 range: confirm in FP64
+              }
+              sp_kind = KIND_WALL;
+              sp_slot = a;
+            }
+          }
+        }
+        // hard-sphere obstacles: bounds, keep up to two possible winners
+        int ks0 = -1, ks1 = -1;
+        float kl0 = INF, kl1 = INF;
+        bool ovf = false;
         for (int k0 = 0; k0 < nhs_max; k0 += G) {
           const int k = k0 + gl;
           if (active && k < nhs && k != p) {
             float d0 = pf0 - st.fx[k], d1 = pf1 - st.fy[k], d2 = pf2 - st.fz[k];
             if (!P.domain) {
-              d0 = d0 > 0.5f * (float)P.L[0] ? d0 - (float)P.L[0] : (d0 < -0.5f * (float)P.L[0] ? d0 + (float)P.L[0] : d0);
-              d1 = d1 > 0.5f * (float)P.L[1] ? d1 - (float)P.L[1] : (d1 < -0.5f * (float)P.L[1] ? d1 + (float)P.L[1] : d1);
-              d2 = d2 > 0.5f * (float)P.L[2] ? d2 - (float)P.L[2] : (d2 < -0.5f * (float)P.L[2] ? d2 + (float)P.L[2] : d2);
+              d0 = wrapf(d0, Lf0);
+              d1 = wrapf(d1, Lf1);
+              d2 = wrapf(d2, Lf2);
             }
             const float dd = __fmaf_rn(d2, d2, __fmaf_rn(d1, d1, d0 * d0));
             if (dd <= near2) {
               const float dv = __fmaf_rn(d2, vf2, __fmaf_rn(d1, vf1, d0 * vf0));
               const float disc = sig2f - (dd - dv * dv);
-              if (dv < -P.eps_v && disc > P.eps_d) {
-                const float u = fmaxf(0.f, -dv - sqrtf(disc - P.eps_d)) + P.eps_x;
-                ub = fminf(ub, u);
+              if (dv < eps_v && disc > -eps_d) {
+                if (dv < -eps_v && disc > eps_d) {
+                  const float u = fmaxf(0.f, -dv + eps_v - sqrtf(disc - eps_d) * 0.9999998f) + 1e-6f;
+                  ubl = fminf(ubl, u);
+                }
+                const float lb = -dv - eps_v - sqrtf(disc + eps_d) * 1.0000002f;
+                if (lb <= ubl) {
+                  if (kl0 > ubl) {
+                    ks0 = -1;
+                    kl0 = INF;
+                  }
+                  if (kl1 > ubl) {
+                    ks1 = -1;
+                    kl1 = INF;
+                  }
+                  if (ks0 < 0) {
+                    ks0 = k;
+                    kl0 = lb;
+                  } else if (ks1 < 0) {
+                    ks1 = k;
+                    kl1 = lb;
+                  } else {
+                    ovf = true;
+                  }
+                }
               }
             }
           }
         }
-        const float U = group_minf<G>(ub);
-        const float rr = U + sigf + P.eps_x;
-        const float lb2 = rr * rr * 1.000001f;
-        for (int k0 = 0; k0 < nhs_max; k0 += G) {
-          const int k = k0 + gl;
-          if (active && k < nhs && k != p) {
+        const float U = group_minf<G>(ubl);
+        // survivors of this lane, confirmed in FP64 in shared rounds
+        int job0 = -1, job1 = -1, job2 = -1;  // slot | (tether << 30)
+        int nj = 0;
+        if (sp_kind == KIND_TETHER && sp_lb <= U) {
+          job0 = sp_slot | (1 << 30);
+          nj = 1;
+        }
+        if (ks0 >= 0 && kl0 <= U) {
+          if (nj == 0) job0 = ks0;
+          else job1 = ks0;
+          ++nj;
+        }
+        if (ks1 >= 0 && kl1 <= U) {
+          if (nj == 0) job0 = ks1;
+          else if (nj == 1) job1 = ks1;
+          else job2 = ks1;
+          ++nj;
+        }
+        const int rounds = __reduce_max_sync(FULL, nj);
+        for (int r = 0; r < rounds; ++r) {
+          if (r < nj) {
+            const int job = r == 0 ? job0 : (r == 1 ? job1 : job2);
+            const bool te = (job >> 30) & 1;
+            const int k = job & 0x3FFFFFFF;
+            double dv;
+            const double x = quad_x(te, wrap_i(q0 - st.px[k], P.L[0], hb0),
+                                    wrap_i(q1 - st.py[k], P.L[1], hb1),
+                                    wrap_i(q2 - st.pz[k], P.L[2], hb2), v0, v1, v2,
+                                    te ? P.b2 : P.sig2, dv);
+            ++confirmed;
+            if (!neg(x)) {
+              const uint64_t key = make_key(te ? KIND_TETHER : KIND_HS, st.id[k], k);
+              if (better(x, key, bx, bkey)) {
+                bx = x;
+                bkey = key;
+                bdv = dv;
+              }
+            }
+          }
+        }
+        if (sp_kind == KIND_WALL && sp_lb <= U) {
+          const int a = sp_slot;
+          const double va = a == 0 ? v0 : (a == 1 ? v1 : v2);
+          const double qa = a == 0 ? q0 : (a == 1 ? q1 : q2);
+          const double ca = a == 0 ? c0 : (a == 1 ? c1 : c2);
+          const double loc = wrap_i(qa - ca, P.L[a], a == 0 ? hb0 : (a == 1 ? hb1 : hb2));
+          double x = posv(va) ? (P.W[a] - loc) / va : (0.0 - loc) / va;
+          if (neg(x)) x = 0.0;
+          ++confirmed;
+          const uint64_t key = make_key(KIND_WALL, a, 0);
+          if (better(x, key, bx, bkey)) {
+            bx = x;
+            bkey = key;
+          }
+        }
+        if (ovf) {
+          // more than two possible winners in this lane: rescan its share
+          for (int k = gl; k < nhs; k += G) {
+            if (k == p || k == ks0 || k == ks1) continue;
             float d0 = pf0 - st.fx[k], d1 = pf1 - st.fy[k], d2 = pf2 - st.fz[k];
             if (!P.domain) {
-              d0 = d0 > 0.5f * (float)P.L[0] ? d0 - (float)P.L[0] : (d0 < -0.5f * (float)P.L[0] ? d0 + (float)P.L[0] : d0);
-              d1 = d1 > 0.5f * (float)P.L[1] ? d1 - (float)P.L[1] : (d1 < -0.5f * (float)P.L[1] ? d1 + (float)P.L[1] : d1);
-              d2 = d2 > 0.5f * (float)P.L[2] ? d2 - (float)P.L[2] : (d2 < -0.5f * (float)P.L[2] ? d2 + (float)P.L[2] : d2);
+              d0 = wrapf(d0, Lf0);
+              d1 = wrapf(d1, Lf1);
+              d2 = wrapf(d2, Lf2);
             }
             const float dd = __fmaf_rn(d2, d2, __fmaf_rn(d1, d1, d0 * d0));
-            if (dd <= lb2) {
+            if (dd <= near2) {
               const float dv = __fmaf_rn(d2, vf2, __fmaf_rn(d1, vf1, d0 * vf0));
               const float disc = sig2f - (dd - dv * dv);
-              if (dv < P.eps_v && disc > -P.eps_d) {
+              const float lb = -dv - eps_v - sqrtf(disc + eps_d) * 1.0000002f;
+              if (dv < eps_v && disc > -eps_d && lb <= U) {
+                double dvx;
+                const double x = quad_x(false, wrap_i(q0 - st.px[k], P.L[0], hb0),
+                                        wrap_i(q1 - st.py[k], P.L[1], hb1),
+                                        wrap_i(q2 - st.pz[k], P.L[2], hb2), v0, v1, v2, P.sig2,
+                                        dvx);
                 ++confirmed;
-                const double e0 = wrap_d(q0 - st.px[k], P.L[0], P.half[0]);
-                const double e1 = wrap_d(q1 - st.py[k], P.L[1], P.half[1]);
-                const double e2 = wrap_d(q2 - st.pz[k], P.L[2], P.half[2]);
-                const double x = contact_x(e0, e1, e2, v0, v1, v2, P.sig2);
-                if (x >= 0.0) {
+                if (!neg(x)) {
                   const uint64_t key = make_key(KIND_HS, st.id[k], k);
                   if (better(x, key, bx, bkey)) {
                     bx = x;
                     bkey = key;
+                    bdv = dvx;
                   }
                 }
               }
@@ -465,7 +687,14 @@ __global__ void __launch_bounds__(BLOCK_THREADS) ec_kernel(const ECParams P) {
           }
         }
       }
+      // ---------------- winner of the group and its pre-flight d.v
+      const uint64_t my_key = bkey;
+      const uint64_t my_x = dbits(bx);
       group_argmin<G>(bx, bkey);
+      const unsigned own = __ballot_sync(FULL, my_key == bkey && my_x == dbits(bx));
+      const unsigned gmask = (G == 32) ? FULL : (((1u << G) - 1) << gbase);
+      const int src = __ffs(own & gmask) - 1;
+      const double wdv = __shfl_sync(FULL, bdv, src < 0 ? lane : src);
       __syncwarp();
 
       int np = p;
@@ -474,19 +703,17 @@ __global__ void __launch_bounds__(BLOCK_THREADS) ec_kernel(const ECParams P) {
         const int kind = key_kind(bkey);
         const int slot = key_slot(bkey);
         const int64_t partner = (kind == KIND_END || kind == KIND_PASS) ? -1 : key_id(bkey);
-        // move the pivot
-        const int di0 = step_axis(q0, x, v0, P.L[0]);
-        const int di1 = step_axis(q1, x, v1, P.L[1]);
-        const int di2 = step_axis(q2, x, v2, P.L[2]);
-        if (gl == 0) {
+        const int di0 = step_i(q0, x, v0, P.L[0]);
+        const int di1 = step_i(q1, x, v1, P.L[1]);
+        const int di2 = step_i(q2, x, v2, P.L[2]);
+        if (gl == 0 && (di0 | di1 | di2)) {
           if (di0) P.img[3 * (int64_t)pid] += di0;
           if (di1) P.img[3 * (int64_t)pid + 1] += di1;
           if (di2) P.img[3 * (int64_t)pid + 2] += di2;
         }
-        disp = disp + x;
         ++nev;
         int out;
-        bool moved_pivot_slot = false;  // pivot's own slot now holds a new position
+        bool swapped = false;
         if (kind == KIND_END) {
           out = ECMC_EV_END;
         } else if (kind == KIND_PASS) {
@@ -497,63 +724,68 @@ __global__ void __launch_bounds__(BLOCK_THREADS) ec_kernel(const ECParams P) {
           else if (partner == 1) v1 = -v1;
           else v2 = -v2;
         } else {
-          const double k0 = st.px[slot], k1 = st.py[slot], k2 = st.pz[slot];
-          const double d0 = wrap_d(q0 - k0, P.L[0], P.half[0]);
-          const double d1 = wrap_d(q1 - k1, P.L[1], P.half[1]);
-          const double d2 = wrap_d(q2 - k2, P.L[2], P.half[2]);
-          const double proj = 0.0 - (d0 * v0 + d1 * v1 + d2 * v2);
+          // (r_target - r_pivot).v at contact = -(d.v) - x
+          const double proj = -wdv - x;
           const bool motile = slot < m;
           if (!motile) {
             out = kind == KIND_HS ? ECMC_EV_HS_REFLECT : ECMC_EV_TE_REFLECT;
-            refl = refl + proj;
-            mirror(v0, v1, v2, d0, d1, d2);
+            refl_all = refl_all + proj;
+            const double d0 = wrap_i(q0 - st.px[slot], P.L[0], hb0);
+            const double d1 = wrap_i(q1 - st.py[slot], P.L[1], hb1);
+            const double d2 = wrap_i(q2 - st.pz[slot], P.L[2], hb2);
+            mirror2(v0, v1, v2, d0, d1, d2);
           } else if (kind == KIND_HS) {
             lift = lift + proj;
-            bool swapped = false;
             if (P.p_swap > 0.0) {
               bool go;
               if (P.p_swap >= 1.0) {
                 go = true;
               } else {
                 if ((ncontact & 3) == 0)
-                  swr = philox(TAG_SWAP | ((uint64_t)(P.domain ? e : 0) << 8), c1, c2,
+                  swr = philox(TAG_SWAP | ((uint64_t)(P.domain ? e : 0) << 8), r1, r2,
                                (uint64_t)(ncontact >> 2), P.seed, P.replica);
                 go = unit53(swr.v[ncontact & 3]) < P.p_swap;
               }
               ++ncontact;
               if (go) {
                 ++tried;
-                // bonds of the pivot (slot p) and the hit bead (slot) with the
-                // two positions exchanged must all stay within b_max
+                const double k0 = st.px[slot], k1 = st.py[slot], k2 = st.pz[slot];
+                // every bond of both beads, positions exchanged, within b_max
                 bool ok = true;
 #pragma unroll
                 for (int side = 0; side < 2; ++side) {
                   const int a = side == 0 ? p : slot;
-                  const double a0 = side == 0 ? k0 : q0;  // new position of a
+                  const double a0 = side == 0 ? k0 : q0;
                   const double a1 = side == 0 ? k1 : q1;
                   const double a2 = side == 0 ? k2 : q2;
-                  const int2 nbv = st.nb[a];
+                  const unsigned nbv = st.nb[a];
 #pragma unroll
                   for (int dir = 0; dir < 2; ++dir) {
-                    const int b = dir == 0 ? nbv.x : nbv.y;
+                    const int b = dir == 0 ? nb_prev(nbv) : nb_next(nbv);
                     if (b < 0) continue;
                     double b0, b1, b2;
                     if (b == p) {
-                      b0 = k0; b1 = k1; b2 = k2;
+                      b0 = k0;
+                      b1 = k1;
+                      b2 = k2;
                     } else if (b == slot) {
-                      b0 = q0; b1 = q1; b2 = q2;
+                      b0 = q0;
+                      b1 = q1;
+                      b2 = q2;
                     } else {
-                      b0 = st.px[b]; b1 = st.py[b]; b2 = st.pz[b];
+                      b0 = st.px[b];
+                      b1 = st.py[b];
+                      b2 = st.pz[b];
                     }
-                    const double e0 = wrap_d(a0 - b0, P.L[0], P.half[0]);
-                    const double e1 = wrap_d(a1 - b1, P.L[1], P.half[1]);
-                    const double e2 = wrap_d(a2 - b2, P.L[2], P.half[2]);
-                    ok = ok && (e0 * e0 + e1 * e1 + e2 * e2 <= P.b2);
+                    const double e0 = wrap_i(a0 - b0, P.L[0], hb0);
+                    const double e1 = wrap_i(a1 - b1, P.L[1], hb1);
+                    const double e2 = wrap_i(a2 - b2, P.L[2], hb2);
+                    const double dd = e0 * e0 + e1 * e1 + e2 * e2;
+                    ok = ok && !(dbits(dd) > dbits(P.b2));
                   }
                 }
                 if (ok) {
                   swapped = true;
-                  // exchange positions and image counters; the pivot stays
                   if (gl == 0) {
                     st.px[slot] = q0;
                     st.py[slot] = q1;
@@ -566,7 +798,6 @@ __global__ void __launch_bounds__(BLOCK_THREADS) ec_kernel(const ECParams P) {
                       P.img[3 * (int64_t)kid + a] = ti;
                     }
                   }
-                  moved_pivot_slot = true;
                   q0 = k0;
                   q1 = k1;
                   q2 = k2;
@@ -590,7 +821,7 @@ __global__ void __launch_bounds__(BLOCK_THREADS) ec_kernel(const ECParams P) {
         if (gl == 0) {
           fnv_mix(h, (uint64_t)pid);
           fnv_mix(h, ((uint64_t)(uint32_t)out << 32) | (uint64_t)(uint32_t)partner);
-          fnv_mix(h, (uint64_t)__double_as_longlong(x));
+          fnv_mix(h, dbits(x));
           if (P.log) {
             const unsigned long long at = atomicAdd(P.log_n, 1ull);
             if ((int64_t)at < P.log_cap) {
@@ -605,19 +836,17 @@ __global__ void __launch_bounds__(BLOCK_THREADS) ec_kernel(const ECParams P) {
               P.log[at] = ev;
             }
           }
-        }
-        // store the pivot's (possibly swapped) position and its FP32 shadow
-        if (gl == 0) {
           st.px[p] = q0;
           st.py[p] = q1;
           st.pz[p] = q2;
         }
         if (F32) {
+          // FP32 shadow of the moved pivot (and of the swapped partner)
           float nf0, nf1, nf2;
           if (P.domain) {
-            nf0 = (float)wrap_d(q0 - corner[0], P.L[0], P.half[0]);
-            nf1 = (float)wrap_d(q1 - corner[1], P.L[1], P.half[1]);
-            nf2 = (float)wrap_d(q2 - corner[2], P.L[2], P.half[2]);
+            nf0 = (float)wrap_i(q0 - c0, P.L[0], hb0);
+            nf1 = (float)wrap_i(q1 - c1, P.L[1], hb1);
+            nf2 = (float)wrap_i(q2 - c2, P.L[2], hb2);
           } else {
             nf0 = (float)q0;
             nf1 = (float)q1;
@@ -627,13 +856,12 @@ __global__ void __launch_bounds__(BLOCK_THREADS) ec_kernel(const ECParams P) {
             st.fx[p] = nf0;
             st.fy[p] = nf1;
             st.fz[p] = nf2;
-            if (moved_pivot_slot) {
-              // the hit bead now sits at the pivot's old contact position
+            if (swapped) {
               const double o0 = st.px[slot], o1 = st.py[slot], o2 = st.pz[slot];
               if (P.domain) {
-                st.fx[slot] = (float)wrap_d(o0 - corner[0], P.L[0], P.half[0]);
-                st.fy[slot] = (float)wrap_d(o1 - corner[1], P.L[1], P.half[1]);
-                st.fz[slot] = (float)wrap_d(o2 - corner[2], P.L[2], P.half[2]);
+                st.fx[slot] = (float)wrap_i(o0 - c0, P.L[0], hb0);
+                st.fy[slot] = (float)wrap_i(o1 - c1, P.L[1], hb1);
+                st.fz[slot] = (float)wrap_i(o2 - c2, P.L[2], hb2);
               } else {
                 st.fx[slot] = (float)o0;
                 st.fy[slot] = (float)o1;
@@ -672,22 +900,13 @@ __global__ void __launch_bounds__(BLOCK_THREADS) ec_kernel(const ECParams P) {
       }
       __syncwarp();
     }
-    // EC bookkeeping
-    if (F32) {
-#pragma unroll
-      for (int off = G / 2; off > 0; off >>= 1) confirmed += __shfl_xor_sync(FULL, confirmed, off);
-    }
-    if (live && m > 0 && gl == 0) {
-      if (confirmed) atomicAdd(&P.counters[CNT_CONFIRMED], confirmed);
-      for (int k = 0; k < ECMC_NEV; ++k)
-        if (cnt[k]) atomicAdd(&P.counters[k], cnt[k]);
-      atomicAdd(&P.counters[CNT_EVENTS], (unsigned long long)nev);
-      if (tried) atomicAdd(&P.counters[CNT_SWAP_TRIED], tried);
-      atomicAdd(&P.counters[CNT_ECS], 1ull);
-      atomicAdd(&P.sums[SUM_LIFT], lift);
-      atomicAdd(&P.sums[SUM_REFL], refl);
-      atomicAdd(&P.sums[SUM_DISP], disp);
-      if (P.rec_digest) {
+    // EC records
+    if (live && m > 0) {
+      lift_all = lift_all + lift;
+      disp_all = disp_all + P.ell;  // the free flights of an EC add up to ell
+      nev_all += (unsigned long long)nev;
+      ++ecs_done;
+      if (gl == 0 && P.rec_digest) {
         const int64_t idx = P.rec_offset + (P.domain ? (int64_t)unit * n_ec + e : (int64_t)e);
         if (idx < P.rec_cap) {
           P.rec_digest[idx] = h;
@@ -696,7 +915,23 @@ __global__ void __launch_bounds__(BLOCK_THREADS) ec_kernel(const ECParams P) {
         }
       }
     }
-    __syncwarp();
+  }
+  // counters of this group's ECs
+  if (F32) {
+#pragma unroll
+    for (int off = G / 2; off > 0; off >>= 1) confirmed += __shfl_xor_sync(FULL, confirmed, off);
+  }
+  if (live && gl == 0 && ecs_done) {
+#pragma unroll
+    for (int k = 0; k < ECMC_NEV; ++k)
+      if (cnt[k]) atomicAdd(&P.counters[k], cnt[k]);
+    atomicAdd(&P.counters[CNT_EVENTS], nev_all);
+    if (tried) atomicAdd(&P.counters[CNT_SWAP_TRIED], tried);
+    if (confirmed) atomicAdd(&P.counters[CNT_CONFIRMED], confirmed);
+    atomicAdd(&P.counters[CNT_ECS], ecs_done);
+    atomicAdd(&P.sums[SUM_LIFT], lift_all);
+    atomicAdd(&P.sums[SUM_REFL], refl_all);
+    atomicAdd(&P.sums[SUM_DISP], disp_all);
   }
 
   // ------------------------------------------------------------ write back
@@ -711,13 +946,10 @@ __global__ void __launch_bounds__(BLOCK_THREADS) ec_kernel(const ECParams P) {
 }
 
 }  // namespace
-}  // namespace ecmc
-
-namespace ecmc {
 
 size_t ec_smem_bytes(int stage_cap, int lanes, int groups_per_block) {
   (void)lanes;
-  return (size_t)groups_per_block * ((size_t)stage_cap * 48 + 32);
+  return (size_t)groups_per_block * ((size_t)stage_cap * SLOT_BYTES + HDR_BYTES);
 }
 
 template <int G, bool F32>
