@@ -87,7 +87,9 @@ typedef struct ecmc_opts {
   int64_t event_cap;     /* events per EC before ECMC_ESTUCK; 0 -> 10^7 */
   double p_swap;         /* swap proposal probability at a motile contact */
   int32_t ecs_per_tile;  /* ECs per tile per sweep (domain); 0 -> 1 */
-  int32_t lanes;         /* lanes per EC: 32, 16 or 8; 0 -> 32 */
+  int32_t lanes;         /* lanes per EC: 32, 16, 8, or 1 (domain mode: one thread
+                            per tile, local cell grid in a per-tile scratch
+                            region); 0 -> 32 */
   int32_t record;        /* 1: keep per-EC digests / lift sums of the last run */
   int32_t stage_cap;     /* staged beads per tile; 0 -> derived from the tile size */
   double cell_side;      /* side of the global cell grid (domain); 0 -> 1.0 sigma */

@@ -59,6 +59,13 @@ struct ecmc_ctx {
   int64_t ncell = 1;
   int32_t stage_cap = 0;
   int32_t lanes = 32;
+  // one-lane-per-tile kernel: per-tile scratch and local grid
+  unsigned char *d_scratch = nullptr;
+  size_t scratch_bytes = 0;
+  int64_t tile_bytes = 0;
+  int32_t lg[3] = {1, 1, 1};
+  float linv[3] = {1, 1, 1};
+  float lorg = 0.f;
   int64_t event_cap = 10000000;
   int32_t ecs_per_tile = 1;
   // stream
@@ -248,7 +255,7 @@ void destroy(ecmc_ctx *c) {
   void *ptrs[] = {c->d_r, c->d_img, c->d_tag, c->d_cell, c->d_rank, c->d_count, c->d_start,
                   c->d_bsum, c->d_cr, c->d_cid, c->d_ctag, c->d_cnt, c->d_sums, c->d_status,
                   c->d_obs_d, c->d_obs_u, c->d_g1ref, c->d_rdig, c->d_rlift, c->d_rev,
-                  c->d_log, c->d_log_n};
+                  c->d_log, c->d_log_n, c->d_scratch};
   for (void *p : ptrs) cudaFree(p);
   for (cudaEvent_t e : c->kev) cudaEventDestroy(e);
   if (c->ev0) cudaEventDestroy(c->ev0);
@@ -429,7 +436,10 @@ ecmc_status ecmc_configure(ecmc_ctx *c, const ecmc_opts *o) {
   const double w = p.joint > 0 ? p.joint : c->b_max;
   if (!(w >= c->b_max)) return fail(ECMC_EINVAL, "joint width must be >= b_max");
   const int lanes = p.lanes ? p.lanes : 32;
-  if (lanes != 32 && lanes != 16 && lanes != 8) return fail(ECMC_EINVAL, "lanes must be 8, 16 or 32");
+  if (lanes != 32 && lanes != 16 && lanes != 8 && lanes != 1)
+    return fail(ECMC_EINVAL, "lanes must be 1, 8, 16 or 32");
+  if (lanes == 1 && p.mode != ECMC_MODE_DOMAIN)
+    return fail(ECMC_EINVAL, "one lane per EC needs the domain mode");
   if (!(p.p_swap >= 0.0)) return fail(ECMC_EINVAL, "p_swap must be >= 0");
   const double margin = p.precision == ECMC_PREC_FP32F ? 0.01 * sig : 0.0;
   for (int a = 0; a < 3; ++a)
@@ -463,14 +473,44 @@ ecmc_status ecmc_configure(ecmc_ctx *c, const ecmc_opts *o) {
         if (!(c->L[a] <= 64.0 * sig)) return fail(ECMC_EINVAL, "FP32 screen (serial) needs L <= 64 sigma");
     stage = (int32_t)c->n;
   }
+  if (p.mode == ECMC_MODE_DOMAIN) stage = (stage + 31) / 32 * 32;  // keeps scratch aligned
   if (stage > 65534) return fail(ECMC_EINVAL, "at most 65534 staged beads per tile (serial: beads)");
-  int dev = 0, smem_max = 0;
-  CU(cudaGetDevice(&dev));
-  CU(cudaDeviceGetAttribute(&smem_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
-  const int gmin = 32 / lanes;
-  if ((int64_t)ec_smem_bytes(stage, lanes, gmin) > smem_max)
-    return fail(ECMC_EINVAL, "staging needs %lld bytes of shared memory (max %d)",
-                (long long)ec_smem_bytes(stage, lanes, gmin), smem_max);
+  if (lanes == 1) {
+    // local cell grid over [-h, W + h] with cells no narrower than one free
+    // flight's reach (s_cap + 1.01 sigma) and than b_max
+    const double hg = halo_te + 1e-3 * sig;
+    const double reach = s_cap + sig + 0.01 * sig;
+    const double side_min = (reach > c->b_max * (1.0 + 1e-6) ? reach : c->b_max * (1.0 + 1e-6)) + 2e-3 * sig;
+    int64_t ncl = 1;
+    for (int a = 0; a < 3; ++a) {
+      const double E = c->W[a] + 2.0 * hg;
+      int g = (int)floor(E / side_min);
+      if (g < 1) g = 1;
+      c->lg[a] = g;
+      c->linv[a] = (float)(g / E);
+      ncl *= g;
+    }
+    c->lorg = (float)(-hg);
+    const int64_t ntile = (int64_t)p.tiles[0] * p.tiles[1] * p.tiles[2];
+    const size_t tb = lane_tile_bytes(stage, (int)ncl);
+    const size_t need = tb * (size_t)ntile;
+    if (need > c->scratch_bytes) {
+      cudaFree(c->d_scratch);
+      c->d_scratch = nullptr;
+      c->scratch_bytes = 0;
+      CU(dalloc(&c->d_scratch, need));
+      c->scratch_bytes = need;
+    }
+    c->tile_bytes = (int64_t)tb;
+  } else {
+    int dev = 0, smem_max = 0;
+    CU(cudaGetDevice(&dev));
+    CU(cudaDeviceGetAttribute(&smem_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+    const int gmin = 32 / lanes;
+    if ((int64_t)ec_smem_bytes(stage, lanes, gmin) > smem_max)
+      return fail(ECMC_EINVAL, "staging needs %lld bytes of shared memory (max %d)",
+                  (long long)ec_smem_bytes(stage, lanes, gmin), smem_max);
+  }
   c->opts = p;
   c->s_cap = s_cap;
   c->w = w;
@@ -527,7 +567,8 @@ static cudaError_t timed_ec(ecmc_ctx *c, const ECParams &P, int64_t slot) {
   }
   cudaError_t err = cudaEventRecord(c->kev[slot], c->stream);
   if (err != cudaSuccess) return err;
-  err = launch_ec(P, c->lanes, c->opts.precision == ECMC_PREC_FP32F, c->stream);
+  err = c->lanes == 1 ? launch_ec_lane(P, c->opts.precision == ECMC_PREC_FP32F, c->stream)
+                      : launch_ec(P, c->lanes, c->opts.precision == ECMC_PREC_FP32F, c->stream);
   if (err != cudaSuccess) return err;
   return cudaEventRecord(c->kev[slot + 1], c->stream);
 }
@@ -564,6 +605,13 @@ static ECParams ec_params(const ecmc_ctx *c, uint64_t seed, double ell) {
   P.eps_v = (float)(2e-4 * c->sigma);
   P.eps_d = (float)(1e-3 * c->sigma * c->sigma);
   P.eps_x = (float)(2e-4 * c->sigma);
+  P.scratch = c->d_scratch;
+  P.tile_bytes = c->tile_bytes;
+  for (int a = 0; a < 3; ++a) {
+    P.lg[a] = c->lg[a];
+    P.linv[a] = c->linv[a];
+  }
+  P.lorg = c->lorg;
   P.r = c->d_r;
   P.img = c->d_img;
   P.cr = c->d_cr;

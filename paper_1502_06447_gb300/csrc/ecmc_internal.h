@@ -66,14 +66,22 @@ struct ECParams {
   ecmc_event *log;
   unsigned long long *log_n;
   int64_t log_cap;
+  // one-lane-per-tile kernel: per-tile scratch and its local cell grid
+  unsigned char *scratch;
+  int64_t tile_bytes;
+  int32_t lg[3];
+  float linv[3];
+  float lorg;
 };
 
 // message for ecmc_last_error (ecmc_api.cu)
 void set_last_error(const char *msg);
 
-// launchers (k_ec.cu)
+// launchers (k_ec.cu, k_ec_lane.cu)
 cudaError_t launch_ec(const ECParams &P, int lanes, int fp32f, cudaStream_t s);
 size_t ec_smem_bytes(int stage_cap, int lanes, int groups_per_block);
+cudaError_t launch_ec_lane(const ECParams &P, int fp32f, cudaStream_t s);
+size_t lane_tile_bytes(int stage_cap, int ncell);
 
 // cell list and domain tags (k_cells.cu)
 struct CellParams {

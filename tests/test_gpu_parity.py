@@ -105,7 +105,7 @@ RAGGED = Melt("ragged_15x17x16_N8", (15, 17, 16), 1.05, 8, ell=4.0, seed=0xEC00A
               mode="domain", dir_mode="iso", sweeps=3, D=(3, 4, 3))
 
 
-@pytest.mark.parametrize("lanes", [32, 16, 8])
+@pytest.mark.parametrize("lanes", [32, 16, 8, 1])
 @pytest.mark.parametrize("prec", ["fp64", "fp32f"])
 @pytest.mark.parametrize("m", [small_domain(), RAGGED], ids=lambda m: m.name)
 def test_domain_parity_small(m, prec, lanes):
@@ -125,23 +125,31 @@ def test_domain_parity_small(m, prec, lanes):
         assert obs[k] == v, k
 
 
-def test_domain_two_ecs_per_tile():
+@pytest.mark.parametrize("lanes", [32, 1])
+def test_domain_two_ecs_per_tile(lanes):
     m = small_domain(seed=0xEC00A3)
     o = oracle_system(m, ecs_per_tile=2)
     res = o.run_domain(2, m.ell, digests=True)
-    ctx = gpu_context(m, ecs_per_tile=2)
+    ctx = gpu_context(m, ecs_per_tile=2, lanes=lanes, precision=ecmc.PREC_FP32F)
     ctx.run(m.ell, seed=m.seed, n_sweeps=2)
     dig, _, _ = ctx.records(2 * 27 * 2)
     assert (dig == res["digest"]).all()
     assert_same_state(ctx, o)
 
 
-@pytest.mark.parametrize("prec", ["fp64", "fp32f"])
-def test_domain_parity_c2_full_size(prec):
-    """C2 at full size (4096 x 64 beads, 16^3 tiles): three sweeps identical."""
+@pytest.fixture(scope="module")
+def c2_oracle():
     o = oracle_system(C2)
     res = o.run_domain(3, C2.ell, digests=True)
-    ctx = gpu_context(C2, precision=PRECS[prec])
+    return o, res
+
+
+@pytest.mark.parametrize("lanes", [32, 1])
+@pytest.mark.parametrize("prec", ["fp64", "fp32f"])
+def test_domain_parity_c2_full_size(c2_oracle, prec, lanes):
+    """C2 at full size (4096 x 64 beads, 16^3 tiles): three sweeps identical."""
+    o, res = c2_oracle
+    ctx = gpu_context(C2, precision=PRECS[prec], lanes=lanes)
     ctx.run(C2.ell, seed=C2.seed, n_sweeps=3)
     dig, lift, ev = ctx.records(3 * 4096)
     assert (dig == res["digest"]).all(), np.nonzero(dig != res["digest"])[0][:5]
@@ -163,12 +171,13 @@ def test_run_split_equals_one_run():
 
 
 # ------------------------------------------------------------------ swap
+@pytest.mark.parametrize("lanes", [32, 1])
 @pytest.mark.parametrize("p_swap", [0.5, 1.0])
-def test_swap_parity_domain(p_swap):
+def test_swap_parity_domain(p_swap, lanes):
     m = small_domain(p_swap=p_swap, seed=0xEC00A4, ell=6.0)
     o = oracle_system(m)
     res = o.run_domain(3, m.ell, digests=True)
-    ctx = gpu_context(m)
+    ctx = gpu_context(m, lanes=lanes, precision=ecmc.PREC_FP32F)
     ctx.run(m.ell, seed=m.seed, n_sweeps=3)
     dig, _, _ = ctx.records(3 * 27)
     assert (dig == res["digest"]).all()
