@@ -132,7 +132,7 @@ def run_gpu(args, rank, world):
                                           b_max=C5.b_max, jitter=C5.jitter, seed=seed)
         ctx.set_stream(stream.cuda_stream)
         ctx.configure(mode=ecmc.MODE_DOMAIN, dir_mode=ecmc.DIR_ISO, precision=precision,
-                      tiles=TILES, lanes=args.lanes)
+                      tiles=TILES, lanes=args.lanes, ecs_per_tile=args.ecs_per_tile)
         return ctx
 
     ctx = make(ecmc.PREC_FP32F)
@@ -242,7 +242,7 @@ def run_gpu(args, rank, world):
                    "lattice": list(C5.dims), "spacing": C5.spacing, "phi": round(phi, 4),
                    "b_max": C5.b_max, "ell": ELL, "tiles": list(TILES), "directions": "iso",
                    "precision": "fp32 screen + fp64 confirm", "swap_attempts_per_bead_sweep":
-                   SWAP_RATE, "lanes_per_ec": args.lanes,
+                   SWAP_RATE, "lanes_per_ec": args.lanes, "ecs_per_tile": args.ecs_per_tile,
                    "l2": "flushed between steps (256 MB write)",
                    "parallelism": "replicas" if world > 1 else "1 GPU"},
         "ell_sweeps_per_s": (ecs / n_beads) / dev_s,
@@ -324,9 +324,13 @@ def main():
     ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
     ap.add_argument("--workload", default="c5", choices=sorted(WORKLOADS),
                     help="c5: the 1e6-bead melt (default); c2/c3: smaller melts")
+    ap.add_argument("--tiles", type=int, default=0, help="tiles per axis (0: workload default)")
+    ap.add_argument("--ecs-per-tile", type=int, default=1)
     args = ap.parse_args()
     global C5, ELL, TILES
     C5, TILES = WORKLOADS[args.workload]
+    if args.tiles:
+        TILES = (args.tiles,) * 3
     ELL = C5.ell
     rank = int(os.environ.get("RANK", 0))
     world = int(os.environ.get("WORLD_SIZE", 1))

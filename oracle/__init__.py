@@ -8,8 +8,9 @@ it.  It shares no code with the CUDA library (own Philox4x64-10, own geometry,
 own cell list) and neither side imports the other.
 
 The arithmetic lives in ``ecmc_oracle.c`` (compiled with
-``-O2 -ffp-contract=off``: every FP64 expression evaluated as written, no
-fused multiply-add).  This module is ctypes marshalling only.
+``-O2 -ffp-contract=off``: every FP64 expression evaluated as written; the
+only fused multiply-adds are explicit C99 ``fma`` calls, one rounding each).
+This module is ctypes marshalling only.
 
 Functions and the passage each follows:
   run_serial / run_domain   EC move, Sec. II (four-step rule, min over
@@ -46,7 +47,7 @@ OUT_NAMES = ("end", "pass", "wall", "hs_lift", "hs_reflect", "te_lift",
 
 
 def build(force: bool = False) -> str:
-    """Compile the oracle with gcc (no fused multiply-add, IEEE FP64)."""
+    """Compile the oracle with gcc (IEEE FP64, no implicit contraction)."""
     newest = max(os.path.getmtime(p) for p in _SRC + _HDR)
     if force or not os.path.exists(_SO) or os.path.getmtime(_SO) < newest:
         tmp = _SO + ".%d.tmp" % os.getpid()

@@ -25,7 +25,9 @@
  * and are written out at each place below.
  *
  * Compiled with -O2 -ffp-contract=off: every FP64 expression is evaluated
- * exactly as written, in IEEE round-to-nearest, no fused multiply-add.
+ * exactly as written, in IEEE round-to-nearest; multiply-adds are fused only
+ * where written as fma() (C99, one rounding): the dot products and squared
+ * lengths of the event geometry, the position update and the reflection.
  */
 #include <math.h>
 #include <stdint.h>
@@ -99,7 +101,7 @@ static double minimg(double d, double L) {
 
 /* r += x v on one axis, then back into [0,L) with the image counter */
 static void advance(double *r, int32_t *img, double x, double v, double L) {
-  double y = *r + x * v;
+  double y = fma(x, v, *r);
   if (y >= L) {
     y -= L;
     *img += 1;
@@ -242,12 +244,12 @@ static double hs_dist(const ctx_t *c, int64_t i, int64_t k, const double v[3],
   double d0 = minimg(c->r[3 * i + 0] - c->r[3 * k + 0], L[0]);
   double d1 = minimg(c->r[3 * i + 1] - c->r[3 * k + 1], L[1]);
   double d2 = minimg(c->r[3 * i + 2] - c->r[3 * k + 2], L[2]);
-  double dv = d0 * v[0] + d1 * v[1] + d2 * v[2];
+  double dv = fma(d2, v[2], fma(d1, v[1], d0 * v[0]));
   *dv_out = dv;
   if (!(dv < 0.0)) return -1.0;
-  double dd = d0 * d0 + d1 * d1 + d2 * d2;
+  double dd = fma(d2, d2, fma(d1, d1, d0 * d0));
   double sig2 = c->P.sigma * c->P.sigma;
-  double disc = sig2 - (dd - dv * dv);
+  double disc = sig2 - fma(-dv, dv, dd);
   if (!(disc > 0.0)) return -1.0;
   double x = -dv - sqrt(disc);
   if (x < 0.0) x = 0.0;
@@ -262,11 +264,11 @@ static double te_dist(const ctx_t *c, int64_t i, int64_t j, const double v[3],
   double d0 = minimg(c->r[3 * i + 0] - c->r[3 * j + 0], L[0]);
   double d1 = minimg(c->r[3 * i + 1] - c->r[3 * j + 1], L[1]);
   double d2 = minimg(c->r[3 * i + 2] - c->r[3 * j + 2], L[2]);
-  double dv = d0 * v[0] + d1 * v[1] + d2 * v[2];
+  double dv = fma(d2, v[2], fma(d1, v[1], d0 * v[0]));
   *dv_out = dv;
-  double dd = d0 * d0 + d1 * d1 + d2 * d2;
+  double dd = fma(d2, d2, fma(d1, d1, d0 * d0));
   double b2 = c->P.b_max * c->P.b_max;
-  double rad = b2 - (dd - dv * dv);
+  double rad = b2 - fma(-dv, dv, dd);
   if (rad < 0.0) rad = 0.0;
   double x = -dv + sqrt(rad);
   if (x < 0.0) x = 0.0;
@@ -323,12 +325,12 @@ static void fnv(uint64_t *h, uint64_t w) {
 
 /* reflect v at the plane normal to d (Fig. 2c): v' = v - (2 v.d / d.d) d */
 static void reflect(double v[3], double d0, double d1, double d2) {
-  double dd = d0 * d0 + d1 * d1 + d2 * d2;
-  double vd = v[0] * d0 + v[1] * d1 + v[2] * d2;
+  double dd = fma(d2, d2, fma(d1, d1, d0 * d0));
+  double vd = fma(v[2], d2, fma(v[1], d1, v[0] * d0));
   double t = (2.0 * vd) / dd;
-  v[0] = v[0] - t * d0;
-  v[1] = v[1] - t * d1;
-  v[2] = v[2] - t * d2;
+  v[0] = fma(-t, d0, v[0]);
+  v[1] = fma(-t, d1, v[1]);
+  v[2] = fma(-t, d2, v[2]);
 }
 
 /* swap test (Sec. II.D): with pivot i and the touched bead k exchanged,
@@ -339,7 +341,7 @@ static int bond_ok(const ctx_t *c, int64_t a, const double *pa, int64_t b,
   double d0 = minimg(pa[0] - pb[0], L[0]);
   double d1 = minimg(pa[1] - pb[1], L[1]);
   double d2 = minimg(pa[2] - pb[2], L[2]);
-  double dd = d0 * d0 + d1 * d1 + d2 * d2;
+  double dd = fma(d2, d2, fma(d1, d1, d0 * d0));
   (void)a;
   (void)b;
   return dd <= c->P.b_max * c->P.b_max;

@@ -58,6 +58,7 @@ struct ecmc_ctx {
   double cs[3] = {1, 1, 1};
   int64_t ncell = 1;
   int32_t stage_cap = 0;
+  int32_t m_cap = 0;
   int32_t lanes = 32;
   // one-lane-per-tile kernel: per-tile scratch and local grid
   unsigned char *d_scratch = nullptr;
@@ -436,8 +437,8 @@ ecmc_status ecmc_configure(ecmc_ctx *c, const ecmc_opts *o) {
   const double w = p.joint > 0 ? p.joint : c->b_max;
   if (!(w >= c->b_max)) return fail(ECMC_EINVAL, "joint width must be >= b_max");
   const int lanes = p.lanes ? p.lanes : 32;
-  if (lanes != 32 && lanes != 16 && lanes != 8 && lanes != 1)
-    return fail(ECMC_EINVAL, "lanes must be 1, 8, 16 or 32");
+  if (lanes != 32 && lanes != 16 && lanes != 8 && lanes != 4 && lanes != 1)
+    return fail(ECMC_EINVAL, "lanes must be 1, 4, 8, 16 or 32");
   if (lanes == 1 && p.mode != ECMC_MODE_DOMAIN)
     return fail(ECMC_EINVAL, "one lane per EC needs the domain mode");
   if (!(p.p_swap >= 0.0)) return fail(ECMC_EINVAL, "p_swap must be >= 0");
@@ -447,6 +448,7 @@ ecmc_status ecmc_configure(ecmc_ctx *c, const ecmc_opts *o) {
   const double halo_hs = sig * (1.0 + 1e-6);
   const double halo_te = (c->b_max > sig ? c->b_max : sig) * (1.0 + 1e-6);
   int32_t stage = p.stage_cap;
+  int32_t mcap = 0;
   if (p.mode == ECMC_MODE_DOMAIN) {
     for (int a = 0; a < 3; ++a) {
       if (p.tiles[a] < 3) return fail(ECMC_EINVAL, "tiles per axis must be >= 3");
@@ -467,21 +469,28 @@ ecmc_status ecmc_configure(ecmc_ctx *c, const ecmc_opts *o) {
       stage = (int32_t)(rho * vol * 1.3 + 32);
       stage = (stage + 31) / 32 * 32;
     }
+    {
+      const double rho = (double)c->n / (c->L[0] * c->L[1] * c->L[2]);
+      mcap = (int32_t)(rho * c->W[0] * c->W[1] * c->W[2] * 1.3 + 32);
+      mcap = (mcap + 31) / 32 * 32;
+    }
   } else {
     if (p.precision == ECMC_PREC_FP32F)
       for (int a = 0; a < 3; ++a)
         if (!(c->L[a] <= 64.0 * sig)) return fail(ECMC_EINVAL, "FP32 screen (serial) needs L <= 64 sigma");
     stage = (int32_t)c->n;
   }
-  if (p.mode == ECMC_MODE_DOMAIN) stage = (stage + 31) / 32 * 32;  // keeps scratch aligned
+  stage = (stage + 31) / 32 * 32;  // keeps the staging layouts 16-byte aligned
   if (stage > 65534) return fail(ECMC_EINVAL, "at most 65534 staged beads per tile (serial: beads)");
-  if (lanes == 1) {
-    // local cell grid over [-h, W + h] with cells no narrower than one free
-    // flight's reach (s_cap + 1.01 sigma) and than b_max
+  int64_t ncl = 0;
+  if (p.mode == ECMC_MODE_DOMAIN) {
+    // local cell grid of a tile over [-h, W + h] with cells no narrower than
+    // one free flight's reach (s_cap + 1.01 sigma) and than b_max
     const double hg = halo_te + 1e-3 * sig;
     const double reach = s_cap + sig + 0.01 * sig;
-    const double side_min = (reach > c->b_max * (1.0 + 1e-6) ? reach : c->b_max * (1.0 + 1e-6)) + 2e-3 * sig;
-    int64_t ncl = 1;
+    const double bm = c->b_max * (1.0 + 1e-6);
+    const double side_min = (reach > bm ? reach : bm) + 2e-3 * sig;
+    ncl = 1;
     for (int a = 0; a < 3; ++a) {
       const double E = c->W[a] + 2.0 * hg;
       int g = (int)floor(E / side_min);
@@ -491,6 +500,8 @@ ecmc_status ecmc_configure(ecmc_ctx *c, const ecmc_opts *o) {
       ncl *= g;
     }
     c->lorg = (float)(-hg);
+  }
+  if (lanes == 1) {
     const int64_t ntile = (int64_t)p.tiles[0] * p.tiles[1] * p.tiles[2];
     const size_t tb = lane_tile_bytes(stage, (int)ncl);
     const size_t need = tb * (size_t)ntile;
@@ -507,9 +518,12 @@ ecmc_status ecmc_configure(ecmc_ctx *c, const ecmc_opts *o) {
     CU(cudaGetDevice(&dev));
     CU(cudaDeviceGetAttribute(&smem_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
     const int gmin = 32 / lanes;
-    if ((int64_t)ec_smem_bytes(stage, lanes, gmin) > smem_max)
+    if (mcap > stage) mcap = stage;
+    const int M = (p.precision == ECMC_PREC_FP32F && p.mode == ECMC_MODE_DOMAIN) ? mcap : stage;
+    const size_t need = ec_smem_bytes(stage, M, (int)ncl, gmin);
+    if ((int64_t)need > smem_max)
       return fail(ECMC_EINVAL, "staging needs %lld bytes of shared memory (max %d)",
-                  (long long)ec_smem_bytes(stage, lanes, gmin), smem_max);
+                  (long long)need, smem_max);
   }
   c->opts = p;
   c->s_cap = s_cap;
@@ -517,6 +531,7 @@ ecmc_status ecmc_configure(ecmc_ctx *c, const ecmc_opts *o) {
   c->halo_hs = halo_hs;
   c->halo_te = halo_te;
   c->stage_cap = stage;
+  c->m_cap = mcap > stage ? stage : mcap;
   c->lanes = lanes;
   c->event_cap = p.event_cap > 0 ? p.event_cap : 10000000;
   c->ecs_per_tile = p.ecs_per_tile > 0 ? p.ecs_per_tile : 1;
@@ -600,6 +615,7 @@ static ECParams ec_params(const ecmc_ctx *c, uint64_t seed, double ell) {
   P.p_swap = c->opts.p_swap;
   P.dir_mode = c->opts.dir_mode;
   P.stage_cap = c->stage_cap;
+  P.m_cap = c->m_cap;
   // FP32 screen margins for tile-local coordinates below 64 sigma (the
   // rounding errors they cover are at most ~1/14 of these)
   P.eps_v = (float)(2e-4 * c->sigma);

@@ -1,9 +1,10 @@
-// Device/host primitives of the EC library: counter-based random numbers and
-// the FP64 geometry of one event (arXiv:1502.06447, Sec. II, Eq. 1).
+// Device/host primitives of the EC library: counter-based random numbers,
+// the minimum image, the candidate kinds and the event digest.  The event
+// geometry itself (arXiv:1502.06447, Sec. II, Eq. 1) lives in the kernels.
 //
-// Every FP64 expression here is evaluated as written (the library is built
-// with -fmad=false), so the event sequence is a pure function of the input
-// state and the Philox key.
+// Every FP64 expression is evaluated as written (the library is built with
+// -fmad=false; fused multiply-adds only where written as __fma_rn), so the
+// event sequence is a pure function of the input state and the Philox key.
 #pragma once
 #include <stdint.h>
 
@@ -85,66 +86,9 @@ ECMC_HD double wrap_d(double d, double L, double half) {
   return d;
 }
 
-// one axis of r += x v, back into [0, L) with the image counter; returns the
-// image change (-1, 0, +1)
-ECMC_HD int step_axis(double &r, double x, double v, double L) {
-  double y = r + x * v;
-  int di = 0;
-  if (y >= L) {
-    y = y - L;
-    di = 1;
-  } else if (y < 0.0) {
-    y = y + L;
-    di = -1;
-    if (y >= L) {  // a tiny negative plus L rounded up to L
-      y = 0.0;
-      di = 0;
-    }
-  }
-  r = y;
-  return di;
-}
-
 // Candidate kinds in tie-break order: an exact tie in x goes to the smaller
 // kind, then to the smaller partner id.
 enum : int { KIND_END = 0, KIND_PASS = 1, KIND_WALL = 2, KIND_HS = 3, KIND_TETHER = 4 };
-
-// Hard-sphere contact (Eq. 1): pivot at p moving along v touches the bead at
-// q when |p + x v - q| = sigma.  d = p - q (minimum image).  Returns x >= 0,
-// or -1 when the path misses or leads away.
-ECMC_HD double contact_x(double d0, double d1, double d2, double v0, double v1,
-                         double v2, double sig2) {
-  const double dv = d0 * v0 + d1 * v1 + d2 * v2;
-  if (!(dv < 0.0)) return -1.0;
-  const double dd = d0 * d0 + d1 * d1 + d2 * d2;
-  const double disc = sig2 - (dd - dv * dv);
-  if (!(disc > 0.0)) return -1.0;
-  double x = -dv - sqrt(disc);
-  return x < 0.0 ? 0.0 : x;
-}
-
-// Tether limit: the bond p - q reaches b_max after the free flight x (the
-// larger root; the bond may shorten first).
-ECMC_HD double tether_x(double d0, double d1, double d2, double v0, double v1,
-                        double v2, double b2) {
-  const double dv = d0 * v0 + d1 * v1 + d2 * v2;
-  const double dd = d0 * d0 + d1 * d1 + d2 * d2;
-  double rad = b2 - (dd - dv * dv);
-  if (rad < 0.0) rad = 0.0;
-  double x = -dv + sqrt(rad);
-  return x < 0.0 ? 0.0 : x;
-}
-
-// v <- v - 2 (v.n) n with n = d/|d| (Fig. 2c: reflection at the plane normal
-// to the bond / contact line)
-ECMC_HD void mirror(double &v0, double &v1, double &v2, double d0, double d1, double d2) {
-  const double len = sqrt(d0 * d0 + d1 * d1 + d2 * d2);
-  const double n0 = d0 / len, n1 = d1 / len, n2 = d2 / len;
-  const double t = 2.0 * (v0 * n0 + v1 * n1 + v2 * n2);
-  v0 = v0 - t * n0;
-  v1 = v1 - t * n1;
-  v2 = v2 - t * n2;
-}
 
 ECMC_HD void fnv_mix(uint64_t &h, uint64_t w) {
   h ^= w;

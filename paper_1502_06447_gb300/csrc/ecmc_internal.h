@@ -44,6 +44,7 @@ struct ECParams {
   double p_swap;
   int32_t dir_mode;
   int32_t stage_cap;
+  int32_t m_cap;        // motile slots with FP64 in shared memory (screened domain form)
   int32_t n_units;      // tiles (domain) or 1 (serial)
   // FP32 screen margins (units of sigma, sigma^2)
   float eps_v, eps_d, eps_x;
@@ -79,7 +80,7 @@ void set_last_error(const char *msg);
 
 // launchers (k_ec.cu, k_ec_lane.cu)
 cudaError_t launch_ec(const ECParams &P, int lanes, int fp32f, cudaStream_t s);
-size_t ec_smem_bytes(int stage_cap, int lanes, int groups_per_block);
+size_t ec_smem_bytes(int stage_cap, int motile_cap, int ncell, int groups_per_block);
 cudaError_t launch_ec_lane(const ECParams &P, int fp32f, cudaStream_t s);
 size_t lane_tile_bytes(int stage_cap, int ncell);
 

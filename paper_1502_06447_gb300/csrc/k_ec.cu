@@ -1,7 +1,7 @@
 // Event-chain kernels (arXiv:1502.06447, Sec. II: EC move; Sec. II.B:
 // tile-joint decomposition with reflections; Sec. II.D: swap move).
 //
-// One group of G lanes (G = 32, 16 or 8) runs the ECs of one tile; the
+// One group of G lanes (G = 32, 16, 8 or 4) runs the ECs of one tile; the
 // 32/G groups of a warp advance in lockstep, one event per iteration, so
 // every warp instruction of the serial part serves all of them.
 //
@@ -13,7 +13,11 @@
 // The start bead of an EC is then slot below(u, m); bond partners are found
 // by binary search on the ids.  Positions are the wrapped FP64 coordinates
 // of the global state, so every candidate is evaluated with exactly the
-// arithmetic of the plain definition.
+// arithmetic of the plain definition.  In the domain mode the hard-sphere
+// slots [0, m + j1) also sit in a local cell grid of side >= one free
+// flight's reach (s_cap + 1.01 sigma), kept current as beads move, and an
+// event scans only the 27 cells around the pivot; the serial mode scans all
+// beads.
 //
 // GB300's FP64 pipe is the scarce resource, so FP64 comparisons are done on
 // the bit patterns with integer instructions (same results), and in the
@@ -57,7 +61,7 @@ __device__ __forceinline__ double wrap_i(double d, double L, uint64_t hbits) {
 
 // r += x v on one axis, back into [0, L); returns the image change
 __device__ __forceinline__ int step_i(double &r, double x, double v, double L) {
-  double y = r + x * v;
+  double y = __fma_rn(x, v, r);
   int di = 0;
   if (ge_pos(y, L)) {
     y = y - L;
@@ -79,10 +83,10 @@ __device__ __forceinline__ int step_i(double &r, double x, double v, double L) {
 // a contact candidate misses; dv = d.v.
 __device__ __forceinline__ double quad_x(bool tether, double d0, double d1, double d2, double v0,
                                          double v1, double v2, double R2, double &dv) {
-  dv = d0 * v0 + d1 * v1 + d2 * v2;
+  dv = __fma_rn(d2, v2, __fma_rn(d1, v1, d0 * v0));
   if (!tether && !neg(dv)) return -1.0;
-  const double dd = d0 * d0 + d1 * d1 + d2 * d2;
-  double rad = R2 - (dd - dv * dv);
+  const double dd = __fma_rn(d2, d2, __fma_rn(d1, d1, d0 * d0));
+  double rad = R2 - __fma_rn(-dv, dv, dd);
   if (tether) {
     if (neg(rad)) rad = 0.0;
   } else if (!posv(rad)) {
@@ -95,12 +99,12 @@ __device__ __forceinline__ double quad_x(bool tether, double d0, double d1, doub
 // v <- v - (2 v.d / d.d) d: reflection at the plane normal to d (Fig. 2c)
 __device__ __forceinline__ void mirror2(double &v0, double &v1, double &v2, double d0, double d1,
                                         double d2) {
-  const double dd = d0 * d0 + d1 * d1 + d2 * d2;
-  const double vd = v0 * d0 + v1 * d1 + v2 * d2;
+  const double dd = __fma_rn(d2, d2, __fma_rn(d1, d1, d0 * d0));
+  const double vd = __fma_rn(v2, d2, __fma_rn(v1, d1, v0 * d0));
   const double t = (2.0 * vd) / dd;
-  v0 = v0 - t * d0;
-  v1 = v1 - t * d1;
-  v2 = v2 - t * d2;
+  v0 = __fma_rn(-t, d0, v0);
+  v1 = __fma_rn(-t, d1, v1);
+  v2 = __fma_rn(-t, d2, v2);
 }
 
 // candidate key: kind (3 bits) | partner id (41 bits) | slot (20 bits).
@@ -145,30 +149,44 @@ __device__ __forceinline__ float wrapf(float d, float L) {
 }
 
 // ---------------------------------------------------------------- staging
-// per slot: FP64 position (24 B), FP32 shadow (12 B), id (4 B), bond partner
-// slots packed as two 16-bit fields (4 B; 0xFFFF = none)
-constexpr int SLOT_BYTES = 44;
+// Shared memory of one group: FP64 positions and bond-partner words of the
+// first M slots (M = the motile capacity in the screened domain form, where
+// joint beads' FP64 positions, static during a sweep, are read from the
+// global array when a confirmation needs them; M = S otherwise); FP32 shadow
+// (12 B) and id (4 B) of all S slots; the local cell grid (16 B per cell:
+// count + 7 slots); the overflow list of beads whose cell was full; a header.
+constexpr int CELL_CAP = 7;
+constexpr int OVF_CAP = 64;
 constexpr int HDR_BYTES = 32;
 
 struct Stage {
-  double *px, *py, *pz;
-  float *fx, *fy, *fz;
-  int *id;
-  unsigned *nb;
-  int *hdr;  // [2] staged count, [3] overflow
+  double *px, *py, *pz;  // [M]
+  unsigned *nb;          // [M] bond partner slots, 16 + 16 bits (0xFFFF = none)
+  float *fx, *fy, *fz;   // [S]
+  int *id;               // [S]
+  uint4 *cell;           // [NC]
+  unsigned short *ovf;   // [OVF_CAP]
+  int *hdr;              // [2] staged count, [3] overflow, [4] overflow-list length
 };
 
-__device__ __forceinline__ Stage carve(unsigned char *base, int S) {
+__host__ __device__ __forceinline__ size_t group_bytes(int S, int M, int NC) {
+  return (size_t)M * 28 + (size_t)S * 16 + (size_t)NC * 16 + OVF_CAP * 2 + HDR_BYTES;
+}
+
+// S and M are multiples of 32, so every array starts 16-byte aligned
+__device__ __forceinline__ Stage carve(unsigned char *base, int S, int M, int NC) {
   Stage s;
   s.px = (double *)base;
-  s.py = s.px + S;
-  s.pz = s.py + S;
-  s.fx = (float *)(s.pz + S);
+  s.py = s.px + M;
+  s.pz = s.py + M;
+  s.nb = (unsigned *)(s.pz + M);
+  s.fx = (float *)(s.nb + M);
   s.fy = s.fx + S;
   s.fz = s.fy + S;
   s.id = (int *)(s.fz + S);
-  s.nb = (unsigned *)(s.id + S);
-  s.hdr = (int *)(s.nb + S);
+  s.cell = (uint4 *)(s.id + S);
+  s.ovf = (unsigned short *)(s.cell + NC);
+  s.hdr = (int *)(s.ovf + OVF_CAP);
   return s;
 }
 
@@ -192,6 +210,147 @@ __device__ __forceinline__ int find_id(const int *ids, int lo, int hi, int id) {
 
 __device__ __forceinline__ void set_status(int *st, int code) { atomicCAS(st, 0, code); }
 
+// ---------------------------------------------------------------- local grid
+__device__ __forceinline__ int cell_count(const uint4 &c) { return (int)(c.x & 0xFFFF); }
+__device__ __forceinline__ int cell_slot(const uint4 &c, int i) {
+  const unsigned w = i == 0 ? (c.x >> 16)
+                   : i == 1 ? (c.y & 0xFFFF)
+                   : i == 2 ? (c.y >> 16)
+                   : i == 3 ? (c.z & 0xFFFF)
+                   : i == 4 ? (c.z >> 16)
+                   : i == 5 ? (c.w & 0xFFFF)
+                            : (c.w >> 16);
+  return (int)(w & 0xFFFF);
+}
+__device__ __forceinline__ void cell_set(uint4 &c, int i, int s) {
+  const unsigned v = (unsigned)s & 0xFFFF;
+  if (i == 0) c.x = (c.x & 0xFFFF) | (v << 16);
+  else if (i == 1) c.y = (c.y & 0xFFFF0000u) | v;
+  else if (i == 2) c.y = (c.y & 0xFFFF) | (v << 16);
+  else if (i == 3) c.z = (c.z & 0xFFFF0000u) | v;
+  else if (i == 4) c.z = (c.z & 0xFFFF) | (v << 16);
+  else if (i == 5) c.w = (c.w & 0xFFFF0000u) | v;
+  else c.w = (c.w & 0xFFFF) | (v << 16);
+}
+
+struct LGrid {
+  int g0, g1, g2;
+  float org, inv0, inv1, inv2;
+};
+
+__device__ __forceinline__ int lcell(const LGrid &L, float f0, float f1, float f2, int &c0,
+                                     int &c1, int &c2) {
+  c0 = (int)((f0 - L.org) * L.inv0);
+  c1 = (int)((f1 - L.org) * L.inv1);
+  c2 = (int)((f2 - L.org) * L.inv2);
+  c0 = c0 < 0 ? 0 : (c0 >= L.g0 ? L.g0 - 1 : c0);
+  c1 = c1 < 0 ? 0 : (c1 >= L.g1 ? L.g1 - 1 : c1);
+  c2 = c2 < 0 ? 0 : (c2 >= L.g2 ? L.g2 - 1 : c2);
+  return (c2 * L.g1 + c1) * L.g0 + c0;
+}
+
+// single-writer updates (one lane of the group)
+__device__ __forceinline__ bool lcell_insert(const Stage &st, int ci, int slot) {
+  uint4 c = st.cell[ci];
+  const int n = cell_count(c);
+  if (n < CELL_CAP) {
+    cell_set(c, n, slot);
+    c.x = (c.x & 0xFFFF0000u) | (unsigned)(n + 1);
+    st.cell[ci] = c;
+    return true;
+  }
+  const int k = st.hdr[4];
+  if (k >= OVF_CAP) return false;
+  st.ovf[k] = (unsigned short)slot;
+  st.hdr[4] = k + 1;
+  return true;
+}
+
+__device__ __forceinline__ void lcell_remove(const Stage &st, int ci, int slot) {
+  uint4 c = st.cell[ci];
+  const int n = cell_count(c);
+  for (int i = 0; i < n; ++i) {
+    if (cell_slot(c, i) == slot) {
+      cell_set(c, i, cell_slot(c, n - 1));
+      c.x = (c.x & 0xFFFF0000u) | (unsigned)(n - 1);
+      st.cell[ci] = c;
+      return;
+    }
+  }
+  const int k = st.hdr[4];
+  for (int i = 0; i < k; ++i) {
+    if (st.ovf[i] == slot) {
+      st.ovf[i] = st.ovf[k - 1];
+      st.hdr[4] = k - 1;
+      return;
+    }
+  }
+}
+
+// FP32 screen of one hard-sphere obstacle k for the pivot shadow pf moving
+// along vf: updates the upper bound ubl and keeps the slot when its lower
+// bound can reach it (two kept per lane, more -> ovf)
+struct Screen {
+  float sig2f, eps_v, eps_d, near2;
+};
+
+__device__ __forceinline__ void screen_hs(const Screen &Z, float d0, float d1, float d2, float vf0,
+                                          float vf1, float vf2, int k, float &ubl, int &ks0,
+                                          float &kl0, int &ks1, float &kl1, bool &ovf) {
+  const float dd = __fmaf_rn(d2, d2, __fmaf_rn(d1, d1, d0 * d0));
+  if (dd > Z.near2) return;
+  const float dv = __fmaf_rn(d2, vf2, __fmaf_rn(d1, vf1, d0 * vf0));
+  const float disc = Z.sig2f - (dd - dv * dv);
+  if (!(dv < Z.eps_v && disc > -Z.eps_d)) return;
+  if (dv < -Z.eps_v && disc > Z.eps_d)
+    ubl = fminf(ubl, fmaxf(0.f, -dv + Z.eps_v - sqrtf(disc - Z.eps_d) * 0.9999998f) + 1e-6f);
+  const float lb = -dv - Z.eps_v - sqrtf(disc + Z.eps_d) * 1.0000002f;
+  if (lb > ubl) return;
+  const float INF = __int_as_float(0x7f800000);
+  if (kl0 > ubl) {
+    ks0 = -1;
+    kl0 = INF;
+  }
+  if (kl1 > ubl) {
+    ks1 = -1;
+    kl1 = INF;
+  }
+  if (ks0 < 0) {
+    ks0 = k;
+    kl0 = lb;
+  } else if (ks1 < 0) {
+    ks1 = k;
+    kl1 = lb;
+  } else {
+    ovf = true;
+  }
+}
+
+__device__ __forceinline__ float screen_lb(const Screen &Z, float d0, float d1, float d2,
+                                           float vf0, float vf1, float vf2, bool &possible) {
+  const float dd = __fmaf_rn(d2, d2, __fmaf_rn(d1, d1, d0 * d0));
+  const float dv = __fmaf_rn(d2, vf2, __fmaf_rn(d1, vf1, d0 * vf0));
+  const float disc = Z.sig2f - (dd - dv * dv);
+  possible = dd <= Z.near2 && dv < Z.eps_v && disc > -Z.eps_d;
+  return -dv - Z.eps_v - sqrtf(fmaxf(disc + Z.eps_d, 0.f)) * 1.0000002f;
+}
+
+// FP64 position of staged slot k: shared memory for the first M slots,
+// otherwise (a joint bead, static this sweep) the global position array
+__device__ __forceinline__ void pos64(const Stage &st, const ECParams &P, int k, bool in_smem,
+                                      double &x, double &y, double &z) {
+  if (in_smem) {
+    x = st.px[k];
+    y = st.py[k];
+    z = st.pz[k];
+  } else {
+    const int64_t b = st.id[k];
+    x = P.r[3 * b];
+    y = P.r[3 * b + 1];
+    z = P.r[3 * b + 2];
+  }
+}
+
 template <int G, bool F32>
 __global__ void __launch_bounds__(128) ec_kernel(const ECParams P) {
   extern __shared__ __align__(16) unsigned char smem[];
@@ -202,9 +361,19 @@ __global__ void __launch_bounds__(128) ec_kernel(const ECParams P) {
   const int gpb = blockDim.x / G;
   const int unit = blockIdx.x * gpb + gib;
   const int S = P.stage_cap;
-  Stage st = carve(smem + (size_t)gib * ((size_t)S * SLOT_BYTES + HDR_BYTES), S);
+  const int NC = P.domain ? P.lg[0] * P.lg[1] * P.lg[2] : 0;
+  const int M = (F32 && P.domain) ? P.m_cap : S;
+  Stage st = carve(smem + (size_t)gib * group_bytes(S, M, NC), S, M, NC);
   bool live = unit < P.n_units;
   const uint64_t hb0 = dbits(P.half[0]), hb1 = dbits(P.half[1]), hb2 = dbits(P.half[2]);
+  LGrid LG;
+  LG.g0 = P.lg[0];
+  LG.g1 = P.lg[1];
+  LG.g2 = P.lg[2];
+  LG.org = P.lorg;
+  LG.inv0 = P.linv[0];
+  LG.inv1 = P.linv[1];
+  LG.inv2 = P.linv[2];
 
   // tile geometry (domain) or the whole box (serial); corner = shift + k T
   int tk[3] = {0, 0, 0};
@@ -223,6 +392,7 @@ __global__ void __launch_bounds__(128) ec_kernel(const ECParams P) {
   if (gl == 0) {
     st.hdr[2] = 0;
     st.hdr[3] = 0;
+    st.hdr[4] = 0;
   }
   __syncwarp();
   int m = 0, j1 = 0, ns = 0;
@@ -321,9 +491,11 @@ __global__ void __launch_bounds__(128) ec_kernel(const ECParams P) {
         cnt_cat0 += (cat == 0);
         cnt_cat1 += (cat == 1);
         const int j = e.x;
-        st.px[rank] = P.cr[3 * (int64_t)j];
-        st.py[rank] = P.cr[3 * (int64_t)j + 1];
-        st.pz[rank] = P.cr[3 * (int64_t)j + 2];
+        if (rank < M) {
+          st.px[rank] = P.cr[3 * (int64_t)j];
+          st.py[rank] = P.cr[3 * (int64_t)j + 1];
+          st.pz[rank] = P.cr[3 * (int64_t)j + 2];
+        }
         st.id[rank] = e.y & ((1 << 29) - 1);
       }
     }
@@ -335,13 +507,20 @@ __global__ void __launch_bounds__(128) ec_kernel(const ECParams P) {
     }
     m = cnt_cat0;
     j1 = cnt_cat1;
-    // pass 3: shadows and bond partners of motile beads
+    if (m > M) {  // more motile beads than the FP64 staging capacity
+      if (gl == 0) set_status(P.status, DEV_CAPACITY);
+      live = false;
+    }
+    // pass 3: shadows and bond partners of motile beads; empty cells
+    for (int i = gl; i < NC; i += G) st.cell[i] = make_uint4(0, 0, 0, 0);
     for (int s0 = 0; s0 < ns_max; s0 += G) {
       const int s = s0 + gl;
-      if (s < ns) {
-        st.fx[s] = (float)wrap_d(st.px[s] - corner[0], P.L[0], P.half[0]);
-        st.fy[s] = (float)wrap_d(st.py[s] - corner[1], P.L[1], P.half[1]);
-        st.fz[s] = (float)wrap_d(st.pz[s] - corner[2], P.L[2], P.half[2]);
+      if (s < ns && live) {
+        double x, y, z;
+        pos64(st, P, s, s < M, x, y, z);
+        st.fx[s] = (float)wrap_d(x - corner[0], P.L[0], P.half[0]);
+        st.fy[s] = (float)wrap_d(y - corner[1], P.L[1], P.half[1]);
+        st.fz[s] = (float)wrap_d(z - corner[2], P.L[2], P.half[2]);
         int prev = -1, next = -1;
         if (s < m) {
           const int id = st.id[s];
@@ -359,10 +538,23 @@ __global__ void __launch_bounds__(128) ec_kernel(const ECParams P) {
             if (next < 0) set_status(P.status, DEV_TILE);
           }
         }
-        st.nb[s] = nb_pack(prev, next);
+        if (s < M) st.nb[s] = nb_pack(prev, next);
       }
     }
     __syncwarp();
+    // pass 4: the hard-sphere slots into the local grid (one writer)
+    if (gl == 0 && live) {
+      for (int s = 0; s < m + j1; ++s) {
+        int a0, a1, a2;
+        if (!lcell_insert(st, lcell(LG, st.fx[s], st.fy[s], st.fz[s], a0, a1, a2), s)) {
+          set_status(P.status, DEV_CAPACITY);
+          st.hdr[3] = 1;
+          break;
+        }
+      }
+    }
+    __syncwarp();
+    if (st.hdr[3]) live = false;
   }
   if (!live) m = 0;
   const int nhs = m + j1;
@@ -370,11 +562,16 @@ __global__ void __launch_bounds__(128) ec_kernel(const ECParams P) {
 
   // ------------------------------------------------------------ ECs
   const int n_ec = P.ecs_per_tile;
-  const float sig2f = (float)P.sig2;
+  Screen Z;
+  Z.sig2f = (float)P.sig2;
+  Z.eps_v = P.eps_v;
+  Z.eps_d = P.eps_d;
+  {
+    const float reach = (float)(P.s_cap + P.sigma + 0.01 * P.sigma);
+    Z.near2 = reach * reach;
+  }
   const float b2f = (float)P.b2;
   const float eps_v = P.eps_v, eps_d = P.eps_d;
-  const float reach = (float)(P.s_cap + P.sigma + 0.01 * P.sigma);
-  const float near2 = reach * reach;
   const float Lf0 = (float)P.L[0], Lf1 = (float)P.L[1], Lf2 = (float)P.L[2];
   const float Wf0 = (float)P.W[0], Wf1 = (float)P.W[1], Wf2 = (float)P.W[2];
   const float INF = __int_as_float(0x7f800000);
@@ -384,6 +581,7 @@ __global__ void __launch_bounds__(128) ec_kernel(const ECParams P) {
 #pragma unroll
   for (int k = 0; k < ECMC_NEV; ++k) cnt[k] = 0;
   unsigned long long tried = 0, confirmed = 0, nev_all = 0, ecs_done = 0;
+  constexpr int ITEMS = G >= 8 ? 1 : 2;  // special candidates per lane
 
   for (int e = 0; e < n_ec; ++e) {
     bool active = live && m > 0;
@@ -443,45 +641,137 @@ __global__ void __launch_bounds__(128) ec_kernel(const ECParams P) {
       uint64_t bkey = ~0ull;
       double bdv = 0.0;
       const unsigned nbw = active ? st.nb[p] : 0xFFFFFFFFu;
-      if (!F32) {
-        // ---------------- plain FP64: every candidate evaluated exactly
-        if (active) {
-          if (gl == 0) {
-            if (dbits(P.s_cap) < dbits(xrem)) {
-              bx = P.s_cap;
-              bkey = make_key(KIND_PASS, 0, 0);
-            } else {
-              bx = xrem;
-              bkey = make_key(KIND_END, 0, 0);
-            }
-          } else if (gl <= 2) {
-            const int t = gl == 1 ? nb_prev(nbw) : nb_next(nbw);
-            if (t >= 0) {
-              double dv;
-              const double x = quad_x(true, wrap_i(q0 - st.px[t], P.L[0], hb0),
-                                      wrap_i(q1 - st.py[t], P.L[1], hb1),
-                                      wrap_i(q2 - st.pz[t], P.L[2], hb2), v0, v1, v2, P.b2, dv);
+      int pc0 = 0, pc1 = 0, pc2 = 0;
+      if (P.domain) lcell(LG, pf0, pf1, pf2, pc0, pc1, pc2);
+      const int n_ovf = P.domain ? st.hdr[4] : 0;
+      // --------- special candidates: item 0 end/pass, 1-2 tethers, 3-5 walls
+      float ubl = INF;
+      int spk[ITEMS], sps[ITEMS];
+      float spl[ITEMS];
+#pragma unroll
+      for (int r = 0; r < ITEMS; ++r) {
+        spk[r] = -1;
+        sps[r] = -1;
+        spl[r] = INF;
+        const int it = gl + r * G;
+        if (!active || it >= 6) continue;
+        if (it == 0) {
+          if (dbits(P.s_cap) < dbits(xrem)) {
+            bx = P.s_cap;
+            bkey = make_key(KIND_PASS, 0, 0);
+          } else {
+            bx = xrem;
+            bkey = make_key(KIND_END, 0, 0);
+          }
+          if (F32) ubl = fminf(ubl, __double2float_ru(bx));
+        } else if (it <= 2) {
+          const int t = it == 1 ? nb_prev(nbw) : nb_next(nbw);
+          if (t < 0) continue;
+          if (!F32) {
+            double dv;
+            const double x = quad_x(true, wrap_i(q0 - st.px[t], P.L[0], hb0),
+                                    wrap_i(q1 - st.py[t], P.L[1], hb1),
+                                    wrap_i(q2 - st.pz[t], P.L[2], hb2), v0, v1, v2, P.b2, dv);
+            const uint64_t key = make_key(KIND_TETHER, st.id[t], t);
+            if (better(x, key, bx, bkey)) {
               bx = x;
-              bkey = make_key(KIND_TETHER, st.id[t], t);
+              bkey = key;
               bdv = dv;
             }
-          } else if (gl <= 5 && P.domain) {
-            const int a = gl - 3;
-            const double va = a == 0 ? v0 : (a == 1 ? v1 : v2);
-            if (nonzero(va)) {
-              const double qa = a == 0 ? q0 : (a == 1 ? q1 : q2);
-              const double ca = a == 0 ? c0 : (a == 1 ? c1 : c2);
-              const double loc = wrap_i(qa - ca, P.L[a], a == 0 ? hb0 : (a == 1 ? hb1 : hb2));
-              double x = posv(va) ? (P.W[a] - loc) / va : (0.0 - loc) / va;
-              if (neg(x)) x = 0.0;
+          } else {
+            float d0 = pf0 - st.fx[t], d1 = pf1 - st.fy[t], d2 = pf2 - st.fz[t];
+            if (!P.domain) {
+              d0 = wrapf(d0, Lf0);
+              d1 = wrapf(d1, Lf1);
+              d2 = wrapf(d2, Lf2);
+            }
+            const float dd = __fmaf_rn(d2, d2, __fmaf_rn(d1, d1, d0 * d0));
+            const float dv = __fmaf_rn(d2, vf2, __fmaf_rn(d1, vf1, d0 * vf0));
+            const float rad = b2f - (dd - dv * dv);
+            const float lo = -dv - eps_v + sqrtf(fmaxf(rad - eps_d, 0.f)) * 0.9999998f;
+            const float hi = -dv + eps_v + sqrtf(fmaxf(rad + eps_d, 0.f)) * 1.0000002f;
+            spl[r] = fmaxf(lo, 0.f);
+            ubl = fminf(ubl, fmaxf(hi, 0.f) + 1e-6f);
+            spk[r] = KIND_TETHER;
+            sps[r] = t;
+          }
+        } else if (P.domain) {
+          const int a = it - 3;
+          const double va = a == 0 ? v0 : (a == 1 ? v1 : v2);
+          if (!nonzero(va)) continue;
+          if (!F32) {
+            const double qa = a == 0 ? q0 : (a == 1 ? q1 : q2);
+            const double ca = a == 0 ? c0 : (a == 1 ? c1 : c2);
+            const double loc = wrap_i(qa - ca, P.L[a], a == 0 ? hb0 : (a == 1 ? hb1 : hb2));
+            double x = posv(va) ? (P.W[a] - loc) / va : (0.0 - loc) / va;
+            if (neg(x)) x = 0.0;
+            const uint64_t key = make_key(KIND_WALL, a, 0);
+            if (better(x, key, bx, bkey)) {
               bx = x;
-              bkey = make_key(KIND_WALL, a, 0);
+              bkey = key;
+            }
+          } else {
+            const float vfa = a == 0 ? vf0 : (a == 1 ? vf1 : vf2);
+            const float pfa = a == 0 ? pf0 : (a == 1 ? pf1 : pf2);
+            const float Wfa = a == 0 ? Wf0 : (a == 1 ? Wf1 : Wf2);
+            const float dist = posv(va) ? Wfa - pfa : pfa;
+            const float av = fabsf(vfa);
+            if (av > 0.f) {
+              spl[r] = fmaxf(dist - eps_v, 0.f) / (av * 1.000001f);
+              ubl = fminf(ubl, (fmaxf(dist, 0.f) + eps_v) / (av * 0.999999f));
+            } else {
+              spl[r] = 0.f;  // |v_a| below FP32 range: confirm in FP64
+            }
+            spk[r] = KIND_WALL;
+            sps[r] = a;
+          }
+        }
+      }
+      // --------- hard-sphere obstacles
+      int ks0 = -1, ks1 = -1;
+      float kl0 = INF, kl1 = INF;
+      bool kovf = false;
+      if (P.domain) {
+        // the 27 cells around the pivot (item 27: the overflow list)
+        for (int ci = gl; ci < 28; ci += G) {
+          if (!active) break;
+          int n;
+          uint4 cc = make_uint4(0, 0, 0, 0);
+          if (ci == 27) {
+            n = n_ovf;
+          } else {
+            const int x = pc0 + ci % 3 - 1, y = pc1 + (ci / 3) % 3 - 1, z = pc2 + ci / 9 - 1;
+            if (x < 0 || y < 0 || z < 0 || x >= LG.g0 || y >= LG.g1 || z >= LG.g2) continue;
+            cc = st.cell[(z * LG.g1 + y) * LG.g0 + x];
+            n = cell_count(cc);
+          }
+          for (int i = 0; i < n; ++i) {
+            const int k = ci == 27 ? (int)st.ovf[i] : cell_slot(cc, i);
+            if (k == p) continue;
+            if (!F32) {
+              double dv;
+              const double x = quad_x(false, wrap_i(q0 - st.px[k], P.L[0], hb0),
+                                      wrap_i(q1 - st.py[k], P.L[1], hb1),
+                                      wrap_i(q2 - st.pz[k], P.L[2], hb2), v0, v1, v2, P.sig2, dv);
+              if (!neg(x)) {
+                const uint64_t key = make_key(KIND_HS, st.id[k], k);
+                if (better(x, key, bx, bkey)) {
+                  bx = x;
+                  bkey = key;
+                  bdv = dv;
+                }
+              }
+            } else {
+              screen_hs(Z, pf0 - st.fx[k], pf1 - st.fy[k], pf2 - st.fz[k], vf0, vf1, vf2, k, ubl,
+                        ks0, kl0, ks1, kl1, kovf);
             }
           }
         }
+      } else {
         for (int k0 = 0; k0 < nhs_max; k0 += G) {
           const int k = k0 + gl;
-          if (active && k < nhs && k != p) {
+          if (!(active && k < nhs && k != p)) continue;
+          if (!F32) {
             double dv;
             const double x = quad_x(false, wrap_i(q0 - st.px[k], P.L[0], hb0),
                                     wrap_i(q1 - st.py[k], P.L[1], hb1),
@@ -494,137 +784,39 @@ __global__ void __launch_bounds__(128) ec_kernel(const ECParams P) {
                 bdv = dv;
               }
             }
+          } else {
+            screen_hs(Z, wrapf(pf0 - st.fx[k], Lf0), wrapf(pf1 - st.fy[k], Lf1),
+                      wrapf(pf2 - st.fz[k], Lf2), vf0, vf1, vf2, k, ubl, ks0, kl0, ks1, kl1, kovf);
           }
         }
-      } else {
-        // ---------------- FP32 screen, FP64 confirmation
-        float ubl = INF;
-        int sp_kind = -1, sp_slot = -1;  // this lane's tether or wall
-        float sp_lb = INF;
-        if (active) {
-          if (gl == 0) {
-            if (dbits(P.s_cap) < dbits(xrem)) {
-              bx = P.s_cap;
-              bkey = make_key(KIND_PASS, 0, 0);
-            } else {
-              bx = xrem;
-              bkey = make_key(KIND_END, 0, 0);
-            }
-            ubl = __double2float_ru(bx);
-          } else if (gl <= 2) {
-            const int t = gl == 1 ? nb_prev(nbw) : nb_next(nbw);
-            if (t >= 0) {
-              float d0 = pf0 - st.fx[t], d1 = pf1 - st.fy[t], d2 = pf2 - st.fz[t];
-              if (!P.domain) {
-                d0 = wrapf(d0, Lf0);
-                d1 = wrapf(d1, Lf1);
-                d2 = wrapf(d2, Lf2);
-              }
-              const float dd = __fmaf_rn(d2, d2, __fmaf_rn(d1, d1, d0 * d0));
-              const float dv = __fmaf_rn(d2, vf2, __fmaf_rn(d1, vf1, d0 * vf0));
-              const float rad = b2f - (dd - dv * dv);
-              const float lo = -dv - eps_v + sqrtf(fmaxf(rad - eps_d, 0.f)) * 0.9999998f;
-              const float hi = -dv + eps_v + sqrtf(fmaxf(rad + eps_d, 0.f)) * 1.0000002f;
-              sp_lb = fmaxf(lo, 0.f);
-              ubl = fmaxf(hi, 0.f) + 1e-6f;
-              sp_kind = KIND_TETHER;
-              sp_slot = t;
-            }
-          } else if (gl <= 5 && P.domain) {
-            const int a = gl - 3;
-            const double va = a == 0 ? v0 : (a == 1 ? v1 : v2);
-            if (nonzero(va)) {
-              const float vfa = a == 0 ? vf0 : (a == 1 ? vf1 : vf2);
-              const float pfa = a == 0 ? pf0 : (a == 1 ? pf1 : pf2);
-              const float Wfa = a == 0 ? Wf0 : (a == 1 ? Wf1 : Wf2);
-              const float dist = posv(va) ? Wfa - pfa : pfa;
-              const float av = fabsf(vfa);
-              if (av > 0.f) {
-                sp_lb = fmaxf(dist - eps_v, 0.f) / (av * 1.000001f);
-                ubl = (fmaxf(dist, 0.f) + eps_v) / (av * 0.999999f);
-              } else {
-                sp_lb = 0.f;  // |v_a| below FP32 range: confirm in FP64
-              }
-              sp_kind = KIND_WALL;
-              sp_slot = a;
-            }
-          }
-        }
-        // hard-sphere obstacles: bounds, keep up to two possible winners
-        int ks0 = -1, ks1 = -1;
-        float kl0 = INF, kl1 = INF;
-        bool ovf = false;
-        for (int k0 = 0; k0 < nhs_max; k0 += G) {
-          const int k = k0 + gl;
-          if (active && k < nhs && k != p) {
-            float d0 = pf0 - st.fx[k], d1 = pf1 - st.fy[k], d2 = pf2 - st.fz[k];
-            if (!P.domain) {
-              d0 = wrapf(d0, Lf0);
-              d1 = wrapf(d1, Lf1);
-              d2 = wrapf(d2, Lf2);
-            }
-            const float dd = __fmaf_rn(d2, d2, __fmaf_rn(d1, d1, d0 * d0));
-            if (dd <= near2) {
-              const float dv = __fmaf_rn(d2, vf2, __fmaf_rn(d1, vf1, d0 * vf0));
-              const float disc = sig2f - (dd - dv * dv);
-              if (dv < eps_v && disc > -eps_d) {
-                if (dv < -eps_v && disc > eps_d) {
-                  const float u = fmaxf(0.f, -dv + eps_v - sqrtf(disc - eps_d) * 0.9999998f) + 1e-6f;
-                  ubl = fminf(ubl, u);
-                }
-                const float lb = -dv - eps_v - sqrtf(disc + eps_d) * 1.0000002f;
-                if (lb <= ubl) {
-                  if (kl0 > ubl) {
-                    ks0 = -1;
-                    kl0 = INF;
-                  }
-                  if (kl1 > ubl) {
-                    ks1 = -1;
-                    kl1 = INF;
-                  }
-                  if (ks0 < 0) {
-                    ks0 = k;
-                    kl0 = lb;
-                  } else if (ks1 < 0) {
-                    ks1 = k;
-                    kl1 = lb;
-                  } else {
-                    ovf = true;
-                  }
-                }
-              }
-            }
-          }
-        }
+      }
+      if (F32) {
         const float U = group_minf<G>(ubl);
         // survivors of this lane, confirmed in FP64 in shared rounds
-        int job0 = -1, job1 = -1, job2 = -1;  // slot | (tether << 30)
+        int jq0 = -1, jq1 = -1, jq2 = -1, jq3 = -1;
         int nj = 0;
-        if (sp_kind == KIND_TETHER && sp_lb <= U) {
-          job0 = sp_slot | (1 << 30);
-          nj = 1;
-        }
-        if (ks0 >= 0 && kl0 <= U) {
-          if (nj == 0) job0 = ks0;
-          else job1 = ks0;
+        auto push = [&](int v) {
+          if (nj == 0) jq0 = v;
+          else if (nj == 1) jq1 = v;
+          else if (nj == 2) jq2 = v;
+          else jq3 = v;
           ++nj;
-        }
-        if (ks1 >= 0 && kl1 <= U) {
-          if (nj == 0) job0 = ks1;
-          else if (nj == 1) job1 = ks1;
-          else job2 = ks1;
-          ++nj;
-        }
+        };
+#pragma unroll
+        for (int r = 0; r < ITEMS; ++r)
+          if (spk[r] == KIND_TETHER && spl[r] <= U) push(sps[r] | (1 << 30));
+        if (ks0 >= 0 && kl0 <= U) push(ks0);
+        if (ks1 >= 0 && kl1 <= U) push(ks1);
         const int rounds = __reduce_max_sync(FULL, nj);
-        for (int r = 0; r < rounds; ++r) {
-          if (r < nj) {
-            const int job = r == 0 ? job0 : (r == 1 ? job1 : job2);
-            const bool te = (job >> 30) & 1;
-            const int k = job & 0x3FFFFFFF;
-            double dv;
-            const double x = quad_x(te, wrap_i(q0 - st.px[k], P.L[0], hb0),
-                                    wrap_i(q1 - st.py[k], P.L[1], hb1),
-                                    wrap_i(q2 - st.pz[k], P.L[2], hb2), v0, v1, v2,
+        for (int rr = 0; rr < rounds; ++rr) {
+          if (rr < nj) {
+            const int jb = rr == 0 ? jq0 : (rr == 1 ? jq1 : (rr == 2 ? jq2 : jq3));
+            const bool te = (jb >> 30) & 1;
+            const int k = jb & 0x3FFFFFFF;
+            double kx, ky, kz, dv;
+            pos64(st, P, k, !F32 || k < m, kx, ky, kz);
+            const double x = quad_x(te, wrap_i(q0 - kx, P.L[0], hb0), wrap_i(q1 - ky, P.L[1], hb1),
+                                    wrap_i(q2 - kz, P.L[2], hb2), v0, v1, v2,
                                     te ? P.b2 : P.sig2, dv);
             ++confirmed;
             if (!neg(x)) {
@@ -637,8 +829,10 @@ __global__ void __launch_bounds__(128) ec_kernel(const ECParams P) {
             }
           }
         }
-        if (sp_kind == KIND_WALL && sp_lb <= U) {
-          const int a = sp_slot;
+#pragma unroll
+        for (int r = 0; r < ITEMS; ++r) {
+          if (!(spk[r] == KIND_WALL && spl[r] <= U)) continue;
+          const int a = sps[r];
           const double va = a == 0 ? v0 : (a == 1 ? v1 : v2);
           const double qa = a == 0 ? q0 : (a == 1 ? q1 : q2);
           const double ca = a == 0 ? c0 : (a == 1 ? c1 : c2);
@@ -652,38 +846,50 @@ __global__ void __launch_bounds__(128) ec_kernel(const ECParams P) {
             bkey = key;
           }
         }
-        if (ovf) {
-          // more than two possible winners in this lane: rescan its share
-          for (int k = gl; k < nhs; k += G) {
-            if (k == p || k == ks0 || k == ks1) continue;
+        if (kovf) {
+          // more than two possible winners in this lane: evaluate again
+          auto rescan = [&](int k) {
+            if (k == p || k == ks0 || k == ks1) return;
+            bool possible;
             float d0 = pf0 - st.fx[k], d1 = pf1 - st.fy[k], d2 = pf2 - st.fz[k];
             if (!P.domain) {
               d0 = wrapf(d0, Lf0);
               d1 = wrapf(d1, Lf1);
               d2 = wrapf(d2, Lf2);
             }
-            const float dd = __fmaf_rn(d2, d2, __fmaf_rn(d1, d1, d0 * d0));
-            if (dd <= near2) {
-              const float dv = __fmaf_rn(d2, vf2, __fmaf_rn(d1, vf1, d0 * vf0));
-              const float disc = sig2f - (dd - dv * dv);
-              const float lb = -dv - eps_v - sqrtf(disc + eps_d) * 1.0000002f;
-              if (dv < eps_v && disc > -eps_d && lb <= U) {
-                double dvx;
-                const double x = quad_x(false, wrap_i(q0 - st.px[k], P.L[0], hb0),
-                                        wrap_i(q1 - st.py[k], P.L[1], hb1),
-                                        wrap_i(q2 - st.pz[k], P.L[2], hb2), v0, v1, v2, P.sig2,
-                                        dvx);
-                ++confirmed;
-                if (!neg(x)) {
-                  const uint64_t key = make_key(KIND_HS, st.id[k], k);
-                  if (better(x, key, bx, bkey)) {
-                    bx = x;
-                    bkey = key;
-                    bdv = dvx;
-                  }
-                }
+            const float lb = screen_lb(Z, d0, d1, d2, vf0, vf1, vf2, possible);
+            if (!possible || lb > U) return;
+            double kx, ky, kz, dvx;
+            pos64(st, P, k, !F32 || k < m, kx, ky, kz);
+            const double x = quad_x(false, wrap_i(q0 - kx, P.L[0], hb0),
+                                    wrap_i(q1 - ky, P.L[1], hb1), wrap_i(q2 - kz, P.L[2], hb2),
+                                    v0, v1, v2, P.sig2, dvx);
+            ++confirmed;
+            if (!neg(x)) {
+              const uint64_t key = make_key(KIND_HS, st.id[k], k);
+              if (better(x, key, bx, bkey)) {
+                bx = x;
+                bkey = key;
+                bdv = dvx;
               }
             }
+          };
+          if (P.domain) {
+            for (int ci = gl; ci < 28; ci += G) {
+              int n;
+              uint4 cc = make_uint4(0, 0, 0, 0);
+              if (ci == 27) {
+                n = n_ovf;
+              } else {
+                const int x = pc0 + ci % 3 - 1, y = pc1 + (ci / 3) % 3 - 1, z = pc2 + ci / 9 - 1;
+                if (x < 0 || y < 0 || z < 0 || x >= LG.g0 || y >= LG.g1 || z >= LG.g2) continue;
+                cc = st.cell[(z * LG.g1 + y) * LG.g0 + x];
+                n = cell_count(cc);
+              }
+              for (int i = 0; i < n; ++i) rescan(ci == 27 ? (int)st.ovf[i] : cell_slot(cc, i));
+            }
+          } else {
+            for (int k = gl; k < nhs; k += G) rescan(k);
           }
         }
       }
@@ -730,10 +936,10 @@ __global__ void __launch_bounds__(128) ec_kernel(const ECParams P) {
           if (!motile) {
             out = kind == KIND_HS ? ECMC_EV_HS_REFLECT : ECMC_EV_TE_REFLECT;
             refl_all = refl_all + proj;
-            const double d0 = wrap_i(q0 - st.px[slot], P.L[0], hb0);
-            const double d1 = wrap_i(q1 - st.py[slot], P.L[1], hb1);
-            const double d2 = wrap_i(q2 - st.pz[slot], P.L[2], hb2);
-            mirror2(v0, v1, v2, d0, d1, d2);
+            double kx, ky, kz;
+            pos64(st, P, slot, !F32 || slot < m, kx, ky, kz);
+            mirror2(v0, v1, v2, wrap_i(q0 - kx, P.L[0], hb0), wrap_i(q1 - ky, P.L[1], hb1),
+                    wrap_i(q2 - kz, P.L[2], hb2));
           } else if (kind == KIND_HS) {
             lift = lift + proj;
             if (P.p_swap > 0.0) {
@@ -773,14 +979,12 @@ __global__ void __launch_bounds__(128) ec_kernel(const ECParams P) {
                       b1 = q1;
                       b2 = q2;
                     } else {
-                      b0 = st.px[b];
-                      b1 = st.py[b];
-                      b2 = st.pz[b];
+                      pos64(st, P, b, !F32 || b < m, b0, b1, b2);
                     }
                     const double e0 = wrap_i(a0 - b0, P.L[0], hb0);
                     const double e1 = wrap_i(a1 - b1, P.L[1], hb1);
                     const double e2 = wrap_i(a2 - b2, P.L[2], hb2);
-                    const double dd = e0 * e0 + e1 * e1 + e2 * e2;
+                    const double dd = __fma_rn(e2, e2, __fma_rn(e1, e1, e0 * e0));
                     ok = ok && !(dbits(dd) > dbits(P.b2));
                   }
                 }
@@ -818,6 +1022,17 @@ __global__ void __launch_bounds__(128) ec_kernel(const ECParams P) {
         }
 #pragma unroll
         for (int k = 0; k < ECMC_NEV; ++k) cnt[k] += (out == k);
+        // FP32 shadow of the moved pivot (and of the swapped partner)
+        float nf0, nf1, nf2;
+        if (P.domain) {
+          nf0 = (float)wrap_i(q0 - c0, P.L[0], hb0);
+          nf1 = (float)wrap_i(q1 - c1, P.L[1], hb1);
+          nf2 = (float)wrap_i(q2 - c2, P.L[2], hb2);
+        } else {
+          nf0 = (float)q0;
+          nf1 = (float)q1;
+          nf2 = (float)q2;
+        }
         if (gl == 0) {
           fnv_mix(h, (uint64_t)pid);
           fnv_mix(h, ((uint64_t)(uint32_t)out << 32) | (uint64_t)(uint32_t)partner);
@@ -839,40 +1054,42 @@ __global__ void __launch_bounds__(128) ec_kernel(const ECParams P) {
           st.px[p] = q0;
           st.py[p] = q1;
           st.pz[p] = q2;
-        }
-        if (F32) {
-          // FP32 shadow of the moved pivot (and of the swapped partner)
-          float nf0, nf1, nf2;
           if (P.domain) {
-            nf0 = (float)wrap_i(q0 - c0, P.L[0], hb0);
-            nf1 = (float)wrap_i(q1 - c1, P.L[1], hb1);
-            nf2 = (float)wrap_i(q2 - c2, P.L[2], hb2);
-          } else {
-            nf0 = (float)q0;
-            nf1 = (float)q1;
-            nf2 = (float)q2;
-          }
-          if (gl == 0) {
-            st.fx[p] = nf0;
-            st.fy[p] = nf1;
-            st.fz[p] = nf2;
+            // keep the local grid current
+            int a0, a1, a2, b0, b1, b2;
+            const int oc = lcell(LG, pf0, pf1, pf2, a0, a1, a2);
+            const int ncl = lcell(LG, nf0, nf1, nf2, b0, b1, b2);
             if (swapped) {
               const double o0 = st.px[slot], o1 = st.py[slot], o2 = st.pz[slot];
-              if (P.domain) {
-                st.fx[slot] = (float)wrap_i(o0 - c0, P.L[0], hb0);
-                st.fy[slot] = (float)wrap_i(o1 - c1, P.L[1], hb1);
-                st.fz[slot] = (float)wrap_i(o2 - c2, P.L[2], hb2);
-              } else {
-                st.fx[slot] = (float)o0;
-                st.fy[slot] = (float)o1;
-                st.fz[slot] = (float)o2;
-              }
+              const float g0 = (float)wrap_i(o0 - c0, P.L[0], hb0);
+              const float g1 = (float)wrap_i(o1 - c1, P.L[1], hb1);
+              const float g2 = (float)wrap_i(o2 - c2, P.L[2], hb2);
+              const int koc = lcell(LG, st.fx[slot], st.fy[slot], st.fz[slot], a0, a1, a2);
+              const int knc = lcell(LG, g0, g1, g2, b0, b1, b2);
+              lcell_remove(st, oc, p);
+              lcell_remove(st, koc, slot);
+              st.fx[slot] = g0;
+              st.fy[slot] = g1;
+              st.fz[slot] = g2;
+              bool ok = lcell_insert(st, ncl, p);
+              ok = lcell_insert(st, knc, slot) && ok;
+              if (!ok) set_status(P.status, DEV_CAPACITY);
+            } else if (oc != ncl) {
+              lcell_remove(st, oc, p);
+              if (!lcell_insert(st, ncl, p)) set_status(P.status, DEV_CAPACITY);
             }
+          } else if (F32 && swapped) {
+            st.fx[slot] = (float)st.px[slot];
+            st.fy[slot] = (float)st.py[slot];
+            st.fz[slot] = (float)st.pz[slot];
           }
-          pf0 = nf0;
-          pf1 = nf1;
-          pf2 = nf2;
+          st.fx[p] = nf0;
+          st.fy[p] = nf1;
+          st.fz[p] = nf2;
         }
+        pf0 = nf0;
+        pf1 = nf1;
+        pf2 = nf2;
         if (out == ECMC_EV_END) {
           active = false;
         } else {
@@ -892,11 +1109,9 @@ __global__ void __launch_bounds__(128) ec_kernel(const ECParams P) {
         q0 = st.px[p];
         q1 = st.py[p];
         q2 = st.pz[p];
-        if (F32) {
-          pf0 = st.fx[p];
-          pf1 = st.fy[p];
-          pf2 = st.fz[p];
-        }
+        pf0 = st.fx[p];
+        pf1 = st.fy[p];
+        pf2 = st.fz[p];
       }
       __syncwarp();
     }
@@ -947,9 +1162,8 @@ __global__ void __launch_bounds__(128) ec_kernel(const ECParams P) {
 
 }  // namespace
 
-size_t ec_smem_bytes(int stage_cap, int lanes, int groups_per_block) {
-  (void)lanes;
-  return (size_t)groups_per_block * ((size_t)stage_cap * SLOT_BYTES + HDR_BYTES);
+size_t ec_smem_bytes(int stage_cap, int motile_cap, int ncell, int groups_per_block) {
+  return (size_t)groups_per_block * group_bytes(stage_cap, motile_cap, ncell);
 }
 
 template <int G, bool F32>
@@ -964,7 +1178,9 @@ static cudaError_t launch_t(const ECParams &P, cudaStream_t s) {
   // whole warps per block (lockstep shuffles use all 32 lanes), at most 128
   // threads, and the staging buffers of all groups within shared memory
   const int per_warp = 32 / G;
-  const size_t per_group = ec_smem_bytes(P.stage_cap, G, 1);
+  const int NC = P.domain ? P.lg[0] * P.lg[1] * P.lg[2] : 0;
+  const int M = (F32 && P.domain) ? P.m_cap : P.stage_cap;
+  const size_t per_group = ec_smem_bytes(P.stage_cap, M, NC, 1);
   int gpb = 128 / G;
   while (gpb > per_warp && (size_t)gpb * per_group > (size_t)smem_max) gpb -= per_warp;
   const int need = (P.n_units + per_warp - 1) / per_warp * per_warp;
@@ -984,6 +1200,7 @@ cudaError_t launch_ec(const ECParams &P, int lanes, int fp32f, cudaStream_t s) {
   if (lanes == 32) return fp32f ? launch_t<32, true>(P, s) : launch_t<32, false>(P, s);
   if (lanes == 16) return fp32f ? launch_t<16, true>(P, s) : launch_t<16, false>(P, s);
   if (lanes == 8) return fp32f ? launch_t<8, true>(P, s) : launch_t<8, false>(P, s);
+  if (lanes == 4) return fp32f ? launch_t<4, true>(P, s) : launch_t<4, false>(P, s);
   return cudaErrorInvalidValue;
 }
 

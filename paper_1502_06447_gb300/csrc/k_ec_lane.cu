@@ -45,7 +45,7 @@ __device__ __forceinline__ double wrap_i(double d, double L, uint64_t hbits) {
   return d;
 }
 __device__ __forceinline__ int step_i(double &r, double x, double v, double L) {
-  double y = r + x * v;
+  double y = __fma_rn(x, v, r);
   int di = 0;
   if (ge_pos(y, L)) {
     y = y - L;
@@ -64,10 +64,10 @@ __device__ __forceinline__ int step_i(double &r, double x, double v, double L) {
 // contact (tether = false, R2 = sigma^2) or tether limit (R2 = b_max^2)
 __device__ __forceinline__ double quad_x(bool tether, double d0, double d1, double d2, double v0,
                                          double v1, double v2, double R2, double &dv) {
-  dv = d0 * v0 + d1 * v1 + d2 * v2;
+  dv = __fma_rn(d2, v2, __fma_rn(d1, v1, d0 * v0));
   if (!tether && !neg(dv)) return -1.0;
-  const double dd = d0 * d0 + d1 * d1 + d2 * d2;
-  double rad = R2 - (dd - dv * dv);
+  const double dd = __fma_rn(d2, d2, __fma_rn(d1, d1, d0 * d0));
+  double rad = R2 - __fma_rn(-dv, dv, dd);
   if (tether) {
     if (neg(rad)) rad = 0.0;
   } else if (!posv(rad)) {
@@ -78,12 +78,12 @@ __device__ __forceinline__ double quad_x(bool tether, double d0, double d1, doub
 }
 __device__ __forceinline__ void mirror2(double &v0, double &v1, double &v2, double d0, double d1,
                                         double d2) {
-  const double dd = d0 * d0 + d1 * d1 + d2 * d2;
-  const double vd = v0 * d0 + v1 * d1 + v2 * d2;
+  const double dd = __fma_rn(d2, d2, __fma_rn(d1, d1, d0 * d0));
+  const double vd = __fma_rn(v2, d2, __fma_rn(v1, d1, v0 * d0));
   const double t = (2.0 * vd) / dd;
-  v0 = v0 - t * d0;
-  v1 = v1 - t * d1;
-  v2 = v2 - t * d2;
+  v0 = __fma_rn(-t, d0, v0);
+  v1 = __fma_rn(-t, d1, v1);
+  v2 = __fma_rn(-t, d2, v2);
 }
 // tie order within equal x: (kind, partner id)
 __device__ __forceinline__ bool better(double x, int kind, int64_t id, double bx, int bkind,
@@ -704,7 +704,7 @@ __global__ void __launch_bounds__(64) ec_lane_kernel(const ECParams P) {
                   const double f0 = wrap_i(e0 - b0, P.L[0], hb0);
                   const double f1 = wrap_i(e1 - b1, P.L[1], hb1);
                   const double f2 = wrap_i(e2 - b2, P.L[2], hb2);
-                  const double dd = f0 * f0 + f1 * f1 + f2 * f2;
+                  const double dd = __fma_rn(f2, f2, __fma_rn(f1, f1, f0 * f0));
                   ok = ok && !(dbits(dd) > dbits(P.b2));
                 }
               }

@@ -105,7 +105,7 @@ RAGGED = Melt("ragged_15x17x16_N8", (15, 17, 16), 1.05, 8, ell=4.0, seed=0xEC00A
               mode="domain", dir_mode="iso", sweeps=3, D=(3, 4, 3))
 
 
-@pytest.mark.parametrize("lanes", [32, 16, 8, 1])
+@pytest.mark.parametrize("lanes", [32, 16, 8, 4, 1])
 @pytest.mark.parametrize("prec", ["fp64", "fp32f"])
 @pytest.mark.parametrize("m", [small_domain(), RAGGED], ids=lambda m: m.name)
 def test_domain_parity_small(m, prec, lanes):
@@ -125,7 +125,7 @@ def test_domain_parity_small(m, prec, lanes):
         assert obs[k] == v, k
 
 
-@pytest.mark.parametrize("lanes", [32, 1])
+@pytest.mark.parametrize("lanes", [32, 8, 1])
 def test_domain_two_ecs_per_tile(lanes):
     m = small_domain(seed=0xEC00A3)
     o = oracle_system(m, ecs_per_tile=2)
@@ -144,7 +144,7 @@ def c2_oracle():
     return o, res
 
 
-@pytest.mark.parametrize("lanes", [32, 1])
+@pytest.mark.parametrize("lanes", [32, 8, 1])
 @pytest.mark.parametrize("prec", ["fp64", "fp32f"])
 def test_domain_parity_c2_full_size(c2_oracle, prec, lanes):
     """C2 at full size (4096 x 64 beads, 16^3 tiles): three sweeps identical."""
@@ -171,7 +171,7 @@ def test_run_split_equals_one_run():
 
 
 # ------------------------------------------------------------------ swap
-@pytest.mark.parametrize("lanes", [32, 1])
+@pytest.mark.parametrize("lanes", [32, 8, 1])
 @pytest.mark.parametrize("p_swap", [0.5, 1.0])
 def test_swap_parity_domain(p_swap, lanes):
     m = small_domain(p_swap=p_swap, seed=0xEC00A4, ell=6.0)
