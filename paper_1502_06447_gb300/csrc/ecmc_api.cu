@@ -613,14 +613,27 @@ static ECParams ec_params(const ecmc_ctx *c, uint64_t seed, double ell) {
   P.ell = ell;
   P.event_cap = c->event_cap;
   P.p_swap = c->opts.p_swap;
+  P.swap_mode = c->opts.p_swap >= 1.0 ? 1 : (c->opts.p_swap > 0.0 ? 2 : 0);
+  P.swap_thr = P.swap_mode == 2 ? (uint64_t)ceil(c->opts.p_swap * 9007199254740992.0) : 0;
   P.dir_mode = c->opts.dir_mode;
   P.stage_cap = c->stage_cap;
   P.m_cap = c->m_cap;
-  // FP32 screen margins for tile-local coordinates below 64 sigma (the
-  // rounding errors they cover are at most ~1/14 of these)
-  P.eps_v = (float)(2e-4 * c->sigma);
-  P.eps_d = (float)(1e-3 * c->sigma * c->sigma);
-  P.eps_x = (float)(2e-4 * c->sigma);
+  // FP32 screen margins.  A shadow coordinate is off by at most
+  // err = 2^-24 (3 L + 64 sigma) (FP32 rounding of the position, of the tile
+  // corner, of their difference and of a wrap); a separation then by
+  // 2 sqrt(3) err, d.v and |d|^2 - (d.v)^2 by about 3.5 err and 18 err.  The
+  // margins keep a factor of 10 over those.
+  {
+    double Lm = c->L[0] > c->L[1] ? c->L[0] : c->L[1];
+    Lm = Lm > c->L[2] ? Lm : c->L[2];
+    const double err = (3.0 * Lm + 64.0 * c->sigma) / 16777216.0;
+    const double ev = 35.0 * err > 2e-4 * c->sigma ? 35.0 * err : 2e-4 * c->sigma;
+    const double ed = 180.0 * err * c->sigma > 1e-3 * c->sigma * c->sigma ? 180.0 * err * c->sigma
+                                                                         : 1e-3 * c->sigma * c->sigma;
+    P.eps_v = (float)ev;
+    P.eps_d = (float)ed;
+    P.eps_x = (float)ev;
+  }
   P.scratch = c->d_scratch;
   P.tile_bytes = c->tile_bytes;
   for (int a = 0; a < 3; ++a) {

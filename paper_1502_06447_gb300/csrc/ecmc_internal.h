@@ -42,6 +42,8 @@ struct ECParams {
   double ell;
   int64_t event_cap;
   double p_swap;
+  int32_t swap_mode;    // 0: never propose, 1: always, 2: draw u < p_swap
+  uint64_t swap_thr;    // u53(w) < p_swap  <=>  (w >> 11) < swap_thr = ceil(p_swap 2^53)
   int32_t dir_mode;
   int32_t stage_cap;
   int32_t m_cap;        // motile slots with FP64 in shared memory (screened domain form)

@@ -59,6 +59,11 @@ __device__ __forceinline__ double wrap_i(double d, double L, uint64_t hbits) {
   return d;
 }
 
+// wrap_i on an axis that can need it; identity on an axis that cannot
+__device__ __forceinline__ double wrapc(double d, double L, uint64_t hbits, bool w) {
+  return w ? wrap_i(d, L, hbits) : d;
+}
+
 // r += x v on one axis, back into [0, L); returns the image change
 __device__ __forceinline__ int step_i(double &r, double x, double v, double L) {
   double y = __fma_rn(x, v, r);
@@ -561,6 +566,17 @@ __global__ void __launch_bounds__(128) ec_kernel(const ECParams P) {
   const int nhs_max = __reduce_max_sync(FULL, nhs);
 
   // ------------------------------------------------------------ ECs
+  // A tile whose halo lies inside (0, L) on an axis never needs the minimum
+  // image or a wrap on that axis: every position it touches stays in one
+  // periodic image.  Those axes skip the wrap code entirely.
+  bool wr0 = true, wr1 = true, wr2 = true;
+  if (P.domain) {
+    wr0 = !(c0 - P.halo_te > 0.0 && c0 + P.W[0] + P.halo_te < P.L[0]);
+    wr1 = !(c1 - P.halo_te > 0.0 && c1 + P.W[1] + P.halo_te < P.L[1]);
+    wr2 = !(c2 - P.halo_te > 0.0 && c2 + P.W[2] + P.halo_te < P.L[2]);
+  }
+  const float cf0 = (float)c0, cf1 = (float)c1, cf2 = (float)c2;
+  const float Lh0 = 0.5f * (float)P.L[0], Lh1 = 0.5f * (float)P.L[1], Lh2 = 0.5f * (float)P.L[2];
   const int n_ec = P.ecs_per_tile;
   Screen Z;
   Z.sig2f = (float)P.sig2;
@@ -669,9 +685,9 @@ __global__ void __launch_bounds__(128) ec_kernel(const ECParams P) {
           if (t < 0) continue;
           if (!F32) {
             double dv;
-            const double x = quad_x(true, wrap_i(q0 - st.px[t], P.L[0], hb0),
-                                    wrap_i(q1 - st.py[t], P.L[1], hb1),
-                                    wrap_i(q2 - st.pz[t], P.L[2], hb2), v0, v1, v2, P.b2, dv);
+            const double x = quad_x(true, wrapc(q0 - st.px[t], P.L[0], hb0, wr0),
+                                    wrapc(q1 - st.py[t], P.L[1], hb1, wr1),
+                                    wrapc(q2 - st.pz[t], P.L[2], hb2, wr2), v0, v1, v2, P.b2, dv);
             const uint64_t key = make_key(KIND_TETHER, st.id[t], t);
             if (better(x, key, bx, bkey)) {
               bx = x;
@@ -702,7 +718,8 @@ __global__ void __launch_bounds__(128) ec_kernel(const ECParams P) {
           if (!F32) {
             const double qa = a == 0 ? q0 : (a == 1 ? q1 : q2);
             const double ca = a == 0 ? c0 : (a == 1 ? c1 : c2);
-            const double loc = wrap_i(qa - ca, P.L[a], a == 0 ? hb0 : (a == 1 ? hb1 : hb2));
+            const double loc = wrapc(qa - ca, P.L[a], a == 0 ? hb0 : (a == 1 ? hb1 : hb2),
+                                     a == 0 ? wr0 : (a == 1 ? wr1 : wr2));
             double x = posv(va) ? (P.W[a] - loc) / va : (0.0 - loc) / va;
             if (neg(x)) x = 0.0;
             const uint64_t key = make_key(KIND_WALL, a, 0);
@@ -750,9 +767,9 @@ __global__ void __launch_bounds__(128) ec_kernel(const ECParams P) {
             if (k == p) continue;
             if (!F32) {
               double dv;
-              const double x = quad_x(false, wrap_i(q0 - st.px[k], P.L[0], hb0),
-                                      wrap_i(q1 - st.py[k], P.L[1], hb1),
-                                      wrap_i(q2 - st.pz[k], P.L[2], hb2), v0, v1, v2, P.sig2, dv);
+              const double x = quad_x(false, wrapc(q0 - st.px[k], P.L[0], hb0, wr0),
+                                      wrapc(q1 - st.py[k], P.L[1], hb1, wr1),
+                                      wrapc(q2 - st.pz[k], P.L[2], hb2, wr2), v0, v1, v2, P.sig2, dv);
               if (!neg(x)) {
                 const uint64_t key = make_key(KIND_HS, st.id[k], k);
                 if (better(x, key, bx, bkey)) {
@@ -773,9 +790,9 @@ __global__ void __launch_bounds__(128) ec_kernel(const ECParams P) {
           if (!(active && k < nhs && k != p)) continue;
           if (!F32) {
             double dv;
-            const double x = quad_x(false, wrap_i(q0 - st.px[k], P.L[0], hb0),
-                                    wrap_i(q1 - st.py[k], P.L[1], hb1),
-                                    wrap_i(q2 - st.pz[k], P.L[2], hb2), v0, v1, v2, P.sig2, dv);
+            const double x = quad_x(false, wrapc(q0 - st.px[k], P.L[0], hb0, wr0),
+                                    wrapc(q1 - st.py[k], P.L[1], hb1, wr1),
+                                    wrapc(q2 - st.pz[k], P.L[2], hb2, wr2), v0, v1, v2, P.sig2, dv);
             if (!neg(x)) {
               const uint64_t key = make_key(KIND_HS, st.id[k], k);
               if (better(x, key, bx, bkey)) {
@@ -815,8 +832,8 @@ __global__ void __launch_bounds__(128) ec_kernel(const ECParams P) {
             const int k = jb & 0x3FFFFFFF;
             double kx, ky, kz, dv;
             pos64(st, P, k, !F32 || k < m, kx, ky, kz);
-            const double x = quad_x(te, wrap_i(q0 - kx, P.L[0], hb0), wrap_i(q1 - ky, P.L[1], hb1),
-                                    wrap_i(q2 - kz, P.L[2], hb2), v0, v1, v2,
+            const double x = quad_x(te, wrapc(q0 - kx, P.L[0], hb0, wr0), wrapc(q1 - ky, P.L[1], hb1, wr1),
+                                    wrapc(q2 - kz, P.L[2], hb2, wr2), v0, v1, v2,
                                     te ? P.b2 : P.sig2, dv);
             ++confirmed;
             if (!neg(x)) {
@@ -836,7 +853,8 @@ __global__ void __launch_bounds__(128) ec_kernel(const ECParams P) {
           const double va = a == 0 ? v0 : (a == 1 ? v1 : v2);
           const double qa = a == 0 ? q0 : (a == 1 ? q1 : q2);
           const double ca = a == 0 ? c0 : (a == 1 ? c1 : c2);
-          const double loc = wrap_i(qa - ca, P.L[a], a == 0 ? hb0 : (a == 1 ? hb1 : hb2));
+          const double loc = wrapc(qa - ca, P.L[a], a == 0 ? hb0 : (a == 1 ? hb1 : hb2),
+                                     a == 0 ? wr0 : (a == 1 ? wr1 : wr2));
           double x = posv(va) ? (P.W[a] - loc) / va : (0.0 - loc) / va;
           if (neg(x)) x = 0.0;
           ++confirmed;
@@ -861,8 +879,8 @@ __global__ void __launch_bounds__(128) ec_kernel(const ECParams P) {
             if (!possible || lb > U) return;
             double kx, ky, kz, dvx;
             pos64(st, P, k, !F32 || k < m, kx, ky, kz);
-            const double x = quad_x(false, wrap_i(q0 - kx, P.L[0], hb0),
-                                    wrap_i(q1 - ky, P.L[1], hb1), wrap_i(q2 - kz, P.L[2], hb2),
+            const double x = quad_x(false, wrapc(q0 - kx, P.L[0], hb0, wr0),
+                                    wrapc(q1 - ky, P.L[1], hb1, wr1), wrapc(q2 - kz, P.L[2], hb2, wr2),
                                     v0, v1, v2, P.sig2, dvx);
             ++confirmed;
             if (!neg(x)) {
@@ -909,9 +927,13 @@ __global__ void __launch_bounds__(128) ec_kernel(const ECParams P) {
         const int kind = key_kind(bkey);
         const int slot = key_slot(bkey);
         const int64_t partner = (kind == KIND_END || kind == KIND_PASS) ? -1 : key_id(bkey);
-        const int di0 = step_i(q0, x, v0, P.L[0]);
-        const int di1 = step_i(q1, x, v1, P.L[1]);
-        const int di2 = step_i(q2, x, v2, P.L[2]);
+        int di0 = 0, di1 = 0, di2 = 0;
+        if (wr0) di0 = step_i(q0, x, v0, P.L[0]);
+        else q0 = __fma_rn(x, v0, q0);
+        if (wr1) di1 = step_i(q1, x, v1, P.L[1]);
+        else q1 = __fma_rn(x, v1, q1);
+        if (wr2) di2 = step_i(q2, x, v2, P.L[2]);
+        else q2 = __fma_rn(x, v2, q2);
         if (gl == 0 && (di0 | di1 | di2)) {
           if (di0) P.img[3 * (int64_t)pid] += di0;
           if (di1) P.img[3 * (int64_t)pid + 1] += di1;
@@ -938,19 +960,19 @@ __global__ void __launch_bounds__(128) ec_kernel(const ECParams P) {
             refl_all = refl_all + proj;
             double kx, ky, kz;
             pos64(st, P, slot, !F32 || slot < m, kx, ky, kz);
-            mirror2(v0, v1, v2, wrap_i(q0 - kx, P.L[0], hb0), wrap_i(q1 - ky, P.L[1], hb1),
-                    wrap_i(q2 - kz, P.L[2], hb2));
+            mirror2(v0, v1, v2, wrapc(q0 - kx, P.L[0], hb0, wr0), wrapc(q1 - ky, P.L[1], hb1, wr1),
+                    wrapc(q2 - kz, P.L[2], hb2, wr2));
           } else if (kind == KIND_HS) {
             lift = lift + proj;
-            if (P.p_swap > 0.0) {
+            if (P.swap_mode) {
               bool go;
-              if (P.p_swap >= 1.0) {
+              if (P.swap_mode == 1) {
                 go = true;
               } else {
                 if ((ncontact & 3) == 0)
                   swr = philox(TAG_SWAP | ((uint64_t)(P.domain ? e : 0) << 8), r1, r2,
                                (uint64_t)(ncontact >> 2), P.seed, P.replica);
-                go = unit53(swr.v[ncontact & 3]) < P.p_swap;
+                go = (swr.v[ncontact & 3] >> 11) < P.swap_thr;
               }
               ++ncontact;
               if (go) {
@@ -981,9 +1003,9 @@ __global__ void __launch_bounds__(128) ec_kernel(const ECParams P) {
                     } else {
                       pos64(st, P, b, !F32 || b < m, b0, b1, b2);
                     }
-                    const double e0 = wrap_i(a0 - b0, P.L[0], hb0);
-                    const double e1 = wrap_i(a1 - b1, P.L[1], hb1);
-                    const double e2 = wrap_i(a2 - b2, P.L[2], hb2);
+                    const double e0 = wrapc(a0 - b0, P.L[0], hb0, wr0);
+                    const double e1 = wrapc(a1 - b1, P.L[1], hb1, wr1);
+                    const double e2 = wrapc(a2 - b2, P.L[2], hb2, wr2);
                     const double dd = __fma_rn(e2, e2, __fma_rn(e1, e1, e0 * e0));
                     ok = ok && !(dbits(dd) > dbits(P.b2));
                   }
@@ -1022,12 +1044,16 @@ __global__ void __launch_bounds__(128) ec_kernel(const ECParams P) {
         }
 #pragma unroll
         for (int k = 0; k < ECMC_NEV; ++k) cnt[k] += (out == k);
-        // FP32 shadow of the moved pivot (and of the swapped partner)
+        // FP32 shadow of the moved pivot: FP32 position minus FP32 corner
+        // (within the margins of the screen)
         float nf0, nf1, nf2;
         if (P.domain) {
-          nf0 = (float)wrap_i(q0 - c0, P.L[0], hb0);
-          nf1 = (float)wrap_i(q1 - c1, P.L[1], hb1);
-          nf2 = (float)wrap_i(q2 - c2, P.L[2], hb2);
+          nf0 = (float)q0 - cf0;
+          nf1 = (float)q1 - cf1;
+          nf2 = (float)q2 - cf2;
+          if (wr0) nf0 = nf0 > Lh0 ? nf0 - (float)P.L[0] : (nf0 < -Lh0 ? nf0 + (float)P.L[0] : nf0);
+          if (wr1) nf1 = nf1 > Lh1 ? nf1 - (float)P.L[1] : (nf1 < -Lh1 ? nf1 + (float)P.L[1] : nf1);
+          if (wr2) nf2 = nf2 > Lh2 ? nf2 - (float)P.L[2] : (nf2 < -Lh2 ? nf2 + (float)P.L[2] : nf2);
         } else {
           nf0 = (float)q0;
           nf1 = (float)q1;
@@ -1061,9 +1087,10 @@ __global__ void __launch_bounds__(128) ec_kernel(const ECParams P) {
             const int ncl = lcell(LG, nf0, nf1, nf2, b0, b1, b2);
             if (swapped) {
               const double o0 = st.px[slot], o1 = st.py[slot], o2 = st.pz[slot];
-              const float g0 = (float)wrap_i(o0 - c0, P.L[0], hb0);
-              const float g1 = (float)wrap_i(o1 - c1, P.L[1], hb1);
-              const float g2 = (float)wrap_i(o2 - c2, P.L[2], hb2);
+              float g0 = (float)o0 - cf0, g1 = (float)o1 - cf1, g2 = (float)o2 - cf2;
+              if (wr0) g0 = g0 > Lh0 ? g0 - (float)P.L[0] : (g0 < -Lh0 ? g0 + (float)P.L[0] : g0);
+              if (wr1) g1 = g1 > Lh1 ? g1 - (float)P.L[1] : (g1 < -Lh1 ? g1 + (float)P.L[1] : g1);
+              if (wr2) g2 = g2 > Lh2 ? g2 - (float)P.L[2] : (g2 < -Lh2 ? g2 + (float)P.L[2] : g2);
               const int koc = lcell(LG, st.fx[slot], st.fy[slot], st.fz[slot], a0, a1, a2);
               const int knc = lcell(LG, g0, g1, g2, b0, b1, b2);
               lcell_remove(st, oc, p);

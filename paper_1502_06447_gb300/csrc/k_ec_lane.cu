@@ -661,15 +661,15 @@ __global__ void __launch_bounds__(64) ec_lane_kernel(const ECParams P) {
                   wrap_i(q2 - k2, P.L[2], hb2));
         } else if (bkind == KIND_HS) {
           lift = lift + proj;
-          if (P.p_swap > 0.0) {
+          if (P.swap_mode) {
             bool go;
-            if (P.p_swap >= 1.0) {
+            if (P.swap_mode == 1) {
               go = true;
             } else {
               if ((ncontact & 3) == 0)
                 swr = philox(TAG_SWAP | ((uint64_t)e << 8), r1, r2, (uint64_t)(ncontact >> 2),
                              P.seed, P.replica);
-              go = unit53(swr.v[ncontact & 3]) < P.p_swap;
+              go = (swr.v[ncontact & 3] >> 11) < P.swap_thr;
             }
             ++ncontact;
             if (go) {
