@@ -2,7 +2,7 @@
 
 Workload (the 10^6-bead melt): 1000 chains x N=1000 on a 100^3 lattice,
 spacing 1.05 sigma (phi ~ 0.45), b_max = 1.2 sigma, ell = 20 sigma,
-20^3 shifted tiles, isotropic directions, FP32 screen + FP64 confirmation,
+25^3 shifted tiles, isotropic directions, FP32 screen + FP64 confirmation,
 swap moves calibrated to 0.1 attempts per bead per sweep.
 One step = one sweep: domain assignment + cell list + one EC per tile.
 
@@ -31,10 +31,10 @@ sys.path.insert(0, ROOT)
 
 from paper_1502_06447_gb300.configs import C2, C3, C5  # noqa: E402
 
-WORKLOADS = {"c5": (C5, (20, 20, 20)), "c3": (C3, (16, 16, 16)), "c2": (C2, (16, 16, 16))}
+WORKLOADS = {"c5": (C5, (25, 25, 25)), "c3": (C3, (20, 20, 20)), "c2": (C2, (16, 16, 16))}
 C5_DEFAULT = C5
 ELL = C5.ell
-TILES = (20, 20, 20)
+TILES = (25, 25, 25)
 SWAP_RATE = 0.1
 METRIC = "events/s (EC sweep, 1e6-bead melt, FP32 screen + FP64 confirm)"
 UNIT = "events/s"
@@ -131,8 +131,9 @@ def run_gpu(args, rank, world):
         ctx = ecmc.Context.create_lattice(C5.dims, C5.spacing, C5.N, sigma=C5.sigma,
                                           b_max=C5.b_max, jitter=C5.jitter, seed=seed)
         ctx.set_stream(stream.cuda_stream)
+        lanes = args.lanes if precision == ecmc.PREC_FP32F else args.lanes64
         ctx.configure(mode=ecmc.MODE_DOMAIN, dir_mode=ecmc.DIR_ISO, precision=precision,
-                      tiles=TILES, lanes=args.lanes, ecs_per_tile=args.ecs_per_tile)
+                      tiles=TILES, lanes=lanes, ecs_per_tile=args.ecs_per_tile)
         return ctx
 
     ctx = make(ecmc.PREC_FP32F)
@@ -254,7 +255,7 @@ def run_gpu(args, rank, world):
         "wall_s": max_wall,
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
                      "frac": achieved / hbm, "traffic": traffic,
-                     "kernel": "ec_kernel<32,true>", "bytes_per_event": bpe,
+                     "kernel": f"ec_kernel<{args.lanes},true>", "bytes_per_event": bpe,
                      "kernel_share_of_step": ec_s / dev_s, "peak_source": peak_src},
         "e2e": {"value": e2e_events / e2e_s, "unit": UNIT,
                 "h2d_bytes_per_step": int(r_host.nbytes + img_host.nbytes),
@@ -320,7 +321,8 @@ def main():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--lanes", type=int, default=32)
+    ap.add_argument("--lanes", type=int, default=8, help="lanes per EC, screened kernel")
+    ap.add_argument("--lanes64", type=int, default=16, help="lanes per EC, plain FP64 kernel")
     ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
     ap.add_argument("--workload", default="c5", choices=sorted(WORKLOADS),
                     help="c5: the 1e6-bead melt (default); c2/c3: smaller melts")

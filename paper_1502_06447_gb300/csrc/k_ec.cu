@@ -169,14 +169,14 @@ struct Stage {
   unsigned *nb;          // [M] bond partner slots, 16 + 16 bits (0xFFFF = none)
   float *fx, *fy, *fz;   // [S]
   int *id;               // [S]
-  uint4 *cell;           // [NC]
+  unsigned short *cell;  // [NC][8]: count, then up to 7 slots
   unsigned short *ovf;   // [OVF_CAP]
   int *hdr;              // [2] staged count, [3] overflow, [4] overflow-list length
 };
 
 __host__ __device__ __forceinline__ size_t group_bytes(int S, int M, int NC) {
   return (size_t)M * 28 + (size_t)S * 16 + (size_t)NC * 16 + OVF_CAP * 2 + HDR_BYTES;
-}
+}  // (16 B per cell: a count and 7 slots of 16 bits)
 
 // S and M are multiples of 32, so every array starts 16-byte aligned
 __device__ __forceinline__ Stage carve(unsigned char *base, int S, int M, int NC) {
@@ -189,8 +189,8 @@ __device__ __forceinline__ Stage carve(unsigned char *base, int S, int M, int NC
   s.fy = s.fx + S;
   s.fz = s.fy + S;
   s.id = (int *)(s.fz + S);
-  s.cell = (uint4 *)(s.id + S);
-  s.ovf = (unsigned short *)(s.cell + NC);
+  s.cell = (unsigned short *)(s.id + S);
+  s.ovf = s.cell + 8 * NC;
   s.hdr = (int *)(s.ovf + OVF_CAP);
   return s;
 }
@@ -216,28 +216,6 @@ __device__ __forceinline__ int find_id(const int *ids, int lo, int hi, int id) {
 __device__ __forceinline__ void set_status(int *st, int code) { atomicCAS(st, 0, code); }
 
 // ---------------------------------------------------------------- local grid
-__device__ __forceinline__ int cell_count(const uint4 &c) { return (int)(c.x & 0xFFFF); }
-__device__ __forceinline__ int cell_slot(const uint4 &c, int i) {
-  const unsigned w = i == 0 ? (c.x >> 16)
-                   : i == 1 ? (c.y & 0xFFFF)
-                   : i == 2 ? (c.y >> 16)
-                   : i == 3 ? (c.z & 0xFFFF)
-                   : i == 4 ? (c.z >> 16)
-                   : i == 5 ? (c.w & 0xFFFF)
-                            : (c.w >> 16);
-  return (int)(w & 0xFFFF);
-}
-__device__ __forceinline__ void cell_set(uint4 &c, int i, int s) {
-  const unsigned v = (unsigned)s & 0xFFFF;
-  if (i == 0) c.x = (c.x & 0xFFFF) | (v << 16);
-  else if (i == 1) c.y = (c.y & 0xFFFF0000u) | v;
-  else if (i == 2) c.y = (c.y & 0xFFFF) | (v << 16);
-  else if (i == 3) c.z = (c.z & 0xFFFF0000u) | v;
-  else if (i == 4) c.z = (c.z & 0xFFFF) | (v << 16);
-  else if (i == 5) c.w = (c.w & 0xFFFF0000u) | v;
-  else c.w = (c.w & 0xFFFF) | (v << 16);
-}
-
 struct LGrid {
   int g0, g1, g2;
   float org, inv0, inv1, inv2;
@@ -256,12 +234,11 @@ __device__ __forceinline__ int lcell(const LGrid &L, float f0, float f1, float f
 
 // single-writer updates (one lane of the group)
 __device__ __forceinline__ bool lcell_insert(const Stage &st, int ci, int slot) {
-  uint4 c = st.cell[ci];
-  const int n = cell_count(c);
+  unsigned short *c = st.cell + 8 * ci;
+  const int n = c[0];
   if (n < CELL_CAP) {
-    cell_set(c, n, slot);
-    c.x = (c.x & 0xFFFF0000u) | (unsigned)(n + 1);
-    st.cell[ci] = c;
+    c[1 + n] = (unsigned short)slot;
+    c[0] = (unsigned short)(n + 1);
     return true;
   }
   const int k = st.hdr[4];
@@ -272,13 +249,12 @@ __device__ __forceinline__ bool lcell_insert(const Stage &st, int ci, int slot) 
 }
 
 __device__ __forceinline__ void lcell_remove(const Stage &st, int ci, int slot) {
-  uint4 c = st.cell[ci];
-  const int n = cell_count(c);
-  for (int i = 0; i < n; ++i) {
-    if (cell_slot(c, i) == slot) {
-      cell_set(c, i, cell_slot(c, n - 1));
-      c.x = (c.x & 0xFFFF0000u) | (unsigned)(n - 1);
-      st.cell[ci] = c;
+  unsigned short *c = st.cell + 8 * ci;
+  const int n = c[0];
+  for (int i = 1; i <= n; ++i) {
+    if (c[i] == slot) {
+      c[i] = c[n];
+      c[0] = (unsigned short)(n - 1);
       return;
     }
   }
@@ -517,7 +493,7 @@ __global__ void __launch_bounds__(128) ec_kernel(const ECParams P) {
       live = false;
     }
     // pass 3: shadows and bond partners of motile beads; empty cells
-    for (int i = gl; i < NC; i += G) st.cell[i] = make_uint4(0, 0, 0, 0);
+    for (int i = gl; i < NC; i += G) st.cell[8 * i] = 0;
     for (int s0 = 0; s0 < ns_max; s0 += G) {
       const int s = s0 + gl;
       if (s < ns && live) {
@@ -753,17 +729,19 @@ __global__ void __launch_bounds__(128) ec_kernel(const ECParams P) {
         for (int ci = gl; ci < 28; ci += G) {
           if (!active) break;
           int n;
-          uint4 cc = make_uint4(0, 0, 0, 0);
+          const unsigned short *lst;
           if (ci == 27) {
             n = n_ovf;
+            lst = st.ovf;
           } else {
             const int x = pc0 + ci % 3 - 1, y = pc1 + (ci / 3) % 3 - 1, z = pc2 + ci / 9 - 1;
             if (x < 0 || y < 0 || z < 0 || x >= LG.g0 || y >= LG.g1 || z >= LG.g2) continue;
-            cc = st.cell[(z * LG.g1 + y) * LG.g0 + x];
-            n = cell_count(cc);
+            const unsigned short *c = st.cell + 8 * ((z * LG.g1 + y) * LG.g0 + x);
+            n = c[0];
+            lst = c + 1;
           }
           for (int i = 0; i < n; ++i) {
-            const int k = ci == 27 ? (int)st.ovf[i] : cell_slot(cc, i);
+            const int k = lst[i];
             if (k == p) continue;
             if (!F32) {
               double dv;
@@ -895,16 +873,18 @@ __global__ void __launch_bounds__(128) ec_kernel(const ECParams P) {
           if (P.domain) {
             for (int ci = gl; ci < 28; ci += G) {
               int n;
-              uint4 cc = make_uint4(0, 0, 0, 0);
+              const unsigned short *lst;
               if (ci == 27) {
                 n = n_ovf;
+                lst = st.ovf;
               } else {
                 const int x = pc0 + ci % 3 - 1, y = pc1 + (ci / 3) % 3 - 1, z = pc2 + ci / 9 - 1;
                 if (x < 0 || y < 0 || z < 0 || x >= LG.g0 || y >= LG.g1 || z >= LG.g2) continue;
-                cc = st.cell[(z * LG.g1 + y) * LG.g0 + x];
-                n = cell_count(cc);
+                const unsigned short *c = st.cell + 8 * ((z * LG.g1 + y) * LG.g0 + x);
+                n = c[0];
+                lst = c + 1;
               }
-              for (int i = 0; i < n; ++i) rescan(ci == 27 ? (int)st.ovf[i] : cell_slot(cc, i));
+              for (int i = 0; i < n; ++i) rescan(lst[i]);
             }
           } else {
             for (int k = gl; k < nhs; k += G) rescan(k);
@@ -1203,16 +1183,43 @@ static cudaError_t launch_t(const ECParams &P, cudaStream_t s) {
     if (e != cudaSuccess) return e;
   }
   // whole warps per block (lockstep shuffles use all 32 lanes), at most 128
-  // threads, and the staging buffers of all groups within shared memory
+  // threads; among those, the block size that keeps the most groups (tiles)
+  // resident per SM, as the occupancy calculator counts them
   const int per_warp = 32 / G;
   const int NC = P.domain ? P.lg[0] * P.lg[1] * P.lg[2] : 0;
   const int M = (F32 && P.domain) ? P.m_cap : P.stage_cap;
   const size_t per_group = ec_smem_bytes(P.stage_cap, M, NC, 1);
-  int gpb = 128 / G;
-  while (gpb > per_warp && (size_t)gpb * per_group > (size_t)smem_max) gpb -= per_warp;
   const int need = (P.n_units + per_warp - 1) / per_warp * per_warp;
-  if (gpb > need) gpb = need;
-  if ((size_t)gpb * per_group > (size_t)smem_max) return cudaErrorInvalidValue;
+  static size_t memo_pg = 0;
+  static int memo_need = 0, memo_gpb = 0;
+  int gpb = 0, best = -1;
+  const bool memo = memo_pg == per_group && memo_need == need;
+  if (memo) {
+    gpb = memo_gpb;
+  } else {
+    cudaError_t e = cudaFuncSetAttribute(ec_kernel<G, F32>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, smem_max);
+    if (e != cudaSuccess) return e;
+  }
+  for (int g = per_warp; !memo && g <= 128 / G; g += per_warp) {
+    if ((size_t)g * per_group > (size_t)smem_max) break;
+    int blocks = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, ec_kernel<G, F32>, g * G,
+                                                      (size_t)g * per_group) != cudaSuccess)
+      return cudaErrorInvalidValue;
+    const int resident = blocks * (g < need ? g : need);
+    if (resident >= best) {
+      best = resident;
+      gpb = g;
+    }
+    if (g >= need) break;
+  }
+  if (best >= 0) {
+    memo_pg = per_group;
+    memo_need = need;
+    memo_gpb = gpb;
+  }
+  if (gpb == 0) return cudaErrorInvalidValue;
   const int threads = gpb * G;
   const size_t smem = (size_t)gpb * per_group;
   cudaError_t e = cudaFuncSetAttribute(ec_kernel<G, F32>,
