@@ -93,6 +93,8 @@ typedef struct ecmc_opts {
   int32_t record;        /* 1: keep per-EC digests / lift sums of the last run */
   int32_t stage_cap;     /* staged beads per tile; 0 -> derived from the tile size */
   double cell_side;      /* side of the global cell grid (domain); 0 -> 1.0 sigma */
+  double tile_side;      /* batch: target tile side when tiles[0] <= 0 (per replica
+                            D = floor(L / tile_side), at least 3); 0 -> 4.2 sigma */
 } ecmc_opts;
 
 /* Observables and counters (Sec. III observables; see ecmc_observables). */
@@ -223,6 +225,47 @@ ecmc_status ecmc_domain_tags(ecmc_ctx *ctx, uint64_t seed, int64_t sweep,
  * (seed, sweep/EC counter), restore + run equals an uninterrupted run. */
 ecmc_status ecmc_checkpoint(ecmc_ctx *ctx, const char *path);
 ecmc_status ecmc_restore(ecmc_ctx *ctx, const char *path);
+
+/* ---- batched replicas ------------------------------------------------------
+ * Many independent melts advanced together: per sweep one domain assignment +
+ * cell list pass over all replicas' beads and one EC launch over all
+ * replicas' tiles (the Sec. II.B sweep of each replica), optionally captured
+ * once in a CUDA graph and replayed (the sweep counter lives on the device).
+ * Replica r is the lattice melt of ecmc_create_lattice with dims, spacing, N
+ * of specs[r] and jitter, and draws every random number with the Philox key
+ * (seed, r): it evolves exactly as a single melt with that key would.  All
+ * replicas share sigma and b_max.  Positions are concatenated in replica
+ * order. */
+typedef struct ecmc_replica_spec {
+  int32_t dims[3];
+  double spacing;
+  int32_t N;
+  double sigma, b_max;
+} ecmc_replica_spec;
+typedef struct ecmc_batch ecmc_batch;
+ecmc_status ecmc_batch_create(const ecmc_replica_spec *specs, int32_t n,
+                              double jitter, uint64_t seed, ecmc_batch **out);
+void ecmc_batch_destroy(ecmc_batch *b);
+/* opts as for ecmc_configure, domain mode only; tiles[0] <= 0 -> per
+ * replica tiles from opts.tile_side; lanes 4, 8, 16 or 32 (0 -> 8). */
+ecmc_status ecmc_batch_configure(ecmc_batch *b, const ecmc_opts *opts);
+/* n_sweeps sweeps of every replica; use_graph = 1 captures one sweep in a
+ * CUDA graph (after one uncaptured sweep) and replays it. */
+ecmc_status ecmc_batch_run(ecmc_batch *b, double ell, uint64_t seed,
+                           int64_t n_sweeps, int32_t use_graph);
+/* replica r's positions / images (host buffers of 3 n_r entries) */
+ecmc_status ecmc_batch_get_positions(ecmc_batch *b, int32_t replica,
+                                     double *xyz_out, int32_t *img_out);
+/* replica r's tiles per axis, first unit in the concatenated tile
+ * numbering, bead count (any output may be NULL) */
+ecmc_status ecmc_batch_info(ecmc_batch *b, int32_t replica, int32_t tiles[3],
+                            int64_t *unit_off, int64_t *n_beads);
+ecmc_status ecmc_batch_stats(ecmc_batch *b, int64_t *events_total,
+                             int64_t *ecs, double *device_seconds);
+/* per-EC records of the last run (opts.record = 1), ordered as
+ * ((sweep * units) + unit) * ecs_per_tile + ec over the concatenated units */
+ecmc_status ecmc_batch_records(ecmc_batch *b, uint64_t *digest, double *lift,
+                               int64_t *events, int64_t *n);
 
 /* ---- domain assignment and cell list without allocation ------------------
  * The paper has no counterpart to this entry point; it serves callers that

@@ -1,0 +1,515 @@
+// Batched replicas (declared in ecmc.h): many independent melts advanced by
+// one launch sequence per sweep — one domain assignment + cell list pass over
+// all replicas' beads and one EC launch over all replicas' tiles — captured
+// once in a CUDA graph and replayed; the sweep counter lives on the device.
+// Replica r draws every random number with the Philox key (seed, r), so each
+// replica evolves exactly as a single melt with that key would.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <string.h>
+
+#include <string>
+#include <vector>
+
+#include "ecmc_dev.cuh"
+#include "ecmc_internal.h"
+
+using namespace ecmc;
+
+namespace {
+ecmc_status bfail(ecmc_status s, const std::string &msg) {
+  set_last_error(msg.c_str());
+  return s;
+}
+#define BCU(call)                                                                             \
+  do {                                                                                        \
+    cudaError_t e_ = (call);                                                                  \
+    if (e_ != cudaSuccess)                                                                    \
+      return bfail(e_ == cudaErrorMemoryAllocation ? ECMC_ENOMEM : ECMC_ECUDA,                \
+                   std::string(#call) + ": " + cudaGetErrorString(e_));                       \
+  } while (0)
+
+template <class T>
+cudaError_t balloc(T **p, size_t count) {
+  *p = nullptr;
+  if (count == 0) count = 1;
+  return cudaMalloc((void **)p, sizeof(T) * count);
+}
+}  // namespace
+
+struct ecmc_batch {
+  int32_t R = 0;
+  std::vector<ecmc_replica_spec> specs;
+  std::vector<RepParams> reps;
+  int64_t n_total = 0, ncell_total = 0, units_total = 0;
+  double sigma = 1.0, b_max = 1.2;
+  uint64_t seed_lattice = 0;
+  ecmc_opts opts{};
+  bool configured = false;
+  double s_cap = 0.25, halo_hs = 0, halo_te = 0;
+  int32_t stage_cap = 0, m_cap = 0, ncl_max = 0, lanes = 8, ecs_per_tile = 1;
+  int64_t event_cap = 10000000;
+  cudaStream_t stream = nullptr;
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+  double *d_r = nullptr;
+  int32_t *d_img = nullptr, *d_rep_of = nullptr, *d_tag = nullptr, *d_cell = nullptr,
+          *d_rank = nullptr, *d_count = nullptr, *d_start = nullptr, *d_bsum = nullptr,
+          *d_cid = nullptr, *d_ctag = nullptr;
+  double *d_cr = nullptr;
+  RepParams *d_reps = nullptr;
+  unsigned long long *d_cnt = nullptr;
+  double *d_sums = nullptr;
+  int *d_status = nullptr;
+  int64_t *d_sweep = nullptr;
+  uint64_t *d_rdig = nullptr;
+  double *d_rlift = nullptr;
+  int64_t *d_rev = nullptr;
+  int64_t rec_cap = 0, rec_n = 0;
+  cudaGraphExec_t graph = nullptr;
+  double graph_ell = -1.0;
+  uint64_t graph_seed = 0;
+  bool graph_rec = false;
+  int64_t graph_rec_sweep0 = -1;
+  int64_t sweeps_done = 0;
+  double device_seconds = 0.0;
+};
+
+namespace {
+
+void batch_free(ecmc_batch *b) {
+  if (!b) return;
+  if (b->stream) cudaStreamSynchronize(b->stream);
+  if (b->graph) cudaGraphExecDestroy(b->graph);
+  void *ptrs[] = {b->d_r, b->d_img, b->d_rep_of, b->d_tag, b->d_cell, b->d_rank, b->d_count,
+                  b->d_start, b->d_bsum, b->d_cid, b->d_ctag, b->d_cr, b->d_reps, b->d_cnt,
+                  b->d_sums, b->d_status, b->d_sweep, b->d_rdig, b->d_rlift, b->d_rev};
+  for (void *p : ptrs) cudaFree(p);
+  if (b->ev0) cudaEventDestroy(b->ev0);
+  if (b->ev1) cudaEventDestroy(b->ev1);
+  if (b->stream) cudaStreamDestroy(b->stream);
+  delete b;
+}
+
+ecmc_status batch_status(ecmc_batch *b) {
+  int st = 0;
+  BCU(cudaMemcpyAsync(&st, b->d_status, sizeof(int), cudaMemcpyDeviceToHost, b->stream));
+  BCU(cudaStreamSynchronize(b->stream));
+  if (st == DEV_STUCK) return bfail(ECMC_ESTUCK, "an event chain exceeded the event cap");
+  if (st == DEV_CAPACITY) return bfail(ECMC_ECAPACITY, "a tile exceeded the staging capacity");
+  if (st == DEV_TILE) return bfail(ECMC_ECAPACITY, "a bonded partner was not staged with its tile");
+  return ECMC_OK;
+}
+
+// one sweep of every replica: domain assignment + cell list, EC kernel,
+// sweep counter advance (all stream-ordered, so it can be captured)
+cudaError_t batch_sweep(ecmc_batch *b, const ECParams &P, uint64_t seed) {
+  CellBatch C{};
+  C.n = b->n_total;
+  C.r = b->d_r;
+  C.rep_of = b->d_rep_of;
+  C.reps = b->d_reps;
+  C.seed = seed;
+  C.sweep_dev = b->d_sweep;
+  C.tag = b->d_tag;
+  C.cell = b->d_cell;
+  C.rank = b->d_rank;
+  C.count = b->d_count;
+  C.start = b->d_start;
+  C.block_sums = b->d_bsum;
+  C.cr = b->d_cr;
+  C.cid = b->d_cid;
+  C.ctag = b->d_ctag;
+  cudaError_t e = launch_cells_batch(C, b->ncell_total, b->stream);
+  if (e != cudaSuccess) return e;
+  e = launch_ec_batch(P, b->lanes, b->opts.precision == ECMC_PREC_FP32F, b->stream);
+  if (e != cudaSuccess) return e;
+  return launch_sweep_advance(b->d_sweep, b->stream);
+}
+
+ECParams batch_params(ecmc_batch *b, uint64_t seed, double ell) {
+  ECParams P{};
+  P.n = b->n_total;
+  P.sigma = b->sigma;
+  P.sig2 = b->sigma * b->sigma;
+  P.b2 = b->b_max * b->b_max;
+  P.s_cap = b->s_cap;
+  P.domain = 1;
+  P.halo_hs = b->halo_hs;
+  P.halo_te = b->halo_te;
+  P.seed = seed;
+  P.ell = ell;
+  P.event_cap = b->event_cap;
+  P.p_swap = b->opts.p_swap;
+  P.swap_mode = b->opts.p_swap >= 1.0 ? 1 : (b->opts.p_swap > 0.0 ? 2 : 0);
+  P.swap_thr = P.swap_mode == 2 ? (uint64_t)ceil(b->opts.p_swap * 9007199254740992.0) : 0;
+  P.dir_mode = b->opts.dir_mode;
+  P.stage_cap = b->stage_cap;
+  P.m_cap = b->m_cap;
+  P.n_units = (int32_t)b->units_total;
+  P.ecs_per_tile = b->ecs_per_tile;
+  double Lm = 0.0;
+  for (const RepParams &R : b->reps)
+    for (int a = 0; a < 3; ++a) Lm = R.L[a] > Lm ? R.L[a] : Lm;
+  const double err = (3.0 * Lm + 64.0 * b->sigma) / 16777216.0;
+  const double ev = 35.0 * err > 2e-4 * b->sigma ? 35.0 * err : 2e-4 * b->sigma;
+  const double ed = 180.0 * err * b->sigma > 1e-3 * b->sigma * b->sigma ? 180.0 * err * b->sigma
+                                                                       : 1e-3 * b->sigma * b->sigma;
+  P.eps_v = (float)ev;
+  P.eps_d = (float)ed;
+  P.eps_x = (float)ev;
+  P.r = b->d_r;
+  P.img = b->d_img;
+  P.cr = b->d_cr;
+  P.cid = b->d_cid;
+  P.ctag = b->d_ctag;
+  P.cstart = b->d_start;
+  P.counters = b->d_cnt;
+  P.sums = b->d_sums;
+  P.status = b->d_status;
+  P.reps = b->d_reps;
+  P.n_reps = b->R;
+  P.ncl_max = b->ncl_max;
+  P.sweep_dev = b->d_sweep;
+  return P;
+}
+
+}  // namespace
+
+extern "C" {
+
+ecmc_status ecmc_batch_create(const ecmc_replica_spec *specs, int32_t n, double jitter,
+                              uint64_t seed, ecmc_batch **out) {
+  if (!specs || !out || n < 1) return bfail(ECMC_EINVAL, "need at least one replica spec");
+  *out = nullptr;
+  const double sigma = specs[0].sigma, b_max = specs[0].b_max;
+  if (!(sigma > 0.0) || !(b_max >= sigma)) return bfail(ECMC_EINVAL, "need 0 < sigma <= b_max");
+  int64_t n_total = 0;
+  for (int32_t r = 0; r < n; ++r) {
+    const ecmc_replica_spec &sp = specs[r];
+    if (sp.sigma != sigma || sp.b_max != b_max)
+      return bfail(ECMC_EINVAL, "all replicas need the same sigma and b_max");
+    if (sp.dims[0] < 1 || sp.dims[1] < 1 || sp.dims[2] < 1 || sp.N < 1)
+      return bfail(ECMC_EINVAL, "replica " + std::to_string(r) + ": bad dims or N");
+    const int64_t nb = (int64_t)sp.dims[0] * sp.dims[1] * sp.dims[2];
+    if (nb % sp.N) return bfail(ECMC_EINVAL, "replica " + std::to_string(r) + ": N must divide the sites");
+    if (!(sp.spacing >= sigma) || (sp.N > 1 && !(sp.spacing <= b_max)))
+      return bfail(ECMC_EINVAL, "replica " + std::to_string(r) + ": need sigma <= spacing <= b_max");
+    if (jitter < 0.0 || (jitter > 0.0 && !(2.0 * jitter < sp.spacing - sigma)))
+      return bfail(ECMC_EINVAL, "jitter must be in [0, (spacing - sigma)/2)");
+    n_total += nb;
+  }
+  if (n_total >= (1ll << 31)) return bfail(ECMC_EINVAL, "at most 2^31 beads in a batch");
+  ecmc_batch *b = new ecmc_batch();
+  b->R = n;
+  b->specs.assign(specs, specs + n);
+  b->sigma = sigma;
+  b->b_max = b_max;
+  b->seed_lattice = seed;
+  b->n_total = n_total;
+  b->reps.resize(n);
+  std::vector<int32_t> rep_of(n_total);
+  int64_t off = 0;
+  for (int32_t r = 0; r < n; ++r) {
+    RepParams &R = b->reps[r];
+    memset(&R, 0, sizeof(R));
+    const ecmc_replica_spec &sp = specs[r];
+    for (int a = 0; a < 3; ++a) {
+      R.L[a] = sp.dims[a] * sp.spacing;
+      R.half[a] = 0.5 * R.L[a];
+    }
+    R.N = sp.N;
+    R.bead_off = off;
+    R.n_beads = (int64_t)sp.dims[0] * sp.dims[1] * sp.dims[2];
+    R.replica = (uint64_t)r;
+    for (int64_t i = 0; i < R.n_beads; ++i) rep_of[off + i] = r;
+    off += R.n_beads;
+  }
+  cudaError_t e = cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaEventCreate(&b->ev0);
+  if (e == cudaSuccess) e = cudaEventCreate(&b->ev1);
+  if (e == cudaSuccess) e = balloc(&b->d_r, 3 * n_total);
+  if (e == cudaSuccess) e = balloc(&b->d_img, 3 * n_total);
+  if (e == cudaSuccess) e = balloc(&b->d_rep_of, n_total);
+  if (e == cudaSuccess) e = balloc(&b->d_tag, n_total);
+  if (e == cudaSuccess) e = balloc(&b->d_cell, n_total);
+  if (e == cudaSuccess) e = balloc(&b->d_rank, n_total);
+  if (e == cudaSuccess) e = balloc(&b->d_cr, 3 * n_total);
+  if (e == cudaSuccess) e = balloc(&b->d_cid, n_total);
+  if (e == cudaSuccess) e = balloc(&b->d_ctag, n_total);
+  if (e == cudaSuccess) e = balloc(&b->d_reps, n);
+  if (e == cudaSuccess) e = balloc(&b->d_cnt, CNT_N);
+  if (e == cudaSuccess) e = balloc(&b->d_sums, SUM_N);
+  if (e == cudaSuccess) e = balloc(&b->d_status, 1);
+  if (e == cudaSuccess) e = balloc(&b->d_sweep, 1);
+  if (e == cudaSuccess) e = cudaMemsetAsync(b->d_img, 0, sizeof(int32_t) * 3 * n_total, b->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(b->d_cnt, 0, sizeof(unsigned long long) * CNT_N, b->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(b->d_sums, 0, sizeof(double) * SUM_N, b->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(b->d_status, 0, sizeof(int), b->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(b->d_rep_of, rep_of.data(), sizeof(int32_t) * n_total,
+                        cudaMemcpyHostToDevice, b->stream);
+  for (int32_t r = 0; r < n && e == cudaSuccess; ++r)
+    e = launch_lattice(specs[r].dims, specs[r].spacing, jitter, seed, (uint64_t)r,
+                       b->d_r + 3 * b->reps[r].bead_off, b->reps[r].n_beads, b->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+  if (e != cudaSuccess) {
+    batch_free(b);
+    return bfail(e == cudaErrorMemoryAllocation ? ECMC_ENOMEM : ECMC_ECUDA,
+                 std::string("batch create: ") + cudaGetErrorString(e));
+  }
+  *out = b;
+  return ECMC_OK;
+}
+
+void ecmc_batch_destroy(ecmc_batch *b) { batch_free(b); }
+
+ecmc_status ecmc_batch_configure(ecmc_batch *b, const ecmc_opts *o) {
+  if (!b || !o) return bfail(ECMC_EINVAL, "NULL argument");
+  ecmc_opts p = *o;
+  if (p.mode != ECMC_MODE_DOMAIN) return bfail(ECMC_EINVAL, "a batch runs in the domain mode");
+  if (p.dir_mode != ECMC_DIR_CART3 && p.dir_mode != ECMC_DIR_ISO) return bfail(ECMC_EINVAL, "bad dir_mode");
+  if (p.precision != ECMC_PREC_FP64 && p.precision != ECMC_PREC_FP32F)
+    return bfail(ECMC_EINVAL, "bad precision");
+  const int lanes = p.lanes ? p.lanes : 8;
+  if (lanes != 32 && lanes != 16 && lanes != 8 && lanes != 4)
+    return bfail(ECMC_EINVAL, "batch lanes must be 4, 8, 16 or 32");
+  if (!(p.p_swap >= 0.0)) return bfail(ECMC_EINVAL, "p_swap must be >= 0");
+  const double sig = b->sigma;
+  const double s_cap = p.s_cap > 0 ? p.s_cap : 0.25 * sig;
+  const double w = p.joint > 0 ? p.joint : b->b_max;
+  if (!(w >= b->b_max)) return bfail(ECMC_EINVAL, "joint width must be >= b_max");
+  const double side = p.cell_side > 0 ? p.cell_side : sig;
+  if (!(side >= sig)) return bfail(ECMC_EINVAL, "cell side must be >= sigma");
+  const double tside = p.tile_side > 0 ? p.tile_side : 4.2 * sig;
+  const double halo_hs = sig * (1.0 + 1e-6);
+  const double halo_te = (b->b_max > sig ? b->b_max : sig) * (1.0 + 1e-6);
+  const double hg = halo_te + 1e-3 * sig;
+  const double reach = s_cap + sig + 0.01 * sig;
+  const double bm = b->b_max * (1.0 + 1e-6);
+  const double side_min = (reach > bm ? reach : bm) + 2e-3 * sig;
+  const double margin = p.precision == ECMC_PREC_FP32F ? 0.01 * sig : 0.0;
+  int64_t cell_off = 0, unit_off = 0;
+  int32_t stage = 0, mcap = 0, nclm = 0;
+  std::vector<RepParams> reps = b->reps;
+  for (int32_t r = 0; r < b->R; ++r) {
+    RepParams &R = reps[r];
+    const double rho = (double)R.n_beads / (R.L[0] * R.L[1] * R.L[2]);
+    int64_t ncl = 1, nce = 1, nt = 1;
+    double vol = 1.0, volm = 1.0;
+    for (int a = 0; a < 3; ++a) {
+      if (!(s_cap + sig + margin < R.half[a]))
+        return bfail(ECMC_EINVAL, "replica " + std::to_string(r) + ": need s_cap + sigma < L/2");
+      int D = p.tiles[a] > 0 ? p.tiles[a] : (int)floor(R.L[a] / tside);
+      if (D < 3) D = 3;
+      // the tile plus its halo must stay below half the box
+      while (D < 1024 && !(R.L[a] / D - w + 2.0 * halo_te < R.half[a])) ++D;
+      const double T = R.L[a] / D, W = T - w;
+      if (!(W > 0.0))
+        return bfail(ECMC_EINVAL, "replica " + std::to_string(r) + ": tile narrower than the joint");
+      if (p.precision == ECMC_PREC_FP32F && !(W + 2.0 * halo_te <= 64.0 * sig))
+        return bfail(ECMC_EINVAL, "FP32 screen needs tiles of at most 64 sigma");
+      R.D[a] = D;
+      R.T[a] = T;
+      R.W[a] = W;
+      int k = (int)floor(R.L[a] / side);
+      if (k < 3) return bfail(ECMC_EINVAL, "replica " + std::to_string(r) + ": box too small");
+      R.nc[a] = k;
+      R.cs[a] = R.L[a] / k;
+      const double E = W + 2.0 * hg;
+      int g = (int)floor(E / side_min);
+      if (g < 1) g = 1;
+      R.lg[a] = g;
+      R.linv[a] = (float)(g / E);
+      ncl *= g;
+      nce *= k;
+      nt *= D;
+      vol *= W + 2.0 * halo_te;
+      volm *= W;
+    }
+    R.lorg = (float)(-hg);
+    R.cell_off = cell_off;
+    R.unit_off = unit_off;
+    cell_off += nce;
+    unit_off += nt;
+    const int32_t st = (int32_t)((rho * vol * 1.3 + 32 + 31) / 32) * 32;
+    const int32_t mc = (int32_t)((rho * volm * 1.3 + 32 + 31) / 32) * 32;
+    stage = st > stage ? st : stage;
+    mcap = mc > mcap ? mc : mcap;
+    nclm = (int32_t)ncl > nclm ? (int32_t)ncl : nclm;
+  }
+  if (p.stage_cap > 0) stage = (p.stage_cap + 31) / 32 * 32;
+  if (mcap > stage) mcap = stage;
+  if (stage > 65534) return bfail(ECMC_EINVAL, "at most 65534 staged beads per tile");
+  if (unit_off >= (1ll << 31)) return bfail(ECMC_EINVAL, "too many tiles");
+  int dev = 0, smem_max = 0;
+  BCU(cudaGetDevice(&dev));
+  BCU(cudaDeviceGetAttribute(&smem_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+  const int M = p.precision == ECMC_PREC_FP32F ? mcap : stage;
+  if ((int64_t)ec_smem_bytes(stage, M, nclm, 32 / lanes) > smem_max)
+    return bfail(ECMC_EINVAL, "staging does not fit in shared memory");
+  // (re)allocate the concatenated cell arrays
+  if (cell_off != b->ncell_total) {
+    cudaFree(b->d_count);
+    cudaFree(b->d_start);
+    cudaFree(b->d_bsum);
+    b->d_count = b->d_start = b->d_bsum = nullptr;
+    BCU(balloc(&b->d_count, cell_off));
+    BCU(balloc(&b->d_start, cell_off + 1));
+    BCU(balloc(&b->d_bsum, cells_scratch_ints(cell_off)));
+    b->ncell_total = cell_off;
+  }
+  b->reps = reps;
+  BCU(cudaMemcpyAsync(b->d_reps, b->reps.data(), sizeof(RepParams) * b->R, cudaMemcpyHostToDevice,
+                      b->stream));
+  BCU(cudaStreamSynchronize(b->stream));
+  b->opts = p;
+  b->opts.lanes = lanes;
+  b->opts.tile_side = tside;
+  b->s_cap = s_cap;
+  b->halo_hs = halo_hs;
+  b->halo_te = halo_te;
+  b->stage_cap = stage;
+  b->m_cap = mcap;
+  b->ncl_max = nclm;
+  b->lanes = lanes;
+  b->ecs_per_tile = p.ecs_per_tile > 0 ? p.ecs_per_tile : 1;
+  b->event_cap = p.event_cap > 0 ? p.event_cap : 10000000;
+  b->units_total = unit_off;
+  b->configured = true;
+  if (b->graph) {
+    cudaGraphExecDestroy(b->graph);
+    b->graph = nullptr;
+  }
+  return ECMC_OK;
+}
+
+ecmc_status ecmc_batch_run(ecmc_batch *b, double ell, uint64_t seed, int64_t n_sweeps,
+                           int32_t use_graph) {
+  if (!b) return bfail(ECMC_EINVAL, "batch is NULL");
+  if (!b->configured) return bfail(ECMC_EINVAL, "call ecmc_batch_configure first");
+  if (!(ell >= 0.0) || !isfinite(ell) || n_sweeps < 0) return bfail(ECMC_EINVAL, "bad ell or n_sweeps");
+  const bool rec = b->opts.record != 0;
+  ECParams P = batch_params(b, seed, ell);
+  if (rec) {
+    const int64_t units = n_sweeps * b->units_total * b->ecs_per_tile;
+    if (units > b->rec_cap) {
+      cudaFree(b->d_rdig);
+      cudaFree(b->d_rlift);
+      cudaFree(b->d_rev);
+      b->d_rdig = nullptr;
+      b->d_rlift = nullptr;
+      b->d_rev = nullptr;
+      b->rec_cap = 0;
+      BCU(balloc(&b->d_rdig, units));
+      BCU(balloc(&b->d_rlift, units));
+      BCU(balloc(&b->d_rev, units));
+      b->rec_cap = units;
+    }
+    BCU(cudaMemsetAsync(b->d_rdig, 0, sizeof(uint64_t) * (units ? units : 1), b->stream));
+    b->rec_n = units;
+    P.rec_digest = b->d_rdig;
+    P.rec_lift = b->d_rlift;
+    P.rec_events = b->d_rev;
+    P.rec_cap = b->rec_cap;
+    P.rec_sweep0 = b->sweeps_done;
+  }
+  BCU(cudaMemsetAsync(b->d_status, 0, sizeof(int), b->stream));
+  BCU(cudaMemcpyAsync(b->d_sweep, &b->sweeps_done, sizeof(int64_t), cudaMemcpyHostToDevice,
+                      b->stream));
+  BCU(cudaEventRecord(b->ev0, b->stream));
+  if (use_graph && n_sweeps > 0) {
+    // records bake their buffers and sweep base into the graph: recapture
+    const bool fresh = rec || !b->graph || b->graph_ell != ell || b->graph_seed != seed ||
+                       b->graph_rec != rec;
+    int64_t done = 0;
+    if (fresh) {
+      if (b->graph) {
+        cudaGraphExecDestroy(b->graph);
+        b->graph = nullptr;
+      }
+      // first sweep uncaptured: kernel attributes and block sizes are
+      // settled outside the capture
+      BCU(batch_sweep(b, P, seed));
+      done = 1;
+      cudaGraph_t g = nullptr;
+      BCU(cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeRelaxed));
+      cudaError_t e = batch_sweep(b, P, seed);
+      cudaError_t e2 = cudaStreamEndCapture(b->stream, &g);
+      if (e != cudaSuccess || e2 != cudaSuccess) {
+        if (g) cudaGraphDestroy(g);
+        return bfail(ECMC_ECUDA, std::string("graph capture: ") +
+                                     cudaGetErrorString(e != cudaSuccess ? e : e2));
+      }
+      e = cudaGraphInstantiate(&b->graph, g, 0);
+      cudaGraphDestroy(g);
+      if (e != cudaSuccess) return bfail(ECMC_ECUDA, std::string("graph: ") + cudaGetErrorString(e));
+      b->graph_ell = ell;
+      b->graph_seed = seed;
+      b->graph_rec = rec;
+      b->graph_rec_sweep0 = b->sweeps_done;
+    }
+    for (int64_t s = done; s < n_sweeps; ++s) BCU(cudaGraphLaunch(b->graph, b->stream));
+  } else {
+    for (int64_t s = 0; s < n_sweeps; ++s) BCU(batch_sweep(b, P, seed));
+  }
+  BCU(cudaEventRecord(b->ev1, b->stream));
+  ecmc_status st = batch_status(b);
+  float ms = 0.f;
+  BCU(cudaEventElapsedTime(&ms, b->ev0, b->ev1));
+  b->device_seconds += 1e-3 * ms;
+  b->sweeps_done += n_sweeps;
+  return st;
+}
+
+ecmc_status ecmc_batch_get_positions(ecmc_batch *b, int32_t replica, double *xyz, int32_t *img) {
+  if (!b || !xyz || replica < 0 || replica >= b->R) return bfail(ECMC_EINVAL, "bad argument");
+  const RepParams &R = b->reps[replica];
+  BCU(cudaMemcpyAsync(xyz, b->d_r + 3 * R.bead_off, sizeof(double) * 3 * R.n_beads,
+                      cudaMemcpyDeviceToHost, b->stream));
+  if (img)
+    BCU(cudaMemcpyAsync(img, b->d_img + 3 * R.bead_off, sizeof(int32_t) * 3 * R.n_beads,
+                        cudaMemcpyDeviceToHost, b->stream));
+  BCU(cudaStreamSynchronize(b->stream));
+  return ECMC_OK;
+}
+
+ecmc_status ecmc_batch_info(ecmc_batch *b, int32_t replica, int32_t tiles[3], int64_t *unit_off,
+                            int64_t *n_beads) {
+  if (!b || replica < 0 || replica >= b->R) return bfail(ECMC_EINVAL, "bad argument");
+  const RepParams &R = b->reps[replica];
+  if (tiles)
+    for (int a = 0; a < 3; ++a) tiles[a] = R.D[a];
+  if (unit_off) *unit_off = R.unit_off;
+  if (n_beads) *n_beads = R.n_beads;
+  return ECMC_OK;
+}
+
+ecmc_status ecmc_batch_stats(ecmc_batch *b, int64_t *events_total, int64_t *ecs,
+                             double *device_seconds) {
+  if (!b) return bfail(ECMC_EINVAL, "batch is NULL");
+  unsigned long long h[CNT_N];
+  BCU(cudaMemcpyAsync(h, b->d_cnt, sizeof(h), cudaMemcpyDeviceToHost, b->stream));
+  BCU(cudaStreamSynchronize(b->stream));
+  if (events_total) *events_total = (int64_t)h[CNT_EVENTS];
+  if (ecs) *ecs = (int64_t)h[CNT_ECS];
+  if (device_seconds) *device_seconds = b->device_seconds;
+  return ECMC_OK;
+}
+
+ecmc_status ecmc_batch_records(ecmc_batch *b, uint64_t *digest, double *lift, int64_t *events,
+                               int64_t *n) {
+  if (!b || !n) return bfail(ECMC_EINVAL, "NULL argument");
+  if (!b->d_rdig) {
+    *n = 0;
+    return ECMC_OK;
+  }
+  const int64_t cnt = b->rec_n < *n ? b->rec_n : *n;
+  if (digest) BCU(cudaMemcpyAsync(digest, b->d_rdig, sizeof(uint64_t) * cnt, cudaMemcpyDeviceToHost, b->stream));
+  if (lift) BCU(cudaMemcpyAsync(lift, b->d_rlift, sizeof(double) * cnt, cudaMemcpyDeviceToHost, b->stream));
+  if (events) BCU(cudaMemcpyAsync(events, b->d_rev, sizeof(int64_t) * cnt, cudaMemcpyDeviceToHost, b->stream));
+  BCU(cudaStreamSynchronize(b->stream));
+  *n = cnt;
+  return ECMC_OK;
+}
+
+}  // extern "C"

@@ -20,6 +20,22 @@ enum : int {
 };
 enum : int { SUM_LIFT = 0, SUM_REFL = 1, SUM_DISP = 2, SUM_N = 3 };
 
+// One replica of a batch (device table): its box, tiles, cell grids, chain
+// length, where its beads, cells and tiles start in the concatenated arrays,
+// and its Philox key word.
+struct RepParams {
+  double L[3], half[3], T[3], W[3], cs[3];
+  int32_t D[3], nc[3], lg[3];
+  float linv[3], lorg;
+  int32_t N;
+  int32_t pad;
+  int64_t bead_off;   // first bead in the concatenated position array
+  int64_t cell_off;   // first cell in the concatenated cell arrays
+  int64_t unit_off;   // first tile in the concatenated tile numbering
+  int64_t n_beads;
+  uint64_t replica;   // Philox key word 1
+};
+
 // Everything one EC launch needs, by value.
 struct ECParams {
   // system
@@ -69,6 +85,14 @@ struct ECParams {
   ecmc_event *log;
   unsigned long long *log_n;
   int64_t log_cap;
+  // batch: replica table (units are the concatenated tiles of all replicas),
+  // the sweep counter on the device (graph replays advance it), and the
+  // largest local grid over the replicas
+  const RepParams *reps;
+  int32_t n_reps;
+  int32_t ncl_max;
+  const int64_t *sweep_dev;
+  int64_t rec_sweep0;
   // one-lane-per-tile kernel: per-tile scratch and its local cell grid
   unsigned char *scratch;
   int64_t tile_bytes;
@@ -82,6 +106,7 @@ void set_last_error(const char *msg);
 
 // launchers (k_ec.cu, k_ec_lane.cu)
 cudaError_t launch_ec(const ECParams &P, int lanes, int fp32f, cudaStream_t s);
+cudaError_t launch_ec_batch(const ECParams &P, int lanes, int fp32f, cudaStream_t s);
 size_t ec_smem_bytes(int stage_cap, int motile_cap, int ncell, int groups_per_block);
 cudaError_t launch_ec_lane(const ECParams &P, int fp32f, cudaStream_t s);
 size_t lane_tile_bytes(int stage_cap, int ncell);
@@ -109,6 +134,28 @@ struct CellParams {
   int32_t *ctag;
 };
 cudaError_t launch_cells(const CellParams &C, int64_t ncell, cudaStream_t s);
+
+// the same for a batch: all replicas' beads at once (per-bead replica index,
+// replica table), concatenated cell grids, one counting sort
+struct CellBatch {
+  int64_t n;                 // beads over all replicas
+  const double *r;
+  const int32_t *rep_of;     // replica of each bead
+  const RepParams *reps;
+  uint64_t seed;
+  const int64_t *sweep_dev;  // sweep counter on the device
+  int32_t *tag;
+  int32_t *cell;
+  int32_t *rank;
+  int32_t *count;
+  int32_t *start;
+  int32_t *block_sums;
+  double *cr;
+  int32_t *cid;              // id within the replica
+  int32_t *ctag;
+};
+cudaError_t launch_cells_batch(const CellBatch &C, int64_t ncell_total, cudaStream_t s);
+cudaError_t launch_sweep_advance(int64_t *sweep_dev, cudaStream_t s);
 size_t cells_scratch_ints(int64_t ncell);
 
 // observables (k_obs.cu)

@@ -145,7 +145,69 @@ __global__ void k_scatter(const CellParams C) {
   C.ctag[pos] = C.tag[b];
 }
 
+__global__ void k_tag_count_b(const CellBatch C) {
+  const int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= C.n) return;
+  const RepParams &R = C.reps[C.rep_of[b]];
+  const double rr[3] = {C.r[3 * b], C.r[3 * b + 1], C.r[3 * b + 2]};
+  const u64x4 w = philox(TAG_SHIFT, (uint64_t)*C.sweep_dev, 0, 0, C.seed, R.replica);
+  int k[3], c[3];
+  bool in = true;
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    const double o = unit53(w.v[a]) * R.T[a];
+    double u = rr[a] - o;
+    if (u < 0.0) u = u + R.L[a];
+    if (u >= R.L[a]) u = u - R.L[a];
+    int t = (int)(u / R.T[a]);
+    if (t > R.D[a] - 1) t = R.D[a] - 1;
+    const double loc = u - (double)t * R.T[a];
+    in = in && (loc < R.W[a]);
+    k[a] = t;
+    int q = (int)(rr[a] / R.cs[a]);
+    if (q >= R.nc[a]) q = R.nc[a] - 1;
+    if (q < 0) q = 0;
+    c[a] = q;
+  }
+  C.tag[b] = in ? (k[2] * R.D[1] + k[1]) * R.D[0] + k[0] : -1;
+  const int64_t cell = R.cell_off + (c[2] * R.nc[1] + c[1]) * R.nc[0] + c[0];
+  C.cell[b] = (int32_t)cell;
+  C.rank[b] = atomicAdd(&C.count[cell], 1);
+}
+
+__global__ void k_scatter_b(const CellBatch C) {
+  const int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= C.n) return;
+  const int64_t pos = (int64_t)C.start[C.cell[b]] + C.rank[b];
+  C.cr[3 * pos] = C.r[3 * b];
+  C.cr[3 * pos + 1] = C.r[3 * b + 1];
+  C.cr[3 * pos + 2] = C.r[3 * b + 2];
+  C.cid[pos] = (int32_t)(b - C.reps[C.rep_of[b]].bead_off);
+  C.ctag[pos] = C.tag[b];
+}
+
+__global__ void k_sweep_advance(int64_t *sweep) { *sweep += 1; }
+
 }  // namespace
+
+cudaError_t launch_cells_batch(const CellBatch &C, int64_t ncell, cudaStream_t s) {
+  cudaError_t e = cudaMemsetAsync(C.count, 0, sizeof(int32_t) * ncell, s);
+  if (e != cudaSuccess) return e;
+  const int T = 256;
+  const int64_t nb = (C.n + T - 1) / T;
+  if (C.n > 0) k_tag_count_b<<<(unsigned)nb, T, 0, s>>>(C);
+  const int64_t tiles = (ncell + SCAN_TILE - 1) / SCAN_TILE;
+  k_scan_tiles<<<(unsigned)tiles, SCAN_BLOCK, 0, s>>>(C.count, ncell, C.start, C.block_sums);
+  k_scan_sums<<<1, SCAN_BLOCK, 0, s>>>(C.block_sums, tiles, C.start + ncell);
+  k_scan_add<<<(unsigned)((ncell + 255) / 256), 256, 0, s>>>(C.start, ncell, C.block_sums);
+  if (C.n > 0) k_scatter_b<<<(unsigned)nb, T, 0, s>>>(C);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_sweep_advance(int64_t *sweep_dev, cudaStream_t s) {
+  k_sweep_advance<<<1, 1, 0, s>>>(sweep_dev);
+  return cudaGetLastError();
+}
 
 size_t cells_scratch_ints(int64_t ncell) { return (size_t)((ncell + SCAN_TILE - 1) / SCAN_TILE) + 1; }
 

@@ -318,7 +318,7 @@ __device__ __forceinline__ float screen_lb(const Screen &Z, float d0, float d1, 
 
 // FP64 position of staged slot k: shared memory for the first M slots,
 // otherwise (a joint bead, static this sweep) the global position array
-__device__ __forceinline__ void pos64(const Stage &st, const ECParams &P, int k, bool in_smem,
+__device__ __forceinline__ void pos64(const Stage &st, const double *r, int k, bool in_smem,
                                       double &x, double &y, double &z) {
   if (in_smem) {
     x = st.px[k];
@@ -326,13 +326,13 @@ __device__ __forceinline__ void pos64(const Stage &st, const ECParams &P, int k,
     z = st.pz[k];
   } else {
     const int64_t b = st.id[k];
-    x = P.r[3 * b];
-    y = P.r[3 * b + 1];
-    z = P.r[3 * b + 2];
+    x = r[3 * b];
+    y = r[3 * b + 1];
+    z = r[3 * b + 2];
   }
 }
 
-template <int G, bool F32>
+template <int G, bool F32, bool BATCH>
 __global__ void __launch_bounds__(128) ec_kernel(const ECParams P) {
   extern __shared__ __align__(16) unsigned char smem[];
   const int lane = threadIdx.x & 31;
@@ -340,33 +340,52 @@ __global__ void __launch_bounds__(128) ec_kernel(const ECParams P) {
   const int gbase = lane & ~(G - 1);
   const int gib = threadIdx.x / G;
   const int gpb = blockDim.x / G;
-  const int unit = blockIdx.x * gpb + gib;
+  const int gunit = blockIdx.x * gpb + gib;  // unit over all replicas
+  // the replica of this unit (batch) and the unit's tile within it
+  const RepParams *rp = nullptr;
+  int unit = gunit;
+  if (BATCH) {
+    int lo = 0, hi = P.n_reps - 1;
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (P.reps[mid].unit_off <= gunit) lo = mid;
+      else hi = mid - 1;
+    }
+    rp = P.reps + lo;
+    unit = gunit - (int)rp->unit_off;
+  }
+#define SYS(f) (BATCH ? rp->f : P.f)
+  double *const Rr = BATCH ? P.r + 3 * rp->bead_off : P.r;
+  int32_t *const Ri = BATCH ? P.img + 3 * rp->bead_off : P.img;
+  const int32_t *const Rstart = BATCH ? P.cstart + rp->cell_off : P.cstart;
+  const uint64_t Rkey = BATCH ? rp->replica : P.replica;
+  const int64_t sweep = P.sweep_dev ? *P.sweep_dev : P.sweep;
   const int S = P.stage_cap;
-  const int NC = P.domain ? P.lg[0] * P.lg[1] * P.lg[2] : 0;
+  const int NC = P.domain ? (BATCH ? P.ncl_max : SYS(lg)[0] * SYS(lg)[1] * SYS(lg)[2]) : 0;
   const int M = (F32 && P.domain) ? P.m_cap : S;
   Stage st = carve(smem + (size_t)gib * group_bytes(S, M, NC), S, M, NC);
-  bool live = unit < P.n_units;
-  const uint64_t hb0 = dbits(P.half[0]), hb1 = dbits(P.half[1]), hb2 = dbits(P.half[2]);
+  bool live = gunit < P.n_units;
+  const uint64_t hb0 = dbits(SYS(half)[0]), hb1 = dbits(SYS(half)[1]), hb2 = dbits(SYS(half)[2]);
   LGrid LG;
-  LG.g0 = P.lg[0];
-  LG.g1 = P.lg[1];
-  LG.g2 = P.lg[2];
-  LG.org = P.lorg;
-  LG.inv0 = P.linv[0];
-  LG.inv1 = P.linv[1];
-  LG.inv2 = P.linv[2];
+  LG.g0 = SYS(lg)[0];
+  LG.g1 = SYS(lg)[1];
+  LG.g2 = SYS(lg)[2];
+  LG.org = SYS(lorg);
+  LG.inv0 = SYS(linv)[0];
+  LG.inv1 = SYS(linv)[1];
+  LG.inv2 = SYS(linv)[2];
 
   // tile geometry (domain) or the whole box (serial); corner = shift + k T
   int tk[3] = {0, 0, 0};
   double c0 = 0.0, c1 = 0.0, c2 = 0.0;
   if (P.domain && live) {
-    tk[0] = unit % P.D[0];
-    tk[1] = (unit / P.D[0]) % P.D[1];
-    tk[2] = unit / (P.D[0] * P.D[1]);
-    const u64x4 w = philox(TAG_SHIFT, (uint64_t)P.sweep, 0, 0, P.seed, P.replica);
-    c0 = unit53(w.v[0]) * P.T[0] + (double)tk[0] * P.T[0];
-    c1 = unit53(w.v[1]) * P.T[1] + (double)tk[1] * P.T[1];
-    c2 = unit53(w.v[2]) * P.T[2] + (double)tk[2] * P.T[2];
+    tk[0] = unit % SYS(D)[0];
+    tk[1] = (unit / SYS(D)[0]) % SYS(D)[1];
+    tk[2] = unit / (SYS(D)[0] * SYS(D)[1]);
+    const u64x4 w = philox(TAG_SHIFT, (uint64_t)sweep, 0, 0, P.seed, Rkey);
+    c0 = unit53(w.v[0]) * SYS(T)[0] + (double)tk[0] * SYS(T)[0];
+    c1 = unit53(w.v[1]) * SYS(T)[1] + (double)tk[1] * SYS(T)[1];
+    c2 = unit53(w.v[2]) * SYS(T)[2] + (double)tk[2] * SYS(T)[2];
   }
 
   // ------------------------------------------------------------ staging
@@ -381,7 +400,7 @@ __global__ void __launch_bounds__(128) ec_kernel(const ECParams P) {
     // serial: every bead, slot = id, all motile
     const int n = (int)P.n;
     for (int b = gl; b < n; b += G) {
-      const double x = P.r[3 * (int64_t)b], y = P.r[3 * (int64_t)b + 1], z = P.r[3 * (int64_t)b + 2];
+      const double x = Rr[3 * (int64_t)b], y = Rr[3 * (int64_t)b + 1], z = Rr[3 * (int64_t)b + 2];
       st.px[b] = x;
       st.py[b] = y;
       st.pz[b] = z;
@@ -389,8 +408,8 @@ __global__ void __launch_bounds__(128) ec_kernel(const ECParams P) {
       st.fy[b] = (float)y;
       st.fz[b] = (float)z;
       st.id[b] = b;
-      const int c = b % P.N;
-      st.nb[b] = nb_pack(c == 0 ? -1 : b - 1, c == P.N - 1 ? -1 : b + 1);
+      const int c = b % SYS(N);
+      st.nb[b] = nb_pack(c == 0 ? -1 : b - 1, c == SYS(N) - 1 ? -1 : b + 1);
     }
     m = n;
     j1 = 0;
@@ -401,13 +420,13 @@ __global__ void __launch_bounds__(128) ec_kernel(const ECParams P) {
     int c_lo[3], c_n[3];
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
-      const double lo = corner[a] - P.halo_te, hi = corner[a] + P.W[a] + P.halo_te;
-      int l = (int)floor(lo / P.cs[a]);
-      const int h = (int)floor(hi / P.cs[a]);
+      const double lo = corner[a] - P.halo_te, hi = corner[a] + SYS(W)[a] + P.halo_te;
+      int l = (int)floor(lo / SYS(cs)[a]);
+      const int h = (int)floor(hi / SYS(cs)[a]);
       int cnt = h - l + 1;
-      if (cnt >= P.nc[a]) {
+      if (cnt >= SYS(nc)[a]) {
         l = 0;
-        cnt = P.nc[a];
+        cnt = SYS(nc)[a];
       }
       c_lo[a] = l;
       c_n[a] = live ? cnt : 0;
@@ -421,14 +440,14 @@ __global__ void __launch_bounds__(128) ec_kernel(const ECParams P) {
       const int q = q0 + gl;
       if (q < ncell) {
         const int qx = q % c_n[0], qy = (q / c_n[0]) % c_n[1], qz = q / (c_n[0] * c_n[1]);
-        int cx = (c_lo[0] + qx) % P.nc[0];
-        int cy = (c_lo[1] + qy) % P.nc[1];
-        int cz = (c_lo[2] + qz) % P.nc[2];
-        if (cx < 0) cx += P.nc[0];
-        if (cy < 0) cy += P.nc[1];
-        if (cz < 0) cz += P.nc[2];
-        const int cell = (cz * P.nc[1] + cy) * P.nc[0] + cx;
-        const int j0 = P.cstart[cell], jend = P.cstart[cell + 1];
+        int cx = (c_lo[0] + qx) % SYS(nc)[0];
+        int cy = (c_lo[1] + qy) % SYS(nc)[1];
+        int cz = (c_lo[2] + qz) % SYS(nc)[2];
+        if (cx < 0) cx += SYS(nc)[0];
+        if (cy < 0) cy += SYS(nc)[1];
+        if (cz < 0) cz += SYS(nc)[2];
+        const int cell = (cz * SYS(nc)[1] + cy) * SYS(nc)[0] + cx;
+        const int j0 = Rstart[cell], jend = Rstart[cell + 1];
         for (int j = j0; j < jend; ++j) {
           const int tg = P.ctag[j];
           int cat = -1;
@@ -438,9 +457,9 @@ __global__ void __launch_bounds__(128) ec_kernel(const ECParams P) {
             bool in_hs = true, in_te = true;
 #pragma unroll
             for (int a = 0; a < 3; ++a) {
-              const double s = wrap_d(P.cr[3 * (int64_t)j + a] - corner[a], P.L[a], P.half[a]);
-              in_hs = in_hs && (s >= -P.halo_hs) && (s <= P.W[a] + P.halo_hs);
-              in_te = in_te && (s >= -P.halo_te) && (s <= P.W[a] + P.halo_te);
+              const double s = wrap_d(P.cr[3 * (int64_t)j + a] - corner[a], SYS(L)[a], SYS(half)[a]);
+              in_hs = in_hs && (s >= -P.halo_hs) && (s <= SYS(W)[a] + P.halo_hs);
+              in_te = in_te && (s >= -P.halo_te) && (s <= SYS(W)[a] + P.halo_te);
             }
             cat = in_hs ? 1 : (in_te ? 2 : -1);
           }
@@ -498,21 +517,21 @@ __global__ void __launch_bounds__(128) ec_kernel(const ECParams P) {
       const int s = s0 + gl;
       if (s < ns && live) {
         double x, y, z;
-        pos64(st, P, s, s < M, x, y, z);
-        st.fx[s] = (float)wrap_d(x - corner[0], P.L[0], P.half[0]);
-        st.fy[s] = (float)wrap_d(y - corner[1], P.L[1], P.half[1]);
-        st.fz[s] = (float)wrap_d(z - corner[2], P.L[2], P.half[2]);
+        pos64(st, Rr, s, s < M, x, y, z);
+        st.fx[s] = (float)wrap_d(x - corner[0], SYS(L)[0], SYS(half)[0]);
+        st.fy[s] = (float)wrap_d(y - corner[1], SYS(L)[1], SYS(half)[1]);
+        st.fz[s] = (float)wrap_d(z - corner[2], SYS(L)[2], SYS(half)[2]);
         int prev = -1, next = -1;
         if (s < m) {
           const int id = st.id[s];
-          const int c = id % P.N;
+          const int c = id % SYS(N);
           if (c != 0) {
             prev = find_id(st.id, 0, m, id - 1);
             if (prev < 0) prev = find_id(st.id, m, m + j1, id - 1);
             if (prev < 0) prev = find_id(st.id, m + j1, ns, id - 1);
             if (prev < 0) set_status(P.status, DEV_TILE);
           }
-          if (c != P.N - 1) {
+          if (c != SYS(N) - 1) {
             next = find_id(st.id, 0, m, id + 1);
             if (next < 0) next = find_id(st.id, m, m + j1, id + 1);
             if (next < 0) next = find_id(st.id, m + j1, ns, id + 1);
@@ -547,12 +566,12 @@ __global__ void __launch_bounds__(128) ec_kernel(const ECParams P) {
   // periodic image.  Those axes skip the wrap code entirely.
   bool wr0 = true, wr1 = true, wr2 = true;
   if (P.domain) {
-    wr0 = !(c0 - P.halo_te > 0.0 && c0 + P.W[0] + P.halo_te < P.L[0]);
-    wr1 = !(c1 - P.halo_te > 0.0 && c1 + P.W[1] + P.halo_te < P.L[1]);
-    wr2 = !(c2 - P.halo_te > 0.0 && c2 + P.W[2] + P.halo_te < P.L[2]);
+    wr0 = !(c0 - P.halo_te > 0.0 && c0 + SYS(W)[0] + P.halo_te < SYS(L)[0]);
+    wr1 = !(c1 - P.halo_te > 0.0 && c1 + SYS(W)[1] + P.halo_te < SYS(L)[1]);
+    wr2 = !(c2 - P.halo_te > 0.0 && c2 + SYS(W)[2] + P.halo_te < SYS(L)[2]);
   }
   const float cf0 = (float)c0, cf1 = (float)c1, cf2 = (float)c2;
-  const float Lh0 = 0.5f * (float)P.L[0], Lh1 = 0.5f * (float)P.L[1], Lh2 = 0.5f * (float)P.L[2];
+  const float Lh0 = 0.5f * (float)SYS(L)[0], Lh1 = 0.5f * (float)SYS(L)[1], Lh2 = 0.5f * (float)SYS(L)[2];
   const int n_ec = P.ecs_per_tile;
   Screen Z;
   Z.sig2f = (float)P.sig2;
@@ -564,8 +583,8 @@ __global__ void __launch_bounds__(128) ec_kernel(const ECParams P) {
   }
   const float b2f = (float)P.b2;
   const float eps_v = P.eps_v, eps_d = P.eps_d;
-  const float Lf0 = (float)P.L[0], Lf1 = (float)P.L[1], Lf2 = (float)P.L[2];
-  const float Wf0 = (float)P.W[0], Wf1 = (float)P.W[1], Wf2 = (float)P.W[2];
+  const float Lf0 = (float)SYS(L)[0], Lf1 = (float)SYS(L)[1], Lf2 = (float)SYS(L)[2];
+  const float Wf0 = (float)SYS(W)[0], Wf1 = (float)SYS(W)[1], Wf2 = (float)SYS(W)[2];
   const float INF = __int_as_float(0x7f800000);
   const double DINF = __longlong_as_double(0x7ff0000000000000ll);
   double lift_all = 0.0, refl_all = 0.0, disp_all = 0.0;
@@ -578,12 +597,12 @@ __global__ void __launch_bounds__(128) ec_kernel(const ECParams P) {
   for (int e = 0; e < n_ec; ++e) {
     bool active = live && m > 0;
     const uint64_t r0 = P.domain ? (TAG_START | ((uint64_t)e << 8)) : TAG_START;
-    const uint64_t r1 = P.domain ? (uint64_t)P.sweep : 0;
-    const uint64_t r2 = P.domain ? (uint64_t)unit : (uint64_t)(P.sweep + e);
+    const uint64_t r1 = P.domain ? (uint64_t)sweep : 0;
+    const uint64_t r2 = P.domain ? (uint64_t)unit : (uint64_t)(sweep + e);
     int p = 0;
     double v0 = 0.0, v1 = 0.0, v2 = 0.0;
     if (active) {
-      u64x4 w = philox(r0, r1, r2, 0, P.seed, P.replica);
+      u64x4 w = philox(r0, r1, r2, 0, P.seed, Rkey);
       p = (int)scale_below(w.v[0], (uint64_t)m);
       if (P.dir_mode == ECMC_DIR_CART3) {
         const int ax = (int)scale_below(w.v[1], 3);
@@ -605,7 +624,7 @@ __global__ void __launch_bounds__(128) ec_kernel(const ECParams P) {
             break;
           }
           ++att;
-          w = philox(r0, r1, r2, att, P.seed, P.replica);
+          w = philox(r0, r1, r2, att, P.seed, Rkey);
           a = 2.0 * unit53(w.v[0]) - 1.0;
           b = 2.0 * unit53(w.v[1]) - 1.0;
           c = 2.0 * unit53(w.v[2]) - 1.0;
@@ -661,9 +680,9 @@ __global__ void __launch_bounds__(128) ec_kernel(const ECParams P) {
           if (t < 0) continue;
           if (!F32) {
             double dv;
-            const double x = quad_x(true, wrapc(q0 - st.px[t], P.L[0], hb0, wr0),
-                                    wrapc(q1 - st.py[t], P.L[1], hb1, wr1),
-                                    wrapc(q2 - st.pz[t], P.L[2], hb2, wr2), v0, v1, v2, P.b2, dv);
+            const double x = quad_x(true, wrapc(q0 - st.px[t], SYS(L)[0], hb0, wr0),
+                                    wrapc(q1 - st.py[t], SYS(L)[1], hb1, wr1),
+                                    wrapc(q2 - st.pz[t], SYS(L)[2], hb2, wr2), v0, v1, v2, P.b2, dv);
             const uint64_t key = make_key(KIND_TETHER, st.id[t], t);
             if (better(x, key, bx, bkey)) {
               bx = x;
@@ -694,9 +713,9 @@ __global__ void __launch_bounds__(128) ec_kernel(const ECParams P) {
           if (!F32) {
             const double qa = a == 0 ? q0 : (a == 1 ? q1 : q2);
             const double ca = a == 0 ? c0 : (a == 1 ? c1 : c2);
-            const double loc = wrapc(qa - ca, P.L[a], a == 0 ? hb0 : (a == 1 ? hb1 : hb2),
+            const double loc = wrapc(qa - ca, SYS(L)[a], a == 0 ? hb0 : (a == 1 ? hb1 : hb2),
                                      a == 0 ? wr0 : (a == 1 ? wr1 : wr2));
-            double x = posv(va) ? (P.W[a] - loc) / va : (0.0 - loc) / va;
+            double x = posv(va) ? (SYS(W)[a] - loc) / va : (0.0 - loc) / va;
             if (neg(x)) x = 0.0;
             const uint64_t key = make_key(KIND_WALL, a, 0);
             if (better(x, key, bx, bkey)) {
@@ -745,9 +764,9 @@ __global__ void __launch_bounds__(128) ec_kernel(const ECParams P) {
             if (k == p) continue;
             if (!F32) {
               double dv;
-              const double x = quad_x(false, wrapc(q0 - st.px[k], P.L[0], hb0, wr0),
-                                      wrapc(q1 - st.py[k], P.L[1], hb1, wr1),
-                                      wrapc(q2 - st.pz[k], P.L[2], hb2, wr2), v0, v1, v2, P.sig2, dv);
+              const double x = quad_x(false, wrapc(q0 - st.px[k], SYS(L)[0], hb0, wr0),
+                                      wrapc(q1 - st.py[k], SYS(L)[1], hb1, wr1),
+                                      wrapc(q2 - st.pz[k], SYS(L)[2], hb2, wr2), v0, v1, v2, P.sig2, dv);
               if (!neg(x)) {
                 const uint64_t key = make_key(KIND_HS, st.id[k], k);
                 if (better(x, key, bx, bkey)) {
@@ -768,9 +787,9 @@ __global__ void __launch_bounds__(128) ec_kernel(const ECParams P) {
           if (!(active && k < nhs && k != p)) continue;
           if (!F32) {
             double dv;
-            const double x = quad_x(false, wrapc(q0 - st.px[k], P.L[0], hb0, wr0),
-                                    wrapc(q1 - st.py[k], P.L[1], hb1, wr1),
-                                    wrapc(q2 - st.pz[k], P.L[2], hb2, wr2), v0, v1, v2, P.sig2, dv);
+            const double x = quad_x(false, wrapc(q0 - st.px[k], SYS(L)[0], hb0, wr0),
+                                    wrapc(q1 - st.py[k], SYS(L)[1], hb1, wr1),
+                                    wrapc(q2 - st.pz[k], SYS(L)[2], hb2, wr2), v0, v1, v2, P.sig2, dv);
             if (!neg(x)) {
               const uint64_t key = make_key(KIND_HS, st.id[k], k);
               if (better(x, key, bx, bkey)) {
@@ -809,9 +828,9 @@ __global__ void __launch_bounds__(128) ec_kernel(const ECParams P) {
             const bool te = (jb >> 30) & 1;
             const int k = jb & 0x3FFFFFFF;
             double kx, ky, kz, dv;
-            pos64(st, P, k, !F32 || k < m, kx, ky, kz);
-            const double x = quad_x(te, wrapc(q0 - kx, P.L[0], hb0, wr0), wrapc(q1 - ky, P.L[1], hb1, wr1),
-                                    wrapc(q2 - kz, P.L[2], hb2, wr2), v0, v1, v2,
+            pos64(st, Rr, k, !F32 || k < m, kx, ky, kz);
+            const double x = quad_x(te, wrapc(q0 - kx, SYS(L)[0], hb0, wr0), wrapc(q1 - ky, SYS(L)[1], hb1, wr1),
+                                    wrapc(q2 - kz, SYS(L)[2], hb2, wr2), v0, v1, v2,
                                     te ? P.b2 : P.sig2, dv);
             ++confirmed;
             if (!neg(x)) {
@@ -831,9 +850,9 @@ __global__ void __launch_bounds__(128) ec_kernel(const ECParams P) {
           const double va = a == 0 ? v0 : (a == 1 ? v1 : v2);
           const double qa = a == 0 ? q0 : (a == 1 ? q1 : q2);
           const double ca = a == 0 ? c0 : (a == 1 ? c1 : c2);
-          const double loc = wrapc(qa - ca, P.L[a], a == 0 ? hb0 : (a == 1 ? hb1 : hb2),
+          const double loc = wrapc(qa - ca, SYS(L)[a], a == 0 ? hb0 : (a == 1 ? hb1 : hb2),
                                      a == 0 ? wr0 : (a == 1 ? wr1 : wr2));
-          double x = posv(va) ? (P.W[a] - loc) / va : (0.0 - loc) / va;
+          double x = posv(va) ? (SYS(W)[a] - loc) / va : (0.0 - loc) / va;
           if (neg(x)) x = 0.0;
           ++confirmed;
           const uint64_t key = make_key(KIND_WALL, a, 0);
@@ -856,9 +875,9 @@ __global__ void __launch_bounds__(128) ec_kernel(const ECParams P) {
             const float lb = screen_lb(Z, d0, d1, d2, vf0, vf1, vf2, possible);
             if (!possible || lb > U) return;
             double kx, ky, kz, dvx;
-            pos64(st, P, k, !F32 || k < m, kx, ky, kz);
-            const double x = quad_x(false, wrapc(q0 - kx, P.L[0], hb0, wr0),
-                                    wrapc(q1 - ky, P.L[1], hb1, wr1), wrapc(q2 - kz, P.L[2], hb2, wr2),
+            pos64(st, Rr, k, !F32 || k < m, kx, ky, kz);
+            const double x = quad_x(false, wrapc(q0 - kx, SYS(L)[0], hb0, wr0),
+                                    wrapc(q1 - ky, SYS(L)[1], hb1, wr1), wrapc(q2 - kz, SYS(L)[2], hb2, wr2),
                                     v0, v1, v2, P.sig2, dvx);
             ++confirmed;
             if (!neg(x)) {
@@ -908,16 +927,16 @@ __global__ void __launch_bounds__(128) ec_kernel(const ECParams P) {
         const int slot = key_slot(bkey);
         const int64_t partner = (kind == KIND_END || kind == KIND_PASS) ? -1 : key_id(bkey);
         int di0 = 0, di1 = 0, di2 = 0;
-        if (wr0) di0 = step_i(q0, x, v0, P.L[0]);
+        if (wr0) di0 = step_i(q0, x, v0, SYS(L)[0]);
         else q0 = __fma_rn(x, v0, q0);
-        if (wr1) di1 = step_i(q1, x, v1, P.L[1]);
+        if (wr1) di1 = step_i(q1, x, v1, SYS(L)[1]);
         else q1 = __fma_rn(x, v1, q1);
-        if (wr2) di2 = step_i(q2, x, v2, P.L[2]);
+        if (wr2) di2 = step_i(q2, x, v2, SYS(L)[2]);
         else q2 = __fma_rn(x, v2, q2);
         if (gl == 0 && (di0 | di1 | di2)) {
-          if (di0) P.img[3 * (int64_t)pid] += di0;
-          if (di1) P.img[3 * (int64_t)pid + 1] += di1;
-          if (di2) P.img[3 * (int64_t)pid + 2] += di2;
+          if (di0) Ri[3 * (int64_t)pid] += di0;
+          if (di1) Ri[3 * (int64_t)pid + 1] += di1;
+          if (di2) Ri[3 * (int64_t)pid + 2] += di2;
         }
         ++nev;
         int out;
@@ -939,9 +958,9 @@ __global__ void __launch_bounds__(128) ec_kernel(const ECParams P) {
             out = kind == KIND_HS ? ECMC_EV_HS_REFLECT : ECMC_EV_TE_REFLECT;
             refl_all = refl_all + proj;
             double kx, ky, kz;
-            pos64(st, P, slot, !F32 || slot < m, kx, ky, kz);
-            mirror2(v0, v1, v2, wrapc(q0 - kx, P.L[0], hb0, wr0), wrapc(q1 - ky, P.L[1], hb1, wr1),
-                    wrapc(q2 - kz, P.L[2], hb2, wr2));
+            pos64(st, Rr, slot, !F32 || slot < m, kx, ky, kz);
+            mirror2(v0, v1, v2, wrapc(q0 - kx, SYS(L)[0], hb0, wr0), wrapc(q1 - ky, SYS(L)[1], hb1, wr1),
+                    wrapc(q2 - kz, SYS(L)[2], hb2, wr2));
           } else if (kind == KIND_HS) {
             lift = lift + proj;
             if (P.swap_mode) {
@@ -951,7 +970,7 @@ __global__ void __launch_bounds__(128) ec_kernel(const ECParams P) {
               } else {
                 if ((ncontact & 3) == 0)
                   swr = philox(TAG_SWAP | ((uint64_t)(P.domain ? e : 0) << 8), r1, r2,
-                               (uint64_t)(ncontact >> 2), P.seed, P.replica);
+                               (uint64_t)(ncontact >> 2), P.seed, Rkey);
                 go = (swr.v[ncontact & 3] >> 11) < P.swap_thr;
               }
               ++ncontact;
@@ -981,11 +1000,11 @@ __global__ void __launch_bounds__(128) ec_kernel(const ECParams P) {
                       b1 = q1;
                       b2 = q2;
                     } else {
-                      pos64(st, P, b, !F32 || b < m, b0, b1, b2);
+                      pos64(st, Rr, b, !F32 || b < m, b0, b1, b2);
                     }
-                    const double e0 = wrapc(a0 - b0, P.L[0], hb0, wr0);
-                    const double e1 = wrapc(a1 - b1, P.L[1], hb1, wr1);
-                    const double e2 = wrapc(a2 - b2, P.L[2], hb2, wr2);
+                    const double e0 = wrapc(a0 - b0, SYS(L)[0], hb0, wr0);
+                    const double e1 = wrapc(a1 - b1, SYS(L)[1], hb1, wr1);
+                    const double e2 = wrapc(a2 - b2, SYS(L)[2], hb2, wr2);
                     const double dd = __fma_rn(e2, e2, __fma_rn(e1, e1, e0 * e0));
                     ok = ok && !(dbits(dd) > dbits(P.b2));
                   }
@@ -999,9 +1018,9 @@ __global__ void __launch_bounds__(128) ec_kernel(const ECParams P) {
                     const int kid = st.id[slot];
 #pragma unroll
                     for (int a = 0; a < 3; ++a) {
-                      const int ti = P.img[3 * (int64_t)pid + a];
-                      P.img[3 * (int64_t)pid + a] = P.img[3 * (int64_t)kid + a];
-                      P.img[3 * (int64_t)kid + a] = ti;
+                      const int ti = Ri[3 * (int64_t)pid + a];
+                      Ri[3 * (int64_t)pid + a] = Ri[3 * (int64_t)kid + a];
+                      Ri[3 * (int64_t)kid + a] = ti;
                     }
                   }
                   q0 = k0;
@@ -1031,9 +1050,9 @@ __global__ void __launch_bounds__(128) ec_kernel(const ECParams P) {
           nf0 = (float)q0 - cf0;
           nf1 = (float)q1 - cf1;
           nf2 = (float)q2 - cf2;
-          if (wr0) nf0 = nf0 > Lh0 ? nf0 - (float)P.L[0] : (nf0 < -Lh0 ? nf0 + (float)P.L[0] : nf0);
-          if (wr1) nf1 = nf1 > Lh1 ? nf1 - (float)P.L[1] : (nf1 < -Lh1 ? nf1 + (float)P.L[1] : nf1);
-          if (wr2) nf2 = nf2 > Lh2 ? nf2 - (float)P.L[2] : (nf2 < -Lh2 ? nf2 + (float)P.L[2] : nf2);
+          if (wr0) nf0 = nf0 > Lh0 ? nf0 - (float)SYS(L)[0] : (nf0 < -Lh0 ? nf0 + (float)SYS(L)[0] : nf0);
+          if (wr1) nf1 = nf1 > Lh1 ? nf1 - (float)SYS(L)[1] : (nf1 < -Lh1 ? nf1 + (float)SYS(L)[1] : nf1);
+          if (wr2) nf2 = nf2 > Lh2 ? nf2 - (float)SYS(L)[2] : (nf2 < -Lh2 ? nf2 + (float)SYS(L)[2] : nf2);
         } else {
           nf0 = (float)q0;
           nf1 = (float)q1;
@@ -1047,7 +1066,7 @@ __global__ void __launch_bounds__(128) ec_kernel(const ECParams P) {
             const unsigned long long at = atomicAdd(P.log_n, 1ull);
             if ((int64_t)at < P.log_cap) {
               ecmc_event ev;
-              ev.unit = P.rec_offset + (P.domain ? (int64_t)unit * n_ec + e : (int64_t)e);
+              ev.unit = P.rec_offset + (P.sweep_dev ? (sweep - P.rec_sweep0) * P.n_units * n_ec : 0) + (P.domain ? (int64_t)gunit * n_ec + e : (int64_t)e);
               ev.seq = (int32_t)(nev - 1);
               ev.pivot = pid;
               ev.kind = out;
@@ -1068,9 +1087,9 @@ __global__ void __launch_bounds__(128) ec_kernel(const ECParams P) {
             if (swapped) {
               const double o0 = st.px[slot], o1 = st.py[slot], o2 = st.pz[slot];
               float g0 = (float)o0 - cf0, g1 = (float)o1 - cf1, g2 = (float)o2 - cf2;
-              if (wr0) g0 = g0 > Lh0 ? g0 - (float)P.L[0] : (g0 < -Lh0 ? g0 + (float)P.L[0] : g0);
-              if (wr1) g1 = g1 > Lh1 ? g1 - (float)P.L[1] : (g1 < -Lh1 ? g1 + (float)P.L[1] : g1);
-              if (wr2) g2 = g2 > Lh2 ? g2 - (float)P.L[2] : (g2 < -Lh2 ? g2 + (float)P.L[2] : g2);
+              if (wr0) g0 = g0 > Lh0 ? g0 - (float)SYS(L)[0] : (g0 < -Lh0 ? g0 + (float)SYS(L)[0] : g0);
+              if (wr1) g1 = g1 > Lh1 ? g1 - (float)SYS(L)[1] : (g1 < -Lh1 ? g1 + (float)SYS(L)[1] : g1);
+              if (wr2) g2 = g2 > Lh2 ? g2 - (float)SYS(L)[2] : (g2 < -Lh2 ? g2 + (float)SYS(L)[2] : g2);
               const int koc = lcell(LG, st.fx[slot], st.fy[slot], st.fz[slot], a0, a1, a2);
               const int knc = lcell(LG, g0, g1, g2, b0, b1, b2);
               lcell_remove(st, oc, p);
@@ -1129,7 +1148,7 @@ __global__ void __launch_bounds__(128) ec_kernel(const ECParams P) {
       nev_all += (unsigned long long)nev;
       ++ecs_done;
       if (gl == 0 && P.rec_digest) {
-        const int64_t idx = P.rec_offset + (P.domain ? (int64_t)unit * n_ec + e : (int64_t)e);
+        const int64_t idx = P.rec_offset + (P.sweep_dev ? (sweep - P.rec_sweep0) * P.n_units * n_ec : 0) + (P.domain ? (int64_t)gunit * n_ec + e : (int64_t)e);
         if (idx < P.rec_cap) {
           P.rec_digest[idx] = h;
           P.rec_lift[idx] = lift;
@@ -1160,12 +1179,13 @@ __global__ void __launch_bounds__(128) ec_kernel(const ECParams P) {
   if (live) {
     for (int s = gl; s < m; s += G) {
       const int64_t b = st.id[s];
-      P.r[3 * b] = st.px[s];
-      P.r[3 * b + 1] = st.py[s];
-      P.r[3 * b + 2] = st.pz[s];
+      Rr[3 * b] = st.px[s];
+      Rr[3 * b + 1] = st.py[s];
+      Rr[3 * b + 2] = st.pz[s];
     }
   }
 }
+#undef SYS
 
 }  // namespace
 
@@ -1173,7 +1193,7 @@ size_t ec_smem_bytes(int stage_cap, int motile_cap, int ncell, int groups_per_bl
   return (size_t)groups_per_block * group_bytes(stage_cap, motile_cap, ncell);
 }
 
-template <int G, bool F32>
+template <int G, bool F32, bool BATCH>
 static cudaError_t launch_t(const ECParams &P, cudaStream_t s) {
   static int smem_max = 0;
   if (!smem_max) {
@@ -1186,7 +1206,7 @@ static cudaError_t launch_t(const ECParams &P, cudaStream_t s) {
   // threads; among those, the block size that keeps the most groups (tiles)
   // resident per SM, as the occupancy calculator counts them
   const int per_warp = 32 / G;
-  const int NC = P.domain ? P.lg[0] * P.lg[1] * P.lg[2] : 0;
+  const int NC = P.domain ? (BATCH ? P.ncl_max : P.lg[0] * P.lg[1] * P.lg[2]) : 0;
   const int M = (F32 && P.domain) ? P.m_cap : P.stage_cap;
   const size_t per_group = ec_smem_bytes(P.stage_cap, M, NC, 1);
   const int need = (P.n_units + per_warp - 1) / per_warp * per_warp;
@@ -1197,14 +1217,14 @@ static cudaError_t launch_t(const ECParams &P, cudaStream_t s) {
   if (memo) {
     gpb = memo_gpb;
   } else {
-    cudaError_t e = cudaFuncSetAttribute(ec_kernel<G, F32>,
+    cudaError_t e = cudaFuncSetAttribute(ec_kernel<G, F32, BATCH>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, smem_max);
     if (e != cudaSuccess) return e;
   }
   for (int g = per_warp; !memo && g <= 128 / G; g += per_warp) {
     if ((size_t)g * per_group > (size_t)smem_max) break;
     int blocks = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, ec_kernel<G, F32>, g * G,
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, ec_kernel<G, F32, BATCH>, g * G,
                                                       (size_t)g * per_group) != cudaSuccess)
       return cudaErrorInvalidValue;
     const int resident = blocks * (g < need ? g : need);
@@ -1222,19 +1242,27 @@ static cudaError_t launch_t(const ECParams &P, cudaStream_t s) {
   if (gpb == 0) return cudaErrorInvalidValue;
   const int threads = gpb * G;
   const size_t smem = (size_t)gpb * per_group;
-  cudaError_t e = cudaFuncSetAttribute(ec_kernel<G, F32>,
+  cudaError_t e = cudaFuncSetAttribute(ec_kernel<G, F32, BATCH>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   const int blocks = (P.n_units + gpb - 1) / gpb;
-  ec_kernel<G, F32><<<blocks, threads, smem, s>>>(P);
+  ec_kernel<G, F32, BATCH><<<blocks, threads, smem, s>>>(P);
   return cudaGetLastError();
 }
 
 cudaError_t launch_ec(const ECParams &P, int lanes, int fp32f, cudaStream_t s) {
-  if (lanes == 32) return fp32f ? launch_t<32, true>(P, s) : launch_t<32, false>(P, s);
-  if (lanes == 16) return fp32f ? launch_t<16, true>(P, s) : launch_t<16, false>(P, s);
-  if (lanes == 8) return fp32f ? launch_t<8, true>(P, s) : launch_t<8, false>(P, s);
-  if (lanes == 4) return fp32f ? launch_t<4, true>(P, s) : launch_t<4, false>(P, s);
+  if (lanes == 32) return fp32f ? launch_t<32, true, false>(P, s) : launch_t<32, false, false>(P, s);
+  if (lanes == 16) return fp32f ? launch_t<16, true, false>(P, s) : launch_t<16, false, false>(P, s);
+  if (lanes == 8) return fp32f ? launch_t<8, true, false>(P, s) : launch_t<8, false, false>(P, s);
+  if (lanes == 4) return fp32f ? launch_t<4, true, false>(P, s) : launch_t<4, false, false>(P, s);
+  return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_ec_batch(const ECParams &P, int lanes, int fp32f, cudaStream_t s) {
+  if (lanes == 32) return fp32f ? launch_t<32, true, true>(P, s) : launch_t<32, false, true>(P, s);
+  if (lanes == 16) return fp32f ? launch_t<16, true, true>(P, s) : launch_t<16, false, true>(P, s);
+  if (lanes == 8) return fp32f ? launch_t<8, true, true>(P, s) : launch_t<8, false, true>(P, s);
+  if (lanes == 4) return fp32f ? launch_t<4, true, true>(P, s) : launch_t<4, false, true>(P, s);
   return cudaErrorInvalidValue;
 }
 

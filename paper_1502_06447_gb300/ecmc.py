@@ -28,7 +28,9 @@ EXPORTS = (
     "ecmc_set_positions", "ecmc_get_positions", "ecmc_get_info", "ecmc_configure", "ecmc_run",
     "ecmc_swap", "ecmc_observables", "ecmc_g1_reset", "ecmc_records", "ecmc_log_reserve",
     "ecmc_event_log", "ecmc_domain_tags", "ecmc_checkpoint", "ecmc_restore",
-    "ecmc_cells_static",
+    "ecmc_cells_static", "ecmc_batch_create", "ecmc_batch_destroy", "ecmc_batch_configure",
+    "ecmc_batch_run", "ecmc_batch_get_positions", "ecmc_batch_info", "ecmc_batch_stats",
+    "ecmc_batch_records",
 )
 
 
@@ -43,7 +45,7 @@ class Opts(C.Structure):
                 ("tiles", C.c_int32 * 3), ("joint", C.c_double), ("s_cap", C.c_double),
                 ("event_cap", C.c_int64), ("p_swap", C.c_double), ("ecs_per_tile", C.c_int32),
                 ("lanes", C.c_int32), ("record", C.c_int32), ("stage_cap", C.c_int32),
-                ("cell_side", C.c_double)]
+                ("cell_side", C.c_double), ("tile_side", C.c_double)]
 
 
 class Obs(C.Structure):
@@ -105,6 +107,14 @@ def load(path: str = LIB_PATH):
             "ecmc_cells_static": [vp, C.c_int64, P(C.c_double), P(C.c_int32), C.c_double,
                                   C.c_double, C.c_uint64, C.c_int64, vp, vp, vp,
                                   P(C.c_double), vp],
+            "ecmc_batch_create": [P(ReplicaSpec), C.c_int32, C.c_double, C.c_uint64, P(vp)],
+            "ecmc_batch_configure": [vp, P(Opts)],
+            "ecmc_batch_run": [vp, C.c_double, C.c_uint64, C.c_int64, C.c_int32],
+            "ecmc_batch_get_positions": [vp, C.c_int32, P(C.c_double), P(C.c_int32)],
+            "ecmc_batch_info": [vp, C.c_int32, P(C.c_int32), P(C.c_int64), P(C.c_int64)],
+            "ecmc_batch_stats": [vp, P(C.c_int64), P(C.c_int64), P(C.c_double)],
+            "ecmc_batch_records": [vp, P(C.c_uint64), P(C.c_double), P(C.c_int64),
+                                   P(C.c_int64)],
         }
         for name, args in sig.items():
             f = getattr(lib, name)
@@ -112,6 +122,8 @@ def load(path: str = LIB_PATH):
             f.restype = C.c_int
         lib.ecmc_destroy.argtypes = [vp]
         lib.ecmc_destroy.restype = None
+        lib.ecmc_batch_destroy.argtypes = [vp]
+        lib.ecmc_batch_destroy.restype = None
         lib.ecmc_last_error.argtypes = []
         lib.ecmc_last_error.restype = C.c_char_p
         _lib = lib
@@ -130,7 +142,7 @@ def _p(a, ct):
 
 def opts(mode=MODE_SERIAL, dir_mode=DIR_CART3, precision=PREC_FP64, tiles=(3, 3, 3), joint=0.0,
          s_cap=0.0, event_cap=0, p_swap=0.0, ecs_per_tile=0, lanes=0, record=0, stage_cap=0,
-         cell_side=0.0) -> Opts:
+         cell_side=0.0, tile_side=0.0) -> Opts:
     o = Opts()
     o.mode, o.dir_mode, o.precision = int(mode), int(dir_mode), int(precision)
     for a in range(3):
@@ -138,7 +150,13 @@ def opts(mode=MODE_SERIAL, dir_mode=DIR_CART3, precision=PREC_FP64, tiles=(3, 3,
     o.joint, o.s_cap, o.event_cap = float(joint), float(s_cap), int(event_cap)
     o.p_swap, o.ecs_per_tile, o.lanes = float(p_swap), int(ecs_per_tile), int(lanes)
     o.record, o.stage_cap, o.cell_side = int(record), int(stage_cap), float(cell_side)
+    o.tile_side = float(tile_side)
     return o
+
+
+class ReplicaSpec(C.Structure):
+    _fields_ = [("dims", C.c_int32 * 3), ("spacing", C.c_double), ("N", C.c_int32),
+                ("sigma", C.c_double), ("b_max", C.c_double)]
 
 
 class Context:
@@ -269,3 +287,74 @@ def cells_static(d_r, n, box, tiles, joint, cell_side, seed, sweep, d_tags, d_ce
                                     C.c_void_p(d_cell_start), C.c_void_p(d_cell_ids),
                                     _p(shift, C.c_double), C.c_void_p(stream)))
     return shift
+
+
+class Batch:
+    """Many independent melts advanced together (wraps an ecmc_batch)."""
+
+    def __init__(self, specs, jitter=0.0, seed=0):
+        arr = (ReplicaSpec * len(specs))()
+        for i, sp in enumerate(specs):
+            for a in range(3):
+                arr[i].dims[a] = int(sp["dims"][a])
+            arr[i].spacing = float(sp["spacing"])
+            arr[i].N = int(sp["N"])
+            arr[i].sigma = float(sp.get("sigma", 1.0))
+            arr[i].b_max = float(sp.get("b_max", 1.2))
+        self._h = C.c_void_p()
+        _check(load().ecmc_batch_create(arr, len(specs), float(jitter), int(seed) & (2**64 - 1),
+                                        C.byref(self._h)))
+        self.n = len(specs)
+
+    def close(self):
+        if self._h:
+            load().ecmc_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def configure(self, **kw):
+        kw.setdefault("mode", MODE_DOMAIN)
+        kw.setdefault("tiles", (0, 0, 0))
+        o = opts(**kw)
+        _check(load().ecmc_batch_configure(self._h, C.byref(o)))
+
+    def run(self, ell, seed=0, n_sweeps=1, graph=True):
+        _check(load().ecmc_batch_run(self._h, float(ell), int(seed) & (2**64 - 1), int(n_sweeps),
+                                     1 if graph else 0))
+
+    def info(self, r):
+        t = np.zeros(3, dtype=np.int32)
+        off = C.c_int64()
+        nb = C.c_int64()
+        _check(load().ecmc_batch_info(self._h, int(r), _p(t, C.c_int32), C.byref(off),
+                                      C.byref(nb)))
+        return tuple(int(x) for x in t), off.value, nb.value
+
+    def get_positions(self, r):
+        _, _, nb = self.info(r)
+        x = np.zeros((nb, 3))
+        img = np.zeros((nb, 3), dtype=np.int32)
+        _check(load().ecmc_batch_get_positions(self._h, int(r), _p(x, C.c_double),
+                                               _p(img, C.c_int32)))
+        return x, img
+
+    def stats(self):
+        ev = C.c_int64()
+        ecs = C.c_int64()
+        sec = C.c_double()
+        _check(load().ecmc_batch_stats(self._h, C.byref(ev), C.byref(ecs), C.byref(sec)))
+        return {"events_total": ev.value, "ecs": ecs.value, "device_seconds": sec.value}
+
+    def records(self, cap):
+        dig = np.zeros(cap, dtype=np.uint64)
+        lift = np.zeros(cap)
+        ev = np.zeros(cap, dtype=np.int64)
+        n = C.c_int64(cap)
+        _check(load().ecmc_batch_records(self._h, _p(dig, C.c_uint64), _p(lift, C.c_double),
+                                         _p(ev, C.c_int64), C.byref(n)))
+        return dig[: n.value], lift[: n.value], ev[: n.value]

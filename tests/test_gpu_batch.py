@@ -1,0 +1,87 @@
+"""Batched replicas: every replica must evolve exactly as a single melt with
+the Philox key (seed, r) does in the oracle, event for event, with and
+without the captured CUDA graph."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1502_06447_gb300 import ecmc
+from paper_1502_06447_gb300.configs import replica_specs
+
+pytestmark = pytest.mark.gpu
+
+SEED = 0xEC0B01
+JITTER = 0.01
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _build():
+    from paper_1502_06447_gb300 import build
+    build.build()
+
+
+def ragged_specs():
+    # uneven N, bead counts, spacings (phi from 0.36 to 0.45)
+    return [dict(dims=(12, 12, 12), spacing=1.05, N=8), dict(dims=(10, 12, 14), spacing=1.12, N=10),
+            dict(dims=(16, 12, 10), spacing=1.18, N=20), dict(dims=(12, 14, 12), spacing=1.08, N=1),
+            dict(dims=(14, 14, 14), spacing=1.15, N=7)]
+
+
+def oracle_replica(sp, r, tiles, ell, sweeps, p_swap=0.0, jitter=JITTER):
+    L = tuple(d * sp["spacing"] for d in sp["dims"])
+    o = oracle.System(oracle.lattice(sp["dims"], sp["spacing"], jitter, SEED, replica=r), L,
+                      sp["N"], mode=oracle.MODE_DOMAIN, dir_mode=oracle.DIR_ISO, D=tiles,
+                      seed=SEED, replica=r, p_swap=p_swap)
+    res = o.run_domain(sweeps, ell, digests=True)
+    assert res["rc"] == 0
+    return o, res
+
+
+def check_batch(specs, lanes, prec, graph, sweeps=3, ell=3.0, p_swap=0.0, jitter=JITTER):
+    b = ecmc.Batch(specs, jitter=jitter, seed=SEED)
+    b.configure(dir_mode=ecmc.DIR_ISO, precision=prec, lanes=lanes, record=1, p_swap=p_swap)
+    b.run(ell, seed=SEED, n_sweeps=sweeps, graph=graph)
+    units = sum(int(np.prod(b.info(r)[0])) for r in range(len(specs)))
+    dig, _, _ = b.records(sweeps * units)
+    for r, sp in enumerate(specs):
+        tiles, off, nb = b.info(r)
+        nt = int(np.prod(tiles))
+        o, res = oracle_replica(sp, r, tiles, ell, sweeps, p_swap, jitter)
+        mine = np.concatenate([dig[s * units + off: s * units + off + nt] for s in range(sweeps)])
+        assert (mine == res["digest"]).all(), (r, np.nonzero(mine != res["digest"])[0][:5])
+        x, img = b.get_positions(r)
+        assert (x == o.r).all() and (img == o.img).all(), r
+    return b
+
+
+@pytest.mark.parametrize("graph", [True, False])
+@pytest.mark.parametrize("lanes,prec", [(8, ecmc.PREC_FP32F), (16, ecmc.PREC_FP32F),
+                                        (32, ecmc.PREC_FP64)])
+def test_batch_replicas_match_oracle(lanes, prec, graph):
+    check_batch(ragged_specs(), lanes, prec, graph)
+
+
+def test_batch_swap_matches_oracle():
+    check_batch(ragged_specs()[:3], 8, ecmc.PREC_FP32F, True, p_swap=0.5, ell=5.0)
+
+
+def test_batch_c4_replicas_sample():
+    """The first replicas of the 256-replica workload (N in {10..160},
+    2k-64k beads, phi in [0.35, 0.50]) against the oracle, two sweeps."""
+    ms = replica_specs()[:6]
+    specs = [dict(dims=m.dims, spacing=m.spacing, N=m.N) for m in ms]
+    check_batch(specs, 8, ecmc.PREC_FP32F, True, sweeps=2, ell=5.0, jitter=ms[0].jitter)
+
+
+def test_batch_graph_equals_plain_launches():
+    specs = ragged_specs()
+    a = ecmc.Batch(specs, jitter=JITTER, seed=SEED)
+    a.configure(dir_mode=ecmc.DIR_ISO, precision=ecmc.PREC_FP32F, lanes=8)
+    a.run(3.0, seed=SEED, n_sweeps=4, graph=True)
+    c = ecmc.Batch(specs, jitter=JITTER, seed=SEED)
+    c.configure(dir_mode=ecmc.DIR_ISO, precision=ecmc.PREC_FP32F, lanes=8)
+    c.run(3.0, seed=SEED, n_sweeps=1, graph=False)
+    c.run(3.0, seed=SEED, n_sweeps=3, graph=True)
+    for r in range(len(specs)):
+        assert (a.get_positions(r)[0] == c.get_positions(r)[0]).all()
+    assert a.stats()["events_total"] == c.stats()["events_total"]
