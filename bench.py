@@ -2,9 +2,15 @@
 
 Workload (the 10^6-bead melt): 1000 chains x N=1000 on a 100^3 lattice,
 spacing 1.05 sigma (phi ~ 0.45), b_max = 1.2 sigma, ell = 20 sigma,
-25^3 shifted tiles, isotropic directions, FP32 screen + FP64 confirmation,
-swap moves calibrated to 0.1 attempts per bead per sweep.
-One step = one sweep: domain assignment + cell list + one EC per tile.
+isotropic directions, FP32 screen + FP64 confirmation, swap moves calibrated
+to 0.1 attempts per bead per sweep; lanes per EC, tile side, cell side and
+ECs per tile picked by the library's autotuner (outside the timed region).
+One step = one sweep: domain assignment + cell list + one EC launch.
+
+The batched form (256 replicas of uneven N, bead count and phi, one CUDA
+graph per sweep, autotuned) is timed in the same run and reported under
+`batched`, against the same replicas advanced one at a time through the
+single-melt API and against the batched plain FP64 kernel.
 
 `value` is events/s of the FP32-screened form (inputs resident in HBM, L2
 flushed between steps, device time from CUDA events).  The plain FP64 kernel
@@ -134,12 +140,14 @@ def run_gpu(args, rank, world):
         lanes = args.lanes if precision == ecmc.PREC_FP32F else args.lanes64
         ctx.configure(mode=ecmc.MODE_DOMAIN, dir_mode=ecmc.DIR_ISO, precision=precision,
                       tiles=TILES, lanes=lanes, ecs_per_tile=args.ecs_per_tile)
-        return ctx
+        tune = ctx.autotune(ELL, seed=seed, trial_sweeps=2) if args.tune else None
+        # swap calibration under the final setting: one sweep without swaps,
+        # then p_swap for 0.1 attempts / bead / sweep
+        ctx.run(ELL, seed=seed, n_sweeps=1)
+        ctx.swap(SWAP_RATE)
+        return ctx, tune
 
-    ctx = make(ecmc.PREC_FP32F)
-    # swap calibration: one sweep without swaps, then p_swap for 0.1 / bead / sweep
-    ctx.run(ELL, seed=seed, n_sweeps=1)
-    ctx.swap(SWAP_RATE)
+    ctx, tune = make(ecmc.PREC_FP32F)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
     for _ in range(args.warmup):
         ctx.run(ELL, seed=seed, n_sweeps=1)
@@ -169,9 +177,7 @@ def run_gpu(args, rank, world):
     assert o1["overlaps"] == 0 and o1["tether_violations"] == 0
 
     # plain FP64 kernel on the same workload (fresh lattice, same calibration)
-    ctx64 = make(ecmc.PREC_FP64)
-    ctx64.run(ELL, seed=seed, n_sweeps=1)
-    ctx64.swap(SWAP_RATE)
+    ctx64, tune64 = make(ecmc.PREC_FP64)
     ctx64.run(ELL, seed=seed, n_sweeps=1)
     p0 = ctx64.observables()
     n64 = max(1, args.steps // 2)
@@ -211,6 +217,7 @@ def run_gpu(args, rank, world):
         torch.distributed.all_reduce(s[:1], op=torch.distributed.ReduceOp.SUM)
         torch.distributed.all_reduce(t[1:3], op=torch.distributed.ReduceOp.MAX)
         tot_events, max_dev, max_wall = float(s[0]), float(t[1]), float(t[2])
+    batched = run_batch(args, stream) if args.batch else None
     if rank != 0:
         return None
     hbm, peak_src = load_peaks()
@@ -241,9 +248,13 @@ def run_gpu(args, rank, world):
         "data": "synthetic",
         "config": {"workload": C5.name, "beads": n_beads, "chains": C5.n_chains, "N": C5.N,
                    "lattice": list(C5.dims), "spacing": C5.spacing, "phi": round(phi, 4),
-                   "b_max": C5.b_max, "ell": ELL, "tiles": list(TILES), "directions": "iso",
+                   "b_max": C5.b_max, "ell": ELL,
+                   "tiles": list(tune["tiles"]) if tune else list(TILES), "directions": "iso",
                    "precision": "fp32 screen + fp64 confirm", "swap_attempts_per_bead_sweep":
-                   SWAP_RATE, "lanes_per_ec": args.lanes, "ecs_per_tile": args.ecs_per_tile,
+                   SWAP_RATE, "lanes_per_ec": tune["lanes"] if tune else args.lanes,
+                   "ecs_per_tile": tune["ecs_per_tile"] if tune else args.ecs_per_tile,
+                   "cell_side": tune["cell_side"] if tune else 1.0,
+                   "tuning": "autotuned (ECs per device-second)" if tune else "fixed",
                    "l2": "flushed between steps (256 MB write)",
                    "parallelism": "replicas" if world > 1 else "1 GPU"},
         "ell_sweeps_per_s": (ecs / n_beads) / dev_s,
@@ -255,17 +266,90 @@ def run_gpu(args, rank, world):
         "wall_s": max_wall,
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
                      "frac": achieved / hbm, "traffic": traffic,
-                     "kernel": f"ec_kernel<{args.lanes},true>", "bytes_per_event": bpe,
+                     "kernel": f"ec_kernel<{tune['lanes'] if tune else args.lanes},true,false>",
+                     "bytes_per_event": bpe,
                      "kernel_share_of_step": ec_s / dev_s, "peak_source": peak_src},
         "e2e": {"value": e2e_events / e2e_s, "unit": UNIT,
                 "h2d_bytes_per_step": int(r_host.nbytes + img_host.nbytes),
                 "d2h_bytes_per_step": int(r_host.nbytes + img_host.nbytes)},
         "gpu_launches": 6 * args.steps,
         "clocks": clk.summary(),
+        "tuning": {"fp32f": tune, "fp64": tune64},
     }
+    if batched is not None:
+        line["batched"] = batched
     if args.cpu_baseline:
         line["cpu_baseline"] = cpu_baseline_run(max_sweeps=1)
     return line
+
+
+def run_batch(args, stream):
+    """256 replicas (N in {10..160}, 2k-64k beads, phi in [0.35, 0.50],
+    ell = 5): aggregate throughput of the graph-captured batched sweep, the
+    same replicas one at a time through the single-melt API, and the batched
+    plain FP64 kernel.  Device time from the library's CUDA events on its
+    stream; the batch state (~0.5 GB) exceeds L2, so no flush."""
+    import torch
+
+    from paper_1502_06447_gb300 import ecmc
+    from paper_1502_06447_gb300.configs import replica_specs
+    ms = replica_specs()
+    specs = [dict(dims=m.dims, spacing=m.spacing, N=m.N) for m in ms]
+    ell, seed, jitter = ms[0].ell, ms[0].seed, ms[0].jitter
+    beads = sum(m.n for m in ms)
+    ksteps = max(3, args.steps // 2)
+    res = {"workload": f"{len(ms)} replicas, N in {{10..160}}, {min(m.n for m in ms)}-"
+                       f"{max(m.n for m in ms)} beads each, phi in [0.35, 0.50], ell = {ell}",
+           "replicas": len(ms), "beads": beads, "steps": ksteps,
+           "l2": "state larger than L2 (no flush)"}
+    for name, prec, lanes in (("fp32f", ecmc.PREC_FP32F, 8), ("fp64", ecmc.PREC_FP64, 16)):
+        b = ecmc.Batch(specs, jitter=jitter, seed=seed)
+        b.configure(dir_mode=ecmc.DIR_ISO, precision=prec, lanes=lanes)
+        tune = b.autotune(ell, seed=seed, trial_sweeps=2)
+        b.run(ell, seed=seed, n_sweeps=max(1, args.warmup), graph=True)
+        s0 = b.stats()
+        b.run(ell, seed=seed, n_sweeps=ksteps, graph=True)
+        s1 = b.stats()
+        dt = s1["device_seconds"] - s0["device_seconds"]
+        ev = s1["events_total"] - s0["events_total"]
+        ecs = s1["ecs"] - s0["ecs"]
+        res[name] = {"events_per_s": ev / dt, "ecs_per_s": ecs / dt,
+                     "ell_sweeps_per_s": ecs / beads / dt, "ms_per_sweep": 1e3 * dt / ksteps,
+                     "tuning": tune}
+        if name == "fp32f":
+            tiles = [b.info(r)[0] for r in range(len(ms))]
+        b.close()
+    res["fp32f_over_fp64"] = res["fp32f"]["events_per_s"] / res["fp64"]["events_per_s"]
+    # the same replicas one at a time (one launch sequence and one host
+    # round trip per replica per sweep), same tuned setting
+    t = res["fp32f"]["tuning"]
+    ctxs = []
+    for m, d in zip(ms, tiles):
+        c = ecmc.Context.create_lattice(m.dims, m.spacing, m.N, jitter=jitter, seed=seed)
+        c.set_stream(stream.cuda_stream)
+        c.configure(mode=ecmc.MODE_DOMAIN, dir_mode=ecmc.DIR_ISO, precision=ecmc.PREC_FP32F,
+                    tiles=d, lanes=t["lanes"], cell_side=t["cell_side"],
+                    ecs_per_tile=t["ecs_per_tile"])
+        c.run(ell, seed=seed, n_sweeps=1)
+        ctxs.append(c)
+    nseq = max(1, ksteps // 3)
+    o0 = [c.observables()["events_total"] for c in ctxs]
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(nseq):
+        for c in ctxs:
+            c.run(ell, seed=seed, n_sweeps=1)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    dt = e0.elapsed_time(e1) / 1e3
+    ev = sum(c.observables()["events_total"] - a for c, a in zip(ctxs, o0))
+    for c in ctxs:
+        c.close()
+    res["sequential"] = {"events_per_s": ev / dt, "ms_per_sweep": 1e3 * dt / nseq,
+                         "steps": nseq}
+    res["batched_over_sequential"] = res["fp32f"]["events_per_s"] / res["sequential"]["events_per_s"]
+    return res
 
 
 def cpu_baseline_run(max_sweeps=1, time_budget=25.0):
@@ -328,6 +412,10 @@ def main():
                     help="c5: the 1e6-bead melt (default); c2/c3: smaller melts")
     ap.add_argument("--tiles", type=int, default=0, help="tiles per axis (0: workload default)")
     ap.add_argument("--ecs-per-tile", type=int, default=1)
+    ap.add_argument("--no-tune", dest="tune", action="store_false",
+                    help="use --lanes/--tiles/--ecs-per-tile instead of the autotuner")
+    ap.add_argument("--no-batch", dest="batch", action="store_false",
+                    help="skip the batched-replicas measurement")
     args = ap.parse_args()
     global C5, ELL, TILES
     C5, TILES = WORKLOADS[args.workload]

@@ -267,6 +267,33 @@ ecmc_status ecmc_batch_stats(ecmc_batch *b, int64_t *events_total,
 ecmc_status ecmc_batch_records(ecmc_batch *b, uint64_t *digest, double *lift,
                                int64_t *events, int64_t *n);
 
+/* ---- autotuner -------------------------------------------------------------
+ * Picks the launch setting of the domain sweep for this machine and system
+ * (the paper fixes none: Sec. II.B leaves the tile size open): lanes per EC
+ * (4, 8, 16, 32), tile side (3.4 ... 7 sigma), global cell side (1 or 1.4
+ * sigma) and ECs per tile (1 or 2), by a coordinate descent over short timed
+ * trials.  Each trial restores the state saved on entry, runs one untimed
+ * sweep and `trial_sweeps` timed ones; the score is ECs per device-second.
+ * On return the context (batch) is configured with the winner and its
+ * positions, images, counters, sums and sweep index are those on entry, so a
+ * run after tuning is the run that would have followed without it (with the
+ * winner's tiles).  Needs a configured domain-mode context; keeps its mode,
+ * direction rule, precision, p_swap, joint, s_cap and record setting. */
+typedef struct ecmc_tuning {
+  int32_t lanes;          /* lanes per EC */
+  double tile_side;       /* target tile side (sigma) */
+  double cell_side;       /* global cell side (sigma) */
+  int32_t ecs_per_tile;
+  int32_t tiles[3];       /* single context: tiles per axis; batch: 0 */
+  double ecs_per_s;       /* score of the winner */
+  double events_per_s;
+  int32_t n_trials;       /* admissible points timed */
+} ecmc_tuning;
+ecmc_status ecmc_autotune(ecmc_ctx *ctx, double ell, uint64_t seed,
+                          int32_t trial_sweeps, ecmc_tuning *out);
+ecmc_status ecmc_batch_autotune(ecmc_batch *b, double ell, uint64_t seed,
+                                int32_t trial_sweeps, ecmc_tuning *out);
+
 /* ---- domain assignment and cell list without allocation ------------------
  * The paper has no counterpart to this entry point; it serves callers that
  * cannot allocate device memory (a host callback, a framework that owns every

@@ -462,18 +462,10 @@ ecmc_status ecmc_configure(ecmc_ctx *c, const ecmc_opts *o) {
       c->T[a] = T;
       c->W[a] = W;
     }
-    if (stage <= 0) {
-      const double rho = (double)c->n / (c->L[0] * c->L[1] * c->L[2]);
-      double vol = 1.0;
-      for (int a = 0; a < 3; ++a) vol *= c->W[a] + 2.0 * halo_te;
-      stage = (int32_t)(rho * vol * 1.3 + 32);
-      stage = (stage + 31) / 32 * 32;
-    }
-    {
-      const double rho = (double)c->n / (c->L[0] * c->L[1] * c->L[2]);
-      mcap = (int32_t)(rho * c->W[0] * c->W[1] * c->W[2] * 1.3 + 32);
-      mcap = (mcap + 31) / 32 * 32;
-    }
+    const double rho = (double)c->n / (c->L[0] * c->L[1] * c->L[2]);
+    const double E[3] = {c->W[0] + 2.0 * halo_te, c->W[1] + 2.0 * halo_te, c->W[2] + 2.0 * halo_te};
+    if (stage <= 0) stage = stage_bound(E, rho);
+    mcap = stage_bound(c->W, rho);
   } else {
     if (p.precision == ECMC_PREC_FP32F)
       for (int a = 0; a < 3; ++a)
@@ -940,6 +932,116 @@ ecmc_status ecmc_restore(ecmc_ctx *c, const char *path) {
   c->ecs_done = hd.ecs_done;
   c->device_seconds = hd.device_seconds;
   if (hd.configured) return ecmc_configure(c, &hd.opts);
+  return ECMC_OK;
+}
+
+ecmc_status ecmc_autotune(ecmc_ctx *c, double ell, uint64_t seed, int32_t trial_sweeps,
+                          ecmc_tuning *out) {
+  if (!c || !out) return fail(ECMC_EINVAL, "NULL argument");
+  if (!c->configured || c->opts.mode != ECMC_MODE_DOMAIN)
+    return fail(ECMC_EINVAL, "autotune needs a context configured in the domain mode");
+  if (trial_sweeps < 1 || !(ell > 0.0) || !isfinite(ell))
+    return fail(ECMC_EINVAL, "need trial_sweeps >= 1 and a finite ell > 0");
+  const ecmc_opts base = c->opts;
+  const double sig = c->sigma;
+  const double w = base.joint > 0 ? base.joint : c->b_max;
+  const double halo_te = (c->b_max > sig ? c->b_max : sig) * (1.0 + 1e-6);
+  // state on entry, restored before every trial and on return
+  struct Saved {
+    double *r = nullptr;
+    int32_t *img = nullptr;
+    ~Saved() {
+      cudaFree(r);
+      cudaFree(img);
+    }
+  } sv;
+  CU(dalloc(&sv.r, 3 * c->n));
+  CU(dalloc(&sv.img, 3 * c->n));
+  unsigned long long cnt0[CNT_N];
+  double sums0[SUM_N];
+  CU(cudaMemcpyAsync(sv.r, c->d_r, sizeof(double) * 3 * c->n, cudaMemcpyDeviceToDevice, c->stream));
+  CU(cudaMemcpyAsync(sv.img, c->d_img, sizeof(int32_t) * 3 * c->n, cudaMemcpyDeviceToDevice, c->stream));
+  CU(cudaMemcpyAsync(cnt0, c->d_cnt, sizeof(cnt0), cudaMemcpyDeviceToHost, c->stream));
+  CU(cudaMemcpyAsync(sums0, c->d_sums, sizeof(sums0), cudaMemcpyDeviceToHost, c->stream));
+  CU(cudaStreamSynchronize(c->stream));
+  const int64_t sw0 = c->sweeps_done, ec0 = c->ecs_done;
+  const double ds0 = c->device_seconds, es0 = c->ec_seconds;
+  auto restore = [&]() -> ecmc_status {
+    CU(cudaMemcpyAsync(c->d_r, sv.r, sizeof(double) * 3 * c->n, cudaMemcpyDeviceToDevice, c->stream));
+    CU(cudaMemcpyAsync(c->d_img, sv.img, sizeof(int32_t) * 3 * c->n, cudaMemcpyDeviceToDevice, c->stream));
+    CU(cudaMemcpyAsync(c->d_cnt, cnt0, sizeof(cnt0), cudaMemcpyHostToDevice, c->stream));
+    CU(cudaMemcpyAsync(c->d_sums, sums0, sizeof(sums0), cudaMemcpyHostToDevice, c->stream));
+    CU(cudaStreamSynchronize(c->stream));
+    c->sweeps_done = sw0;
+    c->ecs_done = ec0;
+    c->device_seconds = ds0;
+    c->ec_seconds = es0;
+    return ECMC_OK;
+  };
+  auto point_opts = [&](const TunePoint &pt) {
+    ecmc_opts o = base;
+    o.lanes = pt.lanes;
+    o.cell_side = pt.cell_side * sig;
+    o.ecs_per_tile = pt.ecs;
+    o.stage_cap = 0;
+    for (int a = 0; a < 3; ++a) {
+      int D = (int)floor(c->L[a] / (pt.tile_side * sig));
+      if (D < 3) D = 3;
+      while (D < 1024 && !(c->L[a] / D - w + 2.0 * halo_te < 0.5 * c->L[a])) ++D;
+      o.tiles[a] = D;
+    }
+    return o;
+  };
+  auto counts = [&](unsigned long long *h) -> ecmc_status {
+    CU(cudaMemcpyAsync(h, c->d_cnt, sizeof(unsigned long long) * CNT_N, cudaMemcpyDeviceToHost, c->stream));
+    CU(cudaStreamSynchronize(c->stream));
+    return ECMC_OK;
+  };
+  auto trial = [&](const TunePoint &pt, TuneScore *sc) -> ecmc_status {
+    ecmc_opts o = point_opts(pt);
+    o.record = 0;
+    ecmc_status st = ecmc_configure(c, &o);
+    if (st != ECMC_OK) return st;
+    if ((st = restore()) != ECMC_OK) return st;
+    st = ecmc_run(c, ell, 0, seed, 1);
+    if (st == ECMC_ECAPACITY) return ECMC_EINVAL;  // staging too small here: not admissible
+    if (st != ECMC_OK) return st;
+    unsigned long long h0[CNT_N], h1[CNT_N];
+    if ((st = counts(h0)) != ECMC_OK) return st;
+    const double t0 = c->device_seconds;
+    st = ecmc_run(c, ell, 0, seed, trial_sweeps);
+    if (st == ECMC_ECAPACITY) return ECMC_EINVAL;
+    if (st != ECMC_OK) return st;
+    if ((st = counts(h1)) != ECMC_OK) return st;
+    const double dt = c->device_seconds - t0;
+    if (!(dt > 0.0)) return ECMC_EINVAL;
+    sc->ecs_per_s = (double)(h1[CNT_ECS] - h0[CNT_ECS]) / dt;
+    sc->events_per_s = (double)(h1[CNT_EVENTS] - h0[CNT_EVENTS]) / dt;
+    return ECMC_OK;
+  };
+  TunePoint start{c->lanes == 1 ? 8 : c->lanes, c->T[0] / sig * (1.0 - 1e-9),
+                  base.cell_side > 0 ? base.cell_side / sig : 1.0, c->ecs_per_tile};
+  TunePoint best{};
+  TuneScore best_s{};
+  int n = 0;
+  ecmc_status st = tune_search(start, trial, &best, &best_s, &n);
+  if (st != ECMC_OK) {
+    const std::string why = g_err;
+    ecmc_configure(c, &base);
+    restore();
+    return fail(st, "autotune: %s", st == ECMC_EINVAL ? "no admissible setting" : why.c_str());
+  }
+  const ecmc_opts o = point_opts(best);
+  if ((st = ecmc_configure(c, &o)) != ECMC_OK) return st;
+  if ((st = restore()) != ECMC_OK) return st;
+  out->lanes = best.lanes;
+  out->tile_side = best.tile_side;
+  out->cell_side = best.cell_side;
+  out->ecs_per_tile = best.ecs;
+  for (int a = 0; a < 3; ++a) out->tiles[a] = o.tiles[a];
+  out->ecs_per_s = best_s.ecs_per_s;
+  out->events_per_s = best_s.events_per_s;
+  out->n_trials = n;
   return ECMC_OK;
 }
 

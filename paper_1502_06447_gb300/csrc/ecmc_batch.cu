@@ -295,7 +295,6 @@ ecmc_status ecmc_batch_configure(ecmc_batch *b, const ecmc_opts *o) {
     RepParams &R = reps[r];
     const double rho = (double)R.n_beads / (R.L[0] * R.L[1] * R.L[2]);
     int64_t ncl = 1, nce = 1, nt = 1;
-    double vol = 1.0, volm = 1.0;
     for (int a = 0; a < 3; ++a) {
       if (!(s_cap + sig + margin < R.half[a]))
         return bfail(ECMC_EINVAL, "replica " + std::to_string(r) + ": need s_cap + sigma < L/2");
@@ -323,16 +322,15 @@ ecmc_status ecmc_batch_configure(ecmc_batch *b, const ecmc_opts *o) {
       ncl *= g;
       nce *= k;
       nt *= D;
-      vol *= W + 2.0 * halo_te;
-      volm *= W;
     }
     R.lorg = (float)(-hg);
     R.cell_off = cell_off;
     R.unit_off = unit_off;
     cell_off += nce;
     unit_off += nt;
-    const int32_t st = (int32_t)((rho * vol * 1.3 + 32 + 31) / 32) * 32;
-    const int32_t mc = (int32_t)((rho * volm * 1.3 + 32 + 31) / 32) * 32;
+    const double E[3] = {R.W[0] + 2.0 * halo_te, R.W[1] + 2.0 * halo_te, R.W[2] + 2.0 * halo_te};
+    const int32_t st = stage_bound(E, rho);
+    const int32_t mc = stage_bound(R.W, rho);
     stage = st > stage ? st : stage;
     mcap = mc > mcap ? mc : mcap;
     nclm = (int32_t)ncl > nclm ? (int32_t)ncl : nclm;
@@ -509,6 +507,102 @@ ecmc_status ecmc_batch_records(ecmc_batch *b, uint64_t *digest, double *lift, in
   if (events) BCU(cudaMemcpyAsync(events, b->d_rev, sizeof(int64_t) * cnt, cudaMemcpyDeviceToHost, b->stream));
   BCU(cudaStreamSynchronize(b->stream));
   *n = cnt;
+  return ECMC_OK;
+}
+
+ecmc_status ecmc_batch_autotune(ecmc_batch *b, double ell, uint64_t seed, int32_t trial_sweeps,
+                                ecmc_tuning *out) {
+  if (!b || !out) return bfail(ECMC_EINVAL, "NULL argument");
+  if (!b->configured) return bfail(ECMC_EINVAL, "call ecmc_batch_configure first");
+  if (trial_sweeps < 1 || !(ell > 0.0) || !isfinite(ell))
+    return bfail(ECMC_EINVAL, "need trial_sweeps >= 1 and a finite ell > 0");
+  const ecmc_opts base = b->opts;
+  const double sig = b->sigma;
+  struct Saved {
+    double *r = nullptr;
+    int32_t *img = nullptr;
+    ~Saved() {
+      cudaFree(r);
+      cudaFree(img);
+    }
+  } sv;
+  const int64_t n3 = 3 * b->n_total;
+  BCU(balloc(&sv.r, n3));
+  BCU(balloc(&sv.img, n3));
+  unsigned long long cnt0[CNT_N];
+  double sums0[SUM_N];
+  BCU(cudaMemcpyAsync(sv.r, b->d_r, sizeof(double) * n3, cudaMemcpyDeviceToDevice, b->stream));
+  BCU(cudaMemcpyAsync(sv.img, b->d_img, sizeof(int32_t) * n3, cudaMemcpyDeviceToDevice, b->stream));
+  BCU(cudaMemcpyAsync(cnt0, b->d_cnt, sizeof(cnt0), cudaMemcpyDeviceToHost, b->stream));
+  BCU(cudaMemcpyAsync(sums0, b->d_sums, sizeof(sums0), cudaMemcpyDeviceToHost, b->stream));
+  BCU(cudaStreamSynchronize(b->stream));
+  const int64_t sw0 = b->sweeps_done;
+  const double ds0 = b->device_seconds;
+  auto restore = [&]() -> ecmc_status {
+    BCU(cudaMemcpyAsync(b->d_r, sv.r, sizeof(double) * n3, cudaMemcpyDeviceToDevice, b->stream));
+    BCU(cudaMemcpyAsync(b->d_img, sv.img, sizeof(int32_t) * n3, cudaMemcpyDeviceToDevice, b->stream));
+    BCU(cudaMemcpyAsync(b->d_cnt, cnt0, sizeof(cnt0), cudaMemcpyHostToDevice, b->stream));
+    BCU(cudaMemcpyAsync(b->d_sums, sums0, sizeof(sums0), cudaMemcpyHostToDevice, b->stream));
+    BCU(cudaStreamSynchronize(b->stream));
+    b->sweeps_done = sw0;
+    b->device_seconds = ds0;
+    return ECMC_OK;
+  };
+  auto point_opts = [&](const TunePoint &pt) {
+    ecmc_opts o = base;
+    o.lanes = pt.lanes;
+    o.tile_side = pt.tile_side * sig;
+    o.tiles[0] = o.tiles[1] = o.tiles[2] = 0;
+    o.cell_side = pt.cell_side * sig;
+    o.ecs_per_tile = pt.ecs;
+    o.stage_cap = 0;
+    return o;
+  };
+  auto trial = [&](const TunePoint &pt, TuneScore *sc) -> ecmc_status {
+    ecmc_opts o = point_opts(pt);
+    o.record = 0;
+    ecmc_status st = ecmc_batch_configure(b, &o);
+    if (st != ECMC_OK) return st;
+    if ((st = restore()) != ECMC_OK) return st;
+    // the first call settles block sizes and captures the sweep graph
+    st = ecmc_batch_run(b, ell, seed, 1, 1);
+    if (st == ECMC_ECAPACITY) return ECMC_EINVAL;
+    if (st != ECMC_OK) return st;
+    int64_t e0 = 0, c0 = 0, e1 = 0, c1 = 0;
+    double t0 = 0, t1 = 0;
+    if ((st = ecmc_batch_stats(b, &e0, &c0, &t0)) != ECMC_OK) return st;
+    st = ecmc_batch_run(b, ell, seed, trial_sweeps, 1);
+    if (st == ECMC_ECAPACITY) return ECMC_EINVAL;
+    if (st != ECMC_OK) return st;
+    if ((st = ecmc_batch_stats(b, &e1, &c1, &t1)) != ECMC_OK) return st;
+    const double dt = t1 - t0;
+    if (!(dt > 0.0)) return ECMC_EINVAL;
+    sc->ecs_per_s = (double)(c1 - c0) / dt;
+    sc->events_per_s = (double)(e1 - e0) / dt;
+    return ECMC_OK;
+  };
+  TunePoint start{b->lanes, base.tile_side / sig, base.cell_side > 0 ? base.cell_side / sig : 1.0,
+                  b->ecs_per_tile};
+  TunePoint best{};
+  TuneScore best_s{};
+  int n = 0;
+  ecmc_status st = tune_search(start, trial, &best, &best_s, &n);
+  if (st != ECMC_OK) {
+    ecmc_batch_configure(b, &base);
+    restore();
+    return bfail(st, st == ECMC_EINVAL ? "autotune: no admissible setting" : "autotune failed");
+  }
+  const ecmc_opts o = point_opts(best);
+  if ((st = ecmc_batch_configure(b, &o)) != ECMC_OK) return st;
+  if ((st = restore()) != ECMC_OK) return st;
+  out->lanes = best.lanes;
+  out->tile_side = best.tile_side;
+  out->cell_side = best.cell_side;
+  out->ecs_per_tile = best.ecs;
+  out->tiles[0] = out->tiles[1] = out->tiles[2] = 0;
+  out->ecs_per_s = best_s.ecs_per_s;
+  out->events_per_s = best_s.events_per_s;
+  out->n_trials = n;
   return ECMC_OK;
 }
 

@@ -1,5 +1,6 @@
 // Internal declarations shared by the library's translation units.
 #pragma once
+#include <math.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -181,5 +182,93 @@ cudaError_t launch_g1_snapshot(const ObsParams &O, double *g1ref, cudaStream_t s
 cudaError_t launch_lattice(const int32_t dims[3], double a, double jitter,
                            uint64_t seed, uint64_t replica, double *r, int64_t n,
                            cudaStream_t s);
+
+// Staging capacity for a box of sides E[3] (a tile plus its halo, or the
+// motile part of a tile) at bead number density rho: the larger of a 30 %
+// density-fluctuation margin, 1.3 rho V + 32, and the most sites a simple-
+// cubic lattice of this density (spacing a = rho^(-1/3), jitter below
+// 0.01 a) can put in the box, prod(floor((E_a + 0.02) / a) + 1) + 8: the
+// lattice start is the densest arrangement these melts meet, and a box
+// aligned with its planes holds floor(E/a) + 1 sites per axis.  Rounded up
+// to a multiple of 32.
+inline int32_t stage_bound(const double E[3], double rho) {
+  const double a_inv = cbrt(rho);
+  const double fluct = 1.3 * rho * E[0] * E[1] * E[2] + 32.0;
+  double lat = 1.0;
+  for (int a = 0; a < 3; ++a) lat *= floor((E[a] + 0.02) * a_inv) + 1.0;
+  lat += 8.0;
+  const double b = fluct > lat ? fluct : lat;
+  const int64_t n = (int64_t)ceil(b);
+  return (int32_t)((n + 31) / 32 * 32);
+}
+
+// ---------------------------------------------------------------- autotuner
+// One launch setting of the domain sweep.  The search is a coordinate
+// descent: lanes per EC, then tile side, then global cell side, then ECs per
+// tile, each axis scanned with the others held at their best so far.  The
+// objective is ECs per device-second (each EC displaces by ell, so this is
+// the rate of progress of the Markov chain; events/s would reward small
+// tiles for their extra wall reflections).
+struct TunePoint {
+  int lanes;
+  double tile_side;  // in units of sigma
+  double cell_side;  // in units of sigma
+  int ecs;
+};
+
+struct TuneScore {
+  double ecs_per_s = 0.0, events_per_s = 0.0;
+};
+
+// trial(point, &score) -> ECMC_OK (scored), ECMC_EINVAL (point not
+// admissible for this system: skipped) or another status (abort).
+template <class Trial>
+ecmc_status tune_search(TunePoint start, Trial trial, TunePoint *best, TuneScore *best_score,
+                        int *n_trials) {
+  static const int lanes_c[] = {4, 8, 16, 32};
+  static const double tile_c[] = {3.4, 4.2, 5.0, 6.0, 7.0};
+  static const double cell_c[] = {1.0, 1.4};
+  static const int ecs_c[] = {1, 2};
+  TunePoint cur = start;
+  TuneScore cur_s{};
+  bool have = false;
+  int n = 0;
+  auto consider = [&](const TunePoint &pt) -> ecmc_status {
+    TuneScore sc{};
+    const ecmc_status st = trial(pt, &sc);
+    if (st == ECMC_EINVAL) return ECMC_OK;
+    if (st != ECMC_OK) return st;
+    ++n;
+    if (!have || sc.ecs_per_s > cur_s.ecs_per_s) {
+      cur = pt;
+      cur_s = sc;
+      have = true;
+    }
+    return ECMC_OK;
+  };
+  ecmc_status st = consider(start);
+  if (st != ECMC_OK) return st;
+  for (int axis = 0; axis < 4; ++axis) {
+    const TunePoint base = cur;
+    const int cnt = axis == 0 ? 4 : axis == 1 ? 5 : 2;
+    for (int i = 0; i < cnt; ++i) {
+      TunePoint pt = base;
+      if (axis == 0) pt.lanes = lanes_c[i];
+      if (axis == 1) pt.tile_side = tile_c[i];
+      if (axis == 2) pt.cell_side = cell_c[i];
+      if (axis == 3) pt.ecs = ecs_c[i];
+      if (pt.lanes == base.lanes && pt.tile_side == base.tile_side &&
+          pt.cell_side == base.cell_side && pt.ecs == base.ecs)
+        continue;
+      st = consider(pt);
+      if (st != ECMC_OK) return st;
+    }
+  }
+  if (!have) return ECMC_EINVAL;
+  *best = cur;
+  *best_score = cur_s;
+  *n_trials = n;
+  return ECMC_OK;
+}
 
 }  // namespace ecmc

@@ -30,7 +30,7 @@ EXPORTS = (
     "ecmc_event_log", "ecmc_domain_tags", "ecmc_checkpoint", "ecmc_restore",
     "ecmc_cells_static", "ecmc_batch_create", "ecmc_batch_destroy", "ecmc_batch_configure",
     "ecmc_batch_run", "ecmc_batch_get_positions", "ecmc_batch_info", "ecmc_batch_stats",
-    "ecmc_batch_records",
+    "ecmc_batch_records", "ecmc_autotune", "ecmc_batch_autotune",
 )
 
 
@@ -115,6 +115,8 @@ def load(path: str = LIB_PATH):
             "ecmc_batch_stats": [vp, P(C.c_int64), P(C.c_int64), P(C.c_double)],
             "ecmc_batch_records": [vp, P(C.c_uint64), P(C.c_double), P(C.c_int64),
                                    P(C.c_int64)],
+            "ecmc_autotune": [vp, C.c_double, C.c_uint64, C.c_int32, P(Tuning)],
+            "ecmc_batch_autotune": [vp, C.c_double, C.c_uint64, C.c_int32, P(Tuning)],
         }
         for name, args in sig.items():
             f = getattr(lib, name)
@@ -154,6 +156,17 @@ def opts(mode=MODE_SERIAL, dir_mode=DIR_CART3, precision=PREC_FP64, tiles=(3, 3,
     return o
 
 
+class Tuning(C.Structure):
+    _fields_ = [("lanes", C.c_int32), ("tile_side", C.c_double), ("cell_side", C.c_double),
+                ("ecs_per_tile", C.c_int32), ("tiles", C.c_int32 * 3), ("ecs_per_s", C.c_double),
+                ("events_per_s", C.c_double), ("n_trials", C.c_int32)]
+
+    def as_dict(self):
+        d = {k: getattr(self, k) for k, _ in self._fields_ if k != "tiles"}
+        d["tiles"] = tuple(self.tiles)
+        return d
+
+
 class ReplicaSpec(C.Structure):
     _fields_ = [("dims", C.c_int32 * 3), ("spacing", C.c_double), ("N", C.c_int32),
                 ("sigma", C.c_double), ("b_max", C.c_double)]
@@ -187,6 +200,14 @@ class Context:
         _check(load().ecmc_create(_p(b, C.c_double), float(phi), int(n_chains), int(N),
                                   float(sigma), float(b_max), C.byref(h)))
         return cls(h)
+
+    def autotune(self, ell, seed=0, trial_sweeps=2):
+        """Pick lanes, tile side, cell side and ECs per tile by timed trials;
+        the state is unchanged on return and the context runs the winner."""
+        t = Tuning()
+        _check(load().ecmc_autotune(self._h, float(ell), int(seed) & (2**64 - 1),
+                                    int(trial_sweeps), C.byref(t)))
+        return t.as_dict()
 
     def close(self):
         if self._h:
@@ -326,6 +347,14 @@ class Batch:
     def run(self, ell, seed=0, n_sweeps=1, graph=True):
         _check(load().ecmc_batch_run(self._h, float(ell), int(seed) & (2**64 - 1), int(n_sweeps),
                                      1 if graph else 0))
+
+    def autotune(self, ell, seed=0, trial_sweeps=2):
+        """As Context.autotune, over the whole batch (per-replica tiles follow
+        the chosen tile side)."""
+        t = Tuning()
+        _check(load().ecmc_batch_autotune(self._h, float(ell), int(seed) & (2**64 - 1),
+                                          int(trial_sweeps), C.byref(t)))
+        return t.as_dict()
 
     def info(self, r):
         t = np.zeros(3, dtype=np.int32)
