@@ -139,7 +139,9 @@ def run_gpu(args, rank, world):
         ctx.set_stream(stream.cuda_stream)
         lanes = args.lanes if precision == ecmc.PREC_FP32F else args.lanes64
         ctx.configure(mode=ecmc.MODE_DOMAIN, dir_mode=ecmc.DIR_ISO, precision=precision,
-                      tiles=TILES, lanes=lanes, ecs_per_tile=args.ecs_per_tile)
+                      tiles=TILES, lanes=lanes, ecs_per_tile=args.ecs_per_tile,
+                      schedule=args.schedule,
+                      block_tiles=args.block_tiles if precision == ecmc.PREC_FP32F else 0)
         tune = ctx.autotune(ELL, seed=seed, trial_sweeps=2) if args.tune else None
         # swap calibration under the final setting: one sweep without swaps,
         # then p_swap for 0.1 attempts / bead / sweep
@@ -412,6 +414,9 @@ def main():
                     help="c5: the 1e6-bead melt (default); c2/c3: smaller melts")
     ap.add_argument("--tiles", type=int, default=0, help="tiles per axis (0: workload default)")
     ap.add_argument("--ecs-per-tile", type=int, default=1)
+    ap.add_argument("--schedule", type=int, default=0,
+                    help="screened kernel: 0 block lockstep, 1 warp lockstep")
+    ap.add_argument("--block-tiles", type=int, default=0, help="block lockstep: tiles per block")
     ap.add_argument("--no-tune", dest="tune", action="store_false",
                     help="use --lanes/--tiles/--ecs-per-tile instead of the autotuner")
     ap.add_argument("--no-batch", dest="batch", action="store_false",

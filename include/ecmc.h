@@ -87,14 +87,22 @@ typedef struct ecmc_opts {
   int64_t event_cap;     /* events per EC before ECMC_ESTUCK; 0 -> 10^7 */
   double p_swap;         /* swap proposal probability at a motile contact */
   int32_t ecs_per_tile;  /* ECs per tile per sweep (domain); 0 -> 1 */
-  int32_t lanes;         /* lanes per EC: 32, 16, 8, or 1 (domain mode: one thread
-                            per tile, local cell grid in a per-tile scratch
-                            region); 0 -> 32 */
+  int32_t lanes;         /* lanes per EC: 32, 16, 8, 4, or 1 (domain mode: one
+                            thread per tile, local cell grid in a per-tile
+                            scratch region); 0 -> 32 */
   int32_t record;        /* 1: keep per-EC digests / lift sums of the last run */
   int32_t stage_cap;     /* staged beads per tile; 0 -> derived from the tile size */
   double cell_side;      /* side of the global cell grid (domain); 0 -> 1.0 sigma */
   double tile_side;      /* batch: target tile side when tiles[0] <= 0 (per replica
                             D = floor(L / tile_side), at least 3); 0 -> 4.2 sigma */
+  int32_t schedule;      /* screened domain form with lanes 4, 8 or 16:
+                            0 -> block lockstep: the tiles of a block advance one
+                            event per step together and their FP64 work (candidate
+                            evaluation, move) is packed one tile per thread;
+                            1 -> warp lockstep: each group of `lanes` lanes does
+                            its own tile's FP64 work.  Same events either way. */
+  int32_t block_tiles;   /* block lockstep: tiles per block (a multiple of
+                            32 / lanes, at most 32); 0 -> most tiles per SM */
 } ecmc_opts;
 
 /* Observables and counters (Sec. III observables; see ecmc_observables). */

@@ -1,0 +1,526 @@
+// Device helpers shared by the EC kernels (arXiv:1502.06447, Sec. II, II.B,
+// II.D): FP64 comparisons on bit patterns, the minimum image, the contact and
+// tether distances (Eq. 1), the reflection (Fig. 2c), candidate keys and the
+// tie rule, the shared-memory staging of one tile and its local cell grid,
+// and the FP32 screen.  Included by the kernel translation units only.
+#pragma once
+#include <cuda_runtime.h>
+#include <float.h>
+
+#include "ecmc_dev.cuh"
+#include "ecmc_internal.h"
+
+namespace ecmc {
+namespace {
+
+constexpr unsigned FULL = 0xffffffffu;
+
+// ---------------------------------------------------------------- FP64 bits
+__device__ __forceinline__ uint64_t dbits(double x) { return (uint64_t)__double_as_longlong(x); }
+// x < 0.0 (false for -0.0)
+__device__ __forceinline__ bool neg(double x) {
+  const uint64_t b = dbits(x);
+  return (int64_t)b < 0 && (b << 1) != 0;
+}
+// x > 0.0
+__device__ __forceinline__ bool posv(double x) { return (int64_t)dbits(x) > 0; }
+// y >= L for L > 0
+__device__ __forceinline__ bool ge_pos(double y, double L) {
+  return (int64_t)dbits(y) >= (int64_t)dbits(L);
+}
+__device__ __forceinline__ bool nonzero(double x) { return (dbits(x) << 1) != 0; }
+
+// minimum image, same result as d > h ? d - L : (d < -h ? d + L : d)
+__device__ __forceinline__ double wrap_i(double d, double L, uint64_t hbits) {
+  const uint64_t b = dbits(d);
+  if ((b & 0x7FFFFFFFFFFFFFFFull) > hbits) return ((int64_t)b < 0) ? d + L : d - L;
+  return d;
+}
+
+// wrap_i on an axis that can need it; identity on an axis that cannot
+__device__ __forceinline__ double wrapc(double d, double L, uint64_t hbits, bool w) {
+  return w ? wrap_i(d, L, hbits) : d;
+}
+
+// r += x v on one axis, back into [0, L); returns the image change
+__device__ __forceinline__ int step_i(double &r, double x, double v, double L) {
+  double y = __fma_rn(x, v, r);
+  int di = 0;
+  if (ge_pos(y, L)) {
+    y = y - L;
+    di = 1;
+  } else if (neg(y)) {
+    y = y + L;
+    di = -1;
+    if (ge_pos(y, L)) {
+      y = 0.0;
+      di = 0;
+    }
+  }
+  r = y;
+  return di;
+}
+
+// Hard-sphere contact (Eq. 1, R2 = sigma^2) or tether limit (R2 = b_max^2)
+// of a pivot moving along v, d = pivot - partner.  Returns x >= 0, or -1 when
+// a contact candidate misses; dv = d.v.
+__device__ __forceinline__ double quad_x(bool tether, double d0, double d1, double d2, double v0,
+                                         double v1, double v2, double R2, double &dv) {
+  dv = __fma_rn(d2, v2, __fma_rn(d1, v1, d0 * v0));
+  if (!tether && !neg(dv)) return -1.0;
+  const double dd = __fma_rn(d2, d2, __fma_rn(d1, d1, d0 * d0));
+  double rad = R2 - __fma_rn(-dv, dv, dd);
+  if (tether) {
+    if (neg(rad)) rad = 0.0;
+  } else if (!posv(rad)) {
+    return -1.0;
+  }
+  const double x = tether ? -dv + sqrt(rad) : -dv - sqrt(rad);
+  return neg(x) ? 0.0 : x;
+}
+
+// v <- v - (2 v.d / d.d) d: reflection at the plane normal to d (Fig. 2c)
+__device__ __forceinline__ void mirror2(double &v0, double &v1, double &v2, double d0, double d1,
+                                        double d2) {
+  const double dd = __fma_rn(d2, d2, __fma_rn(d1, d1, d0 * d0));
+  const double vd = __fma_rn(v2, d2, __fma_rn(v1, d1, v0 * d0));
+  const double t = (2.0 * vd) / dd;
+  v0 = __fma_rn(-t, d0, v0);
+  v1 = __fma_rn(-t, d1, v1);
+  v2 = __fma_rn(-t, d2, v2);
+}
+
+// candidate key: kind (3 bits) | partner id (41 bits) | slot (20 bits).
+// Key order within equal x = (kind, partner id) order, the tie rule.
+__device__ __forceinline__ uint64_t make_key(int kind, int64_t id, int slot) {
+  return ((uint64_t)kind << 61) | (((uint64_t)id & ((1ull << 41) - 1)) << 20) |
+         (uint64_t)(slot & 0xFFFFF);
+}
+__device__ __forceinline__ int key_kind(uint64_t k) { return (int)(k >> 61); }
+__device__ __forceinline__ int64_t key_id(uint64_t k) { return (int64_t)((k >> 20) & ((1ull << 41) - 1)); }
+__device__ __forceinline__ int key_slot(uint64_t k) { return (int)(k & 0xFFFFF); }
+
+// x >= 0 always, so its bit pattern orders like the value
+__device__ __forceinline__ bool better(double x, uint64_t key, double bx, uint64_t bkey) {
+  const uint64_t a = dbits(x), b = dbits(bx);
+  return a < b || (a == b && key < bkey);
+}
+
+template <int G>
+__device__ __forceinline__ void group_argmin(double &bx, uint64_t &bkey) {
+#pragma unroll
+  for (int off = G / 2; off > 0; off >>= 1) {
+    const double ox = __shfl_xor_sync(FULL, bx, off);
+    const uint64_t ok = __shfl_xor_sync(FULL, bkey, off);
+    if (better(ox, ok, bx, bkey)) {
+      bx = ox;
+      bkey = ok;
+    }
+  }
+}
+
+template <int G>
+__device__ __forceinline__ float group_minf(float v) {
+#pragma unroll
+  for (int off = G / 2; off > 0; off >>= 1) v = fminf(v, __shfl_xor_sync(FULL, v, off));
+  return v;
+}
+
+// FP32 minimum image (serial mode only; tile-local shadows need none)
+__device__ __forceinline__ float wrapf(float d, float L) {
+  return d > 0.5f * L ? d - L : (d < -0.5f * L ? d + L : d);
+}
+
+// ---------------------------------------------------------------- staging
+// Shared memory of one group: FP64 positions and bond-partner words of the
+// first M slots (M = the motile capacity in the screened domain form, where
+// joint beads' FP64 positions, static during a sweep, are read from the
+// global array when a confirmation needs them; M = S otherwise); FP32 shadow
+// (12 B) and id (4 B) of all S slots; the local cell grid (16 B per cell:
+// count + 7 slots); the overflow list of beads whose cell was full; a header.
+constexpr int CELL_CAP = 7;
+constexpr int OVF_CAP = 64;
+constexpr int HDR_BYTES = 32;
+
+struct Stage {
+  double *px, *py, *pz;  // [M]
+  unsigned *nb;          // [M] bond partner slots, 16 + 16 bits (0xFFFF = none)
+  float *fx, *fy, *fz;   // [S]
+  int *id;               // [S]
+  unsigned short *cell;  // [NC][8]: count, then up to 7 slots
+  unsigned short *ovf;   // [OVF_CAP]
+  int *hdr;              // [2] staged count, [3] overflow, [4] overflow-list length
+};
+
+__host__ __device__ __forceinline__ size_t group_bytes(int S, int M, int NC) {
+  return (size_t)M * 28 + (size_t)S * 16 + (size_t)NC * 16 + OVF_CAP * 2 + HDR_BYTES;
+}  // (16 B per cell: a count and 7 slots of 16 bits)
+
+// S and M are multiples of 32, so every array starts 16-byte aligned
+__device__ __forceinline__ Stage carve(unsigned char *base, int S, int M, int NC) {
+  Stage s;
+  s.px = (double *)base;
+  s.py = s.px + M;
+  s.pz = s.py + M;
+  s.nb = (unsigned *)(s.pz + M);
+  s.fx = (float *)(s.nb + M);
+  s.fy = s.fx + S;
+  s.fz = s.fy + S;
+  s.id = (int *)(s.fz + S);
+  s.cell = (unsigned short *)(s.id + S);
+  s.ovf = s.cell + 8 * NC;
+  s.hdr = (int *)(s.ovf + OVF_CAP);
+  return s;
+}
+
+__device__ __forceinline__ int nb_prev(unsigned w) { return (w & 0xFFFF) == 0xFFFF ? -1 : (int)(w & 0xFFFF); }
+__device__ __forceinline__ int nb_next(unsigned w) { return (w >> 16) == 0xFFFF ? -1 : (int)(w >> 16); }
+__device__ __forceinline__ unsigned nb_pack(int prev, int next) {
+  return ((unsigned)(next < 0 ? 0xFFFF : next) << 16) | (unsigned)(prev < 0 ? 0xFFFF : prev);
+}
+
+// binary search of id in the sorted range [lo, hi); -1 if absent
+__device__ __forceinline__ int find_id(const int *ids, int lo, int hi, int id) {
+  while (lo < hi) {
+    const int mid = (lo + hi) >> 1;
+    const int v = ids[mid];
+    if (v == id) return mid;
+    if (v < id) lo = mid + 1;
+    else hi = mid;
+  }
+  return -1;
+}
+
+__device__ __forceinline__ void set_status(int *st, int code) { atomicCAS(st, 0, code); }
+
+// ---------------------------------------------------------------- local grid
+struct LGrid {
+  int g0, g1, g2;
+  float org, inv0, inv1, inv2;
+};
+
+__device__ __forceinline__ int lcell(const LGrid &L, float f0, float f1, float f2, int &c0,
+                                     int &c1, int &c2) {
+  c0 = (int)((f0 - L.org) * L.inv0);
+  c1 = (int)((f1 - L.org) * L.inv1);
+  c2 = (int)((f2 - L.org) * L.inv2);
+  c0 = c0 < 0 ? 0 : (c0 >= L.g0 ? L.g0 - 1 : c0);
+  c1 = c1 < 0 ? 0 : (c1 >= L.g1 ? L.g1 - 1 : c1);
+  c2 = c2 < 0 ? 0 : (c2 >= L.g2 ? L.g2 - 1 : c2);
+  return (c2 * L.g1 + c1) * L.g0 + c0;
+}
+
+// single-writer updates (one lane of the group)
+__device__ __forceinline__ bool lcell_insert(const Stage &st, int ci, int slot) {
+  unsigned short *c = st.cell + 8 * ci;
+  const int n = c[0];
+  if (n < CELL_CAP) {
+    c[1 + n] = (unsigned short)slot;
+    c[0] = (unsigned short)(n + 1);
+    return true;
+  }
+  const int k = st.hdr[4];
+  if (k >= OVF_CAP) return false;
+  st.ovf[k] = (unsigned short)slot;
+  st.hdr[4] = k + 1;
+  return true;
+}
+
+__device__ __forceinline__ void lcell_remove(const Stage &st, int ci, int slot) {
+  unsigned short *c = st.cell + 8 * ci;
+  const int n = c[0];
+  for (int i = 1; i <= n; ++i) {
+    if (c[i] == slot) {
+      c[i] = c[n];
+      c[0] = (unsigned short)(n - 1);
+      return;
+    }
+  }
+  const int k = st.hdr[4];
+  for (int i = 0; i < k; ++i) {
+    if (st.ovf[i] == slot) {
+      st.ovf[i] = st.ovf[k - 1];
+      st.hdr[4] = k - 1;
+      return;
+    }
+  }
+}
+
+// FP32 screen of one hard-sphere obstacle k for the pivot shadow pf moving
+// along vf: updates the upper bound ubl and keeps the slot when its lower
+// bound can reach it (two kept per lane, more -> ovf)
+struct Screen {
+  float sig2f, eps_v, eps_d, near2;
+};
+
+__device__ __forceinline__ void screen_hs(const Screen &Z, float d0, float d1, float d2, float vf0,
+                                          float vf1, float vf2, int k, float &ubl, int &ks0,
+                                          float &kl0, int &ks1, float &kl1, bool &ovf) {
+  const float dd = __fmaf_rn(d2, d2, __fmaf_rn(d1, d1, d0 * d0));
+  if (dd > Z.near2) return;
+  const float dv = __fmaf_rn(d2, vf2, __fmaf_rn(d1, vf1, d0 * vf0));
+  const float disc = Z.sig2f - (dd - dv * dv);
+  if (!(dv < Z.eps_v && disc > -Z.eps_d)) return;
+  if (dv < -Z.eps_v && disc > Z.eps_d)
+    ubl = fminf(ubl, fmaxf(0.f, -dv + Z.eps_v - sqrt_lo(disc - Z.eps_d)) + 1e-6f);
+  const float lb = -dv - Z.eps_v - sqrt_hi(disc + Z.eps_d);
+  if (lb > ubl) return;
+  const float INF = __int_as_float(0x7f800000);
+  if (kl0 > ubl) {
+    ks0 = -1;
+    kl0 = INF;
+  }
+  if (kl1 > ubl) {
+    ks1 = -1;
+    kl1 = INF;
+  }
+  if (ks0 < 0) {
+    ks0 = k;
+    kl0 = lb;
+  } else if (ks1 < 0) {
+    ks1 = k;
+    kl1 = lb;
+  } else {
+    ovf = true;
+  }
+}
+
+__device__ __forceinline__ float screen_lb(const Screen &Z, float d0, float d1, float d2,
+                                           float vf0, float vf1, float vf2, bool &possible) {
+  const float dd = __fmaf_rn(d2, d2, __fmaf_rn(d1, d1, d0 * d0));
+  const float dv = __fmaf_rn(d2, vf2, __fmaf_rn(d1, vf1, d0 * vf0));
+  const float disc = Z.sig2f - (dd - dv * dv);
+  possible = dd <= Z.near2 && dv < Z.eps_v && disc > -Z.eps_d;
+  return -dv - Z.eps_v - sqrt_hi(fmaxf(disc + Z.eps_d, 0.f));
+}
+
+// Screen the beads of one local cell (16 bytes: count, then up to 7 slots,
+// read at once) two per round, so that their shadow loads overlap.  The set
+// of candidates a lane keeps or flags does not depend on the order in which
+// it screens them (see screen_hs).
+__device__ __forceinline__ void screen_cell(const Screen &Z, const Stage &st, const unsigned short *rec,
+                                            int p, float a0, float a1, float a2, float w0, float w1,
+                                            float w2, float &ubl, int &ks0, float &kl0, int &ks1,
+                                            float &kl1, bool &ovf) {
+  const uint4 c = *reinterpret_cast<const uint4 *>(rec);
+  const int n = (int)(c.x & 0xFFFF);
+  const int sl[7] = {(int)(c.x >> 16), (int)(c.y & 0xFFFF), (int)(c.y >> 16), (int)(c.z & 0xFFFF),
+                     (int)(c.z >> 16), (int)(c.w & 0xFFFF), (int)(c.w >> 16)};
+#pragma unroll
+  for (int i = 0; i < 7; i += 2) {
+    if (i >= n) break;
+    const int ka = sl[i];
+    const bool two = (i + 1 < 7) && (i + 1 < n);
+    const int kb = (i + 1 < 7) ? (two ? sl[i + 1] : ka) : ka;
+    const float ax = st.fx[ka], ay = st.fy[ka], az = st.fz[ka];
+    const float bx = st.fx[kb], by = st.fy[kb], bz = st.fz[kb];
+    if (ka != p) screen_hs(Z, a0 - ax, a1 - ay, a2 - az, w0, w1, w2, ka, ubl, ks0, kl0, ks1, kl1, ovf);
+    if (two && kb != p)
+      screen_hs(Z, a0 - bx, a1 - by, a2 - bz, w0, w1, w2, kb, ubl, ks0, kl0, ks1, kl1, ovf);
+  }
+}
+
+// FP64 position of staged slot k: shared memory for the first M slots,
+// otherwise (a joint bead, static this sweep) the global position array
+__device__ __forceinline__ void pos64(const Stage &st, const double *r, int k, bool in_smem,
+                                      double &x, double &y, double &z) {
+  if (in_smem) {
+    x = st.px[k];
+    y = st.py[k];
+    z = st.pz[k];
+  } else {
+    const int64_t b = st.id[k];
+    x = r[3 * b];
+    y = r[3 * b + 1];
+    z = r[3 * b + 2];
+  }
+}
+
+// ---------------------------------------------------------------- staging
+// Stage one tile (domain) or the whole system (serial) into the group's
+// shared memory: G lanes of one group call this together; every lane of the
+// warp must call it (warp-wide reductions).  Returns the motile count m, the
+// hard-sphere joint count j1 and the staged count ns; clears `live` when the
+// tile does not fit its capacity.
+#define SYS(f) (BATCH ? rp->f : P.f)
+template <int G, bool F32, bool BATCH>
+__device__ __forceinline__ void stage_tile(const ECParams &P, const RepParams *rp, const Stage &st,
+                                           int gl, bool &live, int unit, double c0, double c1,
+                                           double c2, double *Rr, const int32_t *Rstart, int S,
+                                           int M, int NC, const LGrid &LG, int &m, int &j1,
+                                           int &ns) {
+  if (gl == 0) {
+    st.hdr[2] = 0;
+    st.hdr[3] = 0;
+    st.hdr[4] = 0;
+  }
+  __syncwarp();
+  m = 0;
+  j1 = 0;
+  ns = 0;
+  if (!P.domain) {
+    // serial: every bead, slot = id, all motile
+    const int n = (int)P.n;
+    for (int b = gl; b < n; b += G) {
+      const double x = Rr[3 * (int64_t)b], y = Rr[3 * (int64_t)b + 1], z = Rr[3 * (int64_t)b + 2];
+      st.px[b] = x;
+      st.py[b] = y;
+      st.pz[b] = z;
+      st.fx[b] = (float)x;
+      st.fy[b] = (float)y;
+      st.fz[b] = (float)z;
+      st.id[b] = b;
+      const int c = b % SYS(N);
+      st.nb[b] = nb_pack(c == 0 ? -1 : b - 1, c == SYS(N) - 1 ? -1 : b + 1);
+    }
+    m = n;
+    j1 = 0;
+    ns = n;
+  } else {
+    const double corner[3] = {c0, c1, c2};
+    // cell window covering the tether halo of the tile
+    int c_lo[3], c_n[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      const double lo = corner[a] - P.halo_te, hi = corner[a] + SYS(W)[a] + P.halo_te;
+      int l = (int)floor(lo / SYS(cs)[a]);
+      const int h = (int)floor(hi / SYS(cs)[a]);
+      int cnt = h - l + 1;
+      if (cnt >= SYS(nc)[a]) {
+        l = 0;
+        cnt = SYS(nc)[a];
+      }
+      c_lo[a] = l;
+      c_n[a] = live ? cnt : 0;
+    }
+    const int ncell = c_n[0] * c_n[1] * c_n[2];
+    const int ncell_max = __reduce_max_sync(FULL, ncell);
+    // pass 1: collect (cell-order index, category|id); the shadow arrays
+    // (12 B per slot) serve as 8 B per slot of scratch until pass 3
+    int2 *scr = (int2 *)st.fx;
+    for (int q0 = 0; q0 < ncell_max; q0 += G) {
+      const int q = q0 + gl;
+      if (q < ncell) {
+        const int qx = q % c_n[0], qy = (q / c_n[0]) % c_n[1], qz = q / (c_n[0] * c_n[1]);
+        int cx = (c_lo[0] + qx) % SYS(nc)[0];
+        int cy = (c_lo[1] + qy) % SYS(nc)[1];
+        int cz = (c_lo[2] + qz) % SYS(nc)[2];
+        if (cx < 0) cx += SYS(nc)[0];
+        if (cy < 0) cy += SYS(nc)[1];
+        if (cz < 0) cz += SYS(nc)[2];
+        const int cell = (cz * SYS(nc)[1] + cy) * SYS(nc)[0] + cx;
+        const int j0 = Rstart[cell], jend = Rstart[cell + 1];
+        for (int j = j0; j < jend; ++j) {
+          const int tg = P.ctag[j];
+          int cat = -1;
+          if (tg == unit) {
+            cat = 0;
+          } else if (tg < 0) {
+            bool in_hs = true, in_te = true;
+#pragma unroll
+            for (int a = 0; a < 3; ++a) {
+              const double s = wrap_d(P.cr[3 * (int64_t)j + a] - corner[a], SYS(L)[a], SYS(half)[a]);
+              in_hs = in_hs && (s >= -P.halo_hs) && (s <= SYS(W)[a] + P.halo_hs);
+              in_te = in_te && (s >= -P.halo_te) && (s <= SYS(W)[a] + P.halo_te);
+            }
+            cat = in_hs ? 1 : (in_te ? 2 : -1);
+          }
+          if (cat >= 0) {
+            const int slot = atomicAdd(&st.hdr[2], 1);
+            if (slot < S) scr[slot] = make_int2(j, (cat << 29) | P.cid[j]);
+            else st.hdr[3] = 1;
+          }
+        }
+      }
+    }
+    __syncwarp();
+    ns = st.hdr[2];
+    if (st.hdr[3]) {
+      if (gl == 0) set_status(P.status, DEV_CAPACITY);
+      live = false;
+      ns = 0;
+    }
+    const int ns_max = __reduce_max_sync(FULL, ns);
+    // pass 2: rank by (category, id); place FP64 positions and ids
+    int cnt_cat0 = 0, cnt_cat1 = 0;
+    for (int s0 = 0; s0 < ns_max; s0 += G) {
+      const int s = s0 + gl;
+      if (s < ns) {
+        const int2 e = scr[s];
+        int rank = 0;
+        for (int t = 0; t < ns; ++t) rank += (scr[t].y < e.y);
+        const int cat = e.y >> 29;
+        cnt_cat0 += (cat == 0);
+        cnt_cat1 += (cat == 1);
+        const int j = e.x;
+        if (rank < M) {
+          st.px[rank] = P.cr[3 * (int64_t)j];
+          st.py[rank] = P.cr[3 * (int64_t)j + 1];
+          st.pz[rank] = P.cr[3 * (int64_t)j + 2];
+        }
+        st.id[rank] = e.y & ((1 << 29) - 1);
+      }
+    }
+    __syncwarp();
+#pragma unroll
+    for (int off = G / 2; off > 0; off >>= 1) {
+      cnt_cat0 += __shfl_xor_sync(FULL, cnt_cat0, off);
+      cnt_cat1 += __shfl_xor_sync(FULL, cnt_cat1, off);
+    }
+    m = cnt_cat0;
+    j1 = cnt_cat1;
+    if (m > M) {  // more motile beads than the FP64 staging capacity
+      if (gl == 0) set_status(P.status, DEV_CAPACITY);
+      live = false;
+    }
+    // pass 3: shadows and bond partners of motile beads; empty cells
+    for (int i = gl; i < NC; i += G) st.cell[8 * i] = 0;
+    for (int s0 = 0; s0 < ns_max; s0 += G) {
+      const int s = s0 + gl;
+      if (s < ns && live) {
+        double x, y, z;
+        pos64(st, Rr, s, s < M, x, y, z);
+        st.fx[s] = (float)wrap_d(x - corner[0], SYS(L)[0], SYS(half)[0]);
+        st.fy[s] = (float)wrap_d(y - corner[1], SYS(L)[1], SYS(half)[1]);
+        st.fz[s] = (float)wrap_d(z - corner[2], SYS(L)[2], SYS(half)[2]);
+        int prev = -1, next = -1;
+        if (s < m) {
+          const int id = st.id[s];
+          const int c = id % SYS(N);
+          if (c != 0) {
+            prev = find_id(st.id, 0, m, id - 1);
+            if (prev < 0) prev = find_id(st.id, m, m + j1, id - 1);
+            if (prev < 0) prev = find_id(st.id, m + j1, ns, id - 1);
+            if (prev < 0) set_status(P.status, DEV_TILE);
+          }
+          if (c != SYS(N) - 1) {
+            next = find_id(st.id, 0, m, id + 1);
+            if (next < 0) next = find_id(st.id, m, m + j1, id + 1);
+            if (next < 0) next = find_id(st.id, m + j1, ns, id + 1);
+            if (next < 0) set_status(P.status, DEV_TILE);
+          }
+        }
+        if (s < M) st.nb[s] = nb_pack(prev, next);
+      }
+    }
+    __syncwarp();
+    // pass 4: the hard-sphere slots into the local grid (one writer)
+    if (gl == 0 && live) {
+      for (int s = 0; s < m + j1; ++s) {
+        int a0, a1, a2;
+        if (!lcell_insert(st, lcell(LG, st.fx[s], st.fy[s], st.fz[s], a0, a1, a2), s)) {
+          set_status(P.status, DEV_CAPACITY);
+          st.hdr[3] = 1;
+          break;
+        }
+      }
+    }
+    __syncwarp();
+    if (st.hdr[3]) live = false;
+  }
+  if (!live) m = 0;
+}
+#undef SYS
+
+}  // namespace
+}  // namespace ecmc

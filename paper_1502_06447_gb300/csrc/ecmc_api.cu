@@ -442,6 +442,10 @@ ecmc_status ecmc_configure(ecmc_ctx *c, const ecmc_opts *o) {
   if (lanes == 1 && p.mode != ECMC_MODE_DOMAIN)
     return fail(ECMC_EINVAL, "one lane per EC needs the domain mode");
   if (!(p.p_swap >= 0.0)) return fail(ECMC_EINVAL, "p_swap must be >= 0");
+  if (p.schedule != 0 && p.schedule != 1) return fail(ECMC_EINVAL, "schedule must be 0 or 1");
+  if (p.block_tiles < 0 || p.block_tiles > 32 || p.block_tiles * lanes > 256 ||
+      (p.block_tiles > 0 && lanes > 1 && p.block_tiles % (32 / lanes) != 0))
+    return fail(ECMC_EINVAL, "block_tiles must be a multiple of 32 / lanes, at most 32 and 256 / lanes");
   const double margin = p.precision == ECMC_PREC_FP32F ? 0.01 * sig : 0.0;
   for (int a = 0; a < 3; ++a)
     if (!(s_cap + sig + margin < 0.5 * c->L[a])) return fail(ECMC_EINVAL, "need s_cap + sigma < L/2");
@@ -512,7 +516,10 @@ ecmc_status ecmc_configure(ecmc_ctx *c, const ecmc_opts *o) {
     const int gmin = 32 / lanes;
     if (mcap > stage) mcap = stage;
     const int M = (p.precision == ECMC_PREC_FP32F && p.mode == ECMC_MODE_DOMAIN) ? mcap : stage;
-    const size_t need = ec_smem_bytes(stage, M, (int)ncl, gmin);
+    const bool lock = p.mode == ECMC_MODE_DOMAIN && p.precision == ECMC_PREC_FP32F && p.schedule == 0 &&
+                      (lanes == 4 || lanes == 8 || lanes == 16);
+    const int bt = p.block_tiles > 0 ? p.block_tiles : gmin;
+    const size_t need = lock ? lock_smem_bytes(stage, M, (int)ncl, bt) : ec_smem_bytes(stage, M, (int)ncl, gmin);
     if ((int64_t)need > smem_max)
       return fail(ECMC_EINVAL, "staging needs %lld bytes of shared memory (max %d)",
                   (long long)need, smem_max);
@@ -565,6 +572,12 @@ static ecmc_status reserve_records(ecmc_ctx *c, int64_t units) {
 }
 
 // one EC launch between a pair of events (the pair is reused across runs)
+// the block-lockstep kernel runs the screened domain form with 4, 8 or 16 lanes
+static bool uses_lock(const ecmc_opts &o, int lanes) {
+  return o.mode == ECMC_MODE_DOMAIN && o.precision == ECMC_PREC_FP32F && o.schedule == 0 &&
+         (lanes == 4 || lanes == 8 || lanes == 16);
+}
+
 static cudaError_t timed_ec(ecmc_ctx *c, const ECParams &P, int64_t slot) {
   while ((int64_t)c->kev.size() < slot + 2) {
     cudaEvent_t e;
@@ -574,14 +587,16 @@ static cudaError_t timed_ec(ecmc_ctx *c, const ECParams &P, int64_t slot) {
   }
   cudaError_t err = cudaEventRecord(c->kev[slot], c->stream);
   if (err != cudaSuccess) return err;
-  err = c->lanes == 1 ? launch_ec_lane(P, c->opts.precision == ECMC_PREC_FP32F, c->stream)
-                      : launch_ec(P, c->lanes, c->opts.precision == ECMC_PREC_FP32F, c->stream);
+  if (c->lanes == 1) err = launch_ec_lane(P, c->opts.precision == ECMC_PREC_FP32F, c->stream);
+  else if (uses_lock(c->opts, c->lanes)) err = launch_ec_lock(P, c->lanes, c->stream);
+  else err = launch_ec(P, c->lanes, c->opts.precision == ECMC_PREC_FP32F, c->stream);
   if (err != cudaSuccess) return err;
   return cudaEventRecord(c->kev[slot + 1], c->stream);
 }
 
 static ECParams ec_params(const ecmc_ctx *c, uint64_t seed, double ell) {
   ECParams P{};
+  P.block_tiles = c->opts.block_tiles;
   P.n = c->n;
   P.N = c->N;
   for (int a = 0; a < 3; ++a) {

@@ -121,7 +121,10 @@ cudaError_t batch_sweep(ecmc_batch *b, const ECParams &P, uint64_t seed) {
   C.ctag = b->d_ctag;
   cudaError_t e = launch_cells_batch(C, b->ncell_total, b->stream);
   if (e != cudaSuccess) return e;
-  e = launch_ec_batch(P, b->lanes, b->opts.precision == ECMC_PREC_FP32F, b->stream);
+  const bool lock = b->opts.precision == ECMC_PREC_FP32F && b->opts.schedule == 0 &&
+                    (b->lanes == 4 || b->lanes == 8 || b->lanes == 16);
+  e = lock ? launch_ec_lock_batch(P, b->lanes, b->stream)
+           : launch_ec_batch(P, b->lanes, b->opts.precision == ECMC_PREC_FP32F, b->stream);
   if (e != cudaSuccess) return e;
   return launch_sweep_advance(b->d_sweep, b->stream);
 }
@@ -170,6 +173,7 @@ ECParams batch_params(ecmc_batch *b, uint64_t seed, double ell) {
   P.n_reps = b->R;
   P.ncl_max = b->ncl_max;
   P.sweep_dev = b->d_sweep;
+  P.block_tiles = b->opts.block_tiles;
   return P;
 }
 
@@ -343,7 +347,14 @@ ecmc_status ecmc_batch_configure(ecmc_batch *b, const ecmc_opts *o) {
   BCU(cudaGetDevice(&dev));
   BCU(cudaDeviceGetAttribute(&smem_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
   const int M = p.precision == ECMC_PREC_FP32F ? mcap : stage;
-  if ((int64_t)ec_smem_bytes(stage, M, nclm, 32 / lanes) > smem_max)
+  if (p.schedule != 0 && p.schedule != 1) return bfail(ECMC_EINVAL, "schedule must be 0 or 1");
+  if (p.block_tiles < 0 || p.block_tiles > 32 || p.block_tiles * lanes > 256 ||
+      (p.block_tiles > 0 && p.block_tiles % (32 / lanes)))
+    return bfail(ECMC_EINVAL, "block_tiles must be a multiple of 32 / lanes, at most 32 and 256 / lanes");
+  const bool lock = p.precision == ECMC_PREC_FP32F && p.schedule == 0 && lanes <= 16;
+  const int bt = p.block_tiles > 0 ? p.block_tiles : 32 / lanes;
+  const size_t need = lock ? lock_smem_bytes(stage, M, nclm, bt) : ec_smem_bytes(stage, M, nclm, 32 / lanes);
+  if ((int64_t)need > smem_max)
     return bfail(ECMC_EINVAL, "staging does not fit in shared memory");
   // (re)allocate the concatenated cell arrays
   if (cell_off != b->ncell_total) {

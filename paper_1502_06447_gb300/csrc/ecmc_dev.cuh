@@ -95,4 +95,19 @@ ECMC_HD void fnv_mix(uint64_t &h, uint64_t w) {
   h *= 0x100000001B3ull;
 }
 
+#ifdef __CUDACC__
+// FP32 bounds on a square root and a quotient from the hardware's fast
+// approximations.  rsqrtf errs by at most 2 ulp and __fdividef (divisor in
+// [2^-126, 2^126]) by at most 2 ulp (CUDA's accuracy tables), so after the
+// final product the relative error is below 4e-7 and the factors 1 -+ 1e-6
+// give a lower and an upper bound.  sqrt arguments are raised to 1e-30
+// inside rsqrtf: this keeps 0 finite and moves a result by less than 1e-15
+// in absolute terms, far inside the screen's margin eps_v.
+__device__ __forceinline__ float sqrt_lo(float y) { return y * rsqrtf(fmaxf(y, 1e-30f)) * 0.999999f; }
+__device__ __forceinline__ float sqrt_hi(float y) { return y * rsqrtf(fmaxf(y, 1e-30f)) * 1.000001f; }
+__device__ __forceinline__ float div_lo(float a, float b) { return __fdividef(a, b) * 0.999999f; }
+__device__ __forceinline__ float div_hi(float a, float b) { return __fdividef(a, b) * 1.000001f; }
+
+#endif
+
 }  // namespace ecmc

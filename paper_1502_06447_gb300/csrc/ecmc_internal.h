@@ -100,6 +100,8 @@ struct ECParams {
   int32_t lg[3];
   float linv[3];
   float lorg;
+  // block-lockstep kernel: tiles per block (0: occupancy choice)
+  int32_t block_tiles;
 };
 
 // message for ecmc_last_error (ecmc_api.cu)
@@ -111,6 +113,10 @@ cudaError_t launch_ec_batch(const ECParams &P, int lanes, int fp32f, cudaStream_
 size_t ec_smem_bytes(int stage_cap, int motile_cap, int ncell, int groups_per_block);
 cudaError_t launch_ec_lane(const ECParams &P, int fp32f, cudaStream_t s);
 size_t lane_tile_bytes(int stage_cap, int ncell);
+// block-lockstep kernel of the screened domain form (lanes 4, 8, 16)
+cudaError_t launch_ec_lock(const ECParams &P, int lanes, cudaStream_t s);
+cudaError_t launch_ec_lock_batch(const ECParams &P, int lanes, cudaStream_t s);
+size_t lock_smem_bytes(int stage_cap, int motile_cap, int ncell, int tiles_per_block);
 
 // cell list and domain tags (k_cells.cu)
 struct CellParams {

@@ -434,8 +434,8 @@ __global__ void __launch_bounds__(64) ec_lane_kernel(const ECParams P) {
           const float dd = __fmaf_rn(d2, d2, __fmaf_rn(d1, d1, d0 * d0));
           const float dv = __fmaf_rn(d2, vf2, __fmaf_rn(d1, vf1, d0 * vf0));
           const float rad = b2f - (dd - dv * dv);
-          const float lo = -dv - eps_v + sqrtf(fmaxf(rad - eps_d, 0.f)) * 0.9999998f;
-          const float hi = -dv + eps_v + sqrtf(fmaxf(rad + eps_d, 0.f)) * 1.0000002f;
+          const float lo = -dv - eps_v + sqrt_lo(fmaxf(rad - eps_d, 0.f));
+          const float hi = -dv + eps_v + sqrt_hi(fmaxf(rad + eps_d, 0.f));
           U = fminf(U, fmaxf(hi, 0.f) + 1e-6f);
           keep_s[nk] = (int)tw | (1 << 16);
           keep_l[nk] = fmaxf(lo, 0.f);
@@ -451,9 +451,9 @@ __global__ void __launch_bounds__(64) ec_lane_kernel(const ECParams P) {
           const float Wfa = a == 0 ? Wf0 : (a == 1 ? Wf1 : Wf2);
           const float dist = posv(va) ? Wfa - pfa : pfa;
           const float av = fabsf(vfa);
-          if (av > 0.f) {
-            wall_lb[a] = fmaxf(dist - eps_v, 0.f) / (av * 1.000001f);
-            U = fminf(U, (fmaxf(dist, 0.f) + eps_v) / (av * 0.999999f));
+          if (av >= 1e-30f) {
+            wall_lb[a] = div_lo(fmaxf(dist - eps_v, 0.f), av);
+            U = fminf(U, div_hi(fmaxf(dist, 0.f) + eps_v, av));
           } else {
             wall_lb[a] = 0.f;
           }
@@ -501,8 +501,8 @@ __global__ void __launch_bounds__(64) ec_lane_kernel(const ECParams P) {
           const float disc = sig2f - (dd - dv * dv);
           if (!(dv < eps_v && disc > -eps_d)) continue;
           if (dv < -eps_v && disc > eps_d)
-            U = fminf(U, fmaxf(0.f, -dv + eps_v - sqrtf(disc - eps_d) * 0.9999998f) + 1e-6f);
-          const float lb = -dv - eps_v - sqrtf(disc + eps_d) * 1.0000002f;
+            U = fminf(U, fmaxf(0.f, -dv + eps_v - sqrt_lo(disc - eps_d)) + 1e-6f);
+          const float lb = -dv - eps_v - sqrt_hi(disc + eps_d);
           if (lb > U) continue;
           // keep: drop entries that U has already excluded, then append
           int w = 0;
@@ -566,7 +566,7 @@ __global__ void __launch_bounds__(64) ec_lane_kernel(const ECParams P) {
               if (dd > near2) continue;
               const float dv = __fmaf_rn(d2, vf2, __fmaf_rn(d1, vf1, d0 * vf0));
               const float disc = sig2f - (dd - dv * dv);
-              const float lb = -dv - eps_v - sqrtf(disc + eps_d) * 1.0000002f;
+              const float lb = -dv - eps_v - sqrt_hi(disc + eps_d);
               if (!(dv < eps_v && disc > -eps_d && lb <= U)) continue;
               const int kid = __float_as_int(o.w) & ID_MASK;
               double dvx;

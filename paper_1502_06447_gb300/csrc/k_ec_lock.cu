@@ -1,0 +1,959 @@
+// Block-lockstep EC kernel of the screened domain form (arXiv:1502.06447,
+// Sec. II: EC move; Sec. II.B: tiles, joints and reflections; Sec. II.D:
+// swap move).
+//
+// A block runs NT tiles.  Each tile is staged and screened by a group of G
+// lanes exactly as in ec_kernel, but all NT tiles advance one event per step
+// in lockstep and the FP64 work of the step is packed one tile per lane:
+//   A  every group bounds its pivot's candidates in FP32 (contacts in the 27
+//      local cells, tethers, tile walls) and appends each candidate whose
+//      lower bound can reach the smallest upper bound U to the block's
+//      request list;
+//   B  the requests of all tiles are evaluated in FP64, one per thread;
+//   D  thread t (t < NT) picks tile t's winner among its evaluated requests
+//      and the END/PASS candidate, moves the pivot, lifts, reflects or swaps,
+//      and sets up the next step (or the tile's next EC).
+// An FP64 warp instruction costs the same whatever its active mask, so
+// phases B and D serve up to 32 tiles per FP64 instruction where the G-lane
+// groups of ec_kernel serve 32/G.  Every event is the one ec_kernel (and the
+// oracle) produces: same candidates, same FP64 expressions, same tie rule.
+// A tile whose survivors do not fit the request list (rare) is evaluated
+// exhaustively in FP64 by its own group in phase B.
+#include "ec_device.cuh"
+
+namespace ecmc {
+namespace {
+
+// per-tile record shared by the group (A), the evaluating threads (B) and
+// the owner thread (D)
+struct __align__(16) TileRec {
+  double q[3], v[3];  // pivot position (wrapped FP64) and direction
+  double xrem;        // remaining displacement
+  double c[3];        // tile corner
+  float pf[3], vf[3];
+  float xcap;         // FP32 upper bound of the END/PASS candidate
+  int p;              // pivot slot
+  int active;
+  int vnz;            // bit a: v_a != 0
+  int rq_off, rq_cnt; // this step's requests; rq_cnt < 0: evaluate exhaustively
+  int m, j1;          // staged motile / hard-sphere joint counts
+  int wr;             // bit a: the tile's halo can wrap on axis a
+  int unit, gunit;
+  const RepParams *rp;
+  unsigned long long fb_x, fb_key;  // exhaustive-evaluation result
+  double fb_dv;
+};
+
+struct Res {
+  unsigned long long xb, key;
+  double dv;
+};
+
+constexpr int RQ_PER_TILE = 8;   // request list capacity per tile of the block
+// a lane holds at most four requests per step (pq0..pq3); more send the
+// tile to the exhaustive evaluation
+
+template <int G>
+__device__ __forceinline__ void group_argmin_m(double &bx, uint64_t &bkey, unsigned mask) {
+#pragma unroll
+  for (int off = G / 2; off > 0; off >>= 1) {
+    const double ox = __shfl_xor_sync(mask, bx, off);
+    const uint64_t ok = __shfl_xor_sync(mask, bkey, off);
+    if (better(ox, ok, bx, bkey)) {
+      bx = ox;
+      bkey = ok;
+    }
+  }
+}
+
+__host__ __device__ __forceinline__ size_t lock_tail_bytes(int NT) {
+  return (size_t)NT * sizeof(TileRec) + (size_t)NT * RQ_PER_TILE * (sizeof(int2) + sizeof(Res)) + 16;
+}
+
+#define SYS(f) (BATCH ? rp->f : P.f)
+#define TSYS(R, f) (BATCH ? (R)->f : P.f)
+
+template <int G, bool BATCH>
+__global__ void __launch_bounds__(256) ec_lock_kernel(const ECParams P) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int tid = threadIdx.x;
+  const int lane = tid & 31;
+  const int gl = lane & (G - 1);
+  const int gbase = lane & ~(G - 1);
+  const unsigned gmask = (G == 32) ? FULL : (((1u << G) - 1) << gbase);
+  const int NT = blockDim.x / G;
+  const int gib = tid / G;
+  const int gunit = blockIdx.x * NT + gib;
+  const RepParams *rp = nullptr;
+  int unit = gunit;
+  if (BATCH) {
+    int lo = 0, hi = P.n_reps - 1;
+    const int gu = gunit < P.n_units ? gunit : P.n_units - 1;
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (P.reps[mid].unit_off <= gu) lo = mid;
+      else hi = mid - 1;
+    }
+    rp = P.reps + lo;
+    unit = gunit - (int)rp->unit_off;
+  }
+  double *const Rr = BATCH ? P.r + 3 * rp->bead_off : P.r;
+  const int32_t *const Rstart = BATCH ? P.cstart + rp->cell_off : P.cstart;
+  const int64_t sweep = P.sweep_dev ? *P.sweep_dev : P.sweep;
+  const int S = P.stage_cap;
+  const int NC = BATCH ? P.ncl_max : SYS(lg)[0] * SYS(lg)[1] * SYS(lg)[2];
+  const int M = P.m_cap;
+  const size_t gbytes = group_bytes(S, M, NC);
+  Stage st = carve(smem + (size_t)gib * gbytes, S, M, NC);
+  TileRec *tr = (TileRec *)(smem + (size_t)NT * gbytes);
+  int2 *rq = (int2 *)(tr + NT);
+  Res *rs = (Res *)(rq + NT * RQ_PER_TILE);
+  int *rq_n = (int *)(rs + NT * RQ_PER_TILE);
+  const int RQ_CAP = NT * RQ_PER_TILE;
+  bool live = gunit < P.n_units;
+  LGrid LG;
+  LG.g0 = SYS(lg)[0];
+  LG.g1 = SYS(lg)[1];
+  LG.g2 = SYS(lg)[2];
+  LG.org = SYS(lorg);
+  LG.inv0 = SYS(linv)[0];
+  LG.inv1 = SYS(linv)[1];
+  LG.inv2 = SYS(linv)[2];
+  const uint64_t Rkey = BATCH ? rp->replica : P.replica;
+
+  // ------------------------------------------------------------ staging
+  double c0 = 0.0, c1 = 0.0, c2 = 0.0;
+  if (live) {
+    const int tk0 = unit % SYS(D)[0];
+    const int tk1 = (unit / SYS(D)[0]) % SYS(D)[1];
+    const int tk2 = unit / (SYS(D)[0] * SYS(D)[1]);
+    const u64x4 w = philox(TAG_SHIFT, (uint64_t)sweep, 0, 0, P.seed, Rkey);
+    c0 = unit53(w.v[0]) * SYS(T)[0] + (double)tk0 * SYS(T)[0];
+    c1 = unit53(w.v[1]) * SYS(T)[1] + (double)tk1 * SYS(T)[1];
+    c2 = unit53(w.v[2]) * SYS(T)[2] + (double)tk2 * SYS(T)[2];
+  }
+  int m = 0, j1 = 0, ns = 0;
+  stage_tile<G, true, BATCH>(P, rp, st, gl, live, unit, c0, c1, c2, Rr, Rstart, S, M, NC, LG, m, j1,
+                             ns);
+  if (gl == 0) {
+    TileRec &T = tr[gib];
+    T.c[0] = c0;
+    T.c[1] = c1;
+    T.c[2] = c2;
+    T.m = live ? m : 0;
+    T.j1 = j1;
+    int wr = 0;
+    if (!(c0 - P.halo_te > 0.0 && c0 + SYS(W)[0] + P.halo_te < SYS(L)[0])) wr |= 1;
+    if (!(c1 - P.halo_te > 0.0 && c1 + SYS(W)[1] + P.halo_te < SYS(L)[1])) wr |= 2;
+    if (!(c2 - P.halo_te > 0.0 && c2 + SYS(W)[2] + P.halo_te < SYS(L)[2])) wr |= 4;
+    T.wr = wr;
+    T.unit = unit;
+    T.gunit = gunit;
+    T.rp = rp;
+    T.active = 0;
+    T.rq_cnt = 0;
+  }
+  if (tid == 0) *rq_n = 0;
+  __syncthreads();
+
+  // ------------------------------------------------------------ owner state
+  // thread t < NT owns tile t of the block: its EC state lives in registers
+  const bool owner = tid < NT;
+  const int ot = owner ? tid : 0;
+  const RepParams *orp = tr[ot].rp;
+  const int o_unit = tr[ot].unit, o_gunit = tr[ot].gunit;
+  const bool o_live = owner && o_gunit < P.n_units && tr[ot].m > 0;
+  const int om = tr[ot].m;
+  Stage ost = carve(smem + (size_t)ot * gbytes, S, M, NC);
+  double *const oRr = BATCH ? P.r + 3 * orp->bead_off : P.r;
+  int32_t *const oRi = BATCH ? P.img + 3 * orp->bead_off : P.img;
+  const uint64_t oKey = BATCH ? orp->replica : P.replica;
+  const double oL0 = TSYS(orp, L)[0], oL1 = TSYS(orp, L)[1], oL2 = TSYS(orp, L)[2];
+  const uint64_t ohb0 = dbits(TSYS(orp, half)[0]), ohb1 = dbits(TSYS(orp, half)[1]),
+                 ohb2 = dbits(TSYS(orp, half)[2]);
+  const int owr = tr[ot].wr;
+  const bool owr0 = owr & 1, owr1 = owr & 2, owr2 = owr & 4;
+  const double oc0 = tr[ot].c[0], oc1 = tr[ot].c[1], oc2 = tr[ot].c[2];
+  const float ocf0 = (float)oc0, ocf1 = (float)oc1, ocf2 = (float)oc2;
+  const float oLh0 = 0.5f * (float)oL0, oLh1 = 0.5f * (float)oL1, oLh2 = 0.5f * (float)oL2;
+  LGrid OLG;
+  OLG.g0 = TSYS(orp, lg)[0];
+  OLG.g1 = TSYS(orp, lg)[1];
+  OLG.g2 = TSYS(orp, lg)[2];
+  OLG.org = TSYS(orp, lorg);
+  OLG.inv0 = TSYS(orp, linv)[0];
+  OLG.inv1 = TSYS(orp, linv)[1];
+  OLG.inv2 = TSYS(orp, linv)[2];
+  const int n_ec = P.ecs_per_tile;
+  const uint64_t r1 = (uint64_t)sweep;
+  const uint64_t r2 = (uint64_t)o_unit;
+
+  int e = 0;
+  bool active = false;
+  int p = 0, pid = 0;
+  double q0 = 0.0, q1 = 0.0, q2 = 0.0, v0 = 0.0, v1 = 0.0, v2 = 0.0, xrem = 0.0, lift = 0.0;
+  float pf0 = 0.f, pf1 = 0.f, pf2 = 0.f, vf0 = 0.f, vf1 = 0.f, vf2 = 0.f;
+  int64_t nev = 0, ncontact = 0;
+  u64x4 swr;
+  swr.v[0] = swr.v[1] = swr.v[2] = swr.v[3] = 0;
+  uint64_t h = 0;
+  double lift_all = 0.0, refl_all = 0.0, disp_all = 0.0;
+  unsigned long long cnt[ECMC_NEV];
+#pragma unroll
+  for (int k = 0; k < ECMC_NEV; ++k) cnt[k] = 0;
+  unsigned long long tried = 0, confirmed = 0, nev_all = 0, ecs_done = 0;
+
+  // start EC e of the owned tile: start bead and direction (Sec. II, R6)
+  auto start_ec = [&]() {
+    const uint64_t r0 = TAG_START | ((uint64_t)e << 8);
+    u64x4 w = philox(r0, r1, r2, 0, P.seed, oKey);
+    p = (int)scale_below(w.v[0], (uint64_t)om);
+    if (P.dir_mode == ECMC_DIR_CART3) {
+      const int ax = (int)scale_below(w.v[1], 3);
+      v0 = ax == 0 ? 1.0 : 0.0;
+      v1 = ax == 1 ? 1.0 : 0.0;
+      v2 = ax == 2 ? 1.0 : 0.0;
+    } else {
+      double a = 2.0 * unit53(w.v[1]) - 1.0;
+      double b = 2.0 * unit53(w.v[2]) - 1.0;
+      double c = 2.0 * unit53(w.v[3]) - 1.0;
+      uint64_t att = 0;
+      for (;;) {
+        const double s = a * a + b * b + c * c;
+        if (s > 1e-6 && s <= 1.0) {
+          const double nr = sqrt(s);
+          v0 = a / nr;
+          v1 = b / nr;
+          v2 = c / nr;
+          break;
+        }
+        ++att;
+        w = philox(r0, r1, r2, att, P.seed, oKey);
+        a = 2.0 * unit53(w.v[0]) - 1.0;
+        b = 2.0 * unit53(w.v[1]) - 1.0;
+        c = 2.0 * unit53(w.v[2]) - 1.0;
+      }
+    }
+    pid = ost.id[p];
+    q0 = ost.px[p];
+    q1 = ost.py[p];
+    q2 = ost.pz[p];
+    pf0 = ost.fx[p];
+    pf1 = ost.fy[p];
+    pf2 = ost.fz[p];
+    vf0 = (float)v0;
+    vf1 = (float)v1;
+    vf2 = (float)v2;
+    xrem = P.ell;
+    lift = 0.0;
+    nev = 0;
+    ncontact = 0;
+    swr.v[0] = swr.v[1] = swr.v[2] = swr.v[3] = 0;
+    h = 0xCBF29CE484222325ull;
+    active = true;
+  };
+  // publish the owned tile's state for the next step
+  auto publish = [&]() {
+    TileRec &T = tr[ot];
+    T.active = active ? 1 : 0;
+    if (!active) return;
+    T.q[0] = q0;
+    T.q[1] = q1;
+    T.q[2] = q2;
+    T.v[0] = v0;
+    T.v[1] = v1;
+    T.v[2] = v2;
+    T.xrem = xrem;
+    T.pf[0] = pf0;
+    T.pf[1] = pf1;
+    T.pf[2] = pf2;
+    T.vf[0] = vf0;
+    T.vf[1] = vf1;
+    T.vf[2] = vf2;
+    T.vnz = (nonzero(v0) ? 1 : 0) | (nonzero(v1) ? 2 : 0) | (nonzero(v2) ? 4 : 0);
+    T.xcap = __double2float_ru(dbits(P.s_cap) < dbits(xrem) ? P.s_cap : xrem);
+    T.p = p;
+  };
+  if (o_live) {
+    start_ec();
+    publish();
+  }
+
+  // FP32 screen constants
+  Screen Z;
+  Z.sig2f = (float)P.sig2;
+  Z.eps_v = P.eps_v;
+  Z.eps_d = P.eps_d;
+  {
+    const float reach = (float)(P.s_cap + P.sigma + 0.01 * P.sigma);
+    Z.near2 = reach * reach;
+  }
+  const float b2f = (float)P.b2;
+  const float eps_v = P.eps_v, eps_d = P.eps_d;
+  const float Wf0 = (float)SYS(W)[0], Wf1 = (float)SYS(W)[1], Wf2 = (float)SYS(W)[2];
+  const float INF = __int_as_float(0x7f800000);
+  constexpr int ITEMS = G >= 8 ? 1 : 2;  // special candidates per lane
+
+  for (;;) {
+    if (!__syncthreads_or(o_live && active ? 1 : 0)) break;
+
+    // ---------------------------------------------------------- A: screen
+    {
+      const TileRec &T = tr[gib];
+      const bool act = live && T.active;
+      int a_p = 0;
+      float a0 = 0.f, a1 = 0.f, a2 = 0.f, w0 = 0.f, w1 = 0.f, w2 = 0.f;
+      unsigned nbw = 0xFFFFFFFFu;
+      int vnz = 0;
+      float ubl = INF;
+      if (act) {
+        a_p = T.p;
+        a0 = T.pf[0];
+        a1 = T.pf[1];
+        a2 = T.pf[2];
+        w0 = T.vf[0];
+        w1 = T.vf[1];
+        w2 = T.vf[2];
+        vnz = T.vnz;
+        nbw = st.nb[a_p];
+        if (gl == 0) ubl = T.xcap;
+      }
+      int spk[ITEMS], sps[ITEMS];
+      float spl[ITEMS];
+#pragma unroll
+      for (int r = 0; r < ITEMS; ++r) {
+        spk[r] = -1;
+        sps[r] = -1;
+        spl[r] = INF;
+        const int it = gl + r * G;
+        if (!act || it == 0 || it >= 6) continue;
+        if (it <= 2) {
+          const int t = it == 1 ? nb_prev(nbw) : nb_next(nbw);
+          if (t < 0) continue;
+          const float d0 = a0 - st.fx[t], d1 = a1 - st.fy[t], d2 = a2 - st.fz[t];
+          const float dd = __fmaf_rn(d2, d2, __fmaf_rn(d1, d1, d0 * d0));
+          const float dv = __fmaf_rn(d2, w2, __fmaf_rn(d1, w1, d0 * w0));
+          const float rad = b2f - (dd - dv * dv);
+          const float lo = -dv - eps_v + sqrt_lo(fmaxf(rad - eps_d, 0.f));
+          const float hi = -dv + eps_v + sqrt_hi(fmaxf(rad + eps_d, 0.f));
+          spl[r] = fmaxf(lo, 0.f);
+          ubl = fminf(ubl, fmaxf(hi, 0.f) + 1e-6f);
+          spk[r] = KIND_TETHER;
+          sps[r] = t;
+        } else {
+          const int a = it - 3;
+          if (!((vnz >> a) & 1)) continue;
+          const float vfa = a == 0 ? w0 : (a == 1 ? w1 : w2);
+          const float pfa = a == 0 ? a0 : (a == 1 ? a1 : a2);
+          const float Wfa = a == 0 ? Wf0 : (a == 1 ? Wf1 : Wf2);
+          const float dist = signbit(vfa) ? pfa : Wfa - pfa;
+          const float av = fabsf(vfa);
+          if (av >= 1e-30f) {
+            spl[r] = div_lo(fmaxf(dist - eps_v, 0.f), av);
+            ubl = fminf(ubl, div_hi(fmaxf(dist, 0.f) + eps_v, av));
+          } else {
+            spl[r] = 0.f;  // |v_a| below FP32 range: evaluate in FP64
+          }
+          spk[r] = KIND_WALL;
+          sps[r] = a;
+        }
+      }
+      int pc0 = 0, pc1 = 0, pc2 = 0;
+      lcell(LG, a0, a1, a2, pc0, pc1, pc2);
+      const int n_ovf = st.hdr[4];
+      int ks0 = -1, ks1 = -1;
+      float kl0 = INF, kl1 = INF;
+      bool kovf = false;
+      for (int ci = gl; ci < 28; ci += G) {
+        if (!act) break;
+        if (ci == 27) {
+          for (int i = 0; i < n_ovf; ++i) {
+            const int k = st.ovf[i];
+            if (k == a_p) continue;
+            screen_hs(Z, a0 - st.fx[k], a1 - st.fy[k], a2 - st.fz[k], w0, w1, w2, k, ubl, ks0, kl0,
+                      ks1, kl1, kovf);
+          }
+        } else {
+          const int x = pc0 + ci % 3 - 1, y = pc1 + (ci / 3) % 3 - 1, z = pc2 + ci / 9 - 1;
+          if (x < 0 || y < 0 || z < 0 || x >= LG.g0 || y >= LG.g1 || z >= LG.g2) continue;
+          screen_cell(Z, st, st.cell + 8 * ((z * LG.g1 + y) * LG.g0 + x), a_p, a0, a1, a2, w0, w1, w2,
+                      ubl, ks0, kl0, ks1, kl1, kovf);
+        }
+      }
+      const float U = group_minf<G>(ubl);
+      // survivors of this lane (kind << 28 | slot)
+      int pq0 = 0, pq1 = 0, pq2 = 0, pq3 = 0;
+      int npush = 0;
+      bool over = false;
+      auto push = [&](int code) {
+        if (npush == 0) pq0 = code;
+        else if (npush == 1) pq1 = code;
+        else if (npush == 2) pq2 = code;
+        else if (npush == 3) pq3 = code;
+        else over = true;
+        ++npush;
+      };
+#pragma unroll
+      for (int r = 0; r < ITEMS; ++r)
+        if (spk[r] >= 0 && spl[r] <= U) push((spk[r] << 28) | sps[r]);
+      if (ks0 >= 0 && kl0 <= U) push((KIND_HS << 28) | ks0);
+      if (ks1 >= 0 && kl1 <= U) push((KIND_HS << 28) | ks1);
+      if (act && kovf) {
+        // more than two possible winners in this lane: screen its cells again
+        // against the group's U and keep every one that can reach it
+        for (int ci = gl; ci < 28; ci += G) {
+          int n;
+          const unsigned short *lst;
+          if (ci == 27) {
+            n = n_ovf;
+            lst = st.ovf;
+          } else {
+            const int x = pc0 + ci % 3 - 1, y = pc1 + (ci / 3) % 3 - 1, z = pc2 + ci / 9 - 1;
+            if (x < 0 || y < 0 || z < 0 || x >= LG.g0 || y >= LG.g1 || z >= LG.g2) continue;
+            const unsigned short *c = st.cell + 8 * ((z * LG.g1 + y) * LG.g0 + x);
+            n = c[0];
+            lst = c + 1;
+          }
+          for (int i = 0; i < n; ++i) {
+            const int k = lst[i];
+            if (k == a_p || k == ks0 || k == ks1) continue;
+            bool possible;
+            const float lb = screen_lb(Z, a0 - st.fx[k], a1 - st.fy[k], a2 - st.fz[k], w0, w1, w2,
+                                       possible);
+            if (possible && lb <= U) push((KIND_HS << 28) | k);
+          }
+        }
+      }
+      // reserve the group's slots in the request list
+      const bool gover = (__ballot_sync(FULL, over) & gmask) != 0;
+      int cntl = over ? 0 : npush;
+      int incl = cntl;
+#pragma unroll
+      for (int off = 1; off < G; off <<= 1) {
+        const int y = __shfl_up_sync(FULL, incl, off, G);
+        if (gl >= off) incl += y;
+      }
+      const int total = __shfl_sync(FULL, incl, G - 1, G);
+      int base = 0;
+      if (gl == 0 && act) base = (gover || total == 0) ? 0 : atomicAdd(rq_n, total);
+      base = __shfl_sync(FULL, base, 0, G);
+      const bool fits = act && !gover && base + total <= RQ_CAP;
+      if (act && total > 0 && !gover) {
+        if (fits) {
+          const int at = base + incl - cntl;
+          if (cntl > 0) rq[at] = make_int2(gib, pq0);
+          if (cntl > 1) rq[at + 1] = make_int2(gib, pq1);
+          if (cntl > 2) rq[at + 2] = make_int2(gib, pq2);
+          if (cntl > 3) rq[at + 3] = make_int2(gib, pq3);
+        } else {
+          // reserved slots inside the list carry no request
+          for (int i = base + gl; i < base + total && i < RQ_CAP; i += G) rq[i] = make_int2(-1, 0);
+        }
+      }
+      if (gl == 0 && act) {
+        tr[gib].rq_off = fits ? base : 0;
+        tr[gib].rq_cnt = fits ? total : (total == 0 && !gover ? 0 : -1);
+      }
+    }
+    __syncthreads();
+
+    // ---------------------------------------------------------- B: FP64
+    {
+      const int nreq = *rq_n < RQ_CAP ? *rq_n : RQ_CAP;
+      for (int i = tid; i < nreq; i += blockDim.x) {
+        const int2 r = rq[i];
+        Res out;
+        out.xb = ~0ull;
+        out.key = ~0ull;
+        out.dv = 0.0;
+        if (r.x >= 0) {
+          const TileRec &T = tr[r.x];
+          const RepParams *R = T.rp;
+          const int kind = r.y >> 28;
+          const int k = r.y & 0xFFFFF;
+          const double Q0 = T.q[0], Q1 = T.q[1], Q2 = T.q[2];
+          const double V0 = T.v[0], V1 = T.v[1], V2 = T.v[2];
+          const double L0 = TSYS(R, L)[0], L1 = TSYS(R, L)[1], L2 = TSYS(R, L)[2];
+          const bool W0 = T.wr & 1, W1 = T.wr & 2, W2 = T.wr & 4;
+          ++confirmed;
+          if (kind == KIND_WALL) {
+            const int a = k;
+            const double va = a == 0 ? V0 : (a == 1 ? V1 : V2);
+            const double qa = a == 0 ? Q0 : (a == 1 ? Q1 : Q2);
+            const double ca = T.c[a];
+            const double La = a == 0 ? L0 : (a == 1 ? L1 : L2);
+            const double loc = wrapc(qa - ca, La, dbits(TSYS(R, half)[a]), (T.wr >> a) & 1);
+            double x = posv(va) ? (TSYS(R, W)[a] - loc) / va : (0.0 - loc) / va;
+            if (neg(x)) x = 0.0;
+            out.xb = dbits(x);
+            out.key = make_key(KIND_WALL, a, 0);
+          } else {
+            const bool te = kind == KIND_TETHER;
+            const Stage sk = carve(smem + (size_t)r.x * gbytes, S, M, NC);
+            double kx, ky, kz, dv;
+            double *const Rk = BATCH ? P.r + 3 * R->bead_off : P.r;
+            pos64(sk, Rk, k, k < T.m, kx, ky, kz);
+            const double x =
+                quad_x(te, wrapc(Q0 - kx, L0, dbits(TSYS(R, half)[0]), W0),
+                       wrapc(Q1 - ky, L1, dbits(TSYS(R, half)[1]), W1),
+                       wrapc(Q2 - kz, L2, dbits(TSYS(R, half)[2]), W2), V0, V1, V2,
+                       te ? P.b2 : P.sig2, dv);
+            if (!neg(x)) {
+              out.xb = dbits(x);
+              out.key = make_key(te ? KIND_TETHER : KIND_HS, sk.id[k], k);
+              out.dv = dv;
+            }
+          }
+        }
+        rs[i] = out;
+      }
+      // tiles whose survivors did not fit: exhaustive FP64 evaluation by the
+      // tile's own group (tethers, walls, every contact in the 27 cells)
+      const TileRec &T = tr[gib];
+      if (live && T.active && T.rq_cnt < 0) {
+        const double Q0 = T.q[0], Q1 = T.q[1], Q2 = T.q[2];
+        const double V0 = T.v[0], V1 = T.v[1], V2 = T.v[2];
+        const double L0 = SYS(L)[0], L1 = SYS(L)[1], L2 = SYS(L)[2];
+        const uint64_t hb0 = dbits(SYS(half)[0]), hb1 = dbits(SYS(half)[1]), hb2 = dbits(SYS(half)[2]);
+        const bool W0 = T.wr & 1, W1 = T.wr & 2, W2 = T.wr & 4;
+        const int fp = T.p;
+        const unsigned nbw = st.nb[fp];
+        double bx = __longlong_as_double(0x7ff0000000000000ll);
+        uint64_t bkey = ~0ull;
+        double bdv = 0.0;
+        for (int it = gl; it < 6; it += G) {
+          if (it == 0) continue;
+          if (it <= 2) {
+            const int t = it == 1 ? nb_prev(nbw) : nb_next(nbw);
+            if (t < 0) continue;
+            double kx, ky, kz, dv;
+            pos64(st, Rr, t, t < T.m, kx, ky, kz);
+            const double x = quad_x(true, wrapc(Q0 - kx, L0, hb0, W0), wrapc(Q1 - ky, L1, hb1, W1),
+                                    wrapc(Q2 - kz, L2, hb2, W2), V0, V1, V2, P.b2, dv);
+            const uint64_t key = make_key(KIND_TETHER, st.id[t], t);
+            if (better(x, key, bx, bkey)) {
+              bx = x;
+              bkey = key;
+              bdv = dv;
+            }
+          } else {
+            const int a = it - 3;
+            const double va = a == 0 ? V0 : (a == 1 ? V1 : V2);
+            if (!nonzero(va)) continue;
+            const double qa = a == 0 ? Q0 : (a == 1 ? Q1 : Q2);
+            const double loc = wrapc(qa - T.c[a], SYS(L)[a], dbits(SYS(half)[a]), (T.wr >> a) & 1);
+            double x = posv(va) ? (SYS(W)[a] - loc) / va : (0.0 - loc) / va;
+            if (neg(x)) x = 0.0;
+            const uint64_t key = make_key(KIND_WALL, a, 0);
+            if (better(x, key, bx, bkey)) {
+              bx = x;
+              bkey = key;
+            }
+          }
+        }
+        int pc0 = 0, pc1 = 0, pc2 = 0;
+        lcell(LG, T.pf[0], T.pf[1], T.pf[2], pc0, pc1, pc2);
+        for (int ci = gl; ci < 28; ci += G) {
+          int n;
+          const unsigned short *lst;
+          if (ci == 27) {
+            n = st.hdr[4];
+            lst = st.ovf;
+          } else {
+            const int x = pc0 + ci % 3 - 1, y = pc1 + (ci / 3) % 3 - 1, z = pc2 + ci / 9 - 1;
+            if (x < 0 || y < 0 || z < 0 || x >= LG.g0 || y >= LG.g1 || z >= LG.g2) continue;
+            const unsigned short *c = st.cell + 8 * ((z * LG.g1 + y) * LG.g0 + x);
+            n = c[0];
+            lst = c + 1;
+          }
+          for (int i = 0; i < n; ++i) {
+            const int k = lst[i];
+            if (k == fp) continue;
+            double kx, ky, kz, dv;
+            pos64(st, Rr, k, k < T.m, kx, ky, kz);
+            const double x = quad_x(false, wrapc(Q0 - kx, L0, hb0, W0), wrapc(Q1 - ky, L1, hb1, W1),
+                                    wrapc(Q2 - kz, L2, hb2, W2), V0, V1, V2, P.sig2, dv);
+            ++confirmed;
+            if (!neg(x)) {
+              const uint64_t key = make_key(KIND_HS, st.id[k], k);
+              if (better(x, key, bx, bkey)) {
+                bx = x;
+                bkey = key;
+                bdv = dv;
+              }
+            }
+          }
+        }
+        const uint64_t my_key = bkey;
+        const uint64_t my_x = dbits(bx);
+        group_argmin_m<G>(bx, bkey, gmask);
+        const unsigned own = __ballot_sync(gmask, my_key == bkey && my_x == dbits(bx)) & gmask;
+        const int src = __ffs(own) - 1;
+        const double wdv = __shfl_sync(gmask, bdv, src < 0 ? lane : src);
+        if (gl == 0) {
+          tr[gib].fb_x = dbits(bx);
+          tr[gib].fb_key = bkey;
+          tr[gib].fb_dv = wdv;
+        }
+      }
+    }
+    __syncthreads();
+
+    // ---------------------------------------------------------- D: move
+    if (o_live && active && nev >= P.event_cap) {
+      set_status(P.status, DEV_STUCK);
+      active = false;
+    }
+    if (o_live && active) {
+      double x;
+      uint64_t bkey;
+      double wdv = 0.0;
+      {
+        const TileRec &T = tr[ot];
+        if (dbits(P.s_cap) < dbits(xrem)) {
+          x = P.s_cap;
+          bkey = make_key(KIND_PASS, 0, 0);
+        } else {
+          x = xrem;
+          bkey = make_key(KIND_END, 0, 0);
+        }
+        if (T.rq_cnt < 0) {
+          const double fx = __longlong_as_double((long long)T.fb_x);
+          if (better(fx, T.fb_key, x, bkey)) {
+            x = fx;
+            bkey = T.fb_key;
+            wdv = T.fb_dv;
+          }
+        } else {
+          const int i0 = T.rq_off, i1 = T.rq_off + T.rq_cnt;
+          for (int i = i0; i < i1; ++i) {
+            const unsigned long long xb = rs[i].xb, kb = rs[i].key;
+            if (xb < dbits(x) || (xb == dbits(x) && kb < bkey)) {
+              x = __longlong_as_double((long long)xb);
+              bkey = kb;
+              wdv = rs[i].dv;
+            }
+          }
+        }
+      }
+      const int kind = key_kind(bkey);
+      const int slot = key_slot(bkey);
+      const int64_t partner = (kind == KIND_END || kind == KIND_PASS) ? -1 : key_id(bkey);
+      int di0 = 0, di1 = 0, di2 = 0;
+      if (owr0) di0 = step_i(q0, x, v0, oL0);
+      else q0 = __fma_rn(x, v0, q0);
+      if (owr1) di1 = step_i(q1, x, v1, oL1);
+      else q1 = __fma_rn(x, v1, q1);
+      if (owr2) di2 = step_i(q2, x, v2, oL2);
+      else q2 = __fma_rn(x, v2, q2);
+      if (di0 | di1 | di2) {
+        if (di0) oRi[3 * (int64_t)pid] += di0;
+        if (di1) oRi[3 * (int64_t)pid + 1] += di1;
+        if (di2) oRi[3 * (int64_t)pid + 2] += di2;
+      }
+      ++nev;
+      int out;
+      bool swapped = false;
+      int np = p;
+      if (kind == KIND_END) {
+        out = ECMC_EV_END;
+      } else if (kind == KIND_PASS) {
+        out = ECMC_EV_PASS;
+      } else if (kind == KIND_WALL) {
+        out = ECMC_EV_WALL;
+        if (partner == 0) v0 = -v0;
+        else if (partner == 1) v1 = -v1;
+        else v2 = -v2;
+        vf0 = (float)v0;
+        vf1 = (float)v1;
+        vf2 = (float)v2;
+      } else {
+        // (r_target - r_pivot).v at contact = -(d.v) - x
+        const double proj = -wdv - x;
+        const bool motile = slot < om;
+        if (!motile) {
+          out = kind == KIND_HS ? ECMC_EV_HS_REFLECT : ECMC_EV_TE_REFLECT;
+          refl_all = refl_all + proj;
+          double kx, ky, kz;
+          pos64(ost, oRr, slot, false, kx, ky, kz);
+          mirror2(v0, v1, v2, wrapc(q0 - kx, oL0, ohb0, owr0), wrapc(q1 - ky, oL1, ohb1, owr1),
+                  wrapc(q2 - kz, oL2, ohb2, owr2));
+          vf0 = (float)v0;
+          vf1 = (float)v1;
+          vf2 = (float)v2;
+        } else if (kind == KIND_HS) {
+          lift = lift + proj;
+          if (P.swap_mode) {
+            bool go;
+            if (P.swap_mode == 1) {
+              go = true;
+            } else {
+              if ((ncontact & 3) == 0)
+                swr = philox(TAG_SWAP | ((uint64_t)e << 8), r1, r2, (uint64_t)(ncontact >> 2), P.seed,
+                             oKey);
+              go = (swr.v[ncontact & 3] >> 11) < P.swap_thr;
+            }
+            ++ncontact;
+            if (go) {
+              ++tried;
+              const double k0 = ost.px[slot], k1 = ost.py[slot], k2 = ost.pz[slot];
+              // every bond of both beads, positions exchanged, within b_max
+              bool ok = true;
+#pragma unroll
+              for (int side = 0; side < 2; ++side) {
+                const int a = side == 0 ? p : slot;
+                const double a0 = side == 0 ? k0 : q0;
+                const double a1 = side == 0 ? k1 : q1;
+                const double a2 = side == 0 ? k2 : q2;
+                const unsigned nbv = ost.nb[a];
+#pragma unroll
+                for (int dir = 0; dir < 2; ++dir) {
+                  const int b = dir == 0 ? nb_prev(nbv) : nb_next(nbv);
+                  if (b < 0) continue;
+                  double b0, b1, b2;
+                  if (b == p) {
+                    b0 = k0;
+                    b1 = k1;
+                    b2 = k2;
+                  } else if (b == slot) {
+                    b0 = q0;
+                    b1 = q1;
+                    b2 = q2;
+                  } else {
+                    pos64(ost, oRr, b, b < om, b0, b1, b2);
+                  }
+                  const double e0 = wrapc(a0 - b0, oL0, ohb0, owr0);
+                  const double e1 = wrapc(a1 - b1, oL1, ohb1, owr1);
+                  const double e2 = wrapc(a2 - b2, oL2, ohb2, owr2);
+                  const double dd = __fma_rn(e2, e2, __fma_rn(e1, e1, e0 * e0));
+                  ok = ok && !(dbits(dd) > dbits(P.b2));
+                }
+              }
+              if (ok) {
+                swapped = true;
+                ost.px[slot] = q0;
+                ost.py[slot] = q1;
+                ost.pz[slot] = q2;
+                const int kid = ost.id[slot];
+#pragma unroll
+                for (int a = 0; a < 3; ++a) {
+                  const int ti = oRi[3 * (int64_t)pid + a];
+                  oRi[3 * (int64_t)pid + a] = oRi[3 * (int64_t)kid + a];
+                  oRi[3 * (int64_t)kid + a] = ti;
+                }
+                q0 = k0;
+                q1 = k1;
+                q2 = k2;
+              }
+            }
+          }
+          if (swapped) {
+            out = ECMC_EV_SWAP;
+          } else {
+            out = ECMC_EV_HS_LIFT;
+            np = slot;
+          }
+        } else {
+          lift = lift + proj;
+          out = ECMC_EV_TE_LIFT;
+          np = slot;
+        }
+      }
+#pragma unroll
+      for (int k = 0; k < ECMC_NEV; ++k) cnt[k] += (out == k);
+      // FP32 shadow of the moved pivot: FP32 position minus FP32 corner
+      float nf0 = (float)q0 - ocf0, nf1 = (float)q1 - ocf1, nf2 = (float)q2 - ocf2;
+      if (owr0) nf0 = nf0 > oLh0 ? nf0 - (float)oL0 : (nf0 < -oLh0 ? nf0 + (float)oL0 : nf0);
+      if (owr1) nf1 = nf1 > oLh1 ? nf1 - (float)oL1 : (nf1 < -oLh1 ? nf1 + (float)oL1 : nf1);
+      if (owr2) nf2 = nf2 > oLh2 ? nf2 - (float)oL2 : (nf2 < -oLh2 ? nf2 + (float)oL2 : nf2);
+      fnv_mix(h, (uint64_t)pid);
+      fnv_mix(h, ((uint64_t)(uint32_t)out << 32) | (uint64_t)(uint32_t)partner);
+      fnv_mix(h, dbits(x));
+      if (P.log) {
+        const unsigned long long at = atomicAdd(P.log_n, 1ull);
+        if ((int64_t)at < P.log_cap) {
+          ecmc_event ev;
+          ev.unit = P.rec_offset + (P.sweep_dev ? (sweep - P.rec_sweep0) * P.n_units * n_ec : 0) +
+                    (int64_t)o_gunit * n_ec + e;
+          ev.seq = (int32_t)(nev - 1);
+          ev.pivot = pid;
+          ev.kind = out;
+          ev.pad = 0;
+          ev.partner = partner;
+          ev.x = x;
+          P.log[at] = ev;
+        }
+      }
+      ost.px[p] = q0;
+      ost.py[p] = q1;
+      ost.pz[p] = q2;
+      {
+        // keep the local grid current
+        int a0, a1, a2, b0, b1, b2;
+        const int oc = lcell(OLG, pf0, pf1, pf2, a0, a1, a2);
+        const int ncl = lcell(OLG, nf0, nf1, nf2, b0, b1, b2);
+        if (swapped) {
+          const double o0 = ost.px[slot], o1 = ost.py[slot], o2 = ost.pz[slot];
+          float g0 = (float)o0 - ocf0, g1 = (float)o1 - ocf1, g2 = (float)o2 - ocf2;
+          if (owr0) g0 = g0 > oLh0 ? g0 - (float)oL0 : (g0 < -oLh0 ? g0 + (float)oL0 : g0);
+          if (owr1) g1 = g1 > oLh1 ? g1 - (float)oL1 : (g1 < -oLh1 ? g1 + (float)oL1 : g1);
+          if (owr2) g2 = g2 > oLh2 ? g2 - (float)oL2 : (g2 < -oLh2 ? g2 + (float)oL2 : g2);
+          const int koc = lcell(OLG, ost.fx[slot], ost.fy[slot], ost.fz[slot], a0, a1, a2);
+          const int knc = lcell(OLG, g0, g1, g2, b0, b1, b2);
+          lcell_remove(ost, oc, p);
+          lcell_remove(ost, koc, slot);
+          ost.fx[slot] = g0;
+          ost.fy[slot] = g1;
+          ost.fz[slot] = g2;
+          bool ok = lcell_insert(ost, ncl, p);
+          ok = lcell_insert(ost, knc, slot) && ok;
+          if (!ok) set_status(P.status, DEV_CAPACITY);
+        } else if (oc != ncl) {
+          lcell_remove(ost, oc, p);
+          if (!lcell_insert(ost, ncl, p)) set_status(P.status, DEV_CAPACITY);
+        }
+      }
+      ost.fx[p] = nf0;
+      ost.fy[p] = nf1;
+      ost.fz[p] = nf2;
+      pf0 = nf0;
+      pf1 = nf1;
+      pf2 = nf2;
+      if (out == ECMC_EV_END) {
+        active = false;
+      } else {
+        xrem = xrem - x;
+      }
+      if (active && np != p) {
+        p = np;
+        pid = ost.id[p];
+        q0 = ost.px[p];
+        q1 = ost.py[p];
+        q2 = ost.pz[p];
+        pf0 = ost.fx[p];
+        pf1 = ost.fy[p];
+        pf2 = ost.fz[p];
+      }
+    }
+    // end of an EC: records, then the tile's next EC
+    if (o_live && !active && e < n_ec) {
+      lift_all = lift_all + lift;
+      disp_all = disp_all + P.ell;  // the free flights of an EC add up to ell
+      nev_all += (unsigned long long)nev;
+      ++ecs_done;
+      if (P.rec_digest) {
+        const int64_t idx = P.rec_offset + (P.sweep_dev ? (sweep - P.rec_sweep0) * P.n_units * n_ec : 0) +
+                            (int64_t)o_gunit * n_ec + e;
+        if (idx < P.rec_cap) {
+          P.rec_digest[idx] = h;
+          P.rec_lift[idx] = lift;
+          P.rec_events[idx] = nev;
+        }
+      }
+      ++e;
+      if (e < n_ec) start_ec();
+    }
+    if (owner) publish();
+    if (tid == 0) *rq_n = 0;
+  }
+
+  // ------------------------------------------------------------ counters
+  if (confirmed) atomicAdd(&P.counters[CNT_CONFIRMED], confirmed);
+  if (o_live && ecs_done) {
+#pragma unroll
+    for (int k = 0; k < ECMC_NEV; ++k)
+      if (cnt[k]) atomicAdd(&P.counters[k], cnt[k]);
+    atomicAdd(&P.counters[CNT_EVENTS], nev_all);
+    if (tried) atomicAdd(&P.counters[CNT_SWAP_TRIED], tried);
+    atomicAdd(&P.counters[CNT_ECS], ecs_done);
+    atomicAdd(&P.sums[SUM_LIFT], lift_all);
+    atomicAdd(&P.sums[SUM_REFL], refl_all);
+    atomicAdd(&P.sums[SUM_DISP], disp_all);
+  }
+  __syncthreads();
+  // ------------------------------------------------------------ write back
+  if (live) {
+    for (int s = gl; s < m; s += G) {
+      const int64_t b = st.id[s];
+      Rr[3 * b] = st.px[s];
+      Rr[3 * b + 1] = st.py[s];
+      Rr[3 * b + 2] = st.pz[s];
+    }
+  }
+}
+#undef TSYS
+#undef SYS
+
+}  // namespace
+
+size_t lock_smem_bytes(int stage_cap, int motile_cap, int ncell, int tiles_per_block) {
+  return (size_t)tiles_per_block * group_bytes(stage_cap, motile_cap, ncell) +
+         lock_tail_bytes(tiles_per_block);
+}
+
+template <int G, bool BATCH>
+static cudaError_t launch_lock_t(const ECParams &P, cudaStream_t s) {
+  static int smem_max = 0;
+  if (!smem_max) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&smem_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(ec_lock_kernel<G, BATCH>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             smem_max);
+    if (e != cudaSuccess) return e;
+  }
+  // tiles per block: whole warps, at most 32 (the owners fill warp 0) and
+  // 256 threads; among those, the most tiles resident per SM
+  const int NC = P.domain ? (BATCH ? P.ncl_max : P.lg[0] * P.lg[1] * P.lg[2]) : 0;
+  const int step = 32 / G > 1 ? 32 / G : 1;
+  static size_t memo_key = 0;
+  static int memo_nt = 0;
+  const size_t key = lock_smem_bytes(P.stage_cap, P.m_cap, NC, 1) * 64 + (size_t)P.n_units % 64;
+  int nt = 0;
+  if (P.block_tiles > 0) {
+    nt = P.block_tiles;
+  } else if (memo_key == key && memo_nt) {
+    nt = memo_nt;
+  } else {
+    int best = -1;
+    for (int t = step; t <= 32 && t * G <= 256; t += step) {
+      const size_t sm = lock_smem_bytes(P.stage_cap, P.m_cap, NC, t);
+      if (sm > (size_t)smem_max) break;
+      int blocks = 0;
+      if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, ec_lock_kernel<G, BATCH>, t * G, sm) !=
+          cudaSuccess)
+        return cudaErrorInvalidValue;
+      const int resident = blocks * t;
+      if (resident > best) {
+        best = resident;
+        nt = t;
+      }
+    }
+    memo_key = key;
+    memo_nt = nt;
+  }
+  if (nt == 0 || nt > 32 || nt * G > 256 || (nt * G) % 32) return cudaErrorInvalidValue;
+  const size_t smem = lock_smem_bytes(P.stage_cap, P.m_cap, NC, nt);
+  if (smem > (size_t)smem_max) return cudaErrorInvalidValue;
+  const int blocks = (P.n_units + nt - 1) / nt;
+  ec_lock_kernel<G, BATCH><<<blocks, nt * G, smem, s>>>(P);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_ec_lock(const ECParams &P, int lanes, cudaStream_t s) {
+  if (!P.domain) return cudaErrorInvalidValue;
+  if (lanes == 8) return launch_lock_t<8, false>(P, s);
+  if (lanes == 4) return launch_lock_t<4, false>(P, s);
+  if (lanes == 16) return launch_lock_t<16, false>(P, s);
+  return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_ec_lock_batch(const ECParams &P, int lanes, cudaStream_t s) {
+  if (lanes == 8) return launch_lock_t<8, true>(P, s);
+  if (lanes == 4) return launch_lock_t<4, true>(P, s);
+  if (lanes == 16) return launch_lock_t<16, true>(P, s);
+  return cudaErrorInvalidValue;
+}
+
+}  // namespace ecmc

@@ -45,7 +45,8 @@ class Opts(C.Structure):
                 ("tiles", C.c_int32 * 3), ("joint", C.c_double), ("s_cap", C.c_double),
                 ("event_cap", C.c_int64), ("p_swap", C.c_double), ("ecs_per_tile", C.c_int32),
                 ("lanes", C.c_int32), ("record", C.c_int32), ("stage_cap", C.c_int32),
-                ("cell_side", C.c_double), ("tile_side", C.c_double)]
+                ("cell_side", C.c_double), ("tile_side", C.c_double), ("schedule", C.c_int32),
+                ("block_tiles", C.c_int32)]
 
 
 class Obs(C.Structure):
@@ -144,7 +145,7 @@ def _p(a, ct):
 
 def opts(mode=MODE_SERIAL, dir_mode=DIR_CART3, precision=PREC_FP64, tiles=(3, 3, 3), joint=0.0,
          s_cap=0.0, event_cap=0, p_swap=0.0, ecs_per_tile=0, lanes=0, record=0, stage_cap=0,
-         cell_side=0.0, tile_side=0.0) -> Opts:
+         cell_side=0.0, tile_side=0.0, schedule=0, block_tiles=0) -> Opts:
     o = Opts()
     o.mode, o.dir_mode, o.precision = int(mode), int(dir_mode), int(precision)
     for a in range(3):
@@ -153,6 +154,7 @@ def opts(mode=MODE_SERIAL, dir_mode=DIR_CART3, precision=PREC_FP64, tiles=(3, 3,
     o.p_swap, o.ecs_per_tile, o.lanes = float(p_swap), int(ecs_per_tile), int(lanes)
     o.record, o.stage_cap, o.cell_side = int(record), int(stage_cap), float(cell_side)
     o.tile_side = float(tile_side)
+    o.schedule, o.block_tiles = int(schedule), int(block_tiles)
     return o
 
 

@@ -37,9 +37,11 @@ def oracle_replica(sp, r, tiles, ell, sweeps, p_swap=0.0, jitter=JITTER):
     return o, res
 
 
-def check_batch(specs, lanes, prec, graph, sweeps=3, ell=3.0, p_swap=0.0, jitter=JITTER):
+def check_batch(specs, lanes, prec, graph, sweeps=3, ell=3.0, p_swap=0.0, jitter=JITTER,
+                schedule=0):
     b = ecmc.Batch(specs, jitter=jitter, seed=SEED)
-    b.configure(dir_mode=ecmc.DIR_ISO, precision=prec, lanes=lanes, record=1, p_swap=p_swap)
+    b.configure(dir_mode=ecmc.DIR_ISO, precision=prec, lanes=lanes, record=1, p_swap=p_swap,
+                schedule=schedule)
     b.run(ell, seed=SEED, n_sweeps=sweeps, graph=graph)
     units = sum(int(np.prod(b.info(r)[0])) for r in range(len(specs)))
     dig, _, _ = b.records(sweeps * units)
@@ -55,14 +57,17 @@ def check_batch(specs, lanes, prec, graph, sweeps=3, ell=3.0, p_swap=0.0, jitter
 
 
 @pytest.mark.parametrize("graph", [True, False])
-@pytest.mark.parametrize("lanes,prec", [(8, ecmc.PREC_FP32F), (16, ecmc.PREC_FP32F),
-                                        (32, ecmc.PREC_FP64)])
-def test_batch_replicas_match_oracle(lanes, prec, graph):
-    check_batch(ragged_specs(), lanes, prec, graph)
+@pytest.mark.parametrize("lanes,prec,schedule", [(8, ecmc.PREC_FP32F, 0), (16, ecmc.PREC_FP32F, 0),
+                                                 (4, ecmc.PREC_FP32F, 0), (8, ecmc.PREC_FP32F, 1),
+                                                 (32, ecmc.PREC_FP64, 0)])
+def test_batch_replicas_match_oracle(lanes, prec, schedule, graph):
+    check_batch(ragged_specs(), lanes, prec, graph, schedule=schedule)
 
 
-def test_batch_swap_matches_oracle():
-    check_batch(ragged_specs()[:3], 8, ecmc.PREC_FP32F, True, p_swap=0.5, ell=5.0)
+@pytest.mark.parametrize("schedule", [0, 1])
+def test_batch_swap_matches_oracle(schedule):
+    check_batch(ragged_specs()[:3], 8, ecmc.PREC_FP32F, True, p_swap=0.5, ell=5.0,
+                schedule=schedule)
 
 
 def test_batch_c4_replicas_sample():

@@ -105,14 +105,19 @@ RAGGED = Melt("ragged_15x17x16_N8", (15, 17, 16), 1.05, 8, ell=4.0, seed=0xEC00A
               mode="domain", dir_mode="iso", sweeps=3, D=(3, 4, 3))
 
 
+@pytest.mark.parametrize("schedule", [0, 1])
 @pytest.mark.parametrize("lanes", [32, 16, 8, 4, 1])
 @pytest.mark.parametrize("prec", ["fp64", "fp32f"])
 @pytest.mark.parametrize("m", [small_domain(), RAGGED], ids=lambda m: m.name)
-def test_domain_parity_small(m, prec, lanes):
+def test_domain_parity_small(m, prec, lanes, schedule):
+    """schedule 0 runs the screened form with 4-16 lanes in the block-lockstep
+    kernel, schedule 1 in the warp-lockstep kernel; other settings ignore it."""
+    if schedule == 1 and not (prec == "fp32f" and lanes in (4, 8, 16)):
+        pytest.skip("schedule only selects among screened 4/8/16-lane kernels")
     o = oracle_system(m)
     res = o.run_domain(m.sweeps, m.ell, digests=True)
     assert res["rc"] == 0
-    ctx = gpu_context(m, precision=PRECS[prec], lanes=lanes)
+    ctx = gpu_context(m, precision=PRECS[prec], lanes=lanes, schedule=schedule)
     ctx.run(m.ell, seed=m.seed, n_sweeps=m.sweeps)
     nt = m.D[0] * m.D[1] * m.D[2]
     dig, lift, ev = ctx.records(m.sweeps * nt)
@@ -125,14 +130,37 @@ def test_domain_parity_small(m, prec, lanes):
         assert obs[k] == v, k
 
 
-@pytest.mark.parametrize("lanes", [32, 8, 1])
-def test_domain_two_ecs_per_tile(lanes):
+@pytest.mark.parametrize("lanes,schedule", [(32, 0), (8, 0), (8, 1), (16, 0), (1, 0)])
+def test_domain_two_ecs_per_tile(lanes, schedule):
     m = small_domain(seed=0xEC00A3)
     o = oracle_system(m, ecs_per_tile=2)
     res = o.run_domain(2, m.ell, digests=True)
-    ctx = gpu_context(m, ecs_per_tile=2, lanes=lanes, precision=ecmc.PREC_FP32F)
+    ctx = gpu_context(m, ecs_per_tile=2, lanes=lanes, precision=ecmc.PREC_FP32F,
+                      schedule=schedule)
     ctx.run(m.ell, seed=m.seed, n_sweeps=2)
     dig, _, _ = ctx.records(2 * 27 * 2)
+    assert (dig == res["digest"]).all()
+    assert_same_state(ctx, o)
+
+
+# 252 tiles of side 4.2: 32 of them fit one block's shared memory, and no
+# block size divides 252
+BLOCKS = Melt("blocks_24x24x28_N8", (24, 24, 28), 1.05, 8, ell=4.0, seed=0xEC00A6, mode="domain",
+              dir_mode="iso", sweeps=2, D=(6, 6, 7))
+
+
+@pytest.mark.parametrize("lanes,block_tiles", [(8, 4), (8, 8), (8, 32), (4, 8), (4, 32), (16, 2),
+                                               (16, 16)])
+def test_block_lockstep_block_sizes(lanes, block_tiles):
+    """Every block size of the block-lockstep kernel (tiles per block from
+    32 / lanes to 32, full and ragged last blocks) gives the oracle's events."""
+    m = BLOCKS
+    o = oracle_system(m)
+    res = o.run_domain(m.sweeps, m.ell, digests=True)
+    ctx = gpu_context(m, precision=ecmc.PREC_FP32F, lanes=lanes, block_tiles=block_tiles)
+    ctx.run(m.ell, seed=m.seed, n_sweeps=m.sweeps)
+    nt = m.D[0] * m.D[1] * m.D[2]
+    dig, _, _ = ctx.records(m.sweeps * nt)
     assert (dig == res["digest"]).all()
     assert_same_state(ctx, o)
 
@@ -144,7 +172,7 @@ def c2_oracle():
     return o, res
 
 
-@pytest.mark.parametrize("lanes", [32, 8, 1])
+@pytest.mark.parametrize("lanes", [32, 16, 8, 4, 1])
 @pytest.mark.parametrize("prec", ["fp64", "fp32f"])
 def test_domain_parity_c2_full_size(c2_oracle, prec, lanes):
     """C2 at full size (4096 x 64 beads, 16^3 tiles): three sweeps identical."""
@@ -171,13 +199,13 @@ def test_run_split_equals_one_run():
 
 
 # ------------------------------------------------------------------ swap
-@pytest.mark.parametrize("lanes", [32, 8, 1])
+@pytest.mark.parametrize("lanes,schedule", [(32, 0), (8, 0), (8, 1), (4, 0), (1, 0)])
 @pytest.mark.parametrize("p_swap", [0.5, 1.0])
-def test_swap_parity_domain(p_swap, lanes):
+def test_swap_parity_domain(p_swap, lanes, schedule):
     m = small_domain(p_swap=p_swap, seed=0xEC00A4, ell=6.0)
     o = oracle_system(m)
     res = o.run_domain(3, m.ell, digests=True)
-    ctx = gpu_context(m, lanes=lanes, precision=ecmc.PREC_FP32F)
+    ctx = gpu_context(m, lanes=lanes, precision=ecmc.PREC_FP32F, schedule=schedule)
     ctx.run(m.ell, seed=m.seed, n_sweeps=3)
     dig, _, _ = ctx.records(3 * 27)
     assert (dig == res["digest"]).all()
