@@ -59,6 +59,22 @@ def bytes_per_event(phi, confirmed_per_event, fp32f=True):
     return 24.0 * nbar + 216.0 + 72.0 + 24.0
 
 
+def measured_traffic(kernel):
+    """DRAM bytes per launch of `kernel` on this workload from the committed
+    ncu summary, or None when the summary is for another kernel."""
+    import re
+    p = os.path.join(ROOT, "profiles", "launches_bench_1e6_melt.md")
+    try:
+        txt = open(p).read()
+    except OSError:
+        return None
+    k = re.search(r"^kernel = (.+)$", txt, re.M)
+    b = re.search(r"^dram_bytes_per_launch = ([0-9.eE+]+)$", txt, re.M)
+    if not (k and b and kernel and k.group(1).strip() == kernel and C5.name == "c5_swap_1m"):
+        return None
+    return float(b.group(1))
+
+
 def load_peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     try:
@@ -226,13 +242,8 @@ def run_gpu(args, rank, world):
     phi = C5.phi
     bpe = bytes_per_event(phi, confirmed / max(events, 1))
     achieved = events * bpe / ec_s / 1e9
-    traffic = None
-    prof = os.path.join(ROOT, "profiles", "ec_kernel_traffic.json")
-    if os.path.exists(prof):
-        try:
-            traffic = json.load(open(prof)).get("bytes_per_launch")
-        except Exception:
-            traffic = None
+    traffic = measured_traffic(f"ec_lock_kernel<{tune['lanes'] if tune else args.lanes}, 0>"
+                               if args.schedule == 0 else None)
     n_beads = C5.n
     value = tot_events / max_dev
     line = {
@@ -268,7 +279,9 @@ def run_gpu(args, rank, world):
         "wall_s": max_wall,
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
                      "frac": achieved / hbm, "traffic": traffic,
-                     "kernel": f"ec_kernel<{tune['lanes'] if tune else args.lanes},true,false>",
+                     "kernel": (f"ec_lock_kernel<{tune['lanes'] if tune else args.lanes}, 0>"
+                                if args.schedule == 0 else
+                                f"ec_kernel<{tune['lanes'] if tune else args.lanes}, 1, 0>"),
                      "bytes_per_event": bpe,
                      "kernel_share_of_step": ec_s / dev_s, "peak_source": peak_src},
         "e2e": {"value": e2e_events / e2e_s, "unit": UNIT,
