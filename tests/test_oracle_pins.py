@@ -349,3 +349,50 @@ def test_domain_tags_partition_geometry():
     dist = np.linalg.norm(d, axis=2)
     diff = tags[sub][:, None] != tags[sub][None, :]
     assert dist[diff].min() > w
+
+
+# ---------------------------------------------------------------- observables
+def test_chain_end_to_end_closed_forms():
+    """R_e^2 and bond lengths of chains built from known bond vectors and
+    wrapped into the box: R_e = sum of the bond vectors (the construction),
+    independent of how the oracle undoes the wrapping."""
+    L = np.array([10.0, 9.0, 11.0])
+    rng = np.random.default_rng(7)
+    N, nch = 7, 3
+    r = np.zeros((N * nch, 3))
+    expect_re2, expect_b = [], []
+    for c in range(nch):
+        if c == 0:  # straight along x through the x = L boundary
+            b = np.tile([1.1, 0.0, 0.0], (N - 1, 1))
+            start = np.array([7.0, 4.5, 5.5])
+        else:  # random directions, lengths in [1, 1.2]
+            u = rng.normal(size=(N - 1, 3))
+            b = u / np.linalg.norm(u, axis=1)[:, None] * rng.uniform(1.0, 1.2, size=(N - 1, 1))
+            start = rng.uniform(0, 1, 3) * L
+        pos = start + np.vstack([np.zeros(3), np.cumsum(b, axis=0)])
+        r[c * N:(c + 1) * N] = np.mod(pos, L)
+        expect_re2.append(float(np.sum(b.sum(axis=0) ** 2)))
+        expect_b.extend(np.linalg.norm(b, axis=1))
+    s = oracle.System(r, L, N)
+    re2, bonds = s.chain_obs()
+    assert abs(re2[0] - (6 * 1.1) ** 2) < 1e-12
+    assert np.allclose(re2, expect_re2, rtol=1e-12, atol=1e-12)
+    assert np.allclose(bonds, expect_b, rtol=1e-12, atol=1e-12)
+
+
+def test_unwrapped_displacement_is_ell_along_each_ec_direction():
+    """Serial ECs with v in {+x,+y,+z}: every free flight moves one bead along
+    v, so the summed unwrapped displacement of all beads is ell times the sum
+    of the ECs' directions (pins the image counters behind g1)."""
+    from paper_1502_06447_gb300.configs import C1
+    r = oracle.lattice(C1.dims, C1.spacing, C1.jitter, C1.seed)
+    s = oracle.System(r, C1.L, C1.N, dir_mode=DIR_CART3, seed=C1.seed)
+    u0 = s.unwrapped().copy()
+    n_ec = 2000
+    assert s.run_serial(n_ec, C1.ell)["rc"] == 0
+    _, v = s.start_draws(n_ec)
+    moved = (s.unwrapped() - u0).sum(axis=0)
+    expect = C1.ell * v.sum(axis=0)
+    assert np.allclose(moved, expect, rtol=0, atol=1e-8 * n_ec)
+    # a wrong image sign would be off by whole box lengths
+    assert np.abs(moved - expect).max() < 1e-3
