@@ -45,6 +45,9 @@ SWAP_RATE = 0.1
 METRIC = "events/s (EC sweep, 1e6-bead melt, FP32 screen + FP64 confirm)"
 UNIT = "events/s"
 C0 = 1.2  # stencil cell side of the bytes-per-event definition (= b_max)
+# revision of the block-lockstep kernel; DRAM counters in profiles/ are used
+# only when they were taken on the same revision
+KERNEL_REV = 2
 
 
 def bytes_per_event(phi, confirmed_per_event, fp32f=True):
@@ -242,8 +245,8 @@ def run_gpu(args, rank, world):
     phi = C5.phi
     bpe = bytes_per_event(phi, confirmed / max(events, 1))
     achieved = events * bpe / ec_s / 1e9
-    traffic = measured_traffic(f"ec_lock_kernel<{tune['lanes'] if tune else args.lanes}, 0>"
-                               if args.schedule == 0 else None)
+    traffic = measured_traffic(f"ec_lock_kernel<{tune['lanes'] if tune else args.lanes}, 0> "
+                               f"rev {KERNEL_REV}" if args.schedule == 0 else None)
     n_beads = C5.n
     value = tot_events / max_dev
     line = {

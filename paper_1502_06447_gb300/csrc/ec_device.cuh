@@ -132,38 +132,42 @@ __device__ __forceinline__ float wrapf(float d, float L) {
 }
 
 // ---------------------------------------------------------------- staging
-// Shared memory of one group: FP64 positions and bond-partner words of the
-// first M slots (M = the motile capacity in the screened domain form, where
-// joint beads' FP64 positions, static during a sweep, are read from the
-// global array when a confirmation needs them; M = S otherwise); FP32 shadow
-// (12 B) and id (4 B) of all S slots; the local cell grid (16 B per cell:
-// count + 7 slots); the overflow list of beads whose cell was full; a header.
-constexpr int CELL_CAP = 7;
+// Shared memory of one group: FP64 positions of the first M64 slots (the
+// warp-lockstep kernel: M64 = the motile capacity in the screened domain
+// form, where joint beads' FP64 positions, static during a sweep, are read
+// from the global array when an evaluation needs them, M64 = S otherwise;
+// the block-lockstep kernel keeps every FP64 position in the global array,
+// M64 = 0); bond-partner words of the first MNB slots (the motile beads);
+// FP32 shadow (12 B) and id (4 B) of all S slots; the local cell grid (16 B
+// per cell: a 32-bit count, then 6 slots of 16 bits); the overflow list of
+// beads whose cell was full; a header.
+constexpr int CELL_CAP = 6;
 constexpr int OVF_CAP = 64;
 constexpr int HDR_BYTES = 32;
 
 struct Stage {
-  double *px, *py, *pz;  // [M]
-  unsigned *nb;          // [M] bond partner slots, 16 + 16 bits (0xFFFF = none)
+  double *px, *py, *pz;  // [M64]
+  unsigned *nb;          // [MNB] bond partner slots, 16 + 16 bits (0xFFFF = none)
   float *fx, *fy, *fz;   // [S]
   int *id;               // [S]
-  unsigned short *cell;  // [NC][8]: count, then up to 7 slots
+  unsigned short *cell;  // [NC][8]: 32-bit count, then up to 6 slots
   unsigned short *ovf;   // [OVF_CAP]
   int *hdr;              // [2] staged count, [3] overflow, [4] overflow-list length
 };
 
-__host__ __device__ __forceinline__ size_t group_bytes(int S, int M, int NC) {
-  return (size_t)M * 28 + (size_t)S * 16 + (size_t)NC * 16 + OVF_CAP * 2 + HDR_BYTES;
-}  // (16 B per cell: a count and 7 slots of 16 bits)
+__host__ __device__ __forceinline__ size_t group_bytes(int S, int M64, int MNB, int NC) {
+  return (size_t)M64 * 24 + (size_t)MNB * 4 + (size_t)S * 16 + (size_t)NC * 16 + OVF_CAP * 2 +
+         HDR_BYTES;
+}  // (16 B per cell: a 32-bit count and 6 slots of 16 bits)
 
-// S and M are multiples of 32, so every array starts 16-byte aligned
-__device__ __forceinline__ Stage carve(unsigned char *base, int S, int M, int NC) {
+// S, M64 and MNB are multiples of 32, so every array starts 16-byte aligned
+__device__ __forceinline__ Stage carve(unsigned char *base, int S, int M64, int MNB, int NC) {
   Stage s;
   s.px = (double *)base;
-  s.py = s.px + M;
-  s.pz = s.py + M;
-  s.nb = (unsigned *)(s.pz + M);
-  s.fx = (float *)(s.nb + M);
+  s.py = s.px + M64;
+  s.pz = s.py + M64;
+  s.nb = (unsigned *)(s.pz + M64);
+  s.fx = (float *)(s.nb + MNB);
   s.fy = s.fx + S;
   s.fz = s.fy + S;
   s.id = (int *)(s.fz + S);
@@ -191,6 +195,13 @@ __device__ __forceinline__ int find_id(const int *ids, int lo, int hi, int id) {
   return -1;
 }
 
+// linear search of id in the unsorted range [lo, hi); -1 if absent
+__device__ __forceinline__ int find_id_lin(const int *ids, int lo, int hi, int id) {
+  for (int i = lo; i < hi; ++i)
+    if (ids[i] == id) return i;
+  return -1;
+}
+
 __device__ __forceinline__ void set_status(int *st, int code) { atomicCAS(st, 0, code); }
 
 // ---------------------------------------------------------------- local grid
@@ -210,13 +221,18 @@ __device__ __forceinline__ int lcell(const LGrid &L, float f0, float f1, float f
   return (c2 * L.g1 + c1) * L.g0 + c0;
 }
 
+__device__ __forceinline__ unsigned &cell_count(unsigned short *c) { return *reinterpret_cast<unsigned *>(c); }
+__device__ __forceinline__ int cell_n(const unsigned short *c) {
+  return (int)*reinterpret_cast<const unsigned *>(c);
+}
+
 // single-writer updates (one lane of the group)
 __device__ __forceinline__ bool lcell_insert(const Stage &st, int ci, int slot) {
   unsigned short *c = st.cell + 8 * ci;
-  const int n = c[0];
+  const int n = cell_n(c);
   if (n < CELL_CAP) {
-    c[1 + n] = (unsigned short)slot;
-    c[0] = (unsigned short)(n + 1);
+    c[2 + n] = (unsigned short)slot;
+    cell_count(c) = (unsigned)(n + 1);
     return true;
   }
   const int k = st.hdr[4];
@@ -228,11 +244,11 @@ __device__ __forceinline__ bool lcell_insert(const Stage &st, int ci, int slot) 
 
 __device__ __forceinline__ void lcell_remove(const Stage &st, int ci, int slot) {
   unsigned short *c = st.cell + 8 * ci;
-  const int n = c[0];
-  for (int i = 1; i <= n; ++i) {
+  const int n = cell_n(c);
+  for (int i = 2; i < 2 + n; ++i) {
     if (c[i] == slot) {
-      c[i] = c[n];
-      c[0] = (unsigned short)(n - 1);
+      c[i] = c[1 + n];
+      cell_count(c) = (unsigned)(n - 1);
       return;
     }
   }
@@ -294,7 +310,7 @@ __device__ __forceinline__ float screen_lb(const Screen &Z, float d0, float d1, 
   return -dv - Z.eps_v - sqrt_hi(fmaxf(disc + Z.eps_d, 0.f));
 }
 
-// Screen the beads of one local cell (16 bytes: count, then up to 7 slots,
+// Screen the beads of one local cell (16 bytes: count, then up to 6 slots,
 // read at once) two per round, so that their shadow loads overlap.  The set
 // of candidates a lane keeps or flags does not depend on the order in which
 // it screens them (see screen_hs).
@@ -303,15 +319,15 @@ __device__ __forceinline__ void screen_cell(const Screen &Z, const Stage &st, co
                                             float w2, float &ubl, int &ks0, float &kl0, int &ks1,
                                             float &kl1, bool &ovf) {
   const uint4 c = *reinterpret_cast<const uint4 *>(rec);
-  const int n = (int)(c.x & 0xFFFF);
-  const int sl[7] = {(int)(c.x >> 16), (int)(c.y & 0xFFFF), (int)(c.y >> 16), (int)(c.z & 0xFFFF),
+  const int n = (int)c.x;
+  const int sl[6] = {(int)(c.y & 0xFFFF), (int)(c.y >> 16), (int)(c.z & 0xFFFF),
                      (int)(c.z >> 16), (int)(c.w & 0xFFFF), (int)(c.w >> 16)};
 #pragma unroll
-  for (int i = 0; i < 7; i += 2) {
+  for (int i = 0; i < 6; i += 2) {
     if (i >= n) break;
     const int ka = sl[i];
-    const bool two = (i + 1 < 7) && (i + 1 < n);
-    const int kb = (i + 1 < 7) ? (two ? sl[i + 1] : ka) : ka;
+    const bool two = i + 1 < n;
+    const int kb = two ? sl[i + 1] : ka;
     const float ax = st.fx[ka], ay = st.fy[ka], az = st.fz[ka];
     const float bx = st.fx[kb], by = st.fy[kb], bz = st.fz[kb];
     if (ka != p) screen_hs(Z, a0 - ax, a1 - ay, a2 - az, w0, w1, w2, ka, ubl, ks0, kl0, ks1, kl1, ovf);
@@ -338,8 +354,8 @@ __device__ __forceinline__ void pos64(const Stage &st, const double *r, int k, b
 
 // ---------------------------------------------------------------- staging
 // Stage one tile (domain) or the whole system (serial) into the group's
-// shared memory: G lanes of one group call this together; every lane of the
-// warp must call it (warp-wide reductions).  Returns the motile count m, the
+// shared memory: the lanes in `mask` call this together (the whole warp, or
+// one group of G lanes while the warp's other groups do something else).  Returns the motile count m, the
 // hard-sphere joint count j1 and the staged count ns; clears `live` when the
 // tile does not fit its capacity.
 #define SYS(f) (BATCH ? rp->f : P.f)
@@ -347,14 +363,18 @@ template <int G, bool F32, bool BATCH>
 __device__ __forceinline__ void stage_tile(const ECParams &P, const RepParams *rp, const Stage &st,
                                            int gl, bool &live, int unit, double c0, double c1,
                                            double c2, double *Rr, const int32_t *Rstart, int S,
-                                           int M, int NC, const LGrid &LG, int &m, int &j1,
-                                           int &ns) {
+                                           int M64, int MNB, int NC, const LGrid &LG, int &m,
+                                           int &j1, int &ns, unsigned mask = FULL) {
   if (gl == 0) {
+    st.hdr[0] = 0;
+    st.hdr[1] = 0;
     st.hdr[2] = 0;
     st.hdr[3] = 0;
     st.hdr[4] = 0;
+    st.hdr[5] = 0;
+    st.hdr[6] = 0;
   }
-  __syncwarp();
+  __syncwarp(mask);
   m = 0;
   j1 = 0;
   ns = 0;
@@ -393,67 +413,120 @@ __device__ __forceinline__ void stage_tile(const ECParams &P, const RepParams *r
       c_lo[a] = l;
       c_n[a] = live ? cnt : 0;
     }
-    const int ncell = c_n[0] * c_n[1] * c_n[2];
-    const int ncell_max = __reduce_max_sync(FULL, ncell);
     // pass 1: collect (cell-order index, category|id); the shadow arrays
-    // (12 B per slot) serve as 8 B per slot of scratch until pass 3
+    // (12 B per slot) serve as 8 B per slot of scratch until pass 3.  The
+    // cells of one row of the window (consecutive x) are one contiguous
+    // range of the cell-ordered arrays (two when the row wraps around the
+    // box); each lane takes whole rows and loads four beads at a time.
     int2 *scr = (int2 *)st.fx;
-    for (int q0 = 0; q0 < ncell_max; q0 += G) {
-      const int q = q0 + gl;
-      if (q < ncell) {
-        const int qx = q % c_n[0], qy = (q / c_n[0]) % c_n[1], qz = q / (c_n[0] * c_n[1]);
-        int cx = (c_lo[0] + qx) % SYS(nc)[0];
-        int cy = (c_lo[1] + qy) % SYS(nc)[1];
-        int cz = (c_lo[2] + qz) % SYS(nc)[2];
-        if (cx < 0) cx += SYS(nc)[0];
-        if (cy < 0) cy += SYS(nc)[1];
-        if (cz < 0) cz += SYS(nc)[2];
-        const int cell = (cz * SYS(nc)[1] + cy) * SYS(nc)[0] + cx;
-        const int j0 = Rstart[cell], jend = Rstart[cell + 1];
-        for (int j = j0; j < jend; ++j) {
-          const int tg = P.ctag[j];
+    // halo membership in FP32 from FP32 copies of the positions, widened by
+    // 1e-3 sigma plus four FP32 ulps of the box: a superset of the exact
+    // sets (an extra obstacle beyond reach is never hit; a bond partner is
+    // always within the tether halo)
+    float cf[3], Lf[3], Lhf[3], Wf[3];
+    float Lmax = 0.f;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      cf[a] = (float)corner[a];
+      Lf[a] = (float)SYS(L)[a];
+      Lhf[a] = 0.5f * Lf[a];
+      Wf[a] = (float)SYS(W)[a];
+      Lmax = fmaxf(Lmax, Lf[a]);
+    }
+    const float widen = 1e-3f * (float)P.sigma + 4.8e-7f * Lmax;
+    const float hs_f = (float)P.halo_hs + widen, te_f = (float)P.halo_te + widen;
+    const int nc0 = SYS(nc)[0], nc1 = SYS(nc)[1], nc2 = SYS(nc)[2];
+    const int nrows = c_n[1] * c_n[2];
+    int cx = c_lo[0] % nc0;
+    if (cx < 0) cx += nc0;
+    const int len0 = c_n[0] < nc0 - cx ? c_n[0] : nc0 - cx;
+    for (int r = gl; r < nrows; r += G) {
+      const int qy = r % c_n[1], qz = r / c_n[1];
+      int cy = (c_lo[1] + qy) % nc1;
+      int cz = (c_lo[2] + qz) % nc2;
+      if (cy < 0) cy += nc1;
+      if (cz < 0) cz += nc2;
+      const int base = (cz * nc1 + cy) * nc0;
+      const int a0 = Rstart[base + cx], b0 = Rstart[base + cx + len0];
+      int a1 = 0, b1 = 0;
+      if (len0 < c_n[0]) {
+        a1 = Rstart[base];
+        b1 = Rstart[base + c_n[0] - len0];
+      }
+      const int n0 = b0 - a0, nt = n0 + (b1 - a1);
+      for (int k0 = 0; k0 < nt; k0 += 4) {
+        int tg[4], jj[4], idv[4];
+        float px[4], py[4], pz[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const int k = k0 + u;
+          jj[u] = k < n0 ? a0 + k : a1 + (k - n0);
+          tg[u] = -2;
+          idv[u] = 0;
+          px[u] = py[u] = pz[u] = 0.f;
+          if (k < nt) {
+            const int64_t j = jj[u];
+            tg[u] = P.ctag[j];
+            idv[u] = P.cid[j];
+            px[u] = P.crf[3 * j];
+            py[u] = P.crf[3 * j + 1];
+            pz[u] = P.crf[3 * j + 2];
+          }
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          if (tg[u] == -2) continue;
           int cat = -1;
-          if (tg == unit) {
+          if (tg[u] == unit) {
             cat = 0;
-          } else if (tg < 0) {
+          } else if (tg[u] < 0) {
+            const float pp[3] = {px[u], py[u], pz[u]};
             bool in_hs = true, in_te = true;
 #pragma unroll
             for (int a = 0; a < 3; ++a) {
-              const double s = wrap_d(P.cr[3 * (int64_t)j + a] - corner[a], SYS(L)[a], SYS(half)[a]);
-              in_hs = in_hs && (s >= -P.halo_hs) && (s <= SYS(W)[a] + P.halo_hs);
-              in_te = in_te && (s >= -P.halo_te) && (s <= SYS(W)[a] + P.halo_te);
+              float sa = pp[a] - cf[a];
+              sa = sa > Lhf[a] ? sa - Lf[a] : (sa < -Lhf[a] ? sa + Lf[a] : sa);
+              in_hs = in_hs && (sa >= -hs_f) && (sa <= Wf[a] + hs_f);
+              in_te = in_te && (sa >= -te_f) && (sa <= Wf[a] + te_f);
             }
             cat = in_hs ? 1 : (in_te ? 2 : -1);
           }
           if (cat >= 0) {
             const int slot = atomicAdd(&st.hdr[2], 1);
-            if (slot < S) scr[slot] = make_int2(j, (cat << 29) | P.cid[j]);
+            if (slot < S) scr[slot] = make_int2(jj[u], (cat << 29) | idv[u]);
             else st.hdr[3] = 1;
+            if (cat < 2) atomicAdd(&st.hdr[5 + cat], 1);
           }
         }
       }
     }
-    __syncwarp();
+    __syncwarp(mask);
     ns = st.hdr[2];
     if (st.hdr[3]) {
       if (gl == 0) set_status(P.status, DEV_CAPACITY);
       live = false;
       ns = 0;
     }
-    const int ns_max = __reduce_max_sync(FULL, ns);
-    // pass 2: rank by (category, id); place FP64 positions and ids
-    int cnt_cat0 = 0, cnt_cat1 = 0;
+    const int ns_max = __reduce_max_sync(mask, ns);
+    // pass 2: slots.  Motile beads take their rank by id (the start bead of
+    // an EC is the u-th motile bead in id order); joint beads take the next
+    // free slot of their category (their order matters to nothing).
+    m = st.hdr[5];
+    j1 = st.hdr[6];
     for (int s0 = 0; s0 < ns_max; s0 += G) {
       const int s = s0 + gl;
       if (s < ns) {
         const int2 e = scr[s];
-        int rank = 0;
-        for (int t = 0; t < ns; ++t) rank += (scr[t].y < e.y);
         const int cat = e.y >> 29;
-        cnt_cat0 += (cat == 0);
-        cnt_cat1 += (cat == 1);
+        int rank;
+        if (cat == 0) {
+          rank = 0;
+          for (int t = 0; t < ns; ++t) rank += (scr[t].y < e.y);
+        } else {
+          rank = (cat == 1 ? m : m + j1) + atomicAdd(&st.hdr[cat - 1], 1);
+        }
         const int j = e.x;
-        if (rank < M) {
+        if (rank < M64) {
           st.px[rank] = P.cr[3 * (int64_t)j];
           st.py[rank] = P.cr[3 * (int64_t)j + 1];
           st.pz[rank] = P.cr[3 * (int64_t)j + 2];
@@ -461,62 +534,87 @@ __device__ __forceinline__ void stage_tile(const ECParams &P, const RepParams *r
         st.id[rank] = e.y & ((1 << 29) - 1);
       }
     }
-    __syncwarp();
-#pragma unroll
-    for (int off = G / 2; off > 0; off >>= 1) {
-      cnt_cat0 += __shfl_xor_sync(FULL, cnt_cat0, off);
-      cnt_cat1 += __shfl_xor_sync(FULL, cnt_cat1, off);
-    }
-    m = cnt_cat0;
-    j1 = cnt_cat1;
-    if (m > M) {  // more motile beads than the FP64 staging capacity
+    __syncwarp(mask);
+    if (m > MNB) {  // more motile beads than the motile capacity
       if (gl == 0) set_status(P.status, DEV_CAPACITY);
       live = false;
     }
-    // pass 3: shadows and bond partners of motile beads; empty cells
-    for (int i = gl; i < NC; i += G) st.cell[8 * i] = 0;
-    for (int s0 = 0; s0 < ns_max; s0 += G) {
-      const int s = s0 + gl;
-      if (s < ns && live) {
-        double x, y, z;
-        pos64(st, Rr, s, s < M, x, y, z);
-        st.fx[s] = (float)wrap_d(x - corner[0], SYS(L)[0], SYS(half)[0]);
-        st.fy[s] = (float)wrap_d(y - corner[1], SYS(L)[1], SYS(half)[1]);
-        st.fz[s] = (float)wrap_d(z - corner[2], SYS(L)[2], SYS(half)[2]);
+    // pass 3: shadows (FP32 position minus FP32 corner, the form the moved
+    // pivot's shadow takes too) and bond partners of motile beads; empty
+    // cells.  Four slots at a time (independent loads).
+    for (int i = gl; i < NC; i += G) cell_count(st.cell + 8 * i) = 0u;
+    const float *Rf = P.rf + (BATCH ? 3 * rp->bead_off : 0);
+    for (int s0 = 0; s0 < ns_max; s0 += 4 * G) {
+      float x[4], y[4], z[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int s = s0 + u * G + gl;
+        x[u] = y[u] = z[u] = 0.f;
+        if (s < ns && live) {
+          const int64_t b = st.id[s];
+          x[u] = Rf[3 * b];
+          y[u] = Rf[3 * b + 1];
+          z[u] = Rf[3 * b + 2];
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int s = s0 + u * G + gl;
+        if (!(s < ns && live)) continue;
+        float f0 = x[u] - cf[0], f1 = y[u] - cf[1], f2 = z[u] - cf[2];
+        f0 = f0 > Lhf[0] ? f0 - Lf[0] : (f0 < -Lhf[0] ? f0 + Lf[0] : f0);
+        f1 = f1 > Lhf[1] ? f1 - Lf[1] : (f1 < -Lhf[1] ? f1 + Lf[1] : f1);
+        f2 = f2 > Lhf[2] ? f2 - Lf[2] : (f2 < -Lhf[2] ? f2 + Lf[2] : f2);
+        st.fx[s] = f0;
+        st.fy[s] = f1;
+        st.fz[s] = f2;
         int prev = -1, next = -1;
         if (s < m) {
           const int id = st.id[s];
           const int c = id % SYS(N);
           if (c != 0) {
             prev = find_id(st.id, 0, m, id - 1);
-            if (prev < 0) prev = find_id(st.id, m, m + j1, id - 1);
-            if (prev < 0) prev = find_id(st.id, m + j1, ns, id - 1);
+            if (prev < 0) prev = find_id_lin(st.id, m, ns, id - 1);
             if (prev < 0) set_status(P.status, DEV_TILE);
           }
           if (c != SYS(N) - 1) {
             next = find_id(st.id, 0, m, id + 1);
-            if (next < 0) next = find_id(st.id, m, m + j1, id + 1);
-            if (next < 0) next = find_id(st.id, m + j1, ns, id + 1);
+            if (next < 0) next = find_id_lin(st.id, m, ns, id + 1);
             if (next < 0) set_status(P.status, DEV_TILE);
           }
         }
-        if (s < M) st.nb[s] = nb_pack(prev, next);
+        if (s < MNB) st.nb[s] = nb_pack(prev, next);
       }
     }
-    __syncwarp();
-    // pass 4: the hard-sphere slots into the local grid (one writer)
-    if (gl == 0 && live) {
-      for (int s = 0; s < m + j1; ++s) {
+    __syncwarp(mask);
+    // pass 4: the hard-sphere slots into the local grid, all lanes at once
+    // (the order inside a cell does not matter to the screen)
+    if (live) {
+      for (int s = gl; s < m + j1; s += G) {
         int a0, a1, a2;
-        if (!lcell_insert(st, lcell(LG, st.fx[s], st.fy[s], st.fz[s], a0, a1, a2), s)) {
-          set_status(P.status, DEV_CAPACITY);
-          st.hdr[3] = 1;
-          break;
+        unsigned short *c = st.cell + 8 * lcell(LG, st.fx[s], st.fy[s], st.fz[s], a0, a1, a2);
+        const unsigned old = atomicAdd(&cell_count(c), 1u);
+        if (old < (unsigned)CELL_CAP) {
+          c[2 + old] = (unsigned short)s;
+        } else {
+          const int k = atomicAdd(&st.hdr[4], 1);
+          if (k < OVF_CAP) st.ovf[k] = (unsigned short)s;
+          else st.hdr[3] = 1;
         }
       }
     }
-    __syncwarp();
-    if (st.hdr[3]) live = false;
+    __syncwarp(mask);
+    // counts past a cell's capacity went to the overflow list
+    for (int i = gl; i < NC; i += G) {
+      unsigned &cc = cell_count(st.cell + 8 * i);
+      if (cc > (unsigned)CELL_CAP) cc = CELL_CAP;
+    }
+    __syncwarp(mask);
+    if (st.hdr[3]) {
+      if (gl == 0 && live) set_status(P.status, DEV_CAPACITY);
+      live = false;
+      if (gl == 0) st.hdr[4] = 0;
+    }
   }
   if (!live) m = 0;
 }

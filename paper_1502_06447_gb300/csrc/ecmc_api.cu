@@ -79,10 +79,12 @@ struct ecmc_ctx {
   int32_t *d_tag = nullptr, *d_cell = nullptr, *d_rank = nullptr;
   int32_t *d_count = nullptr, *d_start = nullptr, *d_bsum = nullptr;
   double *d_cr = nullptr;
+  float *d_crf = nullptr, *d_rf = nullptr;
   int32_t *d_cid = nullptr, *d_ctag = nullptr;
   unsigned long long *d_cnt = nullptr;
   double *d_sums = nullptr;
   int *d_status = nullptr;
+  int32_t *d_unit_next = nullptr;
   double *d_obs_d = nullptr;
   unsigned long long *d_obs_u = nullptr;
   double *d_g1ref = nullptr;
@@ -159,6 +161,8 @@ CellParams cell_params(const ecmc_ctx *c, bool domain, uint64_t seed, int64_t sw
   C.start = c->d_start;
   C.block_sums = c->d_bsum;
   C.cr = c->d_cr;
+  C.crf = c->d_crf;
+  C.rf = c->d_rf;
   C.cid = c->d_cid;
   C.ctag = c->d_ctag;
   return C;
@@ -232,6 +236,8 @@ ecmc_status alloc_state(ecmc_ctx *c) {
   CU(dalloc(&c->d_cell, c->n));
   CU(dalloc(&c->d_rank, c->n));
   CU(dalloc(&c->d_cr, 3 * c->n));
+  CU(dalloc(&c->d_crf, 3 * c->n));
+  CU(dalloc(&c->d_rf, 3 * c->n));
   CU(dalloc(&c->d_cid, c->n));
   CU(dalloc(&c->d_ctag, c->n));
   CU(dalloc(&c->d_cnt, CNT_N));
@@ -240,6 +246,7 @@ ecmc_status alloc_state(ecmc_ctx *c) {
   CU(cudaMemset(c->d_sums, 0, sizeof(double) * SUM_N));
   CU(dalloc(&c->d_status, 1));
   CU(cudaMemset(c->d_status, 0, sizeof(int)));
+  CU(dalloc(&c->d_unit_next, 1));
   CU(dalloc(&c->d_obs_d, 4));
   CU(dalloc(&c->d_obs_u, 2));
   CU(dalloc(&c->d_g1ref, 3 * (c->n / c->N)));
@@ -254,8 +261,8 @@ void destroy(ecmc_ctx *c) {
   if (!c) return;
   if (c->stream) cudaStreamSynchronize(c->stream);
   void *ptrs[] = {c->d_r, c->d_img, c->d_tag, c->d_cell, c->d_rank, c->d_count, c->d_start,
-                  c->d_bsum, c->d_cr, c->d_cid, c->d_ctag, c->d_cnt, c->d_sums, c->d_status,
-                  c->d_obs_d, c->d_obs_u, c->d_g1ref, c->d_rdig, c->d_rlift, c->d_rev,
+                  c->d_bsum, c->d_cr, c->d_crf, c->d_rf, c->d_cid, c->d_ctag, c->d_cnt, c->d_sums, c->d_status,
+                  c->d_unit_next, c->d_obs_d, c->d_obs_u, c->d_g1ref, c->d_rdig, c->d_rlift, c->d_rev,
                   c->d_log, c->d_log_n, c->d_scratch};
   for (void *p : ptrs) cudaFree(p);
   for (cudaEvent_t e : c->kev) cudaEventDestroy(e);
@@ -597,6 +604,7 @@ static cudaError_t timed_ec(ecmc_ctx *c, const ECParams &P, int64_t slot) {
 static ECParams ec_params(const ecmc_ctx *c, uint64_t seed, double ell) {
   ECParams P{};
   P.block_tiles = c->opts.block_tiles;
+  P.unit_next = c->d_unit_next;
   P.n = c->n;
   P.N = c->N;
   for (int a = 0; a < 3; ++a) {
@@ -651,6 +659,8 @@ static ECParams ec_params(const ecmc_ctx *c, uint64_t seed, double ell) {
   P.r = c->d_r;
   P.img = c->d_img;
   P.cr = c->d_cr;
+  P.crf = c->d_crf;
+  P.rf = c->d_rf;
   P.cid = c->d_cid;
   P.ctag = c->d_ctag;
   P.cstart = c->d_start;

@@ -56,10 +56,12 @@ struct ecmc_batch {
           *d_rank = nullptr, *d_count = nullptr, *d_start = nullptr, *d_bsum = nullptr,
           *d_cid = nullptr, *d_ctag = nullptr;
   double *d_cr = nullptr;
+  float *d_crf = nullptr, *d_rf = nullptr;
   RepParams *d_reps = nullptr;
   unsigned long long *d_cnt = nullptr;
   double *d_sums = nullptr;
   int *d_status = nullptr;
+  int32_t *d_unit_next = nullptr;
   int64_t *d_sweep = nullptr;
   uint64_t *d_rdig = nullptr;
   double *d_rlift = nullptr;
@@ -81,8 +83,10 @@ void batch_free(ecmc_batch *b) {
   if (b->stream) cudaStreamSynchronize(b->stream);
   if (b->graph) cudaGraphExecDestroy(b->graph);
   void *ptrs[] = {b->d_r, b->d_img, b->d_rep_of, b->d_tag, b->d_cell, b->d_rank, b->d_count,
-                  b->d_start, b->d_bsum, b->d_cid, b->d_ctag, b->d_cr, b->d_reps, b->d_cnt,
-                  b->d_sums, b->d_status, b->d_sweep, b->d_rdig, b->d_rlift, b->d_rev};
+                  b->d_start, b->d_bsum, b->d_cid, b->d_ctag, b->d_cr, b->d_crf, b->d_rf, b->d_reps,
+                  b->d_cnt,
+                  b->d_sums, b->d_status, b->d_unit_next, b->d_sweep, b->d_rdig, b->d_rlift,
+                  b->d_rev};
   for (void *p : ptrs) cudaFree(p);
   if (b->ev0) cudaEventDestroy(b->ev0);
   if (b->ev1) cudaEventDestroy(b->ev1);
@@ -117,6 +121,8 @@ cudaError_t batch_sweep(ecmc_batch *b, const ECParams &P, uint64_t seed) {
   C.start = b->d_start;
   C.block_sums = b->d_bsum;
   C.cr = b->d_cr;
+  C.crf = b->d_crf;
+  C.rf = b->d_rf;
   C.cid = b->d_cid;
   C.ctag = b->d_ctag;
   cudaError_t e = launch_cells_batch(C, b->ncell_total, b->stream);
@@ -163,6 +169,8 @@ ECParams batch_params(ecmc_batch *b, uint64_t seed, double ell) {
   P.r = b->d_r;
   P.img = b->d_img;
   P.cr = b->d_cr;
+  P.crf = b->d_crf;
+  P.rf = b->d_rf;
   P.cid = b->d_cid;
   P.ctag = b->d_ctag;
   P.cstart = b->d_start;
@@ -174,6 +182,7 @@ ECParams batch_params(ecmc_batch *b, uint64_t seed, double ell) {
   P.ncl_max = b->ncl_max;
   P.sweep_dev = b->d_sweep;
   P.block_tiles = b->opts.block_tiles;
+  P.unit_next = b->d_unit_next;
   return P;
 }
 
@@ -238,12 +247,15 @@ ecmc_status ecmc_batch_create(const ecmc_replica_spec *specs, int32_t n, double 
   if (e == cudaSuccess) e = balloc(&b->d_cell, n_total);
   if (e == cudaSuccess) e = balloc(&b->d_rank, n_total);
   if (e == cudaSuccess) e = balloc(&b->d_cr, 3 * n_total);
+  if (e == cudaSuccess) e = balloc(&b->d_crf, 3 * n_total);
+  if (e == cudaSuccess) e = balloc(&b->d_rf, 3 * n_total);
   if (e == cudaSuccess) e = balloc(&b->d_cid, n_total);
   if (e == cudaSuccess) e = balloc(&b->d_ctag, n_total);
   if (e == cudaSuccess) e = balloc(&b->d_reps, n);
   if (e == cudaSuccess) e = balloc(&b->d_cnt, CNT_N);
   if (e == cudaSuccess) e = balloc(&b->d_sums, SUM_N);
   if (e == cudaSuccess) e = balloc(&b->d_status, 1);
+  if (e == cudaSuccess) e = balloc(&b->d_unit_next, 1);
   if (e == cudaSuccess) e = balloc(&b->d_sweep, 1);
   if (e == cudaSuccess) e = cudaMemsetAsync(b->d_img, 0, sizeof(int32_t) * 3 * n_total, b->stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(b->d_cnt, 0, sizeof(unsigned long long) * CNT_N, b->stream);

@@ -74,6 +74,8 @@ struct ECParams {
   const int32_t *cid;      // ids in cell order
   const int32_t *ctag;     // tiles in cell order
   const int32_t *cstart;   // cell starts (ncell + 1)
+  const float *crf;        // FP32 positions in cell order
+  const float *rf;         // FP32 positions by bead
   unsigned long long *counters;
   double *sums;
   int *status;
@@ -100,8 +102,10 @@ struct ECParams {
   int32_t lg[3];
   float linv[3];
   float lorg;
-  // block-lockstep kernel: tiles per block (0: occupancy choice)
+  // block-lockstep kernel: tiles per block (0: occupancy choice) and the
+  // device counter its persistent blocks take units from (reset per launch)
   int32_t block_tiles;
+  int32_t *unit_next;
 };
 
 // message for ecmc_last_error (ecmc_api.cu)
@@ -139,6 +143,8 @@ struct CellParams {
   double *cr;
   int32_t *cid;
   int32_t *ctag;
+  float *crf;         // FP32 positions in cell order (staging's halo test)
+  float *rf;          // FP32 positions by bead (staging's shadows)
 };
 cudaError_t launch_cells(const CellParams &C, int64_t ncell, cudaStream_t s);
 
@@ -160,6 +166,8 @@ struct CellBatch {
   double *cr;
   int32_t *cid;              // id within the replica
   int32_t *ctag;
+  float *crf;                // FP32 positions in cell order
+  float *rf;                 // FP32 positions by bead (concatenated)
 };
 cudaError_t launch_cells_batch(const CellBatch &C, int64_t ncell_total, cudaStream_t s);
 cudaError_t launch_sweep_advance(int64_t *sweep_dev, cudaStream_t s);

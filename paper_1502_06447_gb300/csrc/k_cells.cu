@@ -138,9 +138,16 @@ __global__ void k_scatter(const CellParams C) {
   const int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (b >= C.n) return;
   const int64_t pos = (int64_t)C.start[C.cell[b]] + C.rank[b];
-  C.cr[3 * pos] = C.r[3 * b];
-  C.cr[3 * pos + 1] = C.r[3 * b + 1];
-  C.cr[3 * pos + 2] = C.r[3 * b + 2];
+  const double x = C.r[3 * b], y = C.r[3 * b + 1], z = C.r[3 * b + 2];
+  C.cr[3 * pos] = x;
+  C.cr[3 * pos + 1] = y;
+  C.cr[3 * pos + 2] = z;
+  C.crf[3 * pos] = (float)x;
+  C.crf[3 * pos + 1] = (float)y;
+  C.crf[3 * pos + 2] = (float)z;
+  C.rf[3 * b] = (float)x;
+  C.rf[3 * b + 1] = (float)y;
+  C.rf[3 * b + 2] = (float)z;
   C.cid[pos] = (int32_t)b;
   C.ctag[pos] = C.tag[b];
 }
@@ -179,9 +186,16 @@ __global__ void k_scatter_b(const CellBatch C) {
   const int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (b >= C.n) return;
   const int64_t pos = (int64_t)C.start[C.cell[b]] + C.rank[b];
-  C.cr[3 * pos] = C.r[3 * b];
-  C.cr[3 * pos + 1] = C.r[3 * b + 1];
-  C.cr[3 * pos + 2] = C.r[3 * b + 2];
+  const double x = C.r[3 * b], y = C.r[3 * b + 1], z = C.r[3 * b + 2];
+  C.cr[3 * pos] = x;
+  C.cr[3 * pos + 1] = y;
+  C.cr[3 * pos + 2] = z;
+  C.crf[3 * pos] = (float)x;
+  C.crf[3 * pos + 1] = (float)y;
+  C.crf[3 * pos + 2] = (float)z;
+  C.rf[3 * b] = (float)x;
+  C.rf[3 * b + 1] = (float)y;
+  C.rf[3 * b + 2] = (float)z;
   C.cid[pos] = (int32_t)(b - C.reps[C.rep_of[b]].bead_off);
   C.ctag[pos] = C.tag[b];
 }

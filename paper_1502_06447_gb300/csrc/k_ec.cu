@@ -62,7 +62,7 @@ __global__ void __launch_bounds__(128) ec_kernel(const ECParams P) {
   const int S = P.stage_cap;
   const int NC = P.domain ? (BATCH ? P.ncl_max : SYS(lg)[0] * SYS(lg)[1] * SYS(lg)[2]) : 0;
   const int M = (F32 && P.domain) ? P.m_cap : S;
-  Stage st = carve(smem + (size_t)gib * group_bytes(S, M, NC), S, M, NC);
+  Stage st = carve(smem + (size_t)gib * group_bytes(S, M, M, NC), S, M, M, NC);
   bool live = gunit < P.n_units;
   const uint64_t hb0 = dbits(SYS(half)[0]), hb1 = dbits(SYS(half)[1]), hb2 = dbits(SYS(half)[2]);
   LGrid LG;
@@ -89,8 +89,8 @@ __global__ void __launch_bounds__(128) ec_kernel(const ECParams P) {
 
   // ------------------------------------------------------------ staging
   int m = 0, j1 = 0, ns = 0;
-  stage_tile<G, F32, BATCH>(P, rp, st, gl, live, unit, c0, c1, c2, Rr, Rstart, S, M, NC, LG, m, j1,
-                            ns);
+  stage_tile<G, F32, BATCH>(P, rp, st, gl, live, unit, c0, c1, c2, Rr, Rstart, S, M, M, NC, LG, m,
+                            j1, ns);
   const int nhs = m + j1;
   const int nhs_max = __reduce_max_sync(FULL, nhs);
 
@@ -294,8 +294,8 @@ __global__ void __launch_bounds__(128) ec_kernel(const ECParams P) {
               screen_cell(Z, st, c, p, pf0, pf1, pf2, vf0, vf1, vf2, ubl, ks0, kl0, ks1, kl1, kovf);
               continue;
             }
-            n = c[0];
-            lst = c + 1;
+            n = cell_n(c);
+            lst = c + 2;
           }
           for (int i = 0; i < n; ++i) {
             const int k = lst[i];
@@ -438,8 +438,8 @@ __global__ void __launch_bounds__(128) ec_kernel(const ECParams P) {
                 const int x = pc0 + ci % 3 - 1, y = pc1 + (ci / 3) % 3 - 1, z = pc2 + ci / 9 - 1;
                 if (x < 0 || y < 0 || z < 0 || x >= LG.g0 || y >= LG.g1 || z >= LG.g2) continue;
                 const unsigned short *c = st.cell + 8 * ((z * LG.g1 + y) * LG.g0 + x);
-                n = c[0];
-                lst = c + 1;
+                n = cell_n(c);
+                lst = c + 2;
               }
               for (int i = 0; i < n; ++i) rescan(lst[i]);
             }
@@ -728,7 +728,7 @@ __global__ void __launch_bounds__(128) ec_kernel(const ECParams P) {
 }  // namespace
 
 size_t ec_smem_bytes(int stage_cap, int motile_cap, int ncell, int groups_per_block) {
-  return (size_t)groups_per_block * group_bytes(stage_cap, motile_cap, ncell);
+  return (size_t)groups_per_block * group_bytes(stage_cap, motile_cap, motile_cap, ncell);
 }
 
 template <int G, bool F32, bool BATCH>

@@ -19,6 +19,11 @@
 // oracle) produces: same candidates, same FP64 expressions, same tie rule.
 // A tile whose survivors do not fit the request list (rare) is evaluated
 // exhaustively in FP64 by its own group in phase B.
+//
+// FP64 positions stay in the global array (the owner thread updates its
+// pivot's in place; no other tile touches those beads), so shared memory
+// holds only the FP32 shadows, ids, bond words and local grid of each tile;
+// an evaluated request carries its partner's position to phase D.
 #include "ec_device.cuh"
 
 namespace ecmc {
@@ -36,20 +41,23 @@ struct __align__(16) TileRec {
   int active;
   int vnz;            // bit a: v_a != 0
   int rq_off, rq_cnt; // this step's requests; rq_cnt < 0: evaluate exhaustively
+  int state;          // slot state (SLOT_*)
   int m, j1;          // staged motile / hard-sphere joint counts
   int wr;             // bit a: the tile's halo can wrap on axis a
   int unit, gunit;
   const RepParams *rp;
   unsigned long long fb_x, fb_key;  // exhaustive-evaluation result
   double fb_dv;
+  double fb_k[3];
 };
 
 struct Res {
   unsigned long long xb, key;
   double dv;
+  double k[3];  // the partner's FP64 position
 };
 
-constexpr int RQ_PER_TILE = 8;   // request list capacity per tile of the block
+constexpr int RQ_PER_TILE = 6;   // request list capacity per tile of the block
 // a lane holds at most four requests per step (pq0..pq3); more send the
 // tile to the exhaustive evaluation
 
@@ -83,113 +91,156 @@ __global__ void __launch_bounds__(256) ec_lock_kernel(const ECParams P) {
   const unsigned gmask = (G == 32) ? FULL : (((1u << G) - 1) << gbase);
   const int NT = blockDim.x / G;
   const int gib = tid / G;
-  const int gunit = blockIdx.x * NT + gib;
-  const RepParams *rp = nullptr;
-  int unit = gunit;
-  if (BATCH) {
-    int lo = 0, hi = P.n_reps - 1;
-    const int gu = gunit < P.n_units ? gunit : P.n_units - 1;
-    while (lo < hi) {
-      const int mid = (lo + hi + 1) >> 1;
-      if (P.reps[mid].unit_off <= gu) lo = mid;
-      else hi = mid - 1;
-    }
-    rp = P.reps + lo;
-    unit = gunit - (int)rp->unit_off;
-  }
-  double *const Rr = BATCH ? P.r + 3 * rp->bead_off : P.r;
-  const int32_t *const Rstart = BATCH ? P.cstart + rp->cell_off : P.cstart;
   const int64_t sweep = P.sweep_dev ? *P.sweep_dev : P.sweep;
   const int S = P.stage_cap;
-  const int NC = BATCH ? P.ncl_max : SYS(lg)[0] * SYS(lg)[1] * SYS(lg)[2];
-  const int M = P.m_cap;
-  const size_t gbytes = group_bytes(S, M, NC);
-  Stage st = carve(smem + (size_t)gib * gbytes, S, M, NC);
+  const int NC = BATCH ? P.ncl_max : P.lg[0] * P.lg[1] * P.lg[2];
+  const int MNB = P.m_cap;
+  const size_t gbytes = group_bytes(S, 0, MNB, NC);
+  Stage st = carve(smem + (size_t)gib * gbytes, S, 0, MNB, NC);
   TileRec *tr = (TileRec *)(smem + (size_t)NT * gbytes);
   int2 *rq = (int2 *)(tr + NT);
   Res *rs = (Res *)(rq + NT * RQ_PER_TILE);
   int *rq_n = (int *)(rs + NT * RQ_PER_TILE);
   const int RQ_CAP = NT * RQ_PER_TILE;
-  bool live = gunit < P.n_units;
-  LGrid LG;
-  LG.g0 = SYS(lg)[0];
-  LG.g1 = SYS(lg)[1];
-  LG.g2 = SYS(lg)[2];
-  LG.org = SYS(lorg);
-  LG.inv0 = SYS(linv)[0];
-  LG.inv1 = SYS(linv)[1];
-  LG.inv2 = SYS(linv)[2];
-  const uint64_t Rkey = BATCH ? rp->replica : P.replica;
 
-  // ------------------------------------------------------------ staging
-  double c0 = 0.0, c1 = 0.0, c2 = 0.0;
-  if (live) {
-    const int tk0 = unit % SYS(D)[0];
-    const int tk1 = (unit / SYS(D)[0]) % SYS(D)[1];
-    const int tk2 = unit / (SYS(D)[0] * SYS(D)[1]);
-    const u64x4 w = philox(TAG_SHIFT, (uint64_t)sweep, 0, 0, P.seed, Rkey);
-    c0 = unit53(w.v[0]) * SYS(T)[0] + (double)tk0 * SYS(T)[0];
-    c1 = unit53(w.v[1]) * SYS(T)[1] + (double)tk1 * SYS(T)[1];
-    c2 = unit53(w.v[2]) * SYS(T)[2] + (double)tk2 * SYS(T)[2];
-  }
+  // ------------------------------------------------------------ tile slots
+  // The block keeps NT tile slots busy: a slot whose tile has run its ECs is
+  // refilled with the next unit of the launch (a device counter), staged by
+  // the slot's own group while the other slots go on.  Slot states:
+  enum : int { SLOT_EMPTY = 0, SLOT_FRESH = 1, SLOT_RUN = 2, SLOT_DONE = 3 };
+  // the group's current tile
+  const RepParams *rp = BATCH ? P.reps : nullptr;
+  int unit = 0;
+  bool live = false;
   int m = 0, j1 = 0, ns = 0;
-  stage_tile<G, true, BATCH>(P, rp, st, gl, live, unit, c0, c1, c2, Rr, Rstart, S, M, NC, LG, m, j1,
-                             ns);
+  double *Rr = P.r;
+  LGrid LG;
+  float Wf0 = 0.f, Wf1 = 0.f, Wf2 = 0.f;
   if (gl == 0) {
-    TileRec &T = tr[gib];
-    T.c[0] = c0;
-    T.c[1] = c1;
-    T.c[2] = c2;
-    T.m = live ? m : 0;
-    T.j1 = j1;
-    int wr = 0;
-    if (!(c0 - P.halo_te > 0.0 && c0 + SYS(W)[0] + P.halo_te < SYS(L)[0])) wr |= 1;
-    if (!(c1 - P.halo_te > 0.0 && c1 + SYS(W)[1] + P.halo_te < SYS(L)[1])) wr |= 2;
-    if (!(c2 - P.halo_te > 0.0 && c2 + SYS(W)[2] + P.halo_te < SYS(L)[2])) wr |= 4;
-    T.wr = wr;
-    T.unit = unit;
-    T.gunit = gunit;
-    T.rp = rp;
-    T.active = 0;
-    T.rq_cnt = 0;
+    tr[gib].state = SLOT_EMPTY;
+    tr[gib].active = 0;
+    tr[gib].rq_cnt = 0;
   }
   if (tid == 0) *rq_n = 0;
   __syncthreads();
 
+  // take the next unit and stage it (group-collective); false when none left
+  auto take_tile = [&]() -> bool {
+    int u = 0;
+    if (gl == 0) u = atomicAdd(P.unit_next, 1);
+    u = __shfl_sync(gmask, u, gbase);
+    if (u >= P.n_units) return false;
+    const int gu = u;
+    unit = gu;
+    if (BATCH) {
+      int lo = 0, hi = P.n_reps - 1;
+      while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (P.reps[mid].unit_off <= gu) lo = mid;
+        else hi = mid - 1;
+      }
+      rp = P.reps + lo;
+      unit = gu - (int)rp->unit_off;
+    }
+    Rr = BATCH ? P.r + 3 * rp->bead_off : P.r;
+    const int32_t *const Rstart = BATCH ? P.cstart + rp->cell_off : P.cstart;
+    const uint64_t Rkey = BATCH ? rp->replica : P.replica;
+    LG.g0 = SYS(lg)[0];
+    LG.g1 = SYS(lg)[1];
+    LG.g2 = SYS(lg)[2];
+    LG.org = SYS(lorg);
+    LG.inv0 = SYS(linv)[0];
+    LG.inv1 = SYS(linv)[1];
+    LG.inv2 = SYS(linv)[2];
+    Wf0 = (float)SYS(W)[0];
+    Wf1 = (float)SYS(W)[1];
+    Wf2 = (float)SYS(W)[2];
+    const int tk0 = unit % SYS(D)[0];
+    const int tk1 = (unit / SYS(D)[0]) % SYS(D)[1];
+    const int tk2 = unit / (SYS(D)[0] * SYS(D)[1]);
+    const u64x4 w = philox(TAG_SHIFT, (uint64_t)sweep, 0, 0, P.seed, Rkey);
+    const double c0 = unit53(w.v[0]) * SYS(T)[0] + (double)tk0 * SYS(T)[0];
+    const double c1 = unit53(w.v[1]) * SYS(T)[1] + (double)tk1 * SYS(T)[1];
+    const double c2 = unit53(w.v[2]) * SYS(T)[2] + (double)tk2 * SYS(T)[2];
+    live = true;
+    stage_tile<G, true, BATCH>(P, rp, st, gl, live, unit, c0, c1, c2, Rr, Rstart, S, 0, MNB, NC, LG,
+                               m, j1, ns, gmask);
+    if (!live) m = 0;
+    if (gl == 0) {
+      TileRec &T = tr[gib];
+      T.c[0] = c0;
+      T.c[1] = c1;
+      T.c[2] = c2;
+      T.m = m;
+      T.j1 = j1;
+      int wr = 0;
+      if (!(c0 - P.halo_te > 0.0 && c0 + SYS(W)[0] + P.halo_te < SYS(L)[0])) wr |= 1;
+      if (!(c1 - P.halo_te > 0.0 && c1 + SYS(W)[1] + P.halo_te < SYS(L)[1])) wr |= 2;
+      if (!(c2 - P.halo_te > 0.0 && c2 + SYS(W)[2] + P.halo_te < SYS(L)[2])) wr |= 4;
+      T.wr = wr;
+      T.unit = unit;
+      T.gunit = gu;
+      T.rp = rp;
+    }
+    return true;
+  };
+
   // ------------------------------------------------------------ owner state
-  // thread t < NT owns tile t of the block: its EC state lives in registers
+  // thread t < NT owns slot t: its tile's EC state lives in registers
   const bool owner = tid < NT;
   const int ot = owner ? tid : 0;
-  const RepParams *orp = tr[ot].rp;
-  const int o_unit = tr[ot].unit, o_gunit = tr[ot].gunit;
-  const bool o_live = owner && o_gunit < P.n_units && tr[ot].m > 0;
-  const int om = tr[ot].m;
-  Stage ost = carve(smem + (size_t)ot * gbytes, S, M, NC);
-  double *const oRr = BATCH ? P.r + 3 * orp->bead_off : P.r;
-  int32_t *const oRi = BATCH ? P.img + 3 * orp->bead_off : P.img;
-  const uint64_t oKey = BATCH ? orp->replica : P.replica;
-  const double oL0 = TSYS(orp, L)[0], oL1 = TSYS(orp, L)[1], oL2 = TSYS(orp, L)[2];
-  const uint64_t ohb0 = dbits(TSYS(orp, half)[0]), ohb1 = dbits(TSYS(orp, half)[1]),
-                 ohb2 = dbits(TSYS(orp, half)[2]);
-  const int owr = tr[ot].wr;
-  const bool owr0 = owr & 1, owr1 = owr & 2, owr2 = owr & 4;
-  const double oc0 = tr[ot].c[0], oc1 = tr[ot].c[1], oc2 = tr[ot].c[2];
-  const float ocf0 = (float)oc0, ocf1 = (float)oc1, ocf2 = (float)oc2;
-  const float oLh0 = 0.5f * (float)oL0, oLh1 = 0.5f * (float)oL1, oLh2 = 0.5f * (float)oL2;
+  const RepParams *orp = nullptr;
+  int o_unit = 0, o_gunit = 0, om = 0;
+  Stage ost = carve(smem + (size_t)ot * gbytes, S, 0, MNB, NC);
+  double *oRr = P.r;
+  int32_t *oRi = P.img;
+  uint64_t oKey = P.replica;
+  double oL0 = 0.0, oL1 = 0.0, oL2 = 0.0;
+  uint64_t ohb0 = 0, ohb1 = 0, ohb2 = 0;
+  bool owr0 = false, owr1 = false, owr2 = false;
+  float ocf0 = 0.f, ocf1 = 0.f, ocf2 = 0.f, oLh0 = 0.f, oLh1 = 0.f, oLh2 = 0.f;
   LGrid OLG;
-  OLG.g0 = TSYS(orp, lg)[0];
-  OLG.g1 = TSYS(orp, lg)[1];
-  OLG.g2 = TSYS(orp, lg)[2];
-  OLG.org = TSYS(orp, lorg);
-  OLG.inv0 = TSYS(orp, linv)[0];
-  OLG.inv1 = TSYS(orp, linv)[1];
-  OLG.inv2 = TSYS(orp, linv)[2];
+  uint64_t r2 = 0;
+  // the owned slot's new tile
+  auto load_tile = [&]() {
+    const TileRec &T = tr[ot];
+    orp = T.rp;
+    o_unit = T.unit;
+    o_gunit = T.gunit;
+    om = T.m;
+    oRr = BATCH ? P.r + 3 * orp->bead_off : P.r;
+    oRi = BATCH ? P.img + 3 * orp->bead_off : P.img;
+    oKey = BATCH ? orp->replica : P.replica;
+    oL0 = TSYS(orp, L)[0];
+    oL1 = TSYS(orp, L)[1];
+    oL2 = TSYS(orp, L)[2];
+    ohb0 = dbits(TSYS(orp, half)[0]);
+    ohb1 = dbits(TSYS(orp, half)[1]);
+    ohb2 = dbits(TSYS(orp, half)[2]);
+    owr0 = T.wr & 1;
+    owr1 = T.wr & 2;
+    owr2 = T.wr & 4;
+    ocf0 = (float)T.c[0];
+    ocf1 = (float)T.c[1];
+    ocf2 = (float)T.c[2];
+    oLh0 = 0.5f * (float)oL0;
+    oLh1 = 0.5f * (float)oL1;
+    oLh2 = 0.5f * (float)oL2;
+    OLG.g0 = TSYS(orp, lg)[0];
+    OLG.g1 = TSYS(orp, lg)[1];
+    OLG.g2 = TSYS(orp, lg)[2];
+    OLG.org = TSYS(orp, lorg);
+    OLG.inv0 = TSYS(orp, linv)[0];
+    OLG.inv1 = TSYS(orp, linv)[1];
+    OLG.inv2 = TSYS(orp, linv)[2];
+    r2 = (uint64_t)o_unit;
+  };
   const int n_ec = P.ecs_per_tile;
   const uint64_t r1 = (uint64_t)sweep;
-  const uint64_t r2 = (uint64_t)o_unit;
 
   int e = 0;
   bool active = false;
+  bool o_any = false;  // the slot ran at least one EC
   int p = 0, pid = 0;
   double q0 = 0.0, q1 = 0.0, q2 = 0.0, v0 = 0.0, v1 = 0.0, v2 = 0.0, xrem = 0.0, lift = 0.0;
   float pf0 = 0.f, pf1 = 0.f, pf2 = 0.f, vf0 = 0.f, vf1 = 0.f, vf2 = 0.f;
@@ -235,9 +286,9 @@ __global__ void __launch_bounds__(256) ec_lock_kernel(const ECParams P) {
       }
     }
     pid = ost.id[p];
-    q0 = ost.px[p];
-    q1 = ost.py[p];
-    q2 = ost.pz[p];
+    q0 = oRr[3 * (int64_t)pid];
+    q1 = oRr[3 * (int64_t)pid + 1];
+    q2 = oRr[3 * (int64_t)pid + 2];
     pf0 = ost.fx[p];
     pf1 = ost.fy[p];
     pf2 = ost.fz[p];
@@ -274,11 +325,6 @@ __global__ void __launch_bounds__(256) ec_lock_kernel(const ECParams P) {
     T.xcap = __double2float_ru(dbits(P.s_cap) < dbits(xrem) ? P.s_cap : xrem);
     T.p = p;
   };
-  if (o_live) {
-    start_ec();
-    publish();
-  }
-
   // FP32 screen constants
   Screen Z;
   Z.sig2f = (float)P.sig2;
@@ -290,12 +336,36 @@ __global__ void __launch_bounds__(256) ec_lock_kernel(const ECParams P) {
   }
   const float b2f = (float)P.b2;
   const float eps_v = P.eps_v, eps_d = P.eps_d;
-  const float Wf0 = (float)SYS(W)[0], Wf1 = (float)SYS(W)[1], Wf2 = (float)SYS(W)[2];
   const float INF = __int_as_float(0x7f800000);
   constexpr int ITEMS = G >= 8 ? 1 : 2;  // special candidates per lane
 
   for (;;) {
-    if (!__syncthreads_or(o_live && active ? 1 : 0)) break;
+    __syncthreads();
+    // refill empty slots (each by its own group; tiles without motile beads
+    // have no ECs and are passed over)
+    if (tr[gib].state == SLOT_EMPTY) {
+      for (;;) {
+        if (!take_tile()) {
+          live = false;
+          if (gl == 0) tr[gib].state = SLOT_DONE;
+          break;
+        }
+        if (live && m > 0) {
+          if (gl == 0) tr[gib].state = SLOT_FRESH;
+          break;
+        }
+      }
+    }
+    __syncthreads();
+    if (owner && tr[ot].state == SLOT_FRESH) {
+      load_tile();
+      e = 0;
+      o_any = true;
+      start_ec();
+      tr[ot].state = SLOT_RUN;
+    }
+    if (owner) publish();
+    if (!__syncthreads_or(owner && active ? 1 : 0)) break;
 
     // ---------------------------------------------------------- A: screen
     {
@@ -411,8 +481,8 @@ __global__ void __launch_bounds__(256) ec_lock_kernel(const ECParams P) {
             const int x = pc0 + ci % 3 - 1, y = pc1 + (ci / 3) % 3 - 1, z = pc2 + ci / 9 - 1;
             if (x < 0 || y < 0 || z < 0 || x >= LG.g0 || y >= LG.g1 || z >= LG.g2) continue;
             const unsigned short *c = st.cell + 8 * ((z * LG.g1 + y) * LG.g0 + x);
-            n = c[0];
-            lst = c + 1;
+            n = cell_n(c);
+            lst = c + 2;
           }
           for (int i = 0; i < n; ++i) {
             const int k = lst[i];
@@ -466,6 +536,7 @@ __global__ void __launch_bounds__(256) ec_lock_kernel(const ECParams P) {
         out.xb = ~0ull;
         out.key = ~0ull;
         out.dv = 0.0;
+        out.k[0] = out.k[1] = out.k[2] = 0.0;
         if (r.x >= 0) {
           const TileRec &T = tr[r.x];
           const RepParams *R = T.rp;
@@ -489,10 +560,10 @@ __global__ void __launch_bounds__(256) ec_lock_kernel(const ECParams P) {
             out.key = make_key(KIND_WALL, a, 0);
           } else {
             const bool te = kind == KIND_TETHER;
-            const Stage sk = carve(smem + (size_t)r.x * gbytes, S, M, NC);
+            const Stage sk = carve(smem + (size_t)r.x * gbytes, S, 0, MNB, NC);
             double kx, ky, kz, dv;
             double *const Rk = BATCH ? P.r + 3 * R->bead_off : P.r;
-            pos64(sk, Rk, k, k < T.m, kx, ky, kz);
+            pos64(sk, Rk, k, false, kx, ky, kz);
             const double x =
                 quad_x(te, wrapc(Q0 - kx, L0, dbits(TSYS(R, half)[0]), W0),
                        wrapc(Q1 - ky, L1, dbits(TSYS(R, half)[1]), W1),
@@ -502,6 +573,9 @@ __global__ void __launch_bounds__(256) ec_lock_kernel(const ECParams P) {
               out.xb = dbits(x);
               out.key = make_key(te ? KIND_TETHER : KIND_HS, sk.id[k], k);
               out.dv = dv;
+              out.k[0] = kx;
+              out.k[1] = ky;
+              out.k[2] = kz;
             }
           }
         }
@@ -520,14 +594,14 @@ __global__ void __launch_bounds__(256) ec_lock_kernel(const ECParams P) {
         const unsigned nbw = st.nb[fp];
         double bx = __longlong_as_double(0x7ff0000000000000ll);
         uint64_t bkey = ~0ull;
-        double bdv = 0.0;
+        double bdv = 0.0, bk0 = 0.0, bk1 = 0.0, bk2 = 0.0;
         for (int it = gl; it < 6; it += G) {
           if (it == 0) continue;
           if (it <= 2) {
             const int t = it == 1 ? nb_prev(nbw) : nb_next(nbw);
             if (t < 0) continue;
             double kx, ky, kz, dv;
-            pos64(st, Rr, t, t < T.m, kx, ky, kz);
+            pos64(st, Rr, t, false, kx, ky, kz);
             const double x = quad_x(true, wrapc(Q0 - kx, L0, hb0, W0), wrapc(Q1 - ky, L1, hb1, W1),
                                     wrapc(Q2 - kz, L2, hb2, W2), V0, V1, V2, P.b2, dv);
             const uint64_t key = make_key(KIND_TETHER, st.id[t], t);
@@ -535,6 +609,9 @@ __global__ void __launch_bounds__(256) ec_lock_kernel(const ECParams P) {
               bx = x;
               bkey = key;
               bdv = dv;
+              bk0 = kx;
+              bk1 = ky;
+              bk2 = kz;
             }
           } else {
             const int a = it - 3;
@@ -563,14 +640,14 @@ __global__ void __launch_bounds__(256) ec_lock_kernel(const ECParams P) {
             const int x = pc0 + ci % 3 - 1, y = pc1 + (ci / 3) % 3 - 1, z = pc2 + ci / 9 - 1;
             if (x < 0 || y < 0 || z < 0 || x >= LG.g0 || y >= LG.g1 || z >= LG.g2) continue;
             const unsigned short *c = st.cell + 8 * ((z * LG.g1 + y) * LG.g0 + x);
-            n = c[0];
-            lst = c + 1;
+            n = cell_n(c);
+            lst = c + 2;
           }
           for (int i = 0; i < n; ++i) {
             const int k = lst[i];
             if (k == fp) continue;
             double kx, ky, kz, dv;
-            pos64(st, Rr, k, k < T.m, kx, ky, kz);
+            pos64(st, Rr, k, false, kx, ky, kz);
             const double x = quad_x(false, wrapc(Q0 - kx, L0, hb0, W0), wrapc(Q1 - ky, L1, hb1, W1),
                                     wrapc(Q2 - kz, L2, hb2, W2), V0, V1, V2, P.sig2, dv);
             ++confirmed;
@@ -580,6 +657,9 @@ __global__ void __launch_bounds__(256) ec_lock_kernel(const ECParams P) {
                 bx = x;
                 bkey = key;
                 bdv = dv;
+                bk0 = kx;
+                bk1 = ky;
+                bk2 = kz;
               }
             }
           }
@@ -589,25 +669,32 @@ __global__ void __launch_bounds__(256) ec_lock_kernel(const ECParams P) {
         group_argmin_m<G>(bx, bkey, gmask);
         const unsigned own = __ballot_sync(gmask, my_key == bkey && my_x == dbits(bx)) & gmask;
         const int src = __ffs(own) - 1;
-        const double wdv = __shfl_sync(gmask, bdv, src < 0 ? lane : src);
+        const int from = src < 0 ? lane : src;
+        const double wdv = __shfl_sync(gmask, bdv, from);
+        const double wk0 = __shfl_sync(gmask, bk0, from);
+        const double wk1 = __shfl_sync(gmask, bk1, from);
+        const double wk2 = __shfl_sync(gmask, bk2, from);
         if (gl == 0) {
           tr[gib].fb_x = dbits(bx);
           tr[gib].fb_key = bkey;
           tr[gib].fb_dv = wdv;
+          tr[gib].fb_k[0] = wk0;
+          tr[gib].fb_k[1] = wk1;
+          tr[gib].fb_k[2] = wk2;
         }
       }
     }
     __syncthreads();
 
     // ---------------------------------------------------------- D: move
-    if (o_live && active && nev >= P.event_cap) {
+    if (owner && active && nev >= P.event_cap) {
       set_status(P.status, DEV_STUCK);
       active = false;
     }
-    if (o_live && active) {
+    if (owner && active) {
       double x;
       uint64_t bkey;
-      double wdv = 0.0;
+      double wdv = 0.0, wk0 = 0.0, wk1 = 0.0, wk2 = 0.0;
       {
         const TileRec &T = tr[ot];
         if (dbits(P.s_cap) < dbits(xrem)) {
@@ -623,16 +710,26 @@ __global__ void __launch_bounds__(256) ec_lock_kernel(const ECParams P) {
             x = fx;
             bkey = T.fb_key;
             wdv = T.fb_dv;
+            wk0 = T.fb_k[0];
+            wk1 = T.fb_k[1];
+            wk2 = T.fb_k[2];
           }
         } else {
           const int i0 = T.rq_off, i1 = T.rq_off + T.rq_cnt;
+          int wi = -1;
           for (int i = i0; i < i1; ++i) {
             const unsigned long long xb = rs[i].xb, kb = rs[i].key;
             if (xb < dbits(x) || (xb == dbits(x) && kb < bkey)) {
               x = __longlong_as_double((long long)xb);
               bkey = kb;
-              wdv = rs[i].dv;
+              wi = i;
             }
+          }
+          if (wi >= 0) {
+            wdv = rs[wi].dv;
+            wk0 = rs[wi].k[0];
+            wk1 = rs[wi].k[1];
+            wk2 = rs[wi].k[2];
           }
         }
       }
@@ -654,6 +751,7 @@ __global__ void __launch_bounds__(256) ec_lock_kernel(const ECParams P) {
       ++nev;
       int out;
       bool swapped = false;
+      double sw0 = 0.0, sw1 = 0.0, sw2 = 0.0;  // the partner's position after a swap
       int np = p;
       if (kind == KIND_END) {
         out = ECMC_EV_END;
@@ -674,10 +772,8 @@ __global__ void __launch_bounds__(256) ec_lock_kernel(const ECParams P) {
         if (!motile) {
           out = kind == KIND_HS ? ECMC_EV_HS_REFLECT : ECMC_EV_TE_REFLECT;
           refl_all = refl_all + proj;
-          double kx, ky, kz;
-          pos64(ost, oRr, slot, false, kx, ky, kz);
-          mirror2(v0, v1, v2, wrapc(q0 - kx, oL0, ohb0, owr0), wrapc(q1 - ky, oL1, ohb1, owr1),
-                  wrapc(q2 - kz, oL2, ohb2, owr2));
+          mirror2(v0, v1, v2, wrapc(q0 - wk0, oL0, ohb0, owr0), wrapc(q1 - wk1, oL1, ohb1, owr1),
+                  wrapc(q2 - wk2, oL2, ohb2, owr2));
           vf0 = (float)v0;
           vf1 = (float)v1;
           vf2 = (float)v2;
@@ -696,7 +792,7 @@ __global__ void __launch_bounds__(256) ec_lock_kernel(const ECParams P) {
             ++ncontact;
             if (go) {
               ++tried;
-              const double k0 = ost.px[slot], k1 = ost.py[slot], k2 = ost.pz[slot];
+              const double k0 = wk0, k1 = wk1, k2 = wk2;
               // every bond of both beads, positions exchanged, within b_max
               bool ok = true;
 #pragma unroll
@@ -720,7 +816,7 @@ __global__ void __launch_bounds__(256) ec_lock_kernel(const ECParams P) {
                     b1 = q1;
                     b2 = q2;
                   } else {
-                    pos64(ost, oRr, b, b < om, b0, b1, b2);
+                    pos64(ost, oRr, b, false, b0, b1, b2);
                   }
                   const double e0 = wrapc(a0 - b0, oL0, ohb0, owr0);
                   const double e1 = wrapc(a1 - b1, oL1, ohb1, owr1);
@@ -731,10 +827,13 @@ __global__ void __launch_bounds__(256) ec_lock_kernel(const ECParams P) {
               }
               if (ok) {
                 swapped = true;
-                ost.px[slot] = q0;
-                ost.py[slot] = q1;
-                ost.pz[slot] = q2;
                 const int kid = ost.id[slot];
+                oRr[3 * (int64_t)kid] = q0;
+                oRr[3 * (int64_t)kid + 1] = q1;
+                oRr[3 * (int64_t)kid + 2] = q2;
+                sw0 = q0;
+                sw1 = q1;
+                sw2 = q2;
 #pragma unroll
                 for (int a = 0; a < 3; ++a) {
                   const int ti = oRi[3 * (int64_t)pid + a];
@@ -766,9 +865,11 @@ __global__ void __launch_bounds__(256) ec_lock_kernel(const ECParams P) {
       if (owr0) nf0 = nf0 > oLh0 ? nf0 - (float)oL0 : (nf0 < -oLh0 ? nf0 + (float)oL0 : nf0);
       if (owr1) nf1 = nf1 > oLh1 ? nf1 - (float)oL1 : (nf1 < -oLh1 ? nf1 + (float)oL1 : nf1);
       if (owr2) nf2 = nf2 > oLh2 ? nf2 - (float)oL2 : (nf2 < -oLh2 ? nf2 + (float)oL2 : nf2);
-      fnv_mix(h, (uint64_t)pid);
-      fnv_mix(h, ((uint64_t)(uint32_t)out << 32) | (uint64_t)(uint32_t)partner);
-      fnv_mix(h, dbits(x));
+      if (P.rec_digest) {
+        fnv_mix(h, (uint64_t)pid);
+        fnv_mix(h, ((uint64_t)(uint32_t)out << 32) | (uint64_t)(uint32_t)partner);
+        fnv_mix(h, dbits(x));
+      }
       if (P.log) {
         const unsigned long long at = atomicAdd(P.log_n, 1ull);
         if ((int64_t)at < P.log_cap) {
@@ -784,17 +885,16 @@ __global__ void __launch_bounds__(256) ec_lock_kernel(const ECParams P) {
           P.log[at] = ev;
         }
       }
-      ost.px[p] = q0;
-      ost.py[p] = q1;
-      ost.pz[p] = q2;
+      oRr[3 * (int64_t)pid] = q0;
+      oRr[3 * (int64_t)pid + 1] = q1;
+      oRr[3 * (int64_t)pid + 2] = q2;
       {
         // keep the local grid current
         int a0, a1, a2, b0, b1, b2;
         const int oc = lcell(OLG, pf0, pf1, pf2, a0, a1, a2);
         const int ncl = lcell(OLG, nf0, nf1, nf2, b0, b1, b2);
         if (swapped) {
-          const double o0 = ost.px[slot], o1 = ost.py[slot], o2 = ost.pz[slot];
-          float g0 = (float)o0 - ocf0, g1 = (float)o1 - ocf1, g2 = (float)o2 - ocf2;
+          float g0 = (float)sw0 - ocf0, g1 = (float)sw1 - ocf1, g2 = (float)sw2 - ocf2;
           if (owr0) g0 = g0 > oLh0 ? g0 - (float)oL0 : (g0 < -oLh0 ? g0 + (float)oL0 : g0);
           if (owr1) g1 = g1 > oLh1 ? g1 - (float)oL1 : (g1 < -oLh1 ? g1 + (float)oL1 : g1);
           if (owr2) g2 = g2 > oLh2 ? g2 - (float)oL2 : (g2 < -oLh2 ? g2 + (float)oL2 : g2);
@@ -825,18 +925,19 @@ __global__ void __launch_bounds__(256) ec_lock_kernel(const ECParams P) {
         xrem = xrem - x;
       }
       if (active && np != p) {
+        // lift: the partner (motile, unmoved this event) becomes the pivot
         p = np;
         pid = ost.id[p];
-        q0 = ost.px[p];
-        q1 = ost.py[p];
-        q2 = ost.pz[p];
+        q0 = wk0;
+        q1 = wk1;
+        q2 = wk2;
         pf0 = ost.fx[p];
         pf1 = ost.fy[p];
         pf2 = ost.fz[p];
       }
     }
-    // end of an EC: records, then the tile's next EC
-    if (o_live && !active && e < n_ec) {
+    // end of an EC: records, then the tile's next EC or a new tile
+    if (owner && tr[ot].state == SLOT_RUN && !active) {
       lift_all = lift_all + lift;
       disp_all = disp_all + P.ell;  // the free flights of an EC add up to ell
       nev_all += (unsigned long long)nev;
@@ -852,14 +953,14 @@ __global__ void __launch_bounds__(256) ec_lock_kernel(const ECParams P) {
       }
       ++e;
       if (e < n_ec) start_ec();
+      else tr[ot].state = SLOT_EMPTY;
     }
-    if (owner) publish();
     if (tid == 0) *rq_n = 0;
   }
 
   // ------------------------------------------------------------ counters
   if (confirmed) atomicAdd(&P.counters[CNT_CONFIRMED], confirmed);
-  if (o_live && ecs_done) {
+  if (o_any && ecs_done) {
 #pragma unroll
     for (int k = 0; k < ECMC_NEV; ++k)
       if (cnt[k]) atomicAdd(&P.counters[k], cnt[k]);
@@ -870,16 +971,6 @@ __global__ void __launch_bounds__(256) ec_lock_kernel(const ECParams P) {
     atomicAdd(&P.sums[SUM_REFL], refl_all);
     atomicAdd(&P.sums[SUM_DISP], disp_all);
   }
-  __syncthreads();
-  // ------------------------------------------------------------ write back
-  if (live) {
-    for (int s = gl; s < m; s += G) {
-      const int64_t b = st.id[s];
-      Rr[3 * b] = st.px[s];
-      Rr[3 * b + 1] = st.py[s];
-      Rr[3 * b + 2] = st.pz[s];
-    }
-  }
 }
 #undef TSYS
 #undef SYS
@@ -887,7 +978,7 @@ __global__ void __launch_bounds__(256) ec_lock_kernel(const ECParams P) {
 }  // namespace
 
 size_t lock_smem_bytes(int stage_cap, int motile_cap, int ncell, int tiles_per_block) {
-  return (size_t)tiles_per_block * group_bytes(stage_cap, motile_cap, ncell) +
+  return (size_t)tiles_per_block * group_bytes(stage_cap, 0, motile_cap, ncell) +
          lock_tail_bytes(tiles_per_block);
 }
 
@@ -936,8 +1027,33 @@ static cudaError_t launch_lock_t(const ECParams &P, cudaStream_t s) {
   if (nt == 0 || nt > 32 || nt * G > 256 || (nt * G) % 32) return cudaErrorInvalidValue;
   const size_t smem = lock_smem_bytes(P.stage_cap, P.m_cap, NC, nt);
   if (smem > (size_t)smem_max) return cudaErrorInvalidValue;
-  const int blocks = (P.n_units + nt - 1) / nt;
-  ec_lock_kernel<G, BATCH><<<blocks, nt * G, smem, s>>>(P);
+  // persistent blocks: as many as stay resident, each pulling tiles from the
+  // unit counter until none are left
+  static int sms = 0;
+  static size_t res_key = 0;
+  static int res_blocks = 0;
+  if (!sms) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return e;
+  }
+  const size_t rkey = smem * 64 + (size_t)nt;
+  if (res_key != rkey) {
+    int b = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, ec_lock_kernel<G, BATCH>, nt * G, smem) !=
+        cudaSuccess)
+      return cudaErrorInvalidValue;
+    res_key = rkey;
+    res_blocks = b;
+  }
+  if (res_blocks < 1) return cudaErrorInvalidValue;
+  const long long want = (P.n_units + nt - 1) / nt;
+  const long long room = (long long)res_blocks * sms;
+  const int blocks = (int)(want < room ? want : room);
+  cudaError_t e = cudaMemsetAsync(P.unit_next, 0, sizeof(int32_t), s);
+  if (e != cudaSuccess) return e;
+  if (blocks > 0) ec_lock_kernel<G, BATCH><<<blocks, nt * G, smem, s>>>(P);
   return cudaGetLastError();
 }
 
