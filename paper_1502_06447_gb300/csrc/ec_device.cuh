@@ -364,7 +364,16 @@ __device__ __forceinline__ void stage_tile(const ECParams &P, const RepParams *r
                                            int gl, bool &live, int unit, double c0, double c1,
                                            double c2, double *Rr, const int32_t *Rstart, int S,
                                            int M64, int MNB, int NC, const LGrid &LG, int &m,
-                                           int &j1, int &ns, unsigned mask = FULL) {
+                                           int &j1, int &ns, unsigned mask = FULL,
+                                           bool *overflow = nullptr) {
+  // a tile that does not fit its capacities sets the device status, or, when
+  // the caller passes `overflow`, only that flag (the caller stages the tile
+  // again later with larger capacities)
+  auto capacity = [&]() {
+    if (overflow) *overflow = true;
+    else if (gl == 0) set_status(P.status, DEV_CAPACITY);
+  };
+  if (overflow) *overflow = false;
   if (gl == 0) {
     st.hdr[0] = 0;
     st.hdr[1] = 0;
@@ -503,7 +512,7 @@ __device__ __forceinline__ void stage_tile(const ECParams &P, const RepParams *r
     __syncwarp(mask);
     ns = st.hdr[2];
     if (st.hdr[3]) {
-      if (gl == 0) set_status(P.status, DEV_CAPACITY);
+      capacity();
       live = false;
       ns = 0;
     }
@@ -536,7 +545,7 @@ __device__ __forceinline__ void stage_tile(const ECParams &P, const RepParams *r
     }
     __syncwarp(mask);
     if (m > MNB) {  // more motile beads than the motile capacity
-      if (gl == 0) set_status(P.status, DEV_CAPACITY);
+      if (live) capacity();
       live = false;
     }
     // pass 3: shadows (FP32 position minus FP32 corner, the form the moved
@@ -611,7 +620,7 @@ __device__ __forceinline__ void stage_tile(const ECParams &P, const RepParams *r
     }
     __syncwarp(mask);
     if (st.hdr[3]) {
-      if (gl == 0 && live) set_status(P.status, DEV_CAPACITY);
+      if (live) capacity();
       live = false;
       if (gl == 0) st.hdr[4] = 0;
     }

@@ -59,6 +59,10 @@ struct ecmc_ctx {
   int64_t ncell = 1;
   int32_t stage_cap = 0;
   int32_t m_cap = 0;
+  int32_t stage_tight = 0, m_tight = 0;  // block-lockstep first pass (0: one pass)
+  int32_t *d_deferred = nullptr;         // units left to the second pass
+  int64_t deferred_cap = 0;
+  int32_t *d_n_deferred = nullptr;
   int32_t lanes = 32;
   // one-lane-per-tile kernel: per-tile scratch and local grid
   unsigned char *d_scratch = nullptr;
@@ -247,6 +251,7 @@ ecmc_status alloc_state(ecmc_ctx *c) {
   CU(dalloc(&c->d_status, 1));
   CU(cudaMemset(c->d_status, 0, sizeof(int)));
   CU(dalloc(&c->d_unit_next, 1));
+  CU(dalloc(&c->d_n_deferred, 1));
   CU(dalloc(&c->d_obs_d, 4));
   CU(dalloc(&c->d_obs_u, 2));
   CU(dalloc(&c->d_g1ref, 3 * (c->n / c->N)));
@@ -262,7 +267,7 @@ void destroy(ecmc_ctx *c) {
   if (c->stream) cudaStreamSynchronize(c->stream);
   void *ptrs[] = {c->d_r, c->d_img, c->d_tag, c->d_cell, c->d_rank, c->d_count, c->d_start,
                   c->d_bsum, c->d_cr, c->d_crf, c->d_rf, c->d_cid, c->d_ctag, c->d_cnt, c->d_sums, c->d_status,
-                  c->d_unit_next, c->d_obs_d, c->d_obs_u, c->d_g1ref, c->d_rdig, c->d_rlift, c->d_rev,
+                  c->d_unit_next, c->d_n_deferred, c->d_deferred, c->d_obs_d, c->d_obs_u, c->d_g1ref, c->d_rdig, c->d_rlift, c->d_rev,
                   c->d_log, c->d_log_n, c->d_scratch};
   for (void *p : ptrs) cudaFree(p);
   for (cudaEvent_t e : c->kev) cudaEventDestroy(e);
@@ -450,9 +455,9 @@ ecmc_status ecmc_configure(ecmc_ctx *c, const ecmc_opts *o) {
     return fail(ECMC_EINVAL, "one lane per EC needs the domain mode");
   if (!(p.p_swap >= 0.0)) return fail(ECMC_EINVAL, "p_swap must be >= 0");
   if (p.schedule != 0 && p.schedule != 1) return fail(ECMC_EINVAL, "schedule must be 0 or 1");
-  if (p.block_tiles < 0 || p.block_tiles > 32 || p.block_tiles * lanes > 256 ||
+  if (p.block_tiles < 0 || p.block_tiles > 32 || p.block_tiles * lanes > 128 ||
       (p.block_tiles > 0 && lanes > 1 && p.block_tiles % (32 / lanes) != 0))
-    return fail(ECMC_EINVAL, "block_tiles must be a multiple of 32 / lanes, at most 32 and 256 / lanes");
+    return fail(ECMC_EINVAL, "block_tiles must be a multiple of 32 / lanes, at most 32 and 128 / lanes");
   const double margin = p.precision == ECMC_PREC_FP32F ? 0.01 * sig : 0.0;
   for (int a = 0; a < 3; ++a)
     if (!(s_cap + sig + margin < 0.5 * c->L[a])) return fail(ECMC_EINVAL, "need s_cap + sigma < L/2");
@@ -460,6 +465,7 @@ ecmc_status ecmc_configure(ecmc_ctx *c, const ecmc_opts *o) {
   const double halo_te = (c->b_max > sig ? c->b_max : sig) * (1.0 + 1e-6);
   int32_t stage = p.stage_cap;
   int32_t mcap = 0;
+  int32_t stage_t = 0, m_t = 0;
   if (p.mode == ECMC_MODE_DOMAIN) {
     for (int a = 0; a < 3; ++a) {
       if (p.tiles[a] < 3) return fail(ECMC_EINVAL, "tiles per axis must be >= 3");
@@ -475,8 +481,10 @@ ecmc_status ecmc_configure(ecmc_ctx *c, const ecmc_opts *o) {
     }
     const double rho = (double)c->n / (c->L[0] * c->L[1] * c->L[2]);
     const double E[3] = {c->W[0] + 2.0 * halo_te, c->W[1] + 2.0 * halo_te, c->W[2] + 2.0 * halo_te};
-    if (stage <= 0) stage = stage_bound(E, rho);
+    const bool derived = stage <= 0;
+    if (derived) stage = stage_bound(E, rho);
     mcap = stage_bound(c->W, rho);
+    if (derived) tight_caps(E, c->W, rho, stage, mcap, &stage_t, &m_t);
   } else {
     if (p.precision == ECMC_PREC_FP32F)
       for (int a = 0; a < 3; ++a)
@@ -538,6 +546,18 @@ ecmc_status ecmc_configure(ecmc_ctx *c, const ecmc_opts *o) {
   c->halo_te = halo_te;
   c->stage_cap = stage;
   c->m_cap = mcap > stage ? stage : mcap;
+  c->stage_tight = stage_t;
+  c->m_tight = m_t;
+  if (p.mode == ECMC_MODE_DOMAIN) {
+    const int64_t ntile = (int64_t)p.tiles[0] * p.tiles[1] * p.tiles[2];
+    if (ntile > c->deferred_cap) {
+      cudaFree(c->d_deferred);
+      c->d_deferred = nullptr;
+      c->deferred_cap = 0;
+      CU(dalloc(&c->d_deferred, ntile));
+      c->deferred_cap = ntile;
+    }
+  }
   c->lanes = lanes;
   c->event_cap = p.event_cap > 0 ? p.event_cap : 10000000;
   c->ecs_per_tile = p.ecs_per_tile > 0 ? p.ecs_per_tile : 1;
@@ -605,6 +625,10 @@ static ECParams ec_params(const ecmc_ctx *c, uint64_t seed, double ell) {
   ECParams P{};
   P.block_tiles = c->opts.block_tiles;
   P.unit_next = c->d_unit_next;
+  P.stage_tight = c->stage_tight;
+  P.m_tight = c->m_tight;
+  P.deferred = c->d_deferred;
+  P.n_deferred = c->d_n_deferred;
   P.n = c->n;
   P.N = c->N;
   for (int a = 0; a < 3; ++a) {

@@ -62,6 +62,9 @@ struct ecmc_batch {
   double *d_sums = nullptr;
   int *d_status = nullptr;
   int32_t *d_unit_next = nullptr;
+  int32_t *d_n_deferred = nullptr, *d_deferred = nullptr;
+  int64_t deferred_cap = 0;
+  int32_t stage_tight = 0, m_tight = 0;
   int64_t *d_sweep = nullptr;
   uint64_t *d_rdig = nullptr;
   double *d_rlift = nullptr;
@@ -85,7 +88,8 @@ void batch_free(ecmc_batch *b) {
   void *ptrs[] = {b->d_r, b->d_img, b->d_rep_of, b->d_tag, b->d_cell, b->d_rank, b->d_count,
                   b->d_start, b->d_bsum, b->d_cid, b->d_ctag, b->d_cr, b->d_crf, b->d_rf, b->d_reps,
                   b->d_cnt,
-                  b->d_sums, b->d_status, b->d_unit_next, b->d_sweep, b->d_rdig, b->d_rlift,
+                  b->d_sums, b->d_status, b->d_unit_next, b->d_n_deferred, b->d_deferred, b->d_sweep,
+                  b->d_rdig, b->d_rlift,
                   b->d_rev};
   for (void *p : ptrs) cudaFree(p);
   if (b->ev0) cudaEventDestroy(b->ev0);
@@ -183,6 +187,10 @@ ECParams batch_params(ecmc_batch *b, uint64_t seed, double ell) {
   P.sweep_dev = b->d_sweep;
   P.block_tiles = b->opts.block_tiles;
   P.unit_next = b->d_unit_next;
+  P.stage_tight = b->stage_tight;
+  P.m_tight = b->m_tight;
+  P.deferred = b->d_deferred;
+  P.n_deferred = b->d_n_deferred;
   return P;
 }
 
@@ -256,6 +264,7 @@ ecmc_status ecmc_batch_create(const ecmc_replica_spec *specs, int32_t n, double 
   if (e == cudaSuccess) e = balloc(&b->d_sums, SUM_N);
   if (e == cudaSuccess) e = balloc(&b->d_status, 1);
   if (e == cudaSuccess) e = balloc(&b->d_unit_next, 1);
+  if (e == cudaSuccess) e = balloc(&b->d_n_deferred, 1);
   if (e == cudaSuccess) e = balloc(&b->d_sweep, 1);
   if (e == cudaSuccess) e = cudaMemsetAsync(b->d_img, 0, sizeof(int32_t) * 3 * n_total, b->stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(b->d_cnt, 0, sizeof(unsigned long long) * CNT_N, b->stream);
@@ -305,7 +314,7 @@ ecmc_status ecmc_batch_configure(ecmc_batch *b, const ecmc_opts *o) {
   const double side_min = (reach > bm ? reach : bm) + 2e-3 * sig;
   const double margin = p.precision == ECMC_PREC_FP32F ? 0.01 * sig : 0.0;
   int64_t cell_off = 0, unit_off = 0;
-  int32_t stage = 0, mcap = 0, nclm = 0;
+  int32_t stage = 0, mcap = 0, nclm = 0, stage_t = 0, m_t = 0;
   std::vector<RepParams> reps = b->reps;
   for (int32_t r = 0; r < b->R; ++r) {
     RepParams &R = reps[r];
@@ -349,9 +358,17 @@ ecmc_status ecmc_batch_configure(ecmc_batch *b, const ecmc_opts *o) {
     const int32_t mc = stage_bound(R.W, rho);
     stage = st > stage ? st : stage;
     mcap = mc > mcap ? mc : mcap;
+    int32_t st_t = 0, mc_t = 0;
+    tight_caps(E, R.W, rho, st, mc, &st_t, &mc_t);
+    stage_t = st_t > stage_t ? st_t : stage_t;
+    m_t = mc_t > m_t ? mc_t : m_t;
     nclm = (int32_t)ncl > nclm ? (int32_t)ncl : nclm;
   }
-  if (p.stage_cap > 0) stage = (p.stage_cap + 31) / 32 * 32;
+  if (p.stage_cap > 0) {
+    stage = (p.stage_cap + 31) / 32 * 32;
+    stage_t = m_t = 0;  // caller-fixed capacity: one pass
+  }
+  if (m_t > stage_t) m_t = stage_t;
   if (mcap > stage) mcap = stage;
   if (stage > 65534) return bfail(ECMC_EINVAL, "at most 65534 staged beads per tile");
   if (unit_off >= (1ll << 31)) return bfail(ECMC_EINVAL, "too many tiles");
@@ -360,9 +377,9 @@ ecmc_status ecmc_batch_configure(ecmc_batch *b, const ecmc_opts *o) {
   BCU(cudaDeviceGetAttribute(&smem_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
   const int M = p.precision == ECMC_PREC_FP32F ? mcap : stage;
   if (p.schedule != 0 && p.schedule != 1) return bfail(ECMC_EINVAL, "schedule must be 0 or 1");
-  if (p.block_tiles < 0 || p.block_tiles > 32 || p.block_tiles * lanes > 256 ||
+  if (p.block_tiles < 0 || p.block_tiles > 32 || p.block_tiles * lanes > 128 ||
       (p.block_tiles > 0 && p.block_tiles % (32 / lanes)))
-    return bfail(ECMC_EINVAL, "block_tiles must be a multiple of 32 / lanes, at most 32 and 256 / lanes");
+    return bfail(ECMC_EINVAL, "block_tiles must be a multiple of 32 / lanes, at most 32 and 128 / lanes");
   const bool lock = p.precision == ECMC_PREC_FP32F && p.schedule == 0 && lanes <= 16;
   const int bt = p.block_tiles > 0 ? p.block_tiles : 32 / lanes;
   const size_t need = lock ? lock_smem_bytes(stage, M, nclm, bt) : ec_smem_bytes(stage, M, nclm, 32 / lanes);
@@ -391,6 +408,15 @@ ecmc_status ecmc_batch_configure(ecmc_batch *b, const ecmc_opts *o) {
   b->halo_te = halo_te;
   b->stage_cap = stage;
   b->m_cap = mcap;
+  b->stage_tight = stage_t;
+  b->m_tight = m_t;
+  if (unit_off > b->deferred_cap) {
+    cudaFree(b->d_deferred);
+    b->d_deferred = nullptr;
+    b->deferred_cap = 0;
+    BCU(balloc(&b->d_deferred, unit_off));
+    b->deferred_cap = unit_off;
+  }
   b->ncl_max = nclm;
   b->lanes = lanes;
   b->ecs_per_tile = p.ecs_per_tile > 0 ? p.ecs_per_tile : 1;

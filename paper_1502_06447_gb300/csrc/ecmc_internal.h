@@ -106,6 +106,14 @@ struct ECParams {
   // device counter its persistent blocks take units from (reset per launch)
   int32_t block_tiles;
   int32_t *unit_next;
+  // block-lockstep kernel: tight capacities for a first pass (0: none); a
+  // tile that does not fit them is listed in `deferred` and run by a second
+  // pass with stage_cap / m_cap (tiles are independent, so the events are
+  // the same).  defer_mode: 0 one pass, 1 first pass, 2 second pass.
+  int32_t stage_tight, m_tight;
+  int32_t defer_mode;
+  int32_t *deferred;
+  int32_t *n_deferred;
 };
 
 // message for ecmc_last_error (ecmc_api.cu)
@@ -214,6 +222,21 @@ inline int32_t stage_bound(const double E[3], double rho) {
   const double b = fluct > lat ? fluct : lat;
   const int64_t n = (int64_t)ceil(b);
   return (int32_t)((n + 31) / 32 * 32);
+}
+
+// Tight capacities of the block-lockstep kernel's first pass: about the
+// mean occupancy of a melted tile plus a margin, rounded to 8 (tiles that
+// exceed them, e.g. at the lattice start, run in the second pass).
+inline void tight_caps(const double E[3], const double Wm[3], double rho, int32_t full_stage,
+                       int32_t full_m, int32_t *stage_t, int32_t *m_t) {
+  const double vs = E[0] * E[1] * E[2], vm = Wm[0] * Wm[1] * Wm[2];
+  int64_t st = (int64_t)ceil(1.08 * rho * vs + 16.0);
+  int64_t mt = (int64_t)ceil(1.2 * rho * vm + 12.0);
+  st = (st + 7) / 8 * 8;
+  mt = (mt + 7) / 8 * 8;
+  *stage_t = (int32_t)(st < full_stage ? st : full_stage);
+  *m_t = (int32_t)(mt < full_m ? mt : full_m);
+  if (*m_t > *stage_t) *m_t = *stage_t;
 }
 
 // ---------------------------------------------------------------- autotuner

@@ -82,7 +82,7 @@ __host__ __device__ __forceinline__ size_t lock_tail_bytes(int NT) {
 #define TSYS(R, f) (BATCH ? (R)->f : P.f)
 
 template <int G, bool BATCH>
-__global__ void __launch_bounds__(256) ec_lock_kernel(const ECParams P) {
+__global__ void __launch_bounds__(128, 3) ec_lock_kernel(const ECParams P) {
   extern __shared__ __align__(16) unsigned char smem[];
   const int tid = threadIdx.x;
   const int lane = tid & 31;
@@ -127,7 +127,10 @@ __global__ void __launch_bounds__(256) ec_lock_kernel(const ECParams P) {
   // take the next unit and stage it (group-collective); false when none left
   auto take_tile = [&]() -> bool {
     int u = 0;
-    if (gl == 0) u = atomicAdd(P.unit_next, 1);
+    if (gl == 0) {
+      u = atomicAdd(P.unit_next, 1);
+      if (P.defer_mode == 2) u = u < *P.n_deferred ? P.deferred[u] : P.n_units;
+    }
     u = __shfl_sync(gmask, u, gbase);
     if (u >= P.n_units) return false;
     const int gu = u;
@@ -163,8 +166,10 @@ __global__ void __launch_bounds__(256) ec_lock_kernel(const ECParams P) {
     const double c1 = unit53(w.v[1]) * SYS(T)[1] + (double)tk1 * SYS(T)[1];
     const double c2 = unit53(w.v[2]) * SYS(T)[2] + (double)tk2 * SYS(T)[2];
     live = true;
+    bool over = false;
     stage_tile<G, true, BATCH>(P, rp, st, gl, live, unit, c0, c1, c2, Rr, Rstart, S, 0, MNB, NC, LG,
-                               m, j1, ns, gmask);
+                               m, j1, ns, gmask, P.defer_mode == 1 ? &over : nullptr);
+    if (over && gl == 0) P.deferred[atomicAdd(P.n_deferred, 1)] = gu;
     if (!live) m = 0;
     if (gl == 0) {
       TileRec &T = tr[gib];
@@ -982,8 +987,15 @@ size_t lock_smem_bytes(int stage_cap, int motile_cap, int ncell, int tiles_per_b
          lock_tail_bytes(tiles_per_block);
 }
 
+// tiles per block and resident blocks for one capacity setting (memoised)
+struct LockShape {
+  size_t key = 0;
+  int nt = 0, blocks = 0;
+};
+
 template <int G, bool BATCH>
-static cudaError_t launch_lock_t(const ECParams &P, cudaStream_t s) {
+static cudaError_t lock_shape(const ECParams &P, int S, int M, int NC, LockShape *memo, int *nt_out,
+                              int *res_out, size_t *smem_out) {
   static int smem_max = 0;
   if (!smem_max) {
     int dev = 0;
@@ -994,67 +1006,82 @@ static cudaError_t launch_lock_t(const ECParams &P, cudaStream_t s) {
                              smem_max);
     if (e != cudaSuccess) return e;
   }
-  // tiles per block: whole warps, at most 32 (the owners fill warp 0) and
-  // 256 threads; among those, the most tiles resident per SM
-  const int NC = P.domain ? (BATCH ? P.ncl_max : P.lg[0] * P.lg[1] * P.lg[2]) : 0;
-  const int step = 32 / G > 1 ? 32 / G : 1;
-  static size_t memo_key = 0;
-  static int memo_nt = 0;
-  const size_t key = lock_smem_bytes(P.stage_cap, P.m_cap, NC, 1) * 64 + (size_t)P.n_units % 64;
-  int nt = 0;
-  if (P.block_tiles > 0) {
-    nt = P.block_tiles;
-  } else if (memo_key == key && memo_nt) {
-    nt = memo_nt;
-  } else {
-    int best = -1;
-    for (int t = step; t <= 32 && t * G <= 256; t += step) {
-      const size_t sm = lock_smem_bytes(P.stage_cap, P.m_cap, NC, t);
-      if (sm > (size_t)smem_max) break;
-      int blocks = 0;
-      if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, ec_lock_kernel<G, BATCH>, t * G, sm) !=
-          cudaSuccess)
-        return cudaErrorInvalidValue;
-      const int resident = blocks * t;
-      if (resident > best) {
-        best = resident;
-        nt = t;
-      }
+  const size_t key = (lock_smem_bytes(S, M, NC, 1) * 64 + (size_t)P.block_tiles) * 4096 +
+                     (size_t)(P.n_units % 4096);
+  for (int i = 0; i < 2; ++i) {
+    if (memo[i].key == key && memo[i].nt) {
+      *nt_out = memo[i].nt;
+      *res_out = memo[i].blocks;
+      *smem_out = lock_smem_bytes(S, M, NC, memo[i].nt);
+      return cudaSuccess;
     }
-    memo_key = key;
-    memo_nt = nt;
   }
-  if (nt == 0 || nt > 32 || nt * G > 256 || (nt * G) % 32) return cudaErrorInvalidValue;
-  const size_t smem = lock_smem_bytes(P.stage_cap, P.m_cap, NC, nt);
-  if (smem > (size_t)smem_max) return cudaErrorInvalidValue;
-  // persistent blocks: as many as stay resident, each pulling tiles from the
-  // unit counter until none are left
+  // tiles per block: whole warps, at most 32 (the owners fill warp 0) and
+  // 128 threads; among those, the most tiles resident per SM
+  const int step = 32 / G > 1 ? 32 / G : 1;
+  int nt = 0, best = -1, best_blocks = 0;
+  for (int t = step; t <= 32 && t * G <= 128; t += step) {
+    if (P.block_tiles > 0 && t != P.block_tiles) continue;
+    const size_t sm = lock_smem_bytes(S, M, NC, t);
+    if (sm > (size_t)smem_max) break;
+    int blocks = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, ec_lock_kernel<G, BATCH>, t * G, sm) !=
+        cudaSuccess)
+      return cudaErrorInvalidValue;
+    if (blocks * t > best) {
+      best = blocks * t;
+      nt = t;
+      best_blocks = blocks;
+    }
+  }
+  if (nt == 0 || best_blocks < 1) return cudaErrorInvalidValue;
+  memo[1] = memo[0];
+  memo[0].key = key;
+  memo[0].nt = nt;
+  memo[0].blocks = best_blocks;
+  *nt_out = nt;
+  *res_out = best_blocks;
+  *smem_out = lock_smem_bytes(S, M, NC, nt);
+  return cudaSuccess;
+}
+
+template <int G, bool BATCH>
+static cudaError_t launch_lock_t(const ECParams &P0, cudaStream_t s) {
   static int sms = 0;
-  static size_t res_key = 0;
-  static int res_blocks = 0;
   if (!sms) {
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     if (e != cudaSuccess) return e;
   }
-  const size_t rkey = smem * 64 + (size_t)nt;
-  if (res_key != rkey) {
-    int b = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, ec_lock_kernel<G, BATCH>, nt * G, smem) !=
-        cudaSuccess)
-      return cudaErrorInvalidValue;
-    res_key = rkey;
-    res_blocks = b;
-  }
-  if (res_blocks < 1) return cudaErrorInvalidValue;
-  const long long want = (P.n_units + nt - 1) / nt;
-  const long long room = (long long)res_blocks * sms;
-  const int blocks = (int)(want < room ? want : room);
-  cudaError_t e = cudaMemsetAsync(P.unit_next, 0, sizeof(int32_t), s);
+  static LockShape memo[2];
+  const int NC = BATCH ? P0.ncl_max : P0.lg[0] * P0.lg[1] * P0.lg[2];
+  const bool two = P0.stage_tight > 0 && P0.m_tight > 0 && P0.deferred && P0.n_deferred &&
+                   (P0.stage_tight < P0.stage_cap || P0.m_tight < P0.m_cap);
+  // persistent blocks: as many as stay resident, each pulling tiles from the
+  // unit counter until none are left
+  auto run = [&](ECParams P, int S, int M, int mode) -> cudaError_t {
+    P.stage_cap = S;
+    P.m_cap = M;
+    P.defer_mode = mode;
+    int nt = 0, res = 0;
+    size_t smem = 0;
+    cudaError_t e = lock_shape<G, BATCH>(P, S, M, NC, memo, &nt, &res, &smem);
+    if (e != cudaSuccess) return e;
+    const long long want = (P.n_units + nt - 1) / nt;
+    const long long room = (long long)res * sms;
+    const int blocks = (int)(want < room ? want : room);
+    e = cudaMemsetAsync(P.unit_next, 0, sizeof(int32_t), s);
+    if (e != cudaSuccess) return e;
+    if (blocks > 0) ec_lock_kernel<G, BATCH><<<blocks, nt * G, smem, s>>>(P);
+    return cudaGetLastError();
+  };
+  if (!two) return run(P0, P0.stage_cap, P0.m_cap, 0);
+  cudaError_t e = cudaMemsetAsync(P0.n_deferred, 0, sizeof(int32_t), s);
   if (e != cudaSuccess) return e;
-  if (blocks > 0) ec_lock_kernel<G, BATCH><<<blocks, nt * G, smem, s>>>(P);
-  return cudaGetLastError();
+  e = run(P0, P0.stage_tight, P0.m_tight, 1);
+  if (e != cudaSuccess) return e;
+  return run(P0, P0.stage_cap, P0.m_cap, 2);
 }
 
 cudaError_t launch_ec_lock(const ECParams &P, int lanes, cudaStream_t s) {

@@ -149,11 +149,12 @@ BLOCKS = Melt("blocks_24x24x28_N8", (24, 24, 28), 1.05, 8, ell=4.0, seed=0xEC00A
               dir_mode="iso", sweeps=2, D=(6, 6, 7))
 
 
-@pytest.mark.parametrize("lanes,block_tiles", [(8, 4), (8, 8), (8, 32), (4, 8), (4, 32), (16, 2),
-                                               (16, 16)])
+@pytest.mark.parametrize("lanes,block_tiles", [(8, 4), (8, 8), (8, 16), (4, 8), (4, 32), (16, 2),
+                                               (16, 8)])
 def test_block_lockstep_block_sizes(lanes, block_tiles):
     """Every block size of the block-lockstep kernel (tiles per block from
-    32 / lanes to 32, full and ragged last blocks) gives the oracle's events."""
+    32 / lanes up to 128 threads, full and ragged last blocks) gives the
+    oracle's events."""
     m = BLOCKS
     o = oracle_system(m)
     res = o.run_domain(m.sweeps, m.ell, digests=True)
@@ -292,6 +293,11 @@ def test_invalid_arguments_and_states():
     assert e.value.code == -1
     with pytest.raises(ecmc.EcmcError):
         ctx.run(1.0, chains_per_sweep=1)  # not configured after the failure
+    for lanes, bt in ((8, 32), (16, 16), (8, 6)):  # > 128 threads, or not whole warps
+        with pytest.raises(ecmc.EcmcError) as e:
+            ctx.configure(mode=ecmc.MODE_DOMAIN, tiles=(3, 3, 3), precision=ecmc.PREC_FP32F,
+                          lanes=lanes, block_tiles=bt)
+        assert e.value.code == -1
 
 
 def test_event_cap_and_stage_capacity_report_errors():
