@@ -115,6 +115,8 @@ def _load():
             lib.orc_min_pair.argtypes = [P(Params), P(C.c_double), P(C.c_double),
                                          P(C.c_int64)]
             lib.orc_min_pair_cells.argtypes = lib.orc_min_pair.argtypes
+            lib.orc_contacts.argtypes = [P(Params), P(C.c_double), C.c_double, P(C.c_int64),
+                                         P(C.c_int64)]
             lib.orc_start_draws.argtypes = [P(Params), C.c_int64, C.c_int64, P(C.c_int64),
                                             P(C.c_double)]
             _lib = lib
@@ -239,6 +241,26 @@ class System:
         fn = lib.orc_min_pair_cells if use_cells else lib.orc_min_pair
         fn(C.byref(self.P), _ptr(self.r, C.c_double), C.byref(dmin), C.byref(cnt))
         return dmin.value, cnt.value
+
+    def contacts(self, delta):
+        """Pair counts in the two shells of width delta above sigma and bond
+        counts in the two shells below b_max (every pair, brute force)."""
+        lib = _load()
+        pairs = np.zeros(2, dtype=np.int64)
+        bonds = np.zeros(2, dtype=np.int64)
+        lib.orc_contacts(C.byref(self.P), _ptr(self.r, C.c_double), float(delta),
+                         _ptr(pairs, C.c_int64), _ptr(bonds, C.c_int64))
+        return pairs, bonds
+
+    def contact_pressure(self, delta):
+        """betaP/rho from the contact values (virial theorem for hard
+        constraints): 1 + [sigma f(sigma+) - b_max f_b(b_max-)] / (3 n), with
+        f, f_b the pair and bond counts per unit distance at contact, each
+        extrapolated linearly from its two shells."""
+        pairs, bonds = self.contacts(delta)
+        fs = (1.5 * pairs[0] - 0.5 * pairs[1]) / delta
+        fb = (1.5 * bonds[0] - 0.5 * bonds[1]) / delta
+        return 1.0 + (self.P.sigma * fs - self.P.b_max * fb) / (3.0 * self.P.n)
 
     def start_draws(self, n, ec0=0):
         """Start bead and direction of serial ECs ec0..ec0+n-1."""

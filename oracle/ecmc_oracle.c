@@ -834,6 +834,46 @@ int orc_min_pair_cells(const orc_params *P, double *r, double *dmin,
   return 0;
 }
 
+/* Contact counts behind the configurational pressure (the virial theorem
+ * for hard constraints): pairs with |r_ij| in [sigma, sigma + delta) and
+ * [sigma + delta, sigma + 2 delta) (the first shell also takes pairs a
+ * rounding error inside sigma, as the overlap test does), and bonds with
+ * length in (b_max - delta, b_max] and (b_max - 2 delta, b_max - delta]
+ * (the first shell up to the tether-violation tolerance).  Brute force over
+ * every pair. */
+int orc_contacts(const orc_params *P, const double *r, double delta, int64_t *pairs,
+                 int64_t *bonds) {
+  const double lo = P->sigma * P->sigma * (1.0 - 1e-10);
+  const double s1 = (P->sigma + delta) * (P->sigma + delta);
+  const double s2 = (P->sigma + 2.0 * delta) * (P->sigma + 2.0 * delta);
+  const double t0 = P->b_max * P->b_max * (1.0 + 1e-10);
+  const double t1 = (P->b_max - delta) * (P->b_max - delta);
+  const double t2 = (P->b_max - 2.0 * delta) * (P->b_max - 2.0 * delta);
+  pairs[0] = pairs[1] = 0;
+  bonds[0] = bonds[1] = 0;
+  for (int64_t i = 0; i < P->n; ++i)
+    for (int64_t j = i + 1; j < P->n; ++j) {
+      double dd = 0.0;
+      for (int a = 0; a < 3; ++a) {
+        double d = minimg(r[3 * i + a] - r[3 * j + a], P->L[a]);
+        dd += d * d;
+      }
+      if (dd >= lo && dd < s1) ++pairs[0];
+      else if (dd >= s1 && dd < s2) ++pairs[1];
+    }
+  for (int64_t b = 0; b + 1 < P->n; ++b) {
+    if ((b + 1) % P->N == 0) continue; /* b is the last bead of its chain */
+    double dd = 0.0;
+    for (int a = 0; a < 3; ++a) {
+      double d = minimg(r[3 * (b + 1) + a] - r[3 * b + a], P->L[a]);
+      dd += d * d;
+    }
+    if (dd > t1 && dd <= t0) ++bonds[0];
+    else if (dd > t2 && dd <= t1) ++bonds[1];
+  }
+  return 0;
+}
+
 /* start draws of serial ECs ec0..ec0+n-1 (for the direction/start checks) */
 int orc_start_draws(const orc_params *P, int64_t ec0, int64_t n, int64_t *idx,
                     double *v) {

@@ -213,34 +213,58 @@ def test_domain_single_bead_uniform_in_box():
 
 
 # ---------------------------------------------------------------- 3D hard spheres
-def _hs_fluid(phi, seed, n_eq, n_run, ell=2.0):
+def _hs_fluid(phi, seed, n_eq, n_run, ell=2.0, blocks=50, delta=0.02):
+    """Serial ECs on 252 unbonded spheres: per block the lift-distance
+    pressure and the contact-value pressure of the block's last state."""
     dims = (6, 6, 7)
     a = (math.pi / (6 * phi)) ** (1 / 3)
     r = oracle.lattice(dims, a)
     s = oracle.System(r, tuple(d * a for d in dims), 1, s_cap=0.4, dir_mode=DIR_ISO,
                       seed=seed)
     s.run_serial(n_eq, ell)
-    z = []
-    chunk = n_run // 50
-    for b in range(50):
+    z, zc = [], []
+    chunk = n_run // blocks
+    for b in range(blocks):
         res = s.run_serial(chunk, ell, ec0=n_eq + b * chunk)
         z.append(1.0 + res["stats"]["lift_sum"] / (chunk * ell))
-    return np.array(z), s
+        zc.append(s.contact_pressure(delta))
+    return np.array(z), np.array(zc), s
 
 
 def test_hard_sphere_fluid_pressure_carnahan_starling():
     """Unbonded hard spheres (N=1) at phi = 0.30: the lift-distance estimator
-    must reproduce Carnahan-Starling (1+e+e^2-e^3)/(1-e)^3 within 3 standard
-    errors plus a 1% budget for CS itself and the 252-sphere finite size."""
+    and the contact-value estimator must both reproduce Carnahan-Starling
+    (1+e+e^2-e^3)/(1-e)^3 within 3 standard errors plus a 1% budget for CS
+    itself and the 252-sphere finite size (the contact value also carries
+    the bias of its linear extrapolation over 0.04 sigma)."""
     phi = 0.30
-    z, s = _hs_fluid(phi, 0xC5, 3000, 60000)
+    z, zc, s = _hs_fluid(phi, 0xC5, 3000, 60000, blocks=150)
     zcs = (1 + phi + phi ** 2 - phi ** 3) / (1 - phi) ** 3
     se = z.std(ddof=1) / math.sqrt(len(z))
     assert abs(z.mean() - zcs) < 3 * se + 0.01 * zcs, (z.mean(), se, zcs)
+    sec = zc.std(ddof=1) / math.sqrt(len(zc))
+    assert abs(zc.mean() - zcs) < 3 * sec + 0.015 * zcs, (zc.mean(), sec, zcs)
     dmin, nov = s.min_pair()
     assert nov == 0 and dmin >= 1.0 - 1e-12
 
 
+def test_contact_counts_hand_built():
+    """Contact shells on a hand-built state (delta = 0.02): a dimer at 1.005
+    (pair shell 1), a non-bonded pair at 1.03 across the periodic boundary
+    (pair shell 2), dimers stretched to 1.19 and 1.17 (bond shells 1 and 2)
+    and one at 1.1 (neither); everything else far apart."""
+    L = 20.0
+    r = np.array([
+        [2.0, 2.0, 2.0], [3.005, 2.0, 2.0],      # dimer, pair shell 1
+        [10.0, 10.0, 5.0], [10.0, 11.19, 5.0],   # bond shell 1
+        [5.0, 15.0, 15.0], [5.0, 15.0, 16.17],   # bond shell 2
+        [19.5, 8.0, 8.0], [19.5, 9.1, 8.0],      # plain dimer
+        [0.53, 8.0, 8.0], [0.53, 12.0, 12.0],    # bead 8: 1.03 from bead 6 across x = L
+    ])
+    s = oracle.System(r, (L, L, L), 2, sigma=1.0, b_max=1.2)
+    pairs, bonds = s.contacts(0.02)
+    assert list(pairs) == [1, 1], pairs
+    assert list(bonds) == [1, 1], bonds
 # ---------------------------------------------------------------- invariants
 def test_invariants_after_c1_sized_run():
     """C1 geometry (8x8x10 lattice, N=10): after serial ECs no pair overlaps,
