@@ -269,7 +269,7 @@ def run_gpu(args, rank, world):
                    "precision": "fp32 screen + fp64 confirm", "swap_attempts_per_bead_sweep":
                    SWAP_RATE, "lanes_per_ec": tune["lanes"] if tune else args.lanes,
                    "ecs_per_tile": tune["ecs_per_tile"] if tune else args.ecs_per_tile,
-                   "cell_side": tune["cell_side"] if tune else 1.0,
+                   "cell_side": tune["cell_side"] if tune else 1.05,
                    "tuning": "autotuned (ECs per device-second)" if tune else "fixed",
                    "l2": "flushed between steps (256 MB write)",
                    "parallelism": "replicas" if world > 1 else "1 GPU"},

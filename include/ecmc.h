@@ -92,7 +92,7 @@ typedef struct ecmc_opts {
                             scratch region); 0 -> 32 */
   int32_t record;        /* 1: keep per-EC digests / lift sums of the last run */
   int32_t stage_cap;     /* staged beads per tile; 0 -> derived from the tile size */
-  double cell_side;      /* side of the global cell grid (domain); 0 -> 1.0 sigma */
+  double cell_side;      /* side of the global cell grid (domain); 0 -> 1.05 sigma */
   double tile_side;      /* batch: target tile side when tiles[0] <= 0 (per replica
                             D = floor(L / tile_side), at least 3); 0 -> 4.2 sigma */
   int32_t schedule;      /* screened domain form with lanes 4, 8 or 16:
@@ -117,7 +117,10 @@ typedef struct ecmc_obs {
   double refl_sum;             /* same projection at immotile contacts */
   double disp_sum;             /* sum of all free flights (= ecs * ell) */
   double ell_sum;              /* sum of ell over ECs */
-  double pressure;             /* betaP/rho = 1 + lift_sum / ell_sum */
+  double pressure;             /* betaP/rho = 1 + lift_sum / ell_sum: the
+                                  lift-distance estimator; unbiased for
+                                  serial runs, biased low in the domain mode
+                                  (reflections and walls are not lifts) */
   double re2_mean;             /* <R_e^2> over chains (minimum-image bonds) */
   double bond_max, bond_min;   /* longest / shortest bond */
   int64_t overlaps;            /* pairs with |r_ij|^2 < sigma^2 (1 - 1e-10) */
@@ -126,6 +129,16 @@ typedef struct ecmc_obs {
   double device_seconds;       /* device time of all ecmc_run calls */
   double ec_kernel_seconds;    /* device time of the EC kernel launches alone */
   int64_t confirmed;           /* FP64 confirmations of the FP32 screen */
+  /* contact values of the current state (virial theorem for hard
+   * constraints, valid whatever moves produced the state), shell width
+   * d = contact_delta: */
+  int64_t contact_pairs[2];    /* pairs with |r_ij| in [sigma, sigma + d), [sigma + d, sigma + 2d) */
+  int64_t taut_bonds[2];       /* bonds in (b_max - d, b_max], (b_max - 2d, b_max - d] */
+  double contact_delta;        /* d = 0.02 sigma */
+  double pressure_contact;     /* betaP/rho = 1 + [sigma f(sigma+) - b_max f_b(b_max-)] / (3 n),
+                                  f, f_b pairs / bonds per unit distance at
+                                  contact, each extrapolated linearly from its
+                                  two shells */
 } ecmc_obs;
 
 /* One EC event of the parity log (ecmc_event_log). */
@@ -278,7 +291,7 @@ ecmc_status ecmc_batch_records(ecmc_batch *b, uint64_t *digest, double *lift,
 /* ---- autotuner -------------------------------------------------------------
  * Picks the launch setting of the domain sweep for this machine and system
  * (the paper fixes none: Sec. II.B leaves the tile size open): lanes per EC
- * (4, 8, 16, 32), tile side (3.4 ... 7 sigma), global cell side (1 or 1.4
+ * (4, 8, 16, 32), tile side (3.4 ... 7 sigma), global cell side (1.05 or 1.4
  * sigma) and ECs per tile (1 or 2), by a coordinate descent over short timed
  * trials.  Each trial restores the state saved on entry, runs one untimed
  * sweep and `trial_sweeps` timed ones; the score is ECs per device-second.

@@ -197,20 +197,37 @@ ObsParams obs_params(const ecmc_ctx *c) {
 
 struct ObsHost {
   double re2_sum, bmax, bmin, g1_sum;
-  unsigned long long overlaps, viol;
+  unsigned long long overlaps, viol, pairs[2], taut[2];
 };
+
+// width of the contact shells (units of sigma)
+constexpr double CONTACT_DELTA = 0.02;
 
 // R_e^2, bonds, overlaps, g1 of the current positions (synchronises)
 ecmc_status measure(ecmc_ctx *c, ObsHost *o) {
-  ecmc_status s = set_grid(c, c->configured && c->opts.cell_side > 0 ? c->opts.cell_side : c->sigma);
+  // cells no narrower than the outer contact shell
+  const double reach = (1.0 + 2.0 * CONTACT_DELTA) * c->sigma * (1.0 + 1e-9);
+  double side = c->configured && c->opts.cell_side > 0 ? c->opts.cell_side : 1.05 * c->sigma;
+  if (side < reach) side = reach;
+  ecmc_status s = set_grid(c, side);
   if (s != ECMC_OK) return s;
   CU(launch_cells(cell_params(c, false, 0, 0), c->ncell, c->stream));
   const double init_d[4] = {0.0, 0.0, 1e300, 0.0};
   CU(cudaMemcpyAsync(c->d_obs_d, init_d, sizeof(init_d), cudaMemcpyHostToDevice, c->stream));
-  CU(cudaMemsetAsync(c->d_obs_u, 0, 2 * sizeof(unsigned long long), c->stream));
-  CU(launch_obs(obs_params(c), c->stream));
+  CU(cudaMemsetAsync(c->d_obs_u, 0, 6 * sizeof(unsigned long long), c->stream));
+  ObsParams O = obs_params(c);
+  {
+    const double sg = c->sigma, bm = c->b_max, d = CONTACT_DELTA * c->sigma;
+    O.c_lo = sg * sg * (1.0 - 1e-10);
+    O.c_s1 = (sg + d) * (sg + d);
+    O.c_s2 = (sg + 2.0 * d) * (sg + 2.0 * d);
+    O.c_t0 = bm * bm * (1.0 + 1e-10);
+    O.c_t1 = (bm - d) * (bm - d);
+    O.c_t2 = (bm - 2.0 * d) * (bm - 2.0 * d);
+  }
+  CU(launch_obs(O, c->stream));
   double hd[4];
-  unsigned long long hu[2];
+  unsigned long long hu[6];
   CU(cudaMemcpyAsync(hd, c->d_obs_d, sizeof(hd), cudaMemcpyDeviceToHost, c->stream));
   CU(cudaMemcpyAsync(hu, c->d_obs_u, sizeof(hu), cudaMemcpyDeviceToHost, c->stream));
   CU(cudaStreamSynchronize(c->stream));
@@ -220,6 +237,10 @@ ecmc_status measure(ecmc_ctx *c, ObsHost *o) {
   o->g1_sum = hd[3];
   o->overlaps = hu[0];
   o->viol = hu[1];
+  o->pairs[0] = hu[2];
+  o->pairs[1] = hu[3];
+  o->taut[0] = hu[4];
+  o->taut[1] = hu[5];
   return ECMC_OK;
 }
 
@@ -253,7 +274,7 @@ ecmc_status alloc_state(ecmc_ctx *c) {
   CU(dalloc(&c->d_unit_next, 1));
   CU(dalloc(&c->d_n_deferred, 1));
   CU(dalloc(&c->d_obs_d, 4));
-  CU(dalloc(&c->d_obs_u, 2));
+  CU(dalloc(&c->d_obs_u, 6));
   CU(dalloc(&c->d_g1ref, 3 * (c->n / c->N)));
   CU(cudaStreamCreateWithFlags(&c->own, cudaStreamNonBlocking));
   c->stream = c->own;
@@ -562,7 +583,7 @@ ecmc_status ecmc_configure(ecmc_ctx *c, const ecmc_opts *o) {
   c->event_cap = p.event_cap > 0 ? p.event_cap : 10000000;
   c->ecs_per_tile = p.ecs_per_tile > 0 ? p.ecs_per_tile : 1;
   c->configured = true;
-  const double side = p.cell_side > 0 ? p.cell_side : sig;
+  const double side = p.cell_side > 0 ? p.cell_side : 1.05 * sig;
   if (!(side >= sig)) return fail(ECMC_EINVAL, "cell side must be >= sigma");
   return set_grid(c, side);
 }
@@ -821,6 +842,15 @@ ecmc_status ecmc_observables(ecmc_ctx *c, ecmc_obs *out) {
   out->device_seconds = c->device_seconds;
   out->ec_kernel_seconds = c->ec_seconds;
   out->confirmed = (int64_t)h[CNT_CONFIRMED];
+  const double d = CONTACT_DELTA * c->sigma;
+  for (int k = 0; k < 2; ++k) {
+    out->contact_pairs[k] = (int64_t)o.pairs[k];
+    out->taut_bonds[k] = (int64_t)o.taut[k];
+  }
+  out->contact_delta = d;
+  const double fs = (1.5 * (double)o.pairs[0] - 0.5 * (double)o.pairs[1]) / d;
+  const double fb = (1.5 * (double)o.taut[0] - 0.5 * (double)o.taut[1]) / d;
+  out->pressure_contact = 1.0 + (c->sigma * fs - c->b_max * fb) / (3.0 * (double)c->n);
   return ECMC_OK;
 }
 
@@ -1069,7 +1099,7 @@ ecmc_status ecmc_autotune(ecmc_ctx *c, double ell, uint64_t seed, int32_t trial_
     return ECMC_OK;
   };
   TunePoint start{c->lanes == 1 ? 8 : c->lanes, c->T[0] / sig * (1.0 - 1e-9),
-                  base.cell_side > 0 ? base.cell_side / sig : 1.0, c->ecs_per_tile};
+                  base.cell_side > 0 ? base.cell_side / sig : 1.05, c->ecs_per_tile};
   TunePoint best{};
   TuneScore best_s{};
   int n = 0;

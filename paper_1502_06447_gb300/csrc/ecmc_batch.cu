@@ -303,7 +303,7 @@ ecmc_status ecmc_batch_configure(ecmc_batch *b, const ecmc_opts *o) {
   const double s_cap = p.s_cap > 0 ? p.s_cap : 0.25 * sig;
   const double w = p.joint > 0 ? p.joint : b->b_max;
   if (!(w >= b->b_max)) return bfail(ECMC_EINVAL, "joint width must be >= b_max");
-  const double side = p.cell_side > 0 ? p.cell_side : sig;
+  const double side = p.cell_side > 0 ? p.cell_side : 1.05 * sig;
   if (!(side >= sig)) return bfail(ECMC_EINVAL, "cell side must be >= sigma");
   const double tside = p.tile_side > 0 ? p.tile_side : 4.2 * sig;
   const double halo_hs = sig * (1.0 + 1e-6);
@@ -630,7 +630,7 @@ ecmc_status ecmc_batch_autotune(ecmc_batch *b, double ell, uint64_t seed, int32_
     sc->events_per_s = (double)(e1 - e0) / dt;
     return ECMC_OK;
   };
-  TunePoint start{b->lanes, base.tile_side / sig, base.cell_side > 0 ? base.cell_side / sig : 1.0,
+  TunePoint start{b->lanes, base.tile_side / sig, base.cell_side > 0 ? base.cell_side / sig : 1.05,
                   b->ecs_per_tile};
   TunePoint best{};
   TuneScore best_s{};

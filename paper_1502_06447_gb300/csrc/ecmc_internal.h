@@ -197,7 +197,10 @@ struct ObsParams {
   const int32_t *cstart;
   const int32_t *cell;     // cell of each bead
   double *out_d;           // [re2_sum, bond_max, bond_min(neg), g1_sum]
-  unsigned long long *out_u; // [overlaps, tether_violations]
+  // [overlaps, tether_violations, contact pairs (2 shells), taut bonds (2 shells)]
+  unsigned long long *out_u;
+  // squared shell bounds: pairs [lo, s1), [s1, s2); bonds (t1, t0], (t2, t1]
+  double c_lo, c_s1, c_s2, c_t0, c_t1, c_t2;
 };
 cudaError_t launch_obs(const ObsParams &O, cudaStream_t s);
 cudaError_t launch_g1_snapshot(const ObsParams &O, double *g1ref, cudaStream_t s);
@@ -264,7 +267,7 @@ ecmc_status tune_search(TunePoint start, Trial trial, TunePoint *best, TuneScore
                         int *n_trials) {
   static const int lanes_c[] = {4, 8, 16, 32};
   static const double tile_c[] = {3.4, 4.2, 5.0, 6.0, 7.0};
-  static const double cell_c[] = {1.0, 1.4};
+  static const double cell_c[] = {1.05, 1.4};
   static const int ecs_c[] = {1, 2};
   TunePoint cur = start;
   TuneScore cur_s{};

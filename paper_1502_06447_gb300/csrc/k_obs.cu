@@ -4,7 +4,9 @@
 //   and the ideal-chain law <R^2> = c N sigma^2); bond lengths and tether
 //   violations (b > b_max); hard-sphere overlaps (Eq. 1) from the cell list;
 //   g1, the mean-square displacement of the middle bead N/2 (Eq. for g1 in
-//   Sec. III) against a reference snapshot of unwrapped positions.
+//   Sec. III) against a reference snapshot of unwrapped positions; pair and
+//   bond counts in thin shells at contact (sigma, b_max) for the
+//   contact-value pressure.
 #include <cuda_runtime.h>
 
 #include "ecmc_dev.cuh"
@@ -21,13 +23,14 @@ __device__ __forceinline__ void atomic_min_pos(double *a, double v) {
 }
 
 // out_d: [0] sum R_e^2, [1] max bond, [2] min bond, [3] sum g1
-// out_u: [0] overlaps, [1] tether violations
+// out_u: [0] overlaps, [1] tether violations, [4] [5] bonds in the shells
+// (t1, t0] and (t2, t1] below b_max
 __global__ void k_chains(const ObsParams O) {
   const int64_t ch = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const int64_t nch = O.n / O.N;
   if (ch >= nch) return;
   double R0 = 0.0, R1 = 0.0, R2 = 0.0, bmax = 0.0, bmin = 1e300;
-  unsigned long long viol = 0;
+  unsigned long long viol = 0, tb0 = 0, tb1 = 0;
   const double lim = O.b2 * (1.0 + 1e-10);
   for (int j = 0; j + 1 < O.N; ++j) {
     const int64_t b = ch * O.N + j;
@@ -39,6 +42,8 @@ __global__ void k_chains(const ObsParams O) {
     R2 += d2;
     const double dd = d0 * d0 + d1 * d1 + d2 * d2;
     viol += dd > lim;
+    tb0 += (dd > O.c_t1 && dd <= O.c_t0);
+    tb1 += (dd > O.c_t2 && dd <= O.c_t1);
     const double bl = sqrt(dd);
     bmax = fmax(bmax, bl);
     bmin = fmin(bmin, bl);
@@ -49,6 +54,8 @@ __global__ void k_chains(const ObsParams O) {
     atomic_min_pos(&O.out_d[2], bmin);
   }
   if (viol) atomicAdd(&O.out_u[1], viol);
+  if (tb0) atomicAdd(&O.out_u[4], tb0);
+  if (tb1) atomicAdd(&O.out_u[5], tb1);
   if (O.g1ref) {
     const int64_t b = ch * O.N + O.N / 2;
     double g = 0.0;
@@ -71,8 +78,9 @@ __global__ void k_snapshot(const ObsParams O, double *ref) {
   for (int a = 0; a < 3; ++a) ref[3 * ch + a] = O.r[3 * b + a] + (double)O.img[3 * b + a] * O.L[a];
 }
 
-// pairs i < j closer than sigma (1 - 1e-10)^(1/2), through the cell list
-// (cell side >= sigma, at least 3 cells per axis)
+// pairs i < j closer than sigma (1 - 1e-10)^(1/2), and pairs in the shells
+// [lo, s1) and [s1, s2) above sigma, through the cell list (cell side >=
+// sqrt(s2), at least 3 cells per axis)
 __global__ void k_overlaps(const ObsParams O) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= O.n) return;
@@ -80,7 +88,7 @@ __global__ void k_overlaps(const ObsParams O) {
   const int cx = c % O.nc[0], cy = (c / O.nc[0]) % O.nc[1], cz = c / (O.nc[0] * O.nc[1]);
   const double p0 = O.r[3 * i], p1 = O.r[3 * i + 1], p2 = O.r[3 * i + 2];
   const double lim = O.sig2 * (1.0 - 1e-10);
-  unsigned long long cnt = 0;
+  unsigned long long cnt = 0, cs0 = 0, cs1 = 0;
   for (int dz = -1; dz <= 1; ++dz)
     for (int dy = -1; dy <= 1; ++dy)
       for (int dx = -1; dx <= 1; ++dx) {
@@ -93,10 +101,15 @@ __global__ void k_overlaps(const ObsParams O) {
           const double d0 = wrap_d(p0 - O.cr[3 * (int64_t)j], O.L[0], O.half[0]);
           const double d1 = wrap_d(p1 - O.cr[3 * (int64_t)j + 1], O.L[1], O.half[1]);
           const double d2 = wrap_d(p2 - O.cr[3 * (int64_t)j + 2], O.L[2], O.half[2]);
-          cnt += (d0 * d0 + d1 * d1 + d2 * d2) < lim;
+          const double dd = d0 * d0 + d1 * d1 + d2 * d2;
+          cnt += dd < lim;
+          cs0 += (dd >= O.c_lo && dd < O.c_s1);
+          cs1 += (dd >= O.c_s1 && dd < O.c_s2);
         }
       }
   if (cnt) atomicAdd(&O.out_u[0], cnt);
+  if (cs0) atomicAdd(&O.out_u[2], cs0);
+  if (cs1) atomicAdd(&O.out_u[3], cs1);
 }
 
 __global__ void k_lattice(int n0, int n1, int n2, double a, double jitter, uint64_t seed,

@@ -58,10 +58,15 @@ class Obs(C.Structure):
                 ("bond_max", C.c_double), ("bond_min", C.c_double), ("overlaps", C.c_int64),
                 ("tether_violations", C.c_int64), ("g1", C.c_double),
                 ("device_seconds", C.c_double), ("ec_kernel_seconds", C.c_double),
-                ("confirmed", C.c_int64)]
+                ("confirmed", C.c_int64), ("contact_pairs", C.c_int64 * 2),
+                ("taut_bonds", C.c_int64 * 2), ("contact_delta", C.c_double),
+                ("pressure_contact", C.c_double)]
 
     def as_dict(self):
-        d = {k: getattr(self, k) for k, _ in self._fields_ if k != "events"}
+        d = {k: getattr(self, k) for k, _ in self._fields_
+             if k not in ("events", "contact_pairs", "taut_bonds")}
+        d["contact_pairs"] = tuple(self.contact_pairs)
+        d["taut_bonds"] = tuple(self.taut_bonds)
         for i, name in enumerate(EV_NAMES):
             d[name] = self.events[i]
         return d

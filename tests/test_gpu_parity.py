@@ -247,6 +247,41 @@ def test_observables_match_oracle():
     g1 = ((mid - ref0) ** 2).sum(1).mean()
     assert abs(obs["g1"] - g1) <= 1e-12 * max(g1, 1.0)
     assert abs(obs["disp_sum"] - obs["ecs"] * m.ell) < 1e-9 * obs["ecs"] * m.ell
+    pairs, bonds = o.contacts(obs["contact_delta"])
+    assert obs["contact_delta"] == 0.02
+    assert tuple(obs["contact_pairs"]) == tuple(pairs) and tuple(obs["taut_bonds"]) == tuple(bonds)
+    assert bonds.sum() > 0 and pairs.sum() > 0
+    assert abs(obs["pressure_contact"] - o.contact_pressure(0.02)) <= 1e-12 * abs(obs["pressure_contact"])
+
+
+@pytest.mark.parametrize("lanes", [8, 32])
+def test_contact_pressure_domain_mode_hard_spheres(lanes):
+    """Unbonded hard spheres at phi = 0.30 run in the domain mode: the
+    contact-value pressure of the sampled states matches Carnahan-Starling
+    (within 3 standard errors plus 1.5 % for CS, 1000-sphere finite size and
+    the shell extrapolation), while the lift-distance estimator, which misses
+    the momentum carried by reflections at joint beads and tile walls, comes
+    out far below it."""
+    import math
+    phi = 0.30
+    a = (math.pi / (6 * phi)) ** (1 / 3)
+    ctx = ecmc.Context.create_lattice((10, 10, 10), a, 1, jitter=0.05, seed=12)
+    ctx.configure(mode=ecmc.MODE_DOMAIN, dir_mode=ecmc.DIR_ISO, precision=ecmc.PREC_FP32F,
+                  tiles=(3, 3, 3), lanes=lanes, ecs_per_tile=4)
+    ctx.run(3.0, seed=12, n_sweeps=300)
+    o0 = ctx.observables()
+    zc = []
+    for _ in range(120):
+        ctx.run(3.0, seed=12, n_sweeps=15)
+        zc.append(ctx.observables()["pressure_contact"])
+    o1 = ctx.observables()
+    zc = np.array(zc)
+    zcs = (1 + phi + phi ** 2 - phi ** 3) / (1 - phi) ** 3
+    se = zc.std(ddof=1) / math.sqrt(len(zc))
+    assert abs(zc.mean() - zcs) < 3 * se + 0.015 * zcs, (zc.mean(), se, zcs)
+    z_lift = 1 + (o1["lift_sum"] - o0["lift_sum"]) / (o1["disp_sum"] - o0["disp_sum"])
+    assert z_lift < 0.8 * zcs
+    assert o1["overlaps"] == 0
 
 
 # ------------------------------------------------------------------ checkpoint
