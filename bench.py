@@ -47,7 +47,7 @@ UNIT = "events/s"
 C0 = 1.2  # stencil cell side of the bytes-per-event definition (= b_max)
 # revision of the block-lockstep kernel; DRAM counters in profiles/ are used
 # only when they were taken on the same revision
-KERNEL_REV = 2
+KERNEL_REV = 3
 
 
 def bytes_per_event(phi, confirmed_per_event, fp32f=True):
@@ -161,7 +161,12 @@ def run_gpu(args, rank, world):
                       tiles=TILES, lanes=lanes, ecs_per_tile=args.ecs_per_tile,
                       schedule=args.schedule,
                       block_tiles=args.block_tiles if precision == ecmc.PREC_FP32F else 0)
-        tune = ctx.autotune(ELL, seed=seed, trial_sweeps=2) if args.tune else None
+        # melt the lattice start a little first: trials on the lattice
+        # itself are not representative (its tiles overflow the tight
+        # staging capacities)
+        if args.tune:
+            ctx.run(ELL, seed=seed, n_sweeps=3)
+        tune = ctx.autotune(ELL, seed=seed, trial_sweeps=3) if args.tune else None
         # swap calibration under the final setting: one sweep without swaps,
         # then p_swap for 0.1 attempts / bead / sweep
         ctx.run(ELL, seed=seed, n_sweeps=1)
@@ -172,6 +177,7 @@ def run_gpu(args, rank, world):
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
     for _ in range(args.warmup):
         ctx.run(ELL, seed=seed, n_sweeps=1)
+    ctx.g1_reset()
     o0 = ctx.observables()
     torch.cuda.synchronize()
     if world > 1:
@@ -196,6 +202,17 @@ def run_gpu(args, rank, world):
     ec_s = o1["ec_kernel_seconds"] - o0["ec_kernel_seconds"]
     confirmed = o1["confirmed"] - o0["confirmed"]
     assert o1["overlaps"] == 0 and o1["tether_violations"] == 0
+    tried = o1["swap_tried"] - o0["swap_tried"]
+    physics = {
+        "re2_mean_before": o0["re2_mean"], "re2_mean_after": o1["re2_mean"],
+        "g1_over_timed_steps": o1["g1"], "g1_per_device_second": o1["g1"] / dev_s,
+        "pressure_lift": 1 + (o1["lift_sum"] - o0["lift_sum"]) / (o1["disp_sum"] - o0["disp_sum"]),
+        "pressure_contact": o1["pressure_contact"],
+        "swap_attempts_per_bead_sweep": tried / C5.n / args.steps,
+        "swap_acceptance": (o1["swap"] - o0["swap"]) / tried if tried else None,
+        "overlaps": o1["overlaps"], "tether_violations": o1["tether_violations"],
+        "note": "pressure_lift is the lift-distance estimator (biased in the domain mode); "
+                "pressure_contact the contact-value estimator of the final state"}
 
     # plain FP64 kernel on the same workload (fresh lattice, same calibration)
     ctx64, tune64 = make(ecmc.PREC_FP64)
@@ -290,7 +307,11 @@ def run_gpu(args, rank, world):
         "e2e": {"value": e2e_events / e2e_s, "unit": UNIT,
                 "h2d_bytes_per_step": int(r_host.nbytes + img_host.nbytes),
                 "d2h_bytes_per_step": int(r_host.nbytes + img_host.nbytes)},
-        "gpu_launches": 6 * args.steps,
+        # per sweep: 5 cell-list kernels + the EC launch (two passes for the
+        # block-lockstep kernel: tight capacities, then deferred tiles)
+        "gpu_launches": (7 if args.schedule == 0 and (tune["lanes"] if tune else args.lanes)
+                         in (4, 8, 16) else 6) * args.steps,
+        "physics": physics,
         "clocks": clk.summary(),
         "tuning": {"fp32f": tune, "fp64": tune64},
     }
@@ -323,7 +344,8 @@ def run_batch(args, stream):
     for name, prec, lanes in (("fp32f", ecmc.PREC_FP32F, 8), ("fp64", ecmc.PREC_FP64, 16)):
         b = ecmc.Batch(specs, jitter=jitter, seed=seed)
         b.configure(dir_mode=ecmc.DIR_ISO, precision=prec, lanes=lanes)
-        tune = b.autotune(ell, seed=seed, trial_sweeps=2)
+        b.run(ell, seed=seed, n_sweeps=3, graph=False)  # melt the lattice start first
+        tune = b.autotune(ell, seed=seed, trial_sweeps=3)
         b.run(ell, seed=seed, n_sweeps=max(1, args.warmup), graph=True)
         s0 = b.stats()
         b.run(ell, seed=seed, n_sweeps=ksteps, graph=True)
@@ -348,7 +370,7 @@ def run_batch(args, stream):
         c.configure(mode=ecmc.MODE_DOMAIN, dir_mode=ecmc.DIR_ISO, precision=ecmc.PREC_FP32F,
                     tiles=d, lanes=t["lanes"], cell_side=t["cell_side"],
                     ecs_per_tile=t["ecs_per_tile"])
-        c.run(ell, seed=seed, n_sweeps=1)
+        c.run(ell, seed=seed, n_sweeps=3 + max(1, args.warmup))  # as melted as the batch
         ctxs.append(c)
     nseq = max(1, ksteps // 3)
     o0 = [c.observables()["events_total"] for c in ctxs]

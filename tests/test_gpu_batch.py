@@ -66,7 +66,8 @@ def test_batch_replicas_match_oracle(lanes, prec, schedule, graph):
 
 @pytest.mark.parametrize("schedule", [0, 1])
 def test_batch_swap_matches_oracle(schedule):
-    check_batch(ragged_specs()[:3], 8, ecmc.PREC_FP32F, True, p_swap=0.5, ell=5.0,
+    # the N = 1 replica accepts every swap, the chains almost none
+    check_batch(ragged_specs()[:4], 8, ecmc.PREC_FP32F, True, p_swap=0.5, ell=5.0,
                 schedule=schedule)
 
 

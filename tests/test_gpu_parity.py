@@ -201,9 +201,13 @@ def test_run_split_equals_one_run():
 
 # ------------------------------------------------------------------ swap
 @pytest.mark.parametrize("lanes,schedule", [(32, 0), (8, 0), (8, 1), (4, 0), (1, 0)])
-@pytest.mark.parametrize("p_swap", [0.5, 1.0])
-def test_swap_parity_domain(p_swap, lanes, schedule):
-    m = small_domain(p_swap=p_swap, seed=0xEC00A4, ell=6.0)
+@pytest.mark.parametrize("p_swap,N", [(0.5, 8), (1.0, 8), (1.0, 2), (0.5, 1)])
+def test_swap_parity_domain(p_swap, N, lanes, schedule):
+    """Swaps in the domain mode.  In the 8-bead chains every proposal is
+    rejected (exchanging two touching beads over-stretches a tether), so
+    dimers (about one in six accepted) and free spheres (all accepted) carry
+    the accept branch."""
+    m = small_domain(N=N, p_swap=p_swap, seed=0xEC00A4, ell=6.0)
     o = oracle_system(m)
     res = o.run_domain(3, m.ell, digests=True)
     ctx = gpu_context(m, lanes=lanes, precision=ecmc.PREC_FP32F, schedule=schedule)
