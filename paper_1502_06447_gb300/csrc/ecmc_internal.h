@@ -245,7 +245,8 @@ inline void tight_caps(const double E[3], const double Wm[3], double rho, int32_
 // ---------------------------------------------------------------- autotuner
 // One launch setting of the domain sweep.  The search is a coordinate
 // descent: lanes per EC, then tile side, then global cell side, then ECs per
-// tile, each axis scanned with the others held at their best so far.  The
+// tile, each axis scanned with the others held at their best so far, in up
+// to two rounds.  The
 // objective is ECs per device-second (each EC displaces by ell, so this is
 // the rate of progress of the Markov chain; events/s would reward small
 // tiles for their extra wall reflections).
@@ -273,7 +274,16 @@ ecmc_status tune_search(TunePoint start, Trial trial, TunePoint *best, TuneScore
   TuneScore cur_s{};
   bool have = false;
   int n = 0;
+  // points already timed (a second round revisits none of them)
+  constexpr int VMAX = 64;
+  TunePoint seen[VMAX];
+  int nseen = 0;
   auto consider = [&](const TunePoint &pt) -> ecmc_status {
+    for (int i = 0; i < nseen; ++i)
+      if (seen[i].lanes == pt.lanes && seen[i].tile_side == pt.tile_side &&
+          seen[i].cell_side == pt.cell_side && seen[i].ecs == pt.ecs)
+        return ECMC_OK;
+    if (nseen < VMAX) seen[nseen++] = pt;
     TuneScore sc{};
     const ecmc_status st = trial(pt, &sc);
     if (st == ECMC_EINVAL) return ECMC_OK;
@@ -288,21 +298,26 @@ ecmc_status tune_search(TunePoint start, Trial trial, TunePoint *best, TuneScore
   };
   ecmc_status st = consider(start);
   if (st != ECMC_OK) return st;
-  for (int axis = 0; axis < 4; ++axis) {
-    const TunePoint base = cur;
-    const int cnt = axis == 0 ? 4 : axis == 1 ? 5 : 2;
-    for (int i = 0; i < cnt; ++i) {
-      TunePoint pt = base;
-      if (axis == 0) pt.lanes = lanes_c[i];
-      if (axis == 1) pt.tile_side = tile_c[i];
-      if (axis == 2) pt.cell_side = cell_c[i];
-      if (axis == 3) pt.ecs = ecs_c[i];
-      if (pt.lanes == base.lanes && pt.tile_side == base.tile_side &&
-          pt.cell_side == base.cell_side && pt.ecs == base.ecs)
-        continue;
-      st = consider(pt);
-      if (st != ECMC_OK) return st;
+  // two rounds over the four axes: a later axis can change the best choice
+  // on an earlier one (a round that changes nothing ends the search)
+  for (int round = 0; round < 2; ++round) {
+    const TunePoint before = cur;
+    for (int axis = 0; axis < 4; ++axis) {
+      const TunePoint base = cur;
+      const int cnt = axis == 0 ? 4 : axis == 1 ? 5 : 2;
+      for (int i = 0; i < cnt; ++i) {
+        TunePoint pt = base;
+        if (axis == 0) pt.lanes = lanes_c[i];
+        if (axis == 1) pt.tile_side = tile_c[i];
+        if (axis == 2) pt.cell_side = cell_c[i];
+        if (axis == 3) pt.ecs = ecs_c[i];
+        st = consider(pt);
+        if (st != ECMC_OK) return st;
+      }
     }
+    if (round == 0 && before.lanes == cur.lanes && before.tile_side == cur.tile_side &&
+        before.cell_side == cur.cell_side && before.ecs == cur.ecs)
+      break;
   }
   if (!have) return ECMC_EINVAL;
   *best = cur;
