@@ -62,6 +62,24 @@ def bytes_per_event(phi, confirmed_per_event, fp32f=True):
     return 24.0 * nbar + 216.0 + 72.0 + 24.0
 
 
+def reduce_over_ranks(sums, maxes, device):
+    """Whole-job aggregates of a replicas run: `sums` added over the ranks
+    (events), `maxes` maxed (times).  Returns two lists of floats."""
+    import torch
+    import torch.distributed as dist
+    ts = torch.tensor([float(x) for x in sums], dtype=torch.float64, device=device)
+    tm = torch.tensor([float(x) for x in maxes], dtype=torch.float64, device=device)
+    dist.all_reduce(ts, op=dist.ReduceOp.SUM)
+    dist.all_reduce(tm, op=dist.ReduceOp.MAX)
+    return ts.tolist(), tm.tolist()
+
+
+def rank_seed(base, rank):
+    """Each rank advances its own replica: the Philox key's seed word is
+    offset by the rank."""
+    return int(base) + int(rank)
+
+
 def measured_traffic(kernel):
     """DRAM bytes per launch of `kernel` on this workload from the committed
     ncu summary, or None when the summary is for another kernel."""
@@ -150,7 +168,7 @@ def run_gpu(args, rank, world):
     torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", 0)))
     dev = torch.device("cuda")
     stream = torch.cuda.current_stream()
-    seed = C5.seed + rank  # replicas: independent seeds
+    seed = rank_seed(C5.seed, rank)  # replicas: independent seeds
 
     def make(precision):
         ctx = ecmc.Context.create_lattice(C5.dims, C5.spacing, C5.N, sigma=C5.sigma,
@@ -248,14 +266,12 @@ def run_gpu(args, rank, world):
 
     # aggregate over ranks (replicas; max time, summed events)
     tot_events, max_dev, max_wall = float(events), dev_s, wall
+    e2e_tot, e2e_max = float(e2e_events), e2e_s
     if world > 1:
-        t = torch.tensor([float(events), dev_s, wall, float(e2e_events), e2e_s], device=dev,
-                         dtype=torch.float64)
-        s = t.clone()
-        torch.distributed.all_reduce(s[:1], op=torch.distributed.ReduceOp.SUM)
-        torch.distributed.all_reduce(t[1:3], op=torch.distributed.ReduceOp.MAX)
-        tot_events, max_dev, max_wall = float(s[0]), float(t[1]), float(t[2])
-    batched = run_batch(args, stream) if args.batch else None
+        (tot_events, e2e_tot), (max_dev, max_wall, e2e_max) = reduce_over_ranks(
+            [events, e2e_events], [dev_s, wall, e2e_s], dev)
+    # the batched form is a single-GPU measurement: rank 0 alone runs it
+    batched = run_batch(args, stream) if args.batch and rank == 0 else None
     if rank != 0:
         return None
     hbm, peak_src = load_peaks()
@@ -304,7 +320,7 @@ def run_gpu(args, rank, world):
                                 f"ec_kernel<{tune['lanes'] if tune else args.lanes}, 1, 0>"),
                      "bytes_per_event": bpe,
                      "kernel_share_of_step": ec_s / dev_s, "peak_source": peak_src},
-        "e2e": {"value": e2e_events / e2e_s, "unit": UNIT,
+        "e2e": {"value": e2e_tot / e2e_max, "unit": UNIT,
                 "h2d_bytes_per_step": int(r_host.nbytes + img_host.nbytes),
                 "d2h_bytes_per_step": int(r_host.nbytes + img_host.nbytes)},
         # per sweep: 5 cell-list kernels + the EC launch (two passes for the
