@@ -292,7 +292,7 @@ ecmc_status ecmc_batch_records(ecmc_batch *b, uint64_t *digest, double *lift,
  * Picks the launch setting of the domain sweep for this machine and system
  * (the paper fixes none: Sec. II.B leaves the tile size open): lanes per EC
  * (4, 8, 16, 32), tile side (3.4 ... 7 sigma), global cell side (1.05 or 1.4
- * sigma) and ECs per tile (1 or 2), by a coordinate descent (up to two
+ * sigma) and ECs per tile (1, 2 or 4), by a coordinate descent (up to two
  * rounds) over short timed trials.  Each trial restores the state saved on entry, runs one untimed
  * sweep and `trial_sweeps` timed ones; the score is ECs per device-second.
  * On return the context (batch) is configured with the winner and its

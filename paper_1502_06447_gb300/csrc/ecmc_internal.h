@@ -269,7 +269,7 @@ ecmc_status tune_search(TunePoint start, Trial trial, TunePoint *best, TuneScore
   static const int lanes_c[] = {4, 8, 16, 32};
   static const double tile_c[] = {3.4, 4.2, 5.0, 6.0, 7.0};
   static const double cell_c[] = {1.05, 1.4};
-  static const int ecs_c[] = {1, 2};
+  static const int ecs_c[] = {1, 2, 4};
   TunePoint cur = start;
   TuneScore cur_s{};
   bool have = false;
@@ -304,7 +304,7 @@ ecmc_status tune_search(TunePoint start, Trial trial, TunePoint *best, TuneScore
     const TunePoint before = cur;
     for (int axis = 0; axis < 4; ++axis) {
       const TunePoint base = cur;
-      const int cnt = axis == 0 ? 4 : axis == 1 ? 5 : 2;
+      const int cnt = axis == 0 ? 4 : axis == 1 ? 5 : axis == 2 ? 2 : 3;
       for (int i = 0; i < cnt; ++i) {
         TunePoint pt = base;
         if (axis == 0) pt.lanes = lanes_c[i];
