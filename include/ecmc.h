@@ -184,9 +184,11 @@ const char *ecmc_last_error(void);
 ecmc_status ecmc_set_stream(ecmc_ctx *ctx, void *stream);
 
 /* ---- state --------------------------------------------------------------
- * xyz: host, 3n doubles (caller-owned).  set: wraps into [0,L), resets the
- * image counters to 0 unless img is given (3n int32, may be NULL), checks
- * overlaps and tethers. */
+ * xyz: host, 3n doubles (caller-owned; pinned memory is copied fastest).
+ * set: wraps into [0,L) on the device, adding whole boxes to the image
+ * counters (which start from img, 3n int32, or 0 when img is NULL), then
+ * checks non-finite coordinates (ECMC_EINVAL), overlaps and tethers; after
+ * a failed set the context's state is undefined until a successful one. */
 ecmc_status ecmc_set_positions(ecmc_ctx *ctx, const double *xyz,
                                const int32_t *img);
 ecmc_status ecmc_get_positions(ecmc_ctx *ctx, double *xyz_out,

@@ -274,7 +274,7 @@ ecmc_status alloc_state(ecmc_ctx *c) {
   CU(dalloc(&c->d_unit_next, 1));
   CU(dalloc(&c->d_n_deferred, 1));
   CU(dalloc(&c->d_obs_d, 4));
-  CU(dalloc(&c->d_obs_u, 6));
+  CU(dalloc(&c->d_obs_u, 8));  // [6]: non-finite inputs of set_positions
   CU(dalloc(&c->d_g1ref, 3 * (c->n / c->N)));
   CU(cudaStreamCreateWithFlags(&c->own, cudaStreamNonBlocking));
   c->stream = c->own;
@@ -431,22 +431,20 @@ ecmc_status ecmc_get_info(ecmc_ctx *c, double box[3], int64_t *n_beads, int32_t 
 
 ecmc_status ecmc_set_positions(ecmc_ctx *c, const double *xyz, const int32_t *img) {
   if (!c || !xyz) return fail(ECMC_EINVAL, "NULL argument");
-  std::vector<double> r(3 * c->n);
-  std::vector<int32_t> im(3 * c->n, 0);
-  for (int64_t b = 0; b < c->n; ++b)
-    for (int a = 0; a < 3; ++a) {
-      double x = xyz[3 * b + a];
-      if (!isfinite(x)) return fail(ECMC_EINVAL, "non-finite position");
-      const double f = floor(x / c->L[a]);
-      x -= f * c->L[a];
-      if (x >= c->L[a]) x -= c->L[a];
-      if (x < 0) x = 0;
-      r[3 * b + a] = x;
-      im[3 * b + a] = (img ? img[3 * b + a] : 0) + (int32_t)f;
-    }
-  CU(cudaMemcpyAsync(c->d_r, r.data(), sizeof(double) * r.size(), cudaMemcpyHostToDevice, c->stream));
-  CU(cudaMemcpyAsync(c->d_img, im.data(), sizeof(int32_t) * im.size(), cudaMemcpyHostToDevice, c->stream));
+  // copied as given (straight from pinned memory when the caller's buffers
+  // are pinned), then wrapped and checked on the device
+  CU(cudaMemcpyAsync(c->d_r, xyz, sizeof(double) * 3 * c->n, cudaMemcpyHostToDevice, c->stream));
+  if (img)
+    CU(cudaMemcpyAsync(c->d_img, img, sizeof(int32_t) * 3 * c->n, cudaMemcpyHostToDevice, c->stream));
+  else
+    CU(cudaMemsetAsync(c->d_img, 0, sizeof(int32_t) * 3 * c->n, c->stream));
+  CU(cudaMemsetAsync(c->d_obs_u + 6, 0, sizeof(unsigned long long), c->stream));
+  CU(launch_wrap(c->d_r, c->d_img, c->n, c->L, c->d_obs_u + 6, c->stream));
+  unsigned long long bad = 0;
+  CU(cudaMemcpyAsync(&bad, c->d_obs_u + 6, sizeof(bad), cudaMemcpyDeviceToHost, c->stream));
+  CU(cudaStreamSynchronize(c->stream));
   c->g1_set = false;
+  if (bad) return fail(ECMC_EINVAL, "%llu non-finite coordinates", bad);
   return check_state(c);
 }
 

@@ -203,6 +203,9 @@ struct ObsParams {
   double c_lo, c_s1, c_s2, c_t0, c_t1, c_t2;
 };
 cudaError_t launch_obs(const ObsParams &O, cudaStream_t s);
+// positions copied in as given: wrap into [0, L), fold boxes into img
+cudaError_t launch_wrap(double *r, int32_t *img, int64_t n, const double L[3],
+                        unsigned long long *bad, cudaStream_t s);
 cudaError_t launch_g1_snapshot(const ObsParams &O, double *g1ref, cudaStream_t s);
 cudaError_t launch_lattice(const int32_t dims[3], double a, double jitter,
                            uint64_t seed, uint64_t replica, double *r, int64_t n,

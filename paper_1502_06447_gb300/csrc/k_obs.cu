@@ -135,7 +135,36 @@ __global__ void k_lattice(int n0, int n1, int n2, double a, double jitter, uint6
   }
 }
 
+// wrap caller positions into [0, L) and fold whole boxes into the image
+// counters (the host-side rule, same FP64 operations); counts non-finite
+// coordinates
+__global__ void k_wrap(double *r, int32_t *img, int64_t n3, double L0, double L1, double L2,
+                       unsigned long long *bad) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n3) return;
+  const int a = (int)(i % 3);
+  const double L = a == 0 ? L0 : (a == 1 ? L1 : L2);
+  double x = r[i];
+  if (!isfinite(x)) {
+    atomicAdd(bad, 1ull);
+    return;
+  }
+  const double f = floor(x / L);
+  x -= f * L;
+  if (x >= L) x -= L;
+  if (x < 0) x = 0;
+  r[i] = x;
+  img[i] += (int32_t)f;
+}
+
 }  // namespace
+
+cudaError_t launch_wrap(double *r, int32_t *img, int64_t n, const double L[3],
+                        unsigned long long *bad, cudaStream_t s) {
+  const int64_t n3 = 3 * n;
+  if (n3 > 0) k_wrap<<<(unsigned)((n3 + 255) / 256), 256, 0, s>>>(r, img, n3, L[0], L[1], L[2], bad);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_obs(const ObsParams &O, cudaStream_t s) {
   const int64_t nch = O.n / O.N;

@@ -243,9 +243,19 @@ class Context:
         _check(load().ecmc_set_positions(self._h, _p(r, C.c_double),
                                           None if im is None else _p(im, C.c_int32)))
 
-    def get_positions(self):
-        r = np.zeros((self.n, 3))
-        img = np.zeros((self.n, 3), dtype=np.int32)
+    def get_positions(self, out=None):
+        """Positions (n, 3) float64 and image counters (n, 3) int32.  `out`
+        = (r, img) writes into caller-owned C-contiguous arrays instead (for
+        instance pinned host memory, which the copy reaches fastest)."""
+        if out is None:
+            r = np.zeros((self.n, 3))
+            img = np.zeros((self.n, 3), dtype=np.int32)
+        else:
+            r, img = out
+            if not (r.dtype == np.float64 and img.dtype == np.int32 and r.shape == (self.n, 3)
+                    and img.shape == (self.n, 3) and r.flags.c_contiguous
+                    and img.flags.c_contiguous):
+                raise ValueError("out must be C-contiguous float64 / int32 arrays of shape (n, 3)")
         _check(load().ecmc_get_positions(self._h, _p(r, C.c_double), _p(img, C.c_int32)))
         return r, img
 

@@ -327,6 +327,23 @@ def test_invalid_arguments_and_states():
     with pytest.raises(ecmc.EcmcError) as e:
         ctx.set_positions(bad)
     assert e.value.code in (-4, -5)
+    bad = r.copy()
+    bad[3, 1] = np.nan
+    with pytest.raises(ecmc.EcmcError) as e:
+        ctx.set_positions(bad)
+    assert e.value.code == -1
+    # positions given outside the box come back wrapped, whole boxes in the
+    # image counters (which start from the given ones)
+    L = ctx.L
+    shift = np.array([1, -2, 3])
+    img0 = np.tile(np.array([5, 0, -1], dtype=np.int32), (len(r), 1))
+    ctx.set_positions(r + shift * L, img0)
+    r2, img2 = ctx.get_positions()
+    assert np.abs(r2 - r).max() < 1e-9 * L.max()
+    assert (img2 == img0 + shift).all()
+    out = (np.empty_like(r2), np.empty_like(img2))
+    got = ctx.get_positions(out=out)
+    assert got[0] is out[0] and (out[0] == r2).all() and (out[1] == img2).all()
     with pytest.raises(ecmc.EcmcError) as e:
         ctx.configure(mode=ecmc.MODE_DOMAIN, tiles=(2, 3, 3))
     assert e.value.code == -1
