@@ -60,7 +60,8 @@ C2 = Melt("c2_domain_262k", (64, 64, 64), 1.05, 64, ell=10.0, seed=0xEC0002,
           mode="domain", dir_mode="iso", sweeps=100, D=(16, 16, 16))
 # C3: 2000 x 256 on 80^3, a=1.0156, domain, ell=10
 C3 = Melt("c3_fp32f_512k", (80, 80, 80), 1.0156, 256, ell=10.0, seed=0xEC0003,
-          mode="domain", dir_mode="iso", sweeps=20, D=(16, 16, 16))
+          mode="domain", dir_mode="iso", sweeps=20, D=(16, 16, 16),
+          jitter=0.005)  # spacing 1.0156 leaves 0.0156 sigma between neighbours
 # C5: 1000 x 1000 on 100^3, a=1.05, domain + swap, ell=20
 C5 = Melt("c5_swap_1m", (100, 100, 100), 1.05, 1000, ell=20.0, seed=0xEC0005,
           mode="domain", dir_mode="iso", sweeps=10, D=(20, 20, 20))
