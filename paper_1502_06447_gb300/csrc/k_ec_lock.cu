@@ -58,6 +58,8 @@ struct Res {
 };
 
 constexpr int RQ_PER_TILE = 6;   // request list capacity per tile of the block
+// phase A gathers a tile's screening list into its share of the result area
+constexpr int FLAT_CAP = RQ_PER_TILE * (int)sizeof(Res) / 2;
 // a lane holds at most four requests per step (pq0..pq3); more send the
 // tile to the exhaustive evaluation
 
@@ -433,33 +435,75 @@ __global__ void __launch_bounds__(128, 3) ec_lock_kernel(const ECParams P) {
           sps[r] = a;
         }
       }
+      // gather the slots of the 27 local cells around the pivot and of the
+      // overflow list into one list (in the group's share of the result
+      // area, which phase B fills only after this phase), then screen it G
+      // lanes wide, two slots per lane and round
+      unsigned short *fl = reinterpret_cast<unsigned short *>(rs) + gib * FLAT_CAP;
       int pc0 = 0, pc1 = 0, pc2 = 0;
       lcell(LG, a0, a1, a2, pc0, pc1, pc2);
-      const int n_ovf = st.hdr[4];
+      const int n_ovf = act ? st.hdr[4] : 0;
+      constexpr int CPL = (27 + G - 1) / G;  // cells per lane
+      int cw[CPL];  // cell index << 3 | bead count
+      int cnt_l = 0;
+#pragma unroll
+      for (int j = 0; j < CPL; ++j) {
+        const int ci = gl + j * G;
+        cw[j] = 0;
+        if (!act || ci >= 27) continue;
+        const int x = pc0 + ci % 3 - 1, y = pc1 + (ci / 3) % 3 - 1, z = pc2 + ci / 9 - 1;
+        if (x < 0 || y < 0 || z < 0 || x >= LG.g0 || y >= LG.g1 || z >= LG.g2) continue;
+        const int c = (z * LG.g1 + y) * LG.g0 + x;
+        const int n = cell_n(st.cell + 8 * c);
+        cw[j] = (c << 3) | n;
+        cnt_l += n;
+      }
+      int cincl = cnt_l;
+#pragma unroll
+      for (int off = 1; off < G; off <<= 1) {
+        const int y = __shfl_up_sync(FULL, cincl, off, G);
+        if (gl >= off) cincl += y;
+      }
+      const int ncell = __shfl_sync(FULL, cincl, G - 1, G);
+      const int nfl = ncell + n_ovf;
+      const bool fl_full = nfl > FLAT_CAP;  // the tile is evaluated exhaustively
+      if (!fl_full) {
+        int at = cincl - cnt_l;
+#pragma unroll
+        for (int j = 0; j < CPL; ++j) {
+          const int n = cw[j] & 7;
+          if (n == 0) continue;
+          const uint4 c = *reinterpret_cast<const uint4 *>(st.cell + 8 * (cw[j] >> 3));
+          const unsigned short sl[6] = {(unsigned short)(c.y & 0xFFFF), (unsigned short)(c.y >> 16),
+                                        (unsigned short)(c.z & 0xFFFF), (unsigned short)(c.z >> 16),
+                                        (unsigned short)(c.w & 0xFFFF), (unsigned short)(c.w >> 16)};
+#pragma unroll
+          for (int i = 0; i < 6; ++i)
+            if (i < n) fl[at + i] = sl[i];
+          at += n;
+        }
+        for (int i = gl; i < n_ovf; i += G) fl[ncell + i] = st.ovf[i];
+      }
+      __syncwarp();
+      const int nscr = fl_full ? 0 : nfl;
       int ks0 = -1, ks1 = -1;
       float kl0 = INF, kl1 = INF;
       bool kovf = false;
-      for (int ci = gl; ci < 28; ci += G) {
-        if (!act) break;
-        if (ci == 27) {
-          for (int i = 0; i < n_ovf; ++i) {
-            const int k = st.ovf[i];
-            if (k == a_p) continue;
-            screen_hs(Z, a0 - st.fx[k], a1 - st.fy[k], a2 - st.fz[k], w0, w1, w2, k, ubl, ks0, kl0,
-                      ks1, kl1, kovf);
-          }
-        } else {
-          const int x = pc0 + ci % 3 - 1, y = pc1 + (ci / 3) % 3 - 1, z = pc2 + ci / 9 - 1;
-          if (x < 0 || y < 0 || z < 0 || x >= LG.g0 || y >= LG.g1 || z >= LG.g2) continue;
-          screen_cell(Z, st, st.cell + 8 * ((z * LG.g1 + y) * LG.g0 + x), a_p, a0, a1, a2, w0, w1, w2,
-                      ubl, ks0, kl0, ks1, kl1, kovf);
-        }
+      for (int j = gl; j < nscr; j += 2 * G) {
+        const int ka = fl[j];
+        const bool two = j + G < nscr;
+        const int kb = two ? fl[j + G] : ka;
+        const float ax = st.fx[ka], ay = st.fy[ka], az = st.fz[ka];
+        const float bx = st.fx[kb], by = st.fy[kb], bz = st.fz[kb];
+        if (ka != a_p) screen_hs(Z, a0 - ax, a1 - ay, a2 - az, w0, w1, w2, ka, ubl, ks0, kl0, ks1, kl1, kovf);
+        if (two && kb != a_p)
+          screen_hs(Z, a0 - bx, a1 - by, a2 - bz, w0, w1, w2, kb, ubl, ks0, kl0, ks1, kl1, kovf);
       }
       const float U = group_minf<G>(ubl);
       // survivors of this lane (kind << 28 | slot)
       int pq0 = 0, pq1 = 0, pq2 = 0, pq3 = 0;
       int npush = 0;
-      bool over = false;
+      bool over = act && fl_full;
       auto push = [&](int code) {
         if (npush == 0) pq0 = code;
         else if (npush == 1) pq1 = code;
@@ -474,29 +518,15 @@ __global__ void __launch_bounds__(128, 3) ec_lock_kernel(const ECParams P) {
       if (ks0 >= 0 && kl0 <= U) push((KIND_HS << 28) | ks0);
       if (ks1 >= 0 && kl1 <= U) push((KIND_HS << 28) | ks1);
       if (act && kovf) {
-        // more than two possible winners in this lane: screen its cells again
+        // more than two possible winners in this lane: screen its slots again
         // against the group's U and keep every one that can reach it
-        for (int ci = gl; ci < 28; ci += G) {
-          int n;
-          const unsigned short *lst;
-          if (ci == 27) {
-            n = n_ovf;
-            lst = st.ovf;
-          } else {
-            const int x = pc0 + ci % 3 - 1, y = pc1 + (ci / 3) % 3 - 1, z = pc2 + ci / 9 - 1;
-            if (x < 0 || y < 0 || z < 0 || x >= LG.g0 || y >= LG.g1 || z >= LG.g2) continue;
-            const unsigned short *c = st.cell + 8 * ((z * LG.g1 + y) * LG.g0 + x);
-            n = cell_n(c);
-            lst = c + 2;
-          }
-          for (int i = 0; i < n; ++i) {
-            const int k = lst[i];
-            if (k == a_p || k == ks0 || k == ks1) continue;
-            bool possible;
-            const float lb = screen_lb(Z, a0 - st.fx[k], a1 - st.fy[k], a2 - st.fz[k], w0, w1, w2,
-                                       possible);
-            if (possible && lb <= U) push((KIND_HS << 28) | k);
-          }
+        for (int j = gl; j < nscr; j += G) {
+          const int k = fl[j];
+          if (k == a_p || k == ks0 || k == ks1) continue;
+          bool possible;
+          const float lb = screen_lb(Z, a0 - st.fx[k], a1 - st.fy[k], a2 - st.fz[k], w0, w1, w2,
+                                     possible);
+          if (possible && lb <= U) push((KIND_HS << 28) | k);
         }
       }
       // reserve the group's slots in the request list
