@@ -219,6 +219,7 @@ def run_gpu(args, rank, world):
     dev_s = sum(step_ms) / 1e3
     ec_s = o1["ec_kernel_seconds"] - o0["ec_kernel_seconds"]
     confirmed = o1["confirmed"] - o0["confirmed"]
+    exhaustive = o1["exhaustive"] - o0["exhaustive"]
     assert o1["overlaps"] == 0 and o1["tether_violations"] == 0
     tried = o1["swap_tried"] - o0["swap_tried"]
     physics = {
@@ -310,6 +311,7 @@ def run_gpu(args, rank, world):
         "fp64_events_per_s": fp64_eps,
         "fp32f_over_fp64": value / fp64_eps / world,
         "confirmed_per_event": confirmed / max(events, 1),
+        "exhaustive_per_event": exhaustive / max(events, 1),
         "events_per_ec": events / max(ecs, 1),
         "wall_s": max_wall,
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",

@@ -103,6 +103,13 @@ typedef struct ecmc_opts {
                             its own tile's FP64 work.  Same events either way. */
   int32_t block_tiles;   /* block lockstep: tiles per block (a multiple of
                             32 / lanes, at most 32); 0 -> most tiles per SM */
+  int32_t request_cap;   /* block lockstep: FP64 requests per tile and step in
+                            the block's request list, 1..6; 0 -> 6.  A tile
+                            whose FP32 survivors (or whose list of 24 x cap
+                            screened slots) do not fit is evaluated
+                            exhaustively in FP64 by its own lanes: same
+                            events, slower; small caps exist to exercise that
+                            path (ecmc_obs.exhaustive counts it). */
 } ecmc_opts;
 
 /* Observables and counters (Sec. III observables; see ecmc_observables). */
@@ -139,6 +146,8 @@ typedef struct ecmc_obs {
                                   f, f_b pairs / bonds per unit distance at
                                   contact, each extrapolated linearly from its
                                   two shells */
+  int64_t exhaustive;          /* tile steps of the block-lockstep kernel
+                                  evaluated exhaustively in FP64 */
 } ecmc_obs;
 
 /* One EC event of the parity log (ecmc_event_log). */

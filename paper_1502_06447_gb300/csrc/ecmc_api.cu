@@ -477,6 +477,7 @@ ecmc_status ecmc_configure(ecmc_ctx *c, const ecmc_opts *o) {
   if (p.block_tiles < 0 || p.block_tiles > 32 || p.block_tiles * lanes > 128 ||
       (p.block_tiles > 0 && lanes > 1 && p.block_tiles % (32 / lanes) != 0))
     return fail(ECMC_EINVAL, "block_tiles must be a multiple of 32 / lanes, at most 32 and 128 / lanes");
+  if (p.request_cap < 0 || p.request_cap > 6) return fail(ECMC_EINVAL, "request_cap must be in [0, 6]");
   const double margin = p.precision == ECMC_PREC_FP32F ? 0.01 * sig : 0.0;
   for (int a = 0; a < 3; ++a)
     if (!(s_cap + sig + margin < 0.5 * c->L[a])) return fail(ECMC_EINVAL, "need s_cap + sigma < L/2");
@@ -643,6 +644,7 @@ static cudaError_t timed_ec(ecmc_ctx *c, const ECParams &P, int64_t slot) {
 static ECParams ec_params(const ecmc_ctx *c, uint64_t seed, double ell) {
   ECParams P{};
   P.block_tiles = c->opts.block_tiles;
+  P.rq_per_tile = c->opts.request_cap > 0 ? c->opts.request_cap : 6;
   P.unit_next = c->d_unit_next;
   P.stage_tight = c->stage_tight;
   P.m_tight = c->m_tight;
@@ -840,6 +842,7 @@ ecmc_status ecmc_observables(ecmc_ctx *c, ecmc_obs *out) {
   out->device_seconds = c->device_seconds;
   out->ec_kernel_seconds = c->ec_seconds;
   out->confirmed = (int64_t)h[CNT_CONFIRMED];
+  out->exhaustive = (int64_t)h[CNT_EXHAUSTIVE];
   const double d = CONTACT_DELTA * c->sigma;
   for (int k = 0; k < 2; ++k) {
     out->contact_pairs[k] = (int64_t)o.pairs[k];
@@ -945,7 +948,7 @@ ecmc_status ecmc_checkpoint(ecmc_ctx *c, const char *path) {
   CkptHeader hd;
   memset(&hd, 0, sizeof(hd));
   hd.magic = CKPT_MAGIC;
-  hd.version = 1;
+  hd.version = 2;
   hd.n = c->n;
   hd.N = c->N;
   for (int a = 0; a < 3; ++a) hd.L[a] = c->L[a];
@@ -987,7 +990,7 @@ ecmc_status ecmc_restore(ecmc_ctx *c, const char *path) {
   std::vector<int32_t> im(3 * c->n);
   uint64_t hfile = 0;
   bool ok = fread(&hd, sizeof(hd), 1, f) == 1;
-  ok = ok && hd.magic == CKPT_MAGIC && hd.version == 1 && hd.n == c->n && hd.N == c->N;
+  ok = ok && hd.magic == CKPT_MAGIC && hd.version == 2 && hd.n == c->n && hd.N == c->N;
   ok = ok && fread(r.data(), sizeof(double), r.size(), f) == r.size() &&
        fread(im.data(), sizeof(int32_t), im.size(), f) == im.size() &&
        fread(&hfile, sizeof(hfile), 1, f) == 1;

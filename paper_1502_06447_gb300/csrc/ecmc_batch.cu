@@ -186,6 +186,7 @@ ECParams batch_params(ecmc_batch *b, uint64_t seed, double ell) {
   P.ncl_max = b->ncl_max;
   P.sweep_dev = b->d_sweep;
   P.block_tiles = b->opts.block_tiles;
+  P.rq_per_tile = b->opts.request_cap > 0 ? b->opts.request_cap : 6;
   P.unit_next = b->d_unit_next;
   P.stage_tight = b->stage_tight;
   P.m_tight = b->m_tight;
@@ -380,6 +381,7 @@ ecmc_status ecmc_batch_configure(ecmc_batch *b, const ecmc_opts *o) {
   if (p.block_tiles < 0 || p.block_tiles > 32 || p.block_tiles * lanes > 128 ||
       (p.block_tiles > 0 && p.block_tiles % (32 / lanes)))
     return bfail(ECMC_EINVAL, "block_tiles must be a multiple of 32 / lanes, at most 32 and 128 / lanes");
+  if (p.request_cap < 0 || p.request_cap > 6) return bfail(ECMC_EINVAL, "request_cap must be in [0, 6]");
   const bool lock = p.precision == ECMC_PREC_FP32F && p.schedule == 0 && lanes <= 16;
   const int bt = p.block_tiles > 0 ? p.block_tiles : 32 / lanes;
   const size_t need = lock ? lock_smem_bytes(stage, M, nclm, bt) : ec_smem_bytes(stage, M, nclm, 32 / lanes);

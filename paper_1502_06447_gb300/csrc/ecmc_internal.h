@@ -17,7 +17,8 @@ enum : int {
   CNT_SWAP_TRIED = ECMC_NEV + 1,
   CNT_ECS = ECMC_NEV + 2,
   CNT_CONFIRMED = ECMC_NEV + 3,
-  CNT_N = ECMC_NEV + 4
+  CNT_EXHAUSTIVE = ECMC_NEV + 4,
+  CNT_N = ECMC_NEV + 5
 };
 enum : int { SUM_LIFT = 0, SUM_REFL = 1, SUM_DISP = 2, SUM_N = 3 };
 
@@ -106,6 +107,7 @@ struct ECParams {
   // device counter its persistent blocks take units from (reset per launch)
   int32_t block_tiles;
   int32_t *unit_next;
+  int32_t rq_per_tile;  // request list entries per tile of the block (1..6)
   // block-lockstep kernel: tight capacities for a first pass (0: none); a
   // tile that does not fit them is listed in `deferred` and run by a second
   // pass with stage_cap / m_cap (tiles are independent, so the events are

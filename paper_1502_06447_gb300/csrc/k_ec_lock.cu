@@ -103,7 +103,8 @@ __global__ void __launch_bounds__(128, 3) ec_lock_kernel(const ECParams P) {
   int2 *rq = (int2 *)(tr + NT);
   Res *rs = (Res *)(rq + NT * RQ_PER_TILE);
   int *rq_n = (int *)(rs + NT * RQ_PER_TILE);
-  const int RQ_CAP = NT * RQ_PER_TILE;
+  const int RQ_CAP = NT * P.rq_per_tile;  // at most NT * RQ_PER_TILE
+  const int fl_cap = P.rq_per_tile * (FLAT_CAP / RQ_PER_TILE);
 
   // ------------------------------------------------------------ tile slots
   // The block keeps NT tile slots busy: a slot whose tile has run its ECs is
@@ -260,6 +261,7 @@ __global__ void __launch_bounds__(128, 3) ec_lock_kernel(const ECParams P) {
 #pragma unroll
   for (int k = 0; k < ECMC_NEV; ++k) cnt[k] = 0;
   unsigned long long tried = 0, confirmed = 0, nev_all = 0, ecs_done = 0;
+  unsigned exh = 0;  // exhaustive evaluations led by this lane
 
   // start EC e of the owned tile: start bead and direction (Sec. II, R6)
   auto start_ec = [&]() {
@@ -466,7 +468,7 @@ __global__ void __launch_bounds__(128, 3) ec_lock_kernel(const ECParams P) {
       }
       const int ncell = __shfl_sync(FULL, cincl, G - 1, G);
       const int nfl = ncell + n_ovf;
-      const bool fl_full = nfl > FLAT_CAP;  // the tile is evaluated exhaustively
+      const bool fl_full = nfl > fl_cap;  // the tile is evaluated exhaustively
       if (!fl_full) {
         int at = cincl - cnt_l;
 #pragma unroll
@@ -620,6 +622,7 @@ __global__ void __launch_bounds__(128, 3) ec_lock_kernel(const ECParams P) {
       // tile's own group (tethers, walls, every contact in the 27 cells)
       const TileRec &T = tr[gib];
       if (live && T.active && T.rq_cnt < 0) {
+        if (gl == 0) ++exh;
         const double Q0 = T.q[0], Q1 = T.q[1], Q2 = T.q[2];
         const double V0 = T.v[0], V1 = T.v[1], V2 = T.v[2];
         const double L0 = SYS(L)[0], L1 = SYS(L)[1], L2 = SYS(L)[2];
@@ -995,6 +998,7 @@ __global__ void __launch_bounds__(128, 3) ec_lock_kernel(const ECParams P) {
 
   // ------------------------------------------------------------ counters
   if (confirmed) atomicAdd(&P.counters[CNT_CONFIRMED], confirmed);
+  if (exh) atomicAdd(&P.counters[CNT_EXHAUSTIVE], (unsigned long long)exh);
   if (o_any && ecs_done) {
 #pragma unroll
     for (int k = 0; k < ECMC_NEV; ++k)

@@ -46,7 +46,7 @@ class Opts(C.Structure):
                 ("event_cap", C.c_int64), ("p_swap", C.c_double), ("ecs_per_tile", C.c_int32),
                 ("lanes", C.c_int32), ("record", C.c_int32), ("stage_cap", C.c_int32),
                 ("cell_side", C.c_double), ("tile_side", C.c_double), ("schedule", C.c_int32),
-                ("block_tiles", C.c_int32)]
+                ("block_tiles", C.c_int32), ("request_cap", C.c_int32)]
 
 
 class Obs(C.Structure):
@@ -60,7 +60,7 @@ class Obs(C.Structure):
                 ("device_seconds", C.c_double), ("ec_kernel_seconds", C.c_double),
                 ("confirmed", C.c_int64), ("contact_pairs", C.c_int64 * 2),
                 ("taut_bonds", C.c_int64 * 2), ("contact_delta", C.c_double),
-                ("pressure_contact", C.c_double)]
+                ("pressure_contact", C.c_double), ("exhaustive", C.c_int64)]
 
     def as_dict(self):
         d = {k: getattr(self, k) for k, _ in self._fields_
@@ -150,7 +150,7 @@ def _p(a, ct):
 
 def opts(mode=MODE_SERIAL, dir_mode=DIR_CART3, precision=PREC_FP64, tiles=(3, 3, 3), joint=0.0,
          s_cap=0.0, event_cap=0, p_swap=0.0, ecs_per_tile=0, lanes=0, record=0, stage_cap=0,
-         cell_side=0.0, tile_side=0.0, schedule=0, block_tiles=0) -> Opts:
+         cell_side=0.0, tile_side=0.0, schedule=0, block_tiles=0, request_cap=0) -> Opts:
     o = Opts()
     o.mode, o.dir_mode, o.precision = int(mode), int(dir_mode), int(precision)
     for a in range(3):
@@ -160,6 +160,7 @@ def opts(mode=MODE_SERIAL, dir_mode=DIR_CART3, precision=PREC_FP64, tiles=(3, 3,
     o.record, o.stage_cap, o.cell_side = int(record), int(stage_cap), float(cell_side)
     o.tile_side = float(tile_side)
     o.schedule, o.block_tiles = int(schedule), int(block_tiles)
+    o.request_cap = int(request_cap)
     return o
 
 

@@ -43,3 +43,40 @@ def test_binding_refuses_without_library(tmp_path):
         ecmc._lib = None
         ecmc.load(str(tmp_path / "missing.so"))
     ecmc._lib = None
+
+
+def _c_layout(tmp_path, structs):
+    """sizeof and offsetof of every named field, as gcc lays out include/ecmc.h."""
+    lines = ["#include <stddef.h>", "#include <stdio.h>", '#include "ecmc.h"', "int main(void) {"]
+    for cname, fields in structs.items():
+        lines.append(f'  printf("{cname} %zu\\n", sizeof({cname}));')
+        for f in fields:
+            lines.append(f'  printf("{cname}.{f} %zu\\n", offsetof({cname}, {f}));')
+    lines += ["  return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    import subprocess
+    r = subprocess.run(["gcc", "-std=c11", "-Wall", "-I", os.path.join(ROOT, "include"), str(src),
+                        "-o", str(exe)], capture_output=True, text=True)
+    if r.returncode != 0:
+        pytest.fail(f"include/ecmc.h does not compile as C:\n{r.stderr}")
+    out = subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout
+    return {k: int(v) for k, v in (ln.split() for ln in out.splitlines())}
+
+
+def test_binding_struct_layouts_match_header(tmp_path):
+    """Every struct the binding passes by pointer has the header's size and
+    field offsets (a mismatch would corrupt options or results silently)."""
+    pairs = {"ecmc_opts": ecmc.Opts, "ecmc_obs": ecmc.Obs, "ecmc_tuning": ecmc.Tuning,
+             "ecmc_replica_spec": ecmc.ReplicaSpec}
+    structs = {c: [f for f, _ in py._fields_] for c, py in pairs.items()}
+    structs["ecmc_event"] = list(ecmc.EVENT_DTYPE.names)
+    got = _c_layout(tmp_path, structs)
+    for cname, py in pairs.items():
+        assert got[cname] == ctypes.sizeof(py), cname
+        for f, _ in py._fields_:
+            assert got[f"{cname}.{f}"] == getattr(py, f).offset, (cname, f)
+    assert got["ecmc_event"] == ecmc.EVENT_DTYPE.itemsize
+    for f in ecmc.EVENT_DTYPE.names:
+        assert got[f"ecmc_event.{f}"] == ecmc.EVENT_DTYPE.fields[f][1], f

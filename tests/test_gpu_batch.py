@@ -38,10 +38,10 @@ def oracle_replica(sp, r, tiles, ell, sweeps, p_swap=0.0, jitter=JITTER):
 
 
 def check_batch(specs, lanes, prec, graph, sweeps=3, ell=3.0, p_swap=0.0, jitter=JITTER,
-                schedule=0):
+                schedule=0, **kw):
     b = ecmc.Batch(specs, jitter=jitter, seed=SEED)
     b.configure(dir_mode=ecmc.DIR_ISO, precision=prec, lanes=lanes, record=1, p_swap=p_swap,
-                schedule=schedule)
+                schedule=schedule, **kw)
     b.run(ell, seed=SEED, n_sweeps=sweeps, graph=graph)
     units = sum(int(np.prod(b.info(r)[0])) for r in range(len(specs)))
     dig, _, _ = b.records(sweeps * units)
@@ -69,6 +69,12 @@ def test_batch_swap_matches_oracle(schedule):
     # the N = 1 replica accepts every swap, the chains almost none
     check_batch(ragged_specs()[:4], 8, ecmc.PREC_FP32F, True, p_swap=0.5, ell=5.0,
                 schedule=schedule)
+
+
+@pytest.mark.parametrize("lanes", [8, 4])
+def test_batch_exhaustive_evaluation_matches_oracle(lanes):
+    # one request per tile: most steps take the exhaustive FP64 evaluation
+    check_batch(ragged_specs(), lanes, ecmc.PREC_FP32F, True, sweeps=2, request_cap=1)
 
 
 def test_batch_c4_replicas_sample():

@@ -166,6 +166,38 @@ def test_block_lockstep_block_sizes(lanes, block_tiles):
     assert_same_state(ctx, o)
 
 
+@pytest.mark.parametrize("lanes,request_cap", [(8, 1), (4, 1), (16, 1), (8, 2), (4, 3)])
+def test_block_lockstep_exhaustive_evaluation(lanes, request_cap):
+    """Request lists of 1-3 entries per tile (screening lists of 24-72 slots):
+    with one, most tile steps take the exhaustive FP64 evaluation by the
+    tile's own lanes; the events are still the oracle's."""
+    m = BLOCKS
+    o = oracle_system(m)
+    res = o.run_domain(m.sweeps, m.ell, digests=True)
+    ctx = gpu_context(m, precision=ecmc.PREC_FP32F, lanes=lanes, request_cap=request_cap)
+    ctx.run(m.ell, seed=m.seed, n_sweeps=m.sweeps)
+    nt = m.D[0] * m.D[1] * m.D[2]
+    dig, _, _ = ctx.records(m.sweeps * nt)
+    assert (dig == res["digest"]).all()
+    assert_same_state(ctx, o)
+    if request_cap == 1:  # 24 slots hold fewer than the 27 cells around most pivots
+        ob = ctx.observables()
+        assert ob["exhaustive"] > ob["events_total"] // 4
+
+
+def test_exhaustive_evaluation_is_rare_by_default():
+    """With the default request list the exhaustive evaluation is a rare
+    path of the block-lockstep kernel, and the other kernels never take it."""
+    m = BLOCKS
+    ctx = gpu_context(m, precision=ecmc.PREC_FP32F, lanes=8)
+    ctx.run(m.ell, seed=m.seed, n_sweeps=m.sweeps)
+    ob = ctx.observables()
+    assert ob["exhaustive"] < 1e-3 * ob["events_total"]
+    ctx64 = gpu_context(m, precision=ecmc.PREC_FP64, lanes=8)
+    ctx64.run(m.ell, seed=m.seed, n_sweeps=1)
+    assert ctx64.observables()["exhaustive"] == 0
+
+
 @pytest.fixture(scope="module")
 def c2_oracle():
     o = oracle_system(C2)
@@ -353,6 +385,11 @@ def test_invalid_arguments_and_states():
         with pytest.raises(ecmc.EcmcError) as e:
             ctx.configure(mode=ecmc.MODE_DOMAIN, tiles=(3, 3, 3), precision=ecmc.PREC_FP32F,
                           lanes=lanes, block_tiles=bt)
+        assert e.value.code == -1
+    for rc in (-1, 7):
+        with pytest.raises(ecmc.EcmcError) as e:
+            ctx.configure(mode=ecmc.MODE_DOMAIN, tiles=(3, 3, 3), precision=ecmc.PREC_FP32F,
+                          lanes=8, request_cap=rc)
         assert e.value.code == -1
 
 
