@@ -77,7 +77,8 @@ __device__ __forceinline__ void group_argmin_m(double &bx, uint64_t &bkey, unsig
 }
 
 __host__ __device__ __forceinline__ size_t lock_tail_bytes(int NT) {
-  return (size_t)NT * sizeof(TileRec) + (size_t)NT * RQ_PER_TILE * (sizeof(int2) + sizeof(Res)) + 16;
+  return (size_t)NT * sizeof(TileRec) + (size_t)NT * RQ_PER_TILE * (sizeof(int2) + sizeof(Res)) + 16 +
+         ECMC_NEV * sizeof(unsigned long long);
 }
 
 #define SYS(f) (BATCH ? rp->f : P.f)
@@ -103,6 +104,7 @@ __global__ void __launch_bounds__(128, 3) ec_lock_kernel(const ECParams P) {
   int2 *rq = (int2 *)(tr + NT);
   Res *rs = (Res *)(rq + NT * RQ_PER_TILE);
   int *rq_n = (int *)(rs + NT * RQ_PER_TILE);
+  unsigned long long *ev_cnt = (unsigned long long *)(rq_n + 4);  // events by outcome, this block
   const int RQ_CAP = NT * P.rq_per_tile;  // at most NT * RQ_PER_TILE
   const int fl_cap = P.rq_per_tile * (FLAT_CAP / RQ_PER_TILE);
 
@@ -125,6 +127,7 @@ __global__ void __launch_bounds__(128, 3) ec_lock_kernel(const ECParams P) {
     tr[gib].rq_cnt = 0;
   }
   if (tid == 0) *rq_n = 0;
+  if (tid < ECMC_NEV) ev_cnt[tid] = 0;
   __syncthreads();
 
   // take the next unit and stage it (group-collective); false when none left
@@ -250,6 +253,7 @@ __global__ void __launch_bounds__(128, 3) ec_lock_kernel(const ECParams P) {
   bool active = false;
   bool o_any = false;  // the slot ran at least one EC
   int p = 0, pid = 0;
+  int o_cell = 0;  // local cell of the pivot's shadow
   double q0 = 0.0, q1 = 0.0, q2 = 0.0, v0 = 0.0, v1 = 0.0, v2 = 0.0, xrem = 0.0, lift = 0.0;
   float pf0 = 0.f, pf1 = 0.f, pf2 = 0.f, vf0 = 0.f, vf1 = 0.f, vf2 = 0.f;
   int64_t nev = 0, ncontact = 0;
@@ -257,11 +261,21 @@ __global__ void __launch_bounds__(128, 3) ec_lock_kernel(const ECParams P) {
   swr.v[0] = swr.v[1] = swr.v[2] = swr.v[3] = 0;
   uint64_t h = 0;
   double lift_all = 0.0, refl_all = 0.0, disp_all = 0.0;
-  unsigned long long cnt[ECMC_NEV];
-#pragma unroll
-  for (int k = 0; k < ECMC_NEV; ++k) cnt[k] = 0;
   unsigned long long tried = 0, confirmed = 0, nev_all = 0, ecs_done = 0;
   unsigned exh = 0;  // exhaustive evaluations led by this lane
+  // events by outcome: eight 8-bit fields, added to the block's counters
+  // every 255 events and at the end
+  uint64_t ev_pk = 0;
+  unsigned ev_pn = 0;
+  auto flush_outcomes = [&]() {
+#pragma unroll
+    for (int k = 0; k < ECMC_NEV; ++k) {
+      const unsigned c = (unsigned)(ev_pk >> (8 * k)) & 0xFFu;
+      if (c) atomicAdd(&ev_cnt[k], (unsigned long long)c);
+    }
+    ev_pk = 0;
+    ev_pn = 0;
+  };
 
   // start EC e of the owned tile: start bead and direction (Sec. II, R6)
   auto start_ec = [&]() {
@@ -301,6 +315,10 @@ __global__ void __launch_bounds__(128, 3) ec_lock_kernel(const ECParams P) {
     pf0 = ost.fx[p];
     pf1 = ost.fy[p];
     pf2 = ost.fz[p];
+    {
+      int c0, c1, c2;
+      o_cell = lcell(OLG, pf0, pf1, pf2, c0, c1, c2);
+    }
     vf0 = (float)v0;
     vf1 = (float)v1;
     vf2 = (float)v2;
@@ -345,6 +363,7 @@ __global__ void __launch_bounds__(128, 3) ec_lock_kernel(const ECParams P) {
   }
   const float b2f = (float)P.b2;
   const float eps_v = P.eps_v, eps_d = P.eps_d;
+  const float reach_hs = (float)P.sigma + 2.f * eps_v;  // per-axis reach of a contact
   const float INF = __int_as_float(0x7f800000);
   constexpr int ITEMS = G >= 8 ? 1 : 2;  // special candidates per lane
 
@@ -444,6 +463,26 @@ __global__ void __launch_bounds__(128, 3) ec_lock_kernel(const ECParams P) {
       unsigned short *fl = reinterpret_cast<unsigned short *>(rs) + gib * FLAT_CAP;
       int pc0 = 0, pc1 = 0, pc2 = 0;
       lcell(LG, a0, a1, a2, pc0, pc1, pc2);
+      // only the cells the pivot can reach this step: a hard-sphere partner
+      // lies within sigma (plus the screen's margin) of the path
+      // [pf, pf + xcap vf] on every axis, a box of one to three cells per
+      // axis inside the 27 around the pivot (cells are at least
+      // s_cap + 1.012 sigma wide)
+      int lo0, lo1, lo2, hi0, hi1, hi2;
+      {
+        const float xc = act ? T.xcap : 0.f;
+        const float e0 = xc * w0, e1 = xc * w1, e2 = xc * w2;
+        lcell(LG, a0 - reach_hs + fminf(e0, 0.f), a1 - reach_hs + fminf(e1, 0.f),
+              a2 - reach_hs + fminf(e2, 0.f), lo0, lo1, lo2);
+        lcell(LG, a0 + reach_hs + fmaxf(e0, 0.f), a1 + reach_hs + fmaxf(e1, 0.f),
+              a2 + reach_hs + fmaxf(e2, 0.f), hi0, hi1, hi2);
+        lo0 = max(lo0, pc0 - 1);
+        lo1 = max(lo1, pc1 - 1);
+        lo2 = max(lo2, pc2 - 1);
+        hi0 = min(hi0, pc0 + 1);
+        hi1 = min(hi1, pc1 + 1);
+        hi2 = min(hi2, pc2 + 1);
+      }
       const int n_ovf = act ? st.hdr[4] : 0;
       constexpr int CPL = (27 + G - 1) / G;  // cells per lane
       int cw[CPL];  // cell index << 3 | bead count
@@ -454,7 +493,7 @@ __global__ void __launch_bounds__(128, 3) ec_lock_kernel(const ECParams P) {
         cw[j] = 0;
         if (!act || ci >= 27) continue;
         const int x = pc0 + ci % 3 - 1, y = pc1 + (ci / 3) % 3 - 1, z = pc2 + ci / 9 - 1;
-        if (x < 0 || y < 0 || z < 0 || x >= LG.g0 || y >= LG.g1 || z >= LG.g2) continue;
+        if (x < lo0 || x > hi0 || y < lo1 || y > hi1 || z < lo2 || z > hi2) continue;
         const int c = (z * LG.g1 + y) * LG.g0 + x;
         const int n = cell_n(st.cell + 8 * c);
         cw[j] = (c << 3) | n;
@@ -728,6 +767,9 @@ __global__ void __launch_bounds__(128, 3) ec_lock_kernel(const ECParams P) {
     if (owner && active && nev >= P.event_cap) {
       set_status(P.status, DEV_STUCK);
       active = false;
+      oRr[3 * (int64_t)pid] = q0;
+      oRr[3 * (int64_t)pid + 1] = q1;
+      oRr[3 * (int64_t)pid + 2] = q2;
     }
     if (owner && active) {
       double x;
@@ -896,8 +938,8 @@ __global__ void __launch_bounds__(128, 3) ec_lock_kernel(const ECParams P) {
           np = slot;
         }
       }
-#pragma unroll
-      for (int k = 0; k < ECMC_NEV; ++k) cnt[k] += (out == k);
+      ev_pk += 1ull << (8 * out);
+      if (++ev_pn == 255) flush_outcomes();
       // FP32 shadow of the moved pivot: FP32 position minus FP32 corner
       float nf0 = (float)q0 - ocf0, nf1 = (float)q1 - ocf1, nf2 = (float)q2 - ocf2;
       if (owr0) nf0 = nf0 > oLh0 ? nf0 - (float)oL0 : (nf0 < -oLh0 ? nf0 + (float)oL0 : nf0);
@@ -923,14 +965,20 @@ __global__ void __launch_bounds__(128, 3) ec_lock_kernel(const ECParams P) {
           P.log[at] = ev;
         }
       }
-      oRr[3 * (int64_t)pid] = q0;
-      oRr[3 * (int64_t)pid + 1] = q1;
-      oRr[3 * (int64_t)pid + 2] = q2;
+      if (out == ECMC_EV_END || np != p) {
+        // the pivot's FP64 position stays in registers while it is the
+        // pivot (no other thread reads it) and goes back to the global
+        // array when the EC ends or is handed on
+        oRr[3 * (int64_t)pid] = q0;
+        oRr[3 * (int64_t)pid + 1] = q1;
+        oRr[3 * (int64_t)pid + 2] = q2;
+      }
       {
         // keep the local grid current
         int a0, a1, a2, b0, b1, b2;
-        const int oc = lcell(OLG, pf0, pf1, pf2, a0, a1, a2);
+        const int oc = o_cell;
         const int ncl = lcell(OLG, nf0, nf1, nf2, b0, b1, b2);
+        o_cell = ncl;
         if (swapped) {
           float g0 = (float)sw0 - ocf0, g1 = (float)sw1 - ocf1, g2 = (float)sw2 - ocf2;
           if (owr0) g0 = g0 > oLh0 ? g0 - (float)oL0 : (g0 < -oLh0 ? g0 + (float)oL0 : g0);
@@ -972,6 +1020,8 @@ __global__ void __launch_bounds__(128, 3) ec_lock_kernel(const ECParams P) {
         pf0 = ost.fx[p];
         pf1 = ost.fy[p];
         pf2 = ost.fz[p];
+        int c0, c1, c2;
+        o_cell = lcell(OLG, pf0, pf1, pf2, c0, c1, c2);
       }
     }
     // end of an EC: records, then the tile's next EC or a new tile
@@ -999,10 +1049,10 @@ __global__ void __launch_bounds__(128, 3) ec_lock_kernel(const ECParams P) {
   // ------------------------------------------------------------ counters
   if (confirmed) atomicAdd(&P.counters[CNT_CONFIRMED], confirmed);
   if (exh) atomicAdd(&P.counters[CNT_EXHAUSTIVE], (unsigned long long)exh);
+  if (ev_pn) flush_outcomes();
+  __syncthreads();
+  if (tid < ECMC_NEV && ev_cnt[tid]) atomicAdd(&P.counters[tid], ev_cnt[tid]);
   if (o_any && ecs_done) {
-#pragma unroll
-    for (int k = 0; k < ECMC_NEV; ++k)
-      if (cnt[k]) atomicAdd(&P.counters[k], cnt[k]);
     atomicAdd(&P.counters[CNT_EVENTS], nev_all);
     if (tried) atomicAdd(&P.counters[CNT_SWAP_TRIED], tried);
     atomicAdd(&P.counters[CNT_ECS], ecs_done);
