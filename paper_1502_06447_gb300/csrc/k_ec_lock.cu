@@ -104,6 +104,7 @@ __global__ void __launch_bounds__(128, 3) ec_lock_kernel(const ECParams P) {
   int2 *rq = (int2 *)(tr + NT);
   Res *rs = (Res *)(rq + NT * RQ_PER_TILE);
   int *rq_n = (int *)(rs + NT * RQ_PER_TILE);
+  int *n_run = rq_n + 1;  // slots with a running EC
   unsigned long long *ev_cnt = (unsigned long long *)(rq_n + 4);  // events by outcome, this block
   const int RQ_CAP = NT * P.rq_per_tile;  // at most NT * RQ_PER_TILE
   const int fl_cap = P.rq_per_tile * (FLAT_CAP / RQ_PER_TILE);
@@ -126,7 +127,10 @@ __global__ void __launch_bounds__(128, 3) ec_lock_kernel(const ECParams P) {
     tr[gib].active = 0;
     tr[gib].rq_cnt = 0;
   }
-  if (tid == 0) *rq_n = 0;
+  if (tid == 0) {
+    *rq_n = 0;
+    *n_run = 0;
+  }
   if (tid < ECMC_NEV) ev_cnt[tid] = 0;
   __syncthreads();
 
@@ -352,6 +356,21 @@ __global__ void __launch_bounds__(128, 3) ec_lock_kernel(const ECParams P) {
     T.xcap = __double2float_ru(dbits(P.s_cap) < dbits(xrem) ? P.s_cap : xrem);
     T.p = p;
   };
+  // The pivot's shadow and local cell in the staging area serve only the
+  // other beads' screens (a pivot never screens itself), so they are
+  // brought up to date when the bead stops being the pivot.
+  auto settle_pivot = [&](float f0, float f1, float f2) {
+    int c0, c1, c2;
+    const int nc = lcell(OLG, f0, f1, f2, c0, c1, c2);
+    if (nc != o_cell) {
+      lcell_remove(ost, o_cell, p);
+      if (!lcell_insert(ost, nc, p)) set_status(P.status, DEV_CAPACITY);
+      o_cell = nc;
+    }
+    ost.fx[p] = f0;
+    ost.fy[p] = f1;
+    ost.fz[p] = f2;
+  };
   // FP32 screen constants
   Screen Z;
   Z.sig2f = (float)P.sig2;
@@ -367,33 +386,40 @@ __global__ void __launch_bounds__(128, 3) ec_lock_kernel(const ECParams P) {
   const float INF = __int_as_float(0x7f800000);
   constexpr int ITEMS = G >= 8 ? 1 : 2;  // special candidates per lane
 
+  // One step per iteration.  Owners publish their tile's state at the end
+  // of the step; the barrier that closes it also tells whether a slot has
+  // run out of ECs, and only then do the slots refill.
+  bool refill = true;  // every slot starts empty
   for (;;) {
-    __syncthreads();
-    // refill empty slots (each by its own group; tiles without motile beads
-    // have no ECs and are passed over)
-    if (tr[gib].state == SLOT_EMPTY) {
-      for (;;) {
-        if (!take_tile()) {
-          live = false;
-          if (gl == 0) tr[gib].state = SLOT_DONE;
-          break;
-        }
-        if (live && m > 0) {
-          if (gl == 0) tr[gib].state = SLOT_FRESH;
-          break;
+    if (refill) {
+      // refill empty slots (each by its own group; tiles without motile
+      // beads have no ECs and are passed over)
+      if (tr[gib].state == SLOT_EMPTY) {
+        for (;;) {
+          if (!take_tile()) {
+            live = false;
+            if (gl == 0) tr[gib].state = SLOT_DONE;
+            break;
+          }
+          if (live && m > 0) {
+            if (gl == 0) tr[gib].state = SLOT_FRESH;
+            break;
+          }
         }
       }
+      __syncthreads();
+      if (owner && tr[ot].state == SLOT_FRESH) {
+        load_tile();
+        e = 0;
+        o_any = true;
+        start_ec();
+        tr[ot].state = SLOT_RUN;
+        publish();
+        atomicAdd(n_run, 1);
+      }
+      __syncthreads();
     }
-    __syncthreads();
-    if (owner && tr[ot].state == SLOT_FRESH) {
-      load_tile();
-      e = 0;
-      o_any = true;
-      start_ec();
-      tr[ot].state = SLOT_RUN;
-    }
-    if (owner) publish();
-    if (!__syncthreads_or(owner && active ? 1 : 0)) break;
+    if (*n_run == 0) break;
 
     // ---------------------------------------------------------- A: screen
     {
@@ -770,6 +796,7 @@ __global__ void __launch_bounds__(128, 3) ec_lock_kernel(const ECParams P) {
       oRr[3 * (int64_t)pid] = q0;
       oRr[3 * (int64_t)pid + 1] = q1;
       oRr[3 * (int64_t)pid + 2] = q2;
+      settle_pivot(pf0, pf1, pf2);
     }
     if (owner && active) {
       double x;
@@ -973,35 +1000,24 @@ __global__ void __launch_bounds__(128, 3) ec_lock_kernel(const ECParams P) {
         oRr[3 * (int64_t)pid + 1] = q1;
         oRr[3 * (int64_t)pid + 2] = q2;
       }
-      {
-        // keep the local grid current
-        int a0, a1, a2, b0, b1, b2;
-        const int oc = o_cell;
-        const int ncl = lcell(OLG, nf0, nf1, nf2, b0, b1, b2);
-        o_cell = ncl;
-        if (swapped) {
-          float g0 = (float)sw0 - ocf0, g1 = (float)sw1 - ocf1, g2 = (float)sw2 - ocf2;
-          if (owr0) g0 = g0 > oLh0 ? g0 - (float)oL0 : (g0 < -oLh0 ? g0 + (float)oL0 : g0);
-          if (owr1) g1 = g1 > oLh1 ? g1 - (float)oL1 : (g1 < -oLh1 ? g1 + (float)oL1 : g1);
-          if (owr2) g2 = g2 > oLh2 ? g2 - (float)oL2 : (g2 < -oLh2 ? g2 + (float)oL2 : g2);
-          const int koc = lcell(OLG, ost.fx[slot], ost.fy[slot], ost.fz[slot], a0, a1, a2);
-          const int knc = lcell(OLG, g0, g1, g2, b0, b1, b2);
-          lcell_remove(ost, oc, p);
+      if (swapped) {
+        // the partner takes the pivot's old position: its shadow and local cell
+        float g0 = (float)sw0 - ocf0, g1 = (float)sw1 - ocf1, g2 = (float)sw2 - ocf2;
+        if (owr0) g0 = g0 > oLh0 ? g0 - (float)oL0 : (g0 < -oLh0 ? g0 + (float)oL0 : g0);
+        if (owr1) g1 = g1 > oLh1 ? g1 - (float)oL1 : (g1 < -oLh1 ? g1 + (float)oL1 : g1);
+        if (owr2) g2 = g2 > oLh2 ? g2 - (float)oL2 : (g2 < -oLh2 ? g2 + (float)oL2 : g2);
+        int a0, a1, a2;
+        const int koc = lcell(OLG, ost.fx[slot], ost.fy[slot], ost.fz[slot], a0, a1, a2);
+        const int knc = lcell(OLG, g0, g1, g2, a0, a1, a2);
+        if (koc != knc) {
           lcell_remove(ost, koc, slot);
-          ost.fx[slot] = g0;
-          ost.fy[slot] = g1;
-          ost.fz[slot] = g2;
-          bool ok = lcell_insert(ost, ncl, p);
-          ok = lcell_insert(ost, knc, slot) && ok;
-          if (!ok) set_status(P.status, DEV_CAPACITY);
-        } else if (oc != ncl) {
-          lcell_remove(ost, oc, p);
-          if (!lcell_insert(ost, ncl, p)) set_status(P.status, DEV_CAPACITY);
+          if (!lcell_insert(ost, knc, slot)) set_status(P.status, DEV_CAPACITY);
         }
+        ost.fx[slot] = g0;
+        ost.fy[slot] = g1;
+        ost.fz[slot] = g2;
       }
-      ost.fx[p] = nf0;
-      ost.fy[p] = nf1;
-      ost.fz[p] = nf2;
+      if (out == ECMC_EV_END || np != p) settle_pivot(nf0, nf1, nf2);
       pf0 = nf0;
       pf1 = nf1;
       pf2 = nf2;
@@ -1040,10 +1056,16 @@ __global__ void __launch_bounds__(128, 3) ec_lock_kernel(const ECParams P) {
         }
       }
       ++e;
-      if (e < n_ec) start_ec();
-      else tr[ot].state = SLOT_EMPTY;
+      if (e < n_ec) {
+        start_ec();
+      } else {
+        tr[ot].state = SLOT_EMPTY;
+        atomicSub(n_run, 1);
+      }
     }
+    if (owner) publish();
     if (tid == 0) *rq_n = 0;
+    refill = __syncthreads_or(owner && tr[ot].state == SLOT_EMPTY);
   }
 
   // ------------------------------------------------------------ counters
