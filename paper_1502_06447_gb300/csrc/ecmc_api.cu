@@ -665,6 +665,7 @@ static ECParams ec_params(const ecmc_ctx *c, uint64_t seed, double ell) {
   P.sig2 = c->sigma * c->sigma;
   P.b2 = c->b_max * c->b_max;
   P.s_cap = c->s_cap;
+  P.s_cap_f = round_up_f32(c->s_cap);
   P.domain = c->opts.mode == ECMC_MODE_DOMAIN;
   P.halo_hs = c->halo_hs;
   P.halo_te = c->halo_te;

@@ -146,6 +146,7 @@ ECParams batch_params(ecmc_batch *b, uint64_t seed, double ell) {
   P.sig2 = b->sigma * b->sigma;
   P.b2 = b->b_max * b->b_max;
   P.s_cap = b->s_cap;
+  P.s_cap_f = round_up_f32(b->s_cap);
   P.domain = 1;
   P.halo_hs = b->halo_hs;
   P.halo_te = b->halo_te;

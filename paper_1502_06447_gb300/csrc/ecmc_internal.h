@@ -22,6 +22,13 @@ enum : int {
 };
 enum : int { SUM_LIFT = 0, SUM_REFL = 1, SUM_DISP = 2, SUM_N = 3 };
 
+// x > 0 rounded up to FP32 (host side)
+inline float round_up_f32(double x) {
+  float f = (float)x;
+  if ((double)f < x) f = nextafterf(f, INFINITY);
+  return f;
+}
+
 // One replica of a batch (device table): its box, tiles, cell grids, chain
 // length, where its beads, cells and tiles start in the concatenated arrays,
 // and its Philox key word.
@@ -68,6 +75,7 @@ struct ECParams {
   int32_t n_units;      // tiles (domain) or 1 (serial)
   // FP32 screen margins (units of sigma, sigma^2)
   float eps_v, eps_d, eps_x;
+  float s_cap_f;  // s_cap rounded up to FP32 (the screen's cap on a free flight)
   // buffers
   double *r;
   int32_t *img;

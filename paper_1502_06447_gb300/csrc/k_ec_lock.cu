@@ -24,6 +24,8 @@
 // pivot's in place; no other tile touches those beads), so shared memory
 // holds only the FP32 shadows, ids, bond words and local grid of each tile;
 // an evaluated request carries its partner's position to phase D.
+#include <type_traits>
+
 #include "ec_device.cuh"
 
 namespace ecmc {
@@ -33,7 +35,6 @@ namespace {
 // the owner thread (D)
 struct __align__(16) TileRec {
   double q[3], v[3];  // pivot position (wrapped FP64) and direction
-  double xrem;        // remaining displacement
   double c[3];        // tile corner
   float pf[3], vf[3];
   float xcap;         // FP32 upper bound of the END/PASS candidate
@@ -267,6 +268,7 @@ __global__ void __launch_bounds__(128, 3) ec_lock_kernel(const ECParams P) {
   double lift_all = 0.0, refl_all = 0.0, disp_all = 0.0;
   unsigned long long tried = 0, confirmed = 0, nev_all = 0, ecs_done = 0;
   unsigned exh = 0;  // exhaustive evaluations led by this lane
+  unsigned pub = 0;
   // events by outcome: eight 8-bit fields, added to the block's counters
   // every 255 events and at the end
   uint64_t ev_pk = 0;
@@ -333,8 +335,11 @@ __global__ void __launch_bounds__(128, 3) ec_lock_kernel(const ECParams P) {
     swr.v[0] = swr.v[1] = swr.v[2] = swr.v[3] = 0;
     h = 0xCBF29CE484222325ull;
     active = true;
+    pub = 3;
   };
   // publish the owned tile's state for the next step
+  // (pub: what else changed since the last publish, 1 the direction, 2 the
+  // pivot slot)
   auto publish = [&]() {
     TileRec &T = tr[ot];
     T.active = active ? 1 : 0;
@@ -342,19 +347,21 @@ __global__ void __launch_bounds__(128, 3) ec_lock_kernel(const ECParams P) {
     T.q[0] = q0;
     T.q[1] = q1;
     T.q[2] = q2;
-    T.v[0] = v0;
-    T.v[1] = v1;
-    T.v[2] = v2;
-    T.xrem = xrem;
     T.pf[0] = pf0;
     T.pf[1] = pf1;
     T.pf[2] = pf2;
-    T.vf[0] = vf0;
-    T.vf[1] = vf1;
-    T.vf[2] = vf2;
-    T.vnz = (nonzero(v0) ? 1 : 0) | (nonzero(v1) ? 2 : 0) | (nonzero(v2) ? 4 : 0);
-    T.xcap = __double2float_ru(dbits(P.s_cap) < dbits(xrem) ? P.s_cap : xrem);
-    T.p = p;
+    T.xcap = dbits(P.s_cap) < dbits(xrem) ? P.s_cap_f : __double2float_ru(xrem);
+    if (pub & 1) {
+      T.v[0] = v0;
+      T.v[1] = v1;
+      T.v[2] = v2;
+      T.vf[0] = vf0;
+      T.vf[1] = vf1;
+      T.vf[2] = vf2;
+      T.vnz = (nonzero(v0) ? 1 : 0) | (nonzero(v1) ? 2 : 0) | (nonzero(v2) ? 4 : 0);
+    }
+    if (pub & 2) T.p = p;
+    pub = 0;
   };
   // The pivot's shadow and local cell in the staging area serve only the
   // other beads' screens (a pivot never screens itself), so they are
@@ -385,6 +392,16 @@ __global__ void __launch_bounds__(128, 3) ec_lock_kernel(const ECParams P) {
   const float reach_hs = (float)P.sigma + 2.f * eps_v;  // per-axis reach of a contact
   const float INF = __int_as_float(0x7f800000);
   constexpr int ITEMS = G >= 8 ? 1 : 2;  // special candidates per lane
+  // the cells of the 27-cell stencil this lane gathers, 7 bits each:
+  // offsets dx | dy << 2 | dz << 4 from the stencil's corner, bit 6 set
+  constexpr int CPL = (27 + G - 1) / G;  // cells per lane
+  using CpkT = typename std::conditional<(7 * CPL <= 32), unsigned, uint64_t>::type;
+  CpkT cpk = 0;
+#pragma unroll
+  for (int j = 0; j < CPL; ++j) {
+    const int ci = gl + j * G;
+    if (ci < 27) cpk |= (CpkT)((ci % 3) | ((ci / 3 % 3) << 2) | ((ci / 9) << 4) | 64) << (7 * j);
+  }
 
   // One step per iteration.  Owners publish their tile's state at the end
   // of the step; the barrier that closes it also tells whether a slot has
@@ -510,17 +527,21 @@ __global__ void __launch_bounds__(128, 3) ec_lock_kernel(const ECParams P) {
         hi2 = min(hi2, pc2 + 1);
       }
       const int n_ovf = act ? st.hdr[4] : 0;
-      constexpr int CPL = (27 + G - 1) / G;  // cells per lane
+      // the box relative to the stencil's corner cell (pc - 1 on every axis)
+      const int r0 = lo0 - pc0 + 1, r1 = lo1 - pc1 + 1, r2 = lo2 - pc2 + 1;
+      const unsigned n0 = hi0 - lo0, n1 = hi1 - lo1, n2 = hi2 - lo2;
+      const int g01 = LG.g0 * LG.g1;
+      const int cb = (pc2 - 1) * g01 + (pc1 - 1) * LG.g0 + (pc0 - 1);
       int cw[CPL];  // cell index << 3 | bead count
       int cnt_l = 0;
 #pragma unroll
       for (int j = 0; j < CPL; ++j) {
-        const int ci = gl + j * G;
+        const unsigned d = (unsigned)(cpk >> (7 * j)) & 127u;
         cw[j] = 0;
-        if (!act || ci >= 27) continue;
-        const int x = pc0 + ci % 3 - 1, y = pc1 + (ci / 3) % 3 - 1, z = pc2 + ci / 9 - 1;
-        if (x < lo0 || x > hi0 || y < lo1 || y > hi1 || z < lo2 || z > hi2) continue;
-        const int c = (z * LG.g1 + y) * LG.g0 + x;
+        if (!act || !(d & 64u)) continue;
+        const int dx = d & 3u, dy = (d >> 2) & 3u, dz = (d >> 4) & 3u;
+        if ((unsigned)(dx - r0) > n0 || (unsigned)(dy - r1) > n1 || (unsigned)(dz - r2) > n2) continue;
+        const int c = cb + dz * g01 + dy * LG.g0 + dx;
         const int n = cell_n(st.cell + 8 * c);
         cw[j] = (c << 3) | n;
         cnt_l += n;
@@ -866,6 +887,7 @@ __global__ void __launch_bounds__(128, 3) ec_lock_kernel(const ECParams P) {
         out = ECMC_EV_PASS;
       } else if (kind == KIND_WALL) {
         out = ECMC_EV_WALL;
+        pub |= 1;
         if (partner == 0) v0 = -v0;
         else if (partner == 1) v1 = -v1;
         else v2 = -v2;
@@ -879,6 +901,7 @@ __global__ void __launch_bounds__(128, 3) ec_lock_kernel(const ECParams P) {
         if (!motile) {
           out = kind == KIND_HS ? ECMC_EV_HS_REFLECT : ECMC_EV_TE_REFLECT;
           refl_all = refl_all + proj;
+          pub |= 1;
           mirror2(v0, v1, v2, wrapc(q0 - wk0, oL0, ohb0, owr0), wrapc(q1 - wk1, oL1, ohb1, owr1),
                   wrapc(q2 - wk2, oL2, ohb2, owr2));
           vf0 = (float)v0;
@@ -1029,6 +1052,7 @@ __global__ void __launch_bounds__(128, 3) ec_lock_kernel(const ECParams P) {
       if (active && np != p) {
         // lift: the partner (motile, unmoved this event) becomes the pivot
         p = np;
+        pub |= 2;
         pid = ost.id[p];
         q0 = wk0;
         q1 = wk1;
