@@ -47,7 +47,7 @@ UNIT = "events/s"
 C0 = 1.2  # stencil cell side of the bytes-per-event definition (= b_max)
 # revision of the block-lockstep kernel; DRAM counters in profiles/ are used
 # only when they were taken on the same revision
-KERNEL_REV = 4
+KERNEL_REV = 5
 
 
 def bytes_per_event(phi, confirmed_per_event, fp32f=True):

@@ -888,12 +888,17 @@ __global__ void __launch_bounds__(128, 3) ec_lock_kernel(const ECParams P) {
       } else if (kind == KIND_WALL) {
         out = ECMC_EV_WALL;
         pub |= 1;
-        if (partner == 0) v0 = -v0;
-        else if (partner == 1) v1 = -v1;
-        else v2 = -v2;
-        vf0 = (float)v0;
-        vf1 = (float)v1;
-        vf2 = (float)v2;
+        // (negation is exact in both precisions)
+        if (partner == 0) {
+          v0 = -v0;
+          vf0 = -vf0;
+        } else if (partner == 1) {
+          v1 = -v1;
+          vf1 = -vf1;
+        } else {
+          v2 = -v2;
+          vf2 = -vf2;
+        }
       } else {
         // (r_target - r_pivot).v at contact = -(d.v) - x
         const double proj = -wdv - x;
