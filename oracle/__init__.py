@@ -22,6 +22,12 @@ Functions and the passage each follows:
                             workload's stated synthetic input)
   chain_obs                 end-to-end distance R_e^2 (Sec. III), bond lengths
   min_pair                  hard-sphere constraint check, Eq. 1
+  chain_struct              gyration tensor and centre of mass (R_g and g2,
+                            Sec. III; moment of inertia tensor, Appendix A),
+                            internal distances R^2(n) (Sec. II.C), end-to-end
+                            distance histogram W(R) (Appendix A)
+  shape_descriptors         eigenvalues of the gyration tensor, asphericity,
+                            acylindricity, shape anisotropy (Appendix A)
 All functions are pinned by ``tests/test_oracle_pins.py``.
 """
 from __future__ import annotations
@@ -115,6 +121,8 @@ def _load():
             lib.orc_min_pair.argtypes = [P(Params), P(C.c_double), P(C.c_double),
                                          P(C.c_int64)]
             lib.orc_min_pair_cells.argtypes = lib.orc_min_pair.argtypes
+            lib.orc_chain_struct.argtypes = [P(Params), P(C.c_double), C.c_void_p, C.c_void_p,
+                                             C.c_void_p, C.c_double, C.c_int64, C.c_void_p]
             lib.orc_contacts.argtypes = [P(Params), P(C.c_double), C.c_double, P(C.c_int64),
                                          P(C.c_int64)]
             lib.orc_start_draws.argtypes = [P(Params), C.c_int64, C.c_int64, P(C.c_int64),
@@ -273,3 +281,62 @@ class System:
 
     def unwrapped(self):
         return self.r + self.img * self.L
+
+    def chain_struct(self, dR=0.5, nbins=0, r2n=True):
+        """Gyration tensor per chain (S_xx, S_xy, S_xz, S_yy, S_yz, S_zz),
+        the middle bead relative to the centre of mass, R^2(n) for n < N
+        and the end-to-end distance histogram (bins of width dR, the last
+        taking the rest), all from positions along each chain built from
+        minimum-image bonds."""
+        lib = _load()
+        nch = self.r.shape[0] // self.P.N
+        gyr = np.zeros((nch, 6))
+        mid = np.zeros((nch, 3))
+        rn = np.zeros(self.P.N) if r2n else None
+        hist = np.zeros(max(int(nbins), 1), dtype=np.int64)
+        vp = lambda a: a.ctypes.data_as(C.c_void_p) if a is not None else None
+        rc = lib.orc_chain_struct(C.byref(self.P), _ptr(self.r, C.c_double), vp(gyr), vp(mid),
+                                  vp(rn), float(dR), int(nbins), vp(hist) if nbins else None)
+        if rc != 0:
+            raise RuntimeError(f"orc_chain_struct: {rc}")
+        return {"gyr": gyr, "mid": mid, "r2n": rn, "hist": hist[: int(nbins)]}
+
+
+def seq_sum(x) -> float:
+    """Left-to-right sum in index order (the order the library sums chains in)."""
+    x = np.asarray(x, dtype=np.float64)
+    return float(np.cumsum(x)[-1]) if x.size else 0.0
+
+
+def shape_descriptors(gyr):
+    """Per-chain shape from the gyration tensor S (Appendix A): T = Tr S =
+    R_g^2; P = lam1 lam2 + lam2 lam3 + lam3 lam1 (the sum of the principal
+    2x2 minors); eigenvalues lam1 <= lam2 <= lam3 (numpy.linalg.eigvalsh);
+    asphericity b = lam3 - (lam1 + lam2)/2; acylindricity c = lam2 - lam1;
+    shape anisotropy kappa2 = 1 - 3 P / T^2; 4 b^2 + 3 c^2 = 4 (T^2 - 3 P).
+    The moment of inertia tensor of a chain is N (T 1 - S): its eigenvalues
+    taken in descending order I1 >= I2 >= I3 are N (T - lam1) ... so that
+    I1 + I2 - I3 = 2 N lam3, I1 - I2 + I3 = 2 N lam2, -I1 + I2 + I3 = 2 N lam1
+    and Tr I = 2 N T (the reading under which the paper's ratios and limits
+    hold)."""
+    g = np.asarray(gyr, dtype=np.float64)
+    sxx, sxy, sxz, syy, syz, szz = (g[:, k] for k in range(6))
+    T = (sxx + syy) + szz
+    P = ((sxx * syy - sxy * sxy) + (sxx * szz - sxz * sxz)) + (syy * szz - syz * syz)
+    M = np.empty((g.shape[0], 3, 3))
+    M[:, 0, 0], M[:, 0, 1], M[:, 0, 2] = sxx, sxy, sxz
+    M[:, 1, 0], M[:, 1, 1], M[:, 1, 2] = sxy, syy, syz
+    M[:, 2, 0], M[:, 2, 1], M[:, 2, 2] = sxz, syz, szz
+    lam = np.linalg.eigvalsh(M)  # ascending
+    b = lam[:, 2] - 0.5 * (lam[:, 0] + lam[:, 1])
+    c = lam[:, 1] - lam[:, 0]
+    kappa2 = 1.0 - 3.0 * P / (T * T)
+    bc = 4.0 * (T * T - 3.0 * P)
+    return {"T": T, "P": P, "lam": lam, "b": b, "c": c, "kappa2": kappa2, "bc": bc}
+
+
+def g2_terms(mid_ref, mid):
+    """Per-chain squared displacement of the middle bead relative to the
+    centre of mass (the summand of g2, Sec. III)."""
+    d = np.asarray(mid, dtype=np.float64) - np.asarray(mid_ref, dtype=np.float64)
+    return (d[:, 0] * d[:, 0] + d[:, 1] * d[:, 1]) + d[:, 2] * d[:, 2]

@@ -884,3 +884,97 @@ int orc_start_draws(const orc_params *P, int64_t ec0, int64_t n, int64_t *idx,
     draw_start(&c, TAG_START, 0, (uint64_t)(ec0 + j), P->n, &idx[j], &v[3 * j]);
   return 0;
 }
+
+/*
+ * Chain structure of the current state, each quantity written out from its
+ * definition:
+ *   - radius of gyration R_g^2 and the centre of mass R (Sec. III, the
+ *     plateau of g2), and the moment of inertia tensor of a chain (Appendix
+ *     A), through the gyration tensor S = (1/N) sum_j (u_j - U)(u_j - U)^T
+ *     with U = (1/N) sum_j u_j (the inertia tensor is N (Tr S 1 - S));
+ *   - the middle bead relative to the centre of mass, u_{N/2} - U (the
+ *     quantity whose displacement g2 averages, Sec. III);
+ *   - mean-square internal distances R^2(n) (Sec. II.C):
+ *     r2n[n] = mean over chains and j of |u_{j+n} - u_j|^2, r2n[0] = 0;
+ *   - the end-to-end distance distribution W(R) (Appendix A) as counts of
+ *     chains with floor(|u_{N-1} - u_0| / dR) = b, the last bin taking the
+ *     rest.
+ * u_j are the positions along a chain from minimum-image bonds:
+ * u_0 = 0, u_{j+1} = u_j + minimg(r_{j+1} - r_j).  Sums run in index order
+ * (beads, then chains); any output may be NULL.
+ *   gyr[6 ch + k]: S_xx, S_xy, S_xz, S_yy, S_yz, S_zz
+ *   mid[3 ch + a]: u_{N/2} - U
+ */
+int orc_chain_struct(const orc_params *P, const double *r, double *gyr, double *mid,
+                     double *r2n, double dR, int64_t nbins, int64_t *hist) {
+  const int32_t N = P->N;
+  const int64_t nch = P->n / N;
+  double *u = (double *)malloc(sizeof(double) * 3 * (size_t)N);
+  double *acc = r2n ? (double *)calloc((size_t)N, sizeof(double)) : NULL;
+  if (!u || (r2n && !acc)) {
+    free(u);
+    free(acc);
+    return ORC_EINVAL;
+  }
+  if (hist)
+    for (int64_t b = 0; b < nbins; ++b) hist[b] = 0;
+  for (int64_t ch = 0; ch < nch; ++ch) {
+    const double *rc = r + 3 * ch * N;
+    u[0] = u[1] = u[2] = 0.0;
+    for (int32_t j = 0; j + 1 < N; ++j)
+      for (int a = 0; a < 3; ++a)
+        u[3 * (j + 1) + a] = u[3 * j + a] + minimg(rc[3 * (j + 1) + a] - rc[3 * j + a], P->L[a]);
+    double U[3];
+    for (int a = 0; a < 3; ++a) {
+      double s = 0.0;
+      for (int32_t j = 0; j < N; ++j) s += u[3 * j + a];
+      U[a] = s / (double)N;
+    }
+    if (gyr) {
+      double s00 = 0.0, s01 = 0.0, s02 = 0.0, s11 = 0.0, s12 = 0.0, s22 = 0.0;
+      for (int32_t j = 0; j < N; ++j) {
+        const double d0 = u[3 * j] - U[0], d1 = u[3 * j + 1] - U[1], d2 = u[3 * j + 2] - U[2];
+        s00 += d0 * d0;
+        s01 += d0 * d1;
+        s02 += d0 * d2;
+        s11 += d1 * d1;
+        s12 += d1 * d2;
+        s22 += d2 * d2;
+      }
+      double *g = gyr + 6 * ch;
+      g[0] = s00 / (double)N;
+      g[1] = s01 / (double)N;
+      g[2] = s02 / (double)N;
+      g[3] = s11 / (double)N;
+      g[4] = s12 / (double)N;
+      g[5] = s22 / (double)N;
+    }
+    if (mid)
+      for (int a = 0; a < 3; ++a) mid[3 * ch + a] = u[3 * (N / 2) + a] - U[a];
+    if (hist && nbins > 0) {
+      const double *e = u + 3 * (N - 1);
+      const double R = sqrt(e[0] * e[0] + e[1] * e[1] + e[2] * e[2]);
+      int64_t b = (int64_t)floor(R / dR);
+      if (b >= nbins) b = nbins - 1;
+      ++hist[b];
+    }
+    if (acc)
+      for (int32_t n = 1; n < N; ++n) {
+        double part = 0.0;
+        for (int32_t j = 0; j + n < N; ++j) {
+          const double d0 = u[3 * (j + n)] - u[3 * j];
+          const double d1 = u[3 * (j + n) + 1] - u[3 * j + 1];
+          const double d2 = u[3 * (j + n) + 2] - u[3 * j + 2];
+          part += d0 * d0 + d1 * d1 + d2 * d2;
+        }
+        acc[n] += part;
+      }
+  }
+  if (r2n) {
+    r2n[0] = 0.0;
+    for (int32_t n = 1; n < N; ++n) r2n[n] = acc[n] / ((double)nch * (double)(N - n));
+  }
+  free(u);
+  free(acc);
+  return 0;
+}
