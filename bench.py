@@ -232,6 +232,7 @@ def run_gpu(args, rank, world):
         "overlaps": o1["overlaps"], "tether_violations": o1["tether_violations"],
         "note": "pressure_lift is the lift-distance estimator (biased in the domain mode); "
                 "pressure_contact the contact-value estimator of the final state"}
+    structure = structure_run(ctx, stream)
 
     # plain FP64 kernel on the same workload (fresh lattice, same calibration)
     ctx64, tune64 = make(ecmc.PREC_FP64)
@@ -330,6 +331,7 @@ def run_gpu(args, rank, world):
         "gpu_launches": (7 if args.schedule == 0 and (tune["lanes"] if tune else args.lanes)
                          in (4, 8, 16) else 6) * args.steps,
         "physics": physics,
+        "structure": structure,
         "clocks": clk.summary(),
         "tuning": {"fp32f": tune, "fp64": tune64},
     }
@@ -410,6 +412,38 @@ def run_batch(args, stream):
     return res
 
 
+def structure_run(ctx, stream):
+    """The chain-structure pass (ecmc_structure) on the melt's final state:
+    its device time with and without R^2(n) (CUDA events on the library's
+    stream, after one untimed call) and what it measures.  g2 is over the
+    timed sweeps (the reference is taken before them)."""
+    def timed(r2n, reps=5):
+        ctx.structure(dR=2.0, nbins=64, r2n=r2n)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(reps):
+            out = ctx.structure(dR=2.0, nbins=64, r2n=r2n)
+        b.record(stream)
+        torch.cuda.synchronize()
+        return a.elapsed_time(b) / reps, out
+    ms0, _ = timed(False)
+    ms1, (got, rn, hist) = timed(True)
+    nch, N = got["n_chains"], got["N"]
+    pairs = nch * N * (N - 1) / 2
+    T = got["rg2_sum"] / nch
+    return {"ms": ms1, "ms_without_r2n": ms0, "chains": nch, "N": N,
+            "r2n_fp64_gflops": 9.0 * pairs / ((ms1 - ms0) * 1e-3) / 1e9 if ms1 > ms0 else None,
+            "rg2_mean": T, "re2_mean": got["re2_sum"] / nch,
+            "lam_fractions": [x / got["rg2_sum"] for x in got["lam_sum"]],
+            "kappa2_mean": got["kappa2_sum"] / nch,
+            "bc_over_trI2": got["bc_sum"] / nch / (4.0 * T * T),
+            "g2_over_timed_steps": got["g2_sum"] / nch,
+            "r2n_over_n": {str(n): float(rn[n] / n) for n in (1, 10, 100, N - 1) if n < N},
+            "note": "lam_fractions = <-I1+I2+I3>, <I1-I2+I3>, <I1+I2-I3> over <Tr I> (inertia "
+                    "tensor eigenvalues in descending order); ideal chains give 0.0646, 0.175, "
+                    "0.754 and bc_over_trI2 = 2/3"}
+
+
 def cpu_baseline_run(max_sweeps=1, time_budget=25.0):
     """The oracle as it stands (serial FP64 C, one core) on a bounded sample:
     `max_sweeps` full sweeps of the same 10^6-bead workload."""
@@ -421,9 +455,15 @@ def cpu_baseline_run(max_sweeps=1, time_budget=25.0):
     res = o.run_domain(max_sweeps, ELL)
     dt = time.perf_counter() - t0
     ev = res["stats"]["events"]
+    t1 = time.perf_counter()
+    o.chain_struct(dR=2.0, nbins=64)
+    ds = time.perf_counter() - t1
     return {"value": ev / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
             "sample": f"{max_sweeps} sweep(s) of the 1e6-bead melt without swaps "
-                      f"({ev} events, {dt:.1f} s)"}
+                      f"({ev} events, {dt:.1f} s)",
+            "structure_ms": 1e3 * ds,
+            "structure_sample": "one chain-structure pass (gyration tensors, R^2(n), W(R)) "
+                                "over the same melt"}
 
 
 def run_reference(args, rank):

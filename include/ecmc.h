@@ -229,8 +229,44 @@ ecmc_status ecmc_swap(ecmc_ctx *ctx, double attempts_per_bead_per_sweep);
 /* Fused observables over the current state (R_e^2, bonds, overlaps, g1)
  * together with the counters of all runs so far.  Synchronises. */
 ecmc_status ecmc_observables(ecmc_ctx *ctx, ecmc_obs *out);
-/* take the g1 reference snapshot (unwrapped middle beads) now */
+/* take the g1 reference snapshot (unwrapped middle beads) now; also the
+ * g2 reference of ecmc_structure (middle beads relative to their chain's
+ * centre of mass) */
 ecmc_status ecmc_g1_reset(ecmc_ctx *ctx);
+
+/* Chain structure of the current state (one fused pass, Sec. III: radius of
+ * gyration and g2; Appendix A: moment of inertia tensor and shape
+ * descriptors, end-to-end distance distribution W(R); Sec. II.C: internal
+ * distances R^2(n)).  Positions along a chain come from minimum-image bonds
+ * (u_0 = 0, u_{j+1} = u_j + minimg(r_{j+1} - r_j)); the gyration tensor is
+ * S = (1/N) sum_j (u_j - U)(u_j - U)^T with U = (1/N) sum_j u_j, and the
+ * moment of inertia tensor N (Tr S 1 - S): taken in descending order its
+ * eigenvalues give <I1 + I2 - I3> / <Tr I> = lam_sum[2] / rg2_sum,
+ * <I1 - I2 + I3> / <Tr I> = lam_sum[1] / rg2_sum,
+ * <-I1 + I2 + I3> / <Tr I> = lam_sum[0] / rg2_sum and
+ * <4 b_I^2 + 3 c_I^2> / <Tr I>^2 = n_chains bc_sum / (4 rg2_sum^2).  Sums
+ * run over chains in chain order and are reproducible bit for bit; the
+ * eigenvalues come from a Jacobi iteration (within 1e-14 Tr S of exact). */
+typedef struct ecmc_struct {
+  int64_t n_chains, N;
+  double rg2_sum;     /* sum over chains of R_g^2 = Tr S */
+  double lam_sum[3];  /* sums of the eigenvalues of S, lam1 <= lam2 <= lam3 per chain */
+  double b_sum;       /* asphericity lam3 - (lam1 + lam2) / 2 */
+  double c_sum;       /* acylindricity lam2 - lam1 */
+  double kappa2_sum;  /* shape anisotropy 1 - 3 P / (Tr S)^2, P = lam1 lam2 + lam2 lam3 + lam3 lam1 */
+  double bc_sum;      /* 4 b^2 + 3 c^2 = 4 ((Tr S)^2 - 3 P) */
+  double g2_sum;      /* |m - m_ref|^2, m = u_{N/2} - U, m_ref from the last
+                         ecmc_g1_reset (0 without one) */
+  double re2_sum;     /* |u_{N-1}|^2 */
+} ecmc_struct;
+/* r2n: NULL or N doubles (host), receives R^2(n) = mean over chains and j of
+ * |u_{j+n} - u_j|^2 for n < N (r2n[0] = 0); hist: NULL or nbins int64
+ * (host), receives the chains with floor(|u_{N-1}| / dR) = b (the last bin
+ * takes the rest; dR > 0).  Needs chains of at least 2 beads.  Device
+ * scratch (about 24 B per bead, plus 8 B per bead for R^2(n)) is allocated
+ * on first use.  Synchronises. */
+ecmc_status ecmc_structure(ecmc_ctx *ctx, ecmc_struct *out, double *r2n, double dR,
+                           int64_t nbins, int64_t *hist);
 
 /* Per-EC records of the last ecmc_run (opts.record = 1): digest (64-bit
  * FNV-1a over (pivot, kind<<32|partner, bits of x) of every event), lift sum

@@ -93,6 +93,11 @@ struct ecmc_ctx {
   unsigned long long *d_obs_u = nullptr;
   double *d_g1ref = nullptr;
   bool g1_set = false;
+  // chain structure scratch (allocated on first use)
+  double *d_su = nullptr, *d_srec = nullptr, *d_spart = nullptr, *d_sr2n = nullptr;
+  double *d_ssum = nullptr, *d_g2ref = nullptr;
+  unsigned long long *d_shist = nullptr;
+  int64_t shist_n = 0;
   // records
   uint64_t *d_rdig = nullptr;
   double *d_rlift = nullptr;
@@ -289,7 +294,8 @@ void destroy(ecmc_ctx *c) {
   void *ptrs[] = {c->d_r, c->d_img, c->d_tag, c->d_cell, c->d_rank, c->d_count, c->d_start,
                   c->d_bsum, c->d_cr, c->d_crf, c->d_rf, c->d_cid, c->d_ctag, c->d_cnt, c->d_sums, c->d_status,
                   c->d_unit_next, c->d_n_deferred, c->d_deferred, c->d_obs_d, c->d_obs_u, c->d_g1ref, c->d_rdig, c->d_rlift, c->d_rev,
-                  c->d_log, c->d_log_n, c->d_scratch};
+                  c->d_log, c->d_log_n, c->d_scratch, c->d_su, c->d_srec, c->d_spart,
+                  c->d_sr2n, c->d_ssum, c->d_g2ref, c->d_shist};
   for (void *p : ptrs) cudaFree(p);
   for (cudaEvent_t e : c->kev) cudaEventDestroy(e);
   if (c->ev0) cudaEventDestroy(c->ev0);
@@ -856,11 +862,95 @@ ecmc_status ecmc_observables(ecmc_ctx *c, ecmc_obs *out) {
   return ECMC_OK;
 }
 
+// the chain-structure pass over the current positions (scratch on demand)
+static ecmc_status run_structure(ecmc_ctx *c, bool with_r2n, double dR, int64_t nbins) {
+  const int64_t nch = c->n / c->N;
+  if (!c->d_su) {
+    CU(dalloc(&c->d_su, 3 * c->n));
+    CU(dalloc(&c->d_srec, STRUCT_REC * nch));
+    CU(dalloc(&c->d_ssum, STRUCT_SUMS));
+    CU(dalloc(&c->d_g2ref, 3 * nch));
+  }
+  if (with_r2n && !c->d_spart) {
+    CU(dalloc(&c->d_spart, nch * c->N));
+    CU(dalloc(&c->d_sr2n, c->N));
+  }
+  if (nbins > c->shist_n) {
+    cudaFree(c->d_shist);
+    c->d_shist = nullptr;
+    c->shist_n = 0;
+    CU(cudaMalloc(&c->d_shist, sizeof(unsigned long long) * (size_t)nbins));
+    c->shist_n = nbins;
+  }
+  StructParams S{};
+  S.n = c->n;
+  S.N = c->N;
+  for (int a = 0; a < 3; ++a) {
+    S.L[a] = c->L[a];
+    S.half[a] = 0.5 * c->L[a];
+  }
+  S.r = c->d_r;
+  S.u = c->d_su;
+  S.rec = c->d_srec;
+  S.mref = c->g1_set ? c->d_g2ref : nullptr;
+  S.part = with_r2n ? c->d_spart : nullptr;
+  S.r2n = with_r2n ? c->d_sr2n : nullptr;
+  S.sums = c->d_ssum;
+  S.hist = nbins > 0 ? c->d_shist : nullptr;
+  S.nbins = nbins;
+  S.dR = dR;
+  CU(launch_struct(S, c->stream));
+  return ECMC_OK;
+}
+
 ecmc_status ecmc_g1_reset(ecmc_ctx *c) {
   if (!c) return fail(ECMC_EINVAL, "ctx is NULL");
   CU(launch_g1_snapshot(obs_params(c), c->d_g1ref, c->stream));
+  if (c->N >= 2) {
+    // g2 reference: the middle beads relative to their centre of mass
+    const bool had = c->g1_set;
+    c->g1_set = false;
+    ecmc_status st = run_structure(c, false, 1.0, 0);
+    c->g1_set = had;
+    if (st != ECMC_OK) return st;
+    CU(cudaMemcpy2DAsync(c->d_g2ref, 3 * sizeof(double), c->d_srec + 10, STRUCT_REC * sizeof(double),
+                         3 * sizeof(double), (size_t)(c->n / c->N), cudaMemcpyDeviceToDevice,
+                         c->stream));
+  }
   c->g1_set = true;
   CU(cudaStreamSynchronize(c->stream));
+  return ECMC_OK;
+}
+
+ecmc_status ecmc_structure(ecmc_ctx *c, ecmc_struct *out, double *r2n, double dR, int64_t nbins,
+                           int64_t *hist) {
+  if (!c || !out) return fail(ECMC_EINVAL, "NULL argument");
+  if (c->N < 2) return fail(ECMC_EINVAL, "chain structure needs chains of at least 2 beads");
+  if (nbins < 0 || (nbins > 0 && !hist)) return fail(ECMC_EINVAL, "nbins must be >= 0 with a histogram buffer");
+  if (!hist) nbins = 0;
+  if (nbins > 0 && !(dR > 0.0 && dR < INFINITY)) return fail(ECMC_EINVAL, "dR must be positive and finite");
+  ecmc_status st = run_structure(c, r2n != nullptr, dR, nbins);
+  if (st != ECMC_OK) return st;
+  double sums[STRUCT_SUMS];
+  CU(cudaMemcpyAsync(sums, c->d_ssum, sizeof(sums), cudaMemcpyDeviceToHost, c->stream));
+  if (r2n) CU(cudaMemcpyAsync(r2n, c->d_sr2n, sizeof(double) * c->N, cudaMemcpyDeviceToHost, c->stream));
+  std::vector<unsigned long long> h((size_t)nbins);
+  if (nbins > 0)
+    CU(cudaMemcpyAsync(h.data(), c->d_shist, sizeof(unsigned long long) * (size_t)nbins,
+                       cudaMemcpyDeviceToHost, c->stream));
+  CU(cudaStreamSynchronize(c->stream));
+  for (int64_t b = 0; b < nbins; ++b) hist[b] = (int64_t)h[(size_t)b];
+  memset(out, 0, sizeof(*out));
+  out->n_chains = c->n / c->N;
+  out->N = c->N;
+  out->rg2_sum = sums[0];
+  for (int k = 0; k < 3; ++k) out->lam_sum[k] = sums[1 + k];
+  out->b_sum = sums[4];
+  out->c_sum = sums[5];
+  out->kappa2_sum = sums[6];
+  out->bc_sum = sums[7];
+  out->g2_sum = c->g1_set ? sums[8] : 0.0;
+  out->re2_sum = sums[9];
   return ECMC_OK;
 }
 

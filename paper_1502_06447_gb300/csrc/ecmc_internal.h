@@ -217,6 +217,28 @@ cudaError_t launch_obs(const ObsParams &O, cudaStream_t s);
 cudaError_t launch_wrap(double *r, int32_t *img, int64_t n, const double L[3],
                         unsigned long long *bad, cudaStream_t s);
 cudaError_t launch_g1_snapshot(const ObsParams &O, double *g1ref, cudaStream_t s);
+
+// Chain structure pass (k_struct.cu): per-chain record columns
+// T = Tr S, lam1, lam2, lam3, b, c, kappa2, 4 b^2 + 3 c^2, g2 summand, |R_e|^2,
+// then the middle bead relative to the centre of mass (3); the first
+// STRUCT_SUMS columns are summed over chains in chain order.
+enum : int { STRUCT_REC = 13, STRUCT_SUMS = 10 };
+struct StructParams {
+  int64_t n;
+  int32_t N;
+  double L[3], half[3];
+  const double *r;
+  double *u;                 // [n][3] positions along each chain
+  double *rec;               // [n / N][STRUCT_REC]
+  const double *mref;        // [n / N][3] g2 reference or null
+  double *part;              // [n / N][N] R^2(n) partial sums (with r2n)
+  double *r2n;               // [N] or null
+  double *sums;              // [STRUCT_SUMS]
+  unsigned long long *hist;  // [nbins] or null
+  int64_t nbins;
+  double dR;
+};
+cudaError_t launch_struct(const StructParams &S, cudaStream_t s);
 cudaError_t launch_lattice(const int32_t dims[3], double a, double jitter,
                            uint64_t seed, uint64_t replica, double *r, int64_t n,
                            cudaStream_t s);

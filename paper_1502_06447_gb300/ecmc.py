@@ -30,7 +30,7 @@ EXPORTS = (
     "ecmc_event_log", "ecmc_domain_tags", "ecmc_checkpoint", "ecmc_restore",
     "ecmc_cells_static", "ecmc_batch_create", "ecmc_batch_destroy", "ecmc_batch_configure",
     "ecmc_batch_run", "ecmc_batch_get_positions", "ecmc_batch_info", "ecmc_batch_stats",
-    "ecmc_batch_records", "ecmc_autotune", "ecmc_batch_autotune",
+    "ecmc_batch_records", "ecmc_autotune", "ecmc_batch_autotune", "ecmc_structure",
 )
 
 
@@ -69,6 +69,18 @@ class Obs(C.Structure):
         d["taut_bonds"] = tuple(self.taut_bonds)
         for i, name in enumerate(EV_NAMES):
             d[name] = self.events[i]
+        return d
+
+
+class Struct(C.Structure):
+    _fields_ = [("n_chains", C.c_int64), ("N", C.c_int64), ("rg2_sum", C.c_double),
+                ("lam_sum", C.c_double * 3), ("b_sum", C.c_double), ("c_sum", C.c_double),
+                ("kappa2_sum", C.c_double), ("bc_sum", C.c_double), ("g2_sum", C.c_double),
+                ("re2_sum", C.c_double)]
+
+    def as_dict(self):
+        d = {k: getattr(self, k) for k, _ in self._fields_ if k != "lam_sum"}
+        d["lam_sum"] = tuple(self.lam_sum)
         return d
 
 
@@ -123,6 +135,7 @@ def load(path: str = LIB_PATH):
                                    P(C.c_int64)],
             "ecmc_autotune": [vp, C.c_double, C.c_uint64, C.c_int32, P(Tuning)],
             "ecmc_batch_autotune": [vp, C.c_double, C.c_uint64, C.c_int32, P(Tuning)],
+            "ecmc_structure": [vp, P(Struct), vp, C.c_double, C.c_int64, vp],
         }
         for name, args in sig.items():
             f = getattr(lib, name)
@@ -276,6 +289,19 @@ class Context:
         o = Obs()
         _check(load().ecmc_observables(self._h, C.byref(o)))
         return o.as_dict()
+
+    def structure(self, dR=0.5, nbins=0, r2n=True):
+        """Chain structure of the current state (ecmc_structure): the sums
+        over chains as a dict, R^2(n) (N values, or None) and the end-to-end
+        histogram (nbins counts of width dR)."""
+        o = Struct()
+        nb = int(nbins)
+        hist = np.zeros(max(nb, 1), dtype=np.int64)
+        rn = np.zeros(self.N, dtype=np.float64) if r2n else None
+        _check(load().ecmc_structure(self._h, C.byref(o),
+                                     rn.ctypes.data_as(C.c_void_p) if rn is not None else None,
+                                     float(dR), nb, hist.ctypes.data_as(C.c_void_p) if nb else None))
+        return o.as_dict(), rn, hist[:nb]
 
     def g1_reset(self):
         _check(load().ecmc_g1_reset(self._h))

@@ -69,7 +69,7 @@ def test_binding_struct_layouts_match_header(tmp_path):
     """Every struct the binding passes by pointer has the header's size and
     field offsets (a mismatch would corrupt options or results silently)."""
     pairs = {"ecmc_opts": ecmc.Opts, "ecmc_obs": ecmc.Obs, "ecmc_tuning": ecmc.Tuning,
-             "ecmc_replica_spec": ecmc.ReplicaSpec}
+             "ecmc_replica_spec": ecmc.ReplicaSpec, "ecmc_struct": ecmc.Struct}
     structs = {c: [f for f, _ in py._fields_] for c, py in pairs.items()}
     structs["ecmc_event"] = list(ecmc.EVENT_DTYPE.names)
     got = _c_layout(tmp_path, structs)
