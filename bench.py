@@ -417,6 +417,8 @@ def structure_run(ctx, stream):
     its device time with and without R^2(n) (CUDA events on the library's
     stream, after one untimed call) and what it measures.  g2 is over the
     timed sweeps (the reference is taken before them)."""
+    import torch
+
     def timed(r2n, reps=5):
         ctx.structure(dR=2.0, nbins=64, r2n=r2n)
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
