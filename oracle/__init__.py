@@ -28,6 +28,9 @@ Functions and the passage each follows:
                             distance histogram W(R) (Appendix A)
   shape_descriptors         eigenvalues of the gyration tensor, asphericity,
                             acylindricity, shape anisotropy (Appendix A)
+  phantom_chains            non-reversal random walks without excluded volume,
+                            the first stage of the initial configuration
+                            (Sec. II.C)
 All functions are pinned by ``tests/test_oracle_pins.py``.
 """
 from __future__ import annotations
@@ -121,6 +124,8 @@ def _load():
             lib.orc_min_pair.argtypes = [P(Params), P(C.c_double), P(C.c_double),
                                          P(C.c_int64)]
             lib.orc_min_pair_cells.argtypes = lib.orc_min_pair.argtypes
+            lib.orc_phantom.argtypes = [P(C.c_double), C.c_int64, C.c_int32, C.c_double,
+                                        C.c_double, C.c_uint64, P(C.c_double), P(C.c_int32)]
             lib.orc_chain_struct.argtypes = [P(Params), P(C.c_double), C.c_void_p, C.c_void_p,
                                              C.c_void_p, C.c_double, C.c_int64, C.c_void_p]
             lib.orc_contacts.argtypes = [P(Params), P(C.c_double), C.c_double, P(C.c_int64),
@@ -300,6 +305,19 @@ class System:
         if rc != 0:
             raise RuntimeError(f"orc_chain_struct: {rc}")
         return {"gyr": gyr, "mid": mid, "r2n": rn, "hist": hist[: int(nbins)]}
+
+
+def phantom_chains(L, n_chains, N, bond=1.0, c=1.9, seed=0):
+    """Phantom chains (Sec. II.C): wrapped positions (n_chains N x 3) and
+    image counters of non-reversal random walks with stiffness c."""
+    lib = _load()
+    n = int(n_chains) * int(N)
+    r = np.zeros((n, 3))
+    img = np.zeros((n, 3), dtype=np.int32)
+    Lc = np.ascontiguousarray(L, dtype=np.float64)
+    lib.orc_phantom(_ptr(Lc, C.c_double), int(n_chains), int(N), float(bond), float(c),
+                    int(seed) & (2**64 - 1), _ptr(r, C.c_double), _ptr(img, C.c_int32))
+    return r, img
 
 
 def seq_sum(x) -> float:

@@ -978,3 +978,82 @@ int orc_chain_struct(const orc_params *P, const double *r, double *gyr, double *
   free(acc);
   return 0;
 }
+
+/*
+ * Phantom chains for the initial configuration (Sec. II.C, first stage of
+ * the slow push-off): n_chains chains of N beads without excluded volume,
+ * each a non-reversal random walk with bond length `bond`.  The first bead
+ * is uniform in the box, the first bond uniform on the sphere, and every
+ * next bond t_{j+1} uniform on the cap t_j . t_{j+1} >= ct around the one
+ * before, ct = cos(theta_max) = (c - 3)/(c + 1): then <cos theta> =
+ * (1 + ct)/2 = cos^2(theta_max/2) = (c - 1)/(c + 1) and
+ * <R^2> -> c (N - 1) bond^2 for long chains, c the paper's stiffness
+ * parameter.  (The paper writes the cap with "<"; its own <cos theta>
+ * holds for ">=", reading R21.)
+ * Random numbers: Philox4x64-10, key (seed, 0), counter (5, chain, bead,
+ * attempt).  Bead 0: words 0-2 times L.  Bead j >= 1: cos theta =
+ * 1 - u(w0) (1 - ct_j) (ct_1 = -1: the whole sphere); the azimuth from the
+ * first point (x, y) = (2 u - 1, 2 u' - 1) with 0 < x^2 + y^2 <= 1, taken
+ * from words 1, 2 of attempt 0, then words 0, 1 of attempts 1, 2, ...;
+ * t_{j+1} = cos theta t_j + sin theta (cos phi e1 + sin phi e2) with the
+ * orthonormal pair (e1, e2) of t_j from Duff et al., "Building an
+ * orthonormal basis, revisited" (JCGT 6(1), 2017), then normalised; the
+ * tangent before bond 1 is e_z.  Positions are then wrapped as the library
+ * wraps caller input: f = floor(x / L), x -= f L, x >= L -> x - L,
+ * x < 0 -> 0, image f.
+ */
+int orc_phantom(const double L[3], int64_t nch, int32_t N, double bond, double c, uint64_t seed,
+                double *r, int32_t *img) {
+  const double ct = (c - 3.0) / (c + 1.0);
+  const uint64_t key[2] = {seed, 0};
+  for (int64_t ch = 0; ch < nch; ++ch) {
+    uint64_t ctr[4] = {5, (uint64_t)ch, 0, 0}, w[4];
+    orc_philox4x64_10(ctr, key, w);
+    double p[3], t[3] = {0.0, 0.0, 1.0};
+    for (int a = 0; a < 3; ++a) p[a] = u53(w[a]) * L[a];
+    double *rc = r + 3 * ch * N;
+    for (int a = 0; a < 3; ++a) rc[a] = p[a];
+    for (int32_t j = 1; j < N; ++j) {
+      const double ctj = j == 1 ? -1.0 : ct;
+      uint64_t cj[4] = {5, (uint64_t)ch, (uint64_t)j, 0};
+      orc_philox4x64_10(cj, key, w);
+      const double cth = 1.0 - u53(w[0]) * (1.0 - ctj);
+      double x = 2.0 * u53(w[1]) - 1.0, y = 2.0 * u53(w[2]) - 1.0;
+      double s = x * x + y * y;
+      for (uint64_t att = 1; !(s > 0.0 && s <= 1.0); ++att) {
+        cj[3] = att;
+        orc_philox4x64_10(cj, key, w);
+        x = 2.0 * u53(w[0]) - 1.0;
+        y = 2.0 * u53(w[1]) - 1.0;
+        s = x * x + y * y;
+      }
+      const double sq = sqrt(s);
+      const double cph = x / sq, sph = y / sq;
+      const double sth = sqrt(1.0 - cth * cth);
+      const double sg = t[2] >= 0.0 ? 1.0 : -1.0;
+      const double aa = -1.0 / (sg + t[2]);
+      const double bb = t[0] * t[1] * aa;
+      const double e1[3] = {1.0 + sg * t[0] * t[0] * aa, sg * bb, -sg * t[0]};
+      const double e2[3] = {bb, sg + t[1] * t[1] * aa, -t[1]};
+      double nt[3];
+      for (int a = 0; a < 3; ++a) nt[a] = cth * t[a] + sth * (cph * e1[a] + sph * e2[a]);
+      const double q = sqrt(nt[0] * nt[0] + nt[1] * nt[1] + nt[2] * nt[2]);
+      for (int a = 0; a < 3; ++a) {
+        t[a] = nt[a] / q;
+        p[a] = p[a] + bond * t[a];
+        rc[3 * j + a] = p[a];
+      }
+    }
+  }
+  for (int64_t i = 0; i < 3 * nch * N; ++i) {
+    const double La = L[i % 3];
+    double x = r[i];
+    const double f = floor(x / La);
+    x -= f * La;
+    if (x >= La) x -= La;
+    if (x < 0) x = 0;
+    r[i] = x;
+    img[i] = (int32_t)f;
+  }
+  return 0;
+}
