@@ -161,6 +161,23 @@ typedef struct ecmc_event {
   double x;          /* free flight of the pivot */
 } ecmc_event;
 
+/* Phantom chains (Sec. II.C, the first stage of the paper's initial
+ * configurations: chains without excluded volume, to be pushed apart
+ * afterwards).  n_chains non-reversal random walks of N beads with bond
+ * length `bond` in the periodic box L: the first bead uniform in the box,
+ * the first bond uniform on the sphere, every next bond uniform on the cap
+ * t_j . t_{j+1} >= cos(theta_max) = (c - 3)/(c + 1) around the one before,
+ * so that <cos theta> = (c - 1)/(c + 1) and <R^2> -> c (N - 1) bond^2 for
+ * long chains (c = 1: free random walk; the paper's melts have c = 1.9).
+ * Philox4x64-10 with key (seed, 0), counter (5, chain, bead, attempt); the
+ * azimuth comes from the first point of the unit disc among uniform points
+ * of the square (at most 256 attempts, else ECMC_EINVAL).  xyz_out (host,
+ * 3 n_chains N doubles) receives positions wrapped into [0, L), img_out
+ * (host, 3 n_chains N int32, or NULL) the image counters.  Needs c >= 1,
+ * bond > 0.  Allocates and frees device memory; synchronises. */
+ecmc_status ecmc_phantom_chains(const double L[3], int64_t n_chains, int32_t N, double bond,
+                                double c, uint64_t seed, double *xyz_out, int32_t *img_out);
+
 /* ---- creation ----------------------------------------------------------
  * ecmc_create_lattice: melt on an n0 x n1 x n2 simple-cubic lattice with
  * spacing a in a periodic box L = dims * a.  Sites are visited in a 3-D

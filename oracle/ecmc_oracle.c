@@ -994,7 +994,8 @@ int orc_chain_struct(const orc_params *P, const double *r, double *gyr, double *
  * attempt).  Bead 0: words 0-2 times L.  Bead j >= 1: cos theta =
  * 1 - u(w0) (1 - ct_j) (ct_1 = -1: the whole sphere); the azimuth from the
  * first point (x, y) = (2 u - 1, 2 u' - 1) with 0 < x^2 + y^2 <= 1, taken
- * from words 1, 2 of attempt 0, then words 0, 1 of attempts 1, 2, ...;
+ * from words 1, 2 of attempt 0, then words 0, 1 of attempts 1, 2, ...
+ * (at most 256 attempts, else an error);
  * t_{j+1} = cos theta t_j + sin theta (cos phi e1 + sin phi e2) with the
  * orthonormal pair (e1, e2) of t_j from Duff et al., "Building an
  * orthonormal basis, revisited" (JCGT 6(1), 2017), then normalised; the
@@ -1021,6 +1022,7 @@ int orc_phantom(const double L[3], int64_t nch, int32_t N, double bond, double c
       double x = 2.0 * u53(w[1]) - 1.0, y = 2.0 * u53(w[2]) - 1.0;
       double s = x * x + y * y;
       for (uint64_t att = 1; !(s > 0.0 && s <= 1.0); ++att) {
+        if (att == 256) return ORC_EINVAL; /* (probability 0.21^256) */
         cj[3] = att;
         orc_philox4x64_10(cj, key, w);
         x = 2.0 * u53(w[0]) - 1.0;

@@ -903,6 +903,40 @@ static ecmc_status run_structure(ecmc_ctx *c, bool with_r2n, double dR, int64_t 
   return ECMC_OK;
 }
 
+ecmc_status ecmc_phantom_chains(const double L[3], int64_t n_chains, int32_t N, double bond,
+                                double c, uint64_t seed, double *xyz_out, int32_t *img_out) {
+  if (!L || !xyz_out) return fail(ECMC_EINVAL, "NULL argument");
+  for (int a = 0; a < 3; ++a)
+    if (!(L[a] > 0.0 && L[a] < INFINITY)) return fail(ECMC_EINVAL, "box must be positive and finite");
+  if (n_chains < 1 || N < 1 || n_chains > ((int64_t)1 << 40) / N)
+    return fail(ECMC_EINVAL, "need n_chains >= 1, N >= 1 and at most 2^40 beads");
+  if (!(bond > 0.0 && bond < INFINITY)) return fail(ECMC_EINVAL, "bond must be positive");
+  if (!(c >= 1.0 && c < INFINITY)) return fail(ECMC_EINVAL, "stiffness c must be >= 1");
+  const int64_t n = n_chains * N;
+  double *d_r = nullptr;
+  int32_t *d_img = nullptr;
+  unsigned long long *d_bad = nullptr;
+  cudaError_t e = cudaMalloc(&d_r, sizeof(double) * 3 * (size_t)n);
+  if (e == cudaSuccess) e = cudaMalloc(&d_img, sizeof(int32_t) * 3 * (size_t)n);
+  if (e == cudaSuccess) e = cudaMalloc(&d_bad, sizeof(unsigned long long) * 2);
+  if (e == cudaSuccess) e = cudaMemsetAsync(d_img, 0, sizeof(int32_t) * 3 * (size_t)n, 0);
+  if (e == cudaSuccess) e = cudaMemsetAsync(d_bad, 0, sizeof(unsigned long long) * 2, 0);
+  const double ct = (c - 3.0) / (c + 1.0);
+  if (e == cudaSuccess) e = launch_phantom(n_chains, N, L, bond, ct, seed, d_r, d_bad, 0);
+  if (e == cudaSuccess) e = launch_wrap(d_r, d_img, n, L, d_bad + 1, 0);
+  unsigned long long bad[2] = {0, 0};
+  if (e == cudaSuccess) e = cudaMemcpy(bad, d_bad, sizeof(bad), cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess) e = cudaMemcpy(xyz_out, d_r, sizeof(double) * 3 * (size_t)n, cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess && img_out)
+    e = cudaMemcpy(img_out, d_img, sizeof(int32_t) * 3 * (size_t)n, cudaMemcpyDeviceToHost);
+  cudaFree(d_r);
+  cudaFree(d_img);
+  cudaFree(d_bad);
+  if (e != cudaSuccess) return fail(ECMC_ECUDA, "%s", cudaGetErrorString(e));
+  if (bad[0] || bad[1]) return fail(ECMC_EINVAL, "phantom walk failed (%llu walks, %llu coordinates)", bad[0], bad[1]);
+  return ECMC_OK;
+}
+
 ecmc_status ecmc_g1_reset(ecmc_ctx *c) {
   if (!c) return fail(ECMC_EINVAL, "ctx is NULL");
   CU(launch_g1_snapshot(obs_params(c), c->d_g1ref, c->stream));

@@ -217,6 +217,9 @@ cudaError_t launch_obs(const ObsParams &O, cudaStream_t s);
 cudaError_t launch_wrap(double *r, int32_t *img, int64_t n, const double L[3],
                         unsigned long long *bad, cudaStream_t s);
 cudaError_t launch_g1_snapshot(const ObsParams &O, double *g1ref, cudaStream_t s);
+// phantom chains, unwrapped (k_obs.cu); bad counts walks that ran out of attempts
+cudaError_t launch_phantom(int64_t nch, int N, const double L[3], double bond, double ct,
+                           uint64_t seed, double *r, unsigned long long *bad, cudaStream_t s);
 
 // Chain structure pass (k_struct.cu): per-chain record columns
 // T = Tr S, lam1, lam2, lam3, b, c, kappa2, 4 b^2 + 3 c^2, g2 summand, |R_e|^2,

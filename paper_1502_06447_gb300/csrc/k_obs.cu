@@ -135,6 +135,66 @@ __global__ void k_lattice(int n0, int n1, int n2, double a, double jitter, uint6
   }
 }
 
+// Phantom chains (Sec. II.C, first stage of the initial configuration):
+// one thread per chain walks N beads with bond length `bond`, the first bead
+// uniform in the box, the first bond uniform on the sphere, every next bond
+// uniform on the cap t_j . t_{j+1} >= ct around the one before (cos theta =
+// 1 - u (1 - ct); the azimuth from the first point of the unit disc drawn
+// as (2u - 1, 2u' - 1), at most 256 attempts; the orthonormal pair of t_j
+// after Duff et al., "Building an orthonormal basis, revisited", JCGT 2017);
+// Philox4x64-10 key (seed, 0), counter (TAG_PHANTOM, chain, bead, attempt).
+// Writes unwrapped positions; launch_wrap folds them into the box.
+__global__ void k_phantom(int64_t nch, int N, double L0, double L1, double L2, double bond,
+                          double ct, uint64_t seed, double *r, unsigned long long *bad) {
+  const int64_t ch = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (ch >= nch) return;
+  u64x4 w = philox(TAG_PHANTOM, (uint64_t)ch, 0, 0, seed, 0);
+  double p0 = unit53(w.v[0]) * L0, p1 = unit53(w.v[1]) * L1, p2 = unit53(w.v[2]) * L2;
+  double t0 = 0.0, t1 = 0.0, t2 = 1.0;
+  double *rc = r + 3 * ch * N;
+  rc[0] = p0;
+  rc[1] = p1;
+  rc[2] = p2;
+  for (int j = 1; j < N; ++j) {
+    const double ctj = j == 1 ? -1.0 : ct;
+    w = philox(TAG_PHANTOM, (uint64_t)ch, (uint64_t)j, 0, seed, 0);
+    const double cth = 1.0 - unit53(w.v[0]) * (1.0 - ctj);
+    double x = 2.0 * unit53(w.v[1]) - 1.0, y = 2.0 * unit53(w.v[2]) - 1.0;
+    double s = x * x + y * y;
+    for (uint64_t att = 1; !(s > 0.0 && s <= 1.0); ++att) {
+      if (att == 256) {
+        atomicAdd(bad, 1ull);
+        return;
+      }
+      w = philox(TAG_PHANTOM, (uint64_t)ch, (uint64_t)j, att, seed, 0);
+      x = 2.0 * unit53(w.v[0]) - 1.0;
+      y = 2.0 * unit53(w.v[1]) - 1.0;
+      s = x * x + y * y;
+    }
+    const double sq = sqrt(s);
+    const double cph = x / sq, sph = y / sq;
+    const double sth = sqrt(1.0 - cth * cth);
+    const double sg = t2 >= 0.0 ? 1.0 : -1.0;
+    const double aa = -1.0 / (sg + t2);
+    const double bb = t0 * t1 * aa;
+    const double e10 = 1.0 + sg * t0 * t0 * aa, e11 = sg * bb, e12 = -sg * t0;
+    const double e20 = bb, e21 = sg + t1 * t1 * aa, e22 = -t1;
+    const double n0 = cth * t0 + sth * (cph * e10 + sph * e20);
+    const double n1 = cth * t1 + sth * (cph * e11 + sph * e21);
+    const double n2 = cth * t2 + sth * (cph * e12 + sph * e22);
+    const double q = sqrt(n0 * n0 + n1 * n1 + n2 * n2);
+    t0 = n0 / q;
+    t1 = n1 / q;
+    t2 = n2 / q;
+    p0 = p0 + bond * t0;
+    p1 = p1 + bond * t1;
+    p2 = p2 + bond * t2;
+    rc[3 * j] = p0;
+    rc[3 * j + 1] = p1;
+    rc[3 * j + 2] = p2;
+  }
+}
+
 // wrap caller positions into [0, L) and fold whole boxes into the image
 // counters (the host-side rule, same FP64 operations); counts non-finite
 // coordinates
@@ -163,6 +223,12 @@ cudaError_t launch_wrap(double *r, int32_t *img, int64_t n, const double L[3],
                         unsigned long long *bad, cudaStream_t s) {
   const int64_t n3 = 3 * n;
   if (n3 > 0) k_wrap<<<(unsigned)((n3 + 255) / 256), 256, 0, s>>>(r, img, n3, L[0], L[1], L[2], bad);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_phantom(int64_t nch, int N, const double L[3], double bond, double ct,
+                           uint64_t seed, double *r, unsigned long long *bad, cudaStream_t s) {
+  if (nch > 0) k_phantom<<<(unsigned)((nch + 127) / 128), 128, 0, s>>>(nch, N, L[0], L[1], L[2], bond, ct, seed, r, bad);
   return cudaGetLastError();
 }
 

@@ -31,6 +31,7 @@ EXPORTS = (
     "ecmc_cells_static", "ecmc_batch_create", "ecmc_batch_destroy", "ecmc_batch_configure",
     "ecmc_batch_run", "ecmc_batch_get_positions", "ecmc_batch_info", "ecmc_batch_stats",
     "ecmc_batch_records", "ecmc_autotune", "ecmc_batch_autotune", "ecmc_structure",
+    "ecmc_phantom_chains",
 )
 
 
@@ -136,6 +137,8 @@ def load(path: str = LIB_PATH):
             "ecmc_autotune": [vp, C.c_double, C.c_uint64, C.c_int32, P(Tuning)],
             "ecmc_batch_autotune": [vp, C.c_double, C.c_uint64, C.c_int32, P(Tuning)],
             "ecmc_structure": [vp, P(Struct), vp, C.c_double, C.c_int64, vp],
+            "ecmc_phantom_chains": [P(C.c_double), C.c_int64, C.c_int32, C.c_double, C.c_double,
+                                    C.c_uint64, P(C.c_double), P(C.c_int32)],
         }
         for name, args in sig.items():
             f = getattr(lib, name)
@@ -191,6 +194,19 @@ class Tuning(C.Structure):
 class ReplicaSpec(C.Structure):
     _fields_ = [("dims", C.c_int32 * 3), ("spacing", C.c_double), ("N", C.c_int32),
                 ("sigma", C.c_double), ("b_max", C.c_double)]
+
+
+def phantom_chains(L, n_chains, N, bond=1.0, c=1.9, seed=0):
+    """Phantom chains (ecmc_phantom_chains): wrapped positions (n x 3) and
+    image counters of n_chains non-reversal random walks of N beads."""
+    n = int(n_chains) * int(N)
+    r = np.zeros((n, 3), dtype=np.float64)
+    img = np.zeros((n, 3), dtype=np.int32)
+    Lc = np.ascontiguousarray(L, dtype=np.float64)
+    _check(load().ecmc_phantom_chains(_p(Lc, C.c_double), int(n_chains), int(N), float(bond),
+                                      float(c), int(seed) & (2**64 - 1), _p(r, C.c_double),
+                                      _p(img, C.c_int32)))
+    return r, img
 
 
 class Context:
