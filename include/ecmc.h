@@ -178,6 +178,29 @@ typedef struct ecmc_event {
 ecmc_status ecmc_phantom_chains(const double L[3], int64_t n_chains, int32_t N, double bond,
                                 double c, uint64_t seed, double *xyz_out, int32_t *img_out);
 
+/* Slow push-off (Sec. II.C).  ecmc_create_phantom makes a context whose
+ * beads are phantom chains (as ecmc_phantom_chains: n_chains x N beads,
+ * bond length `bond` <= b_max, stiffness c, key (seed, 0)) in the periodic
+ * box; they may overlap, so ecmc_run refuses it (ECMC_EOVERLAP) until
+ * ecmc_pushoff (or a valid ecmc_set_positions) has resolved it.
+ * ecmc_pushoff grows the hard-sphere diameter from f0 sigma to sigma in
+ * `stages` equal steps, d_k = sigma (f0 + (1 - f0) k / stages), d_stages =
+ * sigma; at every diameter it repeats domain sweeps (the configured tiles;
+ * needs the domain mode, ECMC_PREC_FP64 and 4-32 lanes) in which every tile
+ * runs one EC of length ell from each of its motile beads that overlaps
+ * another bead (|r_ij|^2 < d^2 (1 - 1e-10)), in bead id order, with the
+ * direction draw of EC e as in ecmc_run and the pivot ignoring the beads it
+ * overlaps, until no overlap is left.  Sweeps continue the context's sweep
+ * count (Philox counters as in ecmc_run with `seed`); swaps are off.
+ * *sweeps_out (may be NULL) receives the sweeps run.  ECMC_ESTUCK if a
+ * diameter is not resolved within max_sweeps sweeps; the final state is
+ * checked as ecmc_set_positions checks it. */
+ecmc_status ecmc_create_phantom(const double box[3], int64_t n_chains, int32_t N, double bond,
+                                double stiffness, uint64_t seed, double sigma, double b_max,
+                                ecmc_ctx **out);
+ecmc_status ecmc_pushoff(ecmc_ctx *ctx, double f0, int32_t stages, double ell, uint64_t seed,
+                         int64_t max_sweeps, int64_t *sweeps_out);
+
 /* ---- creation ----------------------------------------------------------
  * ecmc_create_lattice: melt on an n0 x n1 x n2 simple-cubic lattice with
  * spacing a in a periodic box L = dims * a.  Sites are visited in a 3-D

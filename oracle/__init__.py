@@ -31,6 +31,10 @@ Functions and the passage each follows:
   phantom_chains            non-reversal random walks without excluded volume,
                             the first stage of the initial configuration
                             (Sec. II.C)
+  pushoff, overlap_flags    slow push-off of overlapping chains: the
+                            diameter grows in stages, ECs start at the
+                            overlapping beads and ignore their pivot's
+                            overlaps (Sec. II.C)
 All functions are pinned by ``tests/test_oracle_pins.py``.
 """
 from __future__ import annotations
@@ -75,6 +79,7 @@ class Params(C.Structure):
         ("w", C.c_double), ("p_swap", C.c_double), ("event_cap", C.c_int64),
         ("use_cells", C.c_int32), ("ecs_per_tile", C.c_int32),
         ("seed", C.c_uint64), ("replica", C.c_uint64),
+        ("pushoff", C.c_int32), ("pad_po", C.c_int32), ("po_flag", C.c_void_p),
     ]
 
 
@@ -124,6 +129,11 @@ def _load():
             lib.orc_min_pair.argtypes = [P(Params), P(C.c_double), P(C.c_double),
                                          P(C.c_int64)]
             lib.orc_min_pair_cells.argtypes = lib.orc_min_pair.argtypes
+            lib.orc_overlap_flags.argtypes = [P(Params), P(C.c_double), C.c_double, C.c_void_p]
+            lib.orc_overlap_flags.restype = C.c_int64
+            lib.orc_pushoff.argtypes = [P(Params), P(C.c_double), P(C.c_int32), C.c_double,
+                                        C.c_int32, C.c_double, C.c_int64, C.c_int64,
+                                        P(C.c_int64), P(Stats)]
             lib.orc_phantom.argtypes = [P(C.c_double), C.c_int64, C.c_int32, C.c_double,
                                         C.c_double, C.c_uint64, P(C.c_double), P(C.c_int32)]
             lib.orc_chain_struct.argtypes = [P(Params), P(C.c_double), C.c_void_p, C.c_void_p,
@@ -286,6 +296,25 @@ class System:
 
     def unwrapped(self):
         return self.r + self.img * self.L
+
+    def overlap_flags(self, d):
+        """Beads overlapping another bead at diameter d (flags, count)."""
+        lib = _load()
+        flag = np.zeros(self.r.shape[0], dtype=np.uint8)
+        m = lib.orc_overlap_flags(C.byref(self.P), _ptr(self.r, C.c_double), float(d),
+                                  flag.ctypes.data_as(C.c_void_p))
+        return flag, int(m)
+
+    def pushoff(self, f0, stages, ell, max_sweeps, sweep0=0):
+        """Slow push-off in the domain mode with this system's tiles, seed
+        and key; returns (rc, sweeps, stats)."""
+        lib = _load()
+        st = Stats()
+        n_sw = C.c_int64(0)
+        rc = lib.orc_pushoff(C.byref(self.P), _ptr(self.r, C.c_double), _ptr(self.img, C.c_int32),
+                             float(f0), int(stages), float(ell), int(max_sweeps), int(sweep0),
+                             C.byref(n_sw), C.byref(st))
+        return rc, n_sw.value, st.as_dict()
 
     def chain_struct(self, dR=0.5, nbins=0, r2n=True):
         """Gyration tensor per chain (S_xx, S_xy, S_xz, S_yy, S_yz, S_zz),

@@ -249,6 +249,8 @@ static double hs_dist(const ctx_t *c, int64_t i, int64_t k, const double v[3],
   if (!(dv < 0.0)) return -1.0;
   double dd = fma(d2, d2, fma(d1, d1, d0 * d0));
   double sig2 = c->P.sigma * c->P.sigma;
+  /* push-off: a bead the pivot overlaps is no obstacle (Sec. II.C) */
+  if (c->P.pushoff && dd < sig2) return -1.0;
   double disc = sig2 - fma(-dv, dv, dd);
   if (!(disc > 0.0)) return -1.0;
   double x = -dv - sqrt(disc);
@@ -518,9 +520,11 @@ static void run_ec(ctx_t *c, int64_t pivot, double v[3], double ell,
   }
   st->lift_sum += lift;
   st->ecs += 1;
-  if (c->digest) c->digest[ordinal] = h;
-  if (c->ec_lift) c->ec_lift[ordinal] = lift;
-  if (c->ec_events) c->ec_events[ordinal] = nev;
+  if (ordinal >= 0) {
+    if (c->digest) c->digest[ordinal] = h;
+    if (c->ec_lift) c->ec_lift[ordinal] = lift;
+    if (c->ec_events) c->ec_events[ordinal] = nev;
+  }
 }
 
 /* direction: {+x,+y,+z} (global balance, Sec. II), isotropic by rejection
@@ -691,6 +695,20 @@ int orc_run_domain(const orc_params *P, double *r, int32_t *img, int64_t sweep0,
       tl.corner[0] = c.shift[0] + kx * c.T[0];
       tl.corner[1] = c.shift[1] + ky * c.T[1];
       tl.corner[2] = c.shift[2] + kz * c.T[2];
+      if (P->pushoff) {
+        /* one EC from every flagged motile bead, in bead id order; the
+         * direction is EC e's usual draw */
+        int e = 0;
+        for (int64_t q = cnt[t]; q < cnt[t + 1] && st->status == 0; ++q) {
+          if (!P->po_flag[list[q]]) continue;
+          int64_t idx;
+          double v[3];
+          draw_start(&c, TAG_START | ((uint64_t)e << 8), sweep, (uint64_t)t, m, &idx, v);
+          run_ec(&c, list[q], v, ell, &tl, (uint64_t)e, sweep, (uint64_t)t, -1);
+          ++e;
+        }
+        continue;
+      }
       for (int e = 0; e < k && st->status == 0; ++e) {
         int64_t idx;
         double v[3];
@@ -1058,4 +1076,127 @@ int orc_phantom(const double L[3], int64_t nch, int32_t N, double bond, double c
     img[i] = (int32_t)f;
   }
   return 0;
+}
+
+/*
+ * Beads that overlap another bead at diameter d: |r_i - r_k|^2 <
+ * d^2 (1 - 1e-10), minimum image, squared length summed as
+ * d0 d0 + d1 d1 + d2 d2.  A grid of cells no narrower than d (all pairs
+ * when an axis has fewer than three cells).  flag[i] = 1 or 0; returns the
+ * number flagged.
+ */
+int64_t orc_overlap_flags(const orc_params *P, const double *r, double d, uint8_t *flag) {
+  const double thr = d * d * (1.0 - 1e-10);
+  int nc[3];
+  int cells = 1;
+  for (int a = 0; a < 3; ++a) {
+    nc[a] = (int)floor(P->L[a] / d);
+    if (nc[a] > 256) nc[a] = 256;
+    if (nc[a] < 3) cells = 0;
+  }
+  for (int64_t i = 0; i < P->n; ++i) flag[i] = 0;
+  if (!cells) {
+    for (int64_t i = 0; i < P->n; ++i)
+      for (int64_t k = i + 1; k < P->n; ++k) {
+        double dd = 0.0;
+        for (int a = 0; a < 3; ++a) {
+          const double x = minimg(r[3 * i + a] - r[3 * k + a], P->L[a]);
+          dd += x * x;
+        }
+        if (dd < thr) flag[i] = flag[k] = 1;
+      }
+  } else {
+    const int64_t ncell = (int64_t)nc[0] * nc[1] * nc[2];
+    int64_t *start = (int64_t *)calloc((size_t)ncell + 1, sizeof(int64_t));
+    int64_t *order = (int64_t *)malloc(sizeof(int64_t) * (size_t)P->n);
+    int64_t *cellof = (int64_t *)malloc(sizeof(int64_t) * (size_t)P->n);
+    for (int64_t i = 0; i < P->n; ++i) {
+      int64_t ci = 0;
+      for (int a = 2; a >= 0; --a) {
+        int x = (int)floor(r[3 * i + a] / (P->L[a] / nc[a]));
+        if (x < 0) x = 0;
+        if (x >= nc[a]) x = nc[a] - 1;
+        ci = ci * nc[a] + x;
+      }
+      cellof[i] = ci;
+      start[ci + 1] += 1;
+    }
+    for (int64_t c = 0; c < ncell; ++c) start[c + 1] += start[c];
+    {
+      int64_t *fill = (int64_t *)malloc(sizeof(int64_t) * (size_t)ncell);
+      memcpy(fill, start, sizeof(int64_t) * (size_t)ncell);
+      for (int64_t i = 0; i < P->n; ++i) order[fill[cellof[i]]++] = i;
+      free(fill);
+    }
+    for (int64_t i = 0; i < P->n; ++i) {
+      const int64_t ci = cellof[i];
+      const int cx = (int)(ci % nc[0]), cy = (int)((ci / nc[0]) % nc[1]), cz = (int)(ci / ((int64_t)nc[0] * nc[1]));
+      for (int dz = -1; dz <= 1 && !flag[i]; ++dz)
+        for (int dy = -1; dy <= 1 && !flag[i]; ++dy)
+          for (int dx = -1; dx <= 1 && !flag[i]; ++dx) {
+            const int x = (cx + dx + nc[0]) % nc[0], y = (cy + dy + nc[1]) % nc[1], z = (cz + dz + nc[2]) % nc[2];
+            const int64_t cj = ((int64_t)z * nc[1] + y) * nc[0] + x;
+            for (int64_t q = start[cj]; q < start[cj + 1]; ++q) {
+              const int64_t k = order[q];
+              if (k == i) continue;
+              double dd = 0.0;
+              for (int a = 0; a < 3; ++a) {
+                const double y2 = minimg(r[3 * i + a] - r[3 * k + a], P->L[a]);
+                dd += y2 * y2;
+              }
+              if (dd < thr) {
+                flag[i] = 1;
+                break;
+              }
+            }
+          }
+    }
+    free(start);
+    free(order);
+    free(cellof);
+  }
+  int64_t m = 0;
+  for (int64_t i = 0; i < P->n; ++i) m += flag[i];
+  return m;
+}
+
+/*
+ * Slow push-off (Sec. II.C): from chains that may overlap (phantom chains),
+ * grow the hard-sphere diameter from f0 sigma to sigma in `stages` equal
+ * steps, d_k = sigma (f0 + (1 - f0) k / stages) and d_stages = sigma; at
+ * every diameter, repeat domain sweeps (tiles and shifts as in the EC run,
+ * swaps off) whose ECs start at the beads that overlap, one EC each, and
+ * whose pivot ignores the beads it overlaps, until no overlap is left.
+ * Sweeps are numbered from sweep0; *sweeps_out receives their number.
+ * ORC_ESTUCK when a diameter is not resolved within max_sweeps sweeps.
+ */
+int orc_pushoff(const orc_params *P0, double *r, int32_t *img, double f0, int32_t stages,
+                double ell, int64_t max_sweeps, int64_t sweep0, int64_t *sweeps_out,
+                orc_stats *st) {
+  if (!(f0 > 0.0 && f0 <= 1.0) || stages < 1 || max_sweeps < 1) return ORC_EINVAL;
+  orc_params P = *P0;
+  P.mode = ORC_DOMAIN;
+  P.pushoff = 1;
+  P.p_swap = 0.0;
+  uint8_t *flag = (uint8_t *)malloc((size_t)P.n);
+  P.po_flag = flag;
+  int64_t sweeps = 0;
+  int rc = 0;
+  for (int32_t k = 0; k <= stages && rc == 0; ++k) {
+    const double d = k == stages ? P0->sigma : P0->sigma * (f0 + (1.0 - f0) * (double)k / (double)stages);
+    P.sigma = d;
+    for (int64_t s = 0;; ++s) {
+      if (orc_overlap_flags(&P, r, d, flag) == 0) break;
+      if (s == max_sweeps) {
+        rc = ORC_ESTUCK;
+        break;
+      }
+      rc = orc_run_domain(&P, r, img, sweep0 + sweeps, 1, ell, st, NULL, NULL, NULL, NULL, 0, NULL);
+      ++sweeps;
+      if (rc) break;
+    }
+  }
+  free(flag);
+  *sweeps_out = sweeps;
+  return rc;
 }

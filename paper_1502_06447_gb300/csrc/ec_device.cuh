@@ -64,11 +64,15 @@ __device__ __forceinline__ int step_i(double &r, double x, double v, double L) {
 // Hard-sphere contact (Eq. 1, R2 = sigma^2) or tether limit (R2 = b_max^2)
 // of a pivot moving along v, d = pivot - partner.  Returns x >= 0, or -1 when
 // a contact candidate misses; dv = d.v.
+// (skip_overlap: a hard sphere the pivot overlaps is no obstacle, the
+// push-off rule of Sec. II.C)
 __device__ __forceinline__ double quad_x(bool tether, double d0, double d1, double d2, double v0,
-                                         double v1, double v2, double R2, double &dv) {
+                                         double v1, double v2, double R2, double &dv,
+                                         bool skip_overlap = false) {
   dv = __fma_rn(d2, v2, __fma_rn(d1, v1, d0 * v0));
   if (!tether && !neg(dv)) return -1.0;
   const double dd = __fma_rn(d2, d2, __fma_rn(d1, d1, d0 * d0));
+  if (!tether && skip_overlap && dd < R2) return -1.0;
   double rad = R2 - __fma_rn(-dv, dv, dd);
   if (tether) {
     if (neg(rad)) rad = 0.0;

@@ -98,6 +98,11 @@ struct ecmc_ctx {
   double *d_ssum = nullptr, *d_g2ref = nullptr;
   unsigned long long *d_shist = nullptr;
   int64_t shist_n = 0;
+  // slow push-off: overlap flags and their count; a context made from
+  // phantom chains may overlap until ecmc_pushoff has resolved it
+  uint8_t *d_po_flag = nullptr;
+  unsigned long long *d_po_cnt = nullptr;
+  bool pushoff_pending = false;
   // records
   uint64_t *d_rdig = nullptr;
   double *d_rlift = nullptr;
@@ -295,7 +300,7 @@ void destroy(ecmc_ctx *c) {
                   c->d_bsum, c->d_cr, c->d_crf, c->d_rf, c->d_cid, c->d_ctag, c->d_cnt, c->d_sums, c->d_status,
                   c->d_unit_next, c->d_n_deferred, c->d_deferred, c->d_obs_d, c->d_obs_u, c->d_g1ref, c->d_rdig, c->d_rlift, c->d_rev,
                   c->d_log, c->d_log_n, c->d_scratch, c->d_su, c->d_srec, c->d_spart,
-                  c->d_sr2n, c->d_ssum, c->d_g2ref, c->d_shist};
+                  c->d_sr2n, c->d_ssum, c->d_g2ref, c->d_shist, c->d_po_flag, c->d_po_cnt};
   for (void *p : ptrs) cudaFree(p);
   for (cudaEvent_t e : c->kev) cudaEventDestroy(e);
   if (c->ev0) cudaEventDestroy(c->ev0);
@@ -451,7 +456,9 @@ ecmc_status ecmc_set_positions(ecmc_ctx *c, const double *xyz, const int32_t *im
   CU(cudaStreamSynchronize(c->stream));
   c->g1_set = false;
   if (bad) return fail(ECMC_EINVAL, "%llu non-finite coordinates", bad);
-  return check_state(c);
+  ecmc_status st = check_state(c);
+  if (st == ECMC_OK) c->pushoff_pending = false;
+  return st;
 }
 
 ecmc_status ecmc_get_positions(ecmc_ctx *c, double *xyz, int32_t *img) {
@@ -726,6 +733,7 @@ ecmc_status ecmc_run(ecmc_ctx *c, double ell, int64_t chains_per_sweep, uint64_t
                      int64_t n_sweeps) {
   if (!c) return fail(ECMC_EINVAL, "ctx is NULL");
   if (!c->configured) return fail(ECMC_EINVAL, "call ecmc_configure first");
+  if (c->pushoff_pending) return fail(ECMC_EOVERLAP, "phantom chains overlap: run ecmc_pushoff first");
   if (!(ell >= 0.0) || !isfinite(ell)) return fail(ECMC_EINVAL, "ell must be finite and >= 0");
   const bool domain = c->opts.mode == ECMC_MODE_DOMAIN;
   const int64_t ntile = (int64_t)c->opts.tiles[0] * c->opts.tiles[1] * c->opts.tiles[2];
@@ -935,6 +943,103 @@ ecmc_status ecmc_phantom_chains(const double L[3], int64_t n_chains, int32_t N, 
   if (e != cudaSuccess) return fail(ECMC_ECUDA, "%s", cudaGetErrorString(e));
   if (bad[0] || bad[1]) return fail(ECMC_EINVAL, "phantom walk failed (%llu walks, %llu coordinates)", bad[0], bad[1]);
   return ECMC_OK;
+}
+
+ecmc_status ecmc_create_phantom(const double box[3], int64_t n_chains, int32_t N, double bond,
+                                double stiffness, uint64_t seed, double sigma, double b_max,
+                                ecmc_ctx **out) {
+  if (!out || !box) return fail(ECMC_EINVAL, "NULL argument");
+  *out = nullptr;
+  for (int a = 0; a < 3; ++a)
+    if (!(box[a] > 0.0 && box[a] < INFINITY)) return fail(ECMC_EINVAL, "box must be positive and finite");
+  if (n_chains < 1 || N < 1 || n_chains >= ((int64_t)1 << 29) / N)
+    return fail(ECMC_EINVAL, "need n_chains >= 1, N >= 1 and fewer than 2^29 beads");
+  if (!(sigma > 0.0)) return fail(ECMC_EINVAL, "sigma must be > 0");
+  if (!(b_max >= sigma)) return fail(ECMC_EINVAL, "b_max must be >= sigma");
+  if (!(bond > 0.0 && bond <= b_max)) return fail(ECMC_EINVAL, "bond must be in (0, b_max]");
+  if (!(stiffness >= 1.0 && stiffness < INFINITY)) return fail(ECMC_EINVAL, "stiffness c must be >= 1");
+  ecmc_ctx *c = new ecmc_ctx();
+  c->n = n_chains * N;
+  c->N = N;
+  for (int a = 0; a < 3; ++a) c->L[a] = box[a];
+  c->sigma = sigma;
+  c->b_max = b_max;
+  ecmc_status s = alloc_state(c);
+  if (s != ECMC_OK) {
+    destroy(c);
+    return s;
+  }
+  const double ct = (stiffness - 3.0) / (stiffness + 1.0);
+  unsigned long long bad[2] = {0, 0};
+  cudaError_t e = cudaMemsetAsync(c->d_obs_u + 6, 0, 2 * sizeof(unsigned long long), c->stream);
+  if (e == cudaSuccess) e = launch_phantom(n_chains, N, c->L, bond, ct, seed, c->d_r, c->d_obs_u + 6, c->stream);
+  if (e == cudaSuccess) e = launch_wrap(c->d_r, c->d_img, c->n, c->L, c->d_obs_u + 7, c->stream);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(bad, c->d_obs_u + 6, sizeof(bad), cudaMemcpyDeviceToHost, c->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess || bad[0] || bad[1]) {
+    destroy(c);
+    if (e != cudaSuccess) return fail(ECMC_ECUDA, "phantom chains: %s", cudaGetErrorString(e));
+    return fail(ECMC_EINVAL, "phantom walk failed");
+  }
+  c->pushoff_pending = true;
+  *out = c;
+  return ECMC_OK;
+}
+
+ecmc_status ecmc_pushoff(ecmc_ctx *c, double f0, int32_t stages, double ell, uint64_t seed,
+                         int64_t max_sweeps, int64_t *sweeps_out) {
+  if (!c) return fail(ECMC_EINVAL, "ctx is NULL");
+  if (sweeps_out) *sweeps_out = 0;
+  if (!c->configured || c->opts.mode != ECMC_MODE_DOMAIN || c->opts.precision != ECMC_PREC_FP64 ||
+      c->lanes == 1)
+    return fail(ECMC_EINVAL, "push-off needs the domain mode, FP64 and 4-32 lanes per tile");
+  if (!(f0 > 0.0 && f0 <= 1.0) || stages < 1 || max_sweeps < 1 || !(ell >= 0.0 && ell < INFINITY))
+    return fail(ECMC_EINVAL, "need 0 < f0 <= 1, stages >= 1, max_sweeps >= 1, finite ell >= 0");
+  if (!c->d_po_flag) {
+    CU(dalloc(&c->d_po_flag, c->n));
+    CU(dalloc(&c->d_po_cnt, 1));
+  }
+  CU(cudaMemsetAsync(c->d_status, 0, sizeof(int), c->stream));
+  ECParams P = ec_params(c, seed, ell);
+  const int64_t ntile = (int64_t)c->opts.tiles[0] * c->opts.tiles[1] * c->opts.tiles[2];
+  P.n_units = (int32_t)ntile;
+  P.ecs_per_tile = 1;
+  P.swap_mode = 0;
+  P.p_swap = 0.0;
+  P.po_flag = c->d_po_flag;
+  const ObsParams O = obs_params(c);
+  int64_t sweeps = 0;
+  for (int32_t k = 0; k <= stages; ++k) {
+    const double d =
+        k == stages ? c->sigma : c->sigma * (f0 + (1.0 - f0) * (double)k / (double)stages);
+    P.sigma = d;
+    P.sig2 = d * d;
+    const double thr = d * d * (1.0 - 1e-10);
+    for (int64_t s = 0;; ++s) {
+      const int64_t sweep = c->sweeps_done;
+      CU(launch_cells(cell_params(c, true, seed, sweep), c->ncell, c->stream));
+      CU(launch_po_flags(O, thr, c->d_po_flag, c->d_po_cnt, c->stream));
+      unsigned long long cnt = 0;
+      CU(cudaMemcpyAsync(&cnt, c->d_po_cnt, sizeof(cnt), cudaMemcpyDeviceToHost, c->stream));
+      CU(cudaStreamSynchronize(c->stream));
+      if (cnt == 0) break;
+      if (s == max_sweeps) {
+        if (sweeps_out) *sweeps_out = sweeps;
+        return fail(ECMC_ESTUCK, "push-off: %llu beads overlap at diameter %.6g after %lld sweeps",
+                    cnt, d, (long long)max_sweeps);
+      }
+      P.sweep = sweep;
+      CU(timed_ec(c, P, 0));
+      ecmc_status st = device_status(c);
+      if (st != ECMC_OK) return st;
+      c->sweeps_done += 1;
+      ++sweeps;
+    }
+  }
+  if (sweeps_out) *sweeps_out = sweeps;
+  ecmc_status st = check_state(c);
+  if (st == ECMC_OK) c->pushoff_pending = false;
+  return st;
 }
 
 ecmc_status ecmc_g1_reset(ecmc_ctx *c) {

@@ -115,6 +115,10 @@ struct ECParams {
   // device counter its persistent blocks take units from (reset per launch)
   int32_t block_tiles;
   int32_t *unit_next;
+  // slow push-off (plain FP64 domain kernel): the ECs of a tile start at its
+  // flagged motile beads, one each in id order, and a pivot ignores the
+  // beads it overlaps; null otherwise
+  const uint8_t *po_flag;
   int32_t rq_per_tile;  // request list entries per tile of the block (1..6)
   // block-lockstep kernel: tight capacities for a first pass (0: none); a
   // tile that does not fit them is listed in `deferred` and run by a second
@@ -217,6 +221,9 @@ cudaError_t launch_obs(const ObsParams &O, cudaStream_t s);
 cudaError_t launch_wrap(double *r, int32_t *img, int64_t n, const double L[3],
                         unsigned long long *bad, cudaStream_t s);
 cudaError_t launch_g1_snapshot(const ObsParams &O, double *g1ref, cudaStream_t s);
+// beads overlapping another at |d|^2 < thr (cell list of O), as 0/1 flags
+cudaError_t launch_po_flags(const ObsParams &O, double thr, uint8_t *flag,
+                            unsigned long long *count, cudaStream_t s);
 // phantom chains, unwrapped (k_obs.cu); bad counts walks that ran out of attempts
 cudaError_t launch_phantom(int64_t nch, int N, const double L[3], double bond, double ct,
                            uint64_t seed, double *r, unsigned long long *bad, cudaStream_t s);

@@ -128,8 +128,18 @@ __global__ void __launch_bounds__(128) ec_kernel(const ECParams P) {
   unsigned long long tried = 0, confirmed = 0, nev_all = 0, ecs_done = 0;
   constexpr int ITEMS = G >= 8 ? 1 : 2;  // special candidates per lane
 
-  for (int e = 0; e < n_ec; ++e) {
-    bool active = live && m > 0;
+  // push-off: one EC from every flagged motile bead of the tile, in id order
+  int n_ec_g = n_ec;
+  if (P.po_flag) {
+    int f = 0;
+    for (int s = gl; s < m; s += G) f += P.po_flag[st.id[s]] ? 1 : 0;
+#pragma unroll
+    for (int off = G / 2; off > 0; off >>= 1) f += __shfl_xor_sync(FULL, f, off);
+    n_ec_g = live ? f : 0;
+  }
+  const int n_ec_run = P.po_flag ? __reduce_max_sync(FULL, n_ec_g) : n_ec;
+  for (int e = 0; e < n_ec_run; ++e) {
+    bool active = live && m > 0 && e < n_ec_g;
     const uint64_t r0 = P.domain ? (TAG_START | ((uint64_t)e << 8)) : TAG_START;
     const uint64_t r1 = P.domain ? (uint64_t)sweep : 0;
     const uint64_t r2 = P.domain ? (uint64_t)unit : (uint64_t)(sweep + e);
@@ -138,6 +148,17 @@ __global__ void __launch_bounds__(128) ec_kernel(const ECParams P) {
     if (active) {
       u64x4 w = philox(r0, r1, r2, 0, P.seed, Rkey);
       p = (int)scale_below(w.v[0], (uint64_t)m);
+      if (P.po_flag) {
+        // the e-th flagged motile slot (slots are in id order)
+        for (int s = 0, f = 0; s < m; ++s) {
+          if (!P.po_flag[st.id[s]]) continue;
+          if (f == e) {
+            p = s;
+            break;
+          }
+          ++f;
+        }
+      }
       if (P.dir_mode == ECMC_DIR_CART3) {
         const int ax = (int)scale_below(w.v[1], 3);
         v0 = ax == 0 ? 1.0 : 0.0;
@@ -304,7 +325,8 @@ __global__ void __launch_bounds__(128) ec_kernel(const ECParams P) {
               double dv;
               const double x = quad_x(false, wrapc(q0 - st.px[k], SYS(L)[0], hb0, wr0),
                                       wrapc(q1 - st.py[k], SYS(L)[1], hb1, wr1),
-                                      wrapc(q2 - st.pz[k], SYS(L)[2], hb2, wr2), v0, v1, v2, P.sig2, dv);
+                                      wrapc(q2 - st.pz[k], SYS(L)[2], hb2, wr2), v0, v1, v2, P.sig2, dv,
+                                      P.po_flag != nullptr);
               if (!neg(x)) {
                 const uint64_t key = make_key(KIND_HS, st.id[k], k);
                 if (better(x, key, bx, bkey)) {

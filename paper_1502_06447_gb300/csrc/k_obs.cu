@@ -135,6 +135,38 @@ __global__ void k_lattice(int n0, int n1, int n2, double a, double jitter, uint6
   }
 }
 
+// beads that overlap another bead (|d|^2 < thr, minimum image, squared
+// length (d0 d0 + d1 d1) + d2 d2) through the cell list: flag 0/1 per bead
+// and their number (the push-off's start beads, Sec. II.C)
+__global__ void k_po_flags(const ObsParams O, double thr, uint8_t *flag, unsigned long long *count) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= O.n) return;
+  const int c = O.cell[i];
+  const int cx = c % O.nc[0], cy = (c / O.nc[0]) % O.nc[1], cz = c / (O.nc[0] * O.nc[1]);
+  const double p0 = O.r[3 * i], p1 = O.r[3 * i + 1], p2 = O.r[3 * i + 2];
+  uint8_t f = 0;
+  for (int dz = -1; dz <= 1 && !f; ++dz)
+    for (int dy = -1; dy <= 1 && !f; ++dy)
+      for (int dx = -1; dx <= 1 && !f; ++dx) {
+        const int x = (cx + dx + O.nc[0]) % O.nc[0];
+        const int y = (cy + dy + O.nc[1]) % O.nc[1];
+        const int z = (cz + dz + O.nc[2]) % O.nc[2];
+        const int cc = (z * O.nc[1] + y) * O.nc[0] + x;
+        for (int j = O.cstart[cc]; j < O.cstart[cc + 1]; ++j) {
+          if (O.cid[j] == i) continue;
+          const double d0 = wrap_d(p0 - O.cr[3 * (int64_t)j], O.L[0], O.half[0]);
+          const double d1 = wrap_d(p1 - O.cr[3 * (int64_t)j + 1], O.L[1], O.half[1]);
+          const double d2 = wrap_d(p2 - O.cr[3 * (int64_t)j + 2], O.L[2], O.half[2]);
+          if ((d0 * d0 + d1 * d1) + d2 * d2 < thr) {
+            f = 1;
+            break;
+          }
+        }
+      }
+  flag[i] = f;
+  if (f) atomicAdd(count, 1ull);
+}
+
 // Phantom chains (Sec. II.C, first stage of the initial configuration):
 // one thread per chain walks N beads with bond length `bond`, the first bead
 // uniform in the box, the first bond uniform on the sphere, every next bond
@@ -223,6 +255,14 @@ cudaError_t launch_wrap(double *r, int32_t *img, int64_t n, const double L[3],
                         unsigned long long *bad, cudaStream_t s) {
   const int64_t n3 = 3 * n;
   if (n3 > 0) k_wrap<<<(unsigned)((n3 + 255) / 256), 256, 0, s>>>(r, img, n3, L[0], L[1], L[2], bad);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_po_flags(const ObsParams &O, double thr, uint8_t *flag,
+                            unsigned long long *count, cudaStream_t s) {
+  cudaError_t e = cudaMemsetAsync(count, 0, sizeof(unsigned long long), s);
+  if (e != cudaSuccess) return e;
+  if (O.n > 0) k_po_flags<<<(unsigned)((O.n + 255) / 256), 256, 0, s>>>(O, thr, flag, count);
   return cudaGetLastError();
 }
 

@@ -31,7 +31,7 @@ EXPORTS = (
     "ecmc_cells_static", "ecmc_batch_create", "ecmc_batch_destroy", "ecmc_batch_configure",
     "ecmc_batch_run", "ecmc_batch_get_positions", "ecmc_batch_info", "ecmc_batch_stats",
     "ecmc_batch_records", "ecmc_autotune", "ecmc_batch_autotune", "ecmc_structure",
-    "ecmc_phantom_chains",
+    "ecmc_phantom_chains", "ecmc_create_phantom", "ecmc_pushoff",
 )
 
 
@@ -139,6 +139,10 @@ def load(path: str = LIB_PATH):
             "ecmc_structure": [vp, P(Struct), vp, C.c_double, C.c_int64, vp],
             "ecmc_phantom_chains": [P(C.c_double), C.c_int64, C.c_int32, C.c_double, C.c_double,
                                     C.c_uint64, P(C.c_double), P(C.c_int32)],
+            "ecmc_create_phantom": [P(C.c_double), C.c_int64, C.c_int32, C.c_double, C.c_double,
+                                    C.c_uint64, C.c_double, C.c_double, P(vp)],
+            "ecmc_pushoff": [vp, C.c_double, C.c_int32, C.c_double, C.c_uint64, C.c_int64,
+                             P(C.c_int64)],
         }
         for name, args in sig.items():
             f = getattr(lib, name)
@@ -229,6 +233,23 @@ class Context:
                                           int(seed) & (2**64 - 1), int(N), float(sigma),
                                           float(b_max), C.byref(h)))
         return cls(h)
+
+    @classmethod
+    def create_phantom(cls, box, n_chains, N, bond=1.0, c=1.9, seed=0, sigma=1.0, b_max=1.2):
+        """Context of phantom chains (they may overlap until pushoff())."""
+        h = C.c_void_p()
+        b = np.ascontiguousarray(box, dtype=np.float64)
+        _check(load().ecmc_create_phantom(_p(b, C.c_double), int(n_chains), int(N), float(bond),
+                                          float(c), int(seed) & (2**64 - 1), float(sigma),
+                                          float(b_max), C.byref(h)))
+        return cls(h)
+
+    def pushoff(self, f0=0.5, stages=5, ell=2.0, seed=0, max_sweeps=1000):
+        """Slow push-off (ecmc_pushoff); returns the number of sweeps run."""
+        n = C.c_int64(0)
+        _check(load().ecmc_pushoff(self._h, float(f0), int(stages), float(ell),
+                                   int(seed) & (2**64 - 1), int(max_sweeps), C.byref(n)))
+        return n.value
 
     @classmethod
     def create(cls, phi, n_chains, N, sigma=1.0, b_max=1.2, box=None):
