@@ -1007,6 +1007,27 @@ ecmc_status ecmc_pushoff(ecmc_ctx *c, double f0, int32_t stages, double ell, uin
   P.swap_mode = 0;
   P.p_swap = 0.0;
   P.po_flag = c->d_po_flag;
+  {
+    // phantom chains are far more clustered than a melt (a tile's content
+    // varies about three times as much): stage up to 2.5 times the mean
+    // content plus 64 (capacities change no event)
+    const double rho = (double)c->n / (c->L[0] * c->L[1] * c->L[2]);
+    double vol = 1.0;
+    for (int a = 0; a < 3; ++a) vol *= c->W[a] + 2.0 * c->halo_te;
+    int64_t S = (int64_t)ceil(2.5 * rho * vol + 64.0);
+    S = (S + 31) / 32 * 32;
+    if (S < c->stage_cap) S = c->stage_cap;
+    if (S > 65504) S = 65504;
+    int dev = 0, smem_max = 0;
+    CU(cudaGetDevice(&dev));
+    CU(cudaDeviceGetAttribute(&smem_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+    const int ncl = c->lg[0] * c->lg[1] * c->lg[2];
+    if (ec_smem_bytes((int)S, (int)S, ncl, 32 / c->lanes) > (size_t)smem_max)
+      return fail(ECMC_EINVAL, "push-off staging of %lld beads per tile does not fit in shared memory "
+                  "(use smaller tiles or more lanes)", (long long)S);
+    P.stage_cap = (int32_t)S;
+    P.m_cap = (int32_t)S;
+  }
   const ObsParams O = obs_params(c);
   int64_t sweeps = 0;
   for (int32_t k = 0; k <= stages; ++k) {
