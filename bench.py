@@ -233,6 +233,7 @@ def run_gpu(args, rank, world):
         "note": "pressure_lift is the lift-distance estimator (biased in the domain mode); "
                 "pressure_contact the contact-value estimator of the final state"}
     structure = structure_run(ctx, stream)
+    init = init_run()
 
     # plain FP64 kernel on the same workload (fresh lattice, same calibration)
     ctx64, tune64 = make(ecmc.PREC_FP64)
@@ -332,6 +333,7 @@ def run_gpu(args, rank, world):
                          in (4, 8, 16) else 6) * args.steps,
         "physics": physics,
         "structure": structure,
+        "init": init,
         "clocks": clk.summary(),
         "tuning": {"fp32f": tune, "fp64": tune64},
     }
@@ -446,6 +448,38 @@ def structure_run(ctx, stream):
                     "0.754 and bc_over_trI2 = 2/3"}
 
 
+# initial configuration measured beside the EC sweeps: phantom chains of 20
+# beads (c = 1.9) at packing fraction 0.35, pushed off in 5 stages from half
+# the diameter (ECs of length 2, 3^3 tiles), as the paper builds its melts
+INIT = dict(L=20.0, n_chains=267, N=20, c=1.9, seed=51, po_seed=0xEC0F0F, f0=0.5, stages=5,
+            ell=2.0, tiles=(4, 4, 4), max_sweeps=6000)
+
+
+def init_run():
+    """Phantom chains and the slow push-off through the public API (each
+    call synchronises; wall time)."""
+    c = INIT
+    L = (c["L"],) * 3
+    t0 = time.perf_counter()
+    ctx = ecmc.Context.create_phantom(L, c["n_chains"], c["N"], bond=1.0, c=c["c"], seed=c["seed"])
+    t1 = time.perf_counter()
+    ctx.configure(mode=ecmc.MODE_DOMAIN, dir_mode=ecmc.DIR_ISO, precision=ecmc.PREC_FP64,
+                  tiles=c["tiles"], lanes=8)
+    t2 = time.perf_counter()
+    sweeps = ctx.pushoff(f0=c["f0"], stages=c["stages"], ell=c["ell"], seed=c["po_seed"],
+                         max_sweeps=c["max_sweeps"])
+    t3 = time.perf_counter()
+    got, rn, _ = ctx.structure(r2n=True)
+    o = ctx.observables()
+    n = c["n_chains"] * c["N"]
+    return {"beads": n, "eta": n * math.pi / 6 / c["L"] ** 3, "phantom_ms": 1e3 * (t1 - t0),
+            "pushoff_ms": 1e3 * (t3 - t2), "pushoff_sweeps": sweeps,
+            "overlaps": o["overlaps"], "tether_violations": o["tether_violations"],
+            "r2n_over_n": {str(k): float(rn[k] / k) for k in (1, 5, 19)},
+            "setting": "267 chains x 20 beads, c = 1.9, 20^3 box, 4^3 tiles, f0 = 0.5, 5 stages, "
+                       "ECs of length 2, plain FP64 kernel"}
+
+
 def cpu_baseline_run(max_sweeps=1, time_budget=25.0):
     """The oracle as it stands (serial FP64 C, one core) on a bounded sample:
     `max_sweeps` full sweeps of the same 10^6-bead workload."""
@@ -460,12 +494,22 @@ def cpu_baseline_run(max_sweeps=1, time_budget=25.0):
     t1 = time.perf_counter()
     o.chain_struct(dR=2.0, nbins=64)
     ds = time.perf_counter() - t1
+    c = INIT
+    L = (c["L"],) * 3
+    t2 = time.perf_counter()
+    rp, ip = oracle.phantom_chains(L, c["n_chains"], c["N"], bond=1.0, c=c["c"], seed=c["seed"])
+    po = oracle.System(rp, L, c["N"], sigma=1.0, b_max=1.2, mode=oracle.MODE_DOMAIN,
+                       dir_mode=oracle.DIR_ISO, D=c["tiles"], seed=c["po_seed"], img=ip)
+    rc, po_sweeps, _ = po.pushoff(c["f0"], c["stages"], c["ell"], c["max_sweeps"])
+    dp = time.perf_counter() - t2
     return {"value": ev / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
             "sample": f"{max_sweeps} sweep(s) of the 1e6-bead melt without swaps "
                       f"({ev} events, {dt:.1f} s)",
             "structure_ms": 1e3 * ds,
             "structure_sample": "one chain-structure pass (gyration tensors, R^2(n), W(R)) "
-                                "over the same melt"}
+                                "over the same melt",
+            "init_ms": 1e3 * dp, "init_sweeps": po_sweeps, "init_rc": rc,
+            "init_sample": "the phantom chains and push-off of the JSON line's init setting"}
 
 
 def run_reference(args, rank):
