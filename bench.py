@@ -458,6 +458,8 @@ INIT = dict(L=20.0, n_chains=267, N=20, c=1.9, seed=51, po_seed=0xEC0F0F, f0=0.5
 def init_run():
     """Phantom chains and the slow push-off through the public API (each
     call synchronises; wall time)."""
+    from paper_1502_06447_gb300 import ecmc
+
     c = INIT
     L = (c["L"],) * 3
     t0 = time.perf_counter()
