@@ -63,3 +63,20 @@ def test_pushoff_deterministic_and_stuck():
     c, _, _ = phantom_system(0.45, 10, 10.0, 42)
     rc, sweeps, _ = c.pushoff(0.9, 1, 2.0, 1)
     assert rc == -6 and sweeps == 1
+
+
+@pytest.mark.parametrize("L,d", [(12.0, 1.0), (6.0, 1.0), (12.0, 0.6), (2.5, 1.0)])
+def test_overlap_flags_brute_force(L, d):
+    """The push-off's overlap flags (cell grid, or all pairs in small boxes)
+    against a direct numpy evaluation over all minimum-image pairs."""
+    rng = np.random.default_rng(int(L * 10 + d * 100))
+    n = int(0.6 * L ** 3)
+    r = rng.uniform(0, L, (n, 3))
+    s = oracle.System(r, (L, L, L), 1, sigma=1.0, b_max=1.2)
+    flag, m = s.overlap_flags(d)
+    x = r[:, None, :] - r[None, :, :]
+    x -= L * np.round(x / L)
+    dd = (x[..., 0] * x[..., 0] + x[..., 1] * x[..., 1]) + x[..., 2] * x[..., 2]
+    np.fill_diagonal(dd, np.inf)
+    ref = (dd < d * d * (1.0 - 1e-10)).any(axis=1)
+    assert (flag.astype(bool) == ref).all() and m == ref.sum()
