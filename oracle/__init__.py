@@ -31,6 +31,8 @@ Functions and the passage each follows:
   phantom_chains            non-reversal random walks without excluded volume,
                             the first stage of the initial configuration
                             (Sec. II.C)
+  k_spring (System)         bead-spring chains: harmonic bonds with Boltzmann
+                            energies per event instead of tethers (Sec. II)
   pushoff, overlap_flags    slow push-off of overlapping chains: the
                             diameter grows in stages, ECs start at the
                             overlapping beads and ignore their pivot's
@@ -80,6 +82,7 @@ class Params(C.Structure):
         ("use_cells", C.c_int32), ("ecs_per_tile", C.c_int32),
         ("seed", C.c_uint64), ("replica", C.c_uint64),
         ("pushoff", C.c_int32), ("pad_po", C.c_int32), ("po_flag", C.c_void_p),
+        ("k_spring", C.c_double),
     ]
 
 
@@ -129,6 +132,11 @@ def _load():
             lib.orc_min_pair.argtypes = [P(Params), P(C.c_double), P(C.c_double),
                                          P(C.c_int64)]
             lib.orc_min_pair_cells.argtypes = lib.orc_min_pair.argtypes
+            lib.orc_spring_x.argtypes = [P(C.c_double), P(C.c_double), C.c_double, C.c_double,
+                                         C.c_double]
+            lib.orc_spring_x.restype = C.c_double
+            lib.orc_log.argtypes = [C.c_double]
+            lib.orc_log.restype = C.c_double
             lib.orc_overlap_flags.argtypes = [P(Params), P(C.c_double), C.c_double, C.c_void_p]
             lib.orc_overlap_flags.restype = C.c_int64
             lib.orc_pushoff.argtypes = [P(Params), P(C.c_double), P(C.c_int32), C.c_double,
@@ -175,7 +183,7 @@ class System:
     def __init__(self, r, L, N, sigma=1.0, b_max=1.2, s_cap=0.25, mode=MODE_SERIAL,
                  dir_mode=DIR_CART3, D=(1, 1, 1), w=None, p_swap=0.0,
                  event_cap=10_000_000, use_cells=1, ecs_per_tile=1, seed=0,
-                 replica=0, img=None):
+                 replica=0, img=None, k_spring=0.0):
         self.r = np.ascontiguousarray(r, dtype=np.float64).reshape(-1, 3).copy()
         self.img = (np.zeros_like(self.r, dtype=np.int32) if img is None
                     else np.ascontiguousarray(img, dtype=np.int32).reshape(-1, 3).copy())
@@ -198,6 +206,7 @@ class System:
         p.ecs_per_tile = int(ecs_per_tile)
         p.seed = int(seed) & (2**64 - 1)
         p.replica = int(replica) & (2**64 - 1)
+        p.k_spring = float(k_spring)
         self.P = p
 
     @property
@@ -347,6 +356,21 @@ def phantom_chains(L, n_chains, N, bond=1.0, c=1.9, seed=0):
     lib.orc_phantom(_ptr(Lc, C.c_double), int(n_chains), int(N), float(bond), float(c),
                     int(seed) & (2**64 - 1), _ptr(r, C.c_double), _ptr(img, C.c_int32))
     return r, img
+
+
+def spring_x(d, v, sigma, k, dE) -> float:
+    """Spring event distance of a pivot at separation d (pivot minus
+    bonded bead) moving along unit v with consumable energy dE."""
+    dd = np.ascontiguousarray(d, dtype=np.float64)
+    vv = np.ascontiguousarray(v, dtype=np.float64)
+    return float(_load().orc_spring_x(_ptr(dd, C.c_double), _ptr(vv, C.c_double), float(sigma),
+                                      float(k), float(dE)))
+
+
+def own_log(u: float) -> float:
+    """The oracle's own natural logarithm (behind the springs' Boltzmann
+    energies)."""
+    return float(_load().orc_log(float(u)))
 
 
 def seq_sum(x) -> float:

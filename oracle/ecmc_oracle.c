@@ -72,7 +72,7 @@ void orc_philox4x64_10(const uint64_t ctr[4], const uint64_t key[2],
  *   key  = (seed, replica)
  *   ctr  = (tag | ec<<8, sweep, unit, attempt)
  *   tag 1: start bead + direction; tag 2: domain shift; tag 3: swap draws */
-enum { TAG_START = 1, TAG_SHIFT = 2, TAG_SWAP = 3 };
+enum { TAG_START = 1, TAG_SHIFT = 2, TAG_SWAP = 3, TAG_SPRING = 6 };
 
 static void draw(const orc_params *P, uint64_t tag, uint64_t sweep,
                  uint64_t unit, uint64_t attempt, uint64_t out[4]) {
@@ -277,6 +277,70 @@ static double te_dist(const ctx_t *c, int64_t i, int64_t j, const double v[3],
   return x;
 }
 
+/* natural logarithm of u in (0, 1], an own routine from the textbook
+ * reduction: u = m 2^e with m in [sqrt(1/2), sqrt(2)), log u = e ln 2 +
+ * 2 atanh(z), z = (m - 1)/(m + 1) (|z| < 0.1716), atanh z / z =
+ * sum_{n=0..13} z^(2n) / (2n + 1) by Horner's rule (the first term left out
+ * is below 1e-19); ln 2 rounded to double.  Only +, -, *, / and exact bit
+ * manipulations, so that another implementation taking the same steps gets
+ * the same bits.  Within a few ulp of the correctly rounded value. */
+double orc_log(double u) {
+  uint64_t b;
+  memcpy(&b, &u, sizeof(b));
+  int e = (int)((b >> 52) & 0x7FF) - 1023;
+  const uint64_t mb = (b & 0x000FFFFFFFFFFFFFull) | 0x3FF0000000000000ull;
+  double m;
+  memcpy(&m, &mb, sizeof(m));
+  if (m > 1.4142135623730951) {
+    m = m * 0.5;
+    e += 1;
+  }
+  const double z = (m - 1.0) / (m + 1.0);
+  const double z2 = z * z;
+  double s = 1.0 / 29.0;
+  for (int n = 13; n >= 0; --n) s = s * z2 + 1.0 / (double)(2 * n + 1);
+  return (double)e * 0.6931471805599453 + 2.0 * z * s;
+}
+
+/* Harmonic spring (k/2)(b - sigma)^2 between pivot i and its bonded bead j
+ * (Sec. II, ECs with pair potentials): the pivot may move until the energy
+ * its move adds reaches dE, drawn from the Boltzmann distribution.  Hard
+ * spheres keep b >= sigma, so the energy falls while b falls and rises
+ * only after the closest approach along the path (or from the start when
+ * d.v >= 0): from the bond length b_s where it starts rising the pivot goes
+ * on until b_t = sigma + sqrt((b_s - sigma)^2 + 2 dE / k), at
+ * x = -d.v + sqrt(b_t^2 - |d_perp|^2). */
+static double spring_x(double d0, double d1, double d2, const double v[3], double sigma, double k,
+                       double dE, double *dv_out) {
+  double dv = fma(d2, v[2], fma(d1, v[1], d0 * v[0]));
+  *dv_out = dv;
+  double dd = fma(d2, d2, fma(d1, d1, d0 * d0));
+  double perp2 = fma(-dv, dv, dd);
+  if (perp2 < 0.0) perp2 = 0.0;
+  const double bs = dv < 0.0 ? sqrt(perp2) : sqrt(dd);
+  const double e = bs - sigma;
+  const double bt = sigma + sqrt(e * e + 2.0 * dE / k);
+  double x = -dv + sqrt(bt * bt - perp2);
+  if (x < 0.0) x = 0.0;
+  return x;
+}
+
+static double sp_dist(const ctx_t *c, int64_t i, int64_t j, const double v[3], double dE,
+                      double *dv_out) {
+  const double *L = c->P.L;
+  double d0 = minimg(c->r[3 * i + 0] - c->r[3 * j + 0], L[0]);
+  double d1 = minimg(c->r[3 * i + 1] - c->r[3 * j + 1], L[1]);
+  double d2 = minimg(c->r[3 * i + 2] - c->r[3 * j + 2], L[2]);
+  return spring_x(d0, d1, d2, v, c->P.sigma, c->P.k_spring, dE, dv_out);
+}
+
+/* the spring event of a pivot at separation d from its bonded bead, moving
+ * along v with consumable energy dE (for the tests) */
+double orc_spring_x(const double d[3], const double v[3], double sigma, double k, double dE) {
+  double dv;
+  return spring_x(d[0], d[1], d[2], v, sigma, k, dE, &dv);
+}
+
 static void hs_all(const ctx_t *c, int64_t i, const double v[3], cand_t *best) {
   if (c->P.use_cells) {
     int ci = c->cell[i];
@@ -420,7 +484,22 @@ static void run_ec(ctx_t *c, int64_t pivot, double v[3], double ell,
         consider(&best, x, K_WALL, a, 0.0);
       }
     }
-    if (P->N > 1) {
+    if (P->N > 1 && P->k_spring > 0.0) {
+      /* springs: a fresh Boltzmann energy for each bond at every event,
+       * dE = -log(u), u = 1 - u53 from Philox (tag 6 | ec << 8, sweep,
+       * unit, event): word 0 for the bond to i - 1, word 1 for i + 1 */
+      uint64_t w[4];
+      draw(P, TAG_SPRING | (ec << 8), sweep, unit, (uint64_t)nev, w);
+      double dv, x;
+      if (i % P->N != 0) {
+        x = sp_dist(c, i, i - 1, v, -orc_log(1.0 - u53(w[0])), &dv);
+        consider(&best, x, K_TETHER, i - 1, dv);
+      }
+      if (i % P->N != P->N - 1) {
+        x = sp_dist(c, i, i + 1, v, -orc_log(1.0 - u53(w[1])), &dv);
+        consider(&best, x, K_TETHER, i + 1, dv);
+      }
+    } else if (P->N > 1) {
       double dv, x;
       if (i % P->N != 0) {
         x = te_dist(c, i, i - 1, v, &dv);
@@ -575,6 +654,7 @@ int orc_run_serial(const orc_params *P, double *r, int32_t *img, int64_t ec0,
   if (P->n < 1 || P->N < 1 || P->n % P->N != 0 || !(P->sigma > 0.0) ||
       !(P->s_cap > 0.0) || !(ell >= 0.0))
     return ORC_EINVAL;
+  if (!(P->k_spring >= 0.0) || (P->k_spring > 0.0 && P->p_swap > 0.0)) return ORC_EINVAL;
   for (int a = 0; a < 3; ++a)
     if (!(P->s_cap + P->sigma < 0.5 * P->L[a])) return ORC_EINVAL;
   ctx_t c;
@@ -622,6 +702,21 @@ static void domain_setup(ctx_t *c, uint64_t sweep) {
     }
     c->tag[b] = in ? (k[2] * P->D[1] + k[1]) * P->D[0] + k[0] : -1;
   }
+  if (P->k_spring > 0.0 && P->N > 1) {
+    /* springs have no longest bond: a bead whose bonded bead is motile in
+     * another tile would couple the two tiles, so both wait (reading R23);
+     * decided on the tags above, then applied */
+    int8_t *drop = (int8_t *)calloc((size_t)P->n, 1);
+    for (int64_t b = 0; b < P->n; ++b) {
+      if (c->tag[b] < 0) continue;
+      const int64_t nb[2] = {b % P->N != 0 ? b - 1 : -1, b % P->N != P->N - 1 ? b + 1 : -1};
+      for (int q = 0; q < 2; ++q)
+        if (nb[q] >= 0 && c->tag[nb[q]] >= 0 && c->tag[nb[q]] != c->tag[b]) drop[b] = 1;
+    }
+    for (int64_t b = 0; b < P->n; ++b)
+      if (drop[b]) c->tag[b] = -1;
+    free(drop);
+  }
 }
 
 int orc_domain_tags(const orc_params *P, double *r, uint64_t sweep,
@@ -649,6 +744,7 @@ int orc_run_domain(const orc_params *P, double *r, int32_t *img, int64_t sweep0,
       !(P->s_cap > 0.0) || !(ell >= 0.0) || P->ecs_per_tile < 1)
     return ORC_EINVAL;
   if (!(P->w >= P->b_max) || !(P->b_max >= P->sigma)) return ORC_EINVAL;
+  if (!(P->k_spring >= 0.0) || (P->k_spring > 0.0 && P->p_swap > 0.0)) return ORC_EINVAL;
   for (int a = 0; a < 3; ++a) {
     if (P->D[a] < 1) return ORC_EINVAL;
     double T = P->L[a] / P->D[a];

@@ -54,6 +54,10 @@ typedef struct {
   int32_t pushoff;
   int32_t pad_po;
   const uint8_t *po_flag;
+  /* k > 0: bonds are harmonic springs (k/2)(b - sigma)^2 (Sec. II, bead-
+   * spring chains, k in units of kT/sigma^2) instead of tethers; b_max is
+   * then unused and swaps are off */
+  double k_spring;
 } orc_params;
 
 typedef struct {
