@@ -20,6 +20,15 @@
  *     beads is proposed and accepted by Metropolis (infinite tether walls:
  *     accept iff every bond stays <= b_max); accepted -> beads exchanged and
  *     the same pivot continues; rejected -> ordinary transfer.
+ *   - ECs with pair potentials, Sec. II (Fig. 2b): bead-spring chains, each
+ *     bond drawing a Boltzmann energy per event that the pivot's move may
+ *     spend where the bond energy rises.
+ *   - Initial configurations, Sec. II.C: phantom chains grown as
+ *     non-reversal random walks, then the slow push-off (ECs started at
+ *     overlapping beads that ignore their pivot's overlaps, the diameter
+ *     grown in stages).
+ *   - Chain structure, Sec. III and Appendix A: gyration tensor and centre
+ *     of mass, internal distances R^2(n), end-to-end distance histogram.
  * Readings where the paper is silent (the tie order, the pass event, the
  * random-number layout, the joint width) are the same as the CUDA library's
  * and are written out at each place below.
