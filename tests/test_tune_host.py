@@ -103,3 +103,56 @@ def test_tune_search_host(tmp_path):
     assert res["abort"]["st"] == str(-3) and res["abort"]["calls"] == "5"
     o = res["offgrid"]
     assert o["tile"] == "4.4" and o["trials"] != "0"
+
+
+CAPS_SRC = r"""
+#include <cmath>
+#include <cstdio>
+#include "ecmc_internal.h"
+using namespace ecmc;
+int main() {
+  // round_up_f32: the smallest float >= x
+  const double xs[] = {0.25, 0.1, 1.0 / 3.0, 1e-30, 12345.678901234, 0.2500000001};
+  for (double x : xs) {
+    const float f = round_up_f32(x);
+    const float below = nextafterf(f, 0.0f);
+    std::printf("ru %.17g %d %d\n", x, (double)f >= x, (double)below < x);
+  }
+  // staging capacities: the full bound covers a lattice and a 30 % density
+  // excess; the tight caps never exceed it; multiples of 32 and 8
+  const double rhos[] = {0.6, 0.8638, 0.95};
+  const double sides[] = {3.0, 4.2, 5.4, 7.0};
+  for (double rho : rhos)
+    for (double e : sides) {
+      const double E[3] = {e, e, e}, W[3] = {e - 2.4, e - 2.4, e - 2.4};
+      const int32_t S = stage_bound(E, rho), M = stage_bound(W, rho);
+      int32_t st = 0, mt = 0;
+      tight_caps(E, W, rho, S, M, &st, &mt);
+      const double lat = std::pow(std::floor((e + 0.02) * std::cbrt(rho)) + 1.0, 3) + 8.0;
+      std::printf("cap %g %g %d %d %d %d %d\n", rho, e, S, M, st, mt,
+                  S >= 1.3 * rho * e * e * e + 32 && S >= lat && S % 32 == 0 && st <= S && mt <= M &&
+                      mt <= st && st % 8 == 0 && st >= rho * e * e * e);
+    }
+  return 0;
+}
+"""
+
+
+def test_capacity_and_rounding_host(tmp_path):
+    if not os.path.isdir(CUDA_INC):
+        pytest.skip("CUDA headers not found")
+    src = tmp_path / "c.cpp"
+    src.write_text(CAPS_SRC)
+    exe = tmp_path / "c"
+    r = subprocess.run(["g++", "-std=c++17", "-O1", "-I", os.path.join(ROOT, "paper_1502_06447_gb300", "csrc"),
+                        "-I", os.path.join(ROOT, "include"), "-I", CUDA_INC, str(src), "-o", str(exe)],
+                       capture_output=True, text=True)
+    if r.returncode != 0:
+        pytest.fail(r.stderr[-3000:])
+    out = subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout
+    for line in out.splitlines():
+        f = line.split()
+        if f[0] == "ru":
+            assert f[2:] == ["1", "1"], line
+        else:
+            assert f[-1] == "1", line
