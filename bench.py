@@ -504,7 +504,7 @@ def cpu_baseline_run(max_sweeps=1, time_budget=25.0):
                        dir_mode=oracle.DIR_ISO, D=c["tiles"], seed=c["po_seed"], img=ip)
     rc, po_sweeps, _ = po.pushoff(c["f0"], c["stages"], c["ell"], c["max_sweeps"])
     dp = time.perf_counter() - t2
-    return {"value": ev / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+    return {"value": ev / dt, "unit": UNIT, "cores": 1, "host_cores": os.cpu_count(), "kind": "oracle",
             "sample": f"{max_sweeps} sweep(s) of the 1e6-bead melt without swaps "
                       f"({ev} events, {dt:.1f} s)",
             "structure_ms": 1e3 * ds,
