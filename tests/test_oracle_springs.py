@@ -107,3 +107,29 @@ def test_spring_event_against_its_definition():
             rise(xt) + dE, rel=1e-7, abs=1e-10)
         ref = brentq(rise, x0, x0 + 20.0, xtol=1e-14)
         assert oracle.spring_x(d, v, sigma, k, dE) == pytest.approx(ref, rel=1e-9, abs=1e-12)
+
+
+def test_spring_motility_rule_on_domain_tags():
+    """With springs, no bond joins motile beads of two different tiles
+    (reading R23), and exactly the beads with such a bond lose their tile."""
+    L, N = 16.0, 12
+    r, img = oracle.phantom_chains((L, L, L), 60, N, bond=1.6, c=1.0, seed=5)  # long bonds cross joints
+    kw = dict(sigma=1.0, b_max=1.2, mode=oracle.MODE_DOMAIN, D=(4, 4, 4), seed=11, img=img)
+    springs = oracle.System(r, (L, L, L), N, k_spring=30.0, **kw)
+    tethers = oracle.System(r, (L, L, L), N, **kw)
+    crossing_seen = 0
+    for sweep in range(20):
+        ts, _ = springs.domain_tags(sweep)
+        tt, _ = tethers.domain_tags(sweep)
+        a, b = np.arange(len(r) - 1), np.arange(1, len(r))
+        bond = (a // N) == (b // N)
+        a, b = a[bond], b[bond]
+        assert not np.any((ts[a] >= 0) & (ts[b] >= 0) & (ts[a] != ts[b]))
+        cross = (tt[a] >= 0) & (tt[b] >= 0) & (tt[a] != tt[b])
+        crossing_seen += int(cross.sum())
+        dropped = np.zeros(len(r), dtype=bool)
+        dropped[a[cross]] = True
+        dropped[b[cross]] = True
+        assert ((tt >= 0) & (ts < 0) == dropped).all()
+        assert (ts[ts >= 0] == tt[ts >= 0]).all()
+    assert crossing_seen > 0
