@@ -6,7 +6,9 @@
 // -fmad=false; fused multiply-adds only where written as __fma_rn), so the
 // event sequence is a pure function of the input state and the Philox key.
 #pragma once
+#include <math.h>
 #include <stdint.h>
+#include <string.h>
 
 #ifdef __CUDACC__
 #define ECMC_HD __host__ __device__ __forceinline__
@@ -89,6 +91,63 @@ ECMC_HD double wrap_d(double d, double L, double half) {
 // Candidate kinds in tie-break order: an exact tie in x goes to the smaller
 // kind, then to the smaller partner id.
 enum : int { KIND_END = 0, KIND_PASS = 1, KIND_WALL = 2, KIND_HS = 3, KIND_TETHER = 4 };
+
+// ---------------------------------------------------------------- springs
+// Bead-spring chains (Sec. II, ECs with pair potentials): the pieces the EC
+// kernels need for a harmonic bond (k/2)(b - sigma)^2.  Host and device
+// share them, so the host can check them against other implementations.
+#ifdef __CUDA_ARCH__
+#define EC_FMA(a, b, c) __fma_rn(a, b, c)
+#else
+#define EC_FMA(a, b, c) fma(a, b, c)
+#endif
+
+// Natural logarithm of u in (0, 1]: u = m 2^e with m in [sqrt(1/2), sqrt(2)),
+// log u = e ln 2 + 2 atanh(z), z = (m - 1)/(m + 1), atanh(z)/z =
+// sum_{n=0..13} z^(2n)/(2n + 1) by Horner's rule, ln 2 rounded to double.
+// Only +, -, *, / and exact bit moves: every implementation taking these
+// steps gets the same bits (within a few ulp of the exact logarithm).
+ECMC_HD double ec_log(double u) {
+  uint64_t b;
+  memcpy(&b, &u, sizeof(b));
+  int e = (int)((b >> 52) & 0x7FF) - 1023;
+  const uint64_t mb = (b & 0x000FFFFFFFFFFFFFull) | 0x3FF0000000000000ull;
+  double m;
+  memcpy(&m, &mb, sizeof(m));
+  if (m > 1.4142135623730951) {
+    m = m * 0.5;
+    e += 1;
+  }
+  const double z = (m - 1.0) / (m + 1.0);
+  const double z2 = z * z;
+  double s = 1.0 / 29.0;
+  for (int n = 13; n >= 0; --n) s = s * z2 + 1.0 / (double)(2 * n + 1);
+  return (double)e * 0.6931471805599453 + 2.0 * z * s;
+}
+
+// Boltzmann energy of one bond at one event from a Philox word:
+// dE = -log(u), u = 1 - unit53(w) in (0, 1]
+ECMC_HD double spring_dE(uint64_t w) { return -ec_log(1.0 - unit53(w)); }
+
+// Spring event: a pivot at separation d = r_pivot - r_bonded moving along
+// unit v may go on until the energy its move adds reaches dE.  Hard spheres
+// keep b >= sigma, so the energy falls up to the closest approach along the
+// path and rises after it (or from the start when d.v >= 0); dE is spent
+// on the rise: b_t = sigma + sqrt((b_s - sigma)^2 + 2 dE / k) with b_s the
+// bond length where the rise starts, x = -d.v + sqrt(b_t^2 - |d_perp|^2).
+ECMC_HD double spring_x(double d0, double d1, double d2, double v0, double v1, double v2,
+                        double sigma, double k, double dE, double &dv) {
+  dv = EC_FMA(d2, v2, EC_FMA(d1, v1, d0 * v0));
+  const double dd = EC_FMA(d2, d2, EC_FMA(d1, d1, d0 * d0));
+  double perp2 = EC_FMA(-dv, dv, dd);
+  if (perp2 < 0.0) perp2 = 0.0;
+  const double bs = dv < 0.0 ? sqrt(perp2) : sqrt(dd);
+  const double e = bs - sigma;
+  const double bt = sigma + sqrt(e * e + 2.0 * dE / k);
+  double x = -dv + sqrt(bt * bt - perp2);
+  if (x < 0.0) x = 0.0;
+  return x;
+}
 
 ECMC_HD void fnv_mix(uint64_t &h, uint64_t w) {
   h ^= w;
