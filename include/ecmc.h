@@ -10,12 +10,12 @@
  *     for several interaction partners (Sec. II).
  *   - Model: hard spheres of diameter sigma (Eq. 1) bonded into chains by
  *     tethers of maximal length b_max (Sec. II, model paragraph).
- *   - Parallel form: Sec. II.B — spatial tile-joint decomposition re-drawn
+ *   - Parallel form: Sec. II.A — spatial tile-joint decomposition re-drawn
  *     every sweep, reflection of the EC at tile walls, and reflection of v at
  *     the plane normal to the bond when the bonded partner cannot move
  *     (Fig. 2c); the same reflection at a hard-sphere contact with a bead that
  *     cannot move.
- *   - Swap move: Sec. II.D (Fig. 4).
+ *   - Swap move: Sec. II.C (Fig. 4).
  *
  * Conventions (every entry point):
  *   - Returns an ecmc_status; never aborts.  ecmc_last_error() gives a
@@ -87,9 +87,7 @@ typedef struct ecmc_opts {
   int64_t event_cap;     /* events per EC before ECMC_ESTUCK; 0 -> 10^7 */
   double p_swap;         /* swap proposal probability at a motile contact */
   int32_t ecs_per_tile;  /* ECs per tile per sweep (domain); 0 -> 1 */
-  int32_t lanes;         /* lanes per EC: 32, 16, 8, 4, or 1 (domain mode: one
-                            thread per tile, local cell grid in a per-tile
-                            scratch region); 0 -> 32 */
+  int32_t lanes;         /* lanes per EC: 32, 16, 8 or 4; 0 -> 32 */
   int32_t record;        /* 1: keep per-EC digests / lift sums of the last run */
   int32_t stage_cap;     /* staged beads per tile; 0 -> derived from the tile size */
   double cell_side;      /* side of the global cell grid (domain); 0 -> 1.05 sigma */
@@ -112,7 +110,7 @@ typedef struct ecmc_opts {
                             path (ecmc_obs.exhaustive counts it). */
 } ecmc_opts;
 
-/* Observables and counters (Sec. III observables; see ecmc_observables). */
+/* Observables and counters (Sec. IV observables; see ecmc_observables). */
 typedef struct ecmc_obs {
   int64_t n_beads, n_chains, N;
   int64_t sweeps;              /* domain sweeps run so far */
@@ -161,7 +159,7 @@ typedef struct ecmc_event {
   double x;          /* free flight of the pivot */
 } ecmc_event;
 
-/* Phantom chains (Sec. II.C, the first stage of the paper's initial
+/* Phantom chains (Sec. II.B, the first stage of the paper's initial
  * configurations: chains without excluded volume, to be pushed apart
  * afterwards).  n_chains non-reversal random walks of N beads with bond
  * length `bond` in the periodic box L: the first bead uniform in the box,
@@ -178,7 +176,7 @@ typedef struct ecmc_event {
 ecmc_status ecmc_phantom_chains(const double L[3], int64_t n_chains, int32_t N, double bond,
                                 double c, uint64_t seed, double *xyz_out, int32_t *img_out);
 
-/* Slow push-off (Sec. II.C).  ecmc_create_phantom makes a context whose
+/* Slow push-off (Sec. II.B).  ecmc_create_phantom makes a context whose
  * beads are phantom chains (as ecmc_phantom_chains: n_chains x N beads,
  * bond length `bond` <= b_max, stiffness c, key (seed, 0)) in the periodic
  * box; they may overlap, so ecmc_run refuses it (ECMC_EOVERLAP) until
@@ -209,7 +207,7 @@ ecmc_status ecmc_pushoff(ecmc_ctx *ctx, double f0, int32_t stages, double ell, u
  * step (requires sigma <= a <= b_max and N | n0 n1 n2).  Each coordinate is
  * moved by jitter*(2u-1), u from Philox4x64-10 with key (seed, 0) and counter
  * (4, 0, bead, 0), words 0..2 for x..z; jitter 0 keeps the exact lattice.
- * (The paper builds melts by random-walk growth and push-off, Sec. II.C; the
+ * (The paper builds melts by random-walk growth and push-off, Sec. II.B; the
  * lattice start is a synthetic stand-in.)  Checks the start for overlaps
  * and tether violations (ECMC_EOVERLAP / ECMC_ETETHER).  *out receives the
  * context. */
@@ -260,7 +258,7 @@ ecmc_status ecmc_configure(ecmc_ctx *ctx, const ecmc_opts *opts);
 ecmc_status ecmc_run(ecmc_ctx *ctx, double ell, int64_t chains_per_sweep,
                      uint64_t seed, int64_t n_sweeps);
 
-/* Swap moves (Sec. II.D).  Sets p_swap so that the swap attempts per bead
+/* Swap moves (Sec. II.C).  Sets p_swap so that the swap attempts per bead
  * per sweep match the target, from the motile hard-sphere contacts counted
  * so far (needs a previous ecmc_run with p_swap = 0): p_swap =
  * min(1, target * n_beads * sweeps / contacts).  target 0 disables swaps. */
@@ -274,9 +272,9 @@ ecmc_status ecmc_observables(ecmc_ctx *ctx, ecmc_obs *out);
  * centre of mass) */
 ecmc_status ecmc_g1_reset(ecmc_ctx *ctx);
 
-/* Chain structure of the current state (one fused pass, Sec. III: radius of
+/* Chain structure of the current state (one fused pass, Sec. IV: radius of
  * gyration and g2; Appendix A: moment of inertia tensor and shape
- * descriptors, end-to-end distance distribution W(R); Sec. II.C: internal
+ * descriptors, end-to-end distance distribution W(R); Sec. II.B: internal
  * distances R^2(n)).  Positions along a chain come from minimum-image bonds
  * (u_0 = 0, u_{j+1} = u_j + minimg(r_{j+1} - r_j)); the gyration tensor is
  * S = (1/N) sum_j (u_j - U)(u_j - U)^T with U = (1/N) sum_j u_j, and the
@@ -337,7 +335,7 @@ ecmc_status ecmc_restore(ecmc_ctx *ctx, const char *path);
 /* ---- batched replicas ------------------------------------------------------
  * Many independent melts advanced together: per sweep one domain assignment +
  * cell list pass over all replicas' beads and one EC launch over all
- * replicas' tiles (the Sec. II.B sweep of each replica), optionally captured
+ * replicas' tiles (the Sec. II.A sweep of each replica), optionally captured
  * once in a CUDA graph and replayed (the sweep counter lives on the device).
  * Replica r is the lattice melt of ecmc_create_lattice with dims, spacing, N
  * of specs[r] and jitter, and draws every random number with the Philox key
@@ -377,7 +375,7 @@ ecmc_status ecmc_batch_records(ecmc_batch *b, uint64_t *digest, double *lift,
 
 /* ---- autotuner -------------------------------------------------------------
  * Picks the launch setting of the domain sweep for this machine and system
- * (the paper fixes none: Sec. II.B leaves the tile size open): lanes per EC
+ * (the paper fixes none: Sec. II.A leaves the tile size open): lanes per EC
  * (4, 8, 16, 32), tile side (3.4 ... 7 sigma), global cell side (1.05 or 1.4
  * sigma) and ECs per tile (1, 2 or 4), by a coordinate descent (up to two
  * rounds) over short timed trials.  Each trial restores the state saved on entry, runs one untimed
@@ -425,6 +423,12 @@ ecmc_status ecmc_batch_autotune(ecmc_batch *b, double ell, uint64_t seed,
  * every GPU that loads the library holds until the process exits.  The first
  * call on a device looks up that array's device address (cudaGetSymbolAddress)
  * with the device current; make that first call before any stream capture.
+ * The address is kept for the life of the process: after a cudaDeviceReset
+ * of that device it is stale, and this entry point must not be called again
+ * in that process.  Arguments are checked before any launch: box and cell
+ * side must give at most 1,048,576 cells per axis and in total, and the
+ * tiles at most 2^31 - 1 in total (ECMC_EINVAL otherwise).  A CUDA failure
+ * returns ECMC_ECUDA with the CUDA error in ecmc_last_error().
  * All calls share the array and it keeps the last call's contents (the
  * counts are cleared by each call); calls whose work overlaps on the GPU
  * race and must be serialised by the caller.  Asynchronous on `stream`. */

@@ -1,5 +1,5 @@
 """Oracle for the event-chain (EC) Monte Carlo move of tethered hard-sphere
-bead chains (arXiv:1502.06447, Sec. II and Sec. II.B-D).
+bead chains (arXiv:1502.06447, Sec. II and Sec. II.A-D).
 
 TEST INFRASTRUCTURE ONLY.  This is the plain, serial, FP64 checker that the
 CUDA library is compared against.  Only ``tests/``, ``__graft_entry__.smoke()``
@@ -15,28 +15,28 @@ This module is ctypes marshalling only.
 Functions and the passage each follows:
   run_serial / run_domain   EC move, Sec. II (four-step rule, min over
                             partners); tile-joint decomposition and
-                            reflections, Sec. II.B, Fig. 2c; swap, Sec. II.D
-  domain_tags               tile-joint partition, Sec. II.B
+                            reflections, Sec. II.A, Fig. 2c; swap, Sec. II.C
+  domain_tags               tile-joint partition, Sec. II.A
   lattice                   initial lattice melt (a reading: the paper grows
                             random walks instead; the lattice start is the
                             workload's stated synthetic input)
-  chain_obs                 end-to-end distance R_e^2 (Sec. III), bond lengths
+  chain_obs                 end-to-end distance R_e^2 (Sec. IV), bond lengths
   min_pair                  hard-sphere constraint check, Eq. 1
   chain_struct              gyration tensor and centre of mass (R_g and g2,
-                            Sec. III; moment of inertia tensor, Appendix A),
-                            internal distances R^2(n) (Sec. II.C), end-to-end
+                            Sec. IV; moment of inertia tensor, Appendix A),
+                            internal distances R^2(n) (Sec. II.B), end-to-end
                             distance histogram W(R) (Appendix A)
   shape_descriptors         eigenvalues of the gyration tensor, asphericity,
                             acylindricity, shape anisotropy (Appendix A)
   phantom_chains            non-reversal random walks without excluded volume,
                             the first stage of the initial configuration
-                            (Sec. II.C)
+                            (Sec. II.B)
   k_spring (System)         bead-spring chains: harmonic bonds with Boltzmann
                             energies per event instead of tethers (Sec. II)
   pushoff, overlap_flags    slow push-off of overlapping chains: the
                             diameter grows in stages, ECs start at the
                             overlapping beads and ignore their pivot's
-                            overlaps (Sec. II.C)
+                            overlaps (Sec. II.B)
 All functions are pinned by ``tests/test_oracle_pins.py``.
 """
 from __future__ import annotations
@@ -241,7 +241,7 @@ class System:
                          int(n_ec))
 
     def run_domain(self, n_sweeps, ell, sweep0=0, digests=False, log_cap=0):
-        """Domain-decomposed sweeps (Sec. II.B), one EC per tile per sweep x
+        """Domain-decomposed sweeps (Sec. II.A), one EC per tile per sweep x
         ecs_per_tile; sweeps numbered from sweep0."""
         nt = self.P.D[0] * self.P.D[1] * self.P.D[2]
         units = int(n_sweeps) * nt * self.P.ecs_per_tile
@@ -346,7 +346,7 @@ class System:
 
 
 def phantom_chains(L, n_chains, N, bond=1.0, c=1.9, seed=0):
-    """Phantom chains (Sec. II.C): wrapped positions (n_chains N x 3) and
+    """Phantom chains (Sec. II.B): wrapped positions (n_chains N x 3) and
     image counters of non-reversal random walks with stiffness c."""
     lib = _load()
     n = int(n_chains) * int(N)
@@ -408,6 +408,6 @@ def shape_descriptors(gyr):
 
 def g2_terms(mid_ref, mid):
     """Per-chain squared displacement of the middle bead relative to the
-    centre of mass (the summand of g2, Sec. III)."""
+    centre of mass (the summand of g2, Sec. IV)."""
     d = np.asarray(mid, dtype=np.float64) - np.asarray(mid_ref, dtype=np.float64)
     return (d[:, 0] * d[:, 0] + d[:, 1] * d[:, 1]) + d[:, 2] * d[:, 2]

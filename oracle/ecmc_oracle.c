@@ -11,23 +11,23 @@
  *     continued at the partner realising it.  For tethers of length b_max
  *     (Sec. II, model paragraph) the partner limit is where the bond becomes
  *     taut; hard spheres (Eq. 1) limit at contact.
- *   - Parallelisation, Sec. II.B: a spatial decomposition re-drawn every
+ *   - Parallelisation, Sec. II.A: a spatial decomposition re-drawn every
  *     sweep, tile-joint partition, reflection of the EC at cell walls and, for
  *     a bond partner that cannot move, reflection of v at the plane normal to
  *     the bond (Fig. 2c); the same reflection at a hard-sphere contact with a
  *     bead that cannot move.
- *   - Swap move, Sec. II.D: at hard-sphere contact a swap of the two touching
+ *   - Swap move, Sec. II.C: at hard-sphere contact a swap of the two touching
  *     beads is proposed and accepted by Metropolis (infinite tether walls:
  *     accept iff every bond stays <= b_max); accepted -> beads exchanged and
  *     the same pivot continues; rejected -> ordinary transfer.
  *   - ECs with pair potentials, Sec. II (Fig. 2b): bead-spring chains, each
  *     bond drawing a Boltzmann energy per event that the pivot's move may
  *     spend where the bond energy rises.
- *   - Initial configurations, Sec. II.C: phantom chains grown as
+ *   - Initial configurations, Sec. II.B: phantom chains grown as
  *     non-reversal random walks, then the slow push-off (ECs started at
  *     overlapping beads that ignore their pivot's overlaps, the diameter
  *     grown in stages).
- *   - Chain structure, Sec. III and Appendix A: gyration tensor and centre
+ *   - Chain structure, Sec. IV and Appendix A: gyration tensor and centre
  *     of mass, internal distances R^2(n), end-to-end distance histogram.
  * Readings where the paper is silent (the tie order, the pass event, the
  * random-number layout, the joint width) are the same as the CUDA library's
@@ -258,7 +258,7 @@ static double hs_dist(const ctx_t *c, int64_t i, int64_t k, const double v[3],
   if (!(dv < 0.0)) return -1.0;
   double dd = fma(d2, d2, fma(d1, d1, d0 * d0));
   double sig2 = c->P.sigma * c->P.sigma;
-  /* push-off: a bead the pivot overlaps is no obstacle (Sec. II.C) */
+  /* push-off: a bead the pivot overlaps is no obstacle (Sec. II.B) */
   if (c->P.pushoff && dd < sig2) return -1.0;
   double disc = sig2 - fma(-dv, dv, dd);
   if (!(disc > 0.0)) return -1.0;
@@ -289,7 +289,7 @@ static double te_dist(const ctx_t *c, int64_t i, int64_t j, const double v[3],
 /* natural logarithm of u in (0, 1], an own routine from the textbook
  * reduction: u = m 2^e with m in [sqrt(1/2), sqrt(2)), log u = e ln 2 +
  * 2 atanh(z), z = (m - 1)/(m + 1) (|z| < 0.1716), atanh z / z =
- * sum_{n=0..13} z^(2n) / (2n + 1) by Horner's rule (the first term left out
+ * sum_{n=0..14} z^(2n) / (2n + 1) by Horner's rule (the first term left out
  * is below 1e-19); ln 2 rounded to double.  Only +, -, *, / and exact bit
  * manipulations, so that another implementation taking the same steps gets
  * the same bits.  Within a few ulp of the correctly rounded value. */
@@ -329,7 +329,11 @@ static double spring_x(double d0, double d1, double d2, const double v[3], doubl
   const double bs = dv < 0.0 ? sqrt(perp2) : sqrt(dd);
   const double e = bs - sigma;
   const double bt = sigma + sqrt(e * e + 2.0 * dE / k);
-  double x = -dv + sqrt(bt * bt - perp2);
+  /* b_t >= b_s >= |d_perp| exactly; rounding can leave the radicand a few
+   * ulp below zero when dE ~ 0 and the path grazes the closest approach */
+  double rad = bt * bt - perp2;
+  if (rad < 0.0) rad = 0.0;
+  double x = -dv + sqrt(rad);
   if (x < 0.0) x = 0.0;
   return x;
 }
@@ -408,7 +412,7 @@ static void reflect(double v[3], double d0, double d1, double d2) {
   v[2] = fma(-t, d2, v[2]);
 }
 
-/* swap test (Sec. II.D): with pivot i and the touched bead k exchanged,
+/* swap test (Sec. II.C): with pivot i and the touched bead k exchanged,
  * every bond of i and of k must stay within b_max */
 static int bond_ok(const ctx_t *c, int64_t a, const double *pa, int64_t b,
                    const double *pb) {
@@ -686,7 +690,7 @@ int orc_run_serial(const orc_params *P, double *r, int32_t *img, int64_t ec0,
   return (int)st->status;
 }
 
-/* domain assignment (Sec. II.B): shift o in [0,T)^3 drawn per sweep; along
+/* domain assignment (Sec. II.A): shift o in [0,T)^3 drawn per sweep; along
  * each axis tile k covers [o + kT, o + (k+1)T - w), the last w is joint. */
 static void domain_setup(ctx_t *c, uint64_t sweep) {
   const orc_params *P = &c->P;
@@ -1011,13 +1015,13 @@ int orc_start_draws(const orc_params *P, int64_t ec0, int64_t n, int64_t *idx,
 /*
  * Chain structure of the current state, each quantity written out from its
  * definition:
- *   - radius of gyration R_g^2 and the centre of mass R (Sec. III, the
+ *   - radius of gyration R_g^2 and the centre of mass R (Sec. IV, the
  *     plateau of g2), and the moment of inertia tensor of a chain (Appendix
  *     A), through the gyration tensor S = (1/N) sum_j (u_j - U)(u_j - U)^T
  *     with U = (1/N) sum_j u_j (the inertia tensor is N (Tr S 1 - S));
  *   - the middle bead relative to the centre of mass, u_{N/2} - U (the
- *     quantity whose displacement g2 averages, Sec. III);
- *   - mean-square internal distances R^2(n) (Sec. II.C):
+ *     quantity whose displacement g2 averages, Sec. IV);
+ *   - mean-square internal distances R^2(n) (Sec. II.B):
  *     r2n[n] = mean over chains and j of |u_{j+n} - u_j|^2, r2n[0] = 0;
  *   - the end-to-end distance distribution W(R) (Appendix A) as counts of
  *     chains with floor(|u_{N-1} - u_0| / dR) = b, the last bin taking the
@@ -1103,7 +1107,7 @@ int orc_chain_struct(const orc_params *P, const double *r, double *gyr, double *
 }
 
 /*
- * Phantom chains for the initial configuration (Sec. II.C, first stage of
+ * Phantom chains for the initial configuration (Sec. II.B, first stage of
  * the slow push-off): n_chains chains of N beads without excluded volume,
  * each a non-reversal random walk with bond length `bond`.  The first bead
  * is uniform in the box, the first bond uniform on the sphere, and every
@@ -1266,7 +1270,7 @@ int64_t orc_overlap_flags(const orc_params *P, const double *r, double d, uint8_
 }
 
 /*
- * Slow push-off (Sec. II.C): from chains that may overlap (phantom chains),
+ * Slow push-off (Sec. II.B): from chains that may overlap (phantom chains),
  * grow the hard-sphere diameter from f0 sigma to sigma in `stages` equal
  * steps, d_k = sigma (f0 + (1 - f0) k / stages) and d_stages = sigma; at
  * every diameter, repeat domain sweeps (tiles and shifts as in the EC run,

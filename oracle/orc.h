@@ -48,7 +48,7 @@ typedef struct {
   int32_t ecs_per_tile;
   uint64_t seed;
   uint64_t replica;
-  /* slow push-off (Sec. II.C): ECs start at the flagged motile beads of a
+  /* slow push-off (Sec. II.B): ECs start at the flagged motile beads of a
    * tile (one each, in bead id order) and a pivot ignores the beads it
    * overlaps */
   int32_t pushoff;

@@ -4,7 +4,7 @@ This module holds input data only (lattice shapes, spacings, chain lengths,
 run lengths, seeds) and none of the method's arithmetic.  Both the CUDA
 library's tests/benchmark and the oracle read their inputs from here.
 
-The paper measures on synthetic melts too (Systems I-III, Sec. III: M chains
+The paper measures on synthetic melts too (Systems I-III, Sec. IV: M chains
 of N hard-sphere beads in a periodic cube); these workloads stand in for them
 with lattice starts and hard tethers (b_max = 1.2 sigma).
 """

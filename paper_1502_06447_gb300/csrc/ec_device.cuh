@@ -1,5 +1,5 @@
-// Device helpers shared by the EC kernels (arXiv:1502.06447, Sec. II, II.B,
-// II.D): FP64 comparisons on bit patterns, the minimum image, the contact and
+// Device helpers shared by the EC kernels (arXiv:1502.06447, Sec. II, II.A,
+// II.C): FP64 comparisons on bit patterns, the minimum image, the contact and
 // tether distances (Eq. 1), the reflection (Fig. 2c), candidate keys and the
 // tie rule, the shared-memory staging of one tile and its local cell grid,
 // and the FP32 screen.  Included by the kernel translation units only.
@@ -65,7 +65,7 @@ __device__ __forceinline__ int step_i(double &r, double x, double v, double L) {
 // of a pivot moving along v, d = pivot - partner.  Returns x >= 0, or -1 when
 // a contact candidate misses; dv = d.v.
 // (skip_overlap: a hard sphere the pivot overlaps is no obstacle, the
-// push-off rule of Sec. II.C)
+// push-off rule of Sec. II.B)
 __device__ __forceinline__ double quad_x(bool tether, double d0, double d1, double d2, double v0,
                                          double v1, double v2, double R2, double &dv,
                                          bool skip_overlap = false) {

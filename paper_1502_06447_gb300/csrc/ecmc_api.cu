@@ -64,10 +64,7 @@ struct ecmc_ctx {
   int64_t deferred_cap = 0;
   int32_t *d_n_deferred = nullptr;
   int32_t lanes = 32;
-  // one-lane-per-tile kernel: per-tile scratch and local grid
-  unsigned char *d_scratch = nullptr;
-  size_t scratch_bytes = 0;
-  int64_t tile_bytes = 0;
+  // local cell grid of a tile (domain mode)
   int32_t lg[3] = {1, 1, 1};
   float linv[3] = {1, 1, 1};
   float lorg = 0.f;
@@ -139,8 +136,12 @@ ecmc_status alloc_cells(ecmc_ctx *c) {
 ecmc_status set_grid(ecmc_ctx *c, double side) {
   int64_t ncell = 1;
   for (int a = 0; a < 3; ++a) {
-    int k = (int)floor(c->L[a] / side);
-    if (k < 3) return fail(ECMC_EINVAL, "box too small for the cell grid (axis %d)", a);
+    // bounded in double before the cast; the product stays below 2^31
+    const double kd = floor(c->L[a] / side);
+    if (!(kd >= 3.0)) return fail(ECMC_EINVAL, "box too small for the cell grid (axis %d)", a);
+    if (!(kd <= 1048576.0) || (double)ncell * kd > 2147483647.0)
+      return fail(ECMC_EINVAL, "cell grid too fine (axis %d)", a);
+    const int k = (int)kd;
     c->nc[a] = k;
     c->cs[a] = c->L[a] / k;
     ncell *= k;
@@ -299,7 +300,7 @@ void destroy(ecmc_ctx *c) {
   void *ptrs[] = {c->d_r, c->d_img, c->d_tag, c->d_cell, c->d_rank, c->d_count, c->d_start,
                   c->d_bsum, c->d_cr, c->d_crf, c->d_rf, c->d_cid, c->d_ctag, c->d_cnt, c->d_sums, c->d_status,
                   c->d_unit_next, c->d_n_deferred, c->d_deferred, c->d_obs_d, c->d_obs_u, c->d_g1ref, c->d_rdig, c->d_rlift, c->d_rev,
-                  c->d_log, c->d_log_n, c->d_scratch, c->d_su, c->d_srec, c->d_spart,
+                  c->d_log, c->d_log_n, c->d_su, c->d_srec, c->d_spart,
                   c->d_sr2n, c->d_ssum, c->d_g2ref, c->d_shist, c->d_po_flag, c->d_po_cnt};
   for (void *p : ptrs) cudaFree(p);
   for (cudaEvent_t e : c->kev) cudaEventDestroy(e);
@@ -481,10 +482,8 @@ ecmc_status ecmc_configure(ecmc_ctx *c, const ecmc_opts *o) {
   const double w = p.joint > 0 ? p.joint : c->b_max;
   if (!(w >= c->b_max)) return fail(ECMC_EINVAL, "joint width must be >= b_max");
   const int lanes = p.lanes ? p.lanes : 32;
-  if (lanes != 32 && lanes != 16 && lanes != 8 && lanes != 4 && lanes != 1)
-    return fail(ECMC_EINVAL, "lanes must be 1, 4, 8, 16 or 32");
-  if (lanes == 1 && p.mode != ECMC_MODE_DOMAIN)
-    return fail(ECMC_EINVAL, "one lane per EC needs the domain mode");
+  if (lanes != 32 && lanes != 16 && lanes != 8 && lanes != 4)
+    return fail(ECMC_EINVAL, "lanes must be 4, 8, 16 or 32");
   if (!(p.p_swap >= 0.0)) return fail(ECMC_EINVAL, "p_swap must be >= 0");
   if (p.schedule != 0 && p.schedule != 1) return fail(ECMC_EINVAL, "schedule must be 0 or 1");
   if (p.block_tiles < 0 || p.block_tiles > 32 || p.block_tiles * lanes > 128 ||
@@ -545,19 +544,7 @@ ecmc_status ecmc_configure(ecmc_ctx *c, const ecmc_opts *o) {
     }
     c->lorg = (float)(-hg);
   }
-  if (lanes == 1) {
-    const int64_t ntile = (int64_t)p.tiles[0] * p.tiles[1] * p.tiles[2];
-    const size_t tb = lane_tile_bytes(stage, (int)ncl);
-    const size_t need = tb * (size_t)ntile;
-    if (need > c->scratch_bytes) {
-      cudaFree(c->d_scratch);
-      c->d_scratch = nullptr;
-      c->scratch_bytes = 0;
-      CU(dalloc(&c->d_scratch, need));
-      c->scratch_bytes = need;
-    }
-    c->tile_bytes = (int64_t)tb;
-  } else {
+  {
     int dev = 0, smem_max = 0;
     CU(cudaGetDevice(&dev));
     CU(cudaDeviceGetAttribute(&smem_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
@@ -647,8 +634,7 @@ static cudaError_t timed_ec(ecmc_ctx *c, const ECParams &P, int64_t slot) {
   }
   cudaError_t err = cudaEventRecord(c->kev[slot], c->stream);
   if (err != cudaSuccess) return err;
-  if (c->lanes == 1) err = launch_ec_lane(P, c->opts.precision == ECMC_PREC_FP32F, c->stream);
-  else if (uses_lock(c->opts, c->lanes)) err = launch_ec_lock(P, c->lanes, c->stream);
+  if (uses_lock(c->opts, c->lanes)) err = launch_ec_lock(P, c->lanes, c->stream);
   else err = launch_ec(P, c->lanes, c->opts.precision == ECMC_PREC_FP32F, c->stream);
   if (err != cudaSuccess) return err;
   return cudaEventRecord(c->kev[slot + 1], c->stream);
@@ -708,8 +694,6 @@ static ECParams ec_params(const ecmc_ctx *c, uint64_t seed, double ell) {
     P.eps_d = (float)ed;
     P.eps_x = (float)ev;
   }
-  P.scratch = c->d_scratch;
-  P.tile_bytes = c->tile_bytes;
   for (int a = 0; a < 3; ++a) {
     P.lg[a] = c->lg[a];
     P.linv[a] = c->linv[a];
@@ -990,9 +974,8 @@ ecmc_status ecmc_pushoff(ecmc_ctx *c, double f0, int32_t stages, double ell, uin
                          int64_t max_sweeps, int64_t *sweeps_out) {
   if (!c) return fail(ECMC_EINVAL, "ctx is NULL");
   if (sweeps_out) *sweeps_out = 0;
-  if (!c->configured || c->opts.mode != ECMC_MODE_DOMAIN || c->opts.precision != ECMC_PREC_FP64 ||
-      c->lanes == 1)
-    return fail(ECMC_EINVAL, "push-off needs the domain mode, FP64 and 4-32 lanes per tile");
+  if (!c->configured || c->opts.mode != ECMC_MODE_DOMAIN || c->opts.precision != ECMC_PREC_FP64)
+    return fail(ECMC_EINVAL, "push-off needs the domain mode and FP64");
   if (!(f0 > 0.0 && f0 <= 1.0) || stages < 1 || max_sweeps < 1 || !(ell >= 0.0 && ell < INFINITY))
     return fail(ECMC_EINVAL, "need 0 < f0 <= 1, stages >= 1, max_sweeps >= 1, finite ell >= 0");
   if (!c->d_po_flag) {
@@ -1350,7 +1333,7 @@ ecmc_status ecmc_autotune(ecmc_ctx *c, double ell, uint64_t seed, int32_t trial_
     sc->events_per_s = (double)(h1[CNT_EVENTS] - h0[CNT_EVENTS]) / dt;
     return ECMC_OK;
   };
-  TunePoint start{c->lanes == 1 ? 8 : c->lanes, c->T[0] / sig * (1.0 - 1e-9),
+  TunePoint start{c->lanes, c->T[0] / sig * (1.0 - 1e-9),
                   base.cell_side > 0 ? base.cell_side / sig : 1.05, c->ecs_per_tile};
   TunePoint best{};
   TuneScore best_s{};

@@ -104,7 +104,7 @@ enum : int { KIND_END = 0, KIND_PASS = 1, KIND_WALL = 2, KIND_HS = 3, KIND_TETHE
 
 // Natural logarithm of u in (0, 1]: u = m 2^e with m in [sqrt(1/2), sqrt(2)),
 // log u = e ln 2 + 2 atanh(z), z = (m - 1)/(m + 1), atanh(z)/z =
-// sum_{n=0..13} z^(2n)/(2n + 1) by Horner's rule, ln 2 rounded to double.
+// sum_{n=0..14} z^(2n)/(2n + 1) by Horner's rule, ln 2 rounded to double.
 // Only +, -, *, / and exact bit moves: every implementation taking these
 // steps gets the same bits (within a few ulp of the exact logarithm).
 ECMC_HD double ec_log(double u) {
@@ -144,7 +144,11 @@ ECMC_HD double spring_x(double d0, double d1, double d2, double v0, double v1, d
   const double bs = dv < 0.0 ? sqrt(perp2) : sqrt(dd);
   const double e = bs - sigma;
   const double bt = sigma + sqrt(e * e + 2.0 * dE / k);
-  double x = -dv + sqrt(bt * bt - perp2);
+  // b_t >= b_s >= |d_perp| exactly; rounding can leave the radicand a few
+  // ulp below zero when dE ~ 0 and the path grazes the closest approach
+  double rad = bt * bt - perp2;
+  if (rad < 0.0) rad = 0.0;
+  double x = -dv + sqrt(rad);
   if (x < 0.0) x = 0.0;
   return x;
 }

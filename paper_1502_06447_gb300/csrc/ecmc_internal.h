@@ -105,9 +105,7 @@ struct ECParams {
   int32_t ncl_max;
   const int64_t *sweep_dev;
   int64_t rec_sweep0;
-  // one-lane-per-tile kernel: per-tile scratch and its local cell grid
-  unsigned char *scratch;
-  int64_t tile_bytes;
+  // local cell grid of a tile (domain mode)
   int32_t lg[3];
   float linv[3];
   float lorg;
@@ -133,12 +131,10 @@ struct ECParams {
 // message for ecmc_last_error (ecmc_api.cu)
 void set_last_error(const char *msg);
 
-// launchers (k_ec.cu, k_ec_lane.cu)
+// launchers (k_ec.cu)
 cudaError_t launch_ec(const ECParams &P, int lanes, int fp32f, cudaStream_t s);
 cudaError_t launch_ec_batch(const ECParams &P, int lanes, int fp32f, cudaStream_t s);
 size_t ec_smem_bytes(int stage_cap, int motile_cap, int ncell, int groups_per_block);
-cudaError_t launch_ec_lane(const ECParams &P, int fp32f, cudaStream_t s);
-size_t lane_tile_bytes(int stage_cap, int ncell);
 // block-lockstep kernel of the screened domain form (lanes 4, 8, 16)
 cudaError_t launch_ec_lock(const ECParams &P, int lanes, cudaStream_t s);
 cudaError_t launch_ec_lock_batch(const ECParams &P, int lanes, cudaStream_t s);

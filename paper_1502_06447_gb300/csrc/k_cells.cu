@@ -1,4 +1,4 @@
-// Domain assignment and cell list (arXiv:1502.06447, Sec. II.B).
+// Domain assignment and cell list (arXiv:1502.06447, Sec. II.A).
 //
 // Per sweep: the tile shift o in [0,T)^3 is drawn from Philox (tag 2,
 // counter (2, sweep, 0, 0)); along each axis tile k covers

@@ -1,5 +1,5 @@
-// Event-chain kernels (arXiv:1502.06447, Sec. II: EC move; Sec. II.B:
-// tile-joint decomposition with reflections; Sec. II.D: swap move).
+// Event-chain kernels (arXiv:1502.06447, Sec. II: EC move; Sec. II.A:
+// tile-joint decomposition with reflections; Sec. II.C: swap move).
 //
 // One group of G lanes (G = 32, 16, 8 or 4) runs the ECs of one tile; the
 // 32/G groups of a warp advance in lockstep, one event per iteration, so

@@ -1,5 +1,5 @@
 // Block-lockstep EC kernel of the screened domain form (arXiv:1502.06447,
-// Sec. II: EC move; Sec. II.B: tiles, joints and reflections; Sec. II.D:
+// Sec. II: EC move; Sec. II.A: tiles, joints and reflections; Sec. II.C:
 // swap move).
 //
 // A block runs NT tiles.  Each tile is staged and screened by a group of G

@@ -1,10 +1,10 @@
 // Fused observables over the current state and the initial lattice.
 //
-//   R_e^2 per chain from minimum-image bonds (end-to-end distance, Sec. III
+//   R_e^2 per chain from minimum-image bonds (end-to-end distance, Sec. IV
 //   and the ideal-chain law <R^2> = c N sigma^2); bond lengths and tether
 //   violations (b > b_max); hard-sphere overlaps (Eq. 1) from the cell list;
 //   g1, the mean-square displacement of the middle bead N/2 (Eq. for g1 in
-//   Sec. III) against a reference snapshot of unwrapped positions; pair and
+//   Sec. IV) against a reference snapshot of unwrapped positions; pair and
 //   bond counts in thin shells at contact (sigma, b_max) for the
 //   contact-value pressure.
 #include <cuda_runtime.h>
@@ -137,7 +137,7 @@ __global__ void k_lattice(int n0, int n1, int n2, double a, double jitter, uint6
 
 // beads that overlap another bead (|d|^2 < thr, minimum image, squared
 // length (d0 d0 + d1 d1) + d2 d2) through the cell list: flag 0/1 per bead
-// and their number (the push-off's start beads, Sec. II.C)
+// and their number (the push-off's start beads, Sec. II.B)
 __global__ void k_po_flags(const ObsParams O, double thr, uint8_t *flag, unsigned long long *count) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= O.n) return;
@@ -167,7 +167,7 @@ __global__ void k_po_flags(const ObsParams O, double thr, uint8_t *flag, unsigne
   if (f) atomicAdd(count, 1ull);
 }
 
-// Phantom chains (Sec. II.C, first stage of the initial configuration):
+// Phantom chains (Sec. II.B, first stage of the initial configuration):
 // one thread per chain walks N beads with bond length `bond`, the first bead
 // uniform in the box, the first bond uniform on the sphere, every next bond
 // uniform on the cap t_j . t_{j+1} >= ct around the one before (cos theta =

@@ -14,6 +14,9 @@
 // of every bead or -1 for the joint, and beads binned into the cell grid
 // nc_a = floor(L_a / cell_side) (order inside a cell not fixed).
 #include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+#include <stdio.h>
 
 #include <mutex>
 
@@ -169,7 +172,9 @@ __global__ void ks_scatter(const StaticParams S) {
   S.ids[(int64_t)S.start[c] + S.rank[b]] = (int32_t)b;
 }
 
-// device address of g_scratch, looked up once per device
+// device address of g_scratch, looked up once per device and kept for the
+// life of the process (a cudaDeviceReset of that device makes it stale; the
+// header says so)
 std::mutex g_mu;
 int32_t *g_ptr[256] = {nullptr};
 
@@ -212,15 +217,33 @@ extern "C" ecmc_status ecmc_cells_static(const double *d_r, int64_t n, const dou
     return ECMC_EINVAL;
   }
   StaticParams S{};
-  int64_t ncell = 1;
+  // every count is bounded while still in double, before any integer cast
+  // or product: per axis at most STATIC_MAX_CELLS cells, the grid at most
+  // STATIC_MAX_CELLS after every multiply, the tile count within int32
+  int64_t ncell = 1, ntile = 1;
   for (int a = 0; a < 3; ++a) {
-    if (!(box[a] > 0.0) || tiles[a] < 1) {
-      set_last_error("ecmc_cells_static: box must be > 0 and tiles >= 1");
+    if (!(box[a] > 0.0 && box[a] < INFINITY) || tiles[a] < 1) {
+      set_last_error("ecmc_cells_static: box must be finite and > 0 and tiles >= 1");
       return ECMC_EINVAL;
     }
-    const int k = (int)floor(box[a] / cell_side);
-    if (k < 1) {
+    const double kd = floor(box[a] / cell_side);
+    if (!(kd >= 1.0)) {
       set_last_error("ecmc_cells_static: cell_side larger than the box");
+      return ECMC_EINVAL;
+    }
+    if (!(kd <= (double)STATIC_MAX_CELLS)) {
+      set_last_error("ecmc_cells_static: more than 1048576 cells");
+      return ECMC_EINVAL;
+    }
+    const int k = (int)kd;
+    ncell *= k;
+    if (ncell > STATIC_MAX_CELLS) {
+      set_last_error("ecmc_cells_static: more than 1048576 cells");
+      return ECMC_EINVAL;
+    }
+    ntile *= tiles[a];
+    if (ntile > INT32_MAX) {
+      set_last_error("ecmc_cells_static: more than 2^31 - 1 tiles");
       return ECMC_EINVAL;
     }
     S.L[a] = box[a];
@@ -233,16 +256,17 @@ extern "C" ecmc_status ecmc_cells_static(const double *d_r, int64_t n, const dou
       set_last_error("ecmc_cells_static: tile narrower than the joint");
       return ECMC_EINVAL;
     }
-    ncell *= k;
-  }
-  if (ncell > STATIC_MAX_CELLS) {
-    set_last_error("ecmc_cells_static: more than 1048576 cells");
-    return ECMC_EINVAL;
   }
   int32_t *base = nullptr;
-  if (scratch_for_current_device(&base) != cudaSuccess) {
-    set_last_error("ecmc_cells_static: cudaGetSymbolAddress of the scratch array failed");
-    return ECMC_ECUDA;
+  {
+    const cudaError_t e = scratch_for_current_device(&base);
+    if (e != cudaSuccess) {
+      char msg[256];
+      snprintf(msg, sizeof(msg), "ecmc_cells_static: looking up the scratch array failed: %s",
+               cudaGetErrorString(e));
+      set_last_error(msg);
+      return ECMC_ECUDA;
+    }
   }
   cudaStream_t s = (cudaStream_t)stream;
   S.r = d_r;
@@ -255,22 +279,30 @@ extern "C" ecmc_status ecmc_cells_static(const double *d_r, int64_t n, const dou
   S.rank = base;
   S.count = base + STATIC_MAX_BEADS;
   S.bsum = base + STATIC_MAX_BEADS + STATIC_MAX_CELLS;
-  // the counts are the only scratch that must start at zero
-  if (cudaMemsetAsync(S.count, 0, sizeof(int32_t) * ncell, s) != cudaSuccess) {
-    set_last_error("ecmc_cells_static: clearing the counts failed");
+  // a CUDA failure of this call is reported with its code; errors are read
+  // with cudaPeekAtLastError right after each launch, so an error that
+  // earlier, unrelated work left on the thread is not taken for this call's
+  auto failed = [](const char *what, cudaError_t e) {
+    char msg[256];
+    snprintf(msg, sizeof(msg), "ecmc_cells_static: %s: %s", what, cudaGetErrorString(e));
+    set_last_error(msg);
     return ECMC_ECUDA;
-  }
+  };
+  // the counts are the only scratch that must start at zero
+  cudaError_t e = cudaMemsetAsync(S.count, 0, sizeof(int32_t) * ncell, s);
+  if (e != cudaSuccess) return failed("clearing the counts", e);
   const int64_t nb = (n + 255) / 256;
   const int64_t tiles_n = (ncell + ST_TILE - 1) / ST_TILE;
   ks_tag_count<<<(unsigned)nb, 256, 0, s>>>(S);
+  if ((e = cudaPeekAtLastError()) != cudaSuccess) return failed("launching the tag pass", e);
   ks_scan_tiles<<<(unsigned)tiles_n, ST_BLOCK, 0, s>>>(S, ncell);
+  if ((e = cudaPeekAtLastError()) != cudaSuccess) return failed("launching the scan", e);
   ks_scan_sums<<<1, ST_BLOCK, 0, s>>>(S, tiles_n, ncell);
+  if ((e = cudaPeekAtLastError()) != cudaSuccess) return failed("launching the scan", e);
   ks_scan_add<<<(unsigned)((ncell + 255) / 256), 256, 0, s>>>(S, ncell);
+  if ((e = cudaPeekAtLastError()) != cudaSuccess) return failed("launching the scan", e);
   ks_scatter<<<(unsigned)nb, 256, 0, s>>>(S);
-  if (cudaGetLastError() != cudaSuccess) {
-    set_last_error("ecmc_cells_static: kernel launch failed");
-    return ECMC_ECUDA;
-  }
+  if ((e = cudaPeekAtLastError()) != cudaSuccess) return failed("launching the scatter", e);
   if (shift_out) {
     const u64x4 w = philox(TAG_SHIFT, (uint64_t)sweep, 0, 0, seed, 0);
     for (int a = 0; a < 3; ++a) shift_out[a] = unit53(w.v[a]) * S.T[a];

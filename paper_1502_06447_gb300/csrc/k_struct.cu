@@ -1,7 +1,7 @@
-// Chain structure of the current state (arXiv:1502.06447, Sec. III: radius
+// Chain structure of the current state (arXiv:1502.06447, Sec. IV: radius
 // of gyration and the relative MSD g2 of the middle bead; Appendix A: the
 // moment of inertia tensor of a chain, its shape descriptors, and the
-// end-to-end distance distribution W(R); Sec. II.C: mean-square internal
+// end-to-end distance distribution W(R); Sec. II.B: mean-square internal
 // distances R^2(n)).
 //
 // Positions along a chain come from minimum-image bonds: u_0 = 0,

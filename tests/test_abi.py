@@ -80,3 +80,21 @@ def test_binding_struct_layouts_match_header(tmp_path):
     assert got["ecmc_event"] == ecmc.EVENT_DTYPE.itemsize
     for f in ecmc.EVENT_DTYPE.names:
         assert got[f"ecmc_event.{f}"] == ecmc.EVENT_DTYPE.fields[f][1], f
+
+
+@pytest.mark.parametrize("box,cell_side,tiles", [
+    ((2.0 ** 22, 2.0 ** 21, 2.0 ** 21), 1.0, (20, 20, 20)),   # product of the axes wraps in int64
+    ((1e300, 10.0, 10.0), 1.0, (3, 3, 3)),                      # one axis beyond int range
+    ((200.0, 200.0, 200.0), 1.0, (20, 20, 20)),                 # 8e6 cells > 2^20
+    ((float("inf"), 10.0, 10.0), 1.0, (3, 3, 3)),               # non-finite box
+    ((1e5, 1e5, 1e5), 1e4, (2 ** 11, 2 ** 11, 2 ** 11)),        # 2^33 tiles
+])
+def test_cells_static_rejects_bad_sizes_before_any_launch(lib_path, box, cell_side, tiles):
+    """ecmc_cells_static checks every size in double before an integer cast
+    or product and refuses what its fixed scratch array or int32 tile
+    numbering cannot hold; these calls return ECMC_EINVAL without touching a
+    device (the pointers are never dereferenced), so they run on the CPU."""
+    dummy = 1 << 20
+    with pytest.raises(ecmc.EcmcError) as e:
+        ecmc.cells_static(dummy, 1000, box, tiles, 1.2, cell_side, 0, 0, dummy, dummy, dummy)
+    assert e.value.code == -1

@@ -1,6 +1,6 @@
 """Pins of the oracle's phantom-chain generator (non-reversal random walks
 without excluded volume, the first stage of the paper's initial
-configurations, Sec. II.C) against exact properties of the walk: bond
+configurations, Sec. II.B) against exact properties of the walk: bond
 length, the cap bound, <cos theta> = (c - 1)/(c + 1) = cos^2(theta_max/2),
 tangent correlations C^k (each tangent is uniform on a cap around the one
 before, so <t_{j+k} . t_j> = C^k), the freely-rotating-chain <R^2>, a

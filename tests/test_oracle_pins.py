@@ -309,7 +309,7 @@ def test_cell_list_search_equals_all_pairs_search():
 
 
 def test_swap_without_bonds_is_bookkeeping_only():
-    """Sec. II.D: without bonds, EC with and without swaps are identical up
+    """Sec. II.C: without bonds, EC with and without swaps are identical up
     to bookkeeping.  From the same state, one EC with p_swap = 1 must leave
     the same set of occupied positions as one EC without swaps, bit for bit,
     with every no-swap lift replaced by an accepted swap.  (Over several ECs
@@ -335,7 +335,7 @@ def test_swap_without_bonds_is_bookkeeping_only():
 
 
 def test_swap_keeps_tethers():
-    """Swaps in a melt (Sec. II.D, accepted only if every bond stays within
+    """Swaps in a melt (Sec. II.C, accepted only if every bond stays within
     b_max): after swaps all bonds still within [sigma, b_max]."""
     r = oracle.lattice((8, 8, 8), 1.05, 0.01, 13)
     s = oracle.System(r, 8 * 1.05, 8, p_swap=1.0, dir_mode=DIR_ISO, seed=13)
@@ -349,7 +349,7 @@ def test_swap_keeps_tethers():
 
 # ---------------------------------------------------------------- domain partition
 def test_domain_tags_partition_geometry():
-    """Tile-joint partition (Sec. II.B): motile beads of different tiles are
+    """Tile-joint partition (Sec. II.A): motile beads of different tiles are
     more than w apart, joint beads are exactly the points within w of the
     upper faces, and the motile fraction is ((T-w)/T)^3."""
     rng = np.random.default_rng(3)

@@ -1,4 +1,4 @@
-"""Pins of the oracle's slow push-off (Sec. II.C): overlapping beads are
+"""Pins of the oracle's slow push-off (Sec. II.B): overlapping beads are
 pushed apart by ECs that start at them and ignore their pivot's overlaps,
 the diameter growing in stages.  Checked: the final state has no overlap
 and every tether holds; a hand-built overlapping pair is resolved; chain

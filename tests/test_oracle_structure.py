@@ -1,6 +1,6 @@
 """Pins of the oracle's chain-structure observables (gyration tensor and
-shape descriptors, Appendix A; R^2(n), Sec. II.C; W(R), Appendix A; the g2
-summand, Sec. III) against closed forms, brute force and the ideal-chain
+shape descriptors, Appendix A; R^2(n), Sec. II.B; W(R), Appendix A; the g2
+summand, Sec. IV) against closed forms, brute force and the ideal-chain
 values the paper prints.  No GPU."""
 import math
 
