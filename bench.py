@@ -225,15 +225,23 @@ def run_gpu(args, rank, world):
     physics = {
         "re2_mean_before": o0["re2_mean"], "re2_mean_after": o1["re2_mean"],
         "g1_over_timed_steps": o1["g1"], "g1_per_device_second": o1["g1"] / dev_s,
-        "pressure_lift": 1 + (o1["lift_sum"] - o0["lift_sum"]) / (o1["disp_sum"] - o0["disp_sum"]),
         "pressure_contact": o1["pressure_contact"],
+        "pressure_lift": {
+            "value": 1 + (o1["lift_sum"] - o0["lift_sum"]) / (o1["disp_sum"] - o0["disp_sum"]),
+            "valid": False,
+            "why": "the lift-distance estimator is exact for serial (undecomposed) ECs only; "
+                   "in the domain mode reflections at joint beads and tile walls use up "
+                   "displacement without lifting, so it reads low; pressure_contact (contact "
+                   "values of the final state) is the estimate"},
         "swap_attempts_per_bead_sweep": tried / C5.n / args.steps,
         "swap_acceptance": (o1["swap"] - o0["swap"]) / tried if tried else None,
-        "overlaps": o1["overlaps"], "tether_violations": o1["tether_violations"],
-        "note": "pressure_lift is the lift-distance estimator (biased in the domain mode); "
-                "pressure_contact the contact-value estimator of the final state"}
+        "swap_note": "with tethers of 1.2 sigma an exchange of two touching beads almost always "
+                     "over-stretches a bond, so swaps are proposed and timed but change no "
+                     "topology here",
+        "overlaps": o1["overlaps"], "tether_violations": o1["tether_violations"]}
     structure = structure_run(ctx, stream)
     init = init_run()
+    precision, prec_state = precision_run(args, stream) if rank == 0 else (None, None)
 
     # plain FP64 kernel on the same workload (fresh lattice, same calibration)
     ctx64, tune64 = make(ecmc.PREC_FP64)
@@ -339,8 +347,12 @@ def run_gpu(args, rank, world):
     }
     if batched is not None:
         line["batched"] = batched
+    if precision is not None:
+        line["precision"] = precision
     if args.cpu_baseline:
         line["cpu_baseline"] = cpu_baseline_run(max_sweeps=1)
+        if prec_state is not None:
+            line["precision"].update(precision_vs_oracle(prec_state))
     return line
 
 
@@ -412,6 +424,89 @@ def run_batch(args, stream):
                          "steps": nseq}
     res["batched_over_sequential"] = res["fp32f"]["events_per_s"] / res["sequential"]["events_per_s"]
     return res
+
+
+def precision_run(args, stream, sweeps=5):
+    """The precision form on the 512k-bead melt at phi = 0.50 (2000 chains x
+    N = 256 on an 80^3 lattice, spacing 1.0156, ell = 10, 16^3 tiles): the
+    FP32-screened kernel and the plain FP64 kernel from the same lattice and
+    seed, `sweeps` sweeps each with per-EC digests.  Reports whether every
+    EC's event digest is the same in both, the largest position difference
+    between them, and both kernels' events/s (CUDA events on the launching
+    stream).  The sweep-1 state of the screened run is kept for the oracle
+    check of the CPU leg."""
+    import numpy as np
+    import torch
+
+    from paper_1502_06447_gb300 import ecmc
+    m = C3
+    nt = m.D[0] * m.D[1] * m.D[2]
+    out = {}
+    for name, prec, lanes in (("fp32f", ecmc.PREC_FP32F, 8), ("fp64", ecmc.PREC_FP64, 16)):
+        ctx = ecmc.Context.create_lattice(m.dims, m.spacing, m.N, sigma=m.sigma, b_max=m.b_max,
+                                          jitter=m.jitter, seed=m.seed)
+        ctx.set_stream(stream.cuda_stream)
+        ctx.configure(mode=ecmc.MODE_DOMAIN, dir_mode=ecmc.DIR_ISO, precision=prec, tiles=m.D,
+                      lanes=lanes, record=1)
+        ctx.run(m.ell, seed=m.seed, n_sweeps=1)
+        d1, _, _ = ctx.records(nt)
+        r1, i1 = ctx.get_positions()
+        o0 = ctx.observables()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        ctx.run(m.ell, seed=m.seed, n_sweeps=sweeps - 1)
+        b.record(stream)
+        torch.cuda.synchronize()
+        dk, _, _ = ctx.records(nt * (sweeps - 1))
+        rk, ik = ctx.get_positions()
+        o1 = ctx.observables()
+        ev = o1["events_total"] - o0["events_total"]
+        out[name] = {"digests": np.concatenate([d1, dk]), "r1": r1, "i1": i1, "rk": rk,
+                     "events": o1["events_total"], "overlaps": o1["overlaps"],
+                     "tether_violations": o1["tether_violations"],
+                     "events_per_s": ev / (a.elapsed_time(b) / 1e3),
+                     "confirmed_per_event": (o1["confirmed"] - o0["confirmed"]) / max(ev, 1)}
+        ctx.close()
+    f, g = out["fp32f"], out["fp64"]
+    L = np.array(m.L)
+    d = f["rk"] - g["rk"]
+    d -= L * np.round(d / L)
+    res = {"workload": m.name, "beads": m.n, "phi": round(m.phi, 4), "ell": m.ell,
+           "tiles": list(m.D), "sweeps": sweeps, "ecs": int(len(f["digests"])),
+           "events": int(f["events"]),
+           "events_identical": bool(len(f["digests"]) == len(g["digests"]) and
+                                    (f["digests"] == g["digests"]).all()),
+           "max_dr_vs_fp64": float(np.abs(d).max()),
+           "overlaps": int(f["overlaps"]), "tether_violations": int(f["tether_violations"]),
+           "fp32f_events_per_s": f["events_per_s"], "fp64_events_per_s": g["events_per_s"],
+           "fp32f_over_fp64": f["events_per_s"] / g["events_per_s"],
+           "confirmed_per_event": f["confirmed_per_event"],
+           "note": "FP32 screen (block-lockstep kernel, 8 lanes) vs plain FP64 kernel (16 lanes), "
+                   "same lattice and seed; digests are 64-bit FNV-1a over every event of an EC"}
+    state = {"r1": f["r1"], "i1": f["i1"], "d1": f["digests"][:nt]}
+    return res, state
+
+
+def precision_vs_oracle(state):
+    """CPU-leg check of the precision form: the oracle runs the first sweep
+    of the same 512k-bead melt; its per-EC digests and final positions are
+    compared with the screened GPU run's sweep 1 (outside any timed region)."""
+    import numpy as np
+
+    import oracle
+    m = C3
+    o = oracle.System(oracle.lattice(m.dims, m.spacing, m.jitter, m.seed), m.L, m.N,
+                      mode=oracle.MODE_DOMAIN, dir_mode=oracle.DIR_ISO, D=m.D, seed=m.seed)
+    t0 = time.perf_counter()
+    res = o.run_domain(1, m.ell, digests=True)
+    dt = time.perf_counter() - t0
+    L = np.array(m.L)
+    d = state["r1"] - o.r
+    d -= L * np.round(d / L)
+    return {"oracle_sweeps": 1, "oracle_s": dt,
+            "events_identical_vs_oracle": bool((res["digest"] == state["d1"]).all()),
+            "images_identical_vs_oracle": bool((state["i1"] == o.img).all()),
+            "max_dr_vs_oracle": float(np.abs(d).max())}
 
 
 def structure_run(ctx, stream):
