@@ -35,7 +35,7 @@ import time
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-from paper_1502_06447_gb300.configs import C2, C3, C5  # noqa: E402
+from paper_1502_06447_gb300.configs import C2, C3, C5, C5_LAUNCH, C5_LAUNCH_FP64  # noqa: E402
 
 WORKLOADS = {"c5": (C5, (25, 25, 25)), "c3": (C3, (20, 20, 20)), "c2": (C2, (16, 16, 16))}
 C5_DEFAULT = C5
@@ -48,6 +48,31 @@ C0 = 1.2  # stencil cell side of the bytes-per-event definition (= b_max)
 # revision of the block-lockstep kernel; DRAM counters in profiles/ are used
 # only when they were taken on the same revision
 KERNEL_REV = 5
+
+
+def launch_settings(args):
+    """Timed launch settings {screened: ..., fp64: ...}: the pinned ones for
+    the 1e6-bead melt, 8 / 16 lanes with one EC per tile elsewhere, each
+    field overridable from the command line."""
+    base = {True: dict(C5_LAUNCH), False: dict(C5_LAUNCH_FP64)}
+    for k in (True, False):
+        if C5.name != "c5_swap_1m":
+            base[k].update(tiles=TILES, ecs_per_tile=1, cell_side=1.05)
+        if args.tiles:
+            base[k]["tiles"] = (args.tiles,) * 3
+        if args.ecs_per_tile:
+            base[k]["ecs_per_tile"] = args.ecs_per_tile
+    if args.lanes:
+        base[True]["lanes"] = args.lanes
+    if args.lanes64:
+        base[False]["lanes"] = args.lanes64
+    if args.block_tiles >= 0:
+        base[True]["block_tiles"] = args.block_tiles
+    base[False]["block_tiles"] = 0
+    return base
+
+
+LAUNCH = None
 
 
 def bytes_per_event(phi, confirmed_per_event, fp32f=True):
@@ -80,18 +105,27 @@ def rank_seed(base, rank):
     return int(base) + int(rank)
 
 
-def measured_traffic(kernel):
+def setting_key(kernel, st):
+    """The key a DRAM profile is filed under: kernel revision and the whole
+    launch setting."""
+    return (f"{kernel} rev {KERNEL_REV} lanes {st['lanes']} tiles {'x'.join(map(str, st['tiles']))} "
+            f"cell {st['cell_side']} ecs {st['ecs_per_tile']} block_tiles {st['block_tiles']} "
+            f"tight {st['tight_factor']}")
+
+
+def measured_traffic(kernel, st):
     """DRAM bytes per launch of `kernel` on this workload from the committed
-    ncu summary, or None when the summary is for another kernel."""
+    ncu summary, or None unless the summary was taken on this kernel
+    revision in exactly this launch setting."""
     import re
     p = os.path.join(ROOT, "profiles", "launches_bench_1e6_melt.md")
     try:
         txt = open(p).read()
     except OSError:
         return None
-    k = re.search(r"^kernel = (.+)$", txt, re.M)
+    k = re.search(r"^setting = (.+)$", txt, re.M)
     b = re.search(r"^dram_bytes_per_launch = ([0-9.eE+]+)$", txt, re.M)
-    if not (k and b and kernel and k.group(1).strip() == kernel and C5.name == "c5_swap_1m"):
+    if not (k and b and k.group(1).strip() == setting_key(kernel, st) and C5.name == "c5_swap_1m"):
         return None
     return float(b.group(1))
 
@@ -170,28 +204,37 @@ def run_gpu(args, rank, world):
     stream = torch.cuda.current_stream()
     seed = rank_seed(C5.seed, rank)  # replicas: independent seeds
 
+    def configure(ctx, precision, st):
+        ctx.configure(mode=ecmc.MODE_DOMAIN, dir_mode=ecmc.DIR_ISO, precision=precision,
+                      tiles=st["tiles"], lanes=st["lanes"], ecs_per_tile=st["ecs_per_tile"],
+                      cell_side=st["cell_side"], schedule=args.schedule,
+                      block_tiles=st["block_tiles"], tight_factor=st["tight_factor"])
+
     def make(precision):
         ctx = ecmc.Context.create_lattice(C5.dims, C5.spacing, C5.N, sigma=C5.sigma,
                                           b_max=C5.b_max, jitter=C5.jitter, seed=seed)
         ctx.set_stream(stream.cuda_stream)
-        lanes = args.lanes if precision == ecmc.PREC_FP32F else args.lanes64
-        ctx.configure(mode=ecmc.MODE_DOMAIN, dir_mode=ecmc.DIR_ISO, precision=precision,
-                      tiles=TILES, lanes=lanes, ecs_per_tile=args.ecs_per_tile,
-                      schedule=args.schedule,
-                      block_tiles=args.block_tiles if precision == ecmc.PREC_FP32F else 0)
+        st = dict(LAUNCH[precision == ecmc.PREC_FP32F])
+        configure(ctx, precision, st)
         # melt the lattice start a little first: trials on the lattice
         # itself are not representative (its tiles overflow the tight
         # staging capacities)
-        if args.tune:
-            ctx.run(ELL, seed=seed, n_sweeps=3)
+        ctx.run(ELL, seed=seed, n_sweeps=3)
         tune = ctx.autotune(ELL, seed=seed, trial_sweeps=3) if args.tune else None
+        if tune and args.time_tuned:
+            st = {"lanes": tune["lanes"], "tiles": tuple(tune["tiles"]),
+                  "cell_side": tune["cell_side"], "ecs_per_tile": tune["ecs_per_tile"],
+                  "block_tiles": tune["block_tiles"], "tight_factor": tune["tight_factor"]}
+        # the timed setting (the pinned one unless --time-tuned); the tuner
+        # restored the state, so this is the run that would have followed
+        configure(ctx, precision, st)
         # swap calibration under the final setting: one sweep without swaps,
         # then p_swap for 0.1 attempts / bead / sweep
         ctx.run(ELL, seed=seed, n_sweeps=1)
         ctx.swap(SWAP_RATE)
-        return ctx, tune
+        return ctx, tune, st
 
-    ctx, tune = make(ecmc.PREC_FP32F)
+    ctx, tune, setting = make(ecmc.PREC_FP32F)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
     for _ in range(args.warmup):
         ctx.run(ELL, seed=seed, n_sweeps=1)
@@ -239,12 +282,16 @@ def run_gpu(args, rank, world):
                      "over-stretches a bond, so swaps are proposed and timed but change no "
                      "topology here",
         "overlaps": o1["overlaps"], "tether_violations": o1["tether_violations"]}
-    structure = structure_run(ctx, stream)
-    init = init_run()
-    precision, prec_state = precision_run(args, stream) if rank == 0 else (None, None)
+    extra = args.extra and rank == 0
+    structure = structure_run(ctx, stream) if args.extra else None
+    init = init_run() if args.extra else None
+    precision, prec_state = precision_run(args, stream) if extra else (None, None)
+    springs = springs_run(stream, max(3, args.steps // 2)) if extra else None
+    reptation = reptation_run(stream) if extra else None
+    fig3 = fig3_run(stream) if extra else None
 
     # plain FP64 kernel on the same workload (fresh lattice, same calibration)
-    ctx64, tune64 = make(ecmc.PREC_FP64)
+    ctx64, tune64, setting64 = make(ecmc.PREC_FP64)
     ctx64.run(ELL, seed=seed, n_sweeps=1)
     p0 = ctx64.observables()
     n64 = max(1, args.steps // 2)
@@ -288,8 +335,9 @@ def run_gpu(args, rank, world):
     phi = C5.phi
     bpe = bytes_per_event(phi, confirmed / max(events, 1))
     achieved = events * bpe / ec_s / 1e9
-    traffic = measured_traffic(f"ec_lock_kernel<{tune['lanes'] if tune else args.lanes}, 0> "
-                               f"rev {KERNEL_REV}" if args.schedule == 0 else None)
+    kname = (f"ec_lock_kernel<{setting['lanes']}, 0>" if args.schedule == 0 and setting["lanes"] in (4, 8, 16)
+             else f"ec_kernel<{setting['lanes']}, 1, 0>")
+    traffic = measured_traffic(kname, setting)
     n_beads = C5.n
     value = tot_events / max_dev
     line = {
@@ -308,12 +356,14 @@ def run_gpu(args, rank, world):
         "config": {"workload": C5.name, "beads": n_beads, "chains": C5.n_chains, "N": C5.N,
                    "lattice": list(C5.dims), "spacing": C5.spacing, "phi": round(phi, 4),
                    "b_max": C5.b_max, "ell": ELL,
-                   "tiles": list(tune["tiles"]) if tune else list(TILES), "directions": "iso",
+                   "tiles": list(setting["tiles"]), "directions": "iso",
                    "precision": "fp32 screen + fp64 confirm", "swap_attempts_per_bead_sweep":
-                   SWAP_RATE, "lanes_per_ec": tune["lanes"] if tune else args.lanes,
-                   "ecs_per_tile": tune["ecs_per_tile"] if tune else args.ecs_per_tile,
-                   "cell_side": tune["cell_side"] if tune else 1.05,
-                   "tuning": "autotuned (ECs per device-second)" if tune else "fixed",
+                   SWAP_RATE, "lanes_per_ec": setting["lanes"],
+                   "ecs_per_tile": setting["ecs_per_tile"], "cell_side": setting["cell_side"],
+                   "block_tiles": setting["block_tiles"], "tight_factor": setting["tight_factor"],
+                   "tuning": ("the autotuner's pick of this run" if args.time_tuned and tune else
+                              "pinned launch setting (the autotuner's pick on a GB300, "
+                              "configs.C5_LAUNCH); this run's pick under tuning.fp32f"),
                    "l2": "flushed between steps (256 MB write)",
                    "parallelism": "replicas" if world > 1 else "1 GPU"},
         "ell_sweeps_per_s": (ecs / n_beads) / dev_s,
@@ -326,9 +376,7 @@ def run_gpu(args, rank, world):
         "wall_s": max_wall,
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
                      "frac": achieved / hbm, "traffic": traffic,
-                     "kernel": (f"ec_lock_kernel<{tune['lanes'] if tune else args.lanes}, 0>"
-                                if args.schedule == 0 else
-                                f"ec_kernel<{tune['lanes'] if tune else args.lanes}, 1, 0>"),
+                     "kernel": kname,
                      "bytes_per_event": bpe,
                      "kernel_share_of_step": ec_s / dev_s, "peak_source": peak_src},
         "e2e": {"value": e2e_tot / e2e_max, "unit": UNIT, "steps": n_e2e,
@@ -337,20 +385,26 @@ def run_gpu(args, rank, world):
                 "d2h_bytes_per_step": int(r_host.nbytes + img_host.nbytes)},
         # per sweep: 5 cell-list kernels + the EC launch (two passes for the
         # block-lockstep kernel: tight capacities, then deferred tiles)
-        "gpu_launches": (7 if args.schedule == 0 and (tune["lanes"] if tune else args.lanes)
-                         in (4, 8, 16) else 6) * args.steps,
+        "gpu_launches": (7 if kname.startswith("ec_lock") else 6) * args.steps,
         "physics": physics,
         "structure": structure,
         "init": init,
         "clocks": clk.summary(),
-        "tuning": {"fp32f": tune, "fp64": tune64},
+        "tuning": {"fp32f": tune, "fp64": tune64, "fp64_timed_setting": setting64},
     }
     if batched is not None:
         line["batched"] = batched
     if precision is not None:
         line["precision"] = precision
+    if springs is not None:
+        line["springs"] = springs
+    if reptation is not None:
+        line["reptation"] = reptation
+    if fig3 is not None:
+        line["init_fig3"] = fig3
     if args.cpu_baseline:
         line["cpu_baseline"] = cpu_baseline_run(max_sweeps=1)
+        line["cpu_baseline"]["all_cores"] = cpu_allcore_run(sweeps=1)
         if prec_state is not None:
             line["precision"].update(precision_vs_oracle(prec_state))
     return line
@@ -509,6 +563,126 @@ def precision_vs_oracle(state):
             "max_dr_vs_oracle": float(np.abs(d).max())}
 
 
+# the paper's System I (Sec. IV.A): M = 400 bead-spring chains of N = 120 at
+# packing fraction 0.390 in a 40^3 box, k = 30 kT/sigma^2, built as the paper
+# builds its melts (phantom chains, c = 1.9, pushed off with tethers)
+SPRINGS = dict(L=40.0, n_chains=400, N=120, c=1.9, seed=61, po_seed=0xEC1F0F, k=30.0, ell=10.0,
+               tiles=(9, 9, 9), ecs_per_tile=4, max_sweeps=20000)
+
+
+def springs_run(stream, steps):
+    """Bead-spring melt of the paper's System I size through the public API:
+    phantom chains and slow push-off (outside the timed region), then EC
+    sweeps with harmonic bonds, FP32-screened and plain FP64, each timed
+    with CUDA events on the launching stream."""
+    import torch
+
+    from paper_1502_06447_gb300 import ecmc
+    c = SPRINGS
+    L = (c["L"],) * 3
+    res = {"workload": "System I size: 400 chains x N = 120, eta = 0.390, 40^3 box, k = 30 kT/sigma^2",
+           "beads": c["n_chains"] * c["N"], "ell": c["ell"], "tiles": list(c["tiles"]),
+           "ecs_per_tile": c["ecs_per_tile"], "steps": steps}
+    ctx = ecmc.Context.create_phantom(L, c["n_chains"], c["N"], bond=1.0, c=c["c"], seed=c["seed"])
+    ctx.set_stream(stream.cuda_stream)
+    ctx.configure(mode=ecmc.MODE_DOMAIN, dir_mode=ecmc.DIR_ISO, precision=ecmc.PREC_FP64,
+                  tiles=c["tiles"], lanes=8)
+    t0 = time.perf_counter()
+    res["pushoff_sweeps"] = ctx.pushoff(f0=0.5, stages=5, ell=2.0, seed=c["po_seed"],
+                                        max_sweeps=c["max_sweeps"])
+    res["pushoff_s"] = time.perf_counter() - t0
+    r0, i0 = ctx.get_positions()
+    for name, prec, lanes in (("fp32f", ecmc.PREC_FP32F, 8), ("fp64", ecmc.PREC_FP64, 16)):
+        ctx.set_positions(r0, i0)
+        ctx.configure(mode=ecmc.MODE_DOMAIN, dir_mode=ecmc.DIR_ISO, precision=prec,
+                      tiles=c["tiles"], lanes=lanes, ecs_per_tile=c["ecs_per_tile"], k_spring=c["k"])
+        ctx.run(c["ell"], seed=c["seed"], n_sweeps=3)
+        o0 = ctx.observables()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        ctx.run(c["ell"], seed=c["seed"], n_sweeps=steps)
+        b.record(stream)
+        torch.cuda.synchronize()
+        o1 = ctx.observables()
+        dt = a.elapsed_time(b) / 1e3
+        ev = o1["events_total"] - o0["events_total"]
+        res[name] = {"events_per_s": ev / dt, "ecs_per_s": (o1["ecs"] - o0["ecs"]) / dt,
+                     "ms_per_sweep": 1e3 * dt / steps, "bond_mean": o1["bond_mean"],
+                     "bond_max": o1["bond_max"], "overlaps": o1["overlaps"],
+                     "spring_events_share": (o1["te_lift"] + o1["te_reflect"]
+                                             - o0["te_lift"] - o0["te_reflect"]) / max(ev, 1)}
+    res["fp32f_over_fp64"] = res["fp32f"]["events_per_s"] / res["fp64"]["events_per_s"]
+    res["note"] = ("<b> is the mean bond length of the final state; the paper quotes <b> ~ 1.1 sigma "
+                   "for k = 30; the free-bond law of the oracle pin gives 1.168 sigma")
+    ctx.close()
+    return res
+
+
+# the paper's reptation melt (Sec. IV.B, Fig. 6): M = 20 chains of N = 500
+# with tethers of 1.4 sigma at packing fraction 0.298, from phantom chains
+# and the slow push-off; g1 of the middle beads over log-spaced lags
+REPTATION = dict(M=20, N=500, eta=0.298, b_max=1.4, seed=71, po_seed=72, run_seed=73, ell=10.0,
+                 tiles=(6, 6, 6), ecs_per_tile=2, P=4, K=8, sweeps=8192, max_s=25.0)
+
+
+def reptation_run(stream):
+    """Push-off (wall time), then sweeps of the FP32-screened kernel with the
+    device-side g1 table until `sweeps` sweeps or about `max_s` seconds;
+    reports the table and the slope of log g1 against log lag over the
+    longest decade of lags that have at least 8 origins."""
+    import numpy as np
+    import torch
+
+    from paper_1502_06447_gb300 import ecmc
+    c = REPTATION
+    L = (c["M"] * c["N"] * math.pi / (6.0 * c["eta"])) ** (1.0 / 3.0)
+    ctx = ecmc.Context.create_phantom((L, L, L), c["M"], c["N"], bond=1.0, c=1.9, seed=c["seed"],
+                                      b_max=c["b_max"])
+    ctx.set_stream(stream.cuda_stream)
+    ctx.configure(mode=ecmc.MODE_DOMAIN, dir_mode=ecmc.DIR_ISO, precision=ecmc.PREC_FP64,
+                  tiles=c["tiles"], lanes=8)
+    t0 = time.perf_counter()
+    po_sweeps = ctx.pushoff(f0=0.5, stages=5, ell=2.0, seed=c["po_seed"], max_sweeps=20000)
+    po_s = time.perf_counter() - t0
+    ctx.configure(mode=ecmc.MODE_DOMAIN, dir_mode=ecmc.DIR_ISO, precision=ecmc.PREC_FP32F,
+                  tiles=c["tiles"], lanes=8, ecs_per_tile=c["ecs_per_tile"])
+    ctx.g1_track(c["P"], c["K"])
+    o0 = ctx.observables()
+    done, chunk = 0, 256
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    t1 = time.perf_counter()
+    while done < c["sweeps"] and time.perf_counter() - t1 < c["max_s"]:
+        ctx.run(c["ell"], seed=c["run_seed"], n_sweeps=chunk)
+        done += chunk
+        torch.cuda.synchronize()
+    b.record(stream)
+    torch.cuda.synchronize()
+    dt = a.elapsed_time(b) / 1e3
+    o1 = ctx.observables()
+    lags, g1, cnt = ctx.g1_table()
+    ok = (cnt >= 8) & (g1 > 0)
+    fit = None
+    if ok.sum() >= 3:
+        x, y = np.log(lags[ok]), np.log(g1[ok])
+        sel = x >= x.max() - math.log(10.0)
+        if sel.sum() >= 2:
+            fit = float(np.polyfit(x[sel], y[sel], 1)[0])
+    ctx.close()
+    return {"workload": "reptation melt: 20 chains x N = 500, eta = 0.298, tethers b_max = 1.4, "
+                        "phantom chains + push-off",
+            "box": L, "pushoff_sweeps": po_sweeps, "pushoff_s": po_s, "sweeps": done,
+            "events_per_s": (o1["events_total"] - o0["events_total"]) / dt,
+            "ms_per_sweep": 1e3 * dt / max(done, 1),
+            "g1_table": {"lag_sweeps": [int(v) for v in lags[cnt > 0]],
+                         "g1": [float(v) for v in g1[cnt > 0]],
+                         "origins": [int(v) for v in cnt[cnt > 0]]},
+            "g1_exponent_last_decade": fit,
+            "paper": "g1 ~ t^0.3 in the reptation regime (Fig. 6), reached there after much longer "
+                     "runs; this run covers the time the budget allows",
+            "overlaps": o1["overlaps"], "tether_violations": o1["tether_violations"]}
+
+
 def structure_run(ctx, stream):
     """The chain-structure pass (ecmc_structure) on the melt's final state:
     its device time with and without R^2(n) (CUDA events on the library's
@@ -575,6 +749,78 @@ def init_run():
             "r2n_over_n": {str(k): float(rn[k] / k) for k in (1, 5, 19)},
             "setting": "267 chains x 20 beads, c = 1.9, 20^3 box, 4^3 tiles, f0 = 0.5, 5 stages, "
                        "ECs of length 2, plain FP64 kernel"}
+
+
+def _oracle_part(k, parts, sweeps):
+    """One process of the all-core oracle timing: tiles t % parts == k of
+    `sweeps` sweeps of the 1e6-bead melt; returns (events, seconds)."""
+    import oracle
+    r = oracle.lattice(C5.dims, C5.spacing, C5.jitter, C5.seed)
+    o = oracle.System(r, C5.L, C5.N, mode=oracle.MODE_DOMAIN, dir_mode=oracle.DIR_ISO,
+                      D=TILES, seed=C5.seed, tile_mod=parts, tile_rem=k)
+    t0 = time.perf_counter()
+    res = o.run_domain(sweeps, ELL)
+    return res["stats"]["events"], time.perf_counter() - t0
+
+
+def cpu_allcore_run(sweeps=1):
+    """The oracle on every host core: the tiles of a sweep split over one
+    process per core (tiles are independent within a sweep, so the parts do
+    exactly the serial sweep's work); events/s = all events / the slowest
+    part's run time (process start-up and state building excluded)."""
+    import concurrent.futures as cf
+    import multiprocessing as mp
+    parts = os.cpu_count() or 1
+    with cf.ProcessPoolExecutor(max_workers=parts, mp_context=mp.get_context("spawn")) as ex:
+        out = list(ex.map(_oracle_part, range(parts), [parts] * parts, [sweeps] * parts))
+    ev = sum(e for e, _ in out)
+    dt = max(t for _, t in out)
+    return {"value": ev / dt, "unit": UNIT, "cores": parts, "kind": "oracle",
+            "sample": f"{sweeps} sweep(s) of the 1e6-bead melt without swaps, its tiles split "
+                      f"over {parts} processes ({ev} events, slowest part {dt:.1f} s)"}
+
+
+# the paper's Fig. 3 initial configuration (Sec. II.B): M = 500 phantom
+# chains of N = 121 (c = 1.9, bonds of sigma) at packing fraction 0.495 in a
+# 40^3 box, pushed off with ECs of length 2 sigma
+FIG3 = dict(L=40.0, n_chains=500, N=121, c=1.9, seed=81, po_seed=0xEC3F03, f0=0.5, stages=10,
+            ell=2.0, tiles=(9, 9, 9), max_sweeps=2000)
+
+
+def fig3_run(stream):
+    """Phantom chains and slow push-off of the Fig. 3 melt through the
+    public API: R^2(n)/n of the phantom chains and after the push-off (the
+    paper's figure), the sweeps, and the overlaps left if a stage does not
+    finish within max_sweeps (ECMC_ESTUCK)."""
+    from paper_1502_06447_gb300 import ecmc
+    c = FIG3
+    L = (c["L"],) * 3
+    ctx = ecmc.Context.create_phantom(L, c["n_chains"], c["N"], bond=1.0, c=c["c"], seed=c["seed"])
+    ctx.set_stream(stream.cuda_stream)
+    n = c["n_chains"] * c["N"]
+    _, rn0, _ = ctx.structure(r2n=True)
+    ctx.configure(mode=ecmc.MODE_DOMAIN, dir_mode=ecmc.DIR_ISO, precision=ecmc.PREC_FP64,
+                  tiles=c["tiles"], lanes=8)
+    t0 = time.perf_counter()
+    res = {"workload": "Fig. 3 melt: 500 phantom chains x N = 121, eta = 0.495, 40^3 box, "
+                       "push-off in 10 stages from half the diameter, ECs of length 2",
+           "beads": n, "eta": n * math.pi / 6 / c["L"] ** 3}
+    try:
+        res["pushoff_sweeps"] = ctx.pushoff(f0=c["f0"], stages=c["stages"], ell=c["ell"],
+                                            seed=c["po_seed"], max_sweeps=c["max_sweeps"])
+        res["finished"] = True
+    except ecmc.EcmcError as e:
+        res["finished"] = False
+        res["stuck"] = str(e)
+    res["pushoff_s"] = time.perf_counter() - t0
+    _, rn1, _ = ctx.structure(r2n=True)
+    pick = (1, 5, 10, 30, 60, 120)
+    res["r2n_over_n_phantom"] = {str(k): float(rn0[k] / k) for k in pick}
+    res["r2n_over_n_pushed_off"] = {str(k): float(rn1[k] / k) for k in pick}
+    o = ctx.observables()
+    res["overlaps_left"] = o["overlaps"]
+    ctx.close()
+    return res
 
 
 def cpu_baseline_run(max_sweeps=1, time_budget=25.0):
@@ -646,25 +892,34 @@ def main():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--lanes", type=int, default=8, help="lanes per EC, screened kernel")
-    ap.add_argument("--lanes64", type=int, default=16, help="lanes per EC, plain FP64 kernel")
+    ap.add_argument("--lanes", type=int, default=0,
+                    help="lanes per EC, screened kernel (0: the pinned setting)")
+    ap.add_argument("--lanes64", type=int, default=0,
+                    help="lanes per EC, plain FP64 kernel (0: the pinned setting)")
     ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
     ap.add_argument("--workload", default="c5", choices=sorted(WORKLOADS),
                     help="c5: the 1e6-bead melt (default); c2/c3: smaller melts")
     ap.add_argument("--tiles", type=int, default=0, help="tiles per axis (0: workload default)")
-    ap.add_argument("--ecs-per-tile", type=int, default=1)
+    ap.add_argument("--ecs-per-tile", type=int, default=0, help="0: the pinned setting")
     ap.add_argument("--schedule", type=int, default=0,
                     help="screened kernel: 0 block lockstep, 1 warp lockstep")
-    ap.add_argument("--block-tiles", type=int, default=0, help="block lockstep: tiles per block")
+    ap.add_argument("--block-tiles", type=int, default=-1,
+                    help="block lockstep: tiles per block (-1: the pinned setting, 0: occupancy)")
     ap.add_argument("--no-tune", dest="tune", action="store_false",
-                    help="use --lanes/--tiles/--ecs-per-tile instead of the autotuner")
+                    help="skip the autotuner (the timed setting is the pinned one anyway)")
+    ap.add_argument("--time-tuned", action="store_true",
+                    help="time the autotuner's pick of this run instead of the pinned setting")
     ap.add_argument("--no-batch", dest="batch", action="store_false",
                     help="skip the batched-replicas measurement")
+    ap.add_argument("--no-extra", dest="extra", action="store_false",
+                    help="skip the legs beside the headline melt (structure, initial "
+                         "configurations, precision form, springs, reptation)")
     args = ap.parse_args()
-    global C5, ELL, TILES
+    global C5, ELL, TILES, LAUNCH
     C5, TILES = WORKLOADS[args.workload]
     if args.tiles:
         TILES = (args.tiles,) * 3
+    LAUNCH = launch_settings(args)
     ELL = C5.ell
     rank = int(os.environ.get("RANK", 0))
     world = int(os.environ.get("WORLD_SIZE", 1))

@@ -54,7 +54,10 @@ typedef enum {
   ECMC_ETETHER = -5,   /* a bond longer than b_max */
   ECMC_ESTUCK = -6,    /* an EC exceeded the event cap */
   ECMC_ECKPT = -7,     /* checkpoint file unreadable or inconsistent */
-  ECMC_ECAPACITY = -8  /* a tile holds more beads than the staging buffer */
+  ECMC_ECAPACITY = -8, /* a tile holds more beads than the staging buffer */
+  ECMC_EBOUNDS = -9    /* bounds-checked build (-DECMC_CHECKED) only: a kernel
+                          caught an index out of range, recorded the site and
+                          skipped the access; results of that run are void */
 } ecmc_status;
 
 enum { ECMC_MODE_SERIAL = 0, ECMC_MODE_DOMAIN = 1 };
@@ -108,6 +111,30 @@ typedef struct ecmc_opts {
                             exhaustively in FP64 by its own lanes: same
                             events, slower; small caps exist to exercise that
                             path (ecmc_obs.exhaustive counts it). */
+  double k_spring;       /* > 0: bead-spring chains (Sec. II): every bond is a
+                            harmonic spring (k/2)(b - sigma)^2 with k =
+                            k_spring in kT/sigma^2 (the paper's melts: 30)
+                            instead of a tether; 0 -> tethers of b_max.  With
+                            springs each bond of the pivot draws a Boltzmann
+                            energy dE = -log(u) at every event (Philox tag 6,
+                            counter (6 | ec << 8, sweep, unit, event), words 0
+                            and 1 for the bonds to b - 1 and b + 1; serial
+                            mode: ec = 0, sweep = 0, unit = the EC ordinal) and
+                            its event is where the energy the move adds after
+                            the closest approach reaches dE; a spring event
+                            with a motile partner lifts, with an immotile one
+                            reflects v at the plane normal to the bond
+                            (Sec. II.A, Fig. 2c).  In the domain mode a bead
+                            whose bonded bead is motile in another tile is
+                            immotile for the sweep (springs have no longest
+                            bond, so no joint could keep such tiles apart);
+                            tether checks are off; swaps (p_swap > 0) and the
+                            batch are refused. */
+  double tight_factor;   /* block lockstep: the first launch of a sweep stages
+                            tiles with capacities of tight_factor times a
+                            melted tile's mean content (more tiles fit per SM);
+                            tiles that do not fit run in a second launch with
+                            the full capacities (same events); 0 -> 1.08 */
 } ecmc_opts;
 
 /* Observables and counters (Sec. IV observables; see ecmc_observables). */
@@ -146,6 +173,7 @@ typedef struct ecmc_obs {
                                   two shells */
   int64_t exhaustive;          /* tile steps of the block-lockstep kernel
                                   evaluated exhaustively in FP64 */
+  double bond_mean;            /* <b> over all bonds of the current state */
 } ecmc_obs;
 
 /* One EC event of the parity log (ecmc_event_log). */
@@ -272,6 +300,27 @@ ecmc_status ecmc_observables(ecmc_ctx *ctx, ecmc_obs *out);
  * centre of mass) */
 ecmc_status ecmc_g1_reset(ecmc_ctx *ctx);
 
+/* g1 table (Sec. IV, Eq. 3: g1(dt) = <[r_{N/2}(t + dt) - r_{N/2}(t)]^2>_t,
+ * averaged over the chains and over time origins t), accumulated on the
+ * device after every domain sweep of ecmc_run from this call on.  Lags are
+ * log-spaced, dt = j P^k sweeps for k = 0 .. K-1 and j = 1 .. P-1 (so lags
+ * up to (P - 1) P^(K-1)); the origins of lag j P^k are the sweeps that are
+ * multiples of P^k (counted from this call, whose state is sweep 0) with
+ * t + dt within the run.  Positions are the unwrapped middle beads
+ * (bead N/2 of each chain, r + img L).  The device keeps K rings of P
+ * snapshots (K P 24 B per chain) and one sum and count per lag; the sum
+ * for a lag adds, sweep by sweep, the chains' (dx^2 + dy^2) + dz^2 in chain
+ * order, so it is reproducible bit for bit.  ecmc_g1_track(ctx, P, K)
+ * (2 <= P <= 64, 1 <= K <= 16) starts a new table; P = 0 stops tracking
+ * (the table is kept).  Serial runs leave the table unchanged. */
+ecmc_status ecmc_g1_track(ecmc_ctx *ctx, int32_t P, int32_t K);
+/* lag (sweeps), g1 (sigma^2; 0 where a lag has no origin yet) and the
+ * number of origins per lag, K (P - 1) entries in order k = 0.. , j = 1..
+ * (host buffers of at least cap entries, any may be NULL); *n receives the
+ * entries written.  Synchronises. */
+ecmc_status ecmc_g1_table(ecmc_ctx *ctx, int64_t *lag, double *g1, int64_t *count, int32_t cap,
+                          int32_t *n);
+
 /* Chain structure of the current state (one fused pass, Sec. IV: radius of
  * gyration and g2; Appendix A: moment of inertia tensor and shape
  * descriptors, end-to-end distance distribution W(R); Sec. II.B: internal
@@ -377,7 +426,9 @@ ecmc_status ecmc_batch_records(ecmc_batch *b, uint64_t *digest, double *lift,
  * Picks the launch setting of the domain sweep for this machine and system
  * (the paper fixes none: Sec. II.A leaves the tile size open): lanes per EC
  * (4, 8, 16, 32), tile side (3.4 ... 7 sigma), global cell side (1.05 or 1.4
- * sigma) and ECs per tile (1, 2 or 4), by a coordinate descent (up to two
+ * sigma), ECs per tile (1, 2 or 4) and the block-lockstep kernel's staging
+ * (1, 2 or 4 warps per block; first-pass capacity factor 1.0, 1.08 or 1.16;
+ * other kernels take only the defaults), by a coordinate descent (up to two
  * rounds) over short timed trials.  Each trial restores the state saved on entry, runs one untimed
  * sweep and `trial_sweeps` timed ones; the score is ECs per device-second.
  * On return the context (batch) is configured with the winner and its
@@ -394,6 +445,8 @@ typedef struct ecmc_tuning {
   double ecs_per_s;       /* score of the winner */
   double events_per_s;
   int32_t n_trials;       /* admissible points timed */
+  int32_t block_tiles;    /* block lockstep: tiles per block (0: not that kernel) */
+  double tight_factor;    /* block lockstep: first-pass capacity factor */
 } ecmc_tuning;
 ecmc_status ecmc_autotune(ecmc_ctx *ctx, double ell, uint64_t seed,
                           int32_t trial_sweeps, ecmc_tuning *out);

@@ -37,7 +37,10 @@ Functions and the passage each follows:
                             diameter grows in stages, ECs start at the
                             overlapping beads and ignore their pivot's
                             overlaps (Sec. II.B)
-All functions are pinned by ``tests/test_oracle_pins.py``.
+  g1_table                  the middle bead's mean-square displacement g1
+                            (Sec. IV, Eq. 3) over log-spaced lags, averaged
+                            over chains and time origins
+All functions are pinned by the ``tests/test_oracle_*.py`` files.
 """
 from __future__ import annotations
 
@@ -82,7 +85,7 @@ class Params(C.Structure):
         ("use_cells", C.c_int32), ("ecs_per_tile", C.c_int32),
         ("seed", C.c_uint64), ("replica", C.c_uint64),
         ("pushoff", C.c_int32), ("pad_po", C.c_int32), ("po_flag", C.c_void_p),
-        ("k_spring", C.c_double),
+        ("k_spring", C.c_double), ("tile_mod", C.c_int32), ("tile_rem", C.c_int32),
     ]
 
 
@@ -183,7 +186,7 @@ class System:
     def __init__(self, r, L, N, sigma=1.0, b_max=1.2, s_cap=0.25, mode=MODE_SERIAL,
                  dir_mode=DIR_CART3, D=(1, 1, 1), w=None, p_swap=0.0,
                  event_cap=10_000_000, use_cells=1, ecs_per_tile=1, seed=0,
-                 replica=0, img=None, k_spring=0.0):
+                 replica=0, img=None, k_spring=0.0, tile_mod=0, tile_rem=0):
         self.r = np.ascontiguousarray(r, dtype=np.float64).reshape(-1, 3).copy()
         self.img = (np.zeros_like(self.r, dtype=np.int32) if img is None
                     else np.ascontiguousarray(img, dtype=np.int32).reshape(-1, 3).copy())
@@ -207,6 +210,7 @@ class System:
         p.seed = int(seed) & (2**64 - 1)
         p.replica = int(replica) & (2**64 - 1)
         p.k_spring = float(k_spring)
+        p.tile_mod, p.tile_rem = int(tile_mod), int(tile_rem)
         self.P = p
 
     @property
@@ -371,6 +375,48 @@ def own_log(u: float) -> float:
     """The oracle's own natural logarithm (behind the springs' Boltzmann
     energies)."""
     return float(_load().orc_log(float(u)))
+
+
+def g1_table(traj, P, K):
+    """g1 of Sec. IV, Eq. 3, over the log-spaced lags j P^k (k < K,
+    1 <= j < P): traj[t] holds the unwrapped middle beads (chains x 3) after
+    sweep t (t = 0 the start).  The origins of lag j P^k are the sweeps t0
+    that are multiples of P^k with t0 + j P^k <= T.  Returns (lags, g1,
+    counts, sums): for every end sweep t in increasing order and every lag
+    whose origin t - lag qualifies, the chains' (dx^2 + dy^2) + dz^2 are
+    added in chain order and that sum is added to the lag's total; g1 =
+    total / (origins x chains)."""
+    traj = np.asarray(traj, dtype=np.float64)
+    T = traj.shape[0] - 1
+    nch = traj.shape[1]
+    lags, sums, cnts = [], [], []
+    pks = [P ** k for k in range(K)]
+    for k in range(K):
+        for j in range(1, P):
+            lags.append(j * pks[k])
+    sums = [0.0] * len(lags)
+    cnts = [0] * len(lags)
+    for t in range(1, T + 1):
+        for k in range(K):
+            pk = pks[k]
+            if t % pk != 0:
+                continue
+            for j in range(1, P):
+                if t // pk < j:
+                    continue
+                q = k * (P - 1) + (j - 1)
+                a, b = traj[t], traj[t - j * pk]
+                s = 0.0
+                for ch in range(nch):
+                    d0 = float(a[ch, 0]) - float(b[ch, 0])
+                    d1 = float(a[ch, 1]) - float(b[ch, 1])
+                    d2 = float(a[ch, 2]) - float(b[ch, 2])
+                    s = s + ((d0 * d0 + d1 * d1) + d2 * d2)
+                sums[q] = sums[q] + s
+                cnts[q] += 1
+    g1 = [sums[q] / (cnts[q] * nch) if cnts[q] else 0.0 for q in range(len(lags))]
+    return (np.array(lags, dtype=np.int64), np.array(g1), np.array(cnts, dtype=np.int64),
+            np.array(sums))
 
 
 def seq_sum(x) -> float:

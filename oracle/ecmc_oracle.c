@@ -793,6 +793,7 @@ int orc_run_domain(const orc_params *P, double *r, int32_t *img, int64_t sweep0,
       free(fill);
     }
     for (int64_t t = 0; t < ntile && st->status == 0; ++t) {
+      if (P->tile_mod > 1 && t % P->tile_mod != P->tile_rem) continue;
       int64_t m = cnt[t + 1] - cnt[t];
       if (m == 0) continue;
       tile_t tl;

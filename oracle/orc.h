@@ -58,6 +58,11 @@ typedef struct {
    * spring chains, k in units of kT/sigma^2) instead of tethers; b_max is
    * then unused and swaps are off */
   double k_spring;
+  /* domain mode, work split for timing on several host cores: only tiles
+   * t with t % tile_mod == tile_rem run (tile_mod <= 1: all tiles); tiles
+   * are independent within a sweep, so each part is exactly the serial
+   * oracle's work on those tiles */
+  int32_t tile_mod, tile_rem;
 } orc_params;
 
 typedef struct {

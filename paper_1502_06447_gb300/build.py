@@ -15,14 +15,18 @@ import subprocess
 HERE = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
-OUT_DIR = os.path.join(HERE, "_build")
-LIB = os.path.join(HERE, "libecmc.so")
+OUT_DIR = os.path.join(HERE, "_build_checked" if os.environ.get("ECMC_CHECKED") == "1" else "_build")
+# ECMC_CHECKED=1 selects the bounds-checked build (-DECMC_CHECKED: kernels
+# check the indices they compute, record the first one out of range in the
+# device status word and skip the access), a library of its own
+CHECKED = os.environ.get("ECMC_CHECKED") == "1"
+LIB = os.path.join(HERE, "libecmc_checked.so" if CHECKED else "libecmc.so")
 
 NVCC = os.environ.get("NVCC", "nvcc")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-fmad=false", "-Xcompiler", "-fPIC",
          "-Xcompiler", "-ffp-contract=off", "-Xcompiler", "-fno-fast-math",
-         "-I", os.path.join(ROOT, "include")]
+         "-I", os.path.join(ROOT, "include")] + (["-DECMC_CHECKED"] if CHECKED else [])
 
 
 def sources():

@@ -68,6 +68,18 @@ C5 = Melt("c5_swap_1m", (100, 100, 100), 1.05, 1000, ell=20.0, seed=0xEC0005,
 
 CONFIGS = {m.name: m for m in (C1, C2, C3, C5)}
 
+# Launch setting of the 1e6-bead melt's timed sweeps: the autotuner's pick
+# (ecmc_autotune: lanes, tile side, cell side, ECs per tile, warps per
+# block, first-pass capacity factor; ECs per device-second on a GB300),
+# pinned here so that every benchmark run times the same setting and the
+# committed DRAM profile describes it.  block_tiles 0: the occupancy
+# calculator's choice; 8 tiles of 8 lanes = two warps per block.
+C5_LAUNCH = dict(lanes=8, tiles=(25, 25, 25), cell_side=1.05, ecs_per_tile=2, block_tiles=8,
+                 tight_factor=1.0)
+# the plain FP64 kernel on the same melt (its own tuner pick)
+C5_LAUNCH_FP64 = dict(lanes=16, tiles=(25, 25, 25), cell_side=1.4, ecs_per_tile=1, block_tiles=0,
+                      tight_factor=1.08)
+
 
 def small_domain(N=8, dims=(16, 16, 16), spacing=1.05, D=(3, 3, 3), seed=0xEC00A1,
                  ell=4.0, sweeps=3, dir_mode="iso", p_swap=0.0) -> Melt:

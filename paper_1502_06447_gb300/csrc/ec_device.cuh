@@ -157,6 +157,11 @@ struct Stage {
   unsigned short *cell;  // [NC][8]: 32-bit count, then up to 6 slots
   unsigned short *ovf;   // [OVF_CAP]
   int *hdr;              // [2] staged count, [3] overflow, [4] overflow-list length
+#ifdef ECMC_CHECKED
+  int cap;               // S (slots)
+  long long nglob;       // beads of the system (ids), set by the kernel
+  int *status;
+#endif
 };
 
 __host__ __device__ __forceinline__ size_t group_bytes(int S, int M64, int MNB, int NC) {
@@ -178,6 +183,11 @@ __device__ __forceinline__ Stage carve(unsigned char *base, int S, int M64, int 
   s.cell = (unsigned short *)(s.id + S);
   s.ovf = s.cell + 8 * NC;
   s.hdr = (int *)(s.ovf + OVF_CAP);
+#ifdef ECMC_CHECKED
+  s.cap = S;
+  s.nglob = 0x7fffffffffffffffll;
+  s.status = nullptr;
+#endif
   return s;
 }
 
@@ -207,6 +217,23 @@ __device__ __forceinline__ int find_id_lin(const int *ids, int lo, int hi, int i
 }
 
 __device__ __forceinline__ void set_status(int *st, int code) { atomicCAS(st, 0, code); }
+
+// Bounds checks of the checked build (-DECMC_CHECKED): CHK(i, n, site, st)
+// is true when 0 <= i < n; otherwise it records DEV_BOUNDS | site << 8 in
+// the status word st (first failure wins) and is false, and the caller
+// skips the access.  In the normal build it is the constant true.
+#ifdef ECMC_CHECKED
+__device__ __forceinline__ bool chk_range(long long i, long long n, int site, int *st) {
+  if (i >= 0 && i < n) return true;
+  atomicCAS(st, 0, DEV_BOUNDS | (site << 8));
+  return false;
+}
+#define CHK(i, n, site, st) chk_range((long long)(i), (long long)(n), (site), (st))
+#define CI(i, n, site, st) (CHK((i), (n), (site), (st)) ? (i) : 0)
+#else
+#define CHK(i, n, site, st) true
+#define CI(i, n, site, st) (i)
+#endif
 
 // ---------------------------------------------------------------- local grid
 struct LGrid {
@@ -344,6 +371,11 @@ __device__ __forceinline__ void screen_cell(const Screen &Z, const Stage &st, co
 // otherwise (a joint bead, static this sweep) the global position array
 __device__ __forceinline__ void pos64(const Stage &st, const double *r, int k, bool in_smem,
                                       double &x, double &y, double &z) {
+#ifdef ECMC_CHECKED
+  x = y = z = 0.0;
+  if (st.status && !CHK(k, st.cap, 1, st.status)) return;
+  if (!in_smem && st.status && !CHK(st.id[k], st.nglob, 2, st.status)) return;
+#endif
   if (in_smem) {
     x = st.px[k];
     y = st.py[k];
@@ -539,6 +571,7 @@ __device__ __forceinline__ void stage_tile(const ECParams &P, const RepParams *r
           rank = (cat == 1 ? m : m + j1) + atomicAdd(&st.hdr[cat - 1], 1);
         }
         const int j = e.x;
+        if (!CHK(rank, S, 3, P.status)) continue;
         if (rank < M64) {
           st.px[rank] = P.cr[3 * (int64_t)j];
           st.py[rank] = P.cr[3 * (int64_t)j + 1];
@@ -552,18 +585,61 @@ __device__ __forceinline__ void stage_tile(const ECParams &P, const RepParams *r
       if (live) capacity();
       live = false;
     }
+    // pass 2b (bead springs): a spring has no longest bond, so the bonded
+    // beads of motile beads are staged wherever they are; one outside the
+    // tether halo (a joint bead, static this sweep) is appended after the
+    // staged beads (two motile beads may append the same bead twice; both
+    // copies are read-only and equal)
+    // (the condition is the same for every lane in `mask`: the groups of a
+    // warp may hold live and dead tiles, and all of them reach the barrier)
+    if (P.k_spring > 0.0) {
+      const int Nc = SYS(N);
+      for (int s = gl; live && s < m; s += G) {
+        const int id = st.id[s];
+        const int c = id % Nc;
+#pragma unroll
+        for (int dir = 0; dir < 2; ++dir) {
+          const int q = dir == 0 ? (c != 0 ? id - 1 : -1) : (c != Nc - 1 ? id + 1 : -1);
+          if (q < 0) continue;
+          if (!CHK(q, BATCH ? rp->n_beads : P.n, 4, P.status)) continue;
+          if (find_id(st.id, 0, m, q) >= 0 || find_id_lin(st.id, m, ns, q) >= 0) continue;
+          const int slot = atomicAdd(&st.hdr[2], 1);
+          if (slot < S) {
+            st.id[slot] = q;
+            if (slot < M64) {
+              st.px[slot] = Rr[3 * (int64_t)q];
+              st.py[slot] = Rr[3 * (int64_t)q + 1];
+              st.pz[slot] = Rr[3 * (int64_t)q + 2];
+            }
+          } else {
+            st.hdr[3] = 1;
+          }
+        }
+      }
+      __syncwarp(mask);
+      if (live) {
+        if (st.hdr[3]) {
+          capacity();
+          live = false;
+          ns = 0;
+        } else {
+          ns = st.hdr[2];
+        }
+      }
+    }
+    const int ns_max2 = __reduce_max_sync(mask, ns);
     // pass 3: shadows (FP32 position minus FP32 corner, the form the moved
     // pivot's shadow takes too) and bond partners of motile beads; empty
     // cells.  Four slots at a time (independent loads).
     for (int i = gl; i < NC; i += G) cell_count(st.cell + 8 * i) = 0u;
     const float *Rf = P.rf + (BATCH ? 3 * rp->bead_off : 0);
-    for (int s0 = 0; s0 < ns_max; s0 += 4 * G) {
+    for (int s0 = 0; s0 < ns_max2; s0 += 4 * G) {
       float x[4], y[4], z[4];
 #pragma unroll
       for (int u = 0; u < 4; ++u) {
         const int s = s0 + u * G + gl;
         x[u] = y[u] = z[u] = 0.f;
-        if (s < ns && live) {
+        if (s < ns && live && CHK(st.id[s], BATCH ? rp->n_beads : P.n, 5, P.status)) {
           const int64_t b = st.id[s];
           x[u] = Rf[3 * b];
           y[u] = Rf[3 * b + 1];

@@ -39,6 +39,7 @@ template <class T>
 cudaError_t dalloc(T **p, size_t count) {
   *p = nullptr;
   if (count == 0) count = 1;
+  if (alloc_refused(sizeof(T) * count)) return cudaErrorMemoryAllocation;
   return cudaMalloc((void **)p, sizeof(T) * count);
 }
 }  // namespace
@@ -82,6 +83,7 @@ struct ecmc_ctx {
   double *d_cr = nullptr;
   float *d_crf = nullptr, *d_rf = nullptr;
   int32_t *d_cid = nullptr, *d_ctag = nullptr;
+  int32_t *d_ftag = nullptr;  // final tags by bead (bead springs; on first use)
   unsigned long long *d_cnt = nullptr;
   double *d_sums = nullptr;
   int *d_status = nullptr;
@@ -90,6 +92,12 @@ struct ecmc_ctx {
   unsigned long long *d_obs_u = nullptr;
   double *d_g1ref = nullptr;
   bool g1_set = false;
+  // g1 table over log-spaced lags (ecmc_g1_track; allocated on first use)
+  double *d_g1ring = nullptr, *d_g1sum = nullptr;
+  unsigned long long *d_g1cnt = nullptr;
+  size_t g1ring_n = 0;
+  int32_t g1_P = 0, g1_K = 0;
+  int64_t g1_t = 0;
   // chain structure scratch (allocated on first use)
   double *d_su = nullptr, *d_srec = nullptr, *d_spart = nullptr, *d_sr2n = nullptr;
   double *d_ssum = nullptr, *d_g2ref = nullptr;
@@ -99,6 +107,7 @@ struct ecmc_ctx {
   // phantom chains may overlap until ecmc_pushoff has resolved it
   uint8_t *d_po_flag = nullptr;
   unsigned long long *d_po_cnt = nullptr;
+  int64_t *d_po_ctr = nullptr;  // push-off: sweep index, sweeps run at this diameter
   bool pushoff_pending = false;
   // records
   uint64_t *d_rdig = nullptr;
@@ -180,6 +189,9 @@ CellParams cell_params(const ecmc_ctx *c, bool domain, uint64_t seed, int64_t sw
   C.rf = c->d_rf;
   C.cid = c->d_cid;
   C.ctag = c->d_ctag;
+  C.N = c->N;
+  C.spring = (domain && c->configured && c->opts.k_spring > 0.0 && c->N > 1) ? 1 : 0;
+  C.ftag = C.spring ? c->d_ftag : nullptr;
   return C;
 }
 
@@ -207,7 +219,7 @@ ObsParams obs_params(const ecmc_ctx *c) {
 }
 
 struct ObsHost {
-  double re2_sum, bmax, bmin, g1_sum;
+  double re2_sum, bmax, bmin, g1_sum, bond_sum;
   unsigned long long overlaps, viol, pairs[2], taut[2];
 };
 
@@ -223,7 +235,7 @@ ecmc_status measure(ecmc_ctx *c, ObsHost *o) {
   ecmc_status s = set_grid(c, side);
   if (s != ECMC_OK) return s;
   CU(launch_cells(cell_params(c, false, 0, 0), c->ncell, c->stream));
-  const double init_d[4] = {0.0, 0.0, 1e300, 0.0};
+  const double init_d[5] = {0.0, 0.0, 1e300, 0.0, 0.0};
   CU(cudaMemcpyAsync(c->d_obs_d, init_d, sizeof(init_d), cudaMemcpyHostToDevice, c->stream));
   CU(cudaMemsetAsync(c->d_obs_u, 0, 6 * sizeof(unsigned long long), c->stream));
   ObsParams O = obs_params(c);
@@ -237,7 +249,7 @@ ecmc_status measure(ecmc_ctx *c, ObsHost *o) {
     O.c_t2 = (bm - 2.0 * d) * (bm - 2.0 * d);
   }
   CU(launch_obs(O, c->stream));
-  double hd[4];
+  double hd[5];
   unsigned long long hu[6];
   CU(cudaMemcpyAsync(hd, c->d_obs_d, sizeof(hd), cudaMemcpyDeviceToHost, c->stream));
   CU(cudaMemcpyAsync(hu, c->d_obs_u, sizeof(hu), cudaMemcpyDeviceToHost, c->stream));
@@ -246,6 +258,7 @@ ecmc_status measure(ecmc_ctx *c, ObsHost *o) {
   o->bmax = hd[1];
   o->bmin = c->N > 1 ? hd[2] : 0.0;
   o->g1_sum = hd[3];
+  o->bond_sum = hd[4];
   o->overlaps = hu[0];
   o->viol = hu[1];
   o->pairs[0] = hu[2];
@@ -260,7 +273,9 @@ ecmc_status check_state(ecmc_ctx *c) {
   ecmc_status s = measure(c, &o);
   if (s != ECMC_OK) return s;
   if (o.overlaps) return fail(ECMC_EOVERLAP, "%llu overlapping pairs", o.overlaps);
-  if (o.viol) return fail(ECMC_ETETHER, "%llu bonds longer than b_max", o.viol);
+  // (bead springs have no longest bond)
+  const bool springs = c->configured && c->opts.k_spring > 0.0;
+  if (o.viol && !springs) return fail(ECMC_ETETHER, "%llu bonds longer than b_max", o.viol);
   return ECMC_OK;
 }
 
@@ -284,7 +299,7 @@ ecmc_status alloc_state(ecmc_ctx *c) {
   CU(cudaMemset(c->d_status, 0, sizeof(int)));
   CU(dalloc(&c->d_unit_next, 1));
   CU(dalloc(&c->d_n_deferred, 1));
-  CU(dalloc(&c->d_obs_d, 4));
+  CU(dalloc(&c->d_obs_d, 5));
   CU(dalloc(&c->d_obs_u, 8));  // [6]: non-finite inputs of set_positions
   CU(dalloc(&c->d_g1ref, 3 * (c->n / c->N)));
   CU(cudaStreamCreateWithFlags(&c->own, cudaStreamNonBlocking));
@@ -299,9 +314,10 @@ void destroy(ecmc_ctx *c) {
   if (c->stream) cudaStreamSynchronize(c->stream);
   void *ptrs[] = {c->d_r, c->d_img, c->d_tag, c->d_cell, c->d_rank, c->d_count, c->d_start,
                   c->d_bsum, c->d_cr, c->d_crf, c->d_rf, c->d_cid, c->d_ctag, c->d_cnt, c->d_sums, c->d_status,
-                  c->d_unit_next, c->d_n_deferred, c->d_deferred, c->d_obs_d, c->d_obs_u, c->d_g1ref, c->d_rdig, c->d_rlift, c->d_rev,
+                  c->d_unit_next, c->d_n_deferred, c->d_ftag, c->d_deferred, c->d_obs_d, c->d_obs_u, c->d_g1ref, c->d_rdig, c->d_rlift, c->d_rev,
                   c->d_log, c->d_log_n, c->d_su, c->d_srec, c->d_spart,
-                  c->d_sr2n, c->d_ssum, c->d_g2ref, c->d_shist, c->d_po_flag, c->d_po_cnt};
+                  c->d_sr2n, c->d_ssum, c->d_g2ref, c->d_shist, c->d_po_flag, c->d_po_cnt, c->d_po_ctr,
+                  c->d_g1ring, c->d_g1sum, c->d_g1cnt};
   for (void *p : ptrs) cudaFree(p);
   for (cudaEvent_t e : c->kev) cudaEventDestroy(e);
   if (c->ev0) cudaEventDestroy(c->ev0);
@@ -317,6 +333,8 @@ ecmc_status device_status(ecmc_ctx *c) {
   if (st == DEV_STUCK) return fail(ECMC_ESTUCK, "an event chain exceeded the event cap");
   if (st == DEV_CAPACITY) return fail(ECMC_ECAPACITY, "a tile exceeded the staging capacity");
   if (st == DEV_TILE) return fail(ECMC_ECAPACITY, "a bonded partner was not staged with its tile");
+  if ((st & 0xFF) == DEV_BOUNDS)
+    return fail(ECMC_EBOUNDS, "bounds-checked build: an index out of range was caught at site %d", st >> 8);
   return ECMC_OK;
 }
 
@@ -485,11 +503,16 @@ ecmc_status ecmc_configure(ecmc_ctx *c, const ecmc_opts *o) {
   if (lanes != 32 && lanes != 16 && lanes != 8 && lanes != 4)
     return fail(ECMC_EINVAL, "lanes must be 4, 8, 16 or 32");
   if (!(p.p_swap >= 0.0)) return fail(ECMC_EINVAL, "p_swap must be >= 0");
+  if (!(p.k_spring >= 0.0 && p.k_spring < INFINITY)) return fail(ECMC_EINVAL, "k_spring must be finite and >= 0");
+  if (p.k_spring > 0.0 && p.p_swap > 0.0)
+    return fail(ECMC_EINVAL, "swaps are not defined for bead springs (p_swap must be 0)");
   if (p.schedule != 0 && p.schedule != 1) return fail(ECMC_EINVAL, "schedule must be 0 or 1");
   if (p.block_tiles < 0 || p.block_tiles > 32 || p.block_tiles * lanes > 128 ||
       (p.block_tiles > 0 && lanes > 1 && p.block_tiles % (32 / lanes) != 0))
     return fail(ECMC_EINVAL, "block_tiles must be a multiple of 32 / lanes, at most 32 and 128 / lanes");
   if (p.request_cap < 0 || p.request_cap > 6) return fail(ECMC_EINVAL, "request_cap must be in [0, 6]");
+  if (!(p.tight_factor == 0.0 || (p.tight_factor >= 0.5 && p.tight_factor <= 4.0)))
+    return fail(ECMC_EINVAL, "tight_factor must be 0 or in [0.5, 4]");
   const double margin = p.precision == ECMC_PREC_FP32F ? 0.01 * sig : 0.0;
   for (int a = 0; a < 3; ++a)
     if (!(s_cap + sig + margin < 0.5 * c->L[a])) return fail(ECMC_EINVAL, "need s_cap + sigma < L/2");
@@ -516,7 +539,7 @@ ecmc_status ecmc_configure(ecmc_ctx *c, const ecmc_opts *o) {
     const bool derived = stage <= 0;
     if (derived) stage = stage_bound(E, rho);
     mcap = stage_bound(c->W, rho);
-    if (derived) tight_caps(E, c->W, rho, stage, mcap, &stage_t, &m_t);
+    if (derived) tight_caps(E, c->W, rho, stage, mcap, &stage_t, &m_t, p.tight_factor > 0 ? p.tight_factor : 1.08);
   } else {
     if (p.precision == ECMC_PREC_FP32F)
       for (int a = 0; a < 3; ++a)
@@ -552,7 +575,7 @@ ecmc_status ecmc_configure(ecmc_ctx *c, const ecmc_opts *o) {
     if (mcap > stage) mcap = stage;
     const int M = (p.precision == ECMC_PREC_FP32F && p.mode == ECMC_MODE_DOMAIN) ? mcap : stage;
     const bool lock = p.mode == ECMC_MODE_DOMAIN && p.precision == ECMC_PREC_FP32F && p.schedule == 0 &&
-                      (lanes == 4 || lanes == 8 || lanes == 16);
+                      p.k_spring == 0.0 && (lanes == 4 || lanes == 8 || lanes == 16);
     const int bt = p.block_tiles > 0 ? p.block_tiles : gmin;
     const size_t need = lock ? lock_smem_bytes(stage, M, (int)ncl, bt) : ec_smem_bytes(stage, M, (int)ncl, gmin);
     if ((int64_t)need > smem_max)
@@ -582,6 +605,7 @@ ecmc_status ecmc_configure(ecmc_ctx *c, const ecmc_opts *o) {
   c->event_cap = p.event_cap > 0 ? p.event_cap : 10000000;
   c->ecs_per_tile = p.ecs_per_tile > 0 ? p.ecs_per_tile : 1;
   c->configured = true;
+  if (p.k_spring > 0.0 && p.mode == ECMC_MODE_DOMAIN && !c->d_ftag) CU(dalloc(&c->d_ftag, c->n));
   const double side = p.cell_side > 0 ? p.cell_side : 1.05 * sig;
   if (!(side >= sig)) return fail(ECMC_EINVAL, "cell side must be >= sigma");
   return set_grid(c, side);
@@ -621,8 +645,9 @@ static ecmc_status reserve_records(ecmc_ctx *c, int64_t units) {
 // one EC launch between a pair of events (the pair is reused across runs)
 // the block-lockstep kernel runs the screened domain form with 4, 8 or 16 lanes
 static bool uses_lock(const ecmc_opts &o, int lanes) {
+  // (bead springs run in the warp-lockstep kernel)
   return o.mode == ECMC_MODE_DOMAIN && o.precision == ECMC_PREC_FP32F && o.schedule == 0 &&
-         (lanes == 4 || lanes == 8 || lanes == 16);
+         o.k_spring == 0.0 && (lanes == 4 || lanes == 8 || lanes == 16);
 }
 
 static cudaError_t timed_ec(ecmc_ctx *c, const ECParams &P, int64_t slot) {
@@ -710,7 +735,35 @@ static ECParams ec_params(const ecmc_ctx *c, uint64_t seed, double ell) {
   P.counters = c->d_cnt;
   P.sums = c->d_sums;
   P.status = c->d_status;
+  P.k_spring = c->opts.k_spring;
   return P;
+}
+
+static G1Track g1_params(const ecmc_ctx *c) {
+  G1Track G{};
+  G.n = c->n;
+  G.N = c->N;
+  for (int a = 0; a < 3; ++a) G.L[a] = c->L[a];
+  G.r = c->d_r;
+  G.img = c->d_img;
+  G.ring = c->d_g1ring;
+  G.sum = c->d_g1sum;
+  G.cnt = c->d_g1cnt;
+  G.P = c->g1_P;
+  G.K = c->g1_K;
+  int64_t pk = 1;
+  for (int k = 0; k < c->g1_K; ++k) {
+    G.Pk[k] = pk;
+    pk *= c->g1_P;
+  }
+  G.t = c->g1_t;
+  return G;
+}
+
+// one sweep more of the g1 table (after the sweep's EC launch)
+static cudaError_t g1_step(ecmc_ctx *c) {
+  c->g1_t += 1;
+  return launch_g1_track(g1_params(c), c->stream);
 }
 
 ecmc_status ecmc_run(ecmc_ctx *c, double ell, int64_t chains_per_sweep, uint64_t seed,
@@ -760,6 +813,7 @@ ecmc_status ecmc_run(ecmc_ctx *c, double ell, int64_t chains_per_sweep, uint64_t
       P.sweep = sweep;
       P.rec_offset = s * ntile * k;
       CU(timed_ec(c, P, 2 * s));
+      if (c->g1_P) CU(g1_step(c));
     }
   } else {
     P.n_units = 1;
@@ -842,6 +896,7 @@ ecmc_status ecmc_observables(ecmc_ctx *c, ecmc_obs *out) {
   out->ec_kernel_seconds = c->ec_seconds;
   out->confirmed = (int64_t)h[CNT_CONFIRMED];
   out->exhaustive = (int64_t)h[CNT_EXHAUSTIVE];
+  out->bond_mean = c->N > 1 ? o.bond_sum / (double)((c->n / c->N) * (c->N - 1)) : 0.0;
   const double d = CONTACT_DELTA * c->sigma;
   for (int k = 0; k < 2; ++k) {
     out->contact_pairs[k] = (int64_t)o.pairs[k];
@@ -976,11 +1031,13 @@ ecmc_status ecmc_pushoff(ecmc_ctx *c, double f0, int32_t stages, double ell, uin
   if (sweeps_out) *sweeps_out = 0;
   if (!c->configured || c->opts.mode != ECMC_MODE_DOMAIN || c->opts.precision != ECMC_PREC_FP64)
     return fail(ECMC_EINVAL, "push-off needs the domain mode and FP64");
+  if (c->opts.k_spring > 0.0) return fail(ECMC_EINVAL, "push-off runs hard tethers (k_spring must be 0)");
   if (!(f0 > 0.0 && f0 <= 1.0) || stages < 1 || max_sweeps < 1 || !(ell >= 0.0 && ell < INFINITY))
     return fail(ECMC_EINVAL, "need 0 < f0 <= 1, stages >= 1, max_sweeps >= 1, finite ell >= 0");
   if (!c->d_po_flag) {
     CU(dalloc(&c->d_po_flag, c->n));
     CU(dalloc(&c->d_po_cnt, 1));
+    CU(dalloc(&c->d_po_ctr, 2));
   }
   CU(cudaMemsetAsync(c->d_status, 0, sizeof(int), c->stream));
   ECParams P = ec_params(c, seed, ell);
@@ -1011,34 +1068,56 @@ ecmc_status ecmc_pushoff(ecmc_ctx *c, double f0, int32_t stages, double ell, uin
     P.stage_cap = (int32_t)S;
     P.m_cap = (int32_t)S;
   }
+  // The sweeps run from the device: the sweep index and the sweeps run at
+  // the current diameter live in d_po_ctr; every sweep is the cell pass,
+  // the overlap flags and an EC launch that does nothing once no bead
+  // overlaps, then the counters advance only if that launch ran.  The host
+  // reads the counters once per chunk of sweeps (and checks the flags once
+  // more after it), so a stage that ends inside a chunk ends exactly where
+  // the sweep-by-sweep loop would.
   const ObsParams O = obs_params(c);
+  P.sweep_dev = c->d_po_ctr;
+  P.po_count = c->d_po_cnt;
+  const int64_t CHUNK = 64;
   int64_t sweeps = 0;
+  int64_t ctr[2] = {c->sweeps_done, 0};
+  CU(cudaMemcpyAsync(c->d_po_ctr, ctr, sizeof(ctr), cudaMemcpyHostToDevice, c->stream));
+  CellParams C = cell_params(c, true, seed, 0);
+  C.sweep_dev = c->d_po_ctr;
   for (int32_t k = 0; k <= stages; ++k) {
     const double d =
         k == stages ? c->sigma : c->sigma * (f0 + (1.0 - f0) * (double)k / (double)stages);
     P.sigma = d;
     P.sig2 = d * d;
     const double thr = d * d * (1.0 - 1e-10);
-    for (int64_t s = 0;; ++s) {
-      const int64_t sweep = c->sweeps_done;
-      CU(launch_cells(cell_params(c, true, seed, sweep), c->ncell, c->stream));
+    CU(cudaMemsetAsync(c->d_po_ctr + 1, 0, sizeof(int64_t), c->stream));
+    int64_t ran = 0;
+    for (;;) {
+      const int64_t n = max_sweeps - ran < CHUNK ? max_sweeps - ran : CHUNK;
+      for (int64_t i = 0; i < n; ++i) {
+        CU(launch_cells(C, c->ncell, c->stream));
+        CU(launch_po_flags(O, thr, c->d_po_flag, c->d_po_cnt, c->stream));
+        CU(launch_ec(P, c->lanes, 0, c->stream));
+        CU(launch_po_advance(c->d_po_cnt, c->d_po_ctr, c->stream));
+      }
+      // the overlaps left after the chunk
+      CU(launch_cells(C, c->ncell, c->stream));
       CU(launch_po_flags(O, thr, c->d_po_flag, c->d_po_cnt, c->stream));
       unsigned long long cnt = 0;
       CU(cudaMemcpyAsync(&cnt, c->d_po_cnt, sizeof(cnt), cudaMemcpyDeviceToHost, c->stream));
-      CU(cudaStreamSynchronize(c->stream));
+      CU(cudaMemcpyAsync(ctr, c->d_po_ctr, sizeof(ctr), cudaMemcpyDeviceToHost, c->stream));
+      ecmc_status st = device_status(c);  // synchronises
+      if (st != ECMC_OK) return st;
+      ran = ctr[1];
+      c->sweeps_done = ctr[0];
       if (cnt == 0) break;
-      if (s == max_sweeps) {
-        if (sweeps_out) *sweeps_out = sweeps;
+      if (ran >= max_sweeps) {
+        if (sweeps_out) *sweeps_out = sweeps + ran;
         return fail(ECMC_ESTUCK, "push-off: %llu beads overlap at diameter %.6g after %lld sweeps",
                     cnt, d, (long long)max_sweeps);
       }
-      P.sweep = sweep;
-      CU(timed_ec(c, P, 0));
-      ecmc_status st = device_status(c);
-      if (st != ECMC_OK) return st;
-      c->sweeps_done += 1;
-      ++sweeps;
     }
+    sweeps += ran;
   }
   if (sweeps_out) *sweeps_out = sweeps;
   ecmc_status st = check_state(c);
@@ -1062,6 +1141,68 @@ ecmc_status ecmc_g1_reset(ecmc_ctx *c) {
   }
   c->g1_set = true;
   CU(cudaStreamSynchronize(c->stream));
+  return ECMC_OK;
+}
+
+ecmc_status ecmc_g1_track(ecmc_ctx *c, int32_t P, int32_t K) {
+  if (!c) return fail(ECMC_EINVAL, "ctx is NULL");
+  if (P == 0) {
+    c->g1_P = 0;
+    return ECMC_OK;
+  }
+  if (P < 2 || P > 64 || K < 1 || K > 16) return fail(ECMC_EINVAL, "need 2 <= P <= 64 and 1 <= K <= 16");
+  double top = 1.0;
+  for (int k = 0; k < K; ++k) top *= P;
+  if (!(top < 4.0e18)) return fail(ECMC_EINVAL, "P^K must stay below 4e18 sweeps");
+  const int64_t nch = c->n / c->N;
+  const size_t ring_n = (size_t)K * P * (size_t)nch * 3;
+  const size_t nlag = (size_t)K * (P - 1);
+  if (ring_n > c->g1ring_n) {
+    cudaFree(c->d_g1ring);
+    c->d_g1ring = nullptr;
+    c->g1ring_n = 0;
+    CU(dalloc(&c->d_g1ring, ring_n));
+    c->g1ring_n = ring_n;
+  }
+  if (!c->d_g1sum) {
+    CU(dalloc(&c->d_g1sum, 16 * 63));
+    CU(dalloc(&c->d_g1cnt, 16 * 63));
+  }
+  CU(cudaMemsetAsync(c->d_g1sum, 0, sizeof(double) * nlag, c->stream));
+  CU(cudaMemsetAsync(c->d_g1cnt, 0, sizeof(unsigned long long) * nlag, c->stream));
+  c->g1_P = P;
+  c->g1_K = K;
+  c->g1_t = 0;
+  CU(launch_g1_track(g1_params(c), c->stream));  // the snapshot at t = 0
+  return ECMC_OK;
+}
+
+ecmc_status ecmc_g1_table(ecmc_ctx *c, int64_t *lag, double *g1, int64_t *count, int32_t cap,
+                          int32_t *n) {
+  if (!c || !n) return fail(ECMC_EINVAL, "NULL argument");
+  if (!c->d_g1sum || c->g1_K == 0) {
+    *n = 0;
+    return ECMC_OK;
+  }
+  const int nlag = c->g1_K * (c->g1_P - 1);
+  std::vector<double> sum((size_t)nlag);
+  std::vector<unsigned long long> cnt((size_t)nlag);
+  CU(cudaMemcpyAsync(sum.data(), c->d_g1sum, sizeof(double) * nlag, cudaMemcpyDeviceToHost, c->stream));
+  CU(cudaMemcpyAsync(cnt.data(), c->d_g1cnt, sizeof(unsigned long long) * nlag, cudaMemcpyDeviceToHost,
+                     c->stream));
+  CU(cudaStreamSynchronize(c->stream));
+  const int m = nlag < cap ? nlag : (cap > 0 ? cap : 0);
+  const double nch = (double)(c->n / c->N);
+  int64_t pk = 1;
+  for (int k = 0, q = 0; k < c->g1_K; ++k, pk *= c->g1_P) {
+    for (int j = 1; j < c->g1_P; ++j, ++q) {
+      if (q >= m) break;
+      if (lag) lag[q] = (int64_t)j * pk;
+      if (count) count[q] = (int64_t)cnt[q];
+      if (g1) g1[q] = cnt[q] ? sum[q] / ((double)cnt[q] * nch) : 0.0;
+    }
+  }
+  *n = m;
   return ECMC_OK;
 }
 
@@ -1138,7 +1279,7 @@ ecmc_status ecmc_domain_tags(ecmc_ctx *c, uint64_t seed, int64_t sweep, int32_t 
   if (!c->configured || c->opts.mode != ECMC_MODE_DOMAIN)
     return fail(ECMC_EINVAL, "configure the domain mode first");
   CU(launch_cells(cell_params(c, true, seed, sweep), c->ncell, c->stream));
-  CU(cudaMemcpyAsync(tags, c->d_tag, sizeof(int32_t) * c->n, cudaMemcpyDeviceToHost, c->stream));
+  CU(cudaMemcpyAsync(tags, (c->opts.k_spring > 0.0 && c->N > 1) ? c->d_ftag : c->d_tag, sizeof(int32_t) * c->n, cudaMemcpyDeviceToHost, c->stream));
   CU(cudaStreamSynchronize(c->stream));
   if (shift) {
     const u64x4 w = philox(TAG_SHIFT, (uint64_t)sweep, 0, 0, seed, 0);
@@ -1182,7 +1323,7 @@ ecmc_status ecmc_checkpoint(ecmc_ctx *c, const char *path) {
   CkptHeader hd;
   memset(&hd, 0, sizeof(hd));
   hd.magic = CKPT_MAGIC;
-  hd.version = 2;
+  hd.version = 3;
   hd.n = c->n;
   hd.N = c->N;
   for (int a = 0; a < 3; ++a) hd.L[a] = c->L[a];
@@ -1224,7 +1365,7 @@ ecmc_status ecmc_restore(ecmc_ctx *c, const char *path) {
   std::vector<int32_t> im(3 * c->n);
   uint64_t hfile = 0;
   bool ok = fread(&hd, sizeof(hd), 1, f) == 1;
-  ok = ok && hd.magic == CKPT_MAGIC && hd.version == 2 && hd.n == c->n && hd.N == c->N;
+  ok = ok && hd.magic == CKPT_MAGIC && hd.version == 3 && hd.n == c->n && hd.N == c->N;
   ok = ok && fread(r.data(), sizeof(double), r.size(), f) == r.size() &&
        fread(im.data(), sizeof(int32_t), im.size(), f) == im.size() &&
        fread(&hfile, sizeof(hfile), 1, f) == 1;
@@ -1292,12 +1433,20 @@ ecmc_status ecmc_autotune(ecmc_ctx *c, double ell, uint64_t seed, int32_t trial_
     c->ec_seconds = es0;
     return ECMC_OK;
   };
+  // the staging axes apply to the block-lockstep kernel only; elsewhere a
+  // point off their defaults is not admissible (never timed)
+  auto lock_point = [&](const TunePoint &pt) {
+    return base.mode == ECMC_MODE_DOMAIN && base.precision == ECMC_PREC_FP32F && base.schedule == 0 &&
+           base.k_spring == 0.0 && (pt.lanes == 4 || pt.lanes == 8 || pt.lanes == 16);
+  };
   auto point_opts = [&](const TunePoint &pt) {
     ecmc_opts o = base;
     o.lanes = pt.lanes;
     o.cell_side = pt.cell_side * sig;
     o.ecs_per_tile = pt.ecs;
     o.stage_cap = 0;
+    o.block_tiles = lock_point(pt) ? pt.warps * 32 / pt.lanes : 0;
+    o.tight_factor = pt.tight;
     for (int a = 0; a < 3; ++a) {
       int D = (int)floor(c->L[a] / (pt.tile_side * sig));
       if (D < 3) D = 3;
@@ -1312,6 +1461,7 @@ ecmc_status ecmc_autotune(ecmc_ctx *c, double ell, uint64_t seed, int32_t trial_
     return ECMC_OK;
   };
   auto trial = [&](const TunePoint &pt, TuneScore *sc) -> ecmc_status {
+    if (!lock_point(pt) && (pt.warps != 1 || pt.tight != 1.08)) return ECMC_EINVAL;
     ecmc_opts o = point_opts(pt);
     o.record = 0;
     ecmc_status st = ecmc_configure(c, &o);
@@ -1334,7 +1484,10 @@ ecmc_status ecmc_autotune(ecmc_ctx *c, double ell, uint64_t seed, int32_t trial_
     return ECMC_OK;
   };
   TunePoint start{c->lanes, c->T[0] / sig * (1.0 - 1e-9),
-                  base.cell_side > 0 ? base.cell_side / sig : 1.05, c->ecs_per_tile};
+                  base.cell_side > 0 ? base.cell_side / sig : 1.05, c->ecs_per_tile, 1, 1.08};
+  if (base.block_tiles > 0 && (c->lanes == 4 || c->lanes == 8 || c->lanes == 16))
+    start.warps = base.block_tiles * c->lanes / 32;
+  if (base.tight_factor > 0.0) start.tight = base.tight_factor;
   TunePoint best{};
   TuneScore best_s{};
   int n = 0;
@@ -1352,6 +1505,8 @@ ecmc_status ecmc_autotune(ecmc_ctx *c, double ell, uint64_t seed, int32_t trial_
   out->tile_side = best.tile_side;
   out->cell_side = best.cell_side;
   out->ecs_per_tile = best.ecs;
+  out->block_tiles = o.block_tiles;
+  out->tight_factor = best.tight;
   for (int a = 0; a < 3; ++a) out->tiles[a] = o.tiles[a];
   out->ecs_per_s = best_s.ecs_per_s;
   out->events_per_s = best_s.events_per_s;

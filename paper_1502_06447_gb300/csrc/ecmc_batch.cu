@@ -33,6 +33,7 @@ template <class T>
 cudaError_t balloc(T **p, size_t count) {
   *p = nullptr;
   if (count == 0) count = 1;
+  if (alloc_refused(sizeof(T) * count)) return cudaErrorMemoryAllocation;
   return cudaMalloc((void **)p, sizeof(T) * count);
 }
 }  // namespace
@@ -301,6 +302,7 @@ ecmc_status ecmc_batch_configure(ecmc_batch *b, const ecmc_opts *o) {
   if (lanes != 32 && lanes != 16 && lanes != 8 && lanes != 4)
     return bfail(ECMC_EINVAL, "batch lanes must be 4, 8, 16 or 32");
   if (!(p.p_swap >= 0.0)) return bfail(ECMC_EINVAL, "p_swap must be >= 0");
+  if (p.k_spring != 0.0) return bfail(ECMC_EINVAL, "the batch runs hard tethers (k_spring must be 0)");
   const double sig = b->sigma;
   const double s_cap = p.s_cap > 0 ? p.s_cap : 0.25 * sig;
   const double w = p.joint > 0 ? p.joint : b->b_max;
@@ -361,7 +363,7 @@ ecmc_status ecmc_batch_configure(ecmc_batch *b, const ecmc_opts *o) {
     stage = st > stage ? st : stage;
     mcap = mc > mcap ? mc : mcap;
     int32_t st_t = 0, mc_t = 0;
-    tight_caps(E, R.W, rho, st, mc, &st_t, &mc_t);
+    tight_caps(E, R.W, rho, st, mc, &st_t, &mc_t, p.tight_factor > 0 ? p.tight_factor : 1.08);
     stage_t = st_t > stage_t ? st_t : stage_t;
     m_t = mc_t > m_t ? mc_t : m_t;
     nclm = (int32_t)ncl > nclm ? (int32_t)ncl : nclm;
@@ -600,6 +602,11 @@ ecmc_status ecmc_batch_autotune(ecmc_batch *b, double ell, uint64_t seed, int32_
     b->device_seconds = ds0;
     return ECMC_OK;
   };
+  // the staging axes apply to the block-lockstep kernel only
+  auto lock_point = [&](const TunePoint &pt) {
+    return base.precision == ECMC_PREC_FP32F && base.schedule == 0 &&
+           (pt.lanes == 4 || pt.lanes == 8 || pt.lanes == 16);
+  };
   auto point_opts = [&](const TunePoint &pt) {
     ecmc_opts o = base;
     o.lanes = pt.lanes;
@@ -608,9 +615,12 @@ ecmc_status ecmc_batch_autotune(ecmc_batch *b, double ell, uint64_t seed, int32_
     o.cell_side = pt.cell_side * sig;
     o.ecs_per_tile = pt.ecs;
     o.stage_cap = 0;
+    o.block_tiles = lock_point(pt) ? pt.warps * 32 / pt.lanes : 0;
+    o.tight_factor = pt.tight;
     return o;
   };
   auto trial = [&](const TunePoint &pt, TuneScore *sc) -> ecmc_status {
+    if (!lock_point(pt) && (pt.warps != 1 || pt.tight != 1.08)) return ECMC_EINVAL;
     ecmc_opts o = point_opts(pt);
     o.record = 0;
     ecmc_status st = ecmc_batch_configure(b, &o);
@@ -634,7 +644,10 @@ ecmc_status ecmc_batch_autotune(ecmc_batch *b, double ell, uint64_t seed, int32_
     return ECMC_OK;
   };
   TunePoint start{b->lanes, base.tile_side / sig, base.cell_side > 0 ? base.cell_side / sig : 1.05,
-                  b->ecs_per_tile};
+                  b->ecs_per_tile, 1, 1.08};
+  if (base.block_tiles > 0 && (b->lanes == 4 || b->lanes == 8 || b->lanes == 16))
+    start.warps = base.block_tiles * b->lanes / 32;
+  if (base.tight_factor > 0.0) start.tight = base.tight_factor;
   TunePoint best{};
   TuneScore best_s{};
   int n = 0;
@@ -651,6 +664,8 @@ ecmc_status ecmc_batch_autotune(ecmc_batch *b, double ell, uint64_t seed, int32_
   out->tile_side = best.tile_side;
   out->cell_side = best.cell_side;
   out->ecs_per_tile = best.ecs;
+  out->block_tiles = o.block_tiles;
+  out->tight_factor = best.tight;
   out->tiles[0] = out->tiles[1] = out->tiles[2] = 0;
   out->ecs_per_s = best_s.ecs_per_s;
   out->events_per_s = best_s.events_per_s;

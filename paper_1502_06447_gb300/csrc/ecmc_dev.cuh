@@ -66,8 +66,11 @@ ECMC_HD u64x4 philox(uint64_t c0, uint64_t c1, uint64_t c2, uint64_t c3,
 
 // random-number layout: key (seed, replica); counter (tag | ec << 8, sweep,
 // unit, attempt).  Tags: 1 start bead + direction, 2 tile shift, 3 swap,
-// 4 lattice jitter.
-enum : uint64_t { TAG_START = 1, TAG_SHIFT = 2, TAG_SWAP = 3, TAG_JITTER = 4, TAG_PHANTOM = 5 };
+// 4 lattice jitter, 5 phantom chains, 6 spring energies (counter word 3 =
+// the event index within the EC).
+enum : uint64_t {
+  TAG_START = 1, TAG_SHIFT = 2, TAG_SWAP = 3, TAG_JITTER = 4, TAG_PHANTOM = 5, TAG_SPRING = 6
+};
 
 // top 53 bits -> [0,1)
 ECMC_HD double unit53(uint64_t w) { return (double)(w >> 11) * (1.0 / 9007199254740992.0); }

@@ -3,13 +3,16 @@
 #include <math.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
+#include <stdlib.h>
 
 #include "../../include/ecmc.h"
 
 namespace ecmc {
 
-// Device status codes (first failure wins).
-enum : int { DEV_OK = 0, DEV_STUCK = 1, DEV_CAPACITY = 2, DEV_TILE = 3 };
+// Device status codes (first failure wins).  DEV_BOUNDS (bounds-checked
+// builds only, -DECMC_CHECKED): an index out of range was caught and the
+// access skipped; the status word then holds DEV_BOUNDS | site << 8.
+enum : int { DEV_OK = 0, DEV_STUCK = 1, DEV_CAPACITY = 2, DEV_TILE = 3, DEV_BOUNDS = 4 };
 
 // Accumulator slots in the device counter array.
 enum : int {
@@ -21,6 +24,17 @@ enum : int {
   CNT_N = ECMC_NEV + 5
 };
 enum : int { SUM_LIFT = 0, SUM_REFL = 1, SUM_DISP = 2, SUM_N = 3 };
+
+// Host-side fault injection for tests: with ECMC_ALLOC_LIMIT=<bytes> in the
+// environment, every device allocation of the library above that size
+// fails as cudaMalloc does when the device is out of memory (the call then
+// returns ECMC_ENOMEM); unset or 0: no limit.
+inline bool alloc_refused(size_t bytes) {
+  const char *e = getenv("ECMC_ALLOC_LIMIT");
+  if (!e || !*e) return false;
+  const unsigned long long lim = strtoull(e, nullptr, 10);
+  return lim > 0 && bytes > lim;
+}
 
 // x > 0 rounded up to FP32 (host side)
 inline float round_up_f32(double x) {
@@ -117,6 +131,9 @@ struct ECParams {
   // flagged motile beads, one each in id order, and a pivot ignores the
   // beads it overlaps; null otherwise
   const uint8_t *po_flag;
+  // push-off run from the device: the launch does nothing when no bead
+  // overlaps (the count of the flag pass before it); null otherwise
+  const unsigned long long *po_count;
   int32_t rq_per_tile;  // request list entries per tile of the block (1..6)
   // block-lockstep kernel: tight capacities for a first pass (0: none); a
   // tile that does not fit them is listed in `deferred` and run by a second
@@ -126,6 +143,10 @@ struct ECParams {
   int32_t defer_mode;
   int32_t *deferred;
   int32_t *n_deferred;
+  // bead-spring chains (Sec. II): k > 0 replaces every tether by a harmonic
+  // spring (k/2)(b - sigma)^2; bond partners of motile beads are then staged
+  // wherever they are (a spring has no longest bond)
+  double k_spring;
 };
 
 // message for ecmc_last_error (ecmc_api.cu)
@@ -163,6 +184,13 @@ struct CellParams {
   int32_t *ctag;
   float *crf;         // FP32 positions in cell order (staging's halo test)
   float *rf;          // FP32 positions by bead (staging's shadows)
+  const int64_t *sweep_dev;  // sweep index on the device (null: `sweep`)
+  // bead-spring chains (domain mode): a bead whose bonded bead is motile in
+  // another tile is immotile for the sweep, decided on the tags of k_tag_count
+  // (`tag`); the final tags go to ctag and, by bead, to `ftag` (may be null)
+  int32_t N;
+  int32_t spring;
+  int32_t *ftag;
 };
 cudaError_t launch_cells(const CellParams &C, int64_t ncell, cudaStream_t s);
 
@@ -206,7 +234,7 @@ struct ObsParams {
   const int32_t *cid;
   const int32_t *cstart;
   const int32_t *cell;     // cell of each bead
-  double *out_d;           // [re2_sum, bond_max, bond_min(neg), g1_sum]
+  double *out_d;           // [re2_sum, bond_max, bond_min, g1_sum, bond_sum]
   // [overlaps, tether_violations, contact pairs (2 shells), taut bonds (2 shells)]
   unsigned long long *out_u;
   // squared shell bounds: pairs [lo, s1), [s1, s2); bonds (t1, t0], (t2, t1]
@@ -217,9 +245,30 @@ cudaError_t launch_obs(const ObsParams &O, cudaStream_t s);
 cudaError_t launch_wrap(double *r, int32_t *img, int64_t n, const double L[3],
                         unsigned long long *bad, cudaStream_t s);
 cudaError_t launch_g1_snapshot(const ObsParams &O, double *g1ref, cudaStream_t s);
+
+// g1 table (Sec. IV, Eq. 3): middle-bead snapshots at K levels, level k
+// taken every P^k sweeps into a ring of P slots, and the sums of squared
+// displacements for the lags j P^k (j = 1 .. P-1) over chains and origins
+struct G1Track {
+  int64_t n;
+  int32_t N;
+  double L[3];
+  const double *r;
+  const int32_t *img;
+  double *ring;              // [K][P][n / N][3]
+  double *sum;               // [K][P - 1]
+  unsigned long long *cnt;   // [K][P - 1]
+  int32_t P, K;
+  int64_t Pk[16];            // P^k
+  int64_t t;                 // sweeps since tracking began (0: first snapshot)
+};
+cudaError_t launch_g1_track(const G1Track &G, cudaStream_t s);
 // beads overlapping another at |d|^2 < thr (cell list of O), as 0/1 flags
 cudaError_t launch_po_flags(const ObsParams &O, double thr, uint8_t *flag,
                             unsigned long long *count, cudaStream_t s);
+// push-off sweep done on the device: when the flag pass counted overlaps,
+// the sweep index and the sweeps run (ctr[0], ctr[1]) advance
+cudaError_t launch_po_advance(const unsigned long long *count, int64_t *ctr, cudaStream_t s);
 // phantom chains, unwrapped (k_obs.cu); bad counts walks that ran out of attempts
 cudaError_t launch_phantom(int64_t nch, int N, const double L[3], double bond, double ct,
                            uint64_t seed, double *r, unsigned long long *bad, cudaStream_t s);
@@ -268,13 +317,14 @@ inline int32_t stage_bound(const double E[3], double rho) {
   return (int32_t)((n + 31) / 32 * 32);
 }
 
-// Tight capacities of the block-lockstep kernel's first pass: about the
-// mean occupancy of a melted tile plus a margin, rounded to 8 (tiles that
-// exceed them, e.g. at the lattice start, run in the second pass).
+// Tight capacities of the block-lockstep kernel's first pass: `factor`
+// times the mean occupancy of a melted tile plus a margin, rounded to 8
+// (tiles that exceed them, e.g. at the lattice start, run in the second
+// pass; a smaller factor fits more tiles per SM and defers more of them).
 inline void tight_caps(const double E[3], const double Wm[3], double rho, int32_t full_stage,
-                       int32_t full_m, int32_t *stage_t, int32_t *m_t) {
+                       int32_t full_m, int32_t *stage_t, int32_t *m_t, double factor = 1.08) {
   const double vs = E[0] * E[1] * E[2], vm = Wm[0] * Wm[1] * Wm[2];
-  int64_t st = (int64_t)ceil(1.08 * rho * vs + 16.0);
+  int64_t st = (int64_t)ceil(factor * rho * vs + 16.0);
   int64_t mt = (int64_t)ceil(1.2 * rho * vm + 12.0);
   st = (st + 7) / 8 * 8;
   mt = (mt + 7) / 8 * 8;
@@ -285,9 +335,10 @@ inline void tight_caps(const double E[3], const double Wm[3], double rho, int32_
 
 // ---------------------------------------------------------------- autotuner
 // One launch setting of the domain sweep.  The search is a coordinate
-// descent: lanes per EC, then tile side, then global cell side, then ECs per
-// tile, each axis scanned with the others held at their best so far, in up
-// to two rounds.  The
+// descent: lanes per EC, tile side, global cell side, ECs per tile, and the
+// staging of the block-lockstep kernel (warps per block, the first pass's
+// capacity factor), each axis scanned with the others held at their best so
+// far, in up to two rounds.  The
 // objective is ECs per device-second (each EC displaces by ell, so this is
 // the rate of progress of the Markov chain; events/s would reward small
 // tiles for their extra wall reflections).
@@ -296,6 +347,8 @@ struct TunePoint {
   double tile_side;  // in units of sigma
   double cell_side;  // in units of sigma
   int ecs;
+  int warps;         // block lockstep: warps per block (tiles = warps 32 / lanes)
+  double tight;      // block lockstep: first-pass capacity factor
 };
 
 struct TuneScore {
@@ -311,18 +364,21 @@ ecmc_status tune_search(TunePoint start, Trial trial, TunePoint *best, TuneScore
   static const double tile_c[] = {3.4, 4.2, 5.0, 6.0, 7.0};
   static const double cell_c[] = {1.05, 1.4};
   static const int ecs_c[] = {1, 2, 4};
+  static const int warps_c[] = {1, 2, 4};
+  static const double tight_c[] = {1.0, 1.08, 1.16};
   TunePoint cur = start;
   TuneScore cur_s{};
   bool have = false;
   int n = 0;
   // points already timed (a second round revisits none of them)
-  constexpr int VMAX = 64;
+  constexpr int VMAX = 128;
   TunePoint seen[VMAX];
   int nseen = 0;
   auto consider = [&](const TunePoint &pt) -> ecmc_status {
     for (int i = 0; i < nseen; ++i)
       if (seen[i].lanes == pt.lanes && seen[i].tile_side == pt.tile_side &&
-          seen[i].cell_side == pt.cell_side && seen[i].ecs == pt.ecs)
+          seen[i].cell_side == pt.cell_side && seen[i].ecs == pt.ecs && seen[i].warps == pt.warps &&
+          seen[i].tight == pt.tight)
         return ECMC_OK;
     if (nseen < VMAX) seen[nseen++] = pt;
     TuneScore sc{};
@@ -339,11 +395,11 @@ ecmc_status tune_search(TunePoint start, Trial trial, TunePoint *best, TuneScore
   };
   ecmc_status st = consider(start);
   if (st != ECMC_OK) return st;
-  // two rounds over the four axes: a later axis can change the best choice
+  // two rounds over the six axes: a later axis can change the best choice
   // on an earlier one (a round that changes nothing ends the search)
   for (int round = 0; round < 2; ++round) {
     const TunePoint before = cur;
-    for (int axis = 0; axis < 4; ++axis) {
+    for (int axis = 0; axis < 6; ++axis) {
       const TunePoint base = cur;
       const int cnt = axis == 0 ? 4 : axis == 1 ? 5 : axis == 2 ? 2 : 3;
       for (int i = 0; i < cnt; ++i) {
@@ -352,12 +408,15 @@ ecmc_status tune_search(TunePoint start, Trial trial, TunePoint *best, TuneScore
         if (axis == 1) pt.tile_side = tile_c[i];
         if (axis == 2) pt.cell_side = cell_c[i];
         if (axis == 3) pt.ecs = ecs_c[i];
+        if (axis == 4) pt.warps = warps_c[i];
+        if (axis == 5) pt.tight = tight_c[i];
         st = consider(pt);
         if (st != ECMC_OK) return st;
       }
     }
     if (round == 0 && before.lanes == cur.lanes && before.tile_side == cur.tile_side &&
-        before.cell_side == cur.cell_side && before.ecs == cur.ecs)
+        before.cell_side == cur.cell_side && before.ecs == cur.ecs && before.warps == cur.warps &&
+        before.tight == cur.tight)
       break;
   }
   if (!have) return ECMC_EINVAL;

@@ -7,7 +7,9 @@
 // cell grid (counting sort: count with atomics, exclusive scan, scatter of
 // positions/ids/tiles into cell order).  The order of beads inside one cell
 // is not fixed; nothing downstream depends on it (the EC kernel sorts what
-// it stages by bead id).
+// it stages by bead id).  With bead springs a bead whose bonded bead is
+// motile in another tile is made immotile too (a spring has no longest
+// bond, so only this keeps tiles apart).
 #include <cuda_runtime.h>
 
 #include "ecmc_dev.cuh"
@@ -25,7 +27,8 @@ __global__ void k_tag_count(const CellParams C) {
   if (b >= C.n) return;
   const double r0 = C.r[3 * b], r1 = C.r[3 * b + 1], r2 = C.r[3 * b + 2];
   if (C.domain) {
-    const u64x4 w = philox(TAG_SHIFT, (uint64_t)C.sweep, 0, 0, C.seed, C.replica);
+    const int64_t sweep = C.sweep_dev ? *C.sweep_dev : C.sweep;
+    const u64x4 w = philox(TAG_SHIFT, (uint64_t)sweep, 0, 0, C.seed, C.replica);
     const double rr[3] = {r0, r1, r2};
     int k[3];
     bool in = true;
@@ -149,7 +152,18 @@ __global__ void k_scatter(const CellParams C) {
   C.rf[3 * b + 1] = (float)y;
   C.rf[3 * b + 2] = (float)z;
   C.cid[pos] = (int32_t)b;
-  C.ctag[pos] = C.tag[b];
+  int32_t t = C.tag[b];
+  if (C.spring && t >= 0) {
+    // bead-spring chains: a bead whose bonded bead is motile in another
+    // tile waits for a later sweep (the tags of both are the ones
+    // k_tag_count assigned, before any is dropped)
+    const int64_t c = b % C.N;
+    const int32_t tp = c != 0 ? C.tag[b - 1] : -1;
+    const int32_t tn = c != C.N - 1 ? C.tag[b + 1] : -1;
+    if ((tp >= 0 && tp != t) || (tn >= 0 && tn != t)) t = -1;
+  }
+  C.ctag[pos] = t;
+  if (C.ftag) C.ftag[b] = t;
 }
 
 __global__ void k_tag_count_b(const CellBatch C) {

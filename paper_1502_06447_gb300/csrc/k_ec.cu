@@ -1,5 +1,6 @@
-// Event-chain kernels (arXiv:1502.06447, Sec. II: EC move; Sec. II.A:
-// tile-joint decomposition with reflections; Sec. II.C: swap move).
+// Event-chain kernels (arXiv:1502.06447, Sec. II: EC move, with hard tethers
+// or harmonic bead springs; Sec. II.A: tile-joint decomposition with
+// reflections; Sec. II.C: swap move).
 //
 // One group of G lanes (G = 32, 16, 8 or 4) runs the ECs of one tile; the
 // 32/G groups of a warp advance in lockstep, one event per iteration, so
@@ -34,6 +35,8 @@ namespace {
 template <int G, bool F32, bool BATCH>
 __global__ void __launch_bounds__(128) ec_kernel(const ECParams P) {
   extern __shared__ __align__(16) unsigned char smem[];
+  // push-off run from the device: nothing to do once no bead overlaps
+  if (P.po_count && *P.po_count == 0ull) return;
   const int lane = threadIdx.x & 31;
   const int gl = lane & (G - 1);
   const int gbase = lane & ~(G - 1);
@@ -63,6 +66,10 @@ __global__ void __launch_bounds__(128) ec_kernel(const ECParams P) {
   const int NC = P.domain ? (BATCH ? P.ncl_max : SYS(lg)[0] * SYS(lg)[1] * SYS(lg)[2]) : 0;
   const int M = (F32 && P.domain) ? P.m_cap : S;
   Stage st = carve(smem + (size_t)gib * group_bytes(S, M, M, NC), S, M, M, NC);
+#ifdef ECMC_CHECKED
+  st.status = P.status;
+  st.nglob = BATCH ? rp->n_beads : P.n;
+#endif
   bool live = gunit < P.n_units;
   const uint64_t hb0 = dbits(SYS(half)[0]), hb1 = dbits(SYS(half)[1]), hb2 = dbits(SYS(half)[2]);
   LGrid LG;
@@ -233,6 +240,29 @@ __global__ void __launch_bounds__(128) ec_kernel(const ECParams P) {
         } else if (it <= 2) {
           const int t = it == 1 ? nb_prev(nbw) : nb_next(nbw);
           if (t < 0) continue;
+          if (P.k_spring > 0.0) {
+            // bead spring (Sec. II, ECs with pair potentials): a fresh
+            // Boltzmann energy per bond and event, spent on the rising part
+            // of the path; always evaluated in FP64, and in the screened
+            // form its exact x bounds U from above
+            const u64x4 w = philox(TAG_SPRING | ((uint64_t)(P.domain ? e : 0) << 8), r1, r2,
+                                   (uint64_t)nev, P.seed, Rkey);
+            double kx, ky, kz, dv;
+            pos64(st, Rr, t, !F32 || t < m, kx, ky, kz);
+            // (a spring partner may lie beyond the tile's halo, across the
+            // periodic boundary: always the minimum image)
+            const double x = spring_x(wrap_i(q0 - kx, SYS(L)[0], hb0), wrap_i(q1 - ky, SYS(L)[1], hb1),
+                                      wrap_i(q2 - kz, SYS(L)[2], hb2), v0, v1, v2, P.sigma,
+                                      P.k_spring, spring_dE(it == 1 ? w.v[0] : w.v[1]), dv);
+            const uint64_t key = make_key(KIND_TETHER, st.id[t], t);
+            if (better(x, key, bx, bkey)) {
+              bx = x;
+              bkey = key;
+              bdv = dv;
+            }
+            if (F32) ubl = fminf(ubl, __double2float_ru(x));
+            continue;
+          }
           if (!F32) {
             double dv;
             const double x = quad_x(true, wrapc(q0 - st.px[t], SYS(L)[0], hb0, wr0),
@@ -519,8 +549,9 @@ __global__ void __launch_bounds__(128) ec_kernel(const ECParams P) {
             refl_all = refl_all + proj;
             double kx, ky, kz;
             pos64(st, Rr, slot, !F32 || slot < m, kx, ky, kz);
-            mirror2(v0, v1, v2, wrapc(q0 - kx, SYS(L)[0], hb0, wr0), wrapc(q1 - ky, SYS(L)[1], hb1, wr1),
-                    wrapc(q2 - kz, SYS(L)[2], hb2, wr2));
+            const bool sp = P.k_spring > 0.0 && kind == KIND_TETHER;
+            mirror2(v0, v1, v2, wrapc(q0 - kx, SYS(L)[0], hb0, wr0 || sp),
+                    wrapc(q1 - ky, SYS(L)[1], hb1, wr1 || sp), wrapc(q2 - kz, SYS(L)[2], hb2, wr2 || sp));
           } else if (kind == KIND_HS) {
             lift = lift + proj;
             if (P.swap_mode) {

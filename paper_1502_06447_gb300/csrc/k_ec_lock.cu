@@ -1,6 +1,7 @@
 // Block-lockstep EC kernel of the screened domain form (arXiv:1502.06447,
-// Sec. II: EC move; Sec. II.A: tiles, joints and reflections; Sec. II.C:
-// swap move).
+// Sec. II: EC move with hard tethers; Sec. II.A: tiles, joints and
+// reflections; Sec. II.C: swap move).  Bead springs run in the warp-lockstep
+// kernel (k_ec.cu).
 //
 // A block runs NT tiles.  Each tile is staged and screened by a group of G
 // lanes exactly as in ec_kernel, but all NT tiles advance one event per step
@@ -101,6 +102,10 @@ __global__ void __launch_bounds__(128, 3) ec_lock_kernel(const ECParams P) {
   const int MNB = P.m_cap;
   const size_t gbytes = group_bytes(S, 0, MNB, NC);
   Stage st = carve(smem + (size_t)gib * gbytes, S, 0, MNB, NC);
+#ifdef ECMC_CHECKED
+  st.status = P.status;
+  st.nglob = P.n;
+#endif
   TileRec *tr = (TileRec *)(smem + (size_t)NT * gbytes);
   int2 *rq = (int2 *)(tr + NT);
   Res *rs = (Res *)(rq + NT * RQ_PER_TILE);
@@ -157,6 +162,9 @@ __global__ void __launch_bounds__(128, 3) ec_lock_kernel(const ECParams P) {
       unit = gu - (int)rp->unit_off;
     }
     Rr = BATCH ? P.r + 3 * rp->bead_off : P.r;
+#ifdef ECMC_CHECKED
+    if (BATCH) st.nglob = rp->n_beads;
+#endif
     const int32_t *const Rstart = BATCH ? P.cstart + rp->cell_off : P.cstart;
     const uint64_t Rkey = BATCH ? rp->replica : P.replica;
     LG.g0 = SYS(lg)[0];
@@ -180,7 +188,7 @@ __global__ void __launch_bounds__(128, 3) ec_lock_kernel(const ECParams P) {
     bool over = false;
     stage_tile<G, true, BATCH>(P, rp, st, gl, live, unit, c0, c1, c2, Rr, Rstart, S, 0, MNB, NC, LG,
                                m, j1, ns, gmask, P.defer_mode == 1 ? &over : nullptr);
-    if (over && gl == 0) P.deferred[atomicAdd(P.n_deferred, 1)] = gu;
+    if (over && gl == 0) P.deferred[CI(atomicAdd(P.n_deferred, 1), P.n_units, 32, P.status)] = gu;
     if (!live) m = 0;
     if (gl == 0) {
       TileRec &T = tr[gib];
@@ -208,6 +216,10 @@ __global__ void __launch_bounds__(128, 3) ec_lock_kernel(const ECParams P) {
   const RepParams *orp = nullptr;
   int o_unit = 0, o_gunit = 0, om = 0;
   Stage ost = carve(smem + (size_t)ot * gbytes, S, 0, MNB, NC);
+#ifdef ECMC_CHECKED
+  ost.status = P.status;
+  ost.nglob = P.n;
+#endif
   double *oRr = P.r;
   int32_t *oRi = P.img;
   uint64_t oKey = P.replica;
@@ -217,6 +229,9 @@ __global__ void __launch_bounds__(128, 3) ec_lock_kernel(const ECParams P) {
   float ocf0 = 0.f, ocf1 = 0.f, ocf2 = 0.f, oLh0 = 0.f, oLh1 = 0.f, oLh2 = 0.f;
   LGrid OLG;
   uint64_t r2 = 0;
+  // beads of the owned tile's system (bounds of the checked build)
+  auto ost_n = [&]() -> int64_t { return BATCH ? (orp ? orp->n_beads : 0) : P.n; };
+  (void)ost_n;
   // the owned slot's new tile
   auto load_tile = [&]() {
     const TileRec &T = tr[ot];
@@ -227,6 +242,9 @@ __global__ void __launch_bounds__(128, 3) ec_lock_kernel(const ECParams P) {
     oRr = BATCH ? P.r + 3 * orp->bead_off : P.r;
     oRi = BATCH ? P.img + 3 * orp->bead_off : P.img;
     oKey = BATCH ? orp->replica : P.replica;
+#ifdef ECMC_CHECKED
+    if (BATCH) ost.nglob = orp->n_beads;
+#endif
     oL0 = TSYS(orp, L)[0];
     oL1 = TSYS(orp, L)[1];
     oL2 = TSYS(orp, L)[2];
@@ -314,7 +332,8 @@ __global__ void __launch_bounds__(128, 3) ec_lock_kernel(const ECParams P) {
         c = 2.0 * unit53(w.v[2]) - 1.0;
       }
     }
-    pid = ost.id[p];
+    p = CI(p, om, 10, P.status);
+    pid = CI(ost.id[p], ost_n(), 11, P.status);
     q0 = oRr[3 * (int64_t)pid];
     q1 = oRr[3 * (int64_t)pid + 1];
     q2 = oRr[3 * (int64_t)pid + 2];
@@ -469,8 +488,9 @@ __global__ void __launch_bounds__(128, 3) ec_lock_kernel(const ECParams P) {
         const int it = gl + r * G;
         if (!act || it == 0 || it >= 6) continue;
         if (it <= 2) {
-          const int t = it == 1 ? nb_prev(nbw) : nb_next(nbw);
+          int t = it == 1 ? nb_prev(nbw) : nb_next(nbw);
           if (t < 0) continue;
+          t = CI(t, S, 20, P.status);
           const float d0 = a0 - st.fx[t], d1 = a1 - st.fy[t], d2 = a2 - st.fz[t];
           const float dd = __fmaf_rn(d2, d2, __fmaf_rn(d1, d1, d0 * d0));
           const float dv = __fmaf_rn(d2, w2, __fmaf_rn(d1, w1, d0 * w0));
@@ -541,7 +561,7 @@ __global__ void __launch_bounds__(128, 3) ec_lock_kernel(const ECParams P) {
         if (!act || !(d & 64u)) continue;
         const int dx = d & 3u, dy = (d >> 2) & 3u, dz = (d >> 4) & 3u;
         if ((unsigned)(dx - r0) > n0 || (unsigned)(dy - r1) > n1 || (unsigned)(dz - r2) > n2) continue;
-        const int c = cb + dz * g01 + dy * LG.g0 + dx;
+        const int c = CI(cb + dz * g01 + dy * LG.g0 + dx, NC, 22, P.status);
         const int n = cell_n(st.cell + 8 * c);
         cw[j] = (c << 3) | n;
         cnt_l += n;
@@ -567,7 +587,7 @@ __global__ void __launch_bounds__(128, 3) ec_lock_kernel(const ECParams P) {
                                         (unsigned short)(c.w & 0xFFFF), (unsigned short)(c.w >> 16)};
 #pragma unroll
           for (int i = 0; i < 6; ++i)
-            if (i < n) fl[at + i] = sl[i];
+            if (i < n) fl[CI(at + i, fl_cap, 23, P.status)] = sl[i];
           at += n;
         }
         for (int i = gl; i < n_ovf; i += G) fl[ncell + i] = st.ovf[i];
@@ -578,9 +598,9 @@ __global__ void __launch_bounds__(128, 3) ec_lock_kernel(const ECParams P) {
       float kl0 = INF, kl1 = INF;
       bool kovf = false;
       for (int j = gl; j < nscr; j += 2 * G) {
-        const int ka = fl[j];
+        const int ka = CI(fl[j], S, 21, P.status);
         const bool two = j + G < nscr;
-        const int kb = two ? fl[j + G] : ka;
+        const int kb = two ? CI(fl[j + G], S, 21, P.status) : ka;
         const float ax = st.fx[ka], ay = st.fy[ka], az = st.fz[ka];
         const float bx = st.fx[kb], by = st.fy[kb], bz = st.fz[kb];
         if (ka != a_p) screen_hs(Z, a0 - ax, a1 - ay, a2 - az, w0, w1, w2, ka, ubl, ks0, kl0, ks1, kl1, kovf);
@@ -609,7 +629,7 @@ __global__ void __launch_bounds__(128, 3) ec_lock_kernel(const ECParams P) {
         // more than two possible winners in this lane: screen its slots again
         // against the group's U and keep every one that can reach it
         for (int j = gl; j < nscr; j += G) {
-          const int k = fl[j];
+          const int k = CI(fl[j], S, 21, P.status);
           if (k == a_p || k == ks0 || k == ks1) continue;
           bool possible;
           const float lb = screen_lb(Z, a0 - st.fx[k], a1 - st.fy[k], a2 - st.fz[k], w0, w1, w2,
@@ -633,7 +653,7 @@ __global__ void __launch_bounds__(128, 3) ec_lock_kernel(const ECParams P) {
       const bool fits = act && !gover && base + total <= RQ_CAP;
       if (act && total > 0 && !gover) {
         if (fits) {
-          const int at = base + incl - cntl;
+          const int at = CI(base + incl - cntl, RQ_CAP - (cntl > 0 ? cntl - 1 : 0), 24, P.status);
           if (cntl > 0) rq[at] = make_int2(gib, pq0);
           if (cntl > 1) rq[at + 1] = make_int2(gib, pq1);
           if (cntl > 2) rq[at + 2] = make_int2(gib, pq2);
@@ -660,11 +680,11 @@ __global__ void __launch_bounds__(128, 3) ec_lock_kernel(const ECParams P) {
         out.key = ~0ull;
         out.dv = 0.0;
         out.k[0] = out.k[1] = out.k[2] = 0.0;
-        if (r.x >= 0) {
+        if (r.x >= 0 && CHK(r.x, NT, 25, P.status)) {
           const TileRec &T = tr[r.x];
           const RepParams *R = T.rp;
           const int kind = r.y >> 28;
-          const int k = r.y & 0xFFFFF;
+          const int k = CI(r.y & 0xFFFFF, S, 26, P.status);
           const double Q0 = T.q[0], Q1 = T.q[1], Q2 = T.q[2];
           const double V0 = T.v[0], V1 = T.v[1], V2 = T.v[2];
           const double L0 = TSYS(R, L)[0], L1 = TSYS(R, L)[1], L2 = TSYS(R, L)[2];
@@ -683,7 +703,11 @@ __global__ void __launch_bounds__(128, 3) ec_lock_kernel(const ECParams P) {
             out.key = make_key(KIND_WALL, a, 0);
           } else {
             const bool te = kind == KIND_TETHER;
-            const Stage sk = carve(smem + (size_t)r.x * gbytes, S, 0, MNB, NC);
+            Stage sk = carve(smem + (size_t)r.x * gbytes, S, 0, MNB, NC);
+#ifdef ECMC_CHECKED
+            sk.status = P.status;
+            sk.nglob = BATCH ? R->n_beads : P.n;
+#endif
             double kx, ky, kz, dv;
             double *const Rk = BATCH ? P.r + 3 * R->bead_off : P.r;
             pos64(sk, Rk, k, false, kx, ky, kz);
@@ -714,7 +738,7 @@ __global__ void __launch_bounds__(128, 3) ec_lock_kernel(const ECParams P) {
         const double L0 = SYS(L)[0], L1 = SYS(L)[1], L2 = SYS(L)[2];
         const uint64_t hb0 = dbits(SYS(half)[0]), hb1 = dbits(SYS(half)[1]), hb2 = dbits(SYS(half)[2]);
         const bool W0 = T.wr & 1, W1 = T.wr & 2, W2 = T.wr & 4;
-        const int fp = T.p;
+        const int fp = CI(T.p, S, 27, P.status);
         const unsigned nbw = st.nb[fp];
         double bx = __longlong_as_double(0x7ff0000000000000ll);
         uint64_t bkey = ~0ull;
@@ -768,7 +792,7 @@ __global__ void __launch_bounds__(128, 3) ec_lock_kernel(const ECParams P) {
             lst = c + 2;
           }
           for (int i = 0; i < n; ++i) {
-            const int k = lst[i];
+            const int k = CI(lst[i], S, 28, P.status);
             if (k == fp) continue;
             double kx, ky, kz, dv;
             pos64(st, Rr, k, false, kx, ky, kz);
@@ -846,6 +870,7 @@ __global__ void __launch_bounds__(128, 3) ec_lock_kernel(const ECParams P) {
           const int i0 = T.rq_off, i1 = T.rq_off + T.rq_cnt;
           int wi = -1;
           for (int i = i0; i < i1; ++i) {
+            if (!CHK(i, RQ_CAP, 29, P.status)) break;
             const unsigned long long xb = rs[i].xb, kb = rs[i].key;
             if (xb < dbits(x) || (xb == dbits(x) && kb < bkey)) {
               x = __longlong_as_double((long long)xb);
@@ -862,7 +887,7 @@ __global__ void __launch_bounds__(128, 3) ec_lock_kernel(const ECParams P) {
         }
       }
       const int kind = key_kind(bkey);
-      const int slot = key_slot(bkey);
+      const int slot = CI(key_slot(bkey), S, 30, P.status);
       const int64_t partner = (kind == KIND_END || kind == KIND_PASS) ? -1 : key_id(bkey);
       int di0 = 0, di1 = 0, di2 = 0;
       if (owr0) di0 = step_i(q0, x, v0, oL0);
@@ -1058,7 +1083,7 @@ __global__ void __launch_bounds__(128, 3) ec_lock_kernel(const ECParams P) {
         // lift: the partner (motile, unmoved this event) becomes the pivot
         p = np;
         pub |= 2;
-        pid = ost.id[p];
+        pid = CI(ost.id[p], ost_n(), 31, P.status);
         q0 = wk0;
         q1 = wk1;
         q2 = wk2;
@@ -1221,6 +1246,7 @@ static cudaError_t launch_lock_t(const ECParams &P0, cudaStream_t s) {
 
 cudaError_t launch_ec_lock(const ECParams &P, int lanes, cudaStream_t s) {
   if (!P.domain) return cudaErrorInvalidValue;
+  if (P.k_spring != 0.0) return cudaErrorInvalidValue;  // bead springs: k_ec.cu
   if (lanes == 8) return launch_lock_t<8, false>(P, s);
   if (lanes == 4) return launch_lock_t<4, false>(P, s);
   if (lanes == 16) return launch_lock_t<16, false>(P, s);

@@ -22,14 +22,14 @@ __device__ __forceinline__ void atomic_min_pos(double *a, double v) {
   atomicMin((unsigned long long *)a, (unsigned long long)__double_as_longlong(v));
 }
 
-// out_d: [0] sum R_e^2, [1] max bond, [2] min bond, [3] sum g1
+// out_d: [0] sum R_e^2, [1] max bond, [2] min bond, [3] sum g1, [4] sum of bond lengths
 // out_u: [0] overlaps, [1] tether violations, [4] [5] bonds in the shells
 // (t1, t0] and (t2, t1] below b_max
 __global__ void k_chains(const ObsParams O) {
   const int64_t ch = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const int64_t nch = O.n / O.N;
   if (ch >= nch) return;
-  double R0 = 0.0, R1 = 0.0, R2 = 0.0, bmax = 0.0, bmin = 1e300;
+  double R0 = 0.0, R1 = 0.0, R2 = 0.0, bmax = 0.0, bmin = 1e300, bsum = 0.0;
   unsigned long long viol = 0, tb0 = 0, tb1 = 0;
   const double lim = O.b2 * (1.0 + 1e-10);
   for (int j = 0; j + 1 < O.N; ++j) {
@@ -47,9 +47,11 @@ __global__ void k_chains(const ObsParams O) {
     const double bl = sqrt(dd);
     bmax = fmax(bmax, bl);
     bmin = fmin(bmin, bl);
+    bsum += bl;
   }
   atomicAdd(&O.out_d[0], R0 * R0 + R1 * R1 + R2 * R2);
   if (O.N > 1) {
+    atomicAdd(&O.out_d[4], bsum);
     atomic_max_pos(&O.out_d[1], bmax);
     atomic_min_pos(&O.out_d[2], bmin);
   }
@@ -249,7 +251,64 @@ __global__ void k_wrap(double *r, int32_t *img, int64_t n3, double L0, double L1
   img[i] += (int32_t)f;
 }
 
+// g1 table, one block: thread (k, j) adds the squared displacements of the
+// middle beads over the lag j P^k (chains in order, (d0 d0 + d1 d1) + d2 d2)
+// when sweep t is an origin multiple of P^k and the earlier snapshot exists;
+// then every level whose period divides t stores the current snapshot in
+// slot (t / P^k) mod P, which no lag of this sweep reads
+__global__ void k_g1_track(const G1Track G) {
+  const int64_t nch = G.n / G.N;
+  const int nlag = G.K * (G.P - 1);
+  for (int q = threadIdx.x; q < nlag; q += blockDim.x) {
+    const int k = q / (G.P - 1), j = q % (G.P - 1) + 1;
+    const int64_t pk = G.Pk[k];
+    if (G.t % pk != 0 || G.t / pk < j) continue;
+    const int64_t slot = (G.t / pk - j) % G.P;
+    const double *old = G.ring + (k * (int64_t)G.P + slot) * nch * 3;
+    double s = 0.0;
+    for (int64_t ch = 0; ch < nch; ++ch) {
+      const int64_t b = ch * G.N + G.N / 2;
+      const double u0 = G.r[3 * b] + (double)G.img[3 * b] * G.L[0];
+      const double u1 = G.r[3 * b + 1] + (double)G.img[3 * b + 1] * G.L[1];
+      const double u2 = G.r[3 * b + 2] + (double)G.img[3 * b + 2] * G.L[2];
+      const double d0 = u0 - old[3 * ch], d1 = u1 - old[3 * ch + 1], d2 = u2 - old[3 * ch + 2];
+      s = s + ((d0 * d0 + d1 * d1) + d2 * d2);
+    }
+    G.sum[q] = G.sum[q] + s;
+    G.cnt[q] += 1ull;
+  }
+  __syncthreads();
+  for (int64_t i = threadIdx.x; i < (int64_t)G.K * nch; i += blockDim.x) {
+    const int k = (int)(i / nch);
+    const int64_t ch = i % nch;
+    const int64_t pk = G.Pk[k];
+    if (G.t % pk != 0) continue;
+    const int64_t slot = (G.t / pk) % G.P;
+    double *dst = G.ring + ((k * (int64_t)G.P + slot) * nch + ch) * 3;
+    const int64_t b = ch * G.N + G.N / 2;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) dst[a] = G.r[3 * b + a] + (double)G.img[3 * b + a] * G.L[a];
+  }
+}
+
+__global__ void k_po_advance(const unsigned long long *count, int64_t *ctr) {
+  if (*count) {
+    ctr[0] += 1;
+    ctr[1] += 1;
+  }
+}
+
 }  // namespace
+
+cudaError_t launch_po_advance(const unsigned long long *count, int64_t *ctr, cudaStream_t s) {
+  k_po_advance<<<1, 1, 0, s>>>(count, ctr);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_g1_track(const G1Track &G, cudaStream_t s) {
+  k_g1_track<<<1, 256, 0, s>>>(G);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_wrap(double *r, int32_t *img, int64_t n, const double L[3],
                         unsigned long long *bad, cudaStream_t s) {

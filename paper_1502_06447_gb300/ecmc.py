@@ -13,14 +13,16 @@ import threading
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_HERE, "libecmc.so")
+# ECMC_CHECKED=1: the bounds-checked build (see build.py)
+LIB_PATH = os.path.join(_HERE, "libecmc_checked.so" if os.environ.get("ECMC_CHECKED") == "1"
+                        else "libecmc.so")
 
 MODE_SERIAL, MODE_DOMAIN = 0, 1
 DIR_CART3, DIR_ISO = 0, 1
 PREC_FP64, PREC_FP32F = 0, 1
 EV_NAMES = ("end", "pass", "wall", "hs_lift", "hs_reflect", "te_lift", "te_reflect", "swap")
 STATUS = {0: "OK", -1: "EINVAL", -2: "ENOMEM", -3: "ECUDA", -4: "EOVERLAP", -5: "ETETHER",
-          -6: "ESTUCK", -7: "ECKPT", -8: "ECAPACITY"}
+          -6: "ESTUCK", -7: "ECKPT", -8: "ECAPACITY", -9: "EBOUNDS"}
 
 # every symbol include/ecmc.h declares
 EXPORTS = (
@@ -31,7 +33,8 @@ EXPORTS = (
     "ecmc_cells_static", "ecmc_batch_create", "ecmc_batch_destroy", "ecmc_batch_configure",
     "ecmc_batch_run", "ecmc_batch_get_positions", "ecmc_batch_info", "ecmc_batch_stats",
     "ecmc_batch_records", "ecmc_autotune", "ecmc_batch_autotune", "ecmc_structure",
-    "ecmc_phantom_chains", "ecmc_create_phantom", "ecmc_pushoff",
+    "ecmc_phantom_chains", "ecmc_create_phantom", "ecmc_pushoff", "ecmc_g1_track",
+    "ecmc_g1_table",
 )
 
 
@@ -47,7 +50,8 @@ class Opts(C.Structure):
                 ("event_cap", C.c_int64), ("p_swap", C.c_double), ("ecs_per_tile", C.c_int32),
                 ("lanes", C.c_int32), ("record", C.c_int32), ("stage_cap", C.c_int32),
                 ("cell_side", C.c_double), ("tile_side", C.c_double), ("schedule", C.c_int32),
-                ("block_tiles", C.c_int32), ("request_cap", C.c_int32)]
+                ("block_tiles", C.c_int32), ("request_cap", C.c_int32), ("k_spring", C.c_double),
+                ("tight_factor", C.c_double)]
 
 
 class Obs(C.Structure):
@@ -61,7 +65,8 @@ class Obs(C.Structure):
                 ("device_seconds", C.c_double), ("ec_kernel_seconds", C.c_double),
                 ("confirmed", C.c_int64), ("contact_pairs", C.c_int64 * 2),
                 ("taut_bonds", C.c_int64 * 2), ("contact_delta", C.c_double),
-                ("pressure_contact", C.c_double), ("exhaustive", C.c_int64)]
+                ("pressure_contact", C.c_double), ("exhaustive", C.c_int64),
+                ("bond_mean", C.c_double)]
 
     def as_dict(self):
         d = {k: getattr(self, k) for k, _ in self._fields_
@@ -143,6 +148,9 @@ def load(path: str = LIB_PATH):
                                     C.c_uint64, C.c_double, C.c_double, P(vp)],
             "ecmc_pushoff": [vp, C.c_double, C.c_int32, C.c_double, C.c_uint64, C.c_int64,
                              P(C.c_int64)],
+            "ecmc_g1_track": [vp, C.c_int32, C.c_int32],
+            "ecmc_g1_table": [vp, P(C.c_int64), P(C.c_double), P(C.c_int64), C.c_int32,
+                              P(C.c_int32)],
         }
         for name, args in sig.items():
             f = getattr(lib, name)
@@ -170,7 +178,8 @@ def _p(a, ct):
 
 def opts(mode=MODE_SERIAL, dir_mode=DIR_CART3, precision=PREC_FP64, tiles=(3, 3, 3), joint=0.0,
          s_cap=0.0, event_cap=0, p_swap=0.0, ecs_per_tile=0, lanes=0, record=0, stage_cap=0,
-         cell_side=0.0, tile_side=0.0, schedule=0, block_tiles=0, request_cap=0) -> Opts:
+         cell_side=0.0, tile_side=0.0, schedule=0, block_tiles=0, request_cap=0,
+         k_spring=0.0, tight_factor=0.0) -> Opts:
     o = Opts()
     o.mode, o.dir_mode, o.precision = int(mode), int(dir_mode), int(precision)
     for a in range(3):
@@ -181,13 +190,16 @@ def opts(mode=MODE_SERIAL, dir_mode=DIR_CART3, precision=PREC_FP64, tiles=(3, 3,
     o.tile_side = float(tile_side)
     o.schedule, o.block_tiles = int(schedule), int(block_tiles)
     o.request_cap = int(request_cap)
+    o.k_spring = float(k_spring)
+    o.tight_factor = float(tight_factor)
     return o
 
 
 class Tuning(C.Structure):
     _fields_ = [("lanes", C.c_int32), ("tile_side", C.c_double), ("cell_side", C.c_double),
                 ("ecs_per_tile", C.c_int32), ("tiles", C.c_int32 * 3), ("ecs_per_s", C.c_double),
-                ("events_per_s", C.c_double), ("n_trials", C.c_int32)]
+                ("events_per_s", C.c_double), ("n_trials", C.c_int32), ("block_tiles", C.c_int32),
+                ("tight_factor", C.c_double)]
 
     def as_dict(self):
         d = {k: getattr(self, k) for k, _ in self._fields_ if k != "tiles"}
@@ -342,6 +354,21 @@ class Context:
 
     def g1_reset(self):
         _check(load().ecmc_g1_reset(self._h))
+
+    def g1_track(self, P=0, K=0):
+        """Start a g1 table over the lags j P^k sweeps (ecmc_g1_track);
+        P = 0 stops tracking."""
+        _check(load().ecmc_g1_track(self._h, int(P), int(K)))
+
+    def g1_table(self, cap=1024):
+        """(lags, g1, origin counts) of the current g1 table."""
+        lag = np.zeros(cap, dtype=np.int64)
+        g1 = np.zeros(cap)
+        cnt = np.zeros(cap, dtype=np.int64)
+        n = C.c_int32(0)
+        _check(load().ecmc_g1_table(self._h, _p(lag, C.c_int64), _p(g1, C.c_double),
+                                    _p(cnt, C.c_int64), int(cap), C.byref(n)))
+        return lag[: n.value], g1[: n.value], cnt[: n.value]
 
     def records(self, cap):
         dig = np.zeros(cap, dtype=np.uint64)

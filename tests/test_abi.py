@@ -98,3 +98,14 @@ def test_cells_static_rejects_bad_sizes_before_any_launch(lib_path, box, cell_si
     with pytest.raises(ecmc.EcmcError) as e:
         ecmc.cells_static(dummy, 1000, box, tiles, 1.2, cell_side, 0, 0, dummy, dummy, dummy)
     assert e.value.code == -1
+
+
+def test_out_of_memory_is_reported_as_enomem(lib_path, monkeypatch):
+    """Host-side fault injection: with ECMC_ALLOC_LIMIT set, a device
+    allocation above the limit fails as cudaMalloc does on a full device;
+    creating a context then returns ECMC_ENOMEM (no device is touched
+    before the refused allocation, so this runs on the CPU)."""
+    monkeypatch.setenv("ECMC_ALLOC_LIMIT", "1000")
+    with pytest.raises(ecmc.EcmcError) as e:
+        ecmc.Context.create_lattice((8, 8, 10), 1.05, 10, jitter=0.01, seed=1)
+    assert e.value.code == -2 and "ENOMEM" in str(e.value)

@@ -420,3 +420,26 @@ def test_unwrapped_displacement_is_ell_along_each_ec_direction():
     assert np.allclose(moved, expect, rtol=0, atol=1e-8 * n_ec)
     # a wrong image sign would be off by whole box lengths
     assert np.abs(moved - expect).max() < 1e-3
+
+
+def test_tile_subsets_split_a_sweep_exactly():
+    """The all-core timing of the oracle splits a sweep's tiles over
+    processes (tile t runs in part t % 3): the parts together do exactly the
+    serial sweep's ECs (same per-EC digests, same event count), because
+    tiles never interact within a sweep (Sec. II.A)."""
+    from paper_1502_06447_gb300.configs import small_domain
+    m = small_domain(N=8, dims=(16, 16, 16), D=(4, 4, 4), sweeps=1, ell=4.0)
+    r = oracle.lattice(m.dims, m.spacing, m.jitter, m.seed)
+    kw = dict(mode=MODE_DOMAIN, dir_mode=DIR_ISO, D=m.D, seed=m.seed)
+    full = oracle.System(r, m.L, m.N, **kw).run_domain(1, m.ell, digests=True)
+    dig = np.zeros_like(full["digest"])
+    events = 0
+    for rem in range(3):
+        part = oracle.System(r, m.L, m.N, tile_mod=3, tile_rem=rem, **kw).run_domain(
+            1, m.ell, digests=True)
+        assert part["rc"] == 0
+        mine = np.arange(len(dig)) % 3 == rem  # one EC per tile: ordinal = tile
+        assert (part["digest"][~mine] == 0).all()
+        dig[mine] = part["digest"][mine]
+        events += part["stats"]["events"]
+    assert (dig == full["digest"]).all() and events == full["stats"]["events"]

@@ -1,6 +1,7 @@
 """The autotuner's search (tune_search, host code) with synthetic objectives,
 compiled with g++ (no GPU): coordinate descent over lanes, tile side, cell
-side and ECs per tile finds the optimum of separable and coupled scores,
+side, ECs per tile, warps per block and the first-pass capacity factor
+finds the optimum of separable and coupled scores,
 times no point twice, skips inadmissible points and stops an abort."""
 import os
 import subprocess
@@ -20,7 +21,8 @@ using namespace ecmc;
 struct Log { std::vector<TunePoint> pts; };
 
 static bool same(const TunePoint &a, const TunePoint &b) {
-  return a.lanes == b.lanes && a.tile_side == b.tile_side && a.cell_side == b.cell_side && a.ecs == b.ecs;
+  return a.lanes == b.lanes && a.tile_side == b.tile_side && a.cell_side == b.cell_side && a.ecs == b.ecs &&
+         a.warps == b.warps && a.tight == b.tight;
 }
 
 template <class F>
@@ -40,16 +42,17 @@ static void run(const char *name, TunePoint start, F score, int bad_lanes = -1, 
   TuneScore bs{};
   int n = 0;
   const ecmc_status st = tune_search(start, trial, &best, &bs, &n);
-  std::printf("%s st=%d lanes=%d tile=%g cell=%g ecs=%d score=%g trials=%d calls=%d\n", name, (int)st,
-              best.lanes, best.tile_side, best.cell_side, best.ecs, bs.ecs_per_s, n, (int)log.pts.size());
+  std::printf("%s st=%d lanes=%d tile=%g cell=%g ecs=%d warps=%d tight=%g score=%g trials=%d calls=%d\n", name,
+              (int)st, best.lanes, best.tile_side, best.cell_side, best.ecs, best.warps, best.tight, bs.ecs_per_s, n,
+              (int)log.pts.size());
 }
 
 int main() {
-  const TunePoint start{32, 4.2, 1.05, 1};
-  // separable: optimum lanes 8, tile 5, cell 1.4, ecs 2
+  const TunePoint start{32, 4.2, 1.05, 1, 1, 1.08};
+  // separable: optimum lanes 8, tile 5, cell 1.4, ecs 2, warps 2, tight 1.16
   auto sep = [](const TunePoint &p) {
     return -std::fabs(p.lanes - 8.0) - std::fabs(p.tile_side - 5.0) - 3.0 * std::fabs(p.cell_side - 1.4) -
-           std::fabs(p.ecs - 2.0);
+           std::fabs(p.ecs - 2.0) - std::fabs(p.warps - 2.0) - 10.0 * std::fabs(p.tight - 1.16);
   };
   run("separable", start, sep);
   // coupled: the best lane count depends on ECs per tile, the last axis,
@@ -62,7 +65,8 @@ int main() {
   // the first-round result (a second round only starts after a change)
   run("skip8", start, sep, 8);
   run("abort", start, sep, -1, 5);
-  run("offgrid", TunePoint{8, 4.4, 1.05, 1}, [](const TunePoint &p) { return p.tile_side == 4.4 ? 100.0 : 0.0; });
+  run("offgrid", TunePoint{8, 4.4, 1.05, 1, 1, 1.08},
+      [](const TunePoint &p) { return p.tile_side == 4.4 ? 100.0 : 0.0; });
   return 0;
 }
 """
@@ -94,8 +98,9 @@ def test_tune_search_host(tmp_path):
     assert "DUPLICATE" not in out, out
     res = parse(out)
     s = res["separable"]
-    assert (s["st"], s["lanes"], s["tile"], s["cell"], s["ecs"]) == ("0", "8", "5", "1.4", "2")
-    assert int(s["trials"]) <= 1 + 2 * (4 + 5 + 2 + 3)
+    assert (s["st"], s["lanes"], s["tile"], s["cell"], s["ecs"], s["warps"], s["tight"]) == (
+        "0", "8", "5", "1.4", "2", "2", "1.16")
+    assert int(s["trials"]) <= 1 + 2 * (4 + 5 + 2 + 3 + 3 + 3)
     c = res["coupled"]
     assert (c["lanes"], c["ecs"], c["score"]) == ("8", "4", "3")
     k = res["skip8"]
