@@ -130,6 +130,53 @@ def measured_traffic(kernel, st):
     return float(b.group(1))
 
 
+def measured_counters(kernel, st):
+    """Per-event instruction counts of `kernel` from the committed ncu
+    summary (warp instructions, FP64-pipe warp instructions, FP64-pipe
+    cycles per FP64 instruction), or None unless it was taken on this
+    kernel revision in exactly this launch setting."""
+    import re
+    p = os.path.join(ROOT, "profiles", "ec_lock_counters_1e6_melt.md")
+    try:
+        txt = open(p).read()
+    except OSError:
+        return None
+    k = re.search(r"^setting = (.+)$", txt, re.M)
+    if not (k and k.group(1).strip() == setting_key(kernel, st) and C5.name == "c5_swap_1m"):
+        return None
+    out = {}
+    for name in ("warp_instr_per_event", "fp64_warp_instr_per_event", "fp64_cycles_per_instr"):
+        m = re.search(rf"^{name} = ([0-9.eE+]+)$", txt, re.M)
+        if not m:
+            return None
+        out[name] = float(m.group(1))
+    return out
+
+
+def ceilings(cnt, ec_events_per_s, sm_mhz):
+    """Two ceilings of the EC kernel besides HBM: instruction issue (four
+    warp instructions per cycle per SM, one per sub-partition) and the SM's
+    FP64 pipe (busy fp64_cycles_per_instr SM cycles per FP64 warp
+    instruction, the measured ratio of FP64-pipe active cycles to FP64
+    instructions: 16 on GB300, i.e. 64 FP64 flops per 16 cycles per SM,
+    1.26 TFLOP/s at 2.07 GHz), each divided by the kernel's measured
+    per-event counts."""
+    import torch
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    hz = sm_mhz * 1e6
+    issue = 4.0 * sms * hz / cnt["warp_instr_per_event"]
+    fp64 = sms * hz / (cnt["fp64_warp_instr_per_event"] * cnt["fp64_cycles_per_instr"])
+    return {"issue": {"events_per_s": issue, "frac": ec_events_per_s / issue,
+                      "warp_instr_per_event": cnt["warp_instr_per_event"]},
+            "fp64_pipe": {"events_per_s": fp64, "frac": ec_events_per_s / fp64,
+                          "fp64_warp_instr_per_event": cnt["fp64_warp_instr_per_event"],
+                          "fp64_cycles_per_instr": cnt["fp64_cycles_per_instr"]},
+            "sms": sms, "sm_mhz": sm_mhz,
+            "note": "events/s of the EC launches against each ceiling; the kernel is latency "
+                    "bound (dependent FP64 chains, barriers, shared-memory round trips) and "
+                    "reaches neither"}
+
+
 def load_peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     try:
@@ -338,6 +385,9 @@ def run_gpu(args, rank, world):
     kname = (f"ec_lock_kernel<{setting['lanes']}, 0>" if args.schedule == 0 and setting["lanes"] in (4, 8, 16)
              else f"ec_kernel<{setting['lanes']}, 1, 0>")
     traffic = measured_traffic(kname, setting)
+    counters = measured_counters(kname, setting)
+    csum = clk.summary()
+    clk_mhz = csum["sm_mhz"] or csum["sm_max_mhz"] or 2070.0
     n_beads = C5.n
     value = tot_events / max_dev
     line = {
@@ -376,6 +426,7 @@ def run_gpu(args, rank, world):
         "wall_s": max_wall,
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
                      "frac": achieved / hbm, "traffic": traffic,
+                     "ceilings": (ceilings(counters, events / ec_s, clk_mhz) if counters else None),
                      "kernel": kname,
                      "bytes_per_event": bpe,
                      "kernel_share_of_step": ec_s / dev_s, "peak_source": peak_src},
@@ -389,7 +440,7 @@ def run_gpu(args, rank, world):
         "physics": physics,
         "structure": structure,
         "init": init,
-        "clocks": clk.summary(),
+        "clocks": csum,
         "tuning": {"fp32f": tune, "fp64": tune64, "fp64_timed_setting": setting64},
     }
     if batched is not None:
@@ -784,7 +835,7 @@ def cpu_allcore_run(sweeps=1):
 # chains of N = 121 (c = 1.9, bonds of sigma) at packing fraction 0.495 in a
 # 40^3 box, pushed off with ECs of length 2 sigma
 FIG3 = dict(L=40.0, n_chains=500, N=121, c=1.9, seed=81, po_seed=0xEC3F03, f0=0.5, stages=10,
-            ell=2.0, tiles=(9, 9, 9), max_sweeps=2000)
+            ell=2.0, tiles=(9, 9, 9), max_sweeps=10000)
 
 
 def fig3_run(stream):

@@ -425,8 +425,8 @@ ecmc_status ecmc_batch_records(ecmc_batch *b, uint64_t *digest, double *lift,
 /* ---- autotuner -------------------------------------------------------------
  * Picks the launch setting of the domain sweep for this machine and system
  * (the paper fixes none: Sec. II.A leaves the tile size open): lanes per EC
- * (4, 8, 16, 32), tile side (3.4 ... 7 sigma), global cell side (1.05 or 1.4
- * sigma), ECs per tile (1, 2 or 4) and the block-lockstep kernel's staging
+ * (4, 8, 16, 32), tile side (3.4, 3.8, 4.2, 4.6, 5, 6, 7 sigma), global cell side (1.05 or 1.4
+ * sigma), ECs per tile (1, 2, 4 or 8) and the block-lockstep kernel's staging
  * (1, 2 or 4 warps per block; first-pass capacity factor 1.0, 1.08 or 1.16;
  * other kernels take only the defaults), by a coordinate descent (up to two
  * rounds) over short timed trials.  Each trial restores the state saved on entry, runs one untimed

@@ -148,6 +148,13 @@ __device__ __forceinline__ float wrapf(float d, float L) {
 constexpr int CELL_CAP = 6;
 constexpr int OVF_CAP = 64;
 constexpr int HDR_BYTES = 32;
+// the overflow list holds max(64, S / 4) slots, rounded up to a multiple of
+// 8 (16 bytes, so that a group's share of shared memory stays a multiple of
+// 16 bytes for any S that is a multiple of 8): clustered inputs (phantom
+// chains before the push-off) fill many cells past CELL_CAP
+__host__ __device__ __forceinline__ int ovf_cap_for(int S) {
+  return S / 4 > OVF_CAP ? (S / 4 + 7) / 8 * 8 : OVF_CAP;
+}
 
 struct Stage {
   double *px, *py, *pz;  // [M64]
@@ -155,8 +162,9 @@ struct Stage {
   float *fx, *fy, *fz;   // [S]
   int *id;               // [S]
   unsigned short *cell;  // [NC][8]: 32-bit count, then up to 6 slots
-  unsigned short *ovf;   // [OVF_CAP]
+  unsigned short *ovf;   // [ovf_cap]
   int *hdr;              // [2] staged count, [3] overflow, [4] overflow-list length
+  int ovf_cap;           // ovf_cap_for(S)
 #ifdef ECMC_CHECKED
   int cap;               // S (slots)
   long long nglob;       // beads of the system (ids), set by the kernel
@@ -165,11 +173,12 @@ struct Stage {
 };
 
 __host__ __device__ __forceinline__ size_t group_bytes(int S, int M64, int MNB, int NC) {
-  return (size_t)M64 * 24 + (size_t)MNB * 4 + (size_t)S * 16 + (size_t)NC * 16 + OVF_CAP * 2 +
+  return (size_t)M64 * 24 + (size_t)MNB * 4 + (size_t)S * 16 + (size_t)NC * 16 + (size_t)ovf_cap_for(S) * 2 +
          HDR_BYTES;
 }  // (16 B per cell: a 32-bit count and 6 slots of 16 bits)
 
-// S, M64 and MNB are multiples of 32, so every array starts 16-byte aligned
+// S, M64 and MNB are multiples of 8 (capacities are rounded to 8 or 32), so
+// every array starts 16-byte aligned and group_bytes is a multiple of 16
 __device__ __forceinline__ Stage carve(unsigned char *base, int S, int M64, int MNB, int NC) {
   Stage s;
   s.px = (double *)base;
@@ -182,7 +191,8 @@ __device__ __forceinline__ Stage carve(unsigned char *base, int S, int M64, int 
   s.id = (int *)(s.fz + S);
   s.cell = (unsigned short *)(s.id + S);
   s.ovf = s.cell + 8 * NC;
-  s.hdr = (int *)(s.ovf + OVF_CAP);
+  s.ovf_cap = ovf_cap_for(S);
+  s.hdr = (int *)(s.ovf + s.ovf_cap);
 #ifdef ECMC_CHECKED
   s.cap = S;
   s.nglob = 0x7fffffffffffffffll;
@@ -267,7 +277,7 @@ __device__ __forceinline__ bool lcell_insert(const Stage &st, int ci, int slot) 
     return true;
   }
   const int k = st.hdr[4];
-  if (k >= OVF_CAP) return false;
+  if (k >= st.ovf_cap) return false;
   st.ovf[k] = (unsigned short)slot;
   st.hdr[4] = k + 1;
   return true;
@@ -687,7 +697,7 @@ __device__ __forceinline__ void stage_tile(const ECParams &P, const RepParams *r
           c[2 + old] = (unsigned short)s;
         } else {
           const int k = atomicAdd(&st.hdr[4], 1);
-          if (k < OVF_CAP) st.ovf[k] = (unsigned short)s;
+          if (k < st.ovf_cap) st.ovf[k] = (unsigned short)s;
           else st.hdr[3] = 1;
         }
       }

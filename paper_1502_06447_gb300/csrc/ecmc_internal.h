@@ -361,9 +361,9 @@ template <class Trial>
 ecmc_status tune_search(TunePoint start, Trial trial, TunePoint *best, TuneScore *best_score,
                         int *n_trials) {
   static const int lanes_c[] = {4, 8, 16, 32};
-  static const double tile_c[] = {3.4, 4.2, 5.0, 6.0, 7.0};
+  static const double tile_c[] = {3.4, 3.8, 4.2, 4.6, 5.0, 6.0, 7.0};
   static const double cell_c[] = {1.05, 1.4};
-  static const int ecs_c[] = {1, 2, 4};
+  static const int ecs_c[] = {1, 2, 4, 8};
   static const int warps_c[] = {1, 2, 4};
   static const double tight_c[] = {1.0, 1.08, 1.16};
   TunePoint cur = start;
@@ -401,7 +401,7 @@ ecmc_status tune_search(TunePoint start, Trial trial, TunePoint *best, TuneScore
     const TunePoint before = cur;
     for (int axis = 0; axis < 6; ++axis) {
       const TunePoint base = cur;
-      const int cnt = axis == 0 ? 4 : axis == 1 ? 5 : axis == 2 ? 2 : 3;
+      const int cnt = axis == 0 ? 4 : axis == 1 ? 7 : axis == 2 ? 2 : axis == 3 ? 4 : 3;
       for (int i = 0; i < cnt; ++i) {
         TunePoint pt = base;
         if (axis == 0) pt.lanes = lanes_c[i];

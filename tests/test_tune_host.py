@@ -100,7 +100,7 @@ def test_tune_search_host(tmp_path):
     s = res["separable"]
     assert (s["st"], s["lanes"], s["tile"], s["cell"], s["ecs"], s["warps"], s["tight"]) == (
         "0", "8", "5", "1.4", "2", "2", "1.16")
-    assert int(s["trials"]) <= 1 + 2 * (4 + 5 + 2 + 3 + 3 + 3)
+    assert int(s["trials"]) <= 1 + 2 * (4 + 7 + 2 + 4 + 3 + 3)
     c = res["coupled"]
     assert (c["lanes"], c["ecs"], c["score"]) == ("8", "4", "3")
     k = res["skip8"]
