@@ -47,7 +47,7 @@ UNIT = "events/s"
 C0 = 1.2  # stencil cell side of the bytes-per-event definition (= b_max)
 # revision of the block-lockstep kernel; DRAM counters in profiles/ are used
 # only when they were taken on the same revision
-KERNEL_REV = 5
+KERNEL_REV = 6
 
 
 def launch_settings(args):
@@ -73,6 +73,12 @@ def launch_settings(args):
 
 
 LAUNCH = None
+# push-off sweeps run the plain FP64 kernel with one tile per warp: at these
+# sizes (a few hundred tiles, often only a few with overlapping beads) a
+# sweep is as long as its slowest tile, and 32 lanes step a tile fastest
+# (5,340 beads: 0.96 s at 32 lanes, 1.30 s at 16, 1.90 s at 8; the same
+# sweeps and positions)
+PO_LANES = 32
 
 
 def bytes_per_event(phi, confirmed_per_event, fp32f=True):
@@ -637,7 +643,7 @@ def springs_run(stream, steps):
     ctx = ecmc.Context.create_phantom(L, c["n_chains"], c["N"], bond=1.0, c=c["c"], seed=c["seed"])
     ctx.set_stream(stream.cuda_stream)
     ctx.configure(mode=ecmc.MODE_DOMAIN, dir_mode=ecmc.DIR_ISO, precision=ecmc.PREC_FP64,
-                  tiles=c["tiles"], lanes=8)
+                  tiles=c["tiles"], lanes=PO_LANES)
     t0 = time.perf_counter()
     res["pushoff_sweeps"] = ctx.pushoff(f0=0.5, stages=5, ell=2.0, seed=c["po_seed"],
                                         max_sweeps=c["max_sweeps"])
@@ -691,7 +697,7 @@ def reptation_run(stream):
                                       b_max=c["b_max"])
     ctx.set_stream(stream.cuda_stream)
     ctx.configure(mode=ecmc.MODE_DOMAIN, dir_mode=ecmc.DIR_ISO, precision=ecmc.PREC_FP64,
-                  tiles=c["tiles"], lanes=8)
+                  tiles=c["tiles"], lanes=PO_LANES)
     t0 = time.perf_counter()
     po_sweeps = ctx.pushoff(f0=0.5, stages=5, ell=2.0, seed=c["po_seed"], max_sweeps=20000)
     po_s = time.perf_counter() - t0
@@ -786,7 +792,7 @@ def init_run():
     ctx = ecmc.Context.create_phantom(L, c["n_chains"], c["N"], bond=1.0, c=c["c"], seed=c["seed"])
     t1 = time.perf_counter()
     ctx.configure(mode=ecmc.MODE_DOMAIN, dir_mode=ecmc.DIR_ISO, precision=ecmc.PREC_FP64,
-                  tiles=c["tiles"], lanes=8)
+                  tiles=c["tiles"], lanes=PO_LANES)
     t2 = time.perf_counter()
     sweeps = ctx.pushoff(f0=c["f0"], stages=c["stages"], ell=c["ell"], seed=c["po_seed"],
                          max_sweeps=c["max_sweeps"])
@@ -799,7 +805,7 @@ def init_run():
             "overlaps": o["overlaps"], "tether_violations": o["tether_violations"],
             "r2n_over_n": {str(k): float(rn[k] / k) for k in (1, 5, 19)},
             "setting": "267 chains x 20 beads, c = 1.9, 20^3 box, 4^3 tiles, f0 = 0.5, 5 stages, "
-                       "ECs of length 2, plain FP64 kernel"}
+                       "ECs of length 2, plain FP64 kernel, 32 lanes per tile"}
 
 
 def _oracle_part(k, parts, sweeps):
@@ -835,7 +841,7 @@ def cpu_allcore_run(sweeps=1):
 # chains of N = 121 (c = 1.9, bonds of sigma) at packing fraction 0.495 in a
 # 40^3 box, pushed off with ECs of length 2 sigma
 FIG3 = dict(L=40.0, n_chains=500, N=121, c=1.9, seed=81, po_seed=0xEC3F03, f0=0.5, stages=10,
-            ell=2.0, tiles=(9, 9, 9), max_sweeps=10000)
+            ell=2.0, tiles=(9, 9, 9), max_sweeps=4000)
 
 
 def fig3_run(stream):
@@ -851,7 +857,7 @@ def fig3_run(stream):
     n = c["n_chains"] * c["N"]
     _, rn0, _ = ctx.structure(r2n=True)
     ctx.configure(mode=ecmc.MODE_DOMAIN, dir_mode=ecmc.DIR_ISO, precision=ecmc.PREC_FP64,
-                  tiles=c["tiles"], lanes=8)
+                  tiles=c["tiles"], lanes=PO_LANES)
     t0 = time.perf_counter()
     res = {"workload": "Fig. 3 melt: 500 phantom chains x N = 121, eta = 0.495, 40^3 box, "
                        "push-off in 10 stages from half the diameter, ECs of length 2",

@@ -1,8 +1,10 @@
 """Parity at the benchmark's full sizes, in the launch configuration the
 benchmark times.
 
-- The 10^6-bead melt (1000 chains of 1000 on 100^3, ell = 20, 25^3 tiles,
-  8 lanes, 2 ECs per tile, swaps proposed at contacts): one sweep on the GPU
+- The 10^6-bead melt (1000 chains of 1000 on 100^3, ell = 20, swaps
+  proposed at contacts) in the benchmark's pinned launch setting
+  (configs.C5_LAUNCH: 25^3 tiles, 8 lanes, 8 ECs per tile, cell side 1.05,
+  8 tiles per block, first-pass capacity factor 1.0): one sweep on the GPU
   and in the oracle, every per-EC digest, lift sum and event count and every
   position and image counter identical.
 - The 512k melt at phi = 0.50 (2000 chains of 256 on 80^3): the FP32-screened
@@ -13,7 +15,7 @@ import numpy as np
 import pytest
 
 from paper_1502_06447_gb300 import ecmc
-from paper_1502_06447_gb300.configs import C3, C5
+from paper_1502_06447_gb300.configs import C3, C5, C5_LAUNCH
 
 from helpers import gpu_context, oracle_system
 
@@ -26,13 +28,13 @@ def _build():
     build.build()
 
 
-def _compare_sweep(m, tiles, lanes, ecs, p_swap):
+def _compare_sweep(m, tiles, lanes, ecs, p_swap, **launch):
     nt = tiles[0] * tiles[1] * tiles[2]
     o = oracle_system(m, D=tiles, ecs_per_tile=ecs, p_swap=p_swap)
     res = o.run_domain(1, m.ell, digests=True)
     assert res["rc"] == 0
     ctx = gpu_context(m, precision=ecmc.PREC_FP32F, lanes=lanes, tiles=tiles, ecs_per_tile=ecs,
-                      p_swap=p_swap)
+                      p_swap=p_swap, **launch)
     ctx.run(m.ell, seed=m.seed, n_sweeps=1)
     dig, lift, ev = ctx.records(nt * ecs)
     assert (dig == res["digest"]).all(), np.nonzero(dig != res["digest"])[0][:5]
@@ -43,7 +45,10 @@ def _compare_sweep(m, tiles, lanes, ecs, p_swap):
 
 
 def test_million_bead_melt_one_sweep_matches_oracle():
-    ctx, res = _compare_sweep(C5, (25, 25, 25), 8, 2, 0.05)
+    L = C5_LAUNCH
+    ctx, res = _compare_sweep(C5, L["tiles"], L["lanes"], L["ecs_per_tile"], 0.05,
+                              cell_side=L["cell_side"], block_tiles=L["block_tiles"],
+                              tight_factor=L["tight_factor"])
     assert res["stats"]["swap_tried"] > 0
     obs = ctx.observables()
     assert obs["swap_tried"] == res["stats"]["swap_tried"] and obs["overlaps"] == 0
