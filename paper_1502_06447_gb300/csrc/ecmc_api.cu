@@ -119,6 +119,9 @@ struct ecmc_ctx {
   int64_t log_cap = 0;
   // host counters
   int64_t sweeps_done = 0, ecs_done = 0;
+  // counters, sweeps and ECs when the last ecmc_run started (d_cnt + CNT_N
+  // holds that copy of the counters): ecmc_swap calibrates on that run
+  int64_t mark_sweeps = 0, mark_ecs = 0;
   double device_seconds = 0.0;
   double ec_seconds = 0.0;
   std::vector<cudaEvent_t> kev;  // start/stop pairs around EC launches
@@ -291,8 +294,8 @@ ecmc_status alloc_state(ecmc_ctx *c) {
   CU(dalloc(&c->d_rf, 3 * c->n));
   CU(dalloc(&c->d_cid, c->n));
   CU(dalloc(&c->d_ctag, c->n));
-  CU(dalloc(&c->d_cnt, CNT_N));
-  CU(cudaMemset(c->d_cnt, 0, sizeof(unsigned long long) * CNT_N));
+  CU(dalloc(&c->d_cnt, 2 * CNT_N));
+  CU(cudaMemset(c->d_cnt, 0, sizeof(unsigned long long) * 2 * CNT_N));
   CU(dalloc(&c->d_sums, SUM_N));
   CU(cudaMemset(c->d_sums, 0, sizeof(double) * SUM_N));
   CU(dalloc(&c->d_status, 1));
@@ -766,6 +769,15 @@ static cudaError_t g1_step(ecmc_ctx *c) {
   return launch_g1_track(g1_params(c), c->stream);
 }
 
+// copy the counters to the mark (d_cnt + CNT_N) in stream order and note the
+// sweeps and ECs done
+static cudaError_t mark_counters(ecmc_ctx *c) {
+  c->mark_sweeps = c->sweeps_done;
+  c->mark_ecs = c->ecs_done;
+  return cudaMemcpyAsync(c->d_cnt + CNT_N, c->d_cnt, sizeof(unsigned long long) * CNT_N,
+                         cudaMemcpyDeviceToDevice, c->stream);
+}
+
 ecmc_status ecmc_run(ecmc_ctx *c, double ell, int64_t chains_per_sweep, uint64_t seed,
                      int64_t n_sweeps) {
   if (!c) return fail(ECMC_EINVAL, "ctx is NULL");
@@ -784,6 +796,7 @@ ecmc_status ecmc_run(ecmc_ctx *c, double ell, int64_t chains_per_sweep, uint64_t
     units = chains_per_sweep;
   }
   CU(cudaMemsetAsync(c->d_status, 0, sizeof(int), c->stream));
+  CU(mark_counters(c));
   ECParams P = ec_params(c, seed, ell);
   if (c->opts.record) {
     ecmc_status s = reserve_records(c, units);
@@ -849,14 +862,17 @@ ecmc_status ecmc_swap(ecmc_ctx *c, double target) {
     c->opts.p_swap = 0.0;
     return ECMC_OK;
   }
-  unsigned long long h[CNT_N];
+  // the motile contacts and sweeps of the last ecmc_run call
+  unsigned long long h[2 * CNT_N];
   CU(cudaMemcpyAsync(h, c->d_cnt, sizeof(h), cudaMemcpyDeviceToHost, c->stream));
   CU(cudaStreamSynchronize(c->stream));
-  const double contacts = (double)(h[ECMC_EV_HS_LIFT] + h[ECMC_EV_SWAP]);
-  const double sweeps = c->opts.mode == ECMC_MODE_DOMAIN ? (double)c->sweeps_done
-                                                          : (double)c->ecs_done / (double)c->n;
+  const unsigned long long *m = h + CNT_N;
+  const double contacts = (double)((h[ECMC_EV_HS_LIFT] - m[ECMC_EV_HS_LIFT]) + (h[ECMC_EV_SWAP] - m[ECMC_EV_SWAP]));
+  const double sweeps = c->opts.mode == ECMC_MODE_DOMAIN
+                            ? (double)(c->sweeps_done - c->mark_sweeps)
+                            : (double)(c->ecs_done - c->mark_ecs) / (double)c->n;
   if (!(contacts > 0.0) || !(sweeps > 0.0))
-    return fail(ECMC_EINVAL, "run EC sweeps before calibrating swaps");
+    return fail(ECMC_EINVAL, "run EC sweeps (ecmc_run) before calibrating swaps");
   double p = target * (double)c->n * sweeps / contacts;
   c->opts.p_swap = p > 1.0 ? 1.0 : p;
   return ECMC_OK;
@@ -1120,6 +1136,7 @@ ecmc_status ecmc_pushoff(ecmc_ctx *c, double f0, int32_t stages, double ell, uin
     sweeps += ran;
   }
   if (sweeps_out) *sweeps_out = sweeps;
+  CU(mark_counters(c));  // push-off sweeps are no run to calibrate swaps on
   ecmc_status st = check_state(c);
   if (st == ECMC_OK) c->pushoff_pending = false;
   return st;
@@ -1386,6 +1403,7 @@ ecmc_status ecmc_restore(ecmc_ctx *c, const char *path) {
   c->sweeps_done = hd.sweeps_done;
   c->ecs_done = hd.ecs_done;
   c->device_seconds = hd.device_seconds;
+  CU(mark_counters(c));
   if (hd.configured) return ecmc_configure(c, &hd.opts);
   return ECMC_OK;
 }
@@ -1431,6 +1449,8 @@ ecmc_status ecmc_autotune(ecmc_ctx *c, double ell, uint64_t seed, int32_t trial_
     c->ecs_done = ec0;
     c->device_seconds = ds0;
     c->ec_seconds = es0;
+    CU(mark_counters(c));  // the trials are no run to calibrate swaps on
+    CU(cudaStreamSynchronize(c->stream));
     return ECMC_OK;
   };
   // the staging axes apply to the block-lockstep kernel only; elsewhere a

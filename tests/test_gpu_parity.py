@@ -264,6 +264,24 @@ def test_swap_parity_serial():
     assert_same_state(ctx, o)
 
 
+def test_swap_calibration_reaches_the_target_rate():
+    """ecmc_swap sets p_swap from the contacts of the last ecmc_run, so the
+    attempts per bead and sweep that follow match the target on a melted
+    state, whatever the earlier (lattice-start) sweeps counted."""
+    m = small_domain(seed=0xEC00A6, ell=6.0)
+    ctx = gpu_context(m, lanes=8, precision=ecmc.PREC_FP32F, ecs_per_tile=4)
+    with pytest.raises(ecmc.EcmcError):
+        ctx.swap(0.1)  # no run yet
+    ctx.run(m.ell, seed=m.seed, n_sweeps=20)  # melts the lattice start
+    ctx.run(m.ell, seed=m.seed, n_sweeps=4)  # the calibration run
+    ctx.swap(0.1)
+    t0 = ctx.observables()["swap_tried"]
+    ctx.run(m.ell, seed=m.seed, n_sweeps=12)
+    n = ctx.observables()["n_beads"]
+    rate = (ctx.observables()["swap_tried"] - t0) / (n * 12)
+    assert rate == pytest.approx(0.1, rel=0.15)
+
+
 # ------------------------------------------------------------------ observables
 def test_observables_match_oracle():
     m = small_domain()
