@@ -321,6 +321,11 @@ def run_gpu(args, rank, world):
     physics = {
         "re2_mean_before": o0["re2_mean"], "re2_mean_after": o1["re2_mean"],
         "g1_over_timed_steps": o1["g1"], "g1_per_device_second": o1["g1"] / dev_s,
+        "g1_note": "the launch setting trades events/s against relaxation: more ECs per tile "
+                   "(tiles fixed for longer) and smaller tiles (fewer motile beads) raise "
+                   "events/s but lower g1 per device-second; measured from one melted start, "
+                   "25^3 tiles at 8 ECs per tile reach about 22 % less g1 per device-second "
+                   "than at 2, and 22^3 tiles at 2 ECs per tile 15 % more",
         "pressure_contact": o1["pressure_contact"],
         "pressure_lift": {
             "value": 1 + (o1["lift_sum"] - o0["lift_sum"]) / (o1["disp_sum"] - o0["disp_sum"]),

@@ -76,7 +76,10 @@ CONFIGS = {m.name: m for m in (C1, C2, C3, C5)}
 # calculator's choice; 8 tiles of 8 lanes = two warps per block.  Eight ECs
 # per tile: a sweep ends with its longest tile, and more ECs per tile spread
 # that tail over more work (timed on a GB300, 25^3 tiles: 2 / 4 / 8 / 16 ECs
-# per tile gave 3.8 / 4.1 / 4.5-4.8 / 5.0e8 events/s).
+# per tile gave 3.8 / 4.1 / 4.5-4.8 / 5.0e8 events/s).  This maximises
+# events/s, not relaxation: with the tiles fixed for eight ECs the middle
+# beads' g1 grows about 22 % slower per device-second than at two ECs per
+# tile, and 22^3 tiles at one or two ECs per tile relax fastest.
 C5_LAUNCH = dict(lanes=8, tiles=(25, 25, 25), cell_side=1.05, ecs_per_tile=8, block_tiles=8,
                  tight_factor=1.0)
 # the plain FP64 kernel on the same melt (its tuner's lanes and cell side,
