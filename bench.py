@@ -465,7 +465,7 @@ def run_gpu(args, rank, world):
     if fig3 is not None:
         line["init_fig3"] = fig3
     if args.cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline_run(max_sweeps=1)
+        line["cpu_baseline"] = cpu_baseline_run(steps=2)
         line["cpu_baseline"]["all_cores"] = cpu_allcore_run(sweeps=1)
         if prec_state is not None:
             line["precision"].update(precision_vs_oracle(prec_state))
@@ -813,13 +813,67 @@ def init_run():
                        "ECs of length 2, plain FP64 kernel, 32 lanes per tile"}
 
 
+ORC_PARTS = 8  # one-core oracle samples run the tiles t % 8 == 0 of each sweep
+
+
+def oracle_c5(r, img=None, p_swap=0.0, parts=ORC_PARTS, rem=0):
+    """The oracle on the 10^6-bead melt in the timed launch's tiling (the
+    pinned tiles and ECs per tile), running the tiles t % parts == rem of
+    each sweep (tiles are independent within a sweep: a part does exactly
+    the serial sweep's work on those tiles)."""
+    import oracle
+    st = launch_settings_default()
+    return oracle.System(r, C5.L, C5.N, mode=oracle.MODE_DOMAIN, dir_mode=oracle.DIR_ISO,
+                         D=tuple(st["tiles"]), seed=C5.seed, img=img, p_swap=p_swap,
+                         ecs_per_tile=st["ecs_per_tile"], tile_mod=parts, tile_rem=rem)
+
+
+def launch_settings_default():
+    """The timed screened setting of this workload without command-line
+    overrides (the pinned one for the 1e6-bead melt)."""
+    st = dict(C5_LAUNCH)
+    if C5.name != "c5_swap_1m":
+        st.update(tiles=TILES, ecs_per_tile=1, cell_side=1.05)
+    return st
+
+
+def oracle_rate(steps, warmup):
+    """Events/s of the oracle as it stands (serial FP64 C, one core) on
+    bounded samples of the timed workload: from the lattice start, warm-up
+    sweeps with swaps off (the last one calibrates p_swap for 0.1 attempts
+    per bead per sweep from its contacts, as ecmc_swap does), then `steps`
+    timed sweeps with swaps, each running 1/8 of the tiles (a new random
+    shift every sweep).  Returns (events/s, events, seconds, p_swap)."""
+    r = oracle_lattice_c5()
+    o = oracle_c5(r)
+    sweep = 0
+    res = None
+    for _ in range(max(int(warmup), 1)):
+        res = o.run_domain(1, ELL, sweep0=sweep)
+        sweep += 1
+    contacts = res["stats"]["hs_lift"] + res["stats"]["swap"]
+    p = min(1.0, SWAP_RATE * (C5.n / ORC_PARTS) / contacts) if contacts else 0.0
+    o = oracle_c5(o.r, img=o.img, p_swap=p)
+    t0 = time.perf_counter()
+    ev = 0
+    for _ in range(int(steps)):
+        res = o.run_domain(1, ELL, sweep0=sweep)
+        ev += res["stats"]["events"]
+        sweep += 1
+    dt = time.perf_counter() - t0
+    return ev / dt, ev, dt, p
+
+
+def oracle_lattice_c5():
+    import oracle
+    return oracle.lattice(C5.dims, C5.spacing, C5.jitter, C5.seed)
+
+
 def _oracle_part(k, parts, sweeps):
     """One process of the all-core oracle timing: tiles t % parts == k of
-    `sweeps` sweeps of the 1e6-bead melt; returns (events, seconds)."""
-    import oracle
-    r = oracle.lattice(C5.dims, C5.spacing, C5.jitter, C5.seed)
-    o = oracle.System(r, C5.L, C5.N, mode=oracle.MODE_DOMAIN, dir_mode=oracle.DIR_ISO,
-                      D=TILES, seed=C5.seed, tile_mod=parts, tile_rem=k)
+    `sweeps` sweeps of the 1e6-bead melt (timed tiling, swaps off); returns
+    (events, seconds)."""
+    o = oracle_c5(oracle_lattice_c5(), parts=parts, rem=k)
     t0 = time.perf_counter()
     res = o.run_domain(sweeps, ELL)
     return res["stats"]["events"], time.perf_counter() - t0
@@ -838,8 +892,9 @@ def cpu_allcore_run(sweeps=1):
     ev = sum(e for e, _ in out)
     dt = max(t for _, t in out)
     return {"value": ev / dt, "unit": UNIT, "cores": parts, "kind": "oracle",
-            "sample": f"{sweeps} sweep(s) of the 1e6-bead melt without swaps, its tiles split "
-                      f"over {parts} processes ({ev} events, slowest part {dt:.1f} s)"}
+            "sample": f"{sweeps} sweep(s) of the 1e6-bead melt in the timed tiling without swaps, "
+                      f"its tiles split over {parts} processes ({ev} events, slowest part "
+                      f"{dt:.1f} s)"}
 
 
 # the paper's Fig. 3 initial configuration (Sec. II.B): M = 500 phantom
@@ -885,17 +940,15 @@ def fig3_run(stream):
     return res
 
 
-def cpu_baseline_run(max_sweeps=1, time_budget=25.0):
-    """The oracle as it stands (serial FP64 C, one core) on a bounded sample:
-    `max_sweeps` full sweeps of the same 10^6-bead workload."""
+def cpu_baseline_run(steps=2):
+    """The oracle as it stands (serial FP64 C, one core) on a bounded sample
+    of the timed workload (oracle_rate: one warm-up sweep, `steps` timed
+    sweeps of 1/8 of the tiles each), then the structure pass and the
+    init leg's push-off."""
     import oracle
-    r = oracle.lattice(C5.dims, C5.spacing, C5.jitter, C5.seed)
-    o = oracle.System(r, C5.L, C5.N, mode=oracle.MODE_DOMAIN, dir_mode=oracle.DIR_ISO,
-                      D=TILES, seed=C5.seed)
-    t0 = time.perf_counter()
-    res = o.run_domain(max_sweeps, ELL)
-    dt = time.perf_counter() - t0
-    ev = res["stats"]["events"]
+    v, ev, dt, p = oracle_rate(steps, 1)
+    o = oracle.System(oracle_lattice_c5(), C5.L, C5.N, mode=oracle.MODE_DOMAIN,
+                      dir_mode=oracle.DIR_ISO, D=TILES, seed=C5.seed)
     t1 = time.perf_counter()
     o.chain_struct(dR=2.0, nbins=64)
     ds = time.perf_counter() - t1
@@ -907,9 +960,9 @@ def cpu_baseline_run(max_sweeps=1, time_budget=25.0):
                        dir_mode=oracle.DIR_ISO, D=c["tiles"], seed=c["po_seed"], img=ip)
     rc, po_sweeps, _ = po.pushoff(c["f0"], c["stages"], c["ell"], c["max_sweeps"])
     dp = time.perf_counter() - t2
-    return {"value": ev / dt, "unit": UNIT, "cores": 1, "host_cores": os.cpu_count(), "kind": "oracle",
-            "sample": f"{max_sweeps} sweep(s) of the 1e6-bead melt without swaps "
-                      f"({ev} events, {dt:.1f} s)",
+    return {"value": v, "unit": UNIT, "cores": 1, "host_cores": os.cpu_count(), "kind": "oracle",
+            "sample": f"{steps} sweep(s) of 1/{ORC_PARTS} of the 1e6-bead melt's tiles in the "
+                      f"timed tiling, swaps at p_swap = {p:.4g} ({ev} events, {dt:.1f} s)",
             "structure_ms": 1e3 * ds,
             "structure_sample": "one chain-structure pass (gyration tensors, R^2(n), W(R)) "
                                 "over the same melt",
@@ -918,33 +971,24 @@ def cpu_baseline_run(max_sweeps=1, time_budget=25.0):
 
 
 def run_reference(args, rank):
+    """The reference arm: the oracle as it stands, on one host core, on
+    bounded samples of the timed workload (oracle_rate)."""
     if rank != 0:
         return None
     import oracle
     oracle.build()
-    r = oracle.lattice(C5.dims, C5.spacing, C5.jitter, C5.seed)
-    o = oracle.System(r, C5.L, C5.N, mode=oracle.MODE_DOMAIN, dir_mode=oracle.DIR_ISO,
-                      D=TILES, seed=C5.seed)
-    sweep = 0
-    for _ in range(args.warmup if args.warmup < 1 else 1):
-        o.run_domain(1, ELL, sweep0=sweep)
-        sweep += 1
-    t0 = time.perf_counter()
-    ev = 0
-    for _ in range(args.steps):
-        res = o.run_domain(1, ELL, sweep0=sweep)
-        ev += res["stats"]["events"]
-        sweep += 1
-    dt = time.perf_counter() - t0
-    v = ev / dt
+    v, ev, dt, p = oracle_rate(args.steps, args.warmup)
+    st = launch_settings_default()
     return {"metric": METRIC, "value": v, "unit": UNIT, "n_gpus": 0, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "impl": "reference",
-            "config": {"workload": C5.name, "tiles": list(TILES), "ell": ELL,
-                       "sample": "full sweeps without swaps, one core"},
+            "config": {"workload": C5.name, "tiles": list(st["tiles"]), "ell": ELL,
+                       "ecs_per_tile": st["ecs_per_tile"], "p_swap": p,
+                       "sample": f"each step 1/{ORC_PARTS} of the tiles of a sweep, one core"},
             "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
-                             "sample": f"{args.steps} sweep(s) of the 1e6-bead melt"},
+                             "sample": f"{args.steps} sweep(s) of 1/{ORC_PARTS} of the "
+                                       f"1e6-bead melt's tiles ({ev} events)"},
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
 
