@@ -291,6 +291,9 @@ def run_gpu(args, rank, world):
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
     for _ in range(args.warmup):
         ctx.run(ELL, seed=seed, n_sweeps=1)
+        # re-calibrated on the latest sweep: the contacts per sweep fall while
+        # the lattice start melts
+        ctx.swap(SWAP_RATE)
     ctx.g1_reset()
     o0 = ctx.observables()
     torch.cuda.synchronize()

@@ -288,10 +288,11 @@ ecmc_status ecmc_run(ecmc_ctx *ctx, double ell, int64_t chains_per_sweep,
 
 /* Swap moves (Sec. II.C).  Sets p_swap so that the swap attempts per bead
  * per sweep match the target, from the motile hard-sphere contacts counted
- * during the last ecmc_run call (run it with p_swap = 0, on the state and
- * launch setting to be calibrated; push-off, autotuning and restore start
- * no such run): p_swap = min(1, target * n_beads * sweeps / contacts), with
- * sweeps and contacts of that run.  target 0 disables swaps.  ECMC_EINVAL
+ * during the last ecmc_run call (contacts are counted with or without
+ * swaps: each one lifts or swaps; run on the state and launch setting to be
+ * calibrated; push-off, autotuning and restore start no such run):
+ * p_swap = min(1, target * n_beads * sweeps / contacts), with sweeps and
+ * contacts of that run.  target 0 disables swaps.  ECMC_EINVAL
  * when no run with contacts came before. */
 ecmc_status ecmc_swap(ecmc_ctx *ctx, double attempts_per_bead_per_sweep);
 
