@@ -231,15 +231,21 @@ __device__ __forceinline__ void set_status(int *st, int code) { atomicCAS(st, 0,
 // Bounds checks of the checked build (-DECMC_CHECKED): CHK(i, n, site, st)
 // is true when 0 <= i < n; otherwise it records DEV_BOUNDS | site << 8 in
 // the status word st (first failure wins) and is false, and the caller
-// skips the access.  In the normal build it is the constant true.
+// skips the access.  CI(i, ...) is i, or 0 after a failed check; it
+// evaluates i once (the index can be an atomic's result).  In the normal
+// build CHK is the constant true and CI the index itself.
 #ifdef ECMC_CHECKED
 __device__ __forceinline__ bool chk_range(long long i, long long n, int site, int *st) {
   if (i >= 0 && i < n) return true;
   atomicCAS(st, 0, DEV_BOUNDS | (site << 8));
   return false;
 }
+template <class T>
+__device__ __forceinline__ T chk_index(T i, long long n, int site, int *st) {
+  return chk_range((long long)i, n, site, st) ? i : T(0);
+}
 #define CHK(i, n, site, st) chk_range((long long)(i), (long long)(n), (site), (st))
-#define CI(i, n, site, st) (CHK((i), (n), (site), (st)) ? (i) : 0)
+#define CI(i, n, site, st) chk_index((i), (long long)(n), (site), (st))
 #else
 #define CHK(i, n, site, st) true
 #define CI(i, n, site, st) (i)

@@ -188,7 +188,10 @@ __global__ void __launch_bounds__(128, 3) ec_lock_kernel(const ECParams P) {
     bool over = false;
     stage_tile<G, true, BATCH>(P, rp, st, gl, live, unit, c0, c1, c2, Rr, Rstart, S, 0, MNB, NC, LG,
                                m, j1, ns, gmask, P.defer_mode == 1 ? &over : nullptr);
-    if (over && gl == 0) P.deferred[CI(atomicAdd(P.n_deferred, 1), P.n_units, 32, P.status)] = gu;
+    if (over && gl == 0) {
+      const int at = atomicAdd(P.n_deferred, 1);
+      P.deferred[CI(at, P.n_units, 32, P.status)] = gu;
+    }
     if (!live) m = 0;
     if (gl == 0) {
       TileRec &T = tr[gib];
