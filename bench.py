@@ -79,6 +79,8 @@ LAUNCH = None
 # (5,340 beads: 0.96 s at 32 lanes, 1.30 s at 16, 1.90 s at 8; the same
 # sweeps and positions)
 PO_LANES = 32
+# untimed sweeps that melt the lattice start before tuning and timing
+MELT_SWEEPS = 20
 
 
 def bytes_per_event(phi, confirmed_per_event, fp32f=True):
@@ -269,10 +271,11 @@ def run_gpu(args, rank, world):
         ctx.set_stream(stream.cuda_stream)
         st = dict(LAUNCH[precision == ecmc.PREC_FP32F])
         configure(ctx, precision, st)
-        # melt the lattice start a little first: trials on the lattice
-        # itself are not representative (its tiles overflow the tight
-        # staging capacities)
-        ctx.run(ELL, seed=seed, n_sweeps=3)
+        # melt the lattice start first: its contacts per sweep fall by a third
+        # over the first ~20 sweeps, so tuner trials, the swap calibration
+        # and the timed sweeps on the lattice itself would not describe the
+        # melt (and its tiles overflow the tight staging capacities)
+        ctx.run(ELL, seed=seed, n_sweeps=MELT_SWEEPS)
         tune = ctx.autotune(ELL, seed=seed, trial_sweeps=3) if args.tune else None
         if tune and args.time_tuned:
             st = {"lanes": tune["lanes"], "tiles": tuple(tune["tiles"]),
