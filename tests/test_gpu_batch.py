@@ -97,3 +97,41 @@ def test_batch_graph_equals_plain_launches():
     for r in range(len(specs)):
         assert (a.get_positions(r)[0] == c.get_positions(r)[0]).all()
     assert a.stats()["events_total"] == c.stats()["events_total"]
+
+
+def test_batch_full_256_replicas_sampled():
+    """The whole 256-replica workload (4.7 M beads) in the batch, in the
+    launch setting the benchmark's tuner picks for it (8 lanes, 3.4-sigma
+    tiles, 8 ECs per tile, 8 tiles per block, first-pass factor 1.16), one
+    graph-replayed sweep after one plain sweep; every 32nd replica and the
+    largest one against the oracle, event for event, with their positions
+    and images."""
+    ms = replica_specs()
+    specs = [dict(dims=m.dims, spacing=m.spacing, N=m.N) for m in ms]
+    ell, jitter = ms[0].ell, ms[0].jitter
+    b = ecmc.Batch(specs, jitter=jitter, seed=SEED)
+    b.configure(dir_mode=ecmc.DIR_ISO, precision=ecmc.PREC_FP32F, lanes=8, tile_side=3.4,
+                ecs_per_tile=8, block_tiles=8, tight_factor=1.16, record=1)
+    sweeps = 2
+    b.run(ell, seed=SEED, n_sweeps=1, graph=False)
+    b.run(ell, seed=SEED, n_sweeps=1, graph=True)
+    units = sum(int(np.prod(b.info(r)[0])) for r in range(len(specs)))
+    dig, _, _ = b.records(units * 8)
+    assert len(dig) == units * 8  # the records of the last run (one sweep)
+    sample = sorted(set(range(0, len(ms), 32)) | {int(np.argmax([m.n for m in ms]))})
+    for r in sample:
+        sp = specs[r]
+        tiles, off, nb = b.info(r)
+        nt = int(np.prod(tiles))
+        L = tuple(d * sp["spacing"] for d in sp["dims"])
+        o = oracle.System(oracle.lattice(sp["dims"], sp["spacing"], jitter, SEED, replica=r), L,
+                          sp["N"], mode=oracle.MODE_DOMAIN, dir_mode=oracle.DIR_ISO, D=tiles,
+                          seed=SEED, replica=r, ecs_per_tile=8)
+        o.run_domain(1, ell)
+        res = o.run_domain(1, ell, sweep0=1, digests=True)
+        assert res["rc"] == 0
+        mine = dig[off * 8: (off + nt) * 8]
+        assert (mine == res["digest"]).all(), (r, np.nonzero(mine != res["digest"])[0][:5])
+        x, img = b.get_positions(r)
+        assert (x == o.r).all() and (img == o.img).all(), r
+    b.close()
