@@ -8,6 +8,8 @@ equal the oracle's bit for bit, in the serial and the domain form, plain
 FP64 and FP32-screened, for every lane count.  k = 30 kT/sigma^2 is the
 paper's stiffness; k = 2 stretches bonds far beyond the tether halo, so the
 staging has to fetch bonded beads from anywhere in the box."""
+import math
+
 import numpy as np
 import pytest
 
@@ -175,3 +177,23 @@ def test_springs_refuse_swaps_batch_and_pushoff():
     with pytest.raises(ecmc.EcmcError):
         b.configure(dir_mode=ecmc.DIR_ISO, k_spring=30.0)
     b.close()
+
+
+def test_springs_system_one_size_matches_oracle():
+    """48,000 beads (400 chains x N = 120 at packing fraction 0.39, the size
+    and density of the paper's System I) as a lattice melt, in the
+    benchmark's springs setting (FP32 screen, 8 lanes, 4 ECs per tile,
+    k = 30 kT/sigma^2, 4.4-sigma tiles): two sweeps against the oracle,
+    event for event, with positions, images and counts."""
+    a = (math.pi / (6.0 * 0.39)) ** (1.0 / 3.0)
+    m = Melt("system_one_lattice", (40, 40, 30), a, 120, ell=10.0, seed=0xEC00D1, mode="domain",
+             dir_mode="iso", sweeps=2, D=(10, 10, 7))
+    o = oracle_system(m, k_spring=30.0, ecs_per_tile=4)
+    res = o.run_domain(m.sweeps, m.ell, digests=True)
+    assert res["rc"] == 0
+    ctx = gpu_context(m, precision=ecmc.PREC_FP32F, lanes=8, k_spring=30.0, ecs_per_tile=4)
+    ctx.run(m.ell, seed=m.seed, n_sweeps=m.sweeps)
+    dig, _, _ = ctx.records(m.sweeps * 700 * 4)
+    assert (dig == res["digest"]).all(), np.nonzero(dig != res["digest"])[0][:5]
+    assert_same_state(ctx, o)
+    assert_same_counts(ctx, res)
