@@ -216,8 +216,11 @@ ecmc_status ecmc_phantom_chains(const double L[3], int64_t n_chains, int32_t N, 
  * runs one EC of length ell from each of its motile beads that overlaps
  * another bead (|r_ij|^2 < d^2 (1 - 1e-10)), in bead id order, with the
  * direction draw of EC e as in ecmc_run and the pivot ignoring the beads it
- * overlaps, until no overlap is left.  Sweeps continue the context's sweep
- * count (Philox counters as in ecmc_run with `seed`); swaps are off.
+ * overlaps, until no overlap is left.  With bead springs configured
+ * (k_spring > 0) the springs act during the push-off with rest length d, the
+ * current diameter (every length of the model grows together).  Sweeps
+ * continue the context's sweep count (Philox counters as in ecmc_run with
+ * `seed`); swaps are off.
  * *sweeps_out (may be NULL) receives the sweeps run.  ECMC_ESTUCK if a
  * diameter is not resolved within max_sweeps sweeps; the final state is
  * checked as ecmc_set_positions checks it. */

@@ -1047,7 +1047,6 @@ ecmc_status ecmc_pushoff(ecmc_ctx *c, double f0, int32_t stages, double ell, uin
   if (sweeps_out) *sweeps_out = 0;
   if (!c->configured || c->opts.mode != ECMC_MODE_DOMAIN || c->opts.precision != ECMC_PREC_FP64)
     return fail(ECMC_EINVAL, "push-off needs the domain mode and FP64");
-  if (c->opts.k_spring > 0.0) return fail(ECMC_EINVAL, "push-off runs hard tethers (k_spring must be 0)");
   if (!(f0 > 0.0 && f0 <= 1.0) || stages < 1 || max_sweeps < 1 || !(ell >= 0.0 && ell < INFINITY))
     return fail(ECMC_EINVAL, "need 0 < f0 <= 1, stages >= 1, max_sweeps >= 1, finite ell >= 0");
   if (!c->d_po_flag) {

@@ -162,7 +162,7 @@ def test_soft_springs_stage_partners_beyond_the_halo(prec):
     assert obs["bond_mean"] == pytest.approx(float(bonds.mean()), rel=1e-12)
 
 
-def test_springs_refuse_swaps_batch_and_pushoff():
+def test_springs_refuse_swaps_and_batch():
     m = small_domain()
     ctx = gpu_context(m)
     with pytest.raises(ecmc.EcmcError):
@@ -171,8 +171,6 @@ def test_springs_refuse_swaps_batch_and_pushoff():
     with pytest.raises(ecmc.EcmcError):
         ctx.configure(mode=ecmc.MODE_DOMAIN, dir_mode=ecmc.DIR_ISO, tiles=m.D, k_spring=-1.0)
     ctx.configure(mode=ecmc.MODE_DOMAIN, dir_mode=ecmc.DIR_ISO, tiles=m.D, k_spring=30.0)
-    with pytest.raises(ecmc.EcmcError):
-        ctx.pushoff(max_sweeps=10)
     b = ecmc.Batch([dict(dims=(12, 12, 12), spacing=1.05, N=8)], jitter=0.01, seed=1)
     with pytest.raises(ecmc.EcmcError):
         b.configure(dir_mode=ecmc.DIR_ISO, k_spring=30.0)
