@@ -653,8 +653,10 @@ def springs_run(stream, steps):
            "ecs_per_tile": c["ecs_per_tile"], "steps": steps}
     ctx = ecmc.Context.create_phantom(L, c["n_chains"], c["N"], bond=1.0, c=c["c"], seed=c["seed"])
     ctx.set_stream(stream.cuda_stream)
+    # the push-off with the springs acting (the paper builds its spring melts
+    # this way)
     ctx.configure(mode=ecmc.MODE_DOMAIN, dir_mode=ecmc.DIR_ISO, precision=ecmc.PREC_FP64,
-                  tiles=c["tiles"], lanes=PO_LANES)
+                  tiles=c["tiles"], lanes=PO_LANES, k_spring=c["k"])
     t0 = time.perf_counter()
     res["pushoff_sweeps"] = ctx.pushoff(f0=0.5, stages=5, ell=2.0, seed=c["po_seed"],
                                         max_sweeps=c["max_sweeps"])
