@@ -10,11 +10,11 @@ import pytest
 import oracle
 
 
-def phantom_system(eta, N, L, seed, c=1.9, D=(3, 3, 3)):
+def phantom_system(eta, N, L, seed, c=1.9, D=(3, 3, 3), k_spring=0.0):
     nch = int(round(eta * L ** 3 * 6 / np.pi / N))
     r, img = oracle.phantom_chains((L, L, L), nch, N, bond=1.0, c=c, seed=seed)
     s = oracle.System(r, (L, L, L), N, sigma=1.0, b_max=1.2, mode=oracle.MODE_DOMAIN,
-                      dir_mode=oracle.DIR_ISO, D=D, seed=seed + 100, img=img)
+                      dir_mode=oracle.DIR_ISO, D=D, seed=seed + 100, img=img, k_spring=k_spring)
     return s, r.copy(), img.copy()
 
 
@@ -80,3 +80,27 @@ def test_overlap_flags_brute_force(L, d):
     np.fill_diagonal(dd, np.inf)
     ref = (dd < d * d * (1.0 - 1e-10)).any(axis=1)
     assert (flag.astype(bool) == ref).all() and m == ref.sum()
+
+
+def test_pushoff_with_springs_resolves_a_melt():
+    """With bead springs (k = 30) acting during the push-off (rest length the
+    current diameter): no overlap at sigma when it ends, bonded beads no
+    closer than sigma either, bonds stretched beyond the tether length only
+    a little (the springs are stiff: the free-bond law gives <b> = 1.168
+    sigma at k = 30), images following the moves, and chain statistics near
+    the phantom's."""
+    s, r0, img0 = phantom_system(0.40, 16, 14.0, 53, k_spring=30.0)
+    assert s.overlap_flags(1.0)[1] > 100
+    r2n0 = oracle.System(r0, s.L, 16, img=img0).chain_struct()["r2n"]
+    rc, sweeps, st = s.pushoff(0.5, 4, 2.0, 6000)
+    assert rc == 0 and sweeps > 0
+    dmin, n_ov = s.min_pair()
+    assert n_ov == 0 and dmin * dmin >= 1.0 - 1e-10
+    _, bonds = s.chain_obs()
+    assert bonds.min() >= np.sqrt(1.0 - 1e-10)
+    assert 1.0 < bonds.mean() < 1.3 and bonds.max() < 2.0
+    r2n1 = s.chain_struct()["r2n"]
+    for n in (5, 10, 15):
+        assert r2n1[n] == pytest.approx(r2n0[n], rel=0.3)
+    u = s.unwrapped().reshape(-1, 16, 3)
+    assert np.allclose(np.linalg.norm(np.diff(u, axis=1), axis=2).ravel(), bonds, rtol=1e-9)
