@@ -351,6 +351,9 @@ def run_gpu(args, rank, world):
     init = init_run() if args.extra else None
     precision, prec_state = precision_run(args, stream) if extra else (None, None)
     springs = springs_run(stream, max(3, args.steps // 2)) if extra else None
+    systems = ({name: springs_run(stream, max(3, args.steps // 2), name)
+                for name in args.systems.split(",") if name and name != "I"}
+               if extra and args.systems else None)
     reptation = reptation_run(stream) if extra else None
     fig3 = fig3_run(stream) if extra else None
 
@@ -466,6 +469,8 @@ def run_gpu(args, rank, world):
         line["precision"] = precision
     if springs is not None:
         line["springs"] = springs
+    if systems:
+        line["springs_systems"] = systems
     if reptation is not None:
         line["reptation"] = reptation
     if fig3 is not None:
@@ -635,20 +640,27 @@ def precision_vs_oracle(state):
 # packing fraction 0.390 in a 40^3 box, k = 30 kT/sigma^2, built as the paper
 # builds its melts (phantom chains, c = 1.9, pushed off with tethers)
 SPRINGS = dict(L=40.0, n_chains=400, N=120, c=1.9, seed=61, po_seed=0xEC1F0F, k=30.0, ell=10.0,
-               tiles=(9, 9, 9), ecs_per_tile=4, max_sweeps=20000)
+               tiles=(9, 9, 9), ecs_per_tile=4, max_sweeps=40000)
+# the paper's Systems I-III (M chains of N beads in a 40^3 box, k = 30):
+# eta = 0.390, 0.490, 0.490
+SYSTEMS = {"I": dict(n_chains=400, N=120), "II": dict(n_chains=500, N=120),
+           "III": dict(n_chains=250, N=240)}
 
 
-def springs_run(stream, steps):
-    """Bead-spring melt of the paper's System I size through the public API:
-    phantom chains and slow push-off (outside the timed region), then EC
-    sweeps with harmonic bonds, FP32-screened and plain FP64, each timed
-    with CUDA events on the launching stream."""
+def springs_run(stream, steps, system="I"):
+    """Bead-spring melt of the paper's System I (or II, III) size through
+    the public API: phantom chains and slow push-off with the springs acting
+    (outside the timed region), then EC sweeps with harmonic bonds,
+    FP32-screened and plain FP64, each timed with CUDA events on the
+    launching stream."""
     import torch
 
     from paper_1502_06447_gb300 import ecmc
-    c = SPRINGS
+    c = dict(SPRINGS, **SYSTEMS[system])
     L = (c["L"],) * 3
-    res = {"workload": "System I size: 400 chains x N = 120, eta = 0.390, 40^3 box, k = 30 kT/sigma^2",
+    eta = c["n_chains"] * c["N"] * math.pi / 6.0 / c["L"] ** 3
+    res = {"workload": f"System {system} size: {c['n_chains']} chains x N = {c['N']}, "
+                       f"eta = {eta:.3f}, 40^3 box, k = 30 kT/sigma^2",
            "beads": c["n_chains"] * c["N"], "ell": c["ell"], "tiles": list(c["tiles"]),
            "ecs_per_tile": c["ecs_per_tile"], "steps": steps}
     ctx = ecmc.Context.create_phantom(L, c["n_chains"], c["N"], bond=1.0, c=c["c"], seed=c["seed"])
@@ -1029,6 +1041,8 @@ def main():
                     help="time the autotuner's pick of this run instead of the pinned setting")
     ap.add_argument("--no-batch", dest="batch", action="store_false",
                     help="skip the batched-replicas measurement")
+    ap.add_argument("--systems", default="",
+                    help="also run the paper's Systems II, III (comma list, e.g. II,III)")
     ap.add_argument("--no-extra", dest="extra", action="store_false",
                     help="skip the legs beside the headline melt (structure, initial "
                          "configurations, precision form, springs, reptation)")
